@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 HSMA hot path (arXiv:1907.01724, Algorithm 1 steps 4-5).
+
+Workload (default): two cavities of N = 2000 unit charges, 25% within 0.05a of the interface,
+eps1 = 1, eps2 = 80, kappa a in {0.5, 2}, M = 1000 points per shell, p = 20, FP32 pair sums
+with FP64 coefficient/surface/reduction steps.  Both cavities form one batch: one step = the
+whole hot path for both (per-system scalars, Kelvin images, correction coefficients, surface
+images, the tiled pair sum, the FP64 potential/energy reduction) as two CUDA-graph launches.
+
+Metric: Coulomb pair-evaluations per second, counting per cavity N (2N - 1 + 3M) pairs (every
+charge against the other real charges, the N Kelvin images and the 3M surface images of
+eq. phicorrfinall).  Inputs are seeded synthetic data (random charges in the ball, the
+paper's workload type).  L2 is flushed (256 MB write) before every timed step, outside the
+timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own independent cavities (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1907_01724_gb300 import inputs  # noqa: E402
+
+SM_MUFU_PER_CLK = 16  # rsqrt results per SM per clock (one pair evaluation each)
+METRIC = "Coulomb pair-evals/s at rel err <=1e-6 vs FP64"
+
+
+def workload(rank: int):
+    off = 1000 * rank
+    return [inputs.near_interface_system(kappa_a=0.5, seed_offset=off),
+            inputs.near_interface_system(kappa_a=2.0, seed_offset=off)]
+
+
+def pairs(s) -> int:
+    return s.n * (2 * s.n - 1 + 3 * s.M)
+
+
+def evals(s) -> int:
+    """Kernel pair evaluations (one rsqrt each): a surface point carries monopole + dipole."""
+    return s.n * (2 * s.n - 1 + s.M)
+
+
+def config_dict(systems, n_gpus):
+    s = systems[0]
+    return {"workload": f"2 cavities N={s.n} (25% within 0.05a of the interface), eps1=1, eps2=80, "
+                        f"kappa*a in {{0.5,2}}, M={s.M}, p={s.p}, tau=0.1, FP32 pair sums",
+            "systems_per_gpu": len(systems), "N": s.n, "M": s.M, "p": s.p,
+            "pairs_per_step_per_gpu": int(sum(pairs(x) for x in systems)),
+            "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{n_gpus}"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce(world, x: float, op: str) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_run(systems, budget_s: float = 10.0, max_rounds: int = 50):
+    """FP64 oracle over the whole workload, repeated until about budget_s of CPU work."""
+    import oracle
+    t0 = time.perf_counter()
+    done = 0
+    rounds = 0
+    refs = None
+    while True:
+        out = []
+        for s in systems:
+            P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+            out.append(oracle.hsma(P, s.xyz, s.q))
+            done += pairs(s)
+        refs = refs or out
+        rounds += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or rounds >= max_rounds:
+            break
+    return refs, done / el, el, rounds, oracle.threads()
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1907_01724_gb300 import api, batch
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    systems = workload(rank)
+
+    # oracle baseline first (rank 0), before any GPU timing; its results also check accuracy
+    cpu = None
+    refs = None
+    if rank == 0:
+        refs, cpu_rate, cpu_s, rounds, threads = oracle_run(systems, budget_s=0.0 if args.no_cpu_baseline else 10.0,
+                                                            max_rounds=1 if args.no_cpu_baseline else 50)
+        if world == 1:
+            cpu = {"value": cpu_rate, "unit": "pair-evals/s", "cores": threads, "kind": "oracle",
+                   "sample": f"full workload (both cavities, build + potentials + energy) x{rounds}, {cpu_s:.1f} s"}
+
+    n, xyz, q = batch.concat(systems)
+    b = batch.from_systems(systems, precision=api.HSMA_FP32, device=local, stream=stream)
+    gpu_name = torch.cuda.get_device_name(local)
+    cfg = batch.autotuned(b, n, xyz, q, gpu=gpu_name, reps=5)
+    xyz_d = torch.tensor(xyz, device=dev)
+    q_d = torch.tensor(q, device=dev)
+    phi_d = torch.empty(int(n.sum()), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(bb):
+        bb.hsma_batch_build_sources(n, xyz_d, q_d)
+        bb.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
+
+    for _ in range(args.warmup):
+        step(b)
+    torch.cuda.synchronize()
+    acc = None
+    if refs is not None:
+        phi = b.hsma_batch_potential(api.HSMA_TOTAL)
+        et, _ = b.hsma_batch_energy()
+        errs, off = [], 0
+        for s, r, e in zip(systems, refs, et):
+            p = phi[off:off + s.n]
+            off += s.n
+            scale = max(abs(r["E_total"]), 0.5 * float(np.sum(np.abs(s.q * r["phi"]))))
+            errs.append((np.linalg.norm(p - r["phi"]) / np.linalg.norm(r["phi"]), abs(e - r["E_total"]) / scale))
+        acc = {"phi_rel_l2_max": max(x[0] for x in errs), "energy_rel_max": max(x[1] for x in errs),
+               "reference": "FP64 oracle"}
+
+    launches0 = b.hsma_batch_kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pair_ms = []
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    sample_every = max(1, args.steps // 100)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step(b)
+        ev[k][1].record(stream)
+        if k % sample_every == 0:
+            pair_ms.append(b.hsma_batch_last_pair_time())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    launches = b.hsma_batch_kernel_launches() - launches0
+    t_local = sum(a.elapsed_time(c) for a, c in ev) / 1e3
+    t_max = allreduce(world, t_local, "max")
+    total_pairs = allreduce(world, float(sum(pairs(s) for s in systems) * args.steps), "sum")
+    value = total_pairs / t_max
+
+    # dominant kernel alone: evaluations per launch / event-timed launch duration
+    ev_per_launch = sum(evals(s) for s in systems)
+    t_pair = statistics.mean(pair_ms) / 1e3
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = sms * SM_MUFU_PER_CLK * sm_max * 1e6
+    achieved = ev_per_launch / t_pair
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-eval/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "k_pairs_f32",
+            "peak_basis": f"{sms} SMs x {SM_MUFU_PER_CLK} MUFU rsqrt/clk x {sm_max:.0f} MHz (max SM clock)",
+            "pair_kernel_ms": t_pair * 1e3, "pair_config": batch.pair_configs()[cfg],
+            "evals_per_launch": ev_per_launch}
+    if clk.get("sm_mhz"):
+        roof["frac_at_median_clock"] = achieved / (sms * SM_MUFU_PER_CLK * clk["sm_mhz"] * 1e6)
+
+    # plain FP64 path on the same GPU (comparator)
+    b64 = batch.from_systems(systems, precision=api.HSMA_FP64, device=local, stream=stream)
+    b64.hsma_batch_build_sources(n, xyz, q)
+    step(b64)
+    torch.cuda.synchronize()
+    k64 = max(3, min(30, args.steps // 50))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k64):
+        step(b64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    fp64 = {"value": sum(pairs(s) for s in systems) * k64 / t64, "unit": "pair-evals/s",
+            "ms_per_step": t64 / k64 * 1e3, "steps": k64}
+
+    # end to end through the C ABI with pinned host buffers: H2D of inputs, D2H of potentials
+    # and energies inside the timed region
+    xyz_h = torch.tensor(xyz).pin_memory().numpy()
+    q_h = torch.tensor(q).pin_memory().numpy()
+
+    def e2e_step():
+        b.hsma_batch_build_sources(n, xyz_h, q_h)
+        b.hsma_batch_potential(api.HSMA_TOTAL)
+        b.hsma_batch_energy()
+
+    for _ in range(3):
+        e2e_step()
+    ke = max(10, args.steps // 4)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        e2e_step()
+    torch.cuda.synchronize()
+    te = allreduce(world, time.perf_counter() - t0, "max")
+    e2e = {"value": allreduce(world, float(sum(pairs(s) for s in systems) * ke), "sum") / te,
+           "unit": "pair-evals/s", "h2d_bytes_per_step": int(32 * n.sum()),
+           "d2h_bytes_per_step": int(8 * n.sum() + 16 * len(systems)), "steps": ke,
+           "ms_per_step": te / ke * 1e3}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair sums (f64 coefficients/reduction)",
+                "data": "synthetic (seeded random charges in the ball, 25% near the interface)",
+                "config": config_dict(systems, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": int(launches), "accuracy_vs_oracle": acc, "fp64_path": fp64,
+                "impl": "ours"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    systems = workload(0)
+    # warm-up: one full pass (also measures the cost of a step)
+    t0 = time.perf_counter()
+    for s in systems:
+        P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+        oracle.hsma(P, s.xyz, s.q)
+    t_step = time.perf_counter() - t0
+    k = int(max(1, min(args.steps, math.ceil(60.0 / max(t_step, 1e-3)))))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        for s in systems:
+            P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+            oracle.hsma(P, s.xyz, s.q)
+    el = time.perf_counter() - t0
+    value = sum(pairs(s) for s in systems) * k / el
+    line = {"metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": k,
+            "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": el / k * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random charges in the ball, 25% near the interface)",
+            "config": config_dict(systems, 1), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "pair-evals/s", "kind": "oracle", "cores": oracle.threads(),
+                             "sample": f"full workload (both cavities) x{k} steps, bounded to about 60 s"},
+            "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

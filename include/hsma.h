@@ -1,0 +1,215 @@
+/*
+ * hsma.h -- C ABI of the GB300 (sm_103a) implementation of the harmonic surface mapping
+ * algorithm (HSMA) for electrostatic reaction potentials of a spherical cavity in a
+ * linearized Poisson-Boltzmann continuum (Fu & Gan, arXiv:1907.01724).
+ *
+ * The problem (Sec. 2.1): N point charges q_i at x_i inside the sphere |x| < a with
+ * dielectric constant eps1; outside, dielectric eps2 and inverse Debye length kappa.
+ * Inside, Phi_1 = Phi_Coul + Phi_RF (Sec. 2.2).  HSMA writes Phi_RF as a Coulomb sum over
+ * N trapezoid-modified Kelvin images plus 3M discrete surface images on the auxiliary
+ * sphere R_tau = (1+tau) a (Sec. 2.4, eq. phirffinall).  Every step runs in CUDA kernels
+ * on one GPU; no call falls back to the CPU.
+ *
+ * Conventions for every entry point:
+ *   - Return value: HSMA_OK (0) or a negative HSMA_E_* code.  No call aborts the process;
+ *     hsma_last_error() gives a one-line message for the failing handle.
+ *   - "host" pointers are ordinary CPU memory owned by the caller and only read/written
+ *     during the call; "device" pointers are CUDA global memory of the handle's device,
+ *     owned by the caller, accessed in stream order on the handle's stream.
+ *   - Positions are row-major (n, 3) float64 arrays, charges and potentials float64.
+ *   - Potentials are in units of coulomb_k * charge / length (coulomb_k = 1/(4 pi)
+ *     reproduces the paper's Phi = q / (4 pi eps1 r)).
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef HSMA_H
+#define HSMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HSMA_API __attribute__((visibility("default")))
+#else
+#define HSMA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HSMA_OK 0
+#define HSMA_E_INVALID_ARG (-1)   /* bad parameter, size or pointer */
+#define HSMA_E_OUTSIDE (-2)       /* a charge has |x_i| >= a, or a non-finite coordinate */
+#define HSMA_E_STATE (-3)         /* call out of order (e.g. potential before sources) */
+#define HSMA_E_OOM (-4)           /* device allocation failed or workspace too small */
+#define HSMA_E_CUDA (-5)          /* a CUDA runtime call failed */
+#define HSMA_E_TIMEOUT (-6)       /* a bounded device-side wait gave up */
+#define HSMA_E_BUSY (-7)          /* server queue full / no admission */
+#define HSMA_E_NONFINITE (-8)     /* non-finite potential (e.g. coincident charges) */
+
+/* precision of the pair sums */
+#define HSMA_FP32 0   /* FP32 pair sums (hi/lo split coordinates, compensated accumulation);
+                         FP64 coefficient, surface and reduction steps */
+#define HSMA_FP64 1   /* FP64 everywhere */
+
+/* which potential hsma_potential returns */
+#define HSMA_TOTAL 0      /* Phi_Coul (j != i) + Phi_RF */
+#define HSMA_REACTION 1   /* Phi_RF only */
+#define HSMA_COULOMB 2    /* Phi_Coul only */
+
+#define HSMA_P_MAX 80     /* largest truncation order p */
+
+/* Numerical parameters (Sec. 2.4 and Sec. 4). */
+typedef struct {
+  int p;            /* truncation order: n = 0..p (Sec. 2.4 eq. phim); 0 <= p <= HSMA_P_MAX */
+  int M;            /* quadrature points per shell, M = 2(F2+1) (Sec. 2.4, Fibonacci rule);
+                       ignored when F2 > 0 */
+  int F1, F2;       /* successive Fibonacci numbers; F2 = 0 derives F2 = M/2 - 1,
+                       F1 = round(F2 (sqrt5 - 1)/2) (gives 987 for 1597) */
+  double tau;       /* auxiliary sphere R_tau = (1 + tau) a, tau > 0 (Sec. 2.4) */
+  double dy_rel;    /* central-difference step dy = dy_rel * R_tau (Sec. 2.4 eq. approxG;
+                       Sec. 4 uses 1e-5) */
+  double coulomb_k; /* Coulomb prefactor; 1/(4 pi) = the paper's units */
+  int precision;    /* HSMA_FP32 or HSMA_FP64 */
+  int device;       /* CUDA device ordinal */
+  void* stream;     /* cudaStream_t for all work of the handle; NULL = a non-blocking stream
+                       that the handle creates and owns */
+} hsma_params;
+
+typedef struct hsma_t hsma_t;
+
+/* Fill *p with defaults: p=20, M=1000, tau=0.1, dy_rel=1e-5, coulomb_k=1/(4pi), FP32,
+ * device 0, NULL stream (the CPU-time parameters of Sec. 4.2, P=20, tau=0.1). */
+HSMA_API int hsma_default_params(hsma_params* p);
+
+/* Create a handle for one cavity of radius a (Sec. 2.1: eps1 inside, eps2 and kappa
+ * outside).  a > 0, eps1 > 0, eps2 > 0, kappa >= 0.  Allocates nothing on the device until
+ * sources are built.  *out receives the handle (caller destroys it). */
+HSMA_API int hsma_create(double a, double eps1, double eps2, double kappa, const hsma_params* params, hsma_t** out);
+
+/* Destroy a handle and free the device memory it owns (not an attached workspace). */
+HSMA_API void hsma_destroy(hsma_t* h);
+
+/* Last error message of a handle (static storage of the handle; never NULL). */
+HSMA_API const char* hsma_last_error(const hsma_t* h);
+
+/* Device workspace.  hsma_workspace_size returns in *bytes the device memory the handle
+ * needs for n charges; hsma_attach_workspace hands the handle caller-owned device memory
+ * (256-byte aligned, at least that size, alive until detached/destroyed) so that it never
+ * calls cudaMalloc itself (the Python binding passes memory from PyTorch's allocator).
+ * Without an attached workspace the handle allocates (and grows) its own. */
+HSMA_API int hsma_workspace_size(hsma_t* h, int64_t n, size_t* bytes);
+HSMA_API int hsma_attach_workspace(hsma_t* h, void* device_ptr, size_t bytes);
+
+/* Build the source set of eq. phirffinall for n charges (Sec. 2.4, Algorithm 1 step 4):
+ * trapezoid-modified Kelvin images (one per charge), the truncated correction
+ * coefficients, and the 3M monopole/dipole surface images on R_tau.  xyz: host (n,3),
+ * q: host (n).  Every |x_i| must be < a (else HSMA_E_OUTSIDE).  n >= 0.
+ * Asynchronous with respect to the host once the inputs are copied. */
+HSMA_API int hsma_build_sources(hsma_t* h, int64_t n, const double* xyz, const double* q);
+
+/* Same as hsma_build_sources with inputs already resident on the device. */
+HSMA_API int hsma_build_sources_device(hsma_t* h, int64_t n, const double* xyz_dev, const double* q_dev);
+
+/* Potentials at the n charges (Algorithm 1 step 5, by direct tiled summation):
+ * what = HSMA_TOTAL, HSMA_REACTION or HSMA_COULOMB.  phi: host array of n doubles.
+ * Synchronises the handle's stream; returns HSMA_E_NONFINITE for coincident charges. */
+HSMA_API int hsma_potential(hsma_t* h, double* phi, int what);
+
+/* Same, writing n doubles to device memory (stream-ordered; no host synchronisation). */
+HSMA_API int hsma_potential_device(hsma_t* h, double* phi_dev, int what);
+
+/* Energies (Sec. 4.1 generalised to N charges): E_total = 1/2 sum_i q_i [Phi_Coul(x_i) +
+ * Phi_RF(x_i)], E_reaction = 1/2 sum_i q_i Phi_RF(x_i) (either pointer may be NULL).
+ * Host doubles; synchronises the handle's stream. */
+HSMA_API int hsma_energy(hsma_t* h, double* e_total, double* e_reaction);
+
+/* Energy change of moving charge k to x_new (host double[3], |x_new| < a):
+ * *de = E_total(after) - E_total(before), from the resident state without rebuilding all
+ * sources (a Monte Carlo trial move; the paper's method is linear in the charges, Sec. 2.4).
+ * The state is unchanged. */
+HSMA_API int hsma_delta_energy(hsma_t* h, int64_t k, const double* x_new, double* de);
+
+/* Commit a move (an accepted Monte Carlo step): charge k is now at x_new.  Updates the
+ * resident sources incrementally; equivalent to rebuilding with the moved charge. */
+HSMA_API int hsma_apply_move(hsma_t* h, int64_t k, const double* x_new);
+
+/* Number of the library's kernel launches issued so far by this handle (for accounting). */
+HSMA_API int64_t hsma_kernel_launches(const hsma_t* h);
+
+/* Device time in milliseconds of the most recent pair-sum kernel launch of the handle (CUDA
+ * events recorded on the handle's stream just before and after that launch).  Synchronises
+ * the stream.  HSMA_E_STATE if no pair sum has run yet. */
+HSMA_API int hsma_last_pair_time(hsma_t* h, float* ms);
+
+/* Library version string. */
+HSMA_API const char* hsma_version(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched API: many independent cavities (each its own a, eps1, eps2, kappa and charge set;
+ * common numerical parameters) evaluated by the same kernels in single launches.  Arrays
+ * over systems are indexed s = 0..nsys-1; charges are concatenated in system order (system s
+ * owns n[s] consecutive rows).  With the same pair-sum tile configuration, each system's
+ * results are bitwise identical to evaluating it alone: its work split and summation order
+ * depend only on its own sizes, never on the other systems or on scheduling.
+ * --------------------------------------------------------------------------------------- */
+typedef struct hsma_batch_t hsma_batch_t;
+
+/* Create a batch of nsys cavities (host arrays of length nsys; the same constraints as
+ * hsma_create for each system). */
+HSMA_API int hsma_batch_create(int nsys, const double* a, const double* eps1, const double* eps2,
+                               const double* kappa, const hsma_params* params, hsma_batch_t** out);
+HSMA_API void hsma_batch_destroy(hsma_batch_t* b);
+HSMA_API const char* hsma_batch_last_error(const hsma_batch_t* b);
+
+/* Workspace for charge counts n[nsys] (host; the largest over all pair-sum tile
+ * configurations, so it also serves hsma_batch_autotune), and attaching caller-owned device
+ * memory, as for a single handle. */
+HSMA_API int hsma_batch_workspace_size(hsma_batch_t* b, const int64_t* n, size_t* bytes);
+HSMA_API int hsma_batch_attach_workspace(hsma_batch_t* b, void* device_ptr, size_t bytes);
+
+/* Reserve room for up to max_requests single-charge moves per call of hsma_batch_delta_energy
+ * / hsma_batch_apply_moves (default 1; takes effect at the next build). */
+HSMA_API int hsma_batch_set_max_requests(hsma_batch_t* b, int max_requests);
+
+/* Build all sources (Sec. 2.4) for n[nsys] charges per system: xyz (sum n, 3) and q (sum n),
+ * host or device memory respectively. */
+HSMA_API int hsma_batch_build_sources(hsma_batch_t* b, const int64_t* n, const double* xyz, const double* q);
+HSMA_API int hsma_batch_build_sources_device(hsma_batch_t* b, const int64_t* n, const double* xyz_dev,
+                                             const double* q_dev);
+
+/* Potentials of all charges (sum n doubles, concatenated), host or device output. */
+HSMA_API int hsma_batch_potential(hsma_batch_t* b, double* phi, int what);
+HSMA_API int hsma_batch_potential_device(hsma_batch_t* b, double* phi_dev, int what);
+
+/* Energies of every system: e_total[nsys], e_reaction[nsys] (host; either may be NULL). */
+HSMA_API int hsma_batch_energy(hsma_batch_t* b, double* e_total, double* e_reaction);
+
+/* Energy changes of nreq independent trial moves (system sys[r], charge k[r] moved to
+ * x_new[3r..3r+2]); de[r] receives E(after) - E(before) of that system alone.  Host arrays.
+ * The state is unchanged.  nreq <= the reserved maximum. */
+HSMA_API int hsma_batch_delta_energy(hsma_batch_t* b, int nreq, const int* sys, const int64_t* k,
+                                     const double* x_new, double* de);
+
+/* Commit nreq moves, at most one per system per call. */
+HSMA_API int hsma_batch_apply_moves(hsma_batch_t* b, int nreq, const int* sys, const int64_t* k,
+                                    const double* x_new);
+
+HSMA_API int64_t hsma_batch_kernel_launches(const hsma_batch_t* b);
+HSMA_API int hsma_batch_last_pair_time(hsma_batch_t* b, float* ms);
+
+/* Pair-sum tile configurations (CTA threads x targets per thread).  hsma_batch_set_pair_config
+ * forces one (-1 = automatic); hsma_batch_autotune times every configuration on the current
+ * sources (reps launches each, CUDA events) and keeps the fastest for this size class;
+ * *best and *best_ms (nullable) receive the choice and its time. */
+HSMA_API int hsma_pair_config_count(void);
+HSMA_API int hsma_pair_config_info(int idx, int* threads, int* targets_per_thread);
+HSMA_API int hsma_batch_set_pair_config(hsma_batch_t* b, int cfg);
+HSMA_API int hsma_batch_autotune(hsma_batch_t* b, int reps, int* best, float* best_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSMA_H */

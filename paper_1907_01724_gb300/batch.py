@@ -1,0 +1,226 @@
+"""Python binding of the batched C ABI (hsma_batch_* in include/hsma.h): argument marshalling only.
+
+A Batch evaluates many independent cavities (uneven N) with the same kernels in single
+launches; each system's results equal those of evaluating it alone.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+from . import _native
+from .api import HSMA_FP32, HSMA_TOTAL, HsmaError, hsma_default_params
+
+
+def _arr(x, dtype):
+    return np.ascontiguousarray(np.asarray(x, dtype=dtype))
+
+
+def _p(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+class Batch:
+    """hsma_batch_t with a PyTorch-allocated workspace."""
+
+    def __init__(self, a, eps1, eps2, kappa, params=None, max_requests: int = 1, use_torch_workspace: bool = True):
+        self.lib = _native.load()
+        self.params = params if params is not None else hsma_default_params()
+        self.nsys = len(a)
+        # keep every array alive across the call (ctypes holds only the addresses)
+        self._a = _arr(a, np.float64)
+        self._eps1 = _arr(eps1, np.float64)
+        self._eps2 = _arr(eps2, np.float64)
+        self._kappa = _arr(kappa, np.float64)
+        out = ctypes.c_void_p()
+        rc = self.lib.hsma_batch_create(self.nsys, _p(self._a), _p(self._eps1), _p(self._eps2), _p(self._kappa),
+                                        ctypes.byref(self.params), ctypes.byref(out))
+        if rc:
+            raise HsmaError(rc, "hsma_batch_create")
+        self.ptr = out
+        self.use_torch_workspace = use_torch_workspace
+        self.workspace = None
+        self.n = None
+        if max_requests != 1:
+            self.hsma_batch_set_max_requests(max_requests)
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                self.lib.hsma_batch_destroy(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            raise HsmaError(rc, self.lib.hsma_batch_last_error(self.ptr).decode())
+
+    # --- C entry points ---------------------------------------------------------------
+    def hsma_batch_destroy(self):
+        if self.ptr:
+            self.lib.hsma_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def hsma_batch_set_max_requests(self, m: int):
+        self._check(self.lib.hsma_batch_set_max_requests(self.ptr, int(m)))
+
+    def hsma_batch_workspace_size(self, n) -> int:
+        n = _arr(n, np.int64)
+        b = ctypes.c_size_t()
+        self._check(self.lib.hsma_batch_workspace_size(self.ptr, _p(n), ctypes.byref(b)))
+        return int(b.value)
+
+    def _ensure_workspace(self, n):
+        if not self.use_torch_workspace:
+            return
+        key = tuple(int(v) for v in n)
+        if getattr(self, "_ws_key", None) == key:
+            return
+        need = self.hsma_batch_workspace_size(n)
+        self._ws_key = key
+        if self.workspace is None or self.workspace.numel() < need:
+            import torch
+            t = torch.empty(need + need // 4 + 256, dtype=torch.uint8, device=f"cuda:{self.params.device}")
+            off = (-t.data_ptr()) % 256
+            self.workspace = t[off:]
+            self._check(self.lib.hsma_batch_attach_workspace(self.ptr, ctypes.c_void_p(self.workspace.data_ptr()),
+                                                             ctypes.c_size_t(self.workspace.numel())))
+
+    def hsma_batch_build_sources(self, n, xyz, q):
+        n = _arr(n, np.int64)
+        self._ensure_workspace(n)
+        if _is_torch_cuda(xyz):
+            import torch
+            x = xyz.to(torch.float64).contiguous()
+            qq = q.to(torch.float64).contiguous()
+            self._keep = (x, qq)
+            self._check(self.lib.hsma_batch_build_sources_device(self.ptr, _p(n), ctypes.c_void_p(x.data_ptr()),
+                                                                 ctypes.c_void_p(qq.data_ptr())))
+        else:
+            x = _arr(xyz, np.float64).reshape(-1, 3)
+            qq = _arr(q, np.float64)
+            self._check(self.lib.hsma_batch_build_sources(self.ptr, _p(n), _p(x), _p(qq)))
+        self.n = n
+
+    def hsma_batch_potential(self, what: int = HSMA_TOTAL, out=None):
+        if out is not None and _is_torch_cuda(out):
+            self._check(self.lib.hsma_batch_potential_device(self.ptr, ctypes.c_void_p(out.data_ptr()), int(what)))
+            return out
+        phi = np.empty(int(self.n.sum()), dtype=np.float64)
+        self._check(self.lib.hsma_batch_potential(self.ptr, _p(phi), int(what)))
+        return phi
+
+    def hsma_batch_energy(self):
+        et = np.empty(self.nsys)
+        er = np.empty(self.nsys)
+        self._check(self.lib.hsma_batch_energy(self.ptr, _p(et), _p(er)))
+        return et, er
+
+    def hsma_batch_delta_energy(self, sys, k, x_new):
+        sys = _arr(sys, np.int32)
+        k = _arr(k, np.int64)
+        x = _arr(x_new, np.float64).reshape(-1, 3)
+        de = np.empty(len(sys))
+        self._check(self.lib.hsma_batch_delta_energy(self.ptr, len(sys), _p(sys), _p(k), _p(x), _p(de)))
+        return de
+
+    def hsma_batch_apply_moves(self, sys, k, x_new):
+        sys = _arr(sys, np.int32)
+        k = _arr(k, np.int64)
+        x = _arr(x_new, np.float64).reshape(-1, 3)
+        self._check(self.lib.hsma_batch_apply_moves(self.ptr, len(sys), _p(sys), _p(k), _p(x)))
+
+    def hsma_batch_kernel_launches(self) -> int:
+        return int(self.lib.hsma_batch_kernel_launches(self.ptr))
+
+    def hsma_batch_last_pair_time(self) -> float:
+        ms = ctypes.c_float()
+        self._check(self.lib.hsma_batch_last_pair_time(self.ptr, ctypes.byref(ms)))
+        return float(ms.value)
+
+    def hsma_batch_set_pair_config(self, cfg: int):
+        self._check(self.lib.hsma_batch_set_pair_config(self.ptr, int(cfg)))
+
+    def hsma_batch_autotune(self, reps: int = 5):
+        best = ctypes.c_int()
+        ms = ctypes.c_float()
+        self._check(self.lib.hsma_batch_autotune(self.ptr, int(reps), ctypes.byref(best), ctypes.byref(ms)))
+        return int(best.value), float(ms.value)
+
+
+def pair_configs() -> list[tuple[int, int]]:
+    lib = _native.load()
+    out = []
+    for i in range(lib.hsma_pair_config_count()):
+        t, k = ctypes.c_int(), ctypes.c_int()
+        lib.hsma_pair_config_info(i, ctypes.byref(t), ctypes.byref(k))
+        out.append((t.value, k.value))
+    return out
+
+
+def from_systems(systems, precision: int = HSMA_FP32, device: int = 0, stream=None, max_requests: int = 1,
+                 **params) -> Batch:
+    """A Batch for a list of inputs.System-like objects sharing p, M and tau."""
+    s0 = systems[0]
+    prm = hsma_default_params(p=s0.p, M=s0.M, tau=s0.tau, precision=precision, device=device,
+                              stream=stream, **params)
+    return Batch([s.a for s in systems], [s.eps1 for s in systems], [s.eps2 for s in systems],
+                 [s.kappa for s in systems], prm, max_requests=max_requests)
+
+
+def concat(systems):
+    n = np.array([s.n for s in systems], dtype=np.int64)
+    xyz = np.concatenate([s.xyz for s in systems]) if len(systems) else np.zeros((0, 3))
+    q = np.concatenate([s.q for s in systems]) if len(systems) else np.zeros(0)
+    return n, xyz, q
+
+
+class TuneCache:
+    """Autotuned pair configuration per (size class, GPU name), kept in a JSON file."""
+
+    def __init__(self, path: str | None = None):
+        self.path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+        try:
+            self.data = json.load(open(self.path))
+        except Exception:
+            self.data = {}
+
+    @staticmethod
+    def key(n, gpu: str) -> str:
+        tot = int(np.sum(n))
+        return f"{gpu}|nsys={len(n)}|log2N={max(tot, 1).bit_length()}"
+
+    def get(self, n, gpu: str):
+        return self.data.get(self.key(n, gpu))
+
+    def put(self, n, gpu: str, cfg: int, ms: float):
+        self.data[self.key(n, gpu)] = {"cfg": int(cfg), "ms": float(ms)}
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        tmp = self.path + f".{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(self.data, f, indent=1)
+        os.replace(tmp, self.path)
+
+
+def autotuned(batch: Batch, n, xyz, q, gpu: str = "", reps: int = 5, cache: TuneCache | None = None) -> int:
+    """Build, then use the cached tile configuration for this size class or autotune and cache it."""
+    cache = cache or TuneCache()
+    hit = cache.get(n, gpu)
+    if hit is not None:
+        batch.hsma_batch_set_pair_config(hit["cfg"])
+        batch.hsma_batch_build_sources(n, xyz, q)
+        return hit["cfg"]
+    batch.hsma_batch_build_sources(n, xyz, q)
+    cfg, ms = batch.hsma_batch_autotune(reps)
+    batch.hsma_batch_set_pair_config(cfg)
+    batch.hsma_batch_build_sources(n, xyz, q)
+    cache.put(n, gpu, cfg, ms)
+    return cfg

@@ -1,0 +1,953 @@
+// Host engine and C ABI of the HSMA library.
+//
+// An Engine owns the device state of one or more independent cavity systems (a single
+// hsma_t handle is an engine with one system).  It lays every system's arrays out in one
+// device workspace, builds the work lists of the kernels (longest pair items first), and
+// records the two device phases as CUDA graphs:
+//   build:     k_setup -> k_images_moments -> k_coef_reduce -> k_surface   (Sec. 2.3-2.4)
+//   potential: reset counter -> k_pairs -> k_reduce                      (Algorithm 1 step 5)
+// Graphs are re-recorded whenever the layout (sizes) or workspace changes.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace hsma {
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int Engine::fail(int code, const char* fmt, ...)
+{
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  err = buf;
+  return code;
+}
+
+int Engine::cuda_fail(cudaError_t e, const char* what)
+{
+  cudaGetLastError();
+  return fail(HSMA_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+int Engine::init(int dev, void* user_stream, int precision)
+{
+  device = dev;
+  prec = precision;
+  CK(cudaSetDevice(device));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  num_sms = sms;
+  if (user_stream) {
+    stream = (cudaStream_t)user_stream;
+    own_stream = false;
+  } else {
+    // work runs on a stream of our own (graph capture is not possible on the legacy stream),
+    // ordered after and before the caller's legacy-stream work by events (enter/leave)
+    CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    own_stream = true;
+    CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+  }
+  static bool attrs_done[64] = {false};
+  if (device >= 0 && device < 64 && !attrs_done[device]) {
+    init_source_kernels();
+    init_delta_kernels();
+    attrs_done[device] = true;
+  }
+  occ_f32.assign(pair_config_count(), 0);
+  for (int c = 0; c < pair_config_count(); ++c) occ_f32[c] = pairs_f32_occupancy(c);
+  occ_f64 = pairs_f64_occupancy();
+  CK(cudaEventCreate(&ev_pair0));
+  CK(cudaEventCreate(&ev_pair1));
+  CK(cudaGetLastError());
+  return HSMA_OK;
+}
+
+void Engine::enter()
+{
+  if (own_stream) {
+    cudaEventRecord(ev_in, cudaStreamLegacy);
+    cudaStreamWaitEvent(stream, ev_in, 0);
+  }
+}
+
+void Engine::leave()
+{
+  if (own_stream) {
+    cudaEventRecord(ev_out, stream);
+    cudaStreamWaitEvent(cudaStreamLegacy, ev_out, 0);
+  }
+}
+
+int Engine::last_pair_time(float* ms)
+{
+  if (!pair_timed) return fail(HSMA_E_STATE, "no pair sum has run");
+  CK(cudaStreamSynchronize(stream));
+  CK(cudaEventElapsedTime(ms, ev_pair0, ev_pair1));
+  return HSMA_OK;
+}
+
+Engine::~Engine()
+{
+  if (device >= 0) cudaSetDevice(device);
+  drop_graphs();
+  if (ws_owned && ws) cudaFree(ws);
+  if (ev_pair0) cudaEventDestroy(ev_pair0);
+  if (ev_pair1) cudaEventDestroy(ev_pair1);
+  if (ev_in) cudaEventDestroy(ev_in);
+  if (ev_out) cudaEventDestroy(ev_out);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+void Engine::drop_graphs()
+{
+  if (g_build) cudaGraphExecDestroy(g_build);
+  if (g_pot) cudaGraphExecDestroy(g_pot);
+  g_build = g_pot = nullptr;
+}
+
+// ---------------------------------------------------------------------------------------
+Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
+{
+  Layout L;
+  const int nsys = (int)spec.size();
+  L.cfg = cfg;
+  int TB, occ;
+  if (prec == HSMA_FP64) {
+    TB = kF64TargetsPerBlock;
+    occ = occ_f64 > 0 ? occ_f64 : 1;
+  } else {
+    const PairConfig pc = pair_config(cfg);
+    TB = pc.threads * pc.k;
+    occ = occ_f32[cfg] > 0 ? occ_f32[cfg] : 1;
+  }
+  const int slots = num_sms * occ;
+  const double desired = 4.0 * slots;
+  L.sd.resize(nsys);
+  int64_t chg = 0, surf = 0, coef = 0, mn = 0, mom = 0, part = 0;
+  int k5 = 0;
+  L.maxP = 1;
+  L.pmax = 0;
+  for (int s = 0; s < nsys; ++s) {
+    const SysSpec& sp = spec[s];
+    SysDev d;
+    memset(&d, 0, sizeof(d));
+    const int64_t n = ns[s];
+    d.a = sp.a; d.eps1 = sp.eps1; d.eps2 = sp.eps2; d.kappa = sp.kappa; d.tau = sp.tau; d.dy_rel = sp.dy_rel;
+    d.coulk = sp.coulk;
+    d.p = sp.p; d.P = (sp.p + 1) * (sp.p + 1); d.M = sp.M; d.F1 = sp.F1; d.F2 = sp.F2;
+    d.n = (int)n;
+    d.prec = prec;
+    d.chg = chg; d.src = 2 * chg; d.surf = surf; d.coef = coef; d.mn = mn;
+    d.mom = mom;
+    // charges per moment block: enough blocks to cover the SMs twice over the whole engine,
+    // between 8 and kMomTile charges (a multiple of the 8 warps of a block)
+    // (a function of this system alone, so that its summation order is the same alone or batched)
+    {
+      const int64_t want_blocks = 2 * (int64_t)num_sms;
+      int64_t tile = (n + want_blocks - 1) / want_blocks;
+      tile = std::min<int64_t>(kMomTile, std::max<int64_t>(8, (tile + 7) / 8 * 8));
+      d.mom_tile = (int)tile;
+    }
+    d.mom_blocks = (int)((n + d.mom_tile - 1) / d.mom_tile);
+    d.tb = TB;
+    d.n_tb = (int)((n + TB - 1) / TB);
+    if (n > 0) {
+      // source chunks: enough items for this system alone to cover the GPU (a function of
+      // this system only, so batching does not change its summation order)
+      const int64_t chunks_total = std::max<int64_t>(1, (int64_t)std::ceil(desired / d.n_tb));
+      const int64_t per = (2 * n + sp.M + chunks_total - 1) / chunks_total;
+      const int unit = prec == HSMA_FP64 ? kF64TargetsPerBlock : pair_config(cfg).threads;
+      int64_t chunk = std::max<int64_t>(per, unit);
+      chunk = (chunk + unit - 1) / unit * unit;
+      d.chunk = (int)chunk;
+      d.chunk_s = (int)chunk;
+      d.ncr = (int)((n + chunk - 1) / chunk);
+      d.nck = d.ncr;
+      d.ncs = (int)((sp.M + chunk - 1) / chunk);
+    }
+    d.part = part;
+    d.k5_first = k5;
+    d.k5_count = (int)((n + kReduceTargetsPerBlock - 1) / kReduceTargetsPerBlock);
+    L.sd[s] = d;
+    for (int b = 0; b < d.mom_blocks; ++b) L.it12.push_back(make_int2(s, b));
+    for (int c = 0; c < (d.P + kCoefChunk - 1) / kCoefChunk; ++c) L.it2r.push_back(make_int2(s, c));
+    for (int b = 0; b < (sp.M + kSurfPointsPerBlock - 1) / kSurfPointsPerBlock; ++b) L.it3.push_back(make_int2(s, b));
+    for (int b = 0; b < d.k5_count; ++b) L.it5.push_back(make_int2(s, b));
+    const int nch = d.ncr + d.nck + d.ncs;
+    for (int tb = 0; tb < d.n_tb; ++tb)
+      for (int c = 0; c < nch; ++c) L.it4.push_back(make_int4(s, tb, c, 0));
+    chg += n;
+    surf += sp.M;
+    coef += d.P;
+    mn += sp.p + 1;
+    mom += d.mom_blocks;
+    part += (int64_t)nch * n;
+    k5 += d.k5_count;
+    L.maxP = std::max(L.maxP, d.P);
+    L.pmax = std::max(L.pmax, sp.p);
+  }
+  // longest pair items first (cost ~ targets x sources x per-source weight)
+  auto cost = [&](const int4& it) {
+    const SysDev& d = L.sd[it.x];
+    const int64_t nt = std::min<int64_t>(d.tb, d.n - (int64_t)it.y * d.tb);
+    int64_t ns_, w = 10;
+    if (it.z < d.ncr) {
+      ns_ = std::min<int64_t>(d.chunk, d.n - (int64_t)it.z * d.chunk);
+    } else if (it.z < d.ncr + d.nck) {
+      ns_ = std::min<int64_t>(d.chunk, d.n - (int64_t)(it.z - d.ncr) * d.chunk);
+    } else {
+      ns_ = std::min<int64_t>(d.chunk_s, d.M - (int64_t)(it.z - d.ncr - d.nck) * d.chunk_s);
+      w = 13;
+    }
+    return nt * ns_ * w;
+  };
+  for (auto& it : L.it4) it.w = 0;
+  std::stable_sort(L.it4.begin(), L.it4.end(), [&](const int4& x, const int4& y) { return cost(x) > cost(y); });
+  L.totN = chg;
+  L.totM = surf;
+  L.totP = coef;
+  L.totMn = mn;
+  L.totMom = mom;
+  L.totPart = part;
+  L.mom_stride = (int)align_up(2 * (size_t)L.maxP + 1, 2);
+  L.pair_grid = (int)std::max<size_t>(1, std::min<size_t>(L.it4.size(), (size_t)slots));
+
+  // workspace plan
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1), 256);
+    return o;
+  };
+  const int ntri = (L.pmax + 1) * (L.pmax + 2) / 2;
+  L.o_sys = take(sizeof(SysDev) * nsys);
+  L.o_Mn = take(8 * L.totMn);
+  L.o_rec_a = take(8 * (size_t)ntri);
+  L.o_rec_b = take(8 * (size_t)ntri);
+  L.o_sect = take(8 * (size_t)(L.pmax + 1));
+  L.o_inv_np1 = take(8 * (size_t)(L.pmax + 1));
+  L.o_xyz = take(24 * L.totN);
+  L.o_q = take(8 * L.totN);
+  if (prec == HSMA_FP64) {
+    L.o_src64 = take(32 * 2 * L.totN);
+    L.o_surf64a = take(32 * L.totM);
+    L.o_surf64b = take(8 * L.totM);
+    L.o_part64 = take(8 * L.totPart);
+  } else {
+    L.o_srchi = take(16 * 2 * L.totN);
+    L.o_srclo = take(16 * 2 * L.totN);
+    L.o_surfa = take(16 * L.totM);
+    L.o_surfb = take(16 * L.totM);
+    L.o_part = take(8 * L.totPart);
+  }
+  L.o_surfx = take(32 * L.totM);
+  L.o_surfqd = take(16 * L.totM);
+  L.o_vsurf = take(16 * L.totM);
+  {
+    int per_req = 1;
+    for (const auto& d : L.sd)
+      per_req = std::max(per_req, (d.n + kDeltaBlock - 1) / kDeltaBlock + (d.M + kDeltaBlock - 1) / kDeltaBlock);
+    L.max_req = std::max(1, max_requests);
+    L.ditem_cap = L.max_req * per_req;
+    int surf_blocks = 1;
+    for (const auto& d : L.sd) surf_blocks = std::max(surf_blocks, (d.M + kDeltaBlock - 1) / kDeltaBlock);
+    L.mitem_cap = L.max_req * surf_blocks;
+  }
+  L.o_dreq = take(sizeof(DeltaReq) * (size_t)L.max_req);
+  L.o_ditems = take(sizeof(int4) * (size_t)L.ditem_cap);
+  L.o_dreqit = take(sizeof(int2) * (size_t)L.max_req);
+  L.o_mitems = take(sizeof(int2) * (size_t)L.mitem_cap);
+  L.o_dpart = take(8 * (size_t)L.ditem_cap);
+  L.o_de = take(8 * (size_t)L.max_req);
+  L.o_mom = take(8 * (size_t)L.totMom * L.mom_stride);
+  L.o_coef = take(8 * L.totP);
+  L.o_r0 = take(8 * (size_t)nsys);
+  L.o_phic = take(8 * L.totN);
+  L.o_phir = take(8 * L.totN);
+  L.o_phit = take(8 * L.totN);
+  L.o_epart = take(16 * L.it5.size());
+  L.o_energy = take(16 * (size_t)nsys);
+  L.o_ctr = take(16);
+  L.o_it12 = take(sizeof(int2) * L.it12.size());
+  L.o_it2r = take(sizeof(int2) * L.it2r.size());
+  L.o_it3 = take(sizeof(int2) * L.it3.size());
+  L.o_it5 = take(sizeof(int2) * L.it5.size());
+  L.o_it4 = take(sizeof(int4) * L.it4.size());
+  L.bytes = off;
+  return L;
+}
+
+void Engine::carve()
+{
+  char* b = ws;
+  sys_d = (SysDev*)(b + L.o_sys);
+  Mn_d = (double*)(b + L.o_Mn);
+  rec_a_d = (double*)(b + L.o_rec_a);
+  rec_b_d = (double*)(b + L.o_rec_b);
+  sect_d = (double*)(b + L.o_sect);
+  inv_np1_d = (double*)(b + L.o_inv_np1);
+  xyz_d = (double*)(b + L.o_xyz);
+  q_d = (double*)(b + L.o_q);
+  if (prec == HSMA_FP64) {
+    src64_d = (dbl4*)(b + L.o_src64);
+    surf64a_d = (dbl4*)(b + L.o_surf64a);
+    surf64b_d = (double*)(b + L.o_surf64b);
+    part64_d = (double*)(b + L.o_part64);
+    srchi_d = srclo_d = surfa_d = surfb_d = nullptr;
+    part_d = nullptr;
+  } else {
+    srchi_d = (float4*)(b + L.o_srchi);
+    srclo_d = (float4*)(b + L.o_srclo);
+    surfa_d = (float4*)(b + L.o_surfa);
+    surfb_d = (float4*)(b + L.o_surfb);
+    part_d = (float2*)(b + L.o_part);
+    src64_d = nullptr;
+    surf64a_d = nullptr;
+    surf64b_d = nullptr;
+    part64_d = nullptr;
+  }
+  surfx_d = (dbl4*)(b + L.o_surfx);
+  surfqd_d = (double2*)(b + L.o_surfqd);
+  vsurf_d = (double2*)(b + L.o_vsurf);
+  dreq_d = (DeltaReq*)(b + L.o_dreq);
+  ditems_d = (int4*)(b + L.o_ditems);
+  dreqit_d = (int2*)(b + L.o_dreqit);
+  mitems_d = (int2*)(b + L.o_mitems);
+  dpart_d = (double*)(b + L.o_dpart);
+  de_d = (double*)(b + L.o_de);
+  mom_d = (double*)(b + L.o_mom);
+  coef_d = (double*)(b + L.o_coef);
+  r0_d = (double*)(b + L.o_r0);
+  phic_d = (double*)(b + L.o_phic);
+  phir_d = (double*)(b + L.o_phir);
+  phit_d = (double*)(b + L.o_phit);
+  epart_d = (double*)(b + L.o_epart);
+  energy_d = (double*)(b + L.o_energy);
+  unsigned int* ctr = (unsigned int*)(b + L.o_ctr);
+  ctr_pairs_d = ctr;
+  ctr_red_d = ctr + 1;
+  status_d = (int*)(ctr + 2);
+  ctr_delta_d = ctr + 3;
+  it12_d = (int2*)(b + L.o_it12);
+  it2r_d = (int2*)(b + L.o_it2r);
+  it3_d = (int2*)(b + L.o_it3);
+  it5_d = (int2*)(b + L.o_it5);
+  it4_d = (int4*)(b + L.o_it4);
+}
+
+int Engine::attach(void* ptr, size_t bytes)
+{
+  CK(cudaSetDevice(device));
+  if (ptr && ((uintptr_t)ptr % 256) != 0) return fail(HSMA_E_INVALID_ARG, "workspace must be 256-byte aligned");
+  CK(cudaStreamSynchronize(stream));
+  if (ws_owned && ws) cudaFree(ws);
+  ws = (char*)ptr;
+  ws_cap = ptr ? bytes : 0;
+  ws_owned = false;
+  ws_user = ptr != nullptr;
+  layout_uploaded = false;
+  sources_ready = pot_ready = false;
+  drop_graphs();
+  return HSMA_OK;
+}
+
+int Engine::set_sizes(const std::vector<int64_t>& ns)
+{
+  if (have_layout && ns == cur_ns && layout_uploaded) return HSMA_OK;
+  const int cfg = prec == HSMA_FP64 ? 0 : choose_config(ns);
+  L = make_layout(ns, cfg);
+  cur_ns = ns;
+  have_layout = true;
+  if (L.bytes > ws_cap) {
+    if (ws_user) return fail(HSMA_E_OOM, "attached workspace has %zu bytes, %zu needed", ws_cap, L.bytes);
+    CK(cudaStreamSynchronize(stream));
+    if (ws) cudaFree(ws);
+    ws = nullptr;
+    ws_cap = 0;
+    const size_t want = L.bytes + L.bytes / 4;
+    cudaError_t e = cudaMalloc((void**)&ws, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ws = nullptr;
+      return fail(HSMA_E_OOM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    ws_cap = want;
+    ws_owned = true;
+  }
+  carve();
+  drop_graphs();
+  CK(cudaMemcpyAsync(sys_d, L.sd.data(), sizeof(SysDev) * L.sd.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.it12.empty())
+    CK(cudaMemcpyAsync(it12_d, L.it12.data(), sizeof(int2) * L.it12.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.it2r.empty())
+    CK(cudaMemcpyAsync(it2r_d, L.it2r.data(), sizeof(int2) * L.it2r.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.it3.empty())
+    CK(cudaMemcpyAsync(it3_d, L.it3.data(), sizeof(int2) * L.it3.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.it5.empty())
+    CK(cudaMemcpyAsync(it5_d, L.it5.data(), sizeof(int2) * L.it5.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.it4.empty())
+    CK(cudaMemcpyAsync(it4_d, L.it4.data(), sizeof(int4) * L.it4.size(), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(ctr_pairs_d, 0, 16, stream));
+  CK(cudaMemsetAsync(energy_d, 0, 16 * L.sd.size(), stream));
+  // parameter-only quantities (row a1: scalars, M_n, tables, quadrature grid), once per layout
+  launch_setup(sys_d, (int)L.sd.size(), Mn_d, rec_a_d, rec_b_d, sect_d, inv_np1_d, L.pmax, surfx_d, stream);
+  CK(cudaGetLastError());
+  launches += 1;
+  CK(cudaStreamSynchronize(stream));
+  layout_uploaded = true;
+  sources_ready = pot_ready = false;
+  return HSMA_OK;
+}
+
+Tables Engine::tables() const
+{
+  Tables t;
+  t.rec_a = rec_a_d;
+  t.rec_b = rec_b_d;
+  t.sect = sect_d;
+  t.inv_np1 = inv_np1_d;
+  t.pmax = L.pmax;
+  return t;
+}
+
+void Engine::issue_build()
+{
+  launch_images_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, tables(), srchi_d, srclo_d, src64_d,
+                        prec, mom_d, L.mom_stride, status_d, stream);
+  launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, r0_d, stream);
+  launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, tables(), surfa_d, surfb_d, surf64a_d, surf64b_d,
+                 surfx_d, surfqd_d, prec, stream);
+}
+
+int Engine::build_launch_count() const
+{
+  return (L.it12.empty() ? 0 : 1) + (L.it2r.empty() ? 0 : 1) + (L.it3.empty() ? 0 : 1);
+}
+
+void Engine::issue_pot()
+{
+  const int nsys = (int)L.sd.size();
+  cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), stream);
+  if (!L.it4.empty()) {
+    cudaEventRecordWithFlags(ev_pair0, stream, cudaEventRecordExternal);
+    if (prec == HSMA_FP64)
+      launch_pairs_f64(L.pair_grid, sys_d, it4_d, (int)L.it4.size(), ctr_pairs_d, src64_d, surf64a_d, surf64b_d,
+                       part64_d, stream);
+    else
+      launch_pairs_f32(L.cfg, L.pair_grid, sys_d, it4_d, (int)L.it4.size(), ctr_pairs_d, srchi_d, srclo_d, surfa_d,
+                       surfb_d, part_d, stream);
+    cudaEventRecordWithFlags(ev_pair1, stream, cudaEventRecordExternal);
+  }
+  launch_reduce(sys_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, r0_d, phic_d, phir_d, phit_d,
+                epart_d, energy_d, ctr_red_d, status_d, stream);
+}
+
+int Engine::pot_launch_count() const { return (L.it4.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1); }
+
+int Engine::run_graph(cudaGraphExec_t* g, void (Engine::*issue)())
+{
+  if (!use_graphs) {
+    (this->*issue)();
+    CK(cudaGetLastError());
+    return HSMA_OK;
+  }
+  if (!*g) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    (this->*issue)();
+    cudaError_t e = cudaStreamEndCapture(stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(g, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      *g = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+  }
+  CK(cudaGraphLaunch(*g, stream));
+  return HSMA_OK;
+}
+
+int Engine::build(const double* xyz, const double* q, bool device_inputs)
+{
+  CK(cudaSetDevice(device));
+  const int64_t n = L.totN;
+  enter();
+  if (n > 0) {
+    const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(xyz_d, xyz, 24 * n, kind, stream));
+    CK(cudaMemcpyAsync(q_d, q, 8 * n, kind, stream));
+  }
+  int rc = run_graph(&g_build, &Engine::issue_build);
+  if (rc) return rc;
+  leave();
+  launches += build_launch_count();
+  sources_ready = true;
+  pot_ready = false;
+  v_ready = false;
+  return HSMA_OK;
+}
+
+int Engine::potentials()
+{
+  if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
+  if (pot_ready) return HSMA_OK;
+  CK(cudaSetDevice(device));
+  enter();
+  int rc = run_graph(&g_pot, &Engine::issue_pot);
+  if (rc) return rc;
+  leave();
+  launches += pot_launch_count();
+  pot_ready = true;
+  if (!L.it4.empty()) pair_timed = true;
+  return HSMA_OK;
+}
+
+int Engine::check_status()
+{
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, status_d, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  if (st) {
+    CK(cudaMemsetAsync(status_d, 0, sizeof(int), stream));
+    pot_ready = false;
+    if (st & kStOutside) {
+      sources_ready = false;
+      return fail(HSMA_E_OUTSIDE, "a charge lies outside the cavity (|x| >= a) or is not finite");
+    }
+    if (st & kStTimeout) return fail(HSMA_E_TIMEOUT, "a bounded device wait gave up");
+    if (st & kStBadMove) return fail(HSMA_E_OUTSIDE, "moved charge outside the cavity");
+    if (st & kStNonFinite)
+      return fail(HSMA_E_NONFINITE, "non-finite potential (coincident charges?)");
+  }
+  return HSMA_OK;
+}
+
+// Pair-sum tile configuration for a set of sizes: the autotuned choice if one is cached for
+// this size bucket, else a size heuristic.
+int Engine::choose_config(const std::vector<int64_t>& ns) const
+{
+  if (forced_cfg >= 0) return forced_cfg;
+  int64_t tot = 0;
+  for (auto v : ns) tot += v;
+  const int bucket = tune_bucket(tot, (int)ns.size());
+  for (const auto& e : tuned)
+    if (e.first == bucket) return e.second;
+  return 0;
+}
+
+int tune_bucket(int64_t total_n, int nsys)
+{
+  int b = 0;
+  int64_t v = std::max<int64_t>(total_n, 1);
+  while (v > 1) {
+    v >>= 1;
+    ++b;
+  }
+  return b * 2 + (nsys > 1 ? 1 : 0);
+}
+
+}  // namespace hsma
+
+// =======================================================================================
+// C ABI
+// =======================================================================================
+using hsma::Engine;
+
+struct hsma_t {
+  Engine* e = nullptr;
+  int64_t n = -1;
+  std::string err;
+};
+
+static int validate_params(const hsma_params* p, std::string& why)
+{
+  if (!p) {
+    why = "params is NULL";
+    return HSMA_E_INVALID_ARG;
+  }
+  if (p->p < 0 || p->p > HSMA_P_MAX) {
+    why = "p out of range [0, HSMA_P_MAX]";
+    return HSMA_E_INVALID_ARG;
+  }
+  if (p->F2 > 0) {
+    if (p->F1 <= 0 || p->F1 >= p->F2) {
+      why = "need 0 < F1 < F2";
+      return HSMA_E_INVALID_ARG;
+    }
+  } else if (p->M < 4 || (p->M % 2) != 0) {
+    why = "M must be even and >= 4";
+    return HSMA_E_INVALID_ARG;
+  }
+  if (!(p->tau > 0.0) || !std::isfinite(p->tau)) {
+    why = "tau must be > 0";
+    return HSMA_E_INVALID_ARG;
+  }
+  if (!(p->dy_rel > 0.0) || !(p->dy_rel < 0.5) || !std::isfinite(p->dy_rel)) {
+    why = "dy_rel must be in (0, 0.5)";
+    return HSMA_E_INVALID_ARG;
+  }
+  if (!std::isfinite(p->coulomb_k)) {
+    why = "coulomb_k must be finite";
+    return HSMA_E_INVALID_ARG;
+  }
+  if (p->precision != HSMA_FP32 && p->precision != HSMA_FP64) {
+    why = "precision must be HSMA_FP32 or HSMA_FP64";
+    return HSMA_E_INVALID_ARG;
+  }
+  return HSMA_OK;
+}
+
+namespace hsma {
+int make_spec(double a, double eps1, double eps2, double kappa, const hsma_params* prm, SysSpec* out, std::string& why)
+{
+  int rc = validate_params(prm, why);
+  if (rc) return rc;
+  if (!(a > 0.0) || !std::isfinite(a) || !(eps1 > 0.0) || !std::isfinite(eps1) || !(eps2 > 0.0) ||
+      !std::isfinite(eps2) || !(kappa >= 0.0) || !std::isfinite(kappa)) {
+    why = "need a > 0, eps1 > 0, eps2 > 0, kappa >= 0 (finite)";
+    return HSMA_E_INVALID_ARG;
+  }
+  SysSpec s;
+  s.a = a;
+  s.eps1 = eps1;
+  s.eps2 = eps2;
+  s.kappa = kappa;
+  s.tau = prm->tau;
+  s.dy_rel = prm->dy_rel;
+  s.coulk = prm->coulomb_k;
+  s.p = prm->p;
+  if (prm->F2 > 0) {
+    s.F2 = prm->F2;
+    s.F1 = prm->F1;
+  } else {
+    s.F2 = prm->M / 2 - 1;
+    s.F1 = (int)std::lround(s.F2 * (std::sqrt(5.0) - 1.0) / 2.0);
+  }
+  s.M = 2 * (s.F2 + 1);
+  *out = s;
+  return HSMA_OK;
+}
+}  // namespace hsma
+
+static int set_err(hsma_t* h, int code, const char* msg)
+{
+  if (h) h->err = msg;
+  return code;
+}
+
+static int from_engine(hsma_t* h, int rc)
+{
+  if (rc != HSMA_OK) h->err = h->e->err;
+  return rc;
+}
+
+extern "C" {
+
+const char* hsma_version(void) { return "hsma-gb300 0.1 (sm_103a)"; }
+
+int hsma_default_params(hsma_params* p)
+{
+  if (!p) return HSMA_E_INVALID_ARG;
+  memset(p, 0, sizeof(*p));
+  p->p = 20;
+  p->M = 1000;
+  p->F1 = 0;
+  p->F2 = 0;
+  p->tau = 0.1;
+  p->dy_rel = 1e-5;
+  p->coulomb_k = 1.0 / (4.0 * hsma::kPi);
+  p->precision = HSMA_FP32;
+  p->device = 0;
+  p->stream = nullptr;
+  return HSMA_OK;
+}
+
+int hsma_create(double a, double eps1, double eps2, double kappa, const hsma_params* params, hsma_t** out)
+{
+  if (!out) return HSMA_E_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  hsma::SysSpec s;
+  int rc = hsma::make_spec(a, eps1, eps2, kappa, params, &s, why);
+  if (rc) return rc;
+  hsma_t* h = new hsma_t();
+  h->e = new Engine();
+  h->e->spec.push_back(s);
+  rc = h->e->init(params->device, params->stream, params->precision);
+  if (rc) {
+    delete h->e;
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return HSMA_OK;
+}
+
+void hsma_destroy(hsma_t* h)
+{
+  if (!h) return;
+  delete h->e;
+  delete h;
+}
+
+const char* hsma_last_error(const hsma_t* h)
+{
+  if (!h) return "NULL handle";
+  return h->err.c_str();
+}
+
+int hsma_workspace_size(hsma_t* h, int64_t n, size_t* bytes)
+{
+  if (!h || !bytes || n < 0 || n > (int64_t)INT32_MAX / 4) return set_err(h, HSMA_E_INVALID_ARG, "bad argument");
+  const int cfg = h->e->prec == HSMA_FP64 ? 0 : h->e->choose_config({n});
+  *bytes = h->e->make_layout({n}, cfg).bytes;
+  return HSMA_OK;
+}
+
+int hsma_attach_workspace(hsma_t* h, void* device_ptr, size_t bytes)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  h->n = -1;
+  return from_engine(h, h->e->attach(device_ptr, bytes));
+}
+
+static int build_common(hsma_t* h, int64_t n, const double* xyz, const double* q, bool dev)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  if (n < 0 || n > (int64_t)INT32_MAX / 4) return set_err(h, HSMA_E_INVALID_ARG, "n out of range");
+  if (n > 0 && (!xyz || !q)) return set_err(h, HSMA_E_INVALID_ARG, "NULL xyz or q");
+  if (!dev) {
+    const double a = h->e->spec[0].a;
+    for (int64_t i = 0; i < n; ++i) {
+      const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+      const double r2 = x * x + y * y + z * z;
+      if (!(r2 < a * a) || !std::isfinite(q[i]) || !std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z))
+        return set_err(h, HSMA_E_OUTSIDE, "a charge lies outside the cavity (|x| >= a) or is not finite");
+    }
+  }
+  int rc = h->e->set_sizes({n});
+  if (rc) return from_engine(h, rc);
+  h->n = n;
+  return from_engine(h, h->e->build(xyz, q, dev));
+}
+
+int hsma_build_sources(hsma_t* h, int64_t n, const double* xyz, const double* q)
+{
+  return build_common(h, n, xyz, q, false);
+}
+
+int hsma_build_sources_device(hsma_t* h, int64_t n, const double* xyz_dev, const double* q_dev)
+{
+  return build_common(h, n, xyz_dev, q_dev, true);
+}
+
+static const double* pick_phi(Engine* e, int what)
+{
+  if (what == HSMA_TOTAL) return e->phit_d;
+  if (what == HSMA_REACTION) return e->phir_d;
+  if (what == HSMA_COULOMB) return e->phic_d;
+  return nullptr;
+}
+
+int hsma_potential(hsma_t* h, double* phi, int what)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  if (h->n < 0) return set_err(h, HSMA_E_STATE, "sources have not been built");
+  if (h->n > 0 && !phi) return set_err(h, HSMA_E_INVALID_ARG, "NULL phi");
+  const double* src = pick_phi(h->e, what);
+  if (!src) return set_err(h, HSMA_E_INVALID_ARG, "bad 'what'");
+  int rc = h->e->potentials();
+  if (rc) return from_engine(h, rc);
+  if (h->n > 0) {
+    cudaError_t e = cudaMemcpyAsync(phi, src, 8 * h->n, cudaMemcpyDeviceToHost, h->e->stream);
+    if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy phi"));
+  }
+  return from_engine(h, h->e->check_status());
+}
+
+int hsma_potential_device(hsma_t* h, double* phi_dev, int what)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  if (h->n < 0) return set_err(h, HSMA_E_STATE, "sources have not been built");
+  if (h->n > 0 && !phi_dev) return set_err(h, HSMA_E_INVALID_ARG, "NULL phi");
+  const double* src = pick_phi(h->e, what);
+  if (!src) return set_err(h, HSMA_E_INVALID_ARG, "bad 'what'");
+  int rc = h->e->potentials();
+  if (rc) return from_engine(h, rc);
+  if (h->n > 0) {
+    cudaError_t e = cudaMemcpyAsync(phi_dev, src, 8 * h->n, cudaMemcpyDeviceToDevice, h->e->stream);
+    if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy phi"));
+  }
+  return HSMA_OK;
+}
+
+int hsma_energy(hsma_t* h, double* e_total, double* e_reaction)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  if (h->n < 0) return set_err(h, HSMA_E_STATE, "sources have not been built");
+  int rc = h->e->potentials();
+  if (rc) return from_engine(h, rc);
+  double en[2] = {0.0, 0.0};
+  cudaError_t e = cudaMemcpyAsync(en, h->e->energy_d, 16, cudaMemcpyDeviceToHost, h->e->stream);
+  if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy energy"));
+  rc = h->e->check_status();
+  if (rc) return from_engine(h, rc);
+  if (e_total) *e_total = en[0];
+  if (e_reaction) *e_reaction = en[1];
+  return HSMA_OK;
+}
+
+int hsma_delta_energy(hsma_t* h, int64_t k, const double* x_new, double* de)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  return from_engine(h, h->e->delta_energy(k, x_new, de));
+}
+
+int hsma_apply_move(hsma_t* h, int64_t k, const double* x_new)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  return from_engine(h, h->e->apply_move(k, x_new));
+}
+
+int64_t hsma_kernel_launches(const hsma_t* h) { return h ? h->e->launches : 0; }
+
+int hsma_last_pair_time(hsma_t* h, float* ms)
+{
+  if (!h || !ms) return HSMA_E_INVALID_ARG;
+  return from_engine(h, h->e->last_pair_time(ms));
+}
+
+}  // extern "C"
+
+namespace hsma {
+
+// Potentials of the real charges under the surface kernels (needed by Delta E); computed once
+// per build and then updated by committed moves.
+int Engine::ensure_v()
+{
+  if (v_ready) return HSMA_OK;
+  if (!L.it3.empty()) {
+    launch_surface_potentials(sys_d, it3_d, (int)L.it3.size(), xyz_d, q_d, surfx_d, vsurf_d, stream);
+    CK(cudaGetLastError());
+    launches += 1;
+  }
+  v_ready = true;
+  return HSMA_OK;
+}
+
+static int check_moves(Engine& e, const std::vector<DeltaReq>& reqs)
+{
+  if ((int)reqs.size() > e.L.max_req)
+    return e.fail(HSMA_E_INVALID_ARG, "%zu move requests exceed the reserved %d", reqs.size(), e.L.max_req);
+  for (const auto& r : reqs) {
+    if (r.sys < 0 || r.sys >= (int)e.L.sd.size()) return e.fail(HSMA_E_INVALID_ARG, "bad system index");
+    const SysDev& d = e.L.sd[r.sys];
+    if (r.k < 0 || r.k >= d.n) return e.fail(HSMA_E_INVALID_ARG, "charge index %d out of range", r.k);
+    const double r2 = r.x * r.x + r.y * r.y + r.z * r.z;
+    if (!(r2 < d.a * d.a) || !std::isfinite(r2)) return e.fail(HSMA_E_OUTSIDE, "moved charge outside the cavity");
+  }
+  return HSMA_OK;
+}
+
+int Engine::delta_batch(const std::vector<DeltaReq>& reqs, double* de_host)
+{
+  if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
+  int rc = check_moves(*this, reqs);
+  if (rc) return rc;
+  if (reqs.empty()) return HSMA_OK;
+  std::vector<int4> items;
+  std::vector<int2> ranges(reqs.size());
+  for (size_t r = 0; r < reqs.size(); ++r) {
+    const SysDev& d = L.sd[reqs[r].sys];
+    ranges[r].x = (int)items.size();
+    for (int b = 0; b < (d.n + kDeltaBlock - 1) / kDeltaBlock; ++b) items.push_back(make_int4((int)r, 0, b, 0));
+    for (int b = 0; b < (d.M + kDeltaBlock - 1) / kDeltaBlock; ++b) items.push_back(make_int4((int)r, 1, b, 0));
+    ranges[r].y = (int)items.size() - ranges[r].x;
+  }
+  CK(cudaSetDevice(device));
+  enter();
+  rc = ensure_v();
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(dreq_d, reqs.data(), sizeof(DeltaReq) * reqs.size(), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(ditems_d, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(dreqit_d, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice, stream));
+  launch_delta(sys_d, ditems_d, (int)items.size(), dreqit_d, dreq_d, (int)reqs.size(), xyz_d, q_d, srchi_d, srclo_d,
+               src64_d, surfx_d, surfqd_d, vsurf_d, Mn_d, inv_np1_d, dpart_d, de_d, ctr_delta_d, status_d, stream);
+  CK(cudaGetLastError());
+  launches += 1;
+  CK(cudaMemcpyAsync(de_host, de_d, 8 * reqs.size(), cudaMemcpyDeviceToHost, stream));
+  leave();
+  return check_status();
+}
+
+int Engine::move_batch(const std::vector<DeltaReq>& reqs)
+{
+  if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
+  int rc = check_moves(*this, reqs);
+  if (rc) return rc;
+  if (reqs.empty()) return HSMA_OK;
+  std::vector<int2> items;
+  for (size_t r = 0; r < reqs.size(); ++r) {
+    for (size_t o = 0; o < r; ++o)
+      if (reqs[o].sys == reqs[r].sys) return fail(HSMA_E_INVALID_ARG, "two moves of one system in a batch");
+    const SysDev& d = L.sd[reqs[r].sys];
+    for (int b = 0; b < (d.M + kDeltaBlock - 1) / kDeltaBlock; ++b) items.push_back(make_int2((int)r, b));
+  }
+  CK(cudaSetDevice(device));
+  enter();
+  CK(cudaMemcpyAsync(dreq_d, reqs.data(), sizeof(DeltaReq) * reqs.size(), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(mitems_d, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, stream));
+  launch_move(sys_d, mitems_d, (int)items.size(), dreq_d, (int)reqs.size(), tables(), L.maxP, xyz_d, q_d, Mn_d,
+              coef_d, r0_d, surfx_d, surfqd_d, vsurf_d, v_ready ? 1 : 0, surfa_d, surfb_d, surf64a_d, surf64b_d,
+              srchi_d, srclo_d, src64_d, stream);
+  CK(cudaGetLastError());
+  leave();
+  launches += items.empty() ? 1 : 2;
+  pot_ready = false;
+  return HSMA_OK;
+}
+
+int Engine::delta_energy(int64_t k, const double* x_new, double* de)
+{
+  if (!x_new || !de) return fail(HSMA_E_INVALID_ARG, "NULL argument");
+  if (L.sd.empty()) return fail(HSMA_E_STATE, "sources have not been built");
+  DeltaReq r;
+  r.sys = 0;
+  r.k = (int)std::min<int64_t>(std::max<int64_t>(k, -1), INT32_MAX);
+  r.x = x_new[0];
+  r.y = x_new[1];
+  r.z = x_new[2];
+  return delta_batch({r}, de);
+}
+
+int Engine::apply_move(int64_t k, const double* x_new)
+{
+  if (!x_new) return fail(HSMA_E_INVALID_ARG, "NULL argument");
+  if (L.sd.empty()) return fail(HSMA_E_STATE, "sources have not been built");
+  DeltaReq r;
+  r.sys = 0;
+  r.k = (int)std::min<int64_t>(std::max<int64_t>(k, -1), INT32_MAX);
+  r.x = x_new[0];
+  r.y = x_new[1];
+  r.z = x_new[2];
+  return move_batch({r});
+}
+
+}  // namespace hsma

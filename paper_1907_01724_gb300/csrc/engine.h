@@ -1,0 +1,133 @@
+// Engine: device state, layout and launch sequencing for one or more HSMA cavity systems.
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "hsma_internal.cuh"
+
+namespace hsma {
+
+// Host description of one system (Sec. 2.1 inputs plus the numerical parameters).
+struct SysSpec {
+  double a, eps1, eps2, kappa, tau, dy_rel, coulk;
+  int p, M, F1, F2;
+};
+
+int make_spec(double a, double eps1, double eps2, double kappa, const hsma_params* prm, SysSpec* out,
+              std::string& why);
+int tune_bucket(int64_t total_n, int nsys);
+
+// Sizes, offsets into the workspace, and work lists for a set of systems.
+struct Layout {
+  std::vector<SysDev> sd;
+  std::vector<int2> it12, it2r, it3, it5;
+  std::vector<int4> it4;
+  int cfg = 0, maxP = 1, pmax = 0, mom_stride = 3, pair_grid = 1;
+  int64_t totN = 0, totM = 0, totP = 0, totMn = 0, totMom = 0, totPart = 0;
+  size_t o_sys = 0, o_Mn = 0, o_rec_a = 0, o_rec_b = 0, o_sect = 0, o_inv_np1 = 0, o_xyz = 0, o_q = 0;
+  size_t o_src64 = 0, o_surf64a = 0, o_surf64b = 0, o_part64 = 0;
+  size_t o_srchi = 0, o_srclo = 0, o_surfa = 0, o_surfb = 0, o_part = 0;
+  size_t o_surfx = 0, o_surfqd = 0, o_vsurf = 0;
+  int max_req = 1, ditem_cap = 1, mitem_cap = 1;
+  size_t o_dreq = 0, o_ditems = 0, o_dreqit = 0, o_mitems = 0, o_dpart = 0, o_de = 0;
+  size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0;
+  size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0;
+  size_t bytes = 0;
+};
+
+class Engine {
+ public:
+  ~Engine();
+  int init(int dev, void* user_stream, int precision);
+  Layout make_layout(const std::vector<int64_t>& ns, int cfg) const;
+  int set_sizes(const std::vector<int64_t>& ns);
+  int attach(void* ptr, size_t bytes);
+  int build(const double* xyz, const double* q, bool device_inputs);
+  int potentials();
+  int check_status();
+  int delta_energy(int64_t k, const double* x_new, double* de);
+  int apply_move(int64_t k, const double* x_new);
+  int choose_config(const std::vector<int64_t>& ns) const;
+  int autotune(int reps, int* best, float* best_ms);
+  int fail(int code, const char* fmt, ...);
+  int cuda_fail(cudaError_t e, const char* what);
+  void drop_graphs();
+
+  // configuration
+  int device = -1;
+  int prec = HSMA_FP32;
+  int num_sms = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool use_graphs = true;
+  int forced_cfg = -1;
+  std::vector<std::pair<int, int>> tuned;  // (size bucket, pair config)
+  std::vector<int> occ_f32;
+  int occ_f64 = 1;
+  std::vector<SysSpec> spec;
+
+  // layout and workspace
+  Layout L;
+  std::vector<int64_t> cur_ns;
+  bool have_layout = false, layout_uploaded = false;
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  bool ws_owned = false, ws_user = false;
+
+  // device arrays (carved from the workspace)
+  SysDev* sys_d = nullptr;
+  double *Mn_d = nullptr, *rec_a_d = nullptr, *rec_b_d = nullptr, *sect_d = nullptr, *inv_np1_d = nullptr;
+  double *xyz_d = nullptr, *q_d = nullptr;
+  float4 *srchi_d = nullptr, *srclo_d = nullptr, *surfa_d = nullptr, *surfb_d = nullptr;
+  dbl4 *src64_d = nullptr, *surf64a_d = nullptr;
+  double* surf64b_d = nullptr;
+  float2* part_d = nullptr;
+  double* part64_d = nullptr;
+  double *mom_d = nullptr, *coef_d = nullptr, *r0_d = nullptr;
+  double *phic_d = nullptr, *phir_d = nullptr, *phit_d = nullptr, *epart_d = nullptr, *energy_d = nullptr;
+  unsigned int *ctr_pairs_d = nullptr, *ctr_red_d = nullptr, *ctr_delta_d = nullptr;
+  int* status_d = nullptr;
+  dbl4* surfx_d = nullptr;        // FP64 surface point and weight
+  double2* surfqd_d = nullptr;    // FP64 monopole and dipole strength
+  double2* vsurf_d = nullptr;     // potentials of the real charges under the two surface kernels
+  DeltaReq* dreq_d = nullptr;
+  int4* ditems_d = nullptr;
+  int2 *dreqit_d = nullptr, *mitems_d = nullptr;
+  double *dpart_d = nullptr, *de_d = nullptr;
+  int max_requests = 1;           // move requests per launch the layout reserves room for
+  bool v_ready = false;
+  int ensure_v();
+  // batched moves: reqs are (system, k, new position); de receives one double per request
+  int delta_batch(const std::vector<DeltaReq>& reqs, double* de_host);
+  int move_batch(const std::vector<DeltaReq>& reqs);
+  int2 *it12_d = nullptr, *it2r_d = nullptr, *it3_d = nullptr, *it5_d = nullptr;
+  int4* it4_d = nullptr;
+
+  // pair-kernel timing events (recorded around every pair-sum launch)
+  cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;
+  // ordering with the caller's legacy default stream when the handle owns its stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  void enter();
+  void leave();
+  bool pair_timed = false;
+  int last_pair_time(float* ms);
+
+  // state
+  bool sources_ready = false, pot_ready = false;
+  cudaGraphExec_t g_build = nullptr, g_pot = nullptr;
+  int64_t launches = 0;
+  std::string err;
+
+ private:
+  void carve();
+  Tables tables() const;
+  void issue_build();
+  void issue_pot();
+  int build_launch_count() const;
+  int pot_launch_count() const;
+  int run_graph(cudaGraphExec_t* g, void (Engine::*issue)());
+};
+
+}  // namespace hsma

@@ -1,0 +1,142 @@
+// Internal declarations shared by the CUDA translation units of the HSMA library.
+// Layout, per-system descriptors and kernel launchers.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hsma.h"
+
+namespace hsma {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// 32-byte FP64 record (position + strength) for the FP64 path.
+struct __align__(32) dbl4 {
+  double x, y, z, w;
+};
+__host__ __device__ __forceinline__ dbl4 make_dbl4(double x, double y, double z, double w)
+{
+  dbl4 r;
+  r.x = x;
+  r.y = y;
+  r.z = z;
+  r.w = w;
+  return r;
+}
+
+// Status bits written by kernels (the host maps them to HSMA_E_* codes).
+enum : int {
+  kStOutside = 1,    // a charge at |x| >= a or with a non-finite coordinate
+  kStNonFinite = 2,  // a non-finite potential
+  kStTimeout = 4,    // a bounded device wait gave up
+  kStBadMove = 8,    // delta-energy move target outside the cavity
+};
+
+// Charges closer to the centre than this fraction of a use the r_K -> infinity limit of
+// their Kelvin image (a constant potential); the limit differs from the image term by a
+// relative O(r |x| / a^2) <= 1e-12.
+constexpr double kCentreRel = 1e-12;
+
+// Per-system descriptor, resident on the device.  The host fills the inputs and the layout
+// offsets; k_setup fills the derived scalars (Sec. 2.3/2.4).
+struct SysDev {
+  // inputs (Sec. 2.1 and the numerical parameters)
+  double a, eps1, eps2, kappa, tau, dy_rel, coulk;
+  // derived on the device by k_setup
+  double eps, mu, Rtau, dy, gam, sig, dbar, kc;  // kc = coulk / eps1
+  double inv_a, kc_a, Rt_a, inv_Rt;              // 1/a, kc/a, R_tau/a, 1/R_tau
+  int p, P, M, F1, F2;
+  int n;              // charges
+  int prec;           // HSMA_FP32 / HSMA_FP64
+  int pad0;
+  long long chg;      // offset of this system's charges (xyz at 3*chg, q at chg, phi at chg)
+  long long src;      // offset of its 2n real+Kelvin source records (real first)
+  long long surf;     // offset of its M surface records
+  long long coef;     // offset of its P = (p+1)^2 correction coefficients
+  long long mn;       // offset of its p+1 Kirkwood coefficients M_n
+  long long mom;      // index of its first moment block
+  int mom_blocks;     // moment blocks (K12 CTAs) of this system
+  int mom_tile;       // charges per moment block
+  long long part;     // offset of its pair partials (n_chunks * n elements)
+  int ncr, nck, ncs;  // source chunks: real, Kelvin, surface
+  int chunk;          // sources per real/Kelvin chunk
+  int chunk_s;        // points per surface chunk
+  int tb;             // targets per target block
+  int n_tb;           // target blocks
+  int k5_first;       // first reduce item of this system
+  int k5_count;       // reduce items of this system
+  int pad1;
+};
+
+// Offsets of the surface-record and coefficient tables for one engine.
+struct Tables {
+  const double* rec_a;    // vertical recurrence coefficient a_nm, index n(n+1)/2 + m
+  const double* rec_b;    // vertical recurrence coefficient b_nm
+  const double* sect;     // sectoral factor sqrt((2m-1)/(2m)) (m >= 2), 1 for m = 1
+  const double* inv_np1;  // 1/(n+1), for the Legendre recurrence
+  int pmax;
+};
+
+// ---- launchers (k_sources.cu) ----
+void init_source_kernels();  // one-time function attributes (call outside stream capture)
+// Parameter-only work, once per layout: derived scalars, M_n, recurrence tables and the
+// Fibonacci points/weights of every system (written to surfx).
+void launch_setup(SysDev* sys, int nsys, double* Mn, double* rec_a, double* rec_b, double* sect, double* inv_np1,
+                  int pmax, dbl4* surfx, cudaStream_t st);
+constexpr int kCoefChunk = 32;  // coefficients per k_coef_reduce block
+void launch_images_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz,
+                           const double* q, Tables tab, float4* src_hi, float4* src_lo, dbl4* src64, int prec,
+                           double* mom, int mom_stride, int* status, cudaStream_t st);
+int moment_smem_group(int maxP);
+void launch_coef_reduce(const SysDev* sys, const int2* items, int nitems, const double* mom, int mom_stride,
+                        const double* Mn, double* coef, double* r0, cudaStream_t st);
+void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, const double* coef, Tables tab,
+                    float4* surf_a, float4* surf_b, dbl4* surf64_a, double* surf64_b, dbl4* surfx, double2* surfqd,
+                    int prec, cudaStream_t st);
+constexpr int kSurfPointsPerBlock = 8;
+constexpr int kMomTile = 96;
+
+// ---- launchers (k_pairs.cu) ----
+struct PairConfig {
+  int threads;  // CTA size
+  int k;        // targets per thread
+};
+int pair_config_count();
+PairConfig pair_config(int idx);
+int pairs_f32_occupancy(int cfg);
+int pairs_f64_occupancy();
+constexpr int kF64TargetsPerBlock = 128;
+constexpr int kReduceTargetsPerBlock = 256;
+void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
+                      const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
+                      float2* part, cudaStream_t st);
+void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
+                      const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, double* part64,
+                      cudaStream_t st);
+void launch_reduce(const SysDev* sys, int nsys, const int2* items, int nitems, const float2* part,
+                   const double* part64, int prec, const double* q, const double* r0, double* phi_c, double* phi_r,
+                   double* phi_t, double* epart, double* energy, unsigned int* counter, int* status, cudaStream_t st);
+
+// ---- single-charge moves (k_delta.cu) ----
+// One request: move charge k of system sys to (x, y, z).
+struct DeltaReq {
+  int sys;
+  int k;
+  double x, y, z;
+};
+constexpr int kDeltaBlock = 256;  // rows / surface points per delta work item
+void init_delta_kernels();
+void launch_surface_potentials(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
+                               const dbl4* surfx, double2* vsurf, cudaStream_t st);
+void launch_delta(const SysDev* sys, const int4* items, int nitems, const int2* req_items, const DeltaReq* reqs,
+                  int nreq, const double* xyz, const double* q, const float4* src_hi, const float4* src_lo,
+                  const dbl4* src64, const dbl4* surfx, const double2* surfqd, const double2* vsurf,
+                  const double* Mn, const double* inv_np1, double* dpart, double* de, unsigned int* counter,
+                  int* status, cudaStream_t st);
+void launch_move(const SysDev* sys, const int2* surf_items, int n_surf_items, const DeltaReq* reqs, int nreq,
+                 Tables tab, int maxP, double* xyz, const double* q, const double* Mn, double* coef, double* r0,
+                 const dbl4* surfx, double2* surfqd, double2* vsurf, int have_v, float4* surf_a, float4* surf_b,
+                 dbl4* surf64_a, double* surf64_b, float4* src_hi, float4* src_lo, dbl4* src64, cudaStream_t st);
+
+}  // namespace hsma

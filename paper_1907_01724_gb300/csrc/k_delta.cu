@@ -1,0 +1,466 @@
+// Single-charge moves of a Monte Carlo chain: energy change Delta E and the commit of a move.
+//
+// The paper's method (Sec. 2.4) is linear in the charges: with charge k moved from x_k to x',
+// only the terms that involve k change.  With E = E_Coul + E_Kelvin + E_corr,
+//   dE_Coul   = q_k sum_{j!=k} k q_j/eps1 (1/|x'-x_j| - 1/|x_k-x_j|)
+//   dE_Kelvin = 1/2 sum_{j!=k} [q_k (K_j(x') - K_j(x_k)) + q_j (K'_k(x_j) - K_k(x_j))]
+//               + 1/2 q_k (K'_k(x') - K_k(x_k)),
+// where K_j(x) = k q_K,j/(eps1 |x - r_K,j|) is the potential of j's modified Kelvin image
+// (a constant for a centre charge) and K'_k is k's image after the move.  The correction part
+// is E_corr = 1/2 sum_l [Q0_l V0_l + D_l V1_l], where Q0_l, D_l are the monopole/dipole
+// strengths of surface point l (linear in the coefficients A) and V0_l = sum_i q_i G0(x_i, y_l),
+// V1_l = sum_i q_i G1(x_i, y_l) are the potentials of the real charges under the two surface
+// kernels.  The move changes A by a rank-one term dA and V by dV_l = q_k (G(x', y_l) - G(x_k, y_l)):
+//   dE_corr = 1/2 sum_l [dQ0_l (V0_l + dV0_l) + Q0_l dV0_l + dD_l (V1_l + dV1_l) + D_l dV1_l].
+// The surface strengths of dA follow from the addition theorem without touching all P
+// coefficients:  Phi(y; dA) = sum_n a'_n (|x'||y|/a^2)^n P_n(xhat'.yhat) - (same for x_k), with
+// a_n = k q_k/(eps1 a) (M_n - gamma - c(x)), c(x) = dbar (R_tau |x|/a^2 - 1)/2 (Sec. 2.4).
+// Requests are batched: one launch serves many (system, k, x') requests; every request owns a
+// range of work items whose partial sums are added in a fixed order by the last block.
+#include <math.h>
+
+#include "hsma_internal.cuh"
+
+namespace hsma {
+
+constexpr int kDeltaThreads = kDeltaBlock;
+
+__device__ __forceinline__ float rsqrt_f(float x)
+{
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void split2d(double x, float& hi, float& lo)
+{
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
+// hi/lo distance^-1 between two split points (see k_pairs.cu)
+__device__ __forceinline__ float inv_hilo(float ax, float ay, float az, float alx, float aly, float alz, float bx,
+                                          float by, float bz, float blx, float bly, float blz)
+{
+  const float dx = ax - bx, dy = ay - by, dz = az - bz;
+  const float ex = (alx - blx) + dx, ey = (aly - bly) + dy, ez = (alz - blz) + dz;
+  float r2 = ex * ex;
+  r2 = fmaf(ey, ey, r2);
+  r2 = fmaf(ez, ez, r2);
+  return rsqrt_f(r2);
+}
+
+// Kelvin image of a charge (position x, charge q): position, strength k q_K/eps1, or the centre
+// constant when |x| <= kCentreRel a.  Same separately rounded operations as k_images_moments.
+struct Image {
+  double x, y, z, Q, C;  // C: constant potential of a centre charge (then Q = 0)
+  bool centre;
+};
+
+__device__ __forceinline__ Image kelvin_image(const SysDev& S, double x, double y, double z, double q)
+{
+  Image im;
+  const double a = S.a;
+  const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+  if (r <= kCentreRel * a) {
+    im.centre = true;
+    im.x = 1e15 * a;
+    im.y = im.z = 0.0;
+    im.Q = 0.0;
+    im.C = S.kc * q / a * (S.gam - 0.5 * S.dbar);
+  } else {
+    const double ar = __ddiv_rn(a, r);
+    const double s = __dmul_rn(ar, ar);
+    const double rK = __ddiv_rn(__dmul_rn(a, a), r);
+    im.centre = false;
+    im.x = __dmul_rn(s, x);
+    im.y = __dmul_rn(s, y);
+    im.z = __dmul_rn(s, z);
+    im.Q = S.kc * (q / a * (S.gam * rK + S.dbar * (S.Rtau - rK) / 2.0));
+    im.C = 0.0;
+  }
+  return im;
+}
+
+__device__ __forceinline__ double inv_dist64(double ax, double ay, double az, double bx, double by, double bz)
+{
+  const double dx = ax - bx, dy = ay - by, dz = az - bz;
+  return 1.0 / sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+
+__device__ __forceinline__ double img_pot(const Image& im, double x, double y, double z)
+{
+  return im.centre ? im.C : im.Q * inv_dist64(x, y, z, im.x, im.y, im.z);
+}
+
+// Surface kernels at point y (|y| = R_tau): G0 = 1/|x - y|; G1 is the dipole kernel of the
+// path: FP32 path the dy -> 0 limit (R_tau - x.yhat)/d^3, FP64 path the central difference
+// (1/d_- - 1/d_+)/dy = 2 (R_tau - x.yhat)/(d_+ d_- (d_+ + d_-)).
+__device__ __forceinline__ void surf_kernels(const SysDev& S, double x, double y, double z, const dbl4& yl,
+                                             double& g0, double& g1)
+{
+  const double dx = x - yl.x, dy = y - yl.y, dz = z - yl.z;
+  const double d2 = dx * dx + dy * dy + dz * dz;
+  g0 = rsqrt(d2);
+  const double hx = yl.x * S.inv_Rt, hy = yl.y * S.inv_Rt, hz = yl.z * S.inv_Rt;  // |y| = R_tau
+  const double xy = x * hx + y * hy + z * hz;
+  if (S.prec == HSMA_FP64) {
+    const double rm = S.Rtau - 0.5 * S.dy, rp = S.Rtau + 0.5 * S.dy;
+    const double mx = x - rm * hx, my = y - rm * hy, mz = z - rm * hz;
+    const double px = x - rp * hx, py = y - rp * hy, pz = z - rp * hz;
+    const double dm = sqrt(mx * mx + my * my + mz * mz);
+    const double dp = sqrt(px * px + py * py + pz * pz);
+    g1 = 2.0 * (S.Rtau - xy) / (dp * dm * (dp + dm));
+  } else {
+    g1 = (S.Rtau - xy) * (g0 * g0 * g0);
+  }
+}
+
+// Phi(y; A_x) and dPhi/dr for the coefficients of one charge q at x (addition theorem form).
+__device__ __forceinline__ void charge_series(const SysDev& S, const double* __restrict__ Mn,
+                                              const double* __restrict__ inv_np1, double x, double y, double z,
+                                              double q, const dbl4& yl, double& phi, double& dphi)
+{
+  const double a = S.a;
+  const double r2 = x * x + y * y + z * z;
+  const double r = sqrt(r2);
+  const double pref = S.kc_a * q;
+  const double c = S.dbar * (S.Rt_a * r * S.inv_a - 1.0) * 0.5;
+  if (r <= kCentreRel * a) {
+    phi = pref * (Mn[S.mn] - S.gam - c);
+    dphi = 0.0;
+    return;
+  }
+  // |y| = R_tau on the auxiliary sphere
+  const double t = (x * yl.x + y * yl.y + z * yl.z) * rsqrt(r2) * S.inv_Rt;
+  const double u = r * S.Rt_a * S.inv_a;
+  double P0 = 1.0, P1 = t, un = 1.0, s = 0.0, sd = 0.0;
+  for (int n = 0; n <= S.p; ++n) {
+    const double Pn = n == 0 ? P0 : P1;
+    const double term = (Mn[S.mn + n] - S.gam - c) * un * Pn;
+    s += term;
+    sd += (double)n * term;
+    if (n >= 1) {
+      // Bonnet: (n+1) P_{n+1} = (2n+1) t P_n - n P_{n-1}
+      const double Pn1 = ((2.0 * n + 1.0) * t * P1 - (double)n * P0) * inv_np1[n];
+      P0 = P1;
+      P1 = Pn1;
+    }
+    un *= u;
+  }
+  phi = pref * s;
+  dphi = pref * sd * S.inv_Rt;
+}
+
+// Work item: (request, kind 0 = rows / 1 = surface, block)
+__global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restrict__ sys, const int4* __restrict__ items,
+                                                         int nitems, const int2* __restrict__ req_items,
+                                                         const DeltaReq* __restrict__ reqs, int nreq,
+                                                         const double* __restrict__ xyz, const double* __restrict__ q,
+                                                         const float4* __restrict__ src_hi,
+                                                         const float4* __restrict__ src_lo,
+                                                         const dbl4* __restrict__ src64, const dbl4* __restrict__ surfx,
+                                                         const double2* __restrict__ surfqd,
+                                                         const double2* __restrict__ vsurf,
+                                                         const double* __restrict__ Mn,
+                                                         const double* __restrict__ inv_np1, double* __restrict__ dpart,
+                                                         double* __restrict__ de, unsigned int* __restrict__ counter,
+                                                         int* __restrict__ status)
+{
+  __shared__ double red[kDeltaThreads / 32];
+  __shared__ bool last;
+  const int4 it = items[blockIdx.x];
+  const DeltaReq R = reqs[it.x];
+  const SysDev& S = sys[R.sys];
+  const long long kk = S.chg + R.k;
+  const double xo = xyz[3 * kk], yo = xyz[3 * kk + 1], zo = xyz[3 * kk + 2], qk = q[kk];
+  const double xn = R.x, yn = R.y, zn = R.z;
+  double acc = 0.0;
+  const int idx = it.z * kDeltaThreads + threadIdx.x;
+  if (it.y == 0) {
+    const Image In = kelvin_image(S, xn, yn, zn, qk);
+    const Image Io = kelvin_image(S, xo, yo, zo, qk);
+    if (blockIdx.x == req_items[it.x].x && threadIdx.x == 0) {
+      const double rn2 = xn * xn + yn * yn + zn * zn;
+      if (!(rn2 < S.a * S.a) || !isfinite(rn2)) atomicOr(status, kStBadMove);
+      // the moved charge and its own image
+      acc += 0.5 * qk * (img_pot(In, xn, yn, zn) - img_pot(Io, xo, yo, zo));
+    }
+    const int j = idx;
+    if (j < S.n && j != R.k) {
+      const long long gj = S.chg + j;
+      const double qj = q[gj];
+      if (S.prec == HSMA_FP64) {
+        const dbl4 rj = src64[S.src + j];
+        const dbl4 kj = src64[S.src + S.n + j];
+        const double cn = inv_dist64(xn, yn, zn, rj.x, rj.y, rj.z), co = inv_dist64(xo, yo, zo, rj.x, rj.y, rj.z);
+        acc += qk * rj.w * (cn - co);
+        if (kj.w != 0.0) acc += 0.5 * qk * kj.w * (inv_dist64(xn, yn, zn, kj.x, kj.y, kj.z) -
+                                                   inv_dist64(xo, yo, zo, kj.x, kj.y, kj.z));
+        acc += 0.5 * qj * (img_pot(In, rj.x, rj.y, rj.z) - img_pot(Io, rj.x, rj.y, rj.z));
+      } else {
+        float nh[3], nl[3], oh[3], ol[3];
+        split2d(xn, nh[0], nl[0]); split2d(yn, nh[1], nl[1]); split2d(zn, nh[2], nl[2]);
+        split2d(xo, oh[0], ol[0]); split2d(yo, oh[1], ol[1]); split2d(zo, oh[2], ol[2]);
+        const float4 rh = src_hi[S.src + j], rl = src_lo[S.src + j];
+        const float4 kh = src_hi[S.src + S.n + j], kl = src_lo[S.src + S.n + j];
+        float t = rh.w * (inv_hilo(nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], rh.x, rh.y, rh.z, rl.x, rl.y, rl.z) -
+                          inv_hilo(oh[0], oh[1], oh[2], ol[0], ol[1], ol[2], rh.x, rh.y, rh.z, rl.x, rl.y, rl.z));
+        acc += qk * (double)t;
+        t = kh.w * (inv_hilo(nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], kh.x, kh.y, kh.z, kl.x, kl.y, kl.z) -
+                    inv_hilo(oh[0], oh[1], oh[2], ol[0], ol[1], ol[2], kh.x, kh.y, kh.z, kl.x, kl.y, kl.z));
+        acc += 0.5 * qk * (double)t;
+        // j's charge in k's image potential (images split hi/lo like the records)
+        float ih[3], il[3], jh[3], jl[3];
+        double pn, po;
+        if (In.centre) {
+          pn = In.C;
+        } else {
+          split2d(In.x, ih[0], il[0]); split2d(In.y, ih[1], il[1]); split2d(In.z, ih[2], il[2]);
+          jh[0] = rh.x; jh[1] = rh.y; jh[2] = rh.z; jl[0] = rl.x; jl[1] = rl.y; jl[2] = rl.z;
+          pn = In.Q * (double)inv_hilo(jh[0], jh[1], jh[2], jl[0], jl[1], jl[2], ih[0], ih[1], ih[2], il[0], il[1], il[2]);
+        }
+        if (Io.centre) {
+          po = Io.C;
+        } else {
+          split2d(Io.x, ih[0], il[0]); split2d(Io.y, ih[1], il[1]); split2d(Io.z, ih[2], il[2]);
+          po = Io.Q * (double)inv_hilo(rh.x, rh.y, rh.z, rl.x, rl.y, rl.z, ih[0], ih[1], ih[2], il[0], il[1], il[2]);
+        }
+        acc += 0.5 * qj * (pn - po);
+      }
+    }
+  } else {
+    const int l = idx;
+    if (l < S.M) {
+      const dbl4 yl = surfx[S.surf + l];
+      const double2 QD = surfqd[S.surf + l];
+      const double2 V = vsurf[S.surf + l];
+      double g0n, g1n, g0o, g1o, pn, dpn, po, dpo;
+      surf_kernels(S, xn, yn, zn, yl, g0n, g1n);
+      surf_kernels(S, xo, yo, zo, yl, g0o, g1o);
+      charge_series(S, Mn, inv_np1, xn, yn, zn, qk, yl, pn, dpn);
+      charge_series(S, Mn, inv_np1, xo, yo, zo, qk, yl, po, dpo);
+      const double w4 = yl.w / (4.0 * kPi);
+      const double dQ0 = w4 * (dpn - dpo), dD = w4 * (pn - po);
+      const double dV0 = qk * (g0n - g0o), dV1 = qk * (g1n - g1o);
+      acc += 0.5 * (dQ0 * (V.x + dV0) + QD.x * dV0 + dD * (V.y + dV1) + QD.y * dV1);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kDeltaThreads / 32; ++w) s += red[w];
+    dpart[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int r = threadIdx.x; r < nreq; r += kDeltaThreads) {
+    const int2 rg = req_items[r];
+    double s = 0.0;
+    for (int i = 0; i < rg.y; ++i) s += ((volatile double*)dpart)[rg.x + i];
+    de[r] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Potentials of the real charges under the two surface kernels, V0_l and V1_l (FP64; one warp
+// per surface point, fixed lane order and shuffle tree).
+__global__ __launch_bounds__(256) void k_surface_potentials(const SysDev* __restrict__ sys,
+                                                            const int2* __restrict__ items,
+                                                            const double* __restrict__ xyz,
+                                                            const double* __restrict__ q,
+                                                            const dbl4* __restrict__ surfx, double2* __restrict__ vsurf)
+{
+  const int2 it = items[blockIdx.x];
+  const SysDev& S = sys[it.x];
+  const int l = it.y * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (l >= S.M) return;
+  const dbl4 yl = surfx[S.surf + l];
+  double v0 = 0.0, v1 = 0.0;
+  for (int i = lane; i < S.n; i += 32) {
+    const long long g = S.chg + i;
+    double g0, g1;
+    surf_kernels(S, xyz[3 * g], xyz[3 * g + 1], xyz[3 * g + 2], yl, g0, g1);
+    v0 += q[g] * g0;
+    v1 += q[g] * g1;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+  }
+  if (lane == 0) vsurf[S.surf + l] = make_double2(v0, v1);
+}
+
+// Commit of a move, surface part: Q0, D, V0, V1 and the pair-sum surface records of every point.
+// Must run before k_move_charge (it reads the old position).
+__global__ __launch_bounds__(256) void k_move_surface(const SysDev* __restrict__ sys, const int2* __restrict__ items,
+                                                      const DeltaReq* __restrict__ reqs, const double* __restrict__ xyz,
+                                                      const double* __restrict__ q, const double* __restrict__ Mn,
+                                                      const double* __restrict__ inv_np1,
+                                                      const dbl4* __restrict__ surfx, double2* __restrict__ surfqd,
+                                                      double2* __restrict__ vsurf, int have_v,
+                                                      float4* __restrict__ surf_a, float4* __restrict__ surf_b,
+                                                      dbl4* __restrict__ surf64_a, double* __restrict__ surf64_b)
+{
+  const int2 it = items[blockIdx.x];  // (request, block)
+  const DeltaReq R = reqs[it.x];
+  const SysDev& S = sys[R.sys];
+  const int l = it.y * 256 + threadIdx.x;
+  if (l >= S.M) return;
+  const long long kk = S.chg + R.k;
+  const double xo = xyz[3 * kk], yo = xyz[3 * kk + 1], zo = xyz[3 * kk + 2], qk = q[kk];
+  const long long o = S.surf + l;
+  const dbl4 yl = surfx[o];
+  double pn, dpn, po, dpo;
+  charge_series(S, Mn, inv_np1, R.x, R.y, R.z, qk, yl, pn, dpn);
+  charge_series(S, Mn, inv_np1, xo, yo, zo, qk, yl, po, dpo);
+  const double w4 = yl.w / (4.0 * kPi);
+  double2 QD = surfqd[o];
+  QD.x += w4 * (dpn - dpo);
+  QD.y += w4 * (pn - po);
+  surfqd[o] = QD;
+  if (have_v) {
+    double g0n, g1n, g0o, g1o;
+    surf_kernels(S, R.x, R.y, R.z, yl, g0n, g1n);
+    surf_kernels(S, xo, yo, zo, yl, g0o, g1o);
+    double2 V = vsurf[o];
+    V.x += qk * (g0n - g0o);
+    V.y += qk * (g1n - g1o);
+    vsurf[o] = V;
+  }
+  if (S.prec == HSMA_FP64) {
+    surf64_a[o] = make_dbl4(yl.x, yl.y, yl.z, QD.x);
+    surf64_b[o] = QD.y;
+  } else {
+    surf_a[o] = make_float4((float)yl.x, (float)yl.y, (float)yl.z, (float)QD.x);
+    surf_b[o] = make_float4((float)(-QD.y / S.Rtau), 0.f, 0.f, 0.f);
+  }
+}
+
+// Commit of a move, charge part (one block per request): coefficients A += dA (two solid-harmonic
+// columns sets computed by warps 0 and 1), the real and Kelvin records of k, the centre constant,
+// and the position itself.
+__global__ __launch_bounds__(256) void k_move_charge(const SysDev* __restrict__ sys, const DeltaReq* __restrict__ reqs,
+                                                     Tables tab, double* __restrict__ xyz, const double* __restrict__ q,
+                                                     const double* __restrict__ Mn, double* __restrict__ coef,
+                                                     double* __restrict__ r0, float4* __restrict__ src_hi,
+                                                     float4* __restrict__ src_lo, dbl4* __restrict__ src64)
+{
+  extern __shared__ double sm[];
+  const DeltaReq R = reqs[blockIdx.x];
+  const SysDev& S = sys[R.sys];
+  const int P = S.P, p = S.p;
+  double* Tn = sm;
+  double* To = sm + P;
+  const long long kk = S.chg + R.k;
+  const double xo = xyz[3 * kk], yo = xyz[3 * kk + 1], zo = xyz[3 * kk + 2], qk = q[kk];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double a = S.a;
+  if (warp < 2) {
+    const double x = (warp == 0 ? R.x : xo) / a, y = (warp == 0 ? R.y : yo) / a, z = (warp == 0 ? R.z : zo) / a;
+    const double rho2 = x * x + y * y + z * z;
+    double* T = warp == 0 ? Tn : To;
+    for (int m = lane; m <= p; m += 32) {
+      double cr = 1.0, ci = 0.0;
+      for (int kq = 1; kq <= m; ++kq) {
+        const double f = tab.sect[kq];
+        const double nr = f * (cr * x - ci * y);
+        const double ni = f * (cr * y + ci * x);
+        cr = nr;
+        ci = ni;
+      }
+      T[m * m + m + m] = cr;
+      if (m) T[m * m + m - m] = ci;
+      double pr = cr, pi = ci, qr = 0.0, qi = 0.0;
+      for (int n = m + 1; n <= p; ++n) {
+        const int t = n * (n + 1) / 2 + m;
+        const double A = tab.rec_a[t] * z, B = tab.rec_b[t] * rho2;
+        const double nr = A * pr - B * qr;
+        const double ni = A * pi - B * qi;
+        T[n * n + n + m] = nr;
+        if (m) T[n * n + n - m] = ni;
+        qr = pr;
+        qi = pi;
+        pr = nr;
+        pi = ni;
+      }
+    }
+  }
+  __syncthreads();
+  const double rn = sqrt(R.x * R.x + R.y * R.y + R.z * R.z), ro = sqrt(xo * xo + yo * yo + zo * zo);
+  const double cn = S.dbar * (S.Rtau * rn / (a * a) - 1.0) * 0.5;
+  const double co = S.dbar * (S.Rtau * ro / (a * a) - 1.0) * 0.5;
+  for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+    int n = (int)sqrt((double)idx);
+    while (n * n > idx) --n;
+    while ((n + 1) * (n + 1) <= idx) ++n;
+    const double mg = Mn[S.mn + n] - S.gam;
+    coef[S.coef + idx] += S.kc / a * qk * ((mg - cn) * Tn[idx] - (mg - co) * To[idx]);
+  }
+  if (threadIdx.x == 0) {
+    const Image In = kelvin_image(S, R.x, R.y, R.z, qk);
+    const Image Io = kelvin_image(S, xo, yo, zo, qk);
+    r0[R.sys] += In.C - Io.C;
+    const long long sr = S.src + R.k, sk = S.src + S.n + R.k;
+    if (S.prec == HSMA_FP64) {
+      src64[sr] = make_dbl4(R.x, R.y, R.z, S.kc * qk);
+      src64[sk] = make_dbl4(In.x, In.y, In.z, In.Q);
+    } else {
+      float hx, hy, hz, lx, ly, lz;
+      split2d(R.x, hx, lx); split2d(R.y, hy, ly); split2d(R.z, hz, lz);
+      src_hi[sr] = make_float4(hx, hy, hz, (float)(S.kc * qk));
+      src_lo[sr] = make_float4(lx, ly, lz, 0.f);
+      split2d(In.x, hx, lx); split2d(In.y, hy, ly); split2d(In.z, hz, lz);
+      src_hi[sk] = make_float4(hx, hy, hz, (float)In.Q);
+      src_lo[sk] = make_float4(lx, ly, lz, 0.f);
+    }
+    xyz[3 * kk] = R.x;
+    xyz[3 * kk + 1] = R.y;
+    xyz[3 * kk + 2] = R.z;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+void launch_surface_potentials(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
+                               const dbl4* surfx, double2* vsurf, cudaStream_t st)
+{
+  if (nitems <= 0) return;
+  k_surface_potentials<<<nitems, 256, 0, st>>>(sys, items, xyz, q, surfx, vsurf);
+}
+
+void launch_delta(const SysDev* sys, const int4* items, int nitems, const int2* req_items, const DeltaReq* reqs,
+                  int nreq, const double* xyz, const double* q, const float4* src_hi, const float4* src_lo,
+                  const dbl4* src64, const dbl4* surfx, const double2* surfqd, const double2* vsurf,
+                  const double* Mn, const double* inv_np1, double* dpart, double* de, unsigned int* counter,
+                  int* status, cudaStream_t st)
+{
+  if (nitems <= 0) return;
+  k_delta<<<nitems, kDeltaThreads, 0, st>>>(sys, items, nitems, req_items, reqs, nreq, xyz, q, src_hi, src_lo, src64,
+                                            surfx, surfqd, vsurf, Mn, inv_np1, dpart, de, counter, status);
+}
+
+void launch_move(const SysDev* sys, const int2* surf_items, int n_surf_items, const DeltaReq* reqs, int nreq,
+                 Tables tab, int maxP, double* xyz, const double* q, const double* Mn, double* coef, double* r0,
+                 const dbl4* surfx, double2* surfqd, double2* vsurf, int have_v, float4* surf_a, float4* surf_b,
+                 dbl4* surf64_a, double* surf64_b, float4* src_hi, float4* src_lo, dbl4* src64, cudaStream_t st)
+{
+  if (nreq <= 0) return;
+  if (n_surf_items > 0)
+    k_move_surface<<<n_surf_items, 256, 0, st>>>(sys, surf_items, reqs, xyz, q, Mn, tab.inv_np1, surfx, surfqd,
+                                                 vsurf, have_v, surf_a, surf_b, surf64_a, surf64_b);
+  k_move_charge<<<nreq, 256, 2 * (size_t)maxP * sizeof(double), st>>>(sys, reqs, tab, xyz, q, Mn,
+                                                                     coef, r0, src_hi, src_lo, src64);
+}
+
+void init_delta_kernels()
+{
+  cudaFuncSetAttribute(k_move_charge, cudaFuncAttributeMaxDynamicSharedMemorySize, 120 * 1024);
+}
+
+}  // namespace hsma

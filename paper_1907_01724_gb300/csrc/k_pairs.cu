@@ -1,0 +1,467 @@
+// Direct tiled Coulomb sum of HSMA (Algorithm 1 step 5, eq. phirffinall of Fu & Gan,
+// arXiv:1907.01724) and the FP64 reduction to potentials and energies.
+//
+// Sources of one cavity: n real charges (excluding the target itself), n trapezoid-modified
+// Kelvin images, and M surface points each carrying a monopole and a dipole (the 3M discrete
+// images of eq. phicorrfinall).  Work is split into items (system, target block, source
+// chunk); persistent CTAs pull items from an atomic counter (longest items first) and write
+// one compensated FP32 partial per (chunk, target), which k_reduce sums in FP64 in a fixed
+// order, so results do not depend on scheduling.
+//
+// FP32 path (ALU bound, no tensor cores: the sum is not a dense contraction):
+//  * real and Kelvin records hold hi/lo-split coordinates; with dh the FP32 difference of the
+//    high parts (exact for nearby points) and dl that of the low parts, s = dh + dl is the
+//    coordinate difference to FP32 relative accuracy and r^2 = sum s^2, even for a charge next
+//    to its own image (4 FP32 operations per coordinate);
+//  * 1/r is one MUFU rsqrt.approx per pair;
+//  * each target keeps an FP32 partial per staged tile, folded into an (hi, lo) two-sum pair;
+//  * surface points apply the dipole layer in its dy -> 0 limit sharing the monopole's rsqrt.
+// FP64 path: the same structure in double precision with the central-difference dipole in
+// the cancellation-free form 2 (R_tau - x.yhat) / (d+ d- (d+ + d-)).
+#include <math.h>
+
+#include "hsma_internal.cuh"
+
+namespace hsma {
+
+__device__ __forceinline__ float rsqrt_mufu(float x)
+{
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+struct ChunkInfo {
+  int type;       // 0 real, 1 Kelvin, 2 surface
+  int first;      // index of the first source within its kind
+  int count;      // sources in the chunk
+  long long off;  // record offset of the first source
+};
+
+__device__ __forceinline__ ChunkInfo decode_chunk(const SysDev& S, int c)
+{
+  ChunkInfo ci;
+  if (c < S.ncr) {
+    ci.type = 0;
+    ci.first = c * S.chunk;
+    ci.count = min(S.chunk, S.n - ci.first);
+    ci.off = S.src + ci.first;
+  } else if (c < S.ncr + S.nck) {
+    ci.type = 1;
+    ci.first = (c - S.ncr) * S.chunk;
+    ci.count = min(S.chunk, S.n - ci.first);
+    ci.off = S.src + S.n + ci.first;
+  } else {
+    ci.type = 2;
+    ci.first = (c - S.ncr - S.nck) * S.chunk_s;
+    ci.count = min(S.chunk_s, S.M - ci.first);
+    ci.off = S.surf + ci.first;
+  }
+  return ci;
+}
+
+// ---------------------------------------------------------------------------------------
+template <int NT, int K>
+__global__ __launch_bounds__(NT) void k_pairs_f32(const SysDev* __restrict__ sys, const int4* __restrict__ items,
+                                                  int nitems, unsigned int* __restrict__ counter,
+                                                  const float4* __restrict__ src_hi,
+                                                  const float4* __restrict__ src_lo,
+                                                  const float4* __restrict__ surf_a,
+                                                  const float4* __restrict__ surf_b, float2* __restrict__ part)
+{
+  __shared__ __align__(16) float4 shA[2][NT];
+  __shared__ __align__(16) float4 shB[2][NT];
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= nitems) break;
+    const int4 it = items[item];
+    const SysDev& S = sys[it.x];
+    const int n = S.n;
+    const int t0 = it.y * (NT * K);
+    const ChunkInfo ch = decode_chunk(S, it.z);
+
+    // targets: hi/lo of the real records (a slot past the end repeats the block's first target)
+    float txh[K], tyh[K], tzh[K], txl[K], tyl[K], tzl[K];
+    int tix[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = t0 + k * NT + tid;
+      const int ii = i < n ? i : t0;
+      tix[k] = i;
+      const float4 h = src_hi[S.src + ii];
+      const float4 l = src_lo[S.src + ii];
+      txh[k] = h.x; tyh[k] = h.y; tzh[k] = h.z;
+      txl[k] = l.x; tyl[k] = l.y; tzl[k] = l.z;
+    }
+    float H[K], L[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) H[k] = L[k] = 0.f;
+
+    const float4* gA = ch.type == 2 ? surf_a + ch.off : src_hi + ch.off;
+    const float4* gB = ch.type == 2 ? surf_b + ch.off : src_lo + ch.off;
+    const int ntiles = (ch.count + NT - 1) / NT;
+    // the diagonal (target == source) can only occur in a real chunk overlapping the block
+    const bool diag_chunk = ch.type == 0 && ch.first < t0 + NT * K && t0 < ch.first + ch.count;
+
+    if (tid < ch.count) {
+      cp_async16(&shA[0][tid], gA + tid);
+      cp_async16(&shB[0][tid], gB + tid);
+    }
+    cp_async_commit();
+    for (int t = 0; t < ntiles; ++t) {
+      const int buf = t & 1;
+      if (t + 1 < ntiles) {
+        const int s = (t + 1) * NT + tid;
+        if (s < ch.count) {
+          cp_async16(&shA[buf ^ 1][tid], gA + s);
+          cp_async16(&shB[buf ^ 1][tid], gB + s);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const int cnt = min(NT, ch.count - t * NT);
+      const float4* A = shA[buf];
+      const float4* B = shB[buf];
+      float acc[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = 0.f;
+      if (ch.type == 2) {
+#pragma unroll 2
+        for (int s = 0; s < cnt; ++s) {
+          const float4 y = A[s];
+          const float Dp = B[s].x;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const float dx = txh[k] - y.x, dy = tyh[k] - y.y, dz = tzh[k] - y.z;
+            float r2 = dx * dx;
+            r2 = fmaf(dy, dy, r2);
+            r2 = fmaf(dz, dz, r2);
+            const float inv = rsqrt_mufu(r2);
+            float dot = dx * y.x;
+            dot = fmaf(dy, y.y, dot);
+            dot = fmaf(dz, y.z, dot);
+            const float u = dot * (inv * inv);
+            const float v = fmaf(Dp, u, y.w);
+            acc[k] = fmaf(v, inv, acc[k]);
+          }
+        }
+      } else if (diag_chunk && (ch.first + t * NT) < t0 + NT * K && t0 < ch.first + t * NT + cnt) {
+        const int sbase = ch.first + t * NT;
+        for (int s = 0; s < cnt; ++s) {
+          const float4 h = A[s];
+          const float4 l = B[s];
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const float dx = txh[k] - h.x, dy = tyh[k] - h.y, dz = tzh[k] - h.z;
+            const float ex = (txl[k] - l.x) + dx, ey = (tyl[k] - l.y) + dy, ez = (tzl[k] - l.z) + dz;
+            float r2 = ex * ex;
+            r2 = fmaf(ey, ey, r2);
+            r2 = fmaf(ez, ez, r2);
+            float inv = rsqrt_mufu(r2);
+            inv = (sbase + s == tix[k]) ? 0.f : inv;
+            acc[k] = fmaf(h.w, inv, acc[k]);
+          }
+        }
+      } else {
+#pragma unroll 2
+        for (int s = 0; s < cnt; ++s) {
+          const float4 h = A[s];
+          const float4 l = B[s];
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const float dx = txh[k] - h.x, dy = tyh[k] - h.y, dz = tzh[k] - h.z;
+            const float ex = (txl[k] - l.x) + dx, ey = (tyl[k] - l.y) + dy, ez = (tzl[k] - l.z) + dz;
+            float r2 = ex * ex;
+            r2 = fmaf(ey, ey, r2);
+            r2 = fmaf(ez, ez, r2);
+            acc[k] = fmaf(h.w, rsqrt_mufu(r2), acc[k]);
+          }
+        }
+      }
+      // two-sum fold of the tile partial
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float s = H[k] + acc[k];
+        const float bp = s - H[k];
+        L[k] += (H[k] - (s - bp)) + (acc[k] - bp);
+        H[k] = s;
+      }
+      __syncthreads();
+    }
+    float2* out = part + S.part + (long long)it.z * n;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (tix[k] < n) out[tix[k]] = make_float2(H[k], L[k]);
+  }
+}
+
+// Tile configurations (CTA threads, targets per thread); the autotuner picks one per size class.
+#define HSMA_PAIR_CONFIGS(X) \
+  X(0, 128, 4) X(1, 128, 2) X(2, 256, 2) X(3, 256, 4) X(4, 64, 4) X(5, 128, 1) X(6, 256, 1) X(7, 128, 8) \
+  X(8, 64, 2) X(9, 64, 1) X(10, 32, 2) X(11, 32, 4)
+
+static const PairConfig kPairConfigs[] = {
+#define HSMA_CFG_ENTRY(i, nt, k) {nt, k},
+    HSMA_PAIR_CONFIGS(HSMA_CFG_ENTRY)
+#undef HSMA_CFG_ENTRY
+};
+
+int pair_config_count() { return (int)(sizeof(kPairConfigs) / sizeof(kPairConfigs[0])); }
+PairConfig pair_config(int idx) { return kPairConfigs[idx]; }
+
+int pairs_f32_occupancy(int cfg)
+{
+  int b = 0;
+  switch (cfg) {
+#define HSMA_CFG_OCC(i, nt, k) \
+  case i: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_f32<nt, k>, nt, 0); break;
+    HSMA_PAIR_CONFIGS(HSMA_CFG_OCC)
+#undef HSMA_CFG_OCC
+    default: break;
+  }
+  return b;
+}
+
+void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
+                      const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
+                      float2* part, cudaStream_t st)
+{
+  switch (cfg) {
+#define HSMA_CFG_LAUNCH(i, nt, k)                                                                          \
+  case i:                                                                                                  \
+    k_pairs_f32<nt, k><<<grid, nt, 0, st>>>(sys, items, nitems, counter, src_hi, src_lo, surf_a, surf_b, part); \
+    break;
+    HSMA_PAIR_CONFIGS(HSMA_CFG_LAUNCH)
+#undef HSMA_CFG_LAUNCH
+    default: break;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 comparator path: one target per thread, plain staged loads.
+constexpr int kF64Threads = kF64TargetsPerBlock;
+
+__global__ __launch_bounds__(kF64Threads) void k_pairs_f64(const SysDev* __restrict__ sys,
+                                                           const int4* __restrict__ items, int nitems,
+                                                           unsigned int* __restrict__ counter,
+                                                           const dbl4* __restrict__ src64,
+                                                           const dbl4* __restrict__ surf64_a,
+                                                           const double* __restrict__ surf64_b,
+                                                           double* __restrict__ part64)
+{
+  __shared__ dbl4 shA[kF64Threads];
+  __shared__ double shB[kF64Threads];
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= nitems) break;
+    const int4 it = items[item];
+    const SysDev& S = sys[it.x];
+    const int n = S.n;
+    const int i = it.y * kF64Threads + tid;
+    const dbl4 tg = src64[S.src + (i < n ? i : it.y * kF64Threads)];
+    const ChunkInfo ch = decode_chunk(S, it.z);
+    const double Rt = S.Rtau, rm = S.Rtau - 0.5 * S.dy, rp = S.Rtau + 0.5 * S.dy;
+    double acc = 0.0;
+    for (int t0 = 0; t0 < ch.count; t0 += kF64Threads) {
+      const int cnt = min(kF64Threads, ch.count - t0);
+      if (tid < cnt) {
+        if (ch.type == 2) {
+          shA[tid] = surf64_a[ch.off + t0 + tid];
+          shB[tid] = surf64_b[ch.off + t0 + tid];
+        } else {
+          shA[tid] = src64[ch.off + t0 + tid];
+        }
+      }
+      __syncthreads();
+      if (ch.type == 2) {
+        for (int s = 0; s < cnt; ++s) {
+          const dbl4 y = shA[s];
+          const double D = shB[s];
+          const double dx = tg.x - y.x, dy = tg.y - y.y, dz = tg.z - y.z;
+          acc += y.w * rsqrt(dx * dx + dy * dy + dz * dz);
+          const double rho = sqrt(y.x * y.x + y.y * y.y + y.z * y.z);
+          const double hx = y.x / rho, hy = y.y / rho, hz = y.z / rho;
+          const double mx = tg.x - rm * hx, my = tg.y - rm * hy, mz = tg.z - rm * hz;
+          const double px = tg.x - rp * hx, py = tg.y - rp * hy, pz = tg.z - rp * hz;
+          const double dm = sqrt(mx * mx + my * my + mz * mz);
+          const double dp = sqrt(px * px + py * py + pz * pz);
+          const double xy = tg.x * hx + tg.y * hy + tg.z * hz;
+          acc += D * 2.0 * (Rt - xy) / (dp * dm * (dp + dm));
+        }
+      } else {
+        const int sb = ch.first + t0;
+        for (int s = 0; s < cnt; ++s) {
+          const dbl4 h = shA[s];
+          if (ch.type == 0 && sb + s == i) continue;
+          // separately rounded IEEE operations and a correctly rounded sqrt and division: the
+          // distance of a charge to its own nearby Kelvin image is ill-conditioned, so this path
+          // evaluates it exactly as the plain definition does
+          const double dx = tg.x - h.x, dy = tg.y - h.y, dz = tg.z - h.z;
+          const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+          acc += h.w / sqrt(r2);
+        }
+      }
+      __syncthreads();
+    }
+    if (i < n) part64[S.part + (long long)it.z * n + i] = acc;
+  }
+}
+
+int pairs_f64_occupancy()
+{
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_f64, kF64Threads, 0);
+  return b;
+}
+
+void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
+                      const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, double* part64,
+                      cudaStream_t st)
+{
+  k_pairs_f64<<<grid, kF64Threads, 0, st>>>(sys, items, nitems, counter, src64, surf64_a, surf64_b, part64);
+}
+
+// ---------------------------------------------------------------------------------------
+// phi_coul = sum of real-chunk partials, phi_rf = Kelvin + surface partials + centre constant,
+// energies E_total = 1/2 sum q (phi_coul + phi_rf), E_RF = 1/2 sum q phi_rf.  Fixed-order
+// block reductions; the last block to finish sums the block partials of every system in
+// order (so the result does not depend on which block ends last).
+constexpr int kRedThreads = kReduceTargetsPerBlock;
+
+__global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict__ sys, int nsys,
+                                                        const int2* __restrict__ items,
+                                                        const float2* __restrict__ part,
+                                                        const double* __restrict__ part64, int prec,
+                                                        const double* __restrict__ q, const double* __restrict__ r0,
+                                                        double* __restrict__ phi_c, double* __restrict__ phi_r,
+                                                        double* __restrict__ phi_t, double* __restrict__ epart,
+                                                        double* __restrict__ energy, unsigned int* __restrict__ counter,
+                                                        int* __restrict__ status)
+{
+  __shared__ double red[2][kRedThreads / 32];
+  __shared__ bool last;
+  const int2 it = items[blockIdx.x];
+  const SysDev& S = sys[it.x];
+  const int n = S.n;
+  const int i = it.y * kRedThreads + threadIdx.x;
+  double et = 0.0, er = 0.0;
+  if (i < n) {
+    const int nch = S.ncr + S.nck + S.ncs;
+    double pc = 0.0, pr = 0.0;
+    if (prec == HSMA_FP64) {
+      const double* b = part64 + S.part + i;
+      for (int c = 0; c < S.ncr; ++c) pc += b[(long long)c * n];
+      for (int c = S.ncr; c < nch; ++c) pr += b[(long long)c * n];
+    } else {
+      // four interleaved partial sums (fixed assignment c mod 4, fixed final order) keep
+      // several loads in flight
+      const float2* b = part + S.part + i;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int c = 0;
+      for (; c + 3 < S.ncr; c += 4) {
+        const float2 v0 = b[(long long)c * n], v1 = b[(long long)(c + 1) * n];
+        const float2 v2 = b[(long long)(c + 2) * n], v3 = b[(long long)(c + 3) * n];
+        a0 += (double)v0.x + (double)v0.y;
+        a1 += (double)v1.x + (double)v1.y;
+        a2 += (double)v2.x + (double)v2.y;
+        a3 += (double)v3.x + (double)v3.y;
+      }
+      for (; c < S.ncr; ++c) a0 += (double)b[(long long)c * n].x + (double)b[(long long)c * n].y;
+      pc = (a0 + a1) + (a2 + a3);
+      a0 = a1 = a2 = a3 = 0.0;
+      c = S.ncr;
+      for (; c + 3 < nch; c += 4) {
+        const float2 v0 = b[(long long)c * n], v1 = b[(long long)(c + 1) * n];
+        const float2 v2 = b[(long long)(c + 2) * n], v3 = b[(long long)(c + 3) * n];
+        a0 += (double)v0.x + (double)v0.y;
+        a1 += (double)v1.x + (double)v1.y;
+        a2 += (double)v2.x + (double)v2.y;
+        a3 += (double)v3.x + (double)v3.y;
+      }
+      for (; c < nch; ++c) a0 += (double)b[(long long)c * n].x + (double)b[(long long)c * n].y;
+      pr = (a0 + a1) + (a2 + a3);
+    }
+    pr += r0[it.x];
+    const long long o = S.chg + i;
+    phi_c[o] = pc;
+    phi_r[o] = pr;
+    phi_t[o] = pc + pr;
+    if (!isfinite(pc) || !isfinite(pr)) atomicOr(status, kStNonFinite);
+    const double qi = q[o];
+    et = 0.5 * qi * (pc + pr);
+    er = 0.5 * qi * pr;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    et += __shfl_xor_sync(0xffffffffu, et, o);
+    er += __shfl_xor_sync(0xffffffffu, er, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = et;
+    red[1][warp] = er;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    epart[2 * blockIdx.x] = a;
+    epart[2 * blockIdx.x + 1] = b;
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int s = threadIdx.x; s < nsys; s += kRedThreads) {
+    const SysDev& T = sys[s];
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < T.k5_count; ++k) {
+      a += ((volatile double*)epart)[2 * (T.k5_first + k)];
+      b += ((volatile double*)epart)[2 * (T.k5_first + k) + 1];
+    }
+    energy[2 * s] = a;
+    energy[2 * s + 1] = b;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+void launch_reduce(const SysDev* sys, int nsys, const int2* items, int nitems, const float2* part,
+                   const double* part64, int prec, const double* q, const double* r0, double* phi_c, double* phi_r,
+                   double* phi_t, double* epart, double* energy, unsigned int* counter, int* status, cudaStream_t st)
+{
+  if (nitems <= 0) return;
+  k_reduce<<<nitems, kRedThreads, 0, st>>>(sys, nsys, items, part, part64, prec, q, r0, phi_c, phi_r, phi_t, epart,
+                                           energy, counter, status);
+}
+
+}  // namespace hsma

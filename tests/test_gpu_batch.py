@@ -1,0 +1,130 @@
+"""Batched evaluation of many independent cavities through the C ABI (hsma_batch_*).
+
+Each system of a batch must match the oracle at the path's tolerance, and be bitwise identical
+to the same system evaluated alone with the same pair-sum tile configuration.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_01724_gb300 import api, batch, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {api.HSMA_FP32: 1e-6, api.HSMA_FP64: 1e-12}
+
+
+def mixed_systems(seed=3, sizes=(0, 1, 7, 100, 333, 1000, 2048, 3001)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, n in enumerate(sizes):
+        a = float(rng.uniform(0.8, 1.5))
+        ka = float(rng.uniform(0.5, 3.0))
+        eps1 = 1.0 if i % 2 else 78.5
+        out.append(inputs.System(a, eps1, 78.5, ka / a, 12, 400, inputs.uniform_ball(rng, n, a),
+                                 inputs.neutral_charges(rng, n) if n > 1 else np.ones(n)))
+    return out
+
+
+def oracle_of(s):
+    P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+    return oracle.hsma(P, s.xyz, s.q)
+
+
+@pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
+def test_batch_matches_oracle_per_system(prec):
+    systems = mixed_systems()
+    b = batch.from_systems(systems, precision=prec)
+    n, xyz, q = batch.concat(systems)
+    b.hsma_batch_build_sources(n, xyz, q)
+    phi = b.hsma_batch_potential()
+    et, er = b.hsma_batch_energy()
+    off = 0
+    for s, e_t, e_r in zip(systems, et, er):
+        p = phi[off:off + s.n]
+        off += s.n
+        if s.n == 0:
+            assert e_t == 0.0 and e_r == 0.0
+            continue
+        ref = oracle_of(s)
+        assert np.linalg.norm(p - ref["phi"]) / np.linalg.norm(ref["phi"]) <= TOL[prec]
+        scale = max(abs(ref["E_total"]), 0.5 * np.sum(np.abs(s.q * ref["phi"])))
+        assert abs(e_t - ref["E_total"]) <= TOL[prec] * scale
+
+
+@pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
+def test_batch_equals_alone_bitwise(prec):
+    systems = mixed_systems(seed=9, sizes=(5, 640, 1500, 77))
+    b = batch.from_systems(systems, precision=prec)
+    if prec == api.HSMA_FP32:
+        b.hsma_batch_set_pair_config(0)
+    n, xyz, q = batch.concat(systems)
+    b.hsma_batch_build_sources(n, xyz, q)
+    phi = b.hsma_batch_potential()
+    et, _ = b.hsma_batch_energy()
+    off = 0
+    for i, s in enumerate(systems):
+        alone = api.solve(s, precision=prec)
+        assert np.array_equal(alone.phi, phi[off:off + s.n]), i
+        assert alone.E_total == et[i]
+        off += s.n
+
+
+@pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
+def test_batched_moves_match_single_handles(prec):
+    systems = mixed_systems(seed=21, sizes=(50, 400, 900))
+    b = batch.from_systems(systems, precision=prec, max_requests=8)
+    n, xyz, q = batch.concat(systems)
+    b.hsma_batch_build_sources(n, xyz, q)
+    rng = np.random.default_rng(4)
+    sys_idx, ks, xs = [], [], []
+    for r in range(6):
+        si = r % len(systems)
+        s = systems[si]
+        k = int(rng.integers(s.n))
+        x_new = s.xyz[k] * 0.9
+        sys_idx.append(si)
+        ks.append(k)
+        xs.append(x_new)
+    de = b.hsma_batch_delta_energy(sys_idx, ks, xs)
+    for r in range(6):
+        s = systems[sys_idx[r]]
+        prm = api.hsma_default_params(p=s.p, M=s.M, precision=prec)
+        h = api.hsma_create(s.a, s.eps1, s.eps2, s.kappa, prm)
+        api.hsma_build_sources(h, s.xyz, s.q)
+        d1 = api.hsma_delta_energy(h, ks[r], xs[r])
+        assert abs(d1 - de[r]) <= 1e-12 * (abs(d1) + 1.0)
+    # commit one move per system, then compare with the oracle on the moved configurations
+    b.hsma_batch_apply_moves(sys_idx[:3], ks[:3], xs[:3])
+    et, _ = b.hsma_batch_energy()
+    for r in range(3):
+        s = systems[sys_idx[r]]
+        xyz2 = s.xyz.copy()
+        xyz2[ks[r]] = xs[r]
+        ref = oracle_of(inputs.System(s.a, s.eps1, s.eps2, s.kappa, s.p, s.M, xyz2, s.q))
+        scale = max(abs(ref["E_total"]), 0.5 * np.sum(np.abs(s.q * ref["phi"])))
+        assert abs(et[sys_idx[r]] - ref["E_total"]) <= 4 * TOL[prec] * scale
+
+
+def test_two_moves_of_one_system_rejected():
+    systems = mixed_systems(seed=2, sizes=(20, 30))
+    b = batch.from_systems(systems, max_requests=4)
+    n, xyz, q = batch.concat(systems)
+    b.hsma_batch_build_sources(n, xyz, q)
+    with pytest.raises(api.HsmaError):
+        b.hsma_batch_apply_moves([0, 0], [1, 2], [systems[0].xyz[1] * 0.5, systems[0].xyz[2] * 0.5])
+
+
+def test_autotune_picks_a_valid_config_and_stays_accurate():
+    systems = mixed_systems(seed=5, sizes=(1000, 2000, 300))
+    b = batch.from_systems(systems)
+    n, xyz, q = batch.concat(systems)
+    b.hsma_batch_build_sources(n, xyz, q)
+    cfg, ms = b.hsma_batch_autotune(3)
+    assert 0 <= cfg < len(batch.pair_configs()) and ms > 0
+    phi = b.hsma_batch_potential()
+    off = 0
+    for s in systems:
+        ref = oracle_of(s)
+        assert np.linalg.norm(phi[off:off + s.n] - ref["phi"]) / np.linalg.norm(ref["phi"]) <= 1e-6
+        off += s.n
