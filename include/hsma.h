@@ -208,6 +208,26 @@ HSMA_API int hsma_pair_config_info(int idx, int* threads, int* targets_per_threa
 HSMA_API int hsma_batch_set_pair_config(hsma_batch_t* b, int cfg);
 HSMA_API int hsma_batch_autotune(hsma_batch_t* b, int reps, int* best, float* best_ms);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free Coulomb sum.  The paper has no counterpart: this is a service for callers
+ * that may not allocate device memory (code running while a larger application captures a
+ * CUDA graph, allocator or memory-pool callbacks, real-time loops with a fixed memory
+ * budget).  It computes phi[i] = k_over_eps1 * sum_{j != i} q[j] / |x_i - x_j| for n charges
+ * with the library's FP32 tiled pair sum (hi/lo split coordinates, compensated partials;
+ * the same numbers as hsma_potential(..., HSMA_COULOMB) up to the FP32 tolerance).
+ *   xyz_dev (n,3), q_dev (n): device inputs; phi_dev (n): device output; stream: a
+ *   cudaStream_t or NULL (legacy default stream); the call is asynchronous on it.
+ *   n <= HSMA_NOALLOC_MAX_N, else HSMA_E_INVALID_ARG (nothing is launched).
+ * It calls no cudaMalloc/cudaFree or other allocating routine.  Its scratch memory (8 MB of
+ * partial sums and counters) is a static device array that every GPU loading the library
+ * keeps until the process exits.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress, with the device current): make that first call before any stream
+ * capture.  All calls share the array: calls that may overlap on the GPU (different streams
+ * without ordering, or several host threads) race and must be serialised by the caller. */
+#define HSMA_NOALLOC_MAX_N 32768
+HSMA_API int hsma_coulomb_potential_noalloc(int64_t n, const double* xyz_dev, const double* q_dev,
+                                            double k_over_eps1, double* phi_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ CSRC = os.path.join(_HERE, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_HERE, "_build")
 LIB = os.path.join(BUILD, "libhsma.so")
-SOURCES = ["k_sources.cu", "k_pairs.cu", "k_delta.cu", "engine.cu", "batch.cu"]  # those present are built
+SOURCES = ["k_sources.cu", "k_pairs.cu", "k_delta.cu", "engine.cu", "batch.cu", "noalloc.cu"]
 HEADERS = ["hsma_internal.cuh", "engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
@@ -143,6 +143,7 @@ def _declare(lib):
         "hsma_batch_set_pair_config": (ctypes.c_int, [vp, ctypes.c_int]),
         "hsma_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_float)]),
+        "hsma_coulomb_potential_noalloc": (ctypes.c_int, [i64, vp, vp, ctypes.c_double, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
