@@ -129,14 +129,21 @@ def barrier(world):
         dist.barrier()
 
 
-def allreduce(world, x: float, op: str) -> float:
+def allreduce(world, x: float, op: str, device: str = "cuda") -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def aggregate(world: int, local_seconds: float, local_units: float, device: str = "cuda"):
+    """Whole-job throughput over ranks: units of all ranks / the slowest rank's time."""
+    t_max = allreduce(world, local_seconds, "max", device)
+    units = allreduce(world, local_units, "sum", device)
+    return units / t_max, t_max, units
 
 
 def oracle_run(systems, budget_s: float = 10.0, max_rounds: int = 50):
@@ -158,6 +165,120 @@ def oracle_run(systems, budget_s: float = 10.0, max_rounds: int = 50):
         if el >= budget_s or rounds >= max_rounds:
             break
     return refs, done / el, el, rounds, oracle.threads()
+
+
+def run_batched(local, stream, gpu_name):
+    """512 independent cavities (N log-uniform in [100, 1e4]) in one batch: build + potentials +
+    energies per launch pair; requests = systems evaluated.  Compared with the plain FP64
+    single-system path (one handle per system, sequential) on a seeded subset, scaled by pairs."""
+    import torch
+
+    from paper_1907_01724_gb300 import api, batch
+    systems = inputs.batched_systems()
+    n, xyz, q = batch.concat(systems)
+    b = batch.from_systems(systems, device=local, stream=stream)
+    cfg = batch.autotuned(b, n, xyz, q, gpu=gpu_name, reps=3)
+    xyz_d = torch.tensor(xyz, device=f"cuda:{local}")
+    q_d = torch.tensor(q, device=f"cuda:{local}")
+    phi_d = torch.empty(int(n.sum()), dtype=torch.float64, device=f"cuda:{local}")
+    for _ in range(2):
+        b.hsma_batch_build_sources(n, xyz_d, q_d)
+        b.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
+    torch.cuda.synchronize()
+    k = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        b.hsma_batch_build_sources(n, xyz_d, q_d)
+        b.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    tot_pairs = sum(pairs(s) for s in systems)
+    et, _ = b.hsma_batch_energy()
+    # accuracy on a seeded sample against the oracle
+    import oracle
+    rng = np.random.default_rng(7)
+    sample = sorted(rng.choice(len(systems), 4, replace=False).tolist())
+    worst = 0.0
+    for i in sample:
+        s = systems[i]
+        P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M)
+        r = oracle.hsma(P, s.xyz, s.q)
+        scale = max(abs(r["E_total"]), 0.5 * float(np.sum(np.abs(s.q * r["phi"]))))
+        worst = max(worst, abs(et[i] - r["E_total"]) / scale)
+    # plain FP64 single-system path on a seeded subset of 16 systems
+    sub = sorted(rng.choice(len(systems), 16, replace=False).tolist())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in sub:
+        s = systems[i]
+        prm = api.hsma_default_params(p=s.p, M=s.M, tau=s.tau, precision=api.HSMA_FP64, device=local)
+        h = api.hsma_create(s.a, s.eps1, s.eps2, s.kappa, prm)
+        api.hsma_build_sources(h, s.xyz, s.q)
+        api.hsma_energy(h)
+    t64 = time.perf_counter() - t0
+    sub_pairs = sum(pairs(systems[i]) for i in sub)
+    fp64_req_s = len(sub) / t64
+    fp64_pairs_s = sub_pairs / t64
+    return {"workload": f"{len(systems)} cavities, N log-uniform [100, 1e4] (sum {int(n.sum())}), a~U[0.8,1.5], "
+                        "kappa*a~U[0.5,3], eps1 in {1, 78.5}, eps2=78.5, M=1000, p=20",
+            "req_per_s": len(systems) * k / t, "pair_evals_per_s": tot_pairs * k / t, "ms_per_batch": t / k * 1e3,
+            "pair_config": batch.pair_configs()[cfg], "energy_rel_err_max_vs_oracle_sample": worst,
+            "fp64_single_system": {"req_per_s": fp64_req_s, "pair_evals_per_s": fp64_pairs_s,
+                                   "sample": "16 seeded systems, one FP64 handle each, host inputs"}}
+
+
+def run_serving(local):
+    """64 Monte Carlo chains (N log-uniform in [500, 5e4]), 90% move / 10% full-energy requests.
+    Saturation = all requests released at once; then Poisson arrivals at 0.25/0.5/0.8/0.95 of it."""
+    from paper_1907_01724_gb300 import api, server
+    wl = inputs.serving_workload()
+    srv = server.Server(wl.chains, max_batch=64, energy_slots=4, energy_sm_frac=0.75, device=local)
+    srv.hsma_server_load()
+    pos = [c.xyz.copy() for c in wl.chains]
+    # warm-up and saturation
+    reqs, pos = server.make_trace(wl, 500, None, pos)
+    srv.hsma_server_run(reqs)
+    reqs, pos = server.make_trace(wl, 3000, None, pos)
+    res = srv.hsma_server_run(reqs)
+    sat = server.latency_stats(res)
+    out = {"workload": "64 chains, N log-uniform [500, 5e4] (sum %d), M=1000, p=20; 90%% single-move dE "
+                       "(commit with p=0.5), 10%% full energies" % sum(c.n for c in wl.chains),
+           "saturation": sat, "loads": {}}
+    for f in (0.25, 0.5, 0.8, 0.95):
+        rate = f * sat["req_per_s"]
+        nreq = int(min(20000, max(300, rate * 1.0)))
+        reqs, pos = server.make_trace(wl, nreq, rate, pos)
+        res = srv.hsma_server_run(reqs)
+        st = server.latency_stats(res)
+        st["offered_req_per_s"] = rate
+        out["loads"][str(f)] = st
+    # plain FP64 single-system path: the same kind of requests, one handle per chain, sequential
+    rng = np.random.default_rng(11)
+    lat = []
+    for c in sorted(rng.choice(len(wl.chains), 4, replace=False).tolist()):
+        ch = wl.chains[c]
+        prm = api.hsma_default_params(p=ch.p, M=ch.M, tau=ch.tau, precision=api.HSMA_FP64, device=local)
+        h = api.hsma_create(ch.a, ch.eps1, ch.eps2, ch.kappa, prm)
+        api.hsma_build_sources(h, ch.xyz, ch.q)
+        api.hsma_energy(h)
+        for j in range(10):
+            k = int(rng.integers(ch.n))
+            x = ch.xyz[k] * 0.98
+            t0 = time.perf_counter()
+            if j % 10 == 9:
+                api.hsma_build_sources(h, ch.xyz, ch.q)
+                api.hsma_energy(h)
+            else:
+                api.hsma_delta_energy(h, k, x)
+            lat.append(time.perf_counter() - t0)
+    lat = np.array(lat)
+    out["fp64_single_system"] = {"p50_ms": float(np.percentile(lat, 50) * 1e3),
+                                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                                 "req_per_s": float(len(lat) / lat.sum()),
+                                 "sample": "40 requests (9 moves : 1 full energy) on 4 seeded chains, sequential"}
+    return out
 
 
 def run_ours(args):
@@ -232,9 +353,7 @@ def run_ours(args):
     barrier(world)
     launches = b.hsma_batch_kernel_launches() - launches0
     t_local = sum(a.elapsed_time(c) for a, c in ev) / 1e3
-    t_max = allreduce(world, t_local, "max")
-    total_pairs = allreduce(world, float(sum(pairs(s) for s in systems) * args.steps), "sum")
-    value = total_pairs / t_max
+    value, t_max, total_pairs = aggregate(world, t_local, float(sum(pairs(s) for s in systems) * args.steps))
 
     # dominant kernel alone: evaluations per launch / event-timed launch duration
     ev_per_launch = sum(evals(s) for s in systems)
@@ -293,6 +412,11 @@ def run_ours(args):
            "d2h_bytes_per_step": int(8 * n.sum() + 16 * len(systems)), "steps": ke,
            "ms_per_step": te / ke * 1e3}
 
+    batched = serving = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        batched = run_batched(local, stream, gpu_name)
+        serving = run_serving(local)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
@@ -300,7 +424,7 @@ def run_ours(args):
                 "data": "synthetic (seeded random charges in the ball, 25% near the interface)",
                 "config": config_dict(systems, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches), "accuracy_vs_oracle": acc, "fp64_path": fp64,
-                "impl": "ours"}
+                "batched": batched, "serving": serving, "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -346,6 +470,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sections")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

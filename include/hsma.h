@@ -135,6 +135,12 @@ HSMA_API int hsma_delta_energy(hsma_t* h, int64_t k, const double* x_new, double
  * resident sources incrementally; equivalent to rebuilding with the moved charge. */
 HSMA_API int hsma_apply_move(hsma_t* h, int64_t k, const double* x_new);
 
+/* Truncated correction coefficients of the current sources (eq. phim), in the real
+ * normalised solid-harmonic basis T_nm (sum_m T_nm(x) T_nm(y) = |x|^n |y|^n P_n(cos angle)):
+ * Phi_corr(y) = sum_{n<=p, |m|<=n} out[n^2 + n + m] T_nm(y/a), with m < 0 the sine part.
+ * out: host array of len >= (p+1)^2 doubles.  Synchronises the stream. */
+HSMA_API int hsma_coefficients(hsma_t* h, double* out, int64_t len);
+
 /* Number of the library's kernel launches issued so far by this handle (for accounting). */
 HSMA_API int64_t hsma_kernel_launches(const hsma_t* h);
 
@@ -207,6 +213,70 @@ HSMA_API int hsma_pair_config_count(void);
 HSMA_API int hsma_pair_config_info(int idx, int* threads, int* targets_per_thread);
 HSMA_API int hsma_batch_set_pair_config(hsma_batch_t* b, int cfg);
 HSMA_API int hsma_batch_autotune(hsma_batch_t* b, int reps, int* best, float* best_ms);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: Monte Carlo chains (independent cavities) resident on the device, answering
+ * single-charge-move energy changes and full energies as requests arrive.  The request loop
+ * is native (host thread of the caller) and does continuous batching: released requests wait
+ * in a FIFO per chain (one request of a chain in flight at a time, so a chain's results follow
+ * its own order); every ready move request of every idle chain joins the next batched
+ * Delta-E launch (high-priority stream; accepted moves are committed in the same launch
+ * sequence), while full-energy requests run concurrently on low-priority streams with a pair
+ * kernel limited to part of the GPU, so move batches keep running beside them.
+ * --------------------------------------------------------------------------------------- */
+typedef struct hsma_server_t hsma_server_t;
+
+#define HSMA_REQ_DELTA 0   /* energy change of moving charge k of the chain to x; commit if accept */
+#define HSMA_REQ_ENERGY 1  /* total energy of the chain's current configuration */
+
+typedef struct {
+  double t_arrival;  /* release time in seconds after the start of hsma_server_run */
+  int chain;         /* chain (system) index */
+  int kind;          /* HSMA_REQ_DELTA or HSMA_REQ_ENERGY */
+  int accept;        /* DELTA: commit the move after computing Delta E (the caller's MC decision) */
+  int pad;
+  int64_t k;         /* DELTA: charge index */
+  double x[3];       /* DELTA: new position, |x| < a */
+  int64_t id;        /* caller's tag, copied to the result */
+} hsma_request;
+
+typedef struct {
+  int64_t id;        /* the request's tag */
+  int status;        /* HSMA_OK, HSMA_E_BUSY (chain not admitted), HSMA_E_OUTSIDE, ... */
+  int pad;
+  double value;      /* Delta E, or E_total */
+  double t_arrival;  /* release time (s, run clock) */
+  double t_done;     /* completion seen by the loop (s, run clock) */
+} hsma_result;
+
+/* Create a server for nchains cavities (arrays as for hsma_batch_create; common params).
+ * hbm_budget_bytes bounds the device memory of the resident chains (0 = no bound);
+ * max_batch bounds the move requests per batched launch; energy_slots is the number of
+ * full-energy requests that may run at once; energy_sm_frac in (0, 1] is the fraction of the
+ * GPU's resident-block slots a full-energy pair kernel may occupy. */
+HSMA_API int hsma_server_create(int nchains, const double* a, const double* eps1, const double* eps2,
+                                const double* kappa, const hsma_params* params, size_t hbm_budget_bytes,
+                                int max_batch, int energy_slots, double energy_sm_frac, hsma_server_t** out);
+HSMA_API void hsma_server_destroy(hsma_server_t* s);
+HSMA_API const char* hsma_server_last_error(const hsma_server_t* s);
+
+/* Initial charges of every chain: n[nchains], xyz (sum n, 3), q (sum n), host.  Chains are
+ * admitted in index order while their device footprint fits the budget; their sources are
+ * built on the device.  *admitted (nullable) receives the number of resident chains. */
+HSMA_API int hsma_server_load(hsma_server_t* s, const int64_t* n, const double* xyz, const double* q,
+                              int* admitted);
+
+/* Evict chain c (frees its share of the budget) and admit waiting chains that now fit,
+ * rebuilding the resident set from the committed host-side state. */
+HSMA_API int hsma_server_close_chain(hsma_server_t* s, int c, int* admitted);
+
+/* Replay nreq requests (any order of t_arrival) in real time on the calling thread and
+ * return when all are answered; results[r] answers reqs[r].  Requests of non-resident chains
+ * are answered with HSMA_E_BUSY. */
+HSMA_API int hsma_server_run(hsma_server_t* s, int nreq, const hsma_request* reqs, hsma_result* results);
+
+/* Current positions of chain c (n_c x 3 doubles, host) after the committed moves. */
+HSMA_API int hsma_server_positions(hsma_server_t* s, int c, double* xyz_out, int64_t n);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free Coulomb sum.  The paper has no counterpart: this is a service for callers

@@ -19,8 +19,8 @@ CSRC = os.path.join(_HERE, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_HERE, "_build")
 LIB = os.path.join(BUILD, "libhsma.so")
-SOURCES = ["k_sources.cu", "k_pairs.cu", "k_delta.cu", "engine.cu", "batch.cu", "noalloc.cu"]
-HEADERS = ["hsma_internal.cuh", "engine.h"]
+SOURCES = ["k_sources.cu", "k_pairs.cu", "k_delta.cu", "engine.cu", "batch.cu", "server.cu", "noalloc.cu"]
+HEADERS = ["hsma_internal.cuh", "engine.h", "df64.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 LINK_FLAGS = ["-Xlinker", "--exclude-libs,ALL", "-Xcompiler", "-fPIC"]
@@ -122,6 +122,7 @@ def _declare(lib):
         "hsma_apply_move": (ctypes.c_int, [vp, i64, vp]),
         "hsma_kernel_launches": (ctypes.c_int64, [vp]),
         "hsma_last_pair_time": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
+        "hsma_coefficients": (ctypes.c_int, [vp, vp, i64]),
         "hsma_batch_create": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, vp, pp, ctypes.POINTER(vp)]),
         "hsma_batch_destroy": (None, [vp]),
         "hsma_batch_last_error": (ctypes.c_char_p, [vp]),
@@ -144,6 +145,14 @@ def _declare(lib):
         "hsma_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_float)]),
         "hsma_coulomb_potential_noalloc": (ctypes.c_int, [i64, vp, vp, ctypes.c_double, vp, vp]),
+        "hsma_server_create": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, vp, pp, sz, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_double, ctypes.POINTER(vp)]),
+        "hsma_server_destroy": (None, [vp]),
+        "hsma_server_last_error": (ctypes.c_char_p, [vp]),
+        "hsma_server_load": (ctypes.c_int, [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]),
+        "hsma_server_close_chain": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "hsma_server_run": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "hsma_server_positions": (ctypes.c_int, [vp, ctypes.c_int, vp, i64]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)

@@ -191,6 +191,13 @@ def hsma_kernel_launches(h: Handle) -> int:
     return int(_native.load().hsma_kernel_launches(h.ptr))
 
 
+def hsma_coefficients(h: Handle, p: int) -> np.ndarray:
+    """Correction coefficients (eq. phim) in the real normalised solid-harmonic basis, (p+1)^2 values."""
+    out = np.empty((p + 1) ** 2, dtype=np.float64)
+    _check(_native.load().hsma_coefficients(h.ptr, _dptr(out), out.size), h.ptr)
+    return out
+
+
 def hsma_last_pair_time(h: Handle) -> float:
     """Milliseconds of the most recent pair-sum kernel launch (CUDA events on the handle's stream)."""
     ms = ctypes.c_float()

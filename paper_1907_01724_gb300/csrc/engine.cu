@@ -242,6 +242,9 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_rec_b = take(8 * (size_t)ntri);
   L.o_sect = take(8 * (size_t)(L.pmax + 1));
   L.o_inv_np1 = take(8 * (size_t)(L.pmax + 1));
+  L.o_rec_a2 = take(8 * (size_t)ntri);
+  L.o_rec_b2 = take(8 * (size_t)ntri);
+  L.o_sect2 = take(8 * (size_t)(L.pmax + 1));
   L.o_xyz = take(24 * L.totN);
   L.o_q = take(8 * L.totN);
   if (prec == HSMA_FP64) {
@@ -289,6 +292,14 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_it3 = take(sizeof(int2) * L.it3.size());
   L.o_it5 = take(sizeof(int2) * L.it5.size());
   L.o_it4 = take(sizeof(int4) * L.it4.size());
+  L.sel.resize(nsys);
+  L.selrng.resize(nsys);
+  for (int s = 0; s < nsys; ++s) {
+    L.sel[s] = s;
+    L.selrng[s] = make_int2(L.sd[s].k5_first, L.sd[s].k5_count);
+  }
+  L.o_sel = take(sizeof(int) * (size_t)nsys);
+  L.o_selrng = take(sizeof(int2) * (size_t)nsys);
   L.bytes = off;
   return L;
 }
@@ -302,6 +313,9 @@ void Engine::carve()
   rec_b_d = (double*)(b + L.o_rec_b);
   sect_d = (double*)(b + L.o_sect);
   inv_np1_d = (double*)(b + L.o_inv_np1);
+  rec_a2_d = (float2*)(b + L.o_rec_a2);
+  rec_b2_d = (float2*)(b + L.o_rec_b2);
+  sect2_d = (float2*)(b + L.o_sect2);
   xyz_d = (double*)(b + L.o_xyz);
   q_d = (double*)(b + L.o_q);
   if (prec == HSMA_FP64) {
@@ -349,6 +363,8 @@ void Engine::carve()
   it3_d = (int2*)(b + L.o_it3);
   it5_d = (int2*)(b + L.o_it5);
   it4_d = (int4*)(b + L.o_it4);
+  sel_d = (int*)(b + L.o_sel);
+  selrng_d = (int2*)(b + L.o_selrng);
 }
 
 int Engine::attach(void* ptr, size_t bytes)
@@ -403,10 +419,13 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
     CK(cudaMemcpyAsync(it5_d, L.it5.data(), sizeof(int2) * L.it5.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it4.empty())
     CK(cudaMemcpyAsync(it4_d, L.it4.data(), sizeof(int4) * L.it4.size(), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(sel_d, L.sel.data(), sizeof(int) * L.sel.size(), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(selrng_d, L.selrng.data(), sizeof(int2) * L.selrng.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemsetAsync(ctr_pairs_d, 0, 16, stream));
   CK(cudaMemsetAsync(energy_d, 0, 16 * L.sd.size(), stream));
   // parameter-only quantities (row a1: scalars, M_n, tables, quadrature grid), once per layout
-  launch_setup(sys_d, (int)L.sd.size(), Mn_d, rec_a_d, rec_b_d, sect_d, inv_np1_d, L.pmax, surfx_d, stream);
+  launch_setup(sys_d, (int)L.sd.size(), Mn_d, rec_a_d, rec_b_d, sect_d, inv_np1_d, rec_a2_d, rec_b2_d, sect2_d,
+               L.pmax, surfx_d, stream);
   CK(cudaGetLastError());
   launches += 1;
   CK(cudaStreamSynchronize(stream));
@@ -422,6 +441,9 @@ Tables Engine::tables() const
   t.rec_b = rec_b_d;
   t.sect = sect_d;
   t.inv_np1 = inv_np1_d;
+  t.rec_a2 = rec_a2_d;
+  t.rec_b2 = rec_b2_d;
+  t.sect2 = sect2_d;
   t.pmax = L.pmax;
   return t;
 }
@@ -454,8 +476,8 @@ void Engine::issue_pot()
                        surfb_d, part_d, stream);
     cudaEventRecordWithFlags(ev_pair1, stream, cudaEventRecordExternal);
   }
-  launch_reduce(sys_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, r0_d, phic_d, phir_d, phit_d,
-                epart_d, energy_d, ctr_red_d, status_d, stream);
+  launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, r0_d, phic_d,
+                phir_d, phit_d, epart_d, energy_d, ctr_red_d, status_d, stream);
 }
 
 int Engine::pot_launch_count() const { return (L.it4.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1); }
@@ -827,6 +849,17 @@ int hsma_apply_move(hsma_t* h, int64_t k, const double* x_new)
 }
 
 int64_t hsma_kernel_launches(const hsma_t* h) { return h ? h->e->launches : 0; }
+
+int hsma_coefficients(hsma_t* h, double* out, int64_t len)
+{
+  if (!h || !out) return HSMA_E_INVALID_ARG;
+  if (h->n < 0 || !h->e->sources_ready) return set_err(h, HSMA_E_STATE, "sources have not been built");
+  const int P = h->e->L.sd[0].P;
+  if (len < P) return set_err(h, HSMA_E_INVALID_ARG, "output shorter than (p+1)^2");
+  cudaError_t e = cudaMemcpyAsync(out, h->e->coef_d, 8 * (size_t)P, cudaMemcpyDeviceToHost, h->e->stream);
+  if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy coefficients"));
+  return from_engine(h, h->e->check_status());
+}
 
 int hsma_last_pair_time(hsma_t* h, float* ms)
 {

@@ -24,9 +24,13 @@ struct Layout {
   std::vector<SysDev> sd;
   std::vector<int2> it12, it2r, it3, it5;
   std::vector<int4> it4;
+  std::vector<int> sel;       // all systems, in order (energy pass of a full launch)
+  std::vector<int2> selrng;   // their reduce-item ranges
+  size_t o_sel = 0, o_selrng = 0;
   int cfg = 0, maxP = 1, pmax = 0, mom_stride = 3, pair_grid = 1;
   int64_t totN = 0, totM = 0, totP = 0, totMn = 0, totMom = 0, totPart = 0;
   size_t o_sys = 0, o_Mn = 0, o_rec_a = 0, o_rec_b = 0, o_sect = 0, o_inv_np1 = 0, o_xyz = 0, o_q = 0;
+  size_t o_rec_a2 = 0, o_rec_b2 = 0, o_sect2 = 0;
   size_t o_src64 = 0, o_surf64a = 0, o_surf64b = 0, o_part64 = 0;
   size_t o_srchi = 0, o_srclo = 0, o_surfa = 0, o_surfb = 0, o_part = 0;
   size_t o_surfx = 0, o_surfqd = 0, o_vsurf = 0;
@@ -79,6 +83,7 @@ class Engine {
   // device arrays (carved from the workspace)
   SysDev* sys_d = nullptr;
   double *Mn_d = nullptr, *rec_a_d = nullptr, *rec_b_d = nullptr, *sect_d = nullptr, *inv_np1_d = nullptr;
+  float2 *rec_a2_d = nullptr, *rec_b2_d = nullptr, *sect2_d = nullptr;
   double *xyz_d = nullptr, *q_d = nullptr;
   float4 *srchi_d = nullptr, *srclo_d = nullptr, *surfa_d = nullptr, *surfb_d = nullptr;
   dbl4 *src64_d = nullptr, *surf64a_d = nullptr;
@@ -103,6 +108,8 @@ class Engine {
   int delta_batch(const std::vector<DeltaReq>& reqs, double* de_host);
   int move_batch(const std::vector<DeltaReq>& reqs);
   int2 *it12_d = nullptr, *it2r_d = nullptr, *it3_d = nullptr, *it5_d = nullptr;
+  int* sel_d = nullptr;
+  int2* selrng_d = nullptr;
   int4* it4_d = nullptr;
 
   // pair-kernel timing events (recorded around every pair-sum launch)
@@ -120,9 +127,10 @@ class Engine {
   int64_t launches = 0;
   std::string err;
 
+  Tables tables() const;
+
  private:
   void carve();
-  Tables tables() const;
   void issue_build();
   void issue_pot();
   int build_launch_count() const;

@@ -75,6 +75,9 @@ struct Tables {
   const double* rec_b;    // vertical recurrence coefficient b_nm
   const double* sect;     // sectoral factor sqrt((2m-1)/(2m)) (m >= 2), 1 for m = 1
   const double* inv_np1;  // 1/(n+1), for the Legendre recurrence
+  const float2* rec_a2;   // the same three tables as double-float pairs (hi, lo)
+  const float2* rec_b2;
+  const float2* sect2;
   int pmax;
 };
 
@@ -83,7 +86,7 @@ void init_source_kernels();  // one-time function attributes (call outside strea
 // Parameter-only work, once per layout: derived scalars, M_n, recurrence tables and the
 // Fibonacci points/weights of every system (written to surfx).
 void launch_setup(SysDev* sys, int nsys, double* Mn, double* rec_a, double* rec_b, double* sect, double* inv_np1,
-                  int pmax, dbl4* surfx, cudaStream_t st);
+                  float2* rec_a2, float2* rec_b2, float2* sect2, int pmax, dbl4* surfx, cudaStream_t st);
 constexpr int kCoefChunk = 32;  // coefficients per k_coef_reduce block
 void launch_images_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz,
                            const double* q, Tables tab, float4* src_hi, float4* src_lo, dbl4* src64, int prec,
@@ -107,16 +110,19 @@ PairConfig pair_config(int idx);
 int pairs_f32_occupancy(int cfg);
 int pairs_f64_occupancy();
 constexpr int kF64TargetsPerBlock = 128;
-constexpr int kReduceTargetsPerBlock = 256;
+constexpr int kReduceTargetsPerBlock = 64;
 void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
                       const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
                       float2* part, cudaStream_t st);
 void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
                       const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, double* part64,
                       cudaStream_t st);
-void launch_reduce(const SysDev* sys, int nsys, const int2* items, int nitems, const float2* part,
-                   const double* part64, int prec, const double* q, const double* r0, double* phi_c, double* phi_r,
-                   double* phi_t, double* epart, double* energy, unsigned int* counter, int* status, cudaStream_t st);
+// Reduce the pair partials of the launched items to potentials and energies; the energies of
+// system sel[r] are summed from the launch items sel_rng[r] = (first, count).
+void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
+                   const float2* part, const double* part64, int prec, const double* q, const double* r0,
+                   double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy, unsigned int* counter,
+                   int* status, cudaStream_t st);
 
 // ---- single-charge moves (k_delta.cu) ----
 // One request: move charge k of system sys to (x, y, z).

@@ -352,9 +352,12 @@ void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems
 // energies E_total = 1/2 sum q (phi_coul + phi_rf), E_RF = 1/2 sum q phi_rf.  Fixed-order
 // block reductions; the last block to finish sums the block partials of every system in
 // order (so the result does not depend on which block ends last).
-constexpr int kRedThreads = kReduceTargetsPerBlock;
+constexpr int kRedLanes = 4;
+constexpr int kRedThreads = kReduceTargetsPerBlock * kRedLanes;
+static_assert(kRedThreads == 256, "reduce block size");
 
-__global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict__ sys, int nsys,
+__global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict__ sys, const int* __restrict__ sel,
+                                                        const int2* __restrict__ sel_rng, int nsel,
                                                         const int2* __restrict__ items,
                                                         const float2* __restrict__ part,
                                                         const double* __restrict__ part64, int prec,
@@ -369,44 +372,36 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int n = S.n;
-  const int i = it.y * kRedThreads + threadIdx.x;
+  // kRedLanes consecutive threads share a target: lane sub sums the chunks c = sub (mod
+  // kRedLanes), then a fixed butterfly adds the lanes ((l0 + l1) + (l2 + l3)), so several
+  // loads per target are in flight and the order does not depend on scheduling
+  const int sub = threadIdx.x % kRedLanes;
+  const int i = it.y * kReduceTargetsPerBlock + threadIdx.x / kRedLanes;
   double et = 0.0, er = 0.0;
+  double pc = 0.0, pr = 0.0;
+  const int nch = S.ncr + S.nck + S.ncs;
   if (i < n) {
-    const int nch = S.ncr + S.nck + S.ncs;
-    double pc = 0.0, pr = 0.0;
     if (prec == HSMA_FP64) {
       const double* b = part64 + S.part + i;
-      for (int c = 0; c < S.ncr; ++c) pc += b[(long long)c * n];
-      for (int c = S.ncr; c < nch; ++c) pr += b[(long long)c * n];
+      for (int c = sub; c < S.ncr; c += kRedLanes) pc += b[(long long)c * n];
+      for (int c = S.ncr + sub; c < nch; c += kRedLanes) pr += b[(long long)c * n];
     } else {
-      // four interleaved partial sums (fixed assignment c mod 4, fixed final order) keep
-      // several loads in flight
       const float2* b = part + S.part + i;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int c = 0;
-      for (; c + 3 < S.ncr; c += 4) {
-        const float2 v0 = b[(long long)c * n], v1 = b[(long long)(c + 1) * n];
-        const float2 v2 = b[(long long)(c + 2) * n], v3 = b[(long long)(c + 3) * n];
-        a0 += (double)v0.x + (double)v0.y;
-        a1 += (double)v1.x + (double)v1.y;
-        a2 += (double)v2.x + (double)v2.y;
-        a3 += (double)v3.x + (double)v3.y;
+      for (int c = sub; c < S.ncr; c += kRedLanes) {
+        const float2 v = b[(long long)c * n];
+        pc += (double)v.x + (double)v.y;
       }
-      for (; c < S.ncr; ++c) a0 += (double)b[(long long)c * n].x + (double)b[(long long)c * n].y;
-      pc = (a0 + a1) + (a2 + a3);
-      a0 = a1 = a2 = a3 = 0.0;
-      c = S.ncr;
-      for (; c + 3 < nch; c += 4) {
-        const float2 v0 = b[(long long)c * n], v1 = b[(long long)(c + 1) * n];
-        const float2 v2 = b[(long long)(c + 2) * n], v3 = b[(long long)(c + 3) * n];
-        a0 += (double)v0.x + (double)v0.y;
-        a1 += (double)v1.x + (double)v1.y;
-        a2 += (double)v2.x + (double)v2.y;
-        a3 += (double)v3.x + (double)v3.y;
+      for (int c = S.ncr + sub; c < nch; c += kRedLanes) {
+        const float2 v = b[(long long)c * n];
+        pr += (double)v.x + (double)v.y;
       }
-      for (; c < nch; ++c) a0 += (double)b[(long long)c * n].x + (double)b[(long long)c * n].y;
-      pr = (a0 + a1) + (a2 + a3);
     }
+  }
+  for (int o = 1; o < kRedLanes; o <<= 1) {
+    pc += __shfl_xor_sync(0xffffffffu, pc, o);
+    pr += __shfl_xor_sync(0xffffffffu, pr, o);
+  }
+  if (i < n && sub == 0) {
     pr += r0[it.x];
     const long long o = S.chg + i;
     phi_c[o] = pc;
@@ -442,12 +437,14 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int s = threadIdx.x; s < nsys; s += kRedThreads) {
-    const SysDev& T = sys[s];
+  // energies of the launched systems: sel[r] owns launch items sel_rng[r] = (first, count)
+  for (int r = threadIdx.x; r < nsel; r += kRedThreads) {
+    const int s = sel[r];
+    const int2 rg = sel_rng[r];
     double a = 0.0, b = 0.0;
-    for (int k = 0; k < T.k5_count; ++k) {
-      a += ((volatile double*)epart)[2 * (T.k5_first + k)];
-      b += ((volatile double*)epart)[2 * (T.k5_first + k) + 1];
+    for (int k = 0; k < rg.y; ++k) {
+      a += ((volatile double*)epart)[2 * (rg.x + k)];
+      b += ((volatile double*)epart)[2 * (rg.x + k) + 1];
     }
     energy[2 * s] = a;
     energy[2 * s + 1] = b;
@@ -455,13 +452,14 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-void launch_reduce(const SysDev* sys, int nsys, const int2* items, int nitems, const float2* part,
-                   const double* part64, int prec, const double* q, const double* r0, double* phi_c, double* phi_r,
-                   double* phi_t, double* epart, double* energy, unsigned int* counter, int* status, cudaStream_t st)
+void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
+                   const float2* part, const double* part64, int prec, const double* q, const double* r0,
+                   double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy, unsigned int* counter,
+                   int* status, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  k_reduce<<<nitems, kRedThreads, 0, st>>>(sys, nsys, items, part, part64, prec, q, r0, phi_c, phi_r, phi_t, epart,
-                                           energy, counter, status);
+  k_reduce<<<nitems, kRedThreads, 0, st>>>(sys, sel, sel_rng, nsel, items, part, part64, prec, q, r0, phi_c, phi_r,
+                                           phi_t, epart, energy, counter, status);
 }
 
 }  // namespace hsma

@@ -28,6 +28,7 @@
 // the sine part of order |m|.
 #include <math.h>
 
+#include "df64.cuh"
 #include "hsma_internal.cuh"
 
 namespace hsma {
@@ -41,8 +42,15 @@ namespace hsma {
 // M_n = -[(1 - eps)(n+1) + t_n] / [(1 + eps) n + 1 + t_n]  (finite at mu = 0).
 // Fibonacci point j (Sec. 2.4): jj = j/2, z = -1 + 2 jj/F2, theta = arccos(z + sin(pi z)/pi),
 // phi = pi jj F1/F2 (+ pi for odd j), weight w = (2 pi R_tau^2/F2)(1 + cos(pi z)).
+__device__ __forceinline__ float2 pair_of(double x)
+{
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
 __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__ Mn, double* __restrict__ rec_a,
                         double* __restrict__ rec_b, double* __restrict__ sect, double* __restrict__ inv_np1,
+                        float2* __restrict__ rec_a2, float2* __restrict__ rec_b2, float2* __restrict__ sect2,
                         int pmax, dbl4* __restrict__ surfx)
 {
   if (blockIdx.x == 0) {
@@ -61,9 +69,12 @@ __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__
       }
       rec_a[t] = A;
       rec_b[t] = B;
+      rec_a2[t] = pair_of(A);
+      rec_b2[t] = pair_of(B);
     }
     for (int m = threadIdx.x; m <= pmax; m += blockDim.x) {
       sect[m] = (m >= 2) ? sqrt((2.0 * m - 1.0) / (2.0 * m)) : 1.0;
+      sect2[m] = pair_of(sect[m]);
       inv_np1[m] = 1.0 / (m + 1.0);
     }
   }
@@ -103,35 +114,75 @@ __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__
 }
 
 void launch_setup(SysDev* sys, int nsys, double* Mn, double* rec_a, double* rec_b, double* sect, double* inv_np1,
-                  int pmax, dbl4* surfx, cudaStream_t st)
+                  float2* rec_a2, float2* rec_b2, float2* sect2, int pmax, dbl4* surfx, cudaStream_t st)
 {
   const int blocks = nsys < 4096 ? (nsys > 0 ? nsys : 1) : 4096;
-  k_setup<<<blocks, 256, 0, st>>>(sys, nsys, Mn, rec_a, rec_b, sect, inv_np1, pmax, surfx);
+  k_setup<<<blocks, 256, 0, st>>>(sys, nsys, Mn, rec_a, rec_b, sect, inv_np1, rec_a2, rec_b2, sect2, pmax, surfx);
 }
 
 // ---------------------------------------------------------------------------------------
+// Arithmetic of the solid-harmonic steps: native FP64 for the FP64 path, double-float pairs
+// (df64.cuh, ~2^-46 relative) on the FP32 pipes for the FP32 path.
+template <class R>
+struct Num;
+template <>
+struct Num<double> {
+  static __device__ __forceinline__ double from(double x) { return x; }
+  static __device__ __forceinline__ double from_int(int n) { return (double)n; }
+  static __device__ __forceinline__ double to(double x) { return x; }
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double one() { return 1.0; }
+  static __device__ __forceinline__ double ra(const Tables& t, int i) { return t.rec_a[i]; }
+  static __device__ __forceinline__ double rb(const Tables& t, int i) { return t.rec_b[i]; }
+  static __device__ __forceinline__ double sc(const Tables& t, int i) { return t.sect[i]; }
+};
+template <>
+struct Num<df> {
+  static __device__ __forceinline__ df from(double x) { return df_from_double(x); }
+  static __device__ __forceinline__ df from_int(int n) { return df_make((float)n, 0.f); }
+  static __device__ __forceinline__ double to(df x) { return df_to_double(x); }
+  static __device__ __forceinline__ df zero() { return df_make(0.f, 0.f); }
+  static __device__ __forceinline__ df one() { return df_make(1.f, 0.f); }
+  static __device__ __forceinline__ df ra(const Tables& t, int i)
+  {
+    const float2 v = t.rec_a2[i];
+    return df_make(v.x, v.y);
+  }
+  static __device__ __forceinline__ df rb(const Tables& t, int i)
+  {
+    const float2 v = t.rec_b2[i];
+    return df_make(v.x, v.y);
+  }
+  static __device__ __forceinline__ df sc(const Tables& t, int i)
+  {
+    const float2 v = t.sect2[i];
+    return df_make(v.x, v.y);
+  }
+};
+
 // Real normalised solid harmonics of one point (u, v, w) (units of a), column m of the
 // triangle, written to T[idx(n, +-m)] for n = m..p.  Sectoral: T_mm = s_m (u + i v) T_{m-1,m-1};
 // vertical: T_{m+1,m} = sqrt(2m+1) w T_mm, T_nm = a_nm w T_{n-1,m} - b_nm rho^2 T_{n-2,m}.
-__device__ __forceinline__ void solid_column(int m, int p, double u, double v, double w, double rho2,
-                                             const Tables& tab, double* __restrict__ T)
+template <class R>
+__device__ __forceinline__ void solid_column(int m, int p, R u, R v, R w, R rho2, const Tables& tab,
+                                             R* __restrict__ T)
 {
-  double cr = 1.0, ci = 0.0;
+  R cr = Num<R>::one(), ci = Num<R>::zero();
   for (int k = 1; k <= m; ++k) {
-    const double f = tab.sect[k];
-    const double nr = f * (cr * u - ci * v);
-    const double ni = f * (cr * v + ci * u);
+    const R f = Num<R>::sc(tab, k);
+    const R nr = f * (cr * u - ci * v);
+    const R ni = f * (cr * v + ci * u);
     cr = nr;
     ci = ni;
   }
   T[m * m + m + m] = cr;
   if (m) T[m * m + m - m] = ci;
-  double pr = cr, pi = ci, qr = 0.0, qi = 0.0;
+  R pr = cr, pi = ci, qr = Num<R>::zero(), qi = Num<R>::zero();
   for (int n = m + 1; n <= p; ++n) {
     const int t = n * (n + 1) / 2 + m;
-    const double A = tab.rec_a[t] * w, B = tab.rec_b[t] * rho2;
-    const double nr = A * pr - B * qr;
-    const double ni = A * pi - B * qi;
+    const R A = Num<R>::ra(tab, t) * w, B = Num<R>::rb(tab, t) * rho2;
+    const R nr = A * pr - B * qr;
+    const R ni = A * pi - B * qi;
     T[n * n + n + m] = nr;
     if (m) T[n * n + n - m] = ni;
     qr = pr;
@@ -154,7 +205,7 @@ constexpr int kMomWarps = kMomThreads / 32;
 // Kelvin images (Sec. 2.4): r_K = a^2/r along xhat, q_K = (q/a)[gamma r_K + dbar (R_tau - r_K)/2].
 // Records: real charge (x, k q/eps1) and Kelvin image (r_K xhat, k q_K/eps1); FP32 path stores
 // (hi x, hi y, hi z, Q) and (lo x, lo y, lo z, 0).
-template <int MAXJ>
+template <int MAXJ, class R>
 __global__ __launch_bounds__(kMomThreads) void k_images_moments(
     const SysDev* __restrict__ sys, const int2* __restrict__ items, const double* __restrict__ xyz,
     const double* __restrict__ q, Tables tab, float4* __restrict__ src_hi, float4* __restrict__ src_lo,
@@ -169,10 +220,11 @@ __global__ __launch_bounds__(kMomThreads) void k_images_moments(
   const int c1 = min(n, c0 + S.mom_tile);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  double* T = sm;                                  // [G][P]
-  double* qv = sm + (size_t)G * P;                 // [G]
-  double* qc = qv + G;                             // [G]
-  double* red = qc + G;                            // [kMomWarps]
+  static_assert(sizeof(R) == sizeof(double), "moment arithmetic uses 8-byte values");
+  R* T = reinterpret_cast<R*>(sm);                 // [G][P]
+  R* qv = T + (size_t)G * P;                       // [G]
+  R* qc = qv + G;                                  // [G]
+  double* red = reinterpret_cast<double*>(qc + G);  // [kMomWarps]
 
   // images
   double r0 = 0.0;
@@ -231,21 +283,22 @@ __global__ __launch_bounds__(kMomThreads) void k_images_moments(
   }
 
   // charge moments U_nm, V_nm
-  double accU[MAXJ], accV[MAXJ];
+  R accU[MAXJ], accV[MAXJ];
 #pragma unroll
-  for (int j = 0; j < MAXJ; ++j) accU[j] = accV[j] = 0.0;
+  for (int j = 0; j < MAXJ; ++j) accU[j] = accV[j] = Num<R>::zero();
   for (int g0 = c0; g0 < c1; g0 += G) {
     const int gcount = min(G, c1 - g0);
     if (warp < gcount) {
       const long long gi = S.chg + g0 + warp;
       const double x = xyz[3 * gi] * inv_a, y = xyz[3 * gi + 1] * inv_a, z = xyz[3 * gi + 2] * inv_a;
       const double rho2 = x * x + y * y + z * z;
-      double* Tg = T + (size_t)warp * P;
-      for (int m = lane; m <= p; m += 32) solid_column(m, p, x, y, z, rho2, tab, Tg);
+      R* Tg = T + (size_t)warp * P;
+      const R xr = Num<R>::from(x), yr = Num<R>::from(y), zr = Num<R>::from(z), r2r = Num<R>::from(rho2);
+      for (int m = lane; m <= p; m += 32) solid_column<R>(m, p, xr, yr, zr, r2r, tab, Tg);
       if (lane == 0) {
         const double qi = q[gi];
-        qv[warp] = qi;
-        qc[warp] = qi * (dbar * (S.Rt_a * sqrt(rho2) - 1.0) * 0.5);
+        qv[warp] = Num<R>::from(qi);
+        qc[warp] = Num<R>::from(qi * (dbar * (S.Rt_a * sqrt(rho2) - 1.0) * 0.5));
       }
     }
     __syncthreads();
@@ -253,11 +306,11 @@ __global__ __launch_bounds__(kMomThreads) void k_images_moments(
     for (int j = 0; j < MAXJ; ++j) {
       const int idx = tid + j * kMomThreads;
       if (idx < P) {
-        double u = accU[j], v = accV[j];
+        R u = accU[j], v = accV[j];
         for (int g = 0; g < gcount; ++g) {
-          const double t = T[(size_t)g * P + idx];
-          u = fma(qv[g], t, u);
-          v = fma(qc[g], t, v);
+          const R t = T[(size_t)g * P + idx];
+          u = qv[g] * t + u;
+          v = qc[g] * t + v;
         }
         accU[j] = u;
         accV[j] = v;
@@ -269,8 +322,8 @@ __global__ __launch_bounds__(kMomThreads) void k_images_moments(
   for (int j = 0; j < MAXJ; ++j) {
     const int idx = tid + j * kMomThreads;
     if (idx < P) {
-      out[idx] = accU[j];
-      out[P + idx] = accV[j];
+      out[idx] = Num<R>::to(accU[j]);
+      out[P + idx] = Num<R>::to(accV[j]);
     }
   }
 }
@@ -291,8 +344,12 @@ static void launch_im(const SysDev* sys, const int2* items, int nitems, int maxP
 {
   const int G = moment_smem_group(maxP);
   const size_t smem = ((size_t)G * maxP + 2 * G + kMomWarps) * sizeof(double);
-  k_images_moments<MAXJ><<<nitems, kMomThreads, smem, st>>>(sys, items, xyz, q, tab, src_hi, src_lo, src64, prec, mom,
-                                                             mom_stride, G, status);
+  if (prec == HSMA_FP64)
+    k_images_moments<MAXJ, double><<<nitems, kMomThreads, smem, st>>>(sys, items, xyz, q, tab, src_hi, src_lo, src64,
+                                                                       prec, mom, mom_stride, G, status);
+  else
+    k_images_moments<MAXJ, df><<<nitems, kMomThreads, smem, st>>>(sys, items, xyz, q, tab, src_hi, src_lo, src64,
+                                                                   prec, mom, mom_stride, G, status);
 }
 
 void launch_images_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz,
@@ -388,6 +445,7 @@ constexpr int kSurfThreads = 256;
 constexpr int kSurfWarps = kSurfThreads / 32;
 static_assert(kSurfWarps == kSurfPointsPerBlock, "one warp per surface point");
 
+template <class R>
 __global__ __launch_bounds__(kSurfThreads) void k_surface(const SysDev* __restrict__ sys,
                                                           const int2* __restrict__ items,
                                                           const double* __restrict__ coef, Tables tab,
@@ -401,44 +459,46 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface(const SysDev* __restri
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P, p = S.p, M = S.M;
-  double* A = sm;  // [P]
-  for (int i = threadIdx.x; i < P; i += kSurfThreads) A[i] = coef[S.coef + i];
+  R* A = reinterpret_cast<R*>(sm);  // [P]
+  for (int i = threadIdx.x; i < P; i += kSurfThreads) A[i] = Num<R>::from(coef[S.coef + i]);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = it.y * kSurfWarps + warp;
   if (j >= M) return;
   const long long o = S.surf + j;
   const dbl4 yw = surfx[o];
-  const double u = yw.x * S.inv_a, v = yw.y * S.inv_a, ww = yw.z * S.inv_a;
-  const double rho2 = u * u + v * v + ww * ww;
-  double ph = 0.0, dph = 0.0;
+  const double ud = yw.x * S.inv_a, vd = yw.y * S.inv_a, wd = yw.z * S.inv_a;
+  const R u = Num<R>::from(ud), v = Num<R>::from(vd), ww = Num<R>::from(wd);
+  const R rho2 = Num<R>::from(ud * ud + vd * vd + wd * wd);
+  R phr = Num<R>::zero(), dphr = Num<R>::zero();
   for (int m = lane; m <= p; m += 32) {
-    double cr = 1.0, ci = 0.0;
+    R cr = Num<R>::one(), ci = Num<R>::zero();
     for (int k = 1; k <= m; ++k) {
-      const double f = tab.sect[k];
-      const double nr = f * (cr * u - ci * v);
-      const double ni = f * (cr * v + ci * u);
+      const R f = Num<R>::sc(tab, k);
+      const R nr = f * (cr * u - ci * v);
+      const R ni = f * (cr * v + ci * u);
       cr = nr;
       ci = ni;
     }
-    double t = A[m * m + m + m] * cr + (m ? A[m * m + m - m] * ci : 0.0);
-    ph += t;
-    dph += (double)m * t;
-    double pr = cr, pi = ci, qr = 0.0, qi = 0.0;
+    R t = m ? A[m * m + m + m] * cr + A[m * m + m - m] * ci : A[0] * cr;
+    phr = phr + t;
+    dphr = Num<R>::from_int(m) * t + dphr;
+    R pr = cr, pi = ci, qr = Num<R>::zero(), qi = Num<R>::zero();
     for (int n = m + 1; n <= p; ++n) {
       const int tt = n * (n + 1) / 2 + m;
-      const double Aa = tab.rec_a[tt] * ww, Bb = tab.rec_b[tt] * rho2;
-      const double nr = Aa * pr - Bb * qr;
-      const double ni = Aa * pi - Bb * qi;
-      t = A[n * n + n + m] * nr + (m ? A[n * n + n - m] * ni : 0.0);
-      ph += t;
-      dph += (double)n * t;
+      const R Aa = Num<R>::ra(tab, tt) * ww, Bb = Num<R>::rb(tab, tt) * rho2;
+      const R nr = Aa * pr - Bb * qr;
+      const R ni = Aa * pi - Bb * qi;
+      t = m ? A[n * n + n + m] * nr + A[n * n + n - m] * ni : A[n * n + n] * nr;
+      phr = phr + t;
+      dphr = Num<R>::from_int(n) * t + dphr;
       qr = pr;
       qi = pi;
       pr = nr;
       pi = ni;
     }
   }
+  double ph = Num<R>::to(phr), dph = Num<R>::to(dphr);
   for (int off = 16; off > 0; off >>= 1) {
     ph += __shfl_xor_sync(0xffffffffu, ph, off);
     dph += __shfl_xor_sync(0xffffffffu, dph, off);
@@ -466,19 +526,30 @@ void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, 
 {
   if (nitems <= 0) return;
   const size_t smem = (size_t)maxP * sizeof(double);
-  k_surface<<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, tab, surf_a, surf_b, surf64_a, surf64_b, surfx,
-                                                surfqd, prec);
+  if (prec == HSMA_FP64)
+    k_surface<double><<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, tab, surf_a, surf_b, surf64_a, surf64_b,
+                                                          surfx, surfqd, prec);
+  else
+    k_surface<df><<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, tab, surf_a, surf_b, surf64_a, surf64_b,
+                                                      surfx, surfqd, prec);
+}
+
+template <class R>
+static void moment_attrs()
+{
+  cudaFuncSetAttribute(k_images_moments<1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_images_moments<2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_images_moments<4, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_images_moments<8, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_images_moments<16, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_images_moments<26, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_surface<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
 }
 
 void init_source_kernels()
 {
-  cudaFuncSetAttribute(k_images_moments<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<26>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_surface, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  moment_attrs<double>();
+  moment_attrs<df>();
 }
 
 }  // namespace hsma

@@ -181,6 +181,20 @@ def test_results_are_deterministic():
     assert np.array_equal(a.phi, b.phi) and a.E_total == b.E_total
 
 
+@pytest.mark.parametrize("p", [20, 30, 55])
+def test_double_float_coefficients_match_fp64(p):
+    """The FP32 path evaluates the solid-harmonic moments and surface synthesis in double-float
+    arithmetic (~2^-46); its correction coefficients must match the FP64 path's to 1e-12."""
+    s = inputs.near_interface_system(kappa_a=2.0, n=1000)
+    co = []
+    for prec in (api.HSMA_FP32, api.HSMA_FP64):
+        prm = api.hsma_default_params(p=p, M=2 * p * p + 2, precision=prec)
+        h = api.hsma_create(s.a, s.eps1, s.eps2, s.kappa, prm)
+        api.hsma_build_sources(h, s.xyz, s.q)
+        co.append(api.hsma_coefficients(h, p))
+    assert np.linalg.norm(co[0] - co[1]) <= 1e-12 * np.linalg.norm(co[1])
+
+
 def test_kernel_launch_accounting():
     s = inputs.small_system()
     prm = api.hsma_default_params(p=s.p, M=s.M)
