@@ -55,6 +55,21 @@ def evals(s) -> int:
     return s.n * (2 * s.n - 1 + s.M)
 
 
+def profiled_traffic(kernel_src: str, profile_md: str):
+    """DRAM bytes per launch from the committed ncu summary, or None if the kernel's source has
+    changed since that capture (the summary records the source hash it was taken with)."""
+    import hashlib
+    import re
+    try:
+        text = open(profile_md).read()
+        sha = re.search(r"source_sha256 \([^)]*\): ([0-9a-f]+)", text).group(1)
+        traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
+        cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:len(sha)]
+    except (OSError, AttributeError):
+        return None
+    return traffic if cur == sha else None
+
+
 def config_dict(systems, n_gpus):
     s = systems[0]
     return {"workload": f"2 cavities N={s.n} (25% within 0.05a of the interface), eps1=1, eps2=80, "
@@ -363,8 +378,11 @@ def run_ours(args):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = sms * SM_MUFU_PER_CLK * sm_max * 1e6
     achieved = ev_per_launch / t_pair
+    traffic = profiled_traffic(os.path.join(ROOT, "paper_1907_01724_gb300", "csrc", "k_pairs.cu"),
+                               os.path.join(ROOT, "profiles", "k_pairs_f32_N2000x2.md"))
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-eval/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "k_pairs_f32",
+            "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
+            "kernel": "k_pairs_f32",
             "peak_basis": f"{sms} SMs x {SM_MUFU_PER_CLK} MUFU rsqrt/clk x {sm_max:.0f} MHz (max SM clock)",
             "pair_kernel_ms": t_pair * 1e3, "pair_config": batch.pair_configs()[cfg],
             "evals_per_launch": ev_per_launch}
