@@ -489,9 +489,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sections")
+    ap.add_argument("--only", choices=["batched", "serving"], help="run one extra section alone (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
+    if args.only:
+        import torch
+        torch.cuda.set_device(0)
+        st = torch.cuda.Stream()
+        torch.cuda.set_stream(st)
+        out = run_batched(0, st, torch.cuda.get_device_name(0)) if args.only == "batched" else run_serving(0)
+        print(json.dumps(out), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

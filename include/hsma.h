@@ -156,9 +156,10 @@ HSMA_API const char* hsma_version(void);
  * Batched API: many independent cavities (each its own a, eps1, eps2, kappa and charge set;
  * common numerical parameters) evaluated by the same kernels in single launches.  Arrays
  * over systems are indexed s = 0..nsys-1; charges are concatenated in system order (system s
- * owns n[s] consecutive rows).  With the same pair-sum tile configuration, each system's
- * results are bitwise identical to evaluating it alone: its work split and summation order
- * depend only on its own sizes, never on the other systems or on scheduling.
+ * owns n[s] consecutive rows).  The work is split over the whole batch (a system's share of
+ * items follows its share of the work), so a batched system's results equal those of the same
+ * system alone up to the rounding of a different summation split (within the path's
+ * tolerance); for a given batch they are deterministic (no dependence on scheduling).
  * --------------------------------------------------------------------------------------- */
 typedef struct hsma_batch_t hsma_batch_t;
 

@@ -138,6 +138,14 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   }
   const int slots = num_sms * occ;
   const double desired = 4.0 * slots;
+  // the pair items and moment blocks of the whole engine are apportioned by each system's share
+  // of the work, so a batch of many small systems gets few, larger items per system
+  double W = 0.0;
+  int64_t totn_all = 0;
+  for (int s = 0; s < nsys; ++s) {
+    W += (double)ns[s] * (2.0 * ns[s] + 1.3 * spec[s].M);
+    totn_all += ns[s];
+  }
   L.sd.resize(nsys);
   int64_t chg = 0, surf = 0, coef = 0, mn = 0, mom = 0, part = 0;
   int k5 = 0;
@@ -157,9 +165,9 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     d.mom = mom;
     // charges per moment block: enough blocks to cover the SMs twice over the whole engine,
     // between 8 and kMomTile charges (a multiple of the 8 warps of a block)
-    // (a function of this system alone, so that its summation order is the same alone or batched)
     {
-      const int64_t want_blocks = 2 * (int64_t)num_sms;
+      const double share = (double)n / std::max<double>((double)totn_all, 1.0);
+      const int64_t want_blocks = std::max<int64_t>(1, (int64_t)std::llround(2.0 * num_sms * share));
       int64_t tile = (n + want_blocks - 1) / want_blocks;
       tile = std::min<int64_t>(kMomTile, std::max<int64_t>(8, (tile + 7) / 8 * 8));
       d.mom_tile = (int)tile;
@@ -168,9 +176,9 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     d.tb = TB;
     d.n_tb = (int)((n + TB - 1) / TB);
     if (n > 0) {
-      // source chunks: enough items for this system alone to cover the GPU (a function of
-      // this system only, so batching does not change its summation order)
-      const int64_t chunks_total = std::max<int64_t>(1, (int64_t)std::ceil(desired / d.n_tb));
+      const double Ws = (double)n * (2.0 * n + 1.3 * sp.M);
+      const double items_s = std::max(1.0, std::round(desired * Ws / std::max(W, 1.0)));
+      const int64_t chunks_total = std::max<int64_t>(1, (int64_t)std::ceil(items_s / d.n_tb));
       const int64_t per = (2 * n + sp.M + chunks_total - 1) / chunks_total;
       const int unit = prec == HSMA_FP64 ? kF64TargetsPerBlock : pair_config(cfg).threads;
       int64_t chunk = std::max<int64_t>(per, unit);

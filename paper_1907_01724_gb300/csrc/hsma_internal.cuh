@@ -110,7 +110,7 @@ PairConfig pair_config(int idx);
 int pairs_f32_occupancy(int cfg);
 int pairs_f64_occupancy();
 constexpr int kF64TargetsPerBlock = 128;
-constexpr int kReduceTargetsPerBlock = 64;
+constexpr int kReduceTargetsPerBlock = 32;
 void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
                       const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
                       float2* part, cudaStream_t st);

@@ -352,7 +352,7 @@ void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems
 // energies E_total = 1/2 sum q (phi_coul + phi_rf), E_RF = 1/2 sum q phi_rf.  Fixed-order
 // block reductions; the last block to finish sums the block partials of every system in
 // order (so the result does not depend on which block ends last).
-constexpr int kRedLanes = 4;
+constexpr int kRedLanes = 8;
 constexpr int kRedThreads = kReduceTargetsPerBlock * kRedLanes;
 static_assert(kRedThreads == 256, "reduce block size");
 
@@ -373,7 +373,7 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   const SysDev& S = sys[it.x];
   const int n = S.n;
   // kRedLanes consecutive threads share a target: lane sub sums the chunks c = sub (mod
-  // kRedLanes), then a fixed butterfly adds the lanes ((l0 + l1) + (l2 + l3)), so several
+  // kRedLanes), then a fixed xor butterfly adds the lanes pairwise, so several
   // loads per target are in flight and the order does not depend on scheduling
   const int sub = threadIdx.x % kRedLanes;
   const int i = it.y * kReduceTargetsPerBlock + threadIdx.x / kRedLanes;

