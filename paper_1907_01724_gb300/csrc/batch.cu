@@ -18,8 +18,9 @@ struct hsma_batch_t {
 
 namespace hsma {
 
-// Time every pair configuration on the current sources and keep the fastest for this size
-// class.  The inputs (xyz, q) sit before every configuration-dependent buffer of the
+// Time every pair configuration on the current sources (the potentials pass: pair sum plus the
+// reduction of its partials, whose count the configuration sets) and keep the fastest for this
+// size class.  The inputs (xyz, q) sit before every configuration-dependent buffer of the
 // workspace, so each configuration rebuilds its sources from them in place.
 int Engine::autotune(int reps, int* best_out, float* best_ms_out)
 {
@@ -61,7 +62,7 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
       rc = potentials();
       if (rc) return rc;
       float ms = 0.f;
-      rc = last_pair_time(&ms);
+      rc = last_pot_time(&ms);
       if (rc) return rc;
       if (r > 0) t.push_back(ms);
     }

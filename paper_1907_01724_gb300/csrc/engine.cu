@@ -4,7 +4,7 @@
 // hsma_t handle is an engine with one system).  It lays every system's arrays out in one
 // device workspace, builds the work lists of the kernels (longest pair items first), and
 // records the two device phases as CUDA graphs:
-//   build:     k_setup -> k_images_moments -> k_coef_reduce -> k_surface   (Sec. 2.3-2.4)
+//   build:     k_moments -> k_coef_reduce -> k_surface_mat, beside k_order_* -> k_images (Sec. 2.3-2.4)
 //   potential: reset counter -> k_pairs -> k_reduce                      (Algorithm 1 step 5)
 // Graphs are re-recorded whenever the layout (sizes) or workspace changes.
 #include <algorithm>
@@ -12,7 +12,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "engine.h"
@@ -74,6 +76,10 @@ int Engine::init(int dev, void* user_stream, int precision)
   occ_f64 = pairs_f64_occupancy();
   CK(cudaEventCreate(&ev_pair0));
   CK(cudaEventCreate(&ev_pair1));
+  CK(cudaEventCreate(&ev_pot1));
+  CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
   CK(cudaGetLastError());
   return HSMA_OK;
 }
@@ -94,6 +100,14 @@ void Engine::leave()
   }
 }
 
+int Engine::last_pot_time(float* ms)
+{
+  if (!pair_timed) return fail(HSMA_E_STATE, "no pair sum has run");
+  CK(cudaStreamSynchronize(stream));
+  CK(cudaEventElapsedTime(ms, ev_pair0, ev_pot1));
+  return HSMA_OK;
+}
+
 int Engine::last_pair_time(float* ms)
 {
   if (!pair_timed) return fail(HSMA_E_STATE, "no pair sum has run");
@@ -109,6 +123,10 @@ Engine::~Engine()
   if (ws_owned && ws) cudaFree(ws);
   if (ev_pair0) cudaEventDestroy(ev_pair0);
   if (ev_pair1) cudaEventDestroy(ev_pair1);
+  if (ev_pot1) cudaEventDestroy(ev_pot1);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (side) cudaStreamDestroy(side);
   if (ev_in) cudaEventDestroy(ev_in);
   if (ev_out) cudaEventDestroy(ev_out);
   if (own_stream && stream) cudaStreamDestroy(stream);
@@ -142,12 +160,15 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   // of the work, so a batch of many small systems gets few, larger items per system
   double W = 0.0;
   int64_t totn_all = 0;
+  int maxP_all = 1;
   for (int s = 0; s < nsys; ++s) {
     W += (double)ns[s] * (2.0 * ns[s] + 1.3 * spec[s].M);
     totn_all += ns[s];
+    maxP_all = std::max(maxP_all, (spec[s].p + 1) * (spec[s].p + 1));
   }
+  const int G = moment_smem_group(maxP_all);
   L.sd.resize(nsys);
-  int64_t chg = 0, surf = 0, coef = 0, mn = 0, mom = 0, part = 0;
+  int64_t chg = 0, surf = 0, coef = 0, mn = 0, mom = 0, part = 0, boxes = 0;
   int k5 = 0;
   L.maxP = 1;
   L.pmax = 0;
@@ -164,12 +185,13 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     d.chg = chg; d.src = 2 * chg; d.surf = surf; d.coef = coef; d.mn = mn;
     d.mom = mom;
     // charges per moment block: enough blocks to cover the SMs twice over the whole engine,
-    // between 8 and kMomTile charges (a multiple of the 8 warps of a block)
+    // a multiple of the moment group G (charges whose solid harmonics a block forms at once)
     {
       const double share = (double)n / std::max<double>((double)totn_all, 1.0);
       const int64_t want_blocks = std::max<int64_t>(1, (int64_t)std::llround(2.0 * num_sms * share));
       int64_t tile = (n + want_blocks - 1) / want_blocks;
-      tile = std::min<int64_t>(kMomTile, std::max<int64_t>(8, (tile + 7) / 8 * 8));
+      tile = std::max<int64_t>(G, (tile + G - 1) / G * G);
+      tile = std::min<int64_t>(tile, std::max(G, kMomTile / G * G));
       d.mom_tile = (int)tile;
     }
     d.mom_blocks = (int)((n + d.mom_tile - 1) / d.mom_tile);
@@ -190,6 +212,8 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
       d.ncs = (int)((sp.M + chunk - 1) / chunk);
     }
     d.part = part;
+    d.dc2 = (float)((kNearRel * sp.a) * (kNearRel * sp.a));
+    d.bb = boxes;
     d.k5_first = k5;
     d.k5_count = (int)((n + kReduceTargetsPerBlock - 1) / kReduceTargetsPerBlock);
     L.sd[s] = d;
@@ -197,6 +221,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     for (int c = 0; c < (d.P + kCoefChunk - 1) / kCoefChunk; ++c) L.it2r.push_back(make_int2(s, c));
     for (int b = 0; b < (sp.M + kSurfPointsPerBlock - 1) / kSurfPointsPerBlock; ++b) L.it3.push_back(make_int2(s, b));
     for (int b = 0; b < d.k5_count; ++b) L.it5.push_back(make_int2(s, b));
+    for (int b = 0; b < (int)((n + kOrderBlock - 1) / kOrderBlock); ++b) L.itord.push_back(make_int2(s, b));
     const int nch = d.ncr + d.nck + d.ncs;
     for (int tb = 0; tb < d.n_tb; ++tb)
       for (int c = 0; c < nch; ++c) L.it4.push_back(make_int4(s, tb, c, 0));
@@ -206,9 +231,31 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     mn += sp.p + 1;
     mom += d.mom_blocks;
     part += (int64_t)nch * n;
+    boxes += 2 * ((n + kBox - 1) / kBox);
     k5 += d.k5_count;
     L.maxP = std::max(L.maxP, d.P);
     L.pmax = std::max(L.pmax, sp.p);
+  }
+  // auxiliary-sphere solid-harmonic tables, one per distinct (tau, M, F1, F2, p) (the table is
+  // independent of a), built by a representative system
+  {
+    std::map<std::tuple<double, int, int, int, int>, int64_t> groups;
+    int64_t off_sb = 0;
+    for (int s = 0; s < nsys; ++s) {
+      const SysSpec& sp = spec[s];
+      const auto key = std::make_tuple(sp.tau, sp.M, sp.F1, sp.F2, sp.p);
+      auto f = groups.find(key);
+      if (f == groups.end()) {
+        f = groups.emplace(key, off_sb).first;
+        off_sb += (int64_t)sp.M * L.sd[s].P;
+        for (int b = 0; b < (sp.M + kSurfPointsPerBlock - 1) / kSurfPointsPerBlock; ++b)
+          L.itsb.push_back(make_int2(s, b));
+      }
+      L.sd[s].sb = f->second;
+    }
+    L.totSB = off_sb;
+    L.use_sb = 8 * (size_t)off_sb <= kMaxSurfBasisBytes;
+    if (!L.use_sb) L.itsb.clear();
   }
   // longest pair items first (cost ~ targets x sources x per-source weight)
   auto cost = [&](const int4& it) {
@@ -233,6 +280,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.totMn = mn;
   L.totMom = mom;
   L.totPart = part;
+  L.totBoxes = boxes;
   L.mom_stride = (int)align_up(2 * (size_t)L.maxP + 1, 2);
   L.pair_grid = (int)std::max<size_t>(1, std::min<size_t>(L.it4.size(), (size_t)slots));
 
@@ -288,6 +336,17 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_de = take(8 * (size_t)L.max_req);
   L.o_mom = take(8 * (size_t)L.totMom * L.mom_stride);
   L.o_coef = take(8 * L.totP);
+  L.o_coef2 = take(8 * L.totP);
+  L.o_sb = take(L.use_sb ? 8 * (size_t)L.totSB : 0);
+  L.o_itsb = take(sizeof(int2) * L.itsb.size());
+  L.o_perm = take(4 * (size_t)L.totN);
+  L.o_iperm = take(4 * (size_t)L.totN);
+  L.o_key = take(4 * (size_t)L.totN);
+  L.o_hist = take(4 * (size_t)nsys * kOrderCells);
+  L.o_offs = take(4 * (size_t)nsys * kOrderCells);
+  L.o_cursor = take(4 * (size_t)nsys * kOrderCells);
+  L.o_boxes = take(2 * sizeof(float4) * (size_t)L.totBoxes);
+  L.o_itord = take(sizeof(int2) * L.itord.size());
   L.o_r0 = take(8 * (size_t)nsys);
   L.o_phic = take(8 * L.totN);
   L.o_phir = take(8 * L.totN);
@@ -355,6 +414,17 @@ void Engine::carve()
   de_d = (double*)(b + L.o_de);
   mom_d = (double*)(b + L.o_mom);
   coef_d = (double*)(b + L.o_coef);
+  coef2_d = (float2*)(b + L.o_coef2);
+  sb_d = L.use_sb ? (double*)(b + L.o_sb) : nullptr;
+  itsb_d = (int2*)(b + L.o_itsb);
+  perm_d = (int*)(b + L.o_perm);
+  iperm_d = (int*)(b + L.o_iperm);
+  key_d = (int*)(b + L.o_key);
+  hist_d = (int*)(b + L.o_hist);
+  offs_d = (int*)(b + L.o_offs);
+  cursor_d = (int*)(b + L.o_cursor);
+  boxes_d = (float4*)(b + L.o_boxes);
+  itord_d = (int2*)(b + L.o_itord);
   r0_d = (double*)(b + L.o_r0);
   phic_d = (double*)(b + L.o_phic);
   phir_d = (double*)(b + L.o_phir);
@@ -427,15 +497,24 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
     CK(cudaMemcpyAsync(it5_d, L.it5.data(), sizeof(int2) * L.it5.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it4.empty())
     CK(cudaMemcpyAsync(it4_d, L.it4.data(), sizeof(int4) * L.it4.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.itsb.empty())
+    CK(cudaMemcpyAsync(itsb_d, L.itsb.data(), sizeof(int2) * L.itsb.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.itord.empty())
+    CK(cudaMemcpyAsync(itord_d, L.itord.data(), sizeof(int2) * L.itord.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(sel_d, L.sel.data(), sizeof(int) * L.sel.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(selrng_d, L.selrng.data(), sizeof(int2) * L.selrng.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemsetAsync(ctr_pairs_d, 0, 16, stream));
   CK(cudaMemsetAsync(energy_d, 0, 16 * L.sd.size(), stream));
-  // parameter-only quantities (row a1: scalars, M_n, tables, quadrature grid), once per layout
+  // parameter-only quantities (scalars, M_n, tables, quadrature grid, surface basis), once per layout
   launch_setup(sys_d, (int)L.sd.size(), Mn_d, rec_a_d, rec_b_d, sect_d, inv_np1_d, rec_a2_d, rec_b2_d, sect2_d,
                L.pmax, surfx_d, stream);
   CK(cudaGetLastError());
   launches += 1;
+  if (L.use_sb && !L.itsb.empty()) {
+    launch_surface_basis(sys_d, itsb_d, (int)L.itsb.size(), tables(), surfx_d, sb_d, prec, stream);
+    CK(cudaGetLastError());
+    launches += 1;
+  }
   CK(cudaStreamSynchronize(stream));
   layout_uploaded = true;
   sources_ready = pot_ready = false;
@@ -458,16 +537,31 @@ Tables Engine::tables() const
 
 void Engine::issue_build()
 {
-  launch_images_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, tables(), srchi_d, srclo_d, src64_d,
-                        prec, mom_d, L.mom_stride, status_d, stream);
-  launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, r0_d, stream);
-  launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, tables(), surfa_d, surfb_d, surf64a_d, surf64b_d,
-                 surfx_d, surfqd_d, prec, stream);
+  // fork: the spatial order and the pair-sum records on the second stream, beside the
+  // moments -> coefficients -> surface chain; both are joined before the build ends
+  const int nsys = (int)L.sd.size();
+  const bool order = !L.itord.empty();
+  if (order) {
+    cudaEventRecord(ev_fork, stream);
+    cudaStreamWaitEvent(side, ev_fork, 0);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, key_d, hist_d, offs_d, cursor_d, perm_d, iperm_d,
+                 side);
+    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d, prec,
+                  status_d, side);
+    cudaEventRecord(ev_join, side);
+  }
+  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, tables(), prec, mom_d, L.mom_stride, stream);
+  launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
+                     stream);
+  launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
+                 surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
+  if (order) cudaStreamWaitEvent(stream, ev_join, 0);
 }
 
 int Engine::build_launch_count() const
 {
-  return (L.it12.empty() ? 0 : 1) + (L.it2r.empty() ? 0 : 1) + (L.it3.empty() ? 0 : 1);
+  // order: 4 kernels (k_order_cells, _scan, _scatter, _sort) and k_images
+  return (L.itord.empty() ? 0 : 5) + (L.it12.empty() ? 0 : 1) + (L.it2r.empty() ? 0 : 1) + (L.it3.empty() ? 0 : 1);
 }
 
 void Engine::issue_pot()
@@ -481,11 +575,12 @@ void Engine::issue_pot()
                        part64_d, stream);
     else
       launch_pairs_f32(L.cfg, L.pair_grid, sys_d, it4_d, (int)L.it4.size(), ctr_pairs_d, srchi_d, srclo_d, surfa_d,
-                       surfb_d, part_d, stream);
+                       surfb_d, boxes_d, part_d, stream);
     cudaEventRecordWithFlags(ev_pair1, stream, cudaEventRecordExternal);
   }
-  launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, r0_d, phic_d,
-                phir_d, phit_d, epart_d, energy_d, ctr_red_d, status_d, stream);
+  launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
+                phic_d, phir_d, phit_d, epart_d, energy_d, ctr_red_d, status_d, stream);
+  if (!L.it4.empty()) cudaEventRecordWithFlags(ev_pot1, stream, cudaEventRecordExternal);
 }
 
 int Engine::pot_launch_count() const { return (L.it4.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1); }
@@ -929,8 +1024,9 @@ int Engine::delta_batch(const std::vector<DeltaReq>& reqs, double* de_host)
   CK(cudaMemcpyAsync(dreq_d, reqs.data(), sizeof(DeltaReq) * reqs.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(ditems_d, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(dreqit_d, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice, stream));
-  launch_delta(sys_d, ditems_d, (int)items.size(), dreqit_d, dreq_d, (int)reqs.size(), xyz_d, q_d, srchi_d, srclo_d,
-               src64_d, surfx_d, surfqd_d, vsurf_d, Mn_d, inv_np1_d, dpart_d, de_d, ctr_delta_d, status_d, stream);
+  launch_delta(sys_d, ditems_d, (int)items.size(), dreqit_d, dreq_d, (int)reqs.size(), xyz_d, q_d, perm_d, iperm_d,
+               srchi_d, srclo_d, src64_d, surfx_d, surfqd_d, vsurf_d, Mn_d, inv_np1_d, dpart_d, de_d, ctr_delta_d,
+               status_d, stream);
   CK(cudaGetLastError());
   launches += 1;
   CK(cudaMemcpyAsync(de_host, de_d, 8 * reqs.size(), cudaMemcpyDeviceToHost, stream));
@@ -956,8 +1052,8 @@ int Engine::move_batch(const std::vector<DeltaReq>& reqs)
   CK(cudaMemcpyAsync(dreq_d, reqs.data(), sizeof(DeltaReq) * reqs.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(mitems_d, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, stream));
   launch_move(sys_d, mitems_d, (int)items.size(), dreq_d, (int)reqs.size(), tables(), L.maxP, xyz_d, q_d, Mn_d,
-              coef_d, r0_d, surfx_d, surfqd_d, vsurf_d, v_ready ? 1 : 0, surfa_d, surfb_d, surf64a_d, surf64b_d,
-              srchi_d, srclo_d, src64_d, stream);
+              coef_d, coef2_d, r0_d, surfx_d, surfqd_d, vsurf_d, v_ready ? 1 : 0, surfa_d, surfb_d, surf64a_d,
+              surf64b_d, iperm_d, srchi_d, srclo_d, src64_d, boxes_d, stream);
   CK(cudaGetLastError());
   leave();
   launches += items.empty() ? 1 : 2;

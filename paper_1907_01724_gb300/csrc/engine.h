@@ -23,6 +23,11 @@ int tune_bucket(int64_t total_n, int nsys);
 struct Layout {
   std::vector<SysDev> sd;
   std::vector<int2> it12, it2r, it3, it5;
+  std::vector<int2> itsb;     // (representative system, point block) of every surface-basis table
+  std::vector<int2> itord;    // (system, block of kOrderBlock charges): spatial order and records
+  int64_t totBoxes = 0;       // 32-record boxes (real + Kelvin) of all systems
+  bool use_sb = false;        // surface synthesis through the basis tables
+  int64_t totSB = 0;          // 8-byte slots of all basis tables
   std::vector<int4> it4;
   std::vector<int> sel;       // all systems, in order (energy pass of a full launch)
   std::vector<int2> selrng;   // their reduce-item ranges
@@ -36,6 +41,8 @@ struct Layout {
   size_t o_surfx = 0, o_surfqd = 0, o_vsurf = 0;
   int max_req = 1, ditem_cap = 1, mitem_cap = 1;
   size_t o_dreq = 0, o_ditems = 0, o_dreqit = 0, o_mitems = 0, o_dpart = 0, o_de = 0;
+  size_t o_sb = 0, o_coef2 = 0, o_itsb = 0;
+  size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_offs = 0, o_cursor = 0, o_boxes = 0, o_itord = 0;
   size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0;
   size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0;
   size_t bytes = 0;
@@ -91,6 +98,15 @@ class Engine {
   float2* part_d = nullptr;
   double* part64_d = nullptr;
   double *mom_d = nullptr, *coef_d = nullptr, *r0_d = nullptr;
+  float2* coef2_d = nullptr;      // coefficients as FP32 (hi, lo) pairs
+  double* sb_d = nullptr;         // auxiliary-sphere solid-harmonic tables
+  int2* itsb_d = nullptr;
+  int *perm_d = nullptr, *iperm_d = nullptr;  // spatial order (sorted position <-> input index)
+  int *key_d = nullptr, *hist_d = nullptr, *offs_d = nullptr, *cursor_d = nullptr;
+  float4* boxes_d = nullptr;      // bounding boxes of 32 consecutive sorted records
+  int2* itord_d = nullptr;
+  cudaStream_t side = nullptr;    // second stream of the build (order + records beside the moments)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double *phic_d = nullptr, *phir_d = nullptr, *phit_d = nullptr, *epart_d = nullptr, *energy_d = nullptr;
   unsigned int *ctr_pairs_d = nullptr, *ctr_red_d = nullptr, *ctr_delta_d = nullptr;
   int* status_d = nullptr;
@@ -114,12 +130,14 @@ class Engine {
 
   // pair-kernel timing events (recorded around every pair-sum launch)
   cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;
+  cudaEvent_t ev_pot1 = nullptr;  // after the reduction (pair sum + reduction = potentials pass)
   // ordering with the caller's legacy default stream when the handle owns its stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   void enter();
   void leave();
   bool pair_timed = false;
   int last_pair_time(float* ms);
+  int last_pot_time(float* ms);
 
   // state
   bool sources_ready = false, pot_ready = false;

@@ -66,8 +66,23 @@ struct SysDev {
   int n_tb;           // target blocks
   int k5_first;       // first reduce item of this system
   int k5_count;       // reduce items of this system
-  int pad1;
+  float dc2;          // squared near distance of the FP32 pair-sum box test, (kNearRel a)^2
+  long long sb;       // offset (8-byte slots) of its auxiliary-sphere solid-harmonic table (M x P)
+  long long bb;       // first 32-record box of this system (real boxes, then Kelvin boxes)
 };
+
+// Spatial order (k_order.cu): charges sorted by the Morton index of their cell on a 16^3 grid
+// over [-a, a]^3 (input index inside a cell).  perm[chg + i] = input index of sorted position
+// i, iperm its inverse.  Pair-sum records, pair partials and move work use sorted positions.
+constexpr int kOrderGrid = 16;
+constexpr int kOrderCells = kOrderGrid * kOrderGrid * kOrderGrid;
+constexpr int kOrderBlock = 256;  // charges per k_order / k_images work item
+void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, int* key, int* hist,
+                  int* offs, int* cursor, int* perm, int* iperm, cudaStream_t st);
+// Boxes of 32 consecutive sorted records: a warp's targets and a box farther apart than
+// kNearRel a use plain FP32 coordinates in the pair sum, nearer ones the hi/lo-split form.
+constexpr int kBox = 32;
+constexpr double kNearRel = 0.08;
 
 // Offsets of the surface-record and coefficient tables for one engine.
 struct Tables {
@@ -88,17 +103,32 @@ void init_source_kernels();  // one-time function attributes (call outside strea
 void launch_setup(SysDev* sys, int nsys, double* Mn, double* rec_a, double* rec_b, double* sect, double* inv_np1,
                   float2* rec_a2, float2* rec_b2, float2* sect2, int pmax, dbl4* surfx, cudaStream_t st);
 constexpr int kCoefChunk = 32;  // coefficients per k_coef_reduce block
-void launch_images_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz,
-                           const double* q, Tables tab, float4* src_hi, float4* src_lo, dbl4* src64, int prec,
-                           double* mom, int mom_stride, int* status, cudaStream_t st);
+// Records at sorted positions (items = (system, block of kOrderBlock sorted positions)); the
+// FP32 path also writes the boxes (2 float4 per box: min and max of the hi coordinates).
+void launch_images(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
+                   const int* perm, float4* src_hi, float4* src_lo, dbl4* src64, float4* boxes, int prec, int* status,
+                   cudaStream_t st);
+void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
+                    Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st);
 int moment_smem_group(int maxP);
+// Moments are stored in the moment arithmetic (FP64 path: double; FP32 path: FP32 (hi, lo)
+// pairs), one 8-byte slot each; the coefficients as double (coef) and as (hi, lo) pairs (coef2).
 void launch_coef_reduce(const SysDev* sys, const int2* items, int nitems, const double* mom, int mom_stride,
-                        const double* Mn, double* coef, double* r0, cudaStream_t st);
-void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, const double* coef, Tables tab,
-                    float4* surf_a, float4* surf_b, dbl4* surf64_a, double* surf64_b, dbl4* surfx, double2* surfqd,
-                    int prec, cudaStream_t st);
+                        const double* Mn, double* coef, float2* coef2, double* r0, int prec, cudaStream_t st);
+// Solid harmonics of the auxiliary-sphere points (once per layout; items = (system, point block)
+// of one representative system per table).
+void launch_surface_basis(const SysDev* sys, const int2* items, int nitems, Tables tab, const dbl4* surfx, double* sb,
+                          int prec, cudaStream_t st);
+// Surface records from the coefficients: with the basis table sb (a GEMV per point), or, when
+// sb is null, by running the solid-harmonic recurrence at every point.
+void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, const double* coef,
+                    const float2* coef2, const double* sb, Tables tab, float4* surf_a, float4* surf_b,
+                    dbl4* surf64_a, double* surf64_b, dbl4* surfx, double2* surfqd, int prec, cudaStream_t st);
 constexpr int kSurfPointsPerBlock = 8;
-constexpr int kMomTile = 96;
+// Largest total size of the surface-basis tables of one engine; beyond it the surface step runs
+// the recurrence at every point instead.
+constexpr size_t kMaxSurfBasisBytes = size_t(4) << 30;
+constexpr int kMomTile = 256;  // largest moment tile (charges per moment block)
 
 // ---- launchers (k_pairs.cu) ----
 struct PairConfig {
@@ -113,16 +143,16 @@ constexpr int kF64TargetsPerBlock = 128;
 constexpr int kReduceTargetsPerBlock = 32;
 void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
                       const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
-                      float2* part, cudaStream_t st);
+                      const float4* boxes, float2* part, cudaStream_t st);
 void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
                       const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, double* part64,
                       cudaStream_t st);
 // Reduce the pair partials of the launched items to potentials and energies; the energies of
 // system sel[r] are summed from the launch items sel_rng[r] = (first, count).
 void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
-                   const float2* part, const double* part64, int prec, const double* q, const double* r0,
-                   double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy, unsigned int* counter,
-                   int* status, cudaStream_t st);
+                   const float2* part, const double* part64, int prec, const double* q, const int* perm,
+                   const double* r0, double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy,
+                   unsigned int* counter, int* status, cudaStream_t st);
 
 // ---- single-charge moves (k_delta.cu) ----
 // One request: move charge k of system sys to (x, y, z).
@@ -136,13 +166,14 @@ void init_delta_kernels();
 void launch_surface_potentials(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
                                const dbl4* surfx, double2* vsurf, cudaStream_t st);
 void launch_delta(const SysDev* sys, const int4* items, int nitems, const int2* req_items, const DeltaReq* reqs,
-                  int nreq, const double* xyz, const double* q, const float4* src_hi, const float4* src_lo,
-                  const dbl4* src64, const dbl4* surfx, const double2* surfqd, const double2* vsurf,
-                  const double* Mn, const double* inv_np1, double* dpart, double* de, unsigned int* counter,
-                  int* status, cudaStream_t st);
+                  int nreq, const double* xyz, const double* q, const int* perm, const int* iperm,
+                  const float4* src_hi, const float4* src_lo, const dbl4* src64, const dbl4* surfx,
+                  const double2* surfqd, const double2* vsurf, const double* Mn, const double* inv_np1, double* dpart,
+                  double* de, unsigned int* counter, int* status, cudaStream_t st);
 void launch_move(const SysDev* sys, const int2* surf_items, int n_surf_items, const DeltaReq* reqs, int nreq,
-                 Tables tab, int maxP, double* xyz, const double* q, const double* Mn, double* coef, double* r0,
-                 const dbl4* surfx, double2* surfqd, double2* vsurf, int have_v, float4* surf_a, float4* surf_b,
-                 dbl4* surf64_a, double* surf64_b, float4* src_hi, float4* src_lo, dbl4* src64, cudaStream_t st);
+                 Tables tab, int maxP, double* xyz, const double* q, const double* Mn, double* coef, float2* coef2,
+                 double* r0, const dbl4* surfx, double2* surfqd, double2* vsurf, int have_v, float4* surf_a,
+                 float4* surf_b, dbl4* surf64_a, double* surf64_b, const int* iperm, float4* src_hi, float4* src_lo,
+                 dbl4* src64, float4* boxes, cudaStream_t st);
 
 }  // namespace hsma

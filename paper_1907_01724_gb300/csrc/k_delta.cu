@@ -157,6 +157,7 @@ __global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restric
                                                          int nitems, const int2* __restrict__ req_items,
                                                          const DeltaReq* __restrict__ reqs, int nreq,
                                                          const double* __restrict__ xyz, const double* __restrict__ q,
+                                                         const int* __restrict__ perm, const int* __restrict__ iperm,
                                                          const float4* __restrict__ src_hi,
                                                          const float4* __restrict__ src_lo,
                                                          const dbl4* __restrict__ src64, const dbl4* __restrict__ surfx,
@@ -186,10 +187,10 @@ __global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restric
       // the moved charge and its own image
       acc += 0.5 * qk * (img_pot(In, xn, yn, zn) - img_pot(Io, xo, yo, zo));
     }
+    // rows run over sorted positions j (records are in the spatial order of k_order.cu)
     const int j = idx;
-    if (j < S.n && j != R.k) {
-      const long long gj = S.chg + j;
-      const double qj = q[gj];
+    if (j < S.n && j != iperm[kk]) {
+      const double qj = q[S.chg + perm[S.chg + j]];
       if (S.prec == HSMA_FP64) {
         const dbl4 rj = src64[S.src + j];
         const dbl4 kj = src64[S.src + S.n + j];
@@ -297,6 +298,34 @@ __global__ __launch_bounds__(256) void k_surface_potentials(const SysDev* __rest
   if (lane == 0) vsurf[S.surf + l] = make_double2(v0, v1);
 }
 
+// Order-independent float min/max in global memory (integer atomics on the bit patterns:
+// signed for non-negative values, unsigned for values with the sign bit set), so boxes
+// grown by several moves of one launch do not depend on their order.
+__device__ __forceinline__ void atomic_min_f(float* a, float v)
+{
+  if (!signbit(v))
+    atomicMin(reinterpret_cast<int*>(a), __float_as_int(v));
+  else
+    atomicMax(reinterpret_cast<unsigned int*>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_f(float* a, float v)
+{
+  if (!signbit(v))
+    atomicMax(reinterpret_cast<int*>(a), __float_as_int(v));
+  else
+    atomicMin(reinterpret_cast<unsigned int*>(a), __float_as_uint(v));
+}
+// box = (min, max) float4 pair: grow it to contain (x, y, z)
+__device__ __forceinline__ void box_grow(float4* box, float x, float y, float z)
+{
+  atomic_min_f(&box[0].x, x);
+  atomic_min_f(&box[0].y, y);
+  atomic_min_f(&box[0].z, z);
+  atomic_max_f(&box[1].x, x);
+  atomic_max_f(&box[1].y, y);
+  atomic_max_f(&box[1].z, z);
+}
+
 // Commit of a move, surface part: Q0, D, V0, V1 and the pair-sum surface records of every point.
 // Must run before k_move_charge (it reads the old position).
 __global__ __launch_bounds__(256) void k_move_surface(const SysDev* __restrict__ sys, const int2* __restrict__ items,
@@ -349,8 +378,10 @@ __global__ __launch_bounds__(256) void k_move_surface(const SysDev* __restrict__
 __global__ __launch_bounds__(256) void k_move_charge(const SysDev* __restrict__ sys, const DeltaReq* __restrict__ reqs,
                                                      Tables tab, double* __restrict__ xyz, const double* __restrict__ q,
                                                      const double* __restrict__ Mn, double* __restrict__ coef,
-                                                     double* __restrict__ r0, float4* __restrict__ src_hi,
-                                                     float4* __restrict__ src_lo, dbl4* __restrict__ src64)
+                                                     float2* __restrict__ coef2, double* __restrict__ r0,
+                                                     const int* __restrict__ iperm, float4* __restrict__ src_hi,
+                                                     float4* __restrict__ src_lo, dbl4* __restrict__ src64,
+                                                     float4* __restrict__ boxes)
 {
   extern __shared__ double sm[];
   const DeltaReq R = reqs[blockIdx.x];
@@ -401,13 +432,19 @@ __global__ __launch_bounds__(256) void k_move_charge(const SysDev* __restrict__ 
     while (n * n > idx) --n;
     while ((n + 1) * (n + 1) <= idx) ++n;
     const double mg = Mn[S.mn + n] - S.gam;
-    coef[S.coef + idx] += S.kc / a * qk * ((mg - cn) * Tn[idx] - (mg - co) * To[idx]);
+    const double c = coef[S.coef + idx] + S.kc / a * qk * ((mg - cn) * Tn[idx] - (mg - co) * To[idx]);
+    coef[S.coef + idx] = c;
+    const float ch = __double2float_rn(c);
+    coef2[S.coef + idx] = make_float2(ch, __double2float_rn(c - (double)ch));
   }
   if (threadIdx.x == 0) {
     const Image In = kelvin_image(S, R.x, R.y, R.z, qk);
     const Image Io = kelvin_image(S, xo, yo, zo, qk);
     r0[R.sys] += In.C - Io.C;
-    const long long sr = S.src + R.k, sk = S.src + S.n + R.k;
+    // the records sit at k's sorted position; its boxes grow to cover the new points (the
+    // order itself is refreshed by the next full build)
+    const int ks = iperm[kk];
+    const long long sr = S.src + ks, sk = S.src + S.n + ks;
     if (S.prec == HSMA_FP64) {
       src64[sr] = make_dbl4(R.x, R.y, R.z, S.kc * qk);
       src64[sk] = make_dbl4(In.x, In.y, In.z, In.Q);
@@ -416,9 +453,12 @@ __global__ __launch_bounds__(256) void k_move_charge(const SysDev* __restrict__ 
       split2d(R.x, hx, lx); split2d(R.y, hy, ly); split2d(R.z, hz, lz);
       src_hi[sr] = make_float4(hx, hy, hz, (float)(S.kc * qk));
       src_lo[sr] = make_float4(lx, ly, lz, 0.f);
+      const long long b = S.bb + ks / kBox, bk = b + (S.n + kBox - 1) / kBox;
+      box_grow(boxes + 2 * b, hx, hy, hz);
       split2d(In.x, hx, lx); split2d(In.y, hy, ly); split2d(In.z, hz, lz);
       src_hi[sk] = make_float4(hx, hy, hz, (float)In.Q);
       src_lo[sk] = make_float4(lx, ly, lz, 0.f);
+      box_grow(boxes + 2 * bk, hx, hy, hz);
     }
     xyz[3 * kk] = R.x;
     xyz[3 * kk + 1] = R.y;
@@ -435,27 +475,30 @@ void launch_surface_potentials(const SysDev* sys, const int2* items, int nitems,
 }
 
 void launch_delta(const SysDev* sys, const int4* items, int nitems, const int2* req_items, const DeltaReq* reqs,
-                  int nreq, const double* xyz, const double* q, const float4* src_hi, const float4* src_lo,
-                  const dbl4* src64, const dbl4* surfx, const double2* surfqd, const double2* vsurf,
-                  const double* Mn, const double* inv_np1, double* dpart, double* de, unsigned int* counter,
-                  int* status, cudaStream_t st)
+                  int nreq, const double* xyz, const double* q, const int* perm, const int* iperm,
+                  const float4* src_hi, const float4* src_lo, const dbl4* src64, const dbl4* surfx,
+                  const double2* surfqd, const double2* vsurf, const double* Mn, const double* inv_np1, double* dpart,
+                  double* de, unsigned int* counter, int* status, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  k_delta<<<nitems, kDeltaThreads, 0, st>>>(sys, items, nitems, req_items, reqs, nreq, xyz, q, src_hi, src_lo, src64,
-                                            surfx, surfqd, vsurf, Mn, inv_np1, dpart, de, counter, status);
+  k_delta<<<nitems, kDeltaThreads, 0, st>>>(sys, items, nitems, req_items, reqs, nreq, xyz, q, perm, iperm, src_hi,
+                                            src_lo, src64, surfx, surfqd, vsurf, Mn, inv_np1, dpart, de, counter,
+                                            status);
 }
 
 void launch_move(const SysDev* sys, const int2* surf_items, int n_surf_items, const DeltaReq* reqs, int nreq,
-                 Tables tab, int maxP, double* xyz, const double* q, const double* Mn, double* coef, double* r0,
-                 const dbl4* surfx, double2* surfqd, double2* vsurf, int have_v, float4* surf_a, float4* surf_b,
-                 dbl4* surf64_a, double* surf64_b, float4* src_hi, float4* src_lo, dbl4* src64, cudaStream_t st)
+                 Tables tab, int maxP, double* xyz, const double* q, const double* Mn, double* coef, float2* coef2,
+                 double* r0, const dbl4* surfx, double2* surfqd, double2* vsurf, int have_v, float4* surf_a,
+                 float4* surf_b, dbl4* surf64_a, double* surf64_b, const int* iperm, float4* src_hi, float4* src_lo,
+                 dbl4* src64, float4* boxes, cudaStream_t st)
 {
   if (nreq <= 0) return;
   if (n_surf_items > 0)
     k_move_surface<<<n_surf_items, 256, 0, st>>>(sys, surf_items, reqs, xyz, q, Mn, tab.inv_np1, surfx, surfqd,
                                                  vsurf, have_v, surf_a, surf_b, surf64_a, surf64_b);
   k_move_charge<<<nreq, 256, 2 * (size_t)maxP * sizeof(double), st>>>(sys, reqs, tab, xyz, q, Mn,
-                                                                     coef, r0, src_hi, src_lo, src64);
+                                                                     coef, coef2, r0, iperm, src_hi, src_lo, src64,
+                                                                     boxes);
 }
 
 void init_delta_kernels()

@@ -5,14 +5,17 @@
 // Kelvin images, and M surface points each carrying a monopole and a dipole (the 3M discrete
 // images of eq. phicorrfinall).  Work is split into items (system, target block, source
 // chunk); persistent CTAs pull items from an atomic counter (longest items first) and write
-// one compensated FP32 partial per (chunk, target), which k_reduce sums in FP64 in a fixed
-// order, so results do not depend on scheduling.
+// one compensated FP32 partial per (chunk, target), which k_reduce sums in a fixed order
+// (FP64, or double-float on the FP32 path), so results do not depend on scheduling.  Records
+// and partials are in the spatial order of k_order.cu; k_reduce maps them back to input order.
 //
 // FP32 path (ALU bound, no tensor cores: the sum is not a dense contraction):
 //  * real and Kelvin records hold hi/lo-split coordinates; with dh the FP32 difference of the
 //    high parts (exact for nearby points) and dl that of the low parts, s = dh + dl is the
 //    coordinate difference to FP32 relative accuracy and r^2 = sum s^2, even for a charge next
-//    to its own image (4 FP32 operations per coordinate);
+//    to its own image (4 FP32 operations per coordinate); sources in a 32-record box farther
+//    than kNearRel a from the box of a warp's targets use the hi parts alone (1 operation per
+//    coordinate), see k_pairs_f32.cuh;
 //  * 1/r is one MUFU rsqrt.approx per pair;
 //  * each target keeps an FP32 partial per staged tile, folded into an (hi, lo) two-sum pair;
 //  * surface points apply the dipole layer in its dy -> 0 limit sharing the monopole's rsqrt.
@@ -20,6 +23,7 @@
 // the cancellation-free form 2 (R_tau - x.yhat) / (d+ d- (d+ + d-)).
 #include <math.h>
 
+#include "df64.cuh"
 #include "hsma_internal.cuh"
 
 namespace hsma {
@@ -73,148 +77,7 @@ __device__ __forceinline__ ChunkInfo decode_chunk(const SysDev& S, int c)
 }
 
 // ---------------------------------------------------------------------------------------
-template <int NT, int K>
-__global__ __launch_bounds__(NT) void k_pairs_f32(const SysDev* __restrict__ sys, const int4* __restrict__ items,
-                                                  int nitems, unsigned int* __restrict__ counter,
-                                                  const float4* __restrict__ src_hi,
-                                                  const float4* __restrict__ src_lo,
-                                                  const float4* __restrict__ surf_a,
-                                                  const float4* __restrict__ surf_b, float2* __restrict__ part)
-{
-  __shared__ __align__(16) float4 shA[2][NT];
-  __shared__ __align__(16) float4 shB[2][NT];
-  __shared__ int s_item;
-  const int tid = threadIdx.x;
-
-  for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= nitems) break;
-    const int4 it = items[item];
-    const SysDev& S = sys[it.x];
-    const int n = S.n;
-    const int t0 = it.y * (NT * K);
-    const ChunkInfo ch = decode_chunk(S, it.z);
-
-    // targets: hi/lo of the real records (a slot past the end repeats the block's first target)
-    float txh[K], tyh[K], tzh[K], txl[K], tyl[K], tzl[K];
-    int tix[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int i = t0 + k * NT + tid;
-      const int ii = i < n ? i : t0;
-      tix[k] = i;
-      const float4 h = src_hi[S.src + ii];
-      const float4 l = src_lo[S.src + ii];
-      txh[k] = h.x; tyh[k] = h.y; tzh[k] = h.z;
-      txl[k] = l.x; tyl[k] = l.y; tzl[k] = l.z;
-    }
-    float H[K], L[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) H[k] = L[k] = 0.f;
-
-    const float4* gA = ch.type == 2 ? surf_a + ch.off : src_hi + ch.off;
-    const float4* gB = ch.type == 2 ? surf_b + ch.off : src_lo + ch.off;
-    const int ntiles = (ch.count + NT - 1) / NT;
-    // the diagonal (target == source) can only occur in a real chunk overlapping the block
-    const bool diag_chunk = ch.type == 0 && ch.first < t0 + NT * K && t0 < ch.first + ch.count;
-
-    if (tid < ch.count) {
-      cp_async16(&shA[0][tid], gA + tid);
-      cp_async16(&shB[0][tid], gB + tid);
-    }
-    cp_async_commit();
-    for (int t = 0; t < ntiles; ++t) {
-      const int buf = t & 1;
-      if (t + 1 < ntiles) {
-        const int s = (t + 1) * NT + tid;
-        if (s < ch.count) {
-          cp_async16(&shA[buf ^ 1][tid], gA + s);
-          cp_async16(&shB[buf ^ 1][tid], gB + s);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncthreads();
-      const int cnt = min(NT, ch.count - t * NT);
-      const float4* A = shA[buf];
-      const float4* B = shB[buf];
-      float acc[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) acc[k] = 0.f;
-      if (ch.type == 2) {
-#pragma unroll 2
-        for (int s = 0; s < cnt; ++s) {
-          const float4 y = A[s];
-          const float Dp = B[s].x;
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const float dx = txh[k] - y.x, dy = tyh[k] - y.y, dz = tzh[k] - y.z;
-            float r2 = dx * dx;
-            r2 = fmaf(dy, dy, r2);
-            r2 = fmaf(dz, dz, r2);
-            const float inv = rsqrt_mufu(r2);
-            float dot = dx * y.x;
-            dot = fmaf(dy, y.y, dot);
-            dot = fmaf(dz, y.z, dot);
-            const float u = dot * (inv * inv);
-            const float v = fmaf(Dp, u, y.w);
-            acc[k] = fmaf(v, inv, acc[k]);
-          }
-        }
-      } else if (diag_chunk && (ch.first + t * NT) < t0 + NT * K && t0 < ch.first + t * NT + cnt) {
-        const int sbase = ch.first + t * NT;
-        for (int s = 0; s < cnt; ++s) {
-          const float4 h = A[s];
-          const float4 l = B[s];
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const float dx = txh[k] - h.x, dy = tyh[k] - h.y, dz = tzh[k] - h.z;
-            const float ex = (txl[k] - l.x) + dx, ey = (tyl[k] - l.y) + dy, ez = (tzl[k] - l.z) + dz;
-            float r2 = ex * ex;
-            r2 = fmaf(ey, ey, r2);
-            r2 = fmaf(ez, ez, r2);
-            float inv = rsqrt_mufu(r2);
-            inv = (sbase + s == tix[k]) ? 0.f : inv;
-            acc[k] = fmaf(h.w, inv, acc[k]);
-          }
-        }
-      } else {
-#pragma unroll 2
-        for (int s = 0; s < cnt; ++s) {
-          const float4 h = A[s];
-          const float4 l = B[s];
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const float dx = txh[k] - h.x, dy = tyh[k] - h.y, dz = tzh[k] - h.z;
-            const float ex = (txl[k] - l.x) + dx, ey = (tyl[k] - l.y) + dy, ez = (tzl[k] - l.z) + dz;
-            float r2 = ex * ex;
-            r2 = fmaf(ey, ey, r2);
-            r2 = fmaf(ez, ez, r2);
-            acc[k] = fmaf(h.w, rsqrt_mufu(r2), acc[k]);
-          }
-        }
-      }
-      // two-sum fold of the tile partial
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float s = H[k] + acc[k];
-        const float bp = s - H[k];
-        L[k] += (H[k] - (s - bp)) + (acc[k] - bp);
-        H[k] = s;
-      }
-      __syncthreads();
-    }
-    float2* out = part + S.part + (long long)it.z * n;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (tix[k] < n) out[tix[k]] = make_float2(H[k], L[k]);
-  }
-}
+#include "k_pairs_f32.cuh"
 
 // Tile configurations (CTA threads, targets per thread); the autotuner picks one per size class.
 #define HSMA_PAIR_CONFIGS(X) \
@@ -245,12 +108,13 @@ int pairs_f32_occupancy(int cfg)
 
 void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
                       const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
-                      float2* part, cudaStream_t st)
+                      const float4* boxes, float2* part, cudaStream_t st)
 {
   switch (cfg) {
 #define HSMA_CFG_LAUNCH(i, nt, k)                                                                          \
   case i:                                                                                                  \
-    k_pairs_f32<nt, k><<<grid, nt, 0, st>>>(sys, items, nitems, counter, src_hi, src_lo, surf_a, surf_b, part); \
+    k_pairs_f32<nt, k><<<grid, nt, 0, st>>>(sys, items, nitems, counter, src_hi, src_lo, surf_a, surf_b, boxes, \
+                                            part);                                                             \
     break;
     HSMA_PAIR_CONFIGS(HSMA_CFG_LAUNCH)
 #undef HSMA_CFG_LAUNCH
@@ -361,7 +225,8 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
                                                         const int2* __restrict__ items,
                                                         const float2* __restrict__ part,
                                                         const double* __restrict__ part64, int prec,
-                                                        const double* __restrict__ q, const double* __restrict__ r0,
+                                                        const double* __restrict__ q, const int* __restrict__ perm,
+                                                        const double* __restrict__ r0,
                                                         double* __restrict__ phi_c, double* __restrict__ phi_r,
                                                         double* __restrict__ phi_t, double* __restrict__ epart,
                                                         double* __restrict__ energy, unsigned int* __restrict__ counter,
@@ -380,30 +245,42 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   double et = 0.0, er = 0.0;
   double pc = 0.0, pr = 0.0;
   const int nch = S.ncr + S.nck + S.ncs;
-  if (i < n) {
-    if (prec == HSMA_FP64) {
+  if (prec == HSMA_FP64) {
+    if (i < n) {
       const double* b = part64 + S.part + i;
       for (int c = sub; c < S.ncr; c += kRedLanes) pc += b[(long long)c * n];
       for (int c = S.ncr + sub; c < nch; c += kRedLanes) pr += b[(long long)c * n];
-    } else {
+    }
+    for (int o = 1; o < kRedLanes; o <<= 1) {
+      pc += __shfl_xor_sync(0xffffffffu, pc, o);
+      pr += __shfl_xor_sync(0xffffffffu, pr, o);
+    }
+  } else {
+    // the (hi, lo) partials are summed in double-float arithmetic on the FP32 pipes
+    df c = df_make(0.f, 0.f), r = df_make(0.f, 0.f);
+    if (i < n) {
       const float2* b = part + S.part + i;
-      for (int c = sub; c < S.ncr; c += kRedLanes) {
-        const float2 v = b[(long long)c * n];
-        pc += (double)v.x + (double)v.y;
+      for (int k = sub; k < S.ncr; k += kRedLanes) {
+        const float2 v = b[(long long)k * n];
+        c = c + df_make(v.x, v.y);
       }
-      for (int c = S.ncr + sub; c < nch; c += kRedLanes) {
-        const float2 v = b[(long long)c * n];
-        pr += (double)v.x + (double)v.y;
+      for (int k = S.ncr + sub; k < nch; k += kRedLanes) {
+        const float2 v = b[(long long)k * n];
+        r = r + df_make(v.x, v.y);
       }
     }
-  }
-  for (int o = 1; o < kRedLanes; o <<= 1) {
-    pc += __shfl_xor_sync(0xffffffffu, pc, o);
-    pr += __shfl_xor_sync(0xffffffffu, pr, o);
+    for (int o = 1; o < kRedLanes; o <<= 1) {
+      c = c + df_make(__shfl_xor_sync(0xffffffffu, c.hi, o), __shfl_xor_sync(0xffffffffu, c.lo, o));
+      r = r + df_make(__shfl_xor_sync(0xffffffffu, r.hi, o), __shfl_xor_sync(0xffffffffu, r.lo, o));
+    }
+    if (sub == 0) {
+      pc = df_to_double(c);
+      pr = df_to_double(r);
+    }
   }
   if (i < n && sub == 0) {
     pr += r0[it.x];
-    const long long o = S.chg + i;
+    const long long o = S.chg + perm[S.chg + i];  // partials are in sorted order
     phi_c[o] = pc;
     phi_r[o] = pr;
     phi_t[o] = pc + pr;
@@ -453,13 +330,13 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
 }
 
 void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
-                   const float2* part, const double* part64, int prec, const double* q, const double* r0,
-                   double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy, unsigned int* counter,
-                   int* status, cudaStream_t st)
+                   const float2* part, const double* part64, int prec, const double* q, const int* perm,
+                   const double* r0, double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy,
+                   unsigned int* counter, int* status, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  k_reduce<<<nitems, kRedThreads, 0, st>>>(sys, sel, sel_rng, nsel, items, part, part64, prec, q, r0, phi_c, phi_r,
-                                           phi_t, epart, energy, counter, status);
+  k_reduce<<<nitems, kRedThreads, 0, st>>>(sys, sel, sel_rng, nsel, items, part, part64, prec, q, perm, r0, phi_c,
+                                           phi_r, phi_t, epart, energy, counter, status);
 }
 
 }  // namespace hsma

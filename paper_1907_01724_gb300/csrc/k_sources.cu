@@ -2,16 +2,19 @@
 //   k_setup            (once per layout) per-system scalars eps, mu, R_tau, dy, gamma, sigma,
 //                      dbar, the Kirkwood coefficients M_n (Sec. 2.2-2.3), recurrence tables
 //                      and the Fibonacci points and weights of the auxiliary sphere (Sec. 2.4)
-//   k_images_moments   trapezoid-modified Kelvin images q_K at r_K (Sec. 2.4) and the
-//                      charge moments of the truncated correction coefficients
-//   k_coef_reduce      correction coefficients hat A_nm (eq. phim), FP64
-//   k_surface          Phi_corr and dPhi_corr/dr at the Fibonacci points and the monopole /
+//   k_surface_basis    (once per layout) solid harmonics of the auxiliary-sphere points
+//   k_images           trapezoid-modified Kelvin images q_K at r_K (Sec. 2.4) and the pair-sum
+//                      records, in spatial order, with the bounding box of every 32 records
+//   k_moments          charge moments of the truncated correction coefficients
+//   k_coef_reduce      correction coefficients hat A_nm (eq. phim)
+//   k_surface_mat      Phi_corr and dPhi_corr/dr at the Fibonacci points and the monopole /
 //                      dipole surface images (eqs. GreenSecond, approxG, threeintegrals,
 //                      phicorrfinall)
-// All arithmetic here is FP64; the FP32 path only stores its pair-sum records in FP32.
-// FP64 division, square root and trigonometric functions are slow on this GPU, so everything
-// that depends only on the parameters is done once in k_setup, and the per-step kernels use
-// multiplications by stored reciprocals.
+// Geometry (images, radii, centre constants) is FP64.  The solid-harmonic sums run in FP64 on
+// the FP64 path and in double-float arithmetic (df64.cuh) on the FP32 path: FP64 on this GPU
+// runs at about 1/73 of the FP32 rate, and so do its division, square root and trigonometric
+// functions, so everything that depends only on the parameters is done once per layout, and
+// the per-step kernels keep FP64 to a few operations per charge.
 //
 // Spherical harmonics are used as real, normalised solid harmonics
 //   T^c_nm(x) = N_nm r^n P_n^m(cos t) cos(m f),  T^s_nm(x) = N_nm r^n P_n^m(cos t) sin(m f),
@@ -27,6 +30,8 @@
 // charge moments.  Coefficient index: idx(n, m) = n^2 + n + m, m in [-n, n]; m < 0 holds
 // the sine part of order |m|.
 #include <math.h>
+
+#include <cmath>
 
 #include "df64.cuh"
 #include "hsma_internal.cuh"
@@ -135,6 +140,11 @@ struct Num<double> {
   static __device__ __forceinline__ double ra(const Tables& t, int i) { return t.rec_a[i]; }
   static __device__ __forceinline__ double rb(const Tables& t, int i) { return t.rec_b[i]; }
   static __device__ __forceinline__ double sc(const Tables& t, int i) { return t.sect[i]; }
+  // a value in an 8-byte slot of a double-typed buffer
+  static __device__ __forceinline__ double ld(const double* p, long long i) { return p[i]; }
+  static __device__ __forceinline__ void st(double* p, long long i, double v) { p[i] = v; }
+  static __device__ __forceinline__ double shfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  static __device__ __forceinline__ double coefv(const double* c, const float2*, long long i) { return c[i]; }
 };
 template <>
 struct Num<df> {
@@ -156,6 +166,25 @@ struct Num<df> {
   static __device__ __forceinline__ df sc(const Tables& t, int i)
   {
     const float2 v = t.sect2[i];
+    return df_make(v.x, v.y);
+  }
+  // a (hi, lo) pair in an 8-byte slot of a double-typed buffer
+  static __device__ __forceinline__ df ld(const double* p, long long i)
+  {
+    const float2 v = reinterpret_cast<const float2*>(p)[i];
+    return df_make(v.x, v.y);
+  }
+  static __device__ __forceinline__ void st(double* p, long long i, df v)
+  {
+    reinterpret_cast<float2*>(p)[i] = make_float2(v.hi, v.lo);
+  }
+  static __device__ __forceinline__ df shfl(df v, int o)
+  {
+    return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+  }
+  static __device__ __forceinline__ df coefv(const double*, const float2* c2, long long i)
+  {
+    const float2 v = c2[i];
     return df_make(v.x, v.y);
   }
 };
@@ -199,77 +228,165 @@ __device__ __forceinline__ void split2(double x, float& hi, float& lo)
   lo = __double2float_rn(x - (double)hi);
 }
 
-constexpr int kMomThreads = 256;  // moment blocks hold up to kMomTile charges
-constexpr int kMomWarps = kMomThreads / 32;
 
-// Kelvin images (Sec. 2.4): r_K = a^2/r along xhat, q_K = (q/a)[gamma r_K + dbar (R_tau - r_K)/2].
-// Records: real charge (x, k q/eps1) and Kelvin image (r_K xhat, k q_K/eps1); FP32 path stores
-// (hi x, hi y, hi z, Q) and (lo x, lo y, lo z, 0).
-template <int MAXJ, class R>
-__global__ __launch_bounds__(kMomThreads) void k_images_moments(
-    const SysDev* __restrict__ sys, const int2* __restrict__ items, const double* __restrict__ xyz,
-    const double* __restrict__ q, Tables tab, float4* __restrict__ src_hi, float4* __restrict__ src_lo,
-    dbl4* __restrict__ src64, int prec, double* __restrict__ mom, int mom_stride, int G, int* __restrict__ status)
+constexpr int kMomThreads = 256;  // a moment block holds at most kMomTile <= kMomThreads charges
+constexpr int kMomWarps = kMomThreads / 32;
+static_assert(kMomTile <= kMomThreads, "one charge per thread in the preparation pass");
+
+// Kelvin image of one charge (Sec. 2.4): r_K = a^2/r along xhat,
+// q_K = (q/a)[gamma r_K + dbar (R_tau - r_K)/2], strength k q_K/eps1.  r, r_K and the image
+// point use separately rounded IEEE operations (no FMA contraction): a charge at distance d from
+// the interface sits ~2d from its own image, so one ulp in r would be amplified by r/d in the
+// image term.  A charge within kCentreRel a of the centre has its image at infinity: a constant
+// potential k q/(eps1 a) (gamma - dbar/2) at every target (returned in C; the record then has
+// zero strength).
+struct KelvinRec {
+  double r, kx, ky, kz, QK, C;
+};
+__device__ __forceinline__ KelvinRec kelvin_rec(const SysDev& S, double x, double y, double z, double qi)
 {
-  extern __shared__ double sm[];
+  KelvinRec k;
+  k.r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+  k.C = 0.0;
+  if (k.r <= kCentreRel * S.a) {
+    k.C = S.kc_a * qi * (S.gam - 0.5 * S.dbar);
+    k.kx = 1e15 * S.a;
+    k.ky = 0.0;
+    k.kz = 0.0;
+    k.QK = 0.0;
+  } else {
+    const double ar = __ddiv_rn(S.a, k.r);
+    const double s = __dmul_rn(ar, ar);
+    const double rK = __dmul_rn(ar, S.a);
+    k.kx = __dmul_rn(s, x);
+    k.ky = __dmul_rn(s, y);
+    k.kz = __dmul_rn(s, z);
+    k.QK = S.kc * (qi * S.inv_a * (S.gam * rK + S.dbar * (S.Rtau - rK) * 0.5));
+  }
+  return k;
+}
+
+// Pair-sum records in the spatial order of k_order.cu: thread t of item (s, b) handles sorted
+// position i = 256 b + t, i.e. input charge perm[i].  Real record (x, k q/eps1) at src + i and
+// Kelvin record at src + n + i; the FP32 path stores (hi x, hi y, hi z, Q) and
+// (lo x, lo y, lo z, 0) and, per warp (32 consecutive records), the bounding box of the hi
+// coordinates (min, max as two float4) of the real and of the Kelvin records.
+constexpr int kImgThreads = 256;
+__global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict__ sys, const int2* __restrict__ items,
+                                                        const double* __restrict__ xyz, const double* __restrict__ q,
+                                                        const int* __restrict__ perm, float4* __restrict__ src_hi,
+                                                        float4* __restrict__ src_lo, dbl4* __restrict__ src64,
+                                                        float4* __restrict__ boxes, int prec, int* __restrict__ status)
+{
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
-  const int n = S.n, P = S.P, p = S.p;
-  const double a = S.a, kc = S.kc, gam = S.gam, dbar = S.dbar, Rtau = S.Rtau, inv_a = S.inv_a;
-  const int c0 = it.y * S.mom_tile;
-  const int c1 = min(n, c0 + S.mom_tile);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-  static_assert(sizeof(R) == sizeof(double), "moment arithmetic uses 8-byte values");
-  R* T = reinterpret_cast<R*>(sm);                 // [G][P]
-  R* qv = T + (size_t)G * P;                       // [G]
-  R* qc = qv + G;                                  // [G]
-  double* red = reinterpret_cast<double*>(qc + G);  // [kMomWarps]
-
-  // images
-  double r0 = 0.0;
-  for (int i = c0 + tid; i < c1; i += kMomThreads) {
-    const long long gi = S.chg + i;
+  const int n = S.n;
+  const int i = it.y * kImgThreads + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  float bmin[6], bmax[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    bmin[d] = 3.0e38f;
+    bmax[d] = -3.0e38f;
+  }
+  if (i < n) {
+    const long long gi = S.chg + perm[S.chg + i];
     const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
-    // r, r_K and the Kelvin point use separately rounded IEEE operations (no FMA contraction):
-    // a charge at distance d from the interface sits ~2d from its own image, so one ulp in r
-    // would be amplified by r/d in the image term
-    const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
-    if (!(r < a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) atomicOr(status, kStOutside);
-    double kx, ky, kz, QK;
-    if (r <= kCentreRel * a) {
-      // image at infinity: constant potential k q/(eps1 a) (gamma - dbar/2) at every target
-      r0 += S.kc_a * qi * (gam - 0.5 * dbar);
-      kx = 1e15 * a;
-      ky = 0.0;
-      kz = 0.0;
-      QK = 0.0;
-    } else {
-      const double ar = __ddiv_rn(a, r);
-      const double s = __dmul_rn(ar, ar);
-      const double rK = __dmul_rn(ar, a);
-      kx = __dmul_rn(s, x);
-      ky = __dmul_rn(s, y);
-      kz = __dmul_rn(s, z);
-      QK = kc * (qi * inv_a * (gam * rK + dbar * (Rtau - rK) * 0.5));
-    }
+    const KelvinRec k = kelvin_rec(S, x, y, z, qi);
+    if (!(k.r < S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) atomicOr(status, kStOutside);
     const long long sr = S.src + i, sk = S.src + n + i;
     if (prec == HSMA_FP64) {
-      src64[sr] = make_dbl4(x, y, z, kc * qi);
-      src64[sk] = make_dbl4(kx, ky, kz, QK);
+      src64[sr] = make_dbl4(x, y, z, S.kc * qi);
+      src64[sk] = make_dbl4(k.kx, k.ky, k.kz, k.QK);
     } else {
       float hx, hy, hz, lx, ly, lz;
       split2(x, hx, lx);
       split2(y, hy, ly);
       split2(z, hz, lz);
-      src_hi[sr] = make_float4(hx, hy, hz, (float)(kc * qi));
+      src_hi[sr] = make_float4(hx, hy, hz, (float)(S.kc * qi));
       src_lo[sr] = make_float4(lx, ly, lz, 0.f);
-      split2(kx, hx, lx);
-      split2(ky, hy, ly);
-      split2(kz, hz, lz);
-      src_hi[sk] = make_float4(hx, hy, hz, (float)QK);
+      bmin[0] = bmax[0] = hx;
+      bmin[1] = bmax[1] = hy;
+      bmin[2] = bmax[2] = hz;
+      split2(k.kx, hx, lx);
+      split2(k.ky, hy, ly);
+      split2(k.kz, hz, lz);
+      src_hi[sk] = make_float4(hx, hy, hz, (float)k.QK);
       src_lo[sk] = make_float4(lx, ly, lz, 0.f);
+      bmin[3] = bmax[3] = hx;
+      bmin[4] = bmax[4] = hy;
+      bmin[5] = bmax[5] = hz;
     }
+  }
+  if (prec != HSMA_FP64) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d)
+      for (int o = 16; o > 0; o >>= 1) {
+        bmin[d] = fminf(bmin[d], __shfl_xor_sync(0xffffffffu, bmin[d], o));
+        bmax[d] = fmaxf(bmax[d], __shfl_xor_sync(0xffffffffu, bmax[d], o));
+      }
+    if (lane == 0 && i < n) {
+      const long long b = S.bb + i / kBox;
+      const long long bk = b + (n + kBox - 1) / kBox;
+      boxes[2 * b] = make_float4(bmin[0], bmin[1], bmin[2], 0.f);
+      boxes[2 * b + 1] = make_float4(bmax[0], bmax[1], bmax[2], 0.f);
+      boxes[2 * bk] = make_float4(bmin[3], bmin[4], bmin[5], 0.f);
+      boxes[2 * bk + 1] = make_float4(bmax[3], bmax[4], bmax[5], 0.f);
+    }
+  }
+}
+
+void launch_images(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
+                   const int* perm, float4* src_hi, float4* src_lo, dbl4* src64, float4* boxes, int prec, int* status,
+                   cudaStream_t st)
+{
+  if (nitems <= 0) return;
+  k_images<<<nitems, kImgThreads, 0, st>>>(sys, items, xyz, q, perm, src_hi, src_lo, src64, boxes, prec, status);
+}
+
+// Charge moments of the correction coefficients.  Thread t of a block prepares charge c0 + t
+// (FP64): the centre constant of a charge at the centre, and its moment inputs u, v, w = x/a,
+// rho^2, q and q c in the moment arithmetic R (shared memory), so the moment phase runs on R
+// alone: per group of G charges, thread t computes column m = t mod (p+1) of charge t / (p+1)
+// (solid_column), then thread t accumulates coefficients t + j kMomThreads over the group.
+// Moments are stored as R values in 8-byte slots; slot 2P holds the block's centre constant.
+template <int MAXJ, class R>
+__global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restrict__ sys, const int2* __restrict__ items,
+                                                         const double* __restrict__ xyz, const double* __restrict__ q,
+                                                         Tables tab, double* __restrict__ mom, int mom_stride, int G)
+{
+  extern __shared__ double sm[];
+  const int2 it = items[blockIdx.x];
+  const SysDev& S = sys[it.x];
+  const int n = S.n, P = S.P, p = S.p;
+  const double dbar = S.dbar, inv_a = S.inv_a;
+  const int c0 = it.y * S.mom_tile;
+  const int cnt = min(n, c0 + S.mom_tile) - c0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  static_assert(sizeof(R) == sizeof(double), "moment arithmetic uses 8-byte values");
+  R* T = reinterpret_cast<R*>(sm);  // [G][P]
+  R* cu = T + (size_t)G * P;        // per charge of the tile: u, v, w, rho^2, q, q c
+  R* cv = cu + kMomThreads;
+  R* cw = cv + kMomThreads;
+  R* cr2 = cw + kMomThreads;
+  R* cq = cr2 + kMomThreads;
+  R* cqc = cq + kMomThreads;
+  double* red = reinterpret_cast<double*>(cqc + kMomThreads);  // [kMomWarps]
+
+  double r0 = 0.0;
+  if (tid < cnt) {
+    const long long gi = S.chg + c0 + tid;
+    const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
+    const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+    if (r <= kCentreRel * S.a) r0 += S.kc_a * qi * (S.gam - 0.5 * dbar);
+    const double ux = x * inv_a, uy = y * inv_a, uz = z * inv_a;
+    cu[tid] = Num<R>::from(ux);
+    cv[tid] = Num<R>::from(uy);
+    cw[tid] = Num<R>::from(uz);
+    cr2[tid] = Num<R>::from(ux * ux + uy * uy + uz * uz);
+    cq[tid] = Num<R>::from(qi);
+    cqc[tid] = Num<R>::from(qi * (dbar * (S.Rt_a * (r * inv_a) - 1.0) * 0.5));
   }
   // block sum of the centre-charge constants (fixed order)
   for (int o = 16; o > 0; o >>= 1) r0 += __shfl_xor_sync(0xffffffffu, r0, o);
@@ -281,25 +398,17 @@ __global__ __launch_bounds__(kMomThreads) void k_images_moments(
     for (int w = 0; w < kMomWarps; ++w) s += red[w];
     out[2 * P] = s;
   }
-
   // charge moments U_nm, V_nm
   R accU[MAXJ], accV[MAXJ];
 #pragma unroll
   for (int j = 0; j < MAXJ; ++j) accU[j] = accV[j] = Num<R>::zero();
-  for (int g0 = c0; g0 < c1; g0 += G) {
-    const int gcount = min(G, c1 - g0);
-    if (warp < gcount) {
-      const long long gi = S.chg + g0 + warp;
-      const double x = xyz[3 * gi] * inv_a, y = xyz[3 * gi + 1] * inv_a, z = xyz[3 * gi + 2] * inv_a;
-      const double rho2 = x * x + y * y + z * z;
-      R* Tg = T + (size_t)warp * P;
-      const R xr = Num<R>::from(x), yr = Num<R>::from(y), zr = Num<R>::from(z), r2r = Num<R>::from(rho2);
-      for (int m = lane; m <= p; m += 32) solid_column<R>(m, p, xr, yr, zr, r2r, tab, Tg);
-      if (lane == 0) {
-        const double qi = q[gi];
-        qv[warp] = Num<R>::from(qi);
-        qc[warp] = Num<R>::from(qi * (dbar * (S.Rt_a * sqrt(rho2) - 1.0) * 0.5));
-      }
+  const int ncol = p + 1;
+  const int tg = tid / ncol, tm = tid - tg * ncol;
+  for (int g0 = 0; g0 < cnt; g0 += G) {
+    const int gcount = min(G, cnt - g0);
+    if (tg < gcount) {
+      const int c = g0 + tg;
+      solid_column<R>(tm, p, cu[c], cv[c], cw[c], cr2[c], tab, T + (size_t)tg * P);
     }
     __syncthreads();
 #pragma unroll
@@ -309,8 +418,8 @@ __global__ __launch_bounds__(kMomThreads) void k_images_moments(
         R u = accU[j], v = accV[j];
         for (int g = 0; g < gcount; ++g) {
           const R t = T[(size_t)g * P + idx];
-          u = qv[g] * t + u;
-          v = qc[g] * t + v;
+          u = cq[g0 + g] * t + u;
+          v = cqc[g0 + g] * t + v;
         }
         accU[j] = u;
         accV[j] = v;
@@ -322,99 +431,114 @@ __global__ __launch_bounds__(kMomThreads) void k_images_moments(
   for (int j = 0; j < MAXJ; ++j) {
     const int idx = tid + j * kMomThreads;
     if (idx < P) {
-      out[idx] = Num<R>::to(accU[j]);
-      out[P + idx] = Num<R>::to(accV[j]);
+      Num<R>::st(out, idx, accU[j]);
+      Num<R>::st(out, P + idx, accV[j]);
     }
   }
 }
 
+// Charges per moment group: at most one solid-harmonic column per thread (G (p+1) <= 256) and
+// the group's G P values within the shared-memory budget.
 int moment_smem_group(int maxP)
 {
-  const size_t budget = 160 * 1024;
-  int G = (int)(budget / ((size_t)maxP * 8 + 16));
-  if (G > kMomWarps) G = kMomWarps;
+  int pmax = (int)std::lround(std::sqrt((double)maxP)) - 1;
+  if (pmax < 0) pmax = 0;
+  const size_t fixed = (6 * (size_t)kMomThreads + kMomWarps) * sizeof(double);
+  const size_t budget = 192 * 1024;
+  int G = kMomThreads / (pmax + 1);
+  const int Gs = (int)((budget - fixed) / ((size_t)maxP * sizeof(double)));
+  if (G > Gs) G = Gs;
   if (G < 1) G = 1;
   return G;
 }
 
-template <int MAXJ>
-static void launch_im(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
-                      Tables tab, float4* src_hi, float4* src_lo, dbl4* src64, int prec, double* mom,
-                      int mom_stride, int* status, cudaStream_t st)
+static size_t moment_smem_bytes(int maxP)
 {
-  const int G = moment_smem_group(maxP);
-  const size_t smem = ((size_t)G * maxP + 2 * G + kMomWarps) * sizeof(double);
-  if (prec == HSMA_FP64)
-    k_images_moments<MAXJ, double><<<nitems, kMomThreads, smem, st>>>(sys, items, xyz, q, tab, src_hi, src_lo, src64,
-                                                                       prec, mom, mom_stride, G, status);
-  else
-    k_images_moments<MAXJ, df><<<nitems, kMomThreads, smem, st>>>(sys, items, xyz, q, tab, src_hi, src_lo, src64,
-                                                                   prec, mom, mom_stride, G, status);
+  return ((size_t)moment_smem_group(maxP) * maxP + 6 * (size_t)kMomThreads + kMomWarps) * sizeof(double);
 }
 
-void launch_images_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz,
-                           const double* q, Tables tab, float4* src_hi, float4* src_lo, dbl4* src64, int prec,
-                           double* mom, int mom_stride, int* status, cudaStream_t st)
+template <int MAXJ>
+static void launch_mom(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
+                       Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
+{
+  const int G = moment_smem_group(maxP);
+  const size_t smem = moment_smem_bytes(maxP);
+  if (prec == HSMA_FP64)
+    k_moments<MAXJ, double><<<nitems, kMomThreads, smem, st>>>(sys, items, xyz, q, tab, mom, mom_stride, G);
+  else
+    k_moments<MAXJ, df><<<nitems, kMomThreads, smem, st>>>(sys, items, xyz, q, tab, mom, mom_stride, G);
+}
+
+void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
+                    Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
 {
   if (nitems <= 0) return;
   const int J = (maxP + kMomThreads - 1) / kMomThreads;
   if (J <= 1)
-    launch_im<1>(sys, items, nitems, maxP, xyz, q, tab, src_hi, src_lo, src64, prec, mom, mom_stride, status, st);
+    launch_mom<1>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
   else if (J <= 2)
-    launch_im<2>(sys, items, nitems, maxP, xyz, q, tab, src_hi, src_lo, src64, prec, mom, mom_stride, status, st);
+    launch_mom<2>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
   else if (J <= 4)
-    launch_im<4>(sys, items, nitems, maxP, xyz, q, tab, src_hi, src_lo, src64, prec, mom, mom_stride, status, st);
+    launch_mom<4>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
   else if (J <= 8)
-    launch_im<8>(sys, items, nitems, maxP, xyz, q, tab, src_hi, src_lo, src64, prec, mom, mom_stride, status, st);
+    launch_mom<8>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
   else if (J <= 16)
-    launch_im<16>(sys, items, nitems, maxP, xyz, q, tab, src_hi, src_lo, src64, prec, mom, mom_stride, status, st);
+    launch_mom<16>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
   else
-    launch_im<26>(sys, items, nitems, maxP, xyz, q, tab, src_hi, src_lo, src64, prec, mom, mom_stride, status, st);
+    launch_mom<26>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
 }
 
 // ---------------------------------------------------------------------------------------
 // hat A'_nm = (k/(eps1 a)) [(M_n - gamma) U_nm - V_nm].  A block owns kCoefChunk coefficients
 // (one per lane); its kCoefWarps warps split the moment blocks (warp w takes blocks w,
 // w + kCoefWarps, ...), and warp 0 adds the warp sums in order, so the result does not depend
-// on scheduling.
+// on scheduling.  Sums run in the moment arithmetic R; the coefficient is formed in FP64 and
+// also stored as an FP32 (hi, lo) pair for the FP32 path's surface synthesis.
 constexpr int kCoefWarps = 32;
+template <class R>
 __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* __restrict__ sys,
                                                                  const int2* __restrict__ items,
                                                                  const double* __restrict__ mom, int mom_stride,
                                                                  const double* __restrict__ Mn,
-                                                                 double* __restrict__ coef, double* __restrict__ r0)
+                                                                 double* __restrict__ coef, float2* __restrict__ coef2,
+                                                                 double* __restrict__ r0)
 {
-  __shared__ double su[kCoefWarps][kCoefChunk], sv[kCoefWarps][kCoefChunk], sr[kCoefWarps];
+  __shared__ R su[kCoefWarps][kCoefChunk], sv[kCoefWarps][kCoefChunk];
+  __shared__ double sr[kCoefWarps];
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int idx = it.y * kCoefChunk + lane;
   const double* base = mom + (size_t)S.mom * mom_stride;
-  double U = 0.0, V = 0.0, R = 0.0;
+  R U = Num<R>::zero(), V = Num<R>::zero();
+  double Rs = 0.0;
   if (idx < P)
     for (int b = warp; b < S.mom_blocks; b += kCoefWarps) {
-      U += base[(size_t)b * mom_stride + idx];
-      V += base[(size_t)b * mom_stride + P + idx];
+      U = U + Num<R>::ld(base, (long long)b * mom_stride + idx);
+      V = V + Num<R>::ld(base, (long long)b * mom_stride + P + idx);
     }
   if (it.y == 0 && lane == 0)
-    for (int b = warp; b < S.mom_blocks; b += kCoefWarps) R += base[(size_t)b * mom_stride + 2 * P];
+    for (int b = warp; b < S.mom_blocks; b += kCoefWarps) Rs += base[(size_t)b * mom_stride + 2 * P];
   su[warp][lane] = U;
   sv[warp][lane] = V;
-  if (lane == 0) sr[warp] = R;
+  if (lane == 0) sr[warp] = Rs;
   __syncthreads();
   if (warp == 0) {
-    U = 0.0;
-    V = 0.0;
+    U = Num<R>::zero();
+    V = Num<R>::zero();
+#pragma unroll 4
     for (int w = 0; w < kCoefWarps; ++w) {
-      U += su[w][lane];
-      V += sv[w][lane];
+      U = U + su[w][lane];
+      V = V + sv[w][lane];
     }
     if (idx < P) {
       int nn = (int)sqrtf((float)idx);
       while (nn * nn > idx) --nn;
       while ((nn + 1) * (nn + 1) <= idx) ++nn;
-      coef[S.coef + idx] = S.kc_a * ((Mn[S.mn + nn] - S.gam) * U - V);
+      const double c = S.kc_a * ((Mn[S.mn + nn] - S.gam) * Num<R>::to(U) - Num<R>::to(V));
+      coef[S.coef + idx] = c;
+      coef2[S.coef + idx] = pair_of(c);
     }
     if (it.y == 0 && lane == 0) {
       double s = 0.0;
@@ -425,22 +549,129 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
 }
 
 void launch_coef_reduce(const SysDev* sys, const int2* items, int nitems, const double* mom, int mom_stride,
-                        const double* Mn, double* coef, double* r0, cudaStream_t st)
+                        const double* Mn, double* coef, float2* coef2, double* r0, int prec, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  k_coef_reduce<<<nitems, kCoefWarps * 32, 0, st>>>(sys, items, mom, mom_stride, Mn, coef, r0);
+  if (prec == HSMA_FP64)
+    k_coef_reduce<double><<<nitems, kCoefWarps * 32, 0, st>>>(sys, items, mom, mom_stride, Mn, coef, coef2, r0);
+  else
+    k_coef_reduce<df><<<nitems, kCoefWarps * 32, 0, st>>>(sys, items, mom, mom_stride, Mn, coef, coef2, r0);
 }
 
 // ---------------------------------------------------------------------------------------
-// Surface images.  One warp per Fibonacci point y (from k_setup); lane m sums column m of
-//   Phi = sum A'_nm T_nm(y/a),   dPhi/dr = sum n A'_nm T_nm(y/a) / R_tau,
-// then a fixed-order shuffle reduction.  Records (Green's second identity + central
-// difference, eq. threeintegrals): monopole Q0 = w dPhi/dr / (4 pi) at y = R_tau yhat and
-// dipole D = w Phi / (4 pi) between y_- and y_+.
+// Surface images (Green's second identity + central difference, eq. threeintegrals) from
+//   Phi = sum A'_nm T_nm(y/a),   dPhi/dr = sum n A'_nm T_nm(y/a) / R_tau
+// at each Fibonacci point y: monopole Q0 = w dPhi/dr / (4 pi) at y = R_tau yhat and dipole
+// D = w Phi / (4 pi) between y_- and y_+.
 constexpr int kSurfThreads = 256;
 constexpr int kSurfWarps = kSurfThreads / 32;
 static_assert(kSurfWarps == kSurfPointsPerBlock, "one warp per surface point");
 
+__device__ __forceinline__ void surface_records(const SysDev& S, long long o, const dbl4& yw, double ph, double dph,
+                                                int prec, float4* __restrict__ surf_a, float4* __restrict__ surf_b,
+                                                dbl4* __restrict__ surf64_a, double* __restrict__ surf64_b,
+                                                double2* __restrict__ surfqd)
+{
+  const double w4 = yw.w * (0.25 / kPi);
+  const double Q0 = w4 * (dph * S.inv_Rt);
+  const double D = w4 * ph;
+  surfqd[o] = make_double2(Q0, D);
+  if (prec == HSMA_FP64) {
+    surf64_a[o] = make_dbl4(yw.x, yw.y, yw.z, Q0);
+    surf64_b[o] = D;
+  } else {
+    // FP32 path: the dipole is applied through its Delta y -> 0 limit
+    // D (R_tau - x.yhat)/d^3 = Dp ((x - y).y) / d^3 with Dp = -D/R_tau
+    surf_a[o] = make_float4((float)yw.x, (float)yw.y, (float)yw.z, (float)Q0);
+    surf_b[o] = make_float4((float)(-D * S.inv_Rt), 0.f, 0.f, 0.f);
+  }
+}
+
+// Solid harmonics of the auxiliary-sphere points, T_nm(y_j/a), once per layout (FP64; one warp
+// per point, lane = column).  y_j/a = (1 + tau) yhat_j does not depend on a, so systems with the
+// same (tau, M, F1, F2, p) share one table, row j at S.sb + j P; the FP32 path keeps each value
+// as an FP32 (hi, lo) pair in its 8-byte slot.
+__global__ __launch_bounds__(kSurfThreads) void k_surface_basis(const SysDev* __restrict__ sys,
+                                                                const int2* __restrict__ items, Tables tab,
+                                                                const dbl4* __restrict__ surfx, double* __restrict__ sb,
+                                                                int prec)
+{
+  const int2 it = items[blockIdx.x];
+  const SysDev& S = sys[it.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = it.y * kSurfWarps + warp;
+  if (j >= S.M) return;
+  const dbl4 yw = surfx[S.surf + j];
+  const double u = yw.x * S.inv_a, v = yw.y * S.inv_a, w = yw.z * S.inv_a;
+  const double rho2 = u * u + v * v + w * w;
+  double* row = sb + S.sb + (long long)j * S.P;
+  for (int m = lane; m <= S.p; m += 32) solid_column<double>(m, S.p, u, v, w, rho2, tab, row);
+  if (prec != HSMA_FP64) {
+    __syncwarp();
+    for (int i = lane; i < S.P; i += 32) {
+      const double x = row[i];
+      reinterpret_cast<float2*>(row)[i] = pair_of(x);
+    }
+  }
+}
+
+void launch_surface_basis(const SysDev* sys, const int2* items, int nitems, Tables tab, const dbl4* surfx, double* sb,
+                          int prec, cudaStream_t st)
+{
+  if (nitems <= 0) return;
+  k_surface_basis<<<nitems, kSurfThreads, 0, st>>>(sys, items, tab, surfx, sb, prec);
+}
+
+// Per step, with the basis: one warp per point, lanes stride the coefficients (R arithmetic),
+// fixed-order shuffle tree.
+template <class R>
+__global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __restrict__ sys,
+                                                              const int2* __restrict__ items,
+                                                              const double* __restrict__ coef,
+                                                              const float2* __restrict__ coef2,
+                                                              const double* __restrict__ sb,
+                                                              float4* __restrict__ surf_a, float4* __restrict__ surf_b,
+                                                              dbl4* __restrict__ surf64_a,
+                                                              double* __restrict__ surf64_b,
+                                                              const dbl4* __restrict__ surfx,
+                                                              double2* __restrict__ surfqd, int prec)
+{
+  extern __shared__ double sm[];
+  const int2 it = items[blockIdx.x];
+  const SysDev& S = sys[it.x];
+  const int P = S.P, M = S.M;
+  R* A = reinterpret_cast<R*>(sm);  // [P] A'_nm
+  R* nA = A + P;                    // [P] n A'_nm
+  for (int i = threadIdx.x; i < P; i += kSurfThreads) {
+    int nn = (int)sqrtf((float)i);
+    while (nn * nn > i) --nn;
+    while ((nn + 1) * (nn + 1) <= i) ++nn;
+    const R c = Num<R>::coefv(coef, coef2, S.coef + i);
+    A[i] = c;
+    nA[i] = Num<R>::from_int(nn) * c;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = it.y * kSurfWarps + warp;
+  if (j >= M) return;
+  const double* row = sb + S.sb + (long long)j * P;
+  R ph = Num<R>::zero(), dph = Num<R>::zero();
+  for (int i = lane; i < P; i += 32) {
+    const R b = Num<R>::ld(row, i);
+    ph = A[i] * b + ph;
+    dph = nA[i] * b + dph;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    ph = ph + Num<R>::shfl(ph, off);
+    dph = dph + Num<R>::shfl(dph, off);
+  }
+  if (lane == 0)
+    surface_records(S, S.surf + j, surfx[S.surf + j], Num<R>::to(ph), Num<R>::to(dph), prec, surf_a, surf_b,
+                    surf64_a, surf64_b, surfqd);
+}
+
+// Without a basis table (too large for the workspace): lane m runs column m of the recurrence
+// at the point itself.
 template <class R>
 __global__ __launch_bounds__(kSurfThreads) void k_surface(const SysDev* __restrict__ sys,
                                                           const int2* __restrict__ items,
@@ -499,28 +730,24 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface(const SysDev* __restri
     ph += __shfl_xor_sync(0xffffffffu, ph, off);
     dph += __shfl_xor_sync(0xffffffffu, dph, off);
   }
-  if (lane == 0) {
-    const double w4 = yw.w * (0.25 / kPi);
-    const double Q0 = w4 * (dph * S.inv_Rt);
-    const double D = w4 * ph;
-    surfqd[o] = make_double2(Q0, D);
-    if (prec == HSMA_FP64) {
-      surf64_a[o] = make_dbl4(yw.x, yw.y, yw.z, Q0);
-      surf64_b[o] = D;
-    } else {
-      // FP32 path: the dipole is applied through its Delta y -> 0 limit
-      // D (R_tau - x.yhat)/d^3 = Dp ((x - y).y) / d^3 with Dp = -D/R_tau
-      surf_a[o] = make_float4((float)yw.x, (float)yw.y, (float)yw.z, (float)Q0);
-      surf_b[o] = make_float4((float)(-D * S.inv_Rt), 0.f, 0.f, 0.f);
-    }
-  }
+  if (lane == 0) surface_records(S, o, yw, ph, dph, prec, surf_a, surf_b, surf64_a, surf64_b, surfqd);
 }
 
-void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, const double* coef, Tables tab,
-                    float4* surf_a, float4* surf_b, dbl4* surf64_a, double* surf64_b, dbl4* surfx, double2* surfqd,
-                    int prec, cudaStream_t st)
+void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, const double* coef,
+                    const float2* coef2, const double* sb, Tables tab, float4* surf_a, float4* surf_b,
+                    dbl4* surf64_a, double* surf64_b, dbl4* surfx, double2* surfqd, int prec, cudaStream_t st)
 {
   if (nitems <= 0) return;
+  if (sb) {
+    const size_t smem = 2 * (size_t)maxP * sizeof(double);
+    if (prec == HSMA_FP64)
+      k_surface_mat<double><<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, coef2, sb, surf_a, surf_b,
+                                                                surf64_a, surf64_b, surfx, surfqd, prec);
+    else
+      k_surface_mat<df><<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, coef2, sb, surf_a, surf_b, surf64_a,
+                                                            surf64_b, surfx, surfqd, prec);
+    return;
+  }
   const size_t smem = (size_t)maxP * sizeof(double);
   if (prec == HSMA_FP64)
     k_surface<double><<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, tab, surf_a, surf_b, surf64_a, surf64_b,
@@ -533,13 +760,14 @@ void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, 
 template <class R>
 static void moment_attrs()
 {
-  cudaFuncSetAttribute(k_images_moments<1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<4, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<8, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<16, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_images_moments<26, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<4, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<8, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<16, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<26, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_surface<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  cudaFuncSetAttribute(k_surface_mat<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
 }
 
 void init_source_kernels()

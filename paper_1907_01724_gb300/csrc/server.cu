@@ -260,17 +260,18 @@ static int launch_moves(hsma_server_t* s, const std::vector<int>& ridx, const hs
   SCK(cudaMemcpyAsync(e->dreq_d, s->dreq_h, sizeof(DeltaReq) * nr, cudaMemcpyHostToDevice, s->sA));
   SCK(cudaMemcpyAsync(e->ditems_d, s->ditems_h, sizeof(int4) * ni, cudaMemcpyHostToDevice, s->sA));
   SCK(cudaMemcpyAsync(e->dreqit_d, s->dranges_h, sizeof(int2) * nr, cudaMemcpyHostToDevice, s->sA));
-  hsma::launch_delta(e->sys_d, e->ditems_d, ni, e->dreqit_d, e->dreq_d, nr, e->xyz_d, e->q_d, e->srchi_d,
-                     e->srclo_d, e->src64_d, e->surfx_d, e->surfqd_d, e->vsurf_d, e->Mn_d, e->inv_np1_d, e->dpart_d,
-                     e->de_d, e->ctr_delta_d, e->status_d, s->sA);
+  hsma::launch_delta(e->sys_d, e->ditems_d, ni, e->dreqit_d, e->dreq_d, nr, e->xyz_d, e->q_d, e->perm_d, e->iperm_d,
+                     e->srchi_d, e->srclo_d, e->src64_d, e->surfx_d, e->surfqd_d, e->vsurf_d, e->Mn_d, e->inv_np1_d,
+                     e->dpart_d, e->de_d, e->ctr_delta_d, e->status_d, s->sA);
   SCK(cudaGetLastError());
   SCK(cudaMemcpyAsync(s->de_h, e->de_d, 8 * nr, cudaMemcpyDeviceToHost, s->sA));
   if (nacc > 0) {
     SCK(cudaMemcpyAsync(s->mreq_d, s->mreq_h, sizeof(DeltaReq) * nacc, cudaMemcpyHostToDevice, s->sA));
     SCK(cudaMemcpyAsync(s->mitems_d, s->mitems_h, sizeof(int2) * nmi, cudaMemcpyHostToDevice, s->sA));
     hsma::launch_move(e->sys_d, s->mitems_d, nmi, s->mreq_d, nacc, e->tables(), e->L.maxP, e->xyz_d, e->q_d,
-                      e->Mn_d, e->coef_d, e->r0_d, e->surfx_d, e->surfqd_d, e->vsurf_d, 1, e->surfa_d, e->surfb_d,
-                      e->surf64a_d, e->surf64b_d, e->srchi_d, e->srclo_d, e->src64_d, s->sA);
+                      e->Mn_d, e->coef_d, e->coef2_d, e->r0_d, e->surfx_d, e->surfqd_d, e->vsurf_d, 1, e->surfa_d,
+                      e->surfb_d, e->surf64a_d, e->surf64b_d, e->iperm_d, e->srchi_d, e->srclo_d, e->src64_d,
+                      e->boxes_d, s->sA);
     SCK(cudaGetLastError());
     e->launches += nmi > 0 ? 2 : 1;
     // committed state on the host
@@ -314,12 +315,12 @@ static int launch_energy(hsma_server_t* s, EnergySlot& sl, int chain)
                              e->surf64b_d, e->part64_d, sl.st);
     else
       hsma::launch_pairs_f32(e->L.cfg, grid, e->sys_d, sl.items_d, (int)it4.size(), sl.ctr_d, e->srchi_d, e->srclo_d,
-                             e->surfa_d, e->surfb_d, e->part_d, sl.st);
+                             e->surfa_d, e->surfb_d, e->boxes_d, e->part_d, sl.st);
     e->launches += 1;
   }
   if (!it5.empty()) {
     hsma::launch_reduce(e->sys_d, sl.sel_d, sl.selrng_d, 1, sl.it5_d, (int)it5.size(), e->part_d, e->part64_d, e->prec,
-                        e->q_d, e->r0_d, e->phic_d, e->phir_d, e->phit_d, sl.epart_d, e->energy_d, sl.ctr_d + 1,
+                        e->q_d, e->perm_d, e->r0_d, e->phic_d, e->phir_d, e->phit_d, sl.epart_d, e->energy_d, sl.ctr_d + 1,
                         e->status_d, sl.st);
     e->launches += 1;
   }

@@ -201,4 +201,6 @@ def test_kernel_launch_accounting():
     h = api.hsma_create(s.a, s.eps1, s.eps2, s.kappa, prm)
     api.hsma_build_sources(h, s.xyz, s.q)
     api.hsma_energy(h)
-    assert api.hsma_kernel_launches(h) == 6
+    # once per layout: k_setup, k_surface_basis; build: k_order_cells, _scan, _scatter, _sort,
+    # k_images, k_moments, k_coef_reduce, k_surface_mat; potentials: k_pairs, k_reduce
+    assert api.hsma_kernel_launches(h) == 12
