@@ -78,6 +78,9 @@ def _load():
             lib.oracle_eval.restype = ctypes.c_int
             lib.oracle_eval.argtypes = [pp, ctypes.c_int64, dp, dp, dp, dp, ctypes.c_int64, dp, dp, dp, dp,
                                         ctypes.c_double, ctypes.c_int64, dp, i64p, dp, dp]
+            lib.oracle_field.restype = ctypes.c_int
+            lib.oracle_field.argtypes = [pp, ctypes.c_int64, dp, dp, dp, dp, ctypes.c_int64, dp, dp, dp, dp,
+                                         ctypes.c_int64, dp, i64p, dp, dp]
             lib.oracle_energy.restype = ctypes.c_int
             lib.oracle_energy.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp]
             lib.oracle_hsma.restype = ctypes.c_int
@@ -102,7 +105,7 @@ class using_library:
         self.saved = _lib
         lib = ctypes.CDLL(self.path)
         for name in ("oracle_Sn", "oracle_Mn", "oracle_decomposition", "oracle_fibonacci", "oracle_build",
-                     "oracle_eval", "oracle_energy", "oracle_hsma", "oracle_threads"):
+                     "oracle_eval", "oracle_field", "oracle_energy", "oracle_hsma", "oracle_threads"):
             f, g = getattr(lib, name), getattr(self.saved, name)
             f.restype, f.argtypes = g.restype, g.argtypes
         _lib = lib
@@ -238,6 +241,44 @@ def evaluate(P: OracleParams, xyz, q, src, targets, self_index=None, parts=("cou
         nt, _dptr(targets), si.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if si is not None else None,
         _dptr(pc), _dptr(pr))
     return pc, pr
+
+
+def field_at(P: OracleParams, xyz, q, src, targets, self_index=None, parts=("coul", "kelvin", "surface")):
+    """Coulomb and reaction fields E = -grad phi at target points from a source set (the
+    gradient of every term of `evaluate`, sources fixed).  Returns two (nt, 3) arrays."""
+    xyz = _f64(xyz, (-1, 3)) if xyz is not None else None
+    q = _f64(q) if q is not None else None
+    targets = _f64(targets, (-1, 3))
+    nt = len(targets)
+    n = len(q) if q is not None else 0
+    ec = np.zeros((nt, 3))
+    er = np.zeros((nt, 3))
+    si = None
+    if self_index is not None:
+        si = np.ascontiguousarray(np.asarray(self_index, dtype=np.int64))
+    use_c = "coul" in parts
+    use_k = "kelvin" in parts
+    use_s = "surface" in parts
+    M = len(src["surf_w"]) if (use_s and src is not None) else 0
+    _load().oracle_field(
+        ctypes.byref(P), n,
+        _dptr(xyz) if use_c else None, _dptr(q) if use_c else None,
+        _dptr(src["kel_xyz"]) if use_k else None, _dptr(src["kel_q"]) if use_k else None,
+        M,
+        _dptr(src["surf_xyz"]) if use_s else None, _dptr(src["surf_w"]) if use_s else None,
+        _dptr(src["surf_phi"]) if use_s else None, _dptr(src["surf_dphi"]) if use_s else None,
+        nt, _dptr(targets), si.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if si is not None else None,
+        _dptr(ec), _dptr(er))
+    return ec, er
+
+
+def field(P: OracleParams, xyz, q):
+    """Whole method, fields at the charges (own Coulomb term excluded): dict(E_coul, E_rf, E)."""
+    xyz = _f64(xyz, (-1, 3))
+    q = _f64(q)
+    src = build_sources(P, xyz, q)
+    ec, er = field_at(P, xyz, q, src, xyz, self_index=np.arange(len(q)))
+    return dict(E_coul=ec, E_rf=er, E=ec + er)
 
 
 def energy(q, phi_coul, phi_rf):

@@ -15,6 +15,8 @@
  *             truncated correction potential, Green's second identity with the
  *             central difference for dG/dnu, Fibonacci quadrature, discrete images
  *   Sec. 4.1  self energy E_self = Phi_RF(x_s, x_s)/2
+ *   fields    E = -grad phi of the same source set (the gradient of the
+ *             potential the paper defines, for forces F_i = q_i E(x_i))
  *
  * Readings of the paper that this file takes (the paper is silent or ambiguous):
  *   - Units: the paper's expansions use Phi = q/(4 pi eps1 r).  The prefactor
@@ -325,6 +327,93 @@ int oracle_eval(const oracle_params* P, int64_t n, const double* xyz, const doub
         }
         if (phi_coul) phi_coul[t] = pc;
         if (phi_rf) phi_rf[t] = pr;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fields E = -grad phi at nt target points: the gradient, with every source held
+ * fixed, of each term of oracle_eval.  A point source Q at s contributes
+ *   Q (t - s) / |t - s|^3
+ * (real charges except self(t), Kelvin images, monopole layer).  The dipole shells,
+ * strength w Phi/(4 pi dy) at y^- and minus that at y^+, contribute
+ *   dipole_form 0:  strength [ (t - y^-)/d_-^3 - (t - y^+)/d_+^3 ];
+ *   dipole_form 1:  the same difference without cancellation.  With
+ *     (t - y^-) - (t - y^+) = dy yhat  and  d_+^2 - d_-^2 = 2 dy (R_tau - t.yhat),
+ *     d_+^3 - d_-^3 = (d_+ - d_-)(d_+^2 + d_+ d_- + d_-^2),
+ *   it is (w Phi/(4 pi)) [ yhat/d_-^3
+ *          + (t - y^+) 2 (R_tau - t.yhat)(d_+^2 + d_+ d_- + d_-^2) / ((d_+ + d_-) d_-^3 d_+^3) ].
+ * The centre constant r0_const has no field.  Outputs are nt x 3, row-major.   */
+int oracle_field(const oracle_params* P, int64_t n, const double* xyz, const double* q,
+                 const double* kel_xyz, const double* kel_q,
+                 int64_t M, const double* surf_xyz, const double* surf_w,
+                 const double* surf_phi, const double* surf_dphi,
+                 int64_t nt, const double* txyz, const int64_t* self_index,
+                 double* E_coul, double* E_rf)
+{
+    const double kc = P->coulomb_k / P->eps1;
+    const double Rtau = (1.0 + P->tau) * P->a;
+    const double dy = P->dy_rel * Rtau;
+    const double inv4pi = 1.0 / (4.0 * ORACLE_PI);
+#ifdef _OPENMP
+    if (P->nthreads > 0) omp_set_num_threads(P->nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t t = 0; t < nt; ++t) {
+        const double* x = txyz + 3 * t;
+        int64_t self = self_index ? self_index[t] : -1;
+        double ec[3] = {0.0, 0.0, 0.0}, er[3] = {0.0, 0.0, 0.0};
+        if (xyz && q) {
+            for (int64_t j = 0; j < n; ++j) {
+                if (self == j) continue;
+                double u[3] = {x[0] - xyz[3 * j], x[1] - xyz[3 * j + 1], x[2] - xyz[3 * j + 2]};
+                double d = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                double c = kc * q[j] / (d * d * d);
+                for (int k = 0; k < 3; ++k) ec[k] += c * u[k];
+            }
+        }
+        if (kel_xyz && kel_q) {
+            for (int64_t j = 0; j < n; ++j) {
+                if (kel_q[j] == 0.0) continue; /* centre charge: constant potential, no field */
+                double u[3] = {x[0] - kel_xyz[3 * j], x[1] - kel_xyz[3 * j + 1], x[2] - kel_xyz[3 * j + 2]};
+                double d = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                double c = kc * kel_q[j] / (d * d * d);
+                for (int k = 0; k < 3; ++k) er[k] += c * u[k];
+            }
+        }
+        if (surf_xyz) {
+            for (int64_t l = 0; l < M; ++l) {
+                const double* y = surf_xyz + 3 * l;
+                double rho = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+                double yh[3] = {y[0] / rho, y[1] / rho, y[2] / rho};
+                /* monopole layer at R_tau yhat */
+                double u[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+                double d = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                double c = surf_w[l] * surf_dphi[l] * inv4pi / (d * d * d);
+                for (int k = 0; k < 3; ++k) er[k] += c * u[k];
+                /* dipole layer from the central difference */
+                double rm = Rtau - 0.5 * dy, rp = Rtau + 0.5 * dy;
+                double um[3] = {x[0] - rm * yh[0], x[1] - rm * yh[1], x[2] - rm * yh[2]};
+                double up[3] = {x[0] - rp * yh[0], x[1] - rp * yh[1], x[2] - rp * yh[2]};
+                double dm = sqrt(um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+                double dp = sqrt(up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
+                if (P->dipole_form == 0) {
+                    double strength = surf_w[l] * surf_phi[l] * inv4pi / dy;
+                    for (int k = 0; k < 3; ++k)
+                        er[k] += strength * (um[k] / (dm * dm * dm) - up[k] / (dp * dp * dp));
+                } else {
+                    double D = surf_w[l] * surf_phi[l] * inv4pi;
+                    double xy = x[0] * yh[0] + x[1] * yh[1] + x[2] * yh[2];
+                    double dm3 = dm * dm * dm, dp3 = dp * dp * dp;
+                    double f = 2.0 * (Rtau - xy) * (dp * dp + dp * dm + dm * dm) / ((dp + dm) * dm3 * dp3);
+                    for (int k = 0; k < 3; ++k) er[k] += D * (yh[k] / dm3 + up[k] * f);
+                }
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            if (E_coul) E_coul[3 * t + k] = ec[k];
+            if (E_rf) E_rf[3 * t + k] = er[k];
+        }
     }
     return 0;
 }

@@ -13,6 +13,7 @@ import oracle
 from paper_1907_01724_gb300 import inputs
 
 from test_oracle_pins import K4PI, kirkwood_rf, _mn_ratio_recurrence  # noqa: E402
+from test_oracle_field_pins import fd_field_system, fd_gradient  # noqa: E402
 
 MUTANTS = {
     "dbar_sign": ("*dbar = g * (1.0 - s) - mu / (1.0 + eps);", "*dbar = g * (1.0 - s) + mu / (1.0 + eps);"),
@@ -34,6 +35,16 @@ MUTANTS = {
     "truncation_off_by_one": ("for (int k = 0; k <= p; ++k) {\n                    double Mhat",
                               "for (int k = 0; k < p; ++k) {\n                    double Mhat"),
     "tau_radius": ("const double Rtau = (1.0 + P->tau) * a;\n    const int p", "const double Rtau = (1.0 + P->tau);\n    const int p"),
+    # fields
+    "field_kelvin_sign": ("double c = kc * kel_q[j] / (d * d * d);", "double c = -kc * kel_q[j] / (d * d * d);"),
+    "field_coul_index": ("double u[3] = {x[0] - xyz[3 * j], x[1] - xyz[3 * j + 1], x[2] - xyz[3 * j + 2]};",
+                         "double u[3] = {x[0] - xyz[3 * j], x[1] - xyz[3 * j + 2], x[2] - xyz[3 * j + 1]};"),
+    "field_monopole_power": ("double c = surf_w[l] * surf_dphi[l] * inv4pi / (d * d * d);",
+                             "double c = surf_w[l] * surf_dphi[l] * inv4pi / (d * d);"),
+    "field_dipole_literal_sign": ("er[k] += strength * (um[k] / (dm * dm * dm) - up[k] / (dp * dp * dp));",
+                                  "er[k] += strength * (up[k] / (dp * dp * dp) - um[k] / (dm * dm * dm));"),
+    "field_dipole_fused_shell": ("er[k] += D * (yh[k] / dm3 + up[k] * f);", "er[k] += D * (yh[k] / dp3 + up[k] * f);"),
+    "field_dipole_fused_factor": ("double f = 2.0 * (Rtau - xy)", "double f = (Rtau - xy)"),
 }
 
 
@@ -89,6 +100,32 @@ def _checks():
     if not (abs(w.sum() - 4 * math.pi * 1.21) < 1e-12 and
             abs((w * (pts[:, 2] / 1.1) ** 2).sum() - 4 * math.pi * 1.21 / 3) < 1e-6):
         failed.append("fibonacci")
+    # fields: minus the numerical gradient of the (pinned) potential, both dipole forms, with
+    # charges next to the interface; and the Kirkwood reaction field of a pair
+    rng = np.random.default_rng(11)
+    xyz, q = fd_field_system(rng, n=6, near=2)
+    for form in (0, 1):
+        P = oracle.make_params(a=1.0, eps1=1.0, eps2=80.0, kappa=2.0, p=12, M=400, dipole_form=form)
+        src = oracle.build_sources(P, xyz, q)
+        ec, er = oracle.field_at(P, xyz, q, src, xyz, self_index=np.arange(len(q)))
+        ok = True
+        for i in range(len(q)):
+            def phi(x):
+                pc, pr = oracle.evaluate(P, xyz, q, src, x[None, :], self_index=[i])
+                return pc[0] + pr[0]
+            ref = -fd_gradient(phi, xyz[i], 1e-4)
+            ok = ok and np.linalg.norm(ec[i] + er[i] - ref) <= 1e-7 * np.linalg.norm(ref)
+        if not ok:
+            failed.append(f"field_fd_form{form}")
+    a, eps1, eps2, kappa = 1.2, 1.0, 78.5, 1.5
+    P = oracle.make_params(a=a, eps1=eps1, eps2=eps2, kappa=kappa, p=24, M=1600, tau=0.1)
+    xyz = inputs.uniform_ball(np.random.default_rng(7), 2, 0.6 * a)
+    q = np.array([1.0, -1.0])
+    E = oracle.field(P, xyz, q)["E_rf"]
+    ref = -fd_gradient(lambda x: sum(q[j] * kirkwood_rf(x, xyz[j], a, eps1, eps2, kappa) for j in range(2)),
+                       xyz[0], 1e-4)
+    if not np.linalg.norm(E[0] - ref) <= 1e-9 * np.linalg.norm(ref):
+        failed.append("kirkwood_field")
     return failed
 
 
