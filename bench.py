@@ -244,6 +244,53 @@ def run_batched(local, stream, gpu_name):
                                    "sample": "16 seeded systems, one FP64 handle each, host inputs"}}
 
 
+def run_field(local, stream, systems, gpu_name):
+    """Fields and potentials in one pass (hsma_batch_field) on the headline workload: build +
+    field per step, the field pass's pair-evals/s, its kernel alone, and E against the oracle."""
+    import torch
+
+    from paper_1907_01724_gb300 import api, batch
+    n, xyz, q = batch.concat(systems)
+    b = batch.from_systems(systems, precision=api.HSMA_FP32, device=local, stream=stream)
+    cfg = batch.autotuned(b, n, xyz, q, gpu=gpu_name, reps=3)
+    xyz_d = torch.tensor(xyz, device=f"cuda:{local}")
+    q_d = torch.tensor(q, device=f"cuda:{local}")
+    E_d = torch.empty((int(n.sum()), 3), dtype=torch.float64, device=f"cuda:{local}")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    for _ in range(5):
+        b.hsma_batch_build_sources(n, xyz_d, q_d)
+        b.hsma_batch_field(api.HSMA_TOTAL, out=E_d)
+    torch.cuda.synchronize()
+    k = 500
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    kern = []
+    for i in range(k):
+        flush.zero_()
+        ev[i][0].record(stream)
+        b.hsma_batch_build_sources(n, xyz_d, q_d)
+        b.hsma_batch_field(api.HSMA_TOTAL, out=E_d)
+        ev[i][1].record(stream)
+        if i % 10 == 0:
+            kern.append(b.hsma_batch_last_pair_time())
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(c) for a, c in ev) / 1e3
+    E = E_d.cpu().numpy()
+    import oracle
+    worst, off = 0.0, 0
+    for s in systems:
+        P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+        ref = oracle.field(P, s.xyz, s.q)["E"]
+        worst = max(worst, float(np.linalg.norm(E[off:off + s.n] - ref) / np.linalg.norm(ref)))
+        off += s.n
+    tk = statistics.mean(kern) / 1e3
+    ev_per_launch = sum(evals(s) for s in systems)
+    return {"workload": "the headline workload, fields and potentials in one pass (build + field per step)",
+            "pair_evals_per_s": sum(pairs(s) for s in systems) * k / t, "ms_per_step": t / k * 1e3, "steps": k,
+            "field_kernel_ms": tk * 1e3, "field_kernel_evals_per_s": ev_per_launch / tk,
+            "pair_config": batch.pair_configs()[cfg], "E_rel_l2_max_vs_oracle": worst,
+            "l2": "flushed before every timed step (256 MB write)"}
+
+
 def run_serving(local):
     """64 Monte Carlo chains (N log-uniform in [500, 5e4]), 90% move / 10% full-energy requests.
     Saturation = all requests released at once; then Poisson arrivals at 0.25/0.5/0.8/0.95 of it."""
@@ -430,8 +477,9 @@ def run_ours(args):
            "d2h_bytes_per_step": int(8 * n.sum() + 16 * len(systems)), "steps": ke,
            "ms_per_step": te / ke * 1e3}
 
-    batched = serving = None
+    batched = serving = fieldres = None
     if rank == 0 and world == 1 and not args.no_extras:
+        fieldres = run_field(local, stream, systems, gpu_name)
         batched = run_batched(local, stream, gpu_name)
         serving = run_serving(local)
 
@@ -442,7 +490,7 @@ def run_ours(args):
                 "data": "synthetic (seeded random charges in the ball, 25% near the interface)",
                 "config": config_dict(systems, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches), "accuracy_vs_oracle": acc, "fp64_path": fp64,
-                "batched": batched, "serving": serving, "impl": "ours"}
+                "field": fieldres, "batched": batched, "serving": serving, "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -489,7 +537,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sections")
-    ap.add_argument("--only", choices=["batched", "serving"], help="run one extra section alone (profiling)")
+    ap.add_argument("--only", choices=["batched", "serving", "field"], help="run one extra section alone (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.only:
@@ -497,7 +545,12 @@ def main():
         torch.cuda.set_device(0)
         st = torch.cuda.Stream()
         torch.cuda.set_stream(st)
-        out = run_batched(0, st, torch.cuda.get_device_name(0)) if args.only == "batched" else run_serving(0)
+        if args.only == "batched":
+            out = run_batched(0, st, torch.cuda.get_device_name(0))
+        elif args.only == "field":
+            out = run_field(0, st, workload(0), torch.cuda.get_device_name(0))
+        else:
+            out = run_serving(0)
         print(json.dumps(out), flush=True)
     elif args.impl == "reference":
         run_reference(args)

@@ -120,6 +120,19 @@ HSMA_API int hsma_potential(hsma_t* h, double* phi, int what);
 /* Same, writing n doubles to device memory (stream-ordered; no host synchronisation). */
 HSMA_API int hsma_potential_device(hsma_t* h, double* phi_dev, int what);
 
+/* Fields E = -grad phi at the n charges: the gradient, with every source held fixed, of each
+ * term of the potential above (real charges other than the charge itself, Kelvin images, the
+ * monopole and dipole layers of Sec. 2.4), so that the force on charge i is q_i E_i.
+ * what = HSMA_TOTAL, HSMA_REACTION or HSMA_COULOMB.  E: host array of n x 3 doubles (row-major,
+ * caller-owned).  The same pass refreshes the potentials and energies, so hsma_potential and
+ * hsma_energy then return without another pair sum.  The first call allocates the pass's
+ * buffers (32 bytes per pair partial, 72 bytes per charge; HSMA_E_OOM if that fails).
+ * Synchronises the handle's stream; HSMA_E_NONFINITE for coincident charges. */
+HSMA_API int hsma_field(hsma_t* h, double* E, int what);
+
+/* Same, writing n x 3 doubles to device memory (stream-ordered; no host synchronisation). */
+HSMA_API int hsma_field_device(hsma_t* h, double* E_dev, int what);
+
 /* Energies (Sec. 4.1 generalised to N charges): E_total = 1/2 sum_i q_i [Phi_Coul(x_i) +
  * Phi_RF(x_i)], E_reaction = 1/2 sum_i q_i Phi_RF(x_i) (either pointer may be NULL).
  * Host doubles; synchronises the handle's stream. */
@@ -144,8 +157,9 @@ HSMA_API int hsma_coefficients(hsma_t* h, double* out, int64_t len);
 /* Number of the library's kernel launches issued so far by this handle (for accounting). */
 HSMA_API int64_t hsma_kernel_launches(const hsma_t* h);
 
-/* Device time in milliseconds of the most recent pair-sum kernel launch of the handle (CUDA
- * events recorded on the handle's stream just before and after that launch).  Synchronises
+/* Device time in milliseconds of the most recent pair-sum kernel launch of the handle (the
+ * potential pass's or, after hsma_field, the field pass's; CUDA events recorded on the
+ * handle's stream just before and after that launch).  Synchronises
  * the stream.  HSMA_E_STATE if no pair sum has run yet. */
 HSMA_API int hsma_last_pair_time(hsma_t* h, float* ms);
 
@@ -189,6 +203,10 @@ HSMA_API int hsma_batch_build_sources_device(hsma_batch_t* b, const int64_t* n, 
 /* Potentials of all charges (sum n doubles, concatenated), host or device output. */
 HSMA_API int hsma_batch_potential(hsma_batch_t* b, double* phi, int what);
 HSMA_API int hsma_batch_potential_device(hsma_batch_t* b, double* phi_dev, int what);
+
+/* Fields of all charges (sum n x 3 doubles, concatenated; see hsma_field), host or device. */
+HSMA_API int hsma_batch_field(hsma_batch_t* b, double* E, int what);
+HSMA_API int hsma_batch_field_device(hsma_batch_t* b, double* E_dev, int what);
 
 /* Energies of every system: e_total[nsys], e_reaction[nsys] (host; either may be NULL). */
 HSMA_API int hsma_batch_energy(hsma_batch_t* b, double* e_total, double* e_reaction);

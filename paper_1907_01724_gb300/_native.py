@@ -19,7 +19,7 @@ CSRC = os.path.join(_HERE, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_HERE, "_build")
 LIB = os.path.join(BUILD, "libhsma.so")
-SOURCES = ["k_order.cu", "k_sources.cu", "k_pairs.cu", "k_delta.cu", "engine.cu", "batch.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["k_order.cu", "k_sources.cu", "k_pairs.cu", "k_field.cu", "k_delta.cu", "engine.cu", "batch.cu", "server.cu", "noalloc.cu"]
 HEADERS = ["hsma_internal.cuh", "engine.h", "df64.cuh", "k_pairs_f32.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
@@ -117,6 +117,8 @@ def _declare(lib):
         "hsma_build_sources_device": (ctypes.c_int, [vp, i64, vp, vp]),
         "hsma_potential": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "hsma_potential_device": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "hsma_field": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "hsma_field_device": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "hsma_energy": (ctypes.c_int, [vp, dp, dp]),
         "hsma_delta_energy": (ctypes.c_int, [vp, i64, vp, dp]),
         "hsma_apply_move": (ctypes.c_int, [vp, i64, vp]),
@@ -133,6 +135,8 @@ def _declare(lib):
         "hsma_batch_build_sources_device": (ctypes.c_int, [vp, vp, vp, vp]),
         "hsma_batch_potential": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "hsma_batch_potential_device": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "hsma_batch_field": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "hsma_batch_field_device": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "hsma_batch_energy": (ctypes.c_int, [vp, vp, vp]),
         "hsma_batch_delta_energy": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp]),
         "hsma_batch_apply_moves": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp]),

@@ -169,6 +169,17 @@ def hsma_potential(h: Handle, what: int = HSMA_TOTAL, out=None):
     return phi
 
 
+def hsma_field(h: Handle, what: int = HSMA_TOTAL, out=None):
+    """Fields E = -grad phi at the charges, (n, 3): numpy array, or into a torch CUDA tensor given as out."""
+    lib = _native.load()
+    if out is not None and _is_torch_cuda(out):
+        _check(lib.hsma_field_device(h.ptr, ctypes.c_void_p(out.data_ptr()), int(what)), h.ptr)
+        return out
+    E = np.empty((max(h.n, 0), 3), dtype=np.float64)
+    _check(lib.hsma_field(h.ptr, _dptr(E), int(what)), h.ptr)
+    return E
+
+
 def hsma_energy(h: Handle) -> tuple[float, float]:
     et, er = ctypes.c_double(), ctypes.c_double()
     _check(_native.load().hsma_energy(h.ptr, ctypes.byref(et), ctypes.byref(er)), h.ptr)

@@ -118,6 +118,14 @@ class Batch:
         self._check(self.lib.hsma_batch_potential(self.ptr, _p(phi), int(what)))
         return phi
 
+    def hsma_batch_field(self, what: int = HSMA_TOTAL, out=None):
+        if out is not None and _is_torch_cuda(out):
+            self._check(self.lib.hsma_batch_field_device(self.ptr, ctypes.c_void_p(out.data_ptr()), int(what)))
+            return out
+        E = np.empty((int(self.n.sum()), 3), dtype=np.float64)
+        self._check(self.lib.hsma_batch_field(self.ptr, _p(E), int(what)))
+        return E
+
     def hsma_batch_energy(self):
         et = np.empty(self.nsys)
         er = np.empty(self.nsys)

@@ -256,6 +256,29 @@ static int batch_pot(hsma_batch_t* b, double* phi, int what, bool dev)
   return bfrom(b, b->e->check_status());
 }
 
+static int batch_field(hsma_batch_t* b, double* E, int what, bool dev)
+{
+  if (!b) return HSMA_E_INVALID_ARG;
+  if (b->n.empty()) return berr(b, HSMA_E_STATE, "sources have not been built");
+  if (what != HSMA_TOTAL && what != HSMA_REACTION && what != HSMA_COULOMB) return berr(b, HSMA_E_INVALID_ARG, "bad 'what'");
+  int64_t tot = 0;
+  for (auto v : b->n) tot += v;
+  if (tot > 0 && !E) return berr(b, HSMA_E_INVALID_ARG, "NULL E");
+  int rc = b->e->field();
+  if (rc) return bfrom(b, rc);
+  const double* src = what == HSMA_TOTAL ? b->e->Et_d : (what == HSMA_REACTION ? b->e->Er_d : b->e->Ec_d);
+  if (tot > 0) {
+    cudaError_t e = cudaMemcpyAsync(E, src, 24 * tot, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    b->e->stream);
+    if (e != cudaSuccess) return bfrom(b, b->e->cuda_fail(e, "copy E"));
+  }
+  if (dev) return HSMA_OK;
+  return bfrom(b, b->e->check_status());
+}
+
+int hsma_batch_field(hsma_batch_t* b, double* E, int what) { return batch_field(b, E, what, false); }
+int hsma_batch_field_device(hsma_batch_t* b, double* E_dev, int what) { return batch_field(b, E_dev, what, true); }
+
 int hsma_batch_potential(hsma_batch_t* b, double* phi, int what) { return batch_pot(b, phi, what, false); }
 int hsma_batch_potential_device(hsma_batch_t* b, double* phi_dev, int what)
 {

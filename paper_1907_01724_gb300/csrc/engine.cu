@@ -74,6 +74,9 @@ int Engine::init(int dev, void* user_stream, int precision)
   occ_f32.assign(pair_config_count(), 0);
   for (int c = 0; c < pair_config_count(); ++c) occ_f32[c] = pairs_f32_occupancy(c);
   occ_f64 = pairs_f64_occupancy();
+  occ_field.assign(pair_config_count(), 0);
+  for (int c = 0; c < pair_config_count(); ++c) occ_field[c] = field_f32_occupancy(c);
+  occ_field64 = field_f64_occupancy();
   CK(cudaEventCreate(&ev_pair0));
   CK(cudaEventCreate(&ev_pair1));
   CK(cudaEventCreate(&ev_pot1));
@@ -121,6 +124,8 @@ Engine::~Engine()
   if (device >= 0) cudaSetDevice(device);
   drop_graphs();
   if (ws_owned && ws) cudaFree(ws);
+  if (fpart_d) cudaFree(fpart_d);
+  if (E_d) cudaFree(E_d);
   if (ev_pair0) cudaEventDestroy(ev_pair0);
   if (ev_pair1) cudaEventDestroy(ev_pair1);
   if (ev_pot1) cudaEventDestroy(ev_pot1);
@@ -136,7 +141,8 @@ void Engine::drop_graphs()
 {
   if (g_build) cudaGraphExecDestroy(g_build);
   if (g_pot) cudaGraphExecDestroy(g_pot);
-  g_build = g_pot = nullptr;
+  if (g_field) cudaGraphExecDestroy(g_field);
+  g_build = g_pot = g_field = nullptr;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -190,7 +196,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
       const double share = (double)n / std::max<double>((double)totn_all, 1.0);
       const int64_t want_blocks = std::max<int64_t>(1, (int64_t)std::llround(2.0 * num_sms * share));
       int64_t tile = (n + want_blocks - 1) / want_blocks;
-      tile = std::max<int64_t>(G, (tile + G - 1) / G * G);
+      tile = std::max<int64_t>(G, tile / G * G);
       tile = std::min<int64_t>(tile, std::max(G, kMomTile / G * G));
       d.mom_tile = (int)tile;
     }
@@ -354,6 +360,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_epart = take(16 * L.it5.size());
   L.o_energy = take(16 * (size_t)nsys);
   L.o_ctr = take(16);
+  L.o_redctr = take(4 * (size_t)nsys);
   L.o_it12 = take(sizeof(int2) * L.it12.size());
   L.o_it2r = take(sizeof(int2) * L.it2r.size());
   L.o_it3 = take(sizeof(int2) * L.it3.size());
@@ -433,7 +440,7 @@ void Engine::carve()
   energy_d = (double*)(b + L.o_energy);
   unsigned int* ctr = (unsigned int*)(b + L.o_ctr);
   ctr_pairs_d = ctr;
-  ctr_red_d = ctr + 1;
+  ctr_red_d = (unsigned int*)(b + L.o_redctr);
   status_d = (int*)(ctr + 2);
   ctr_delta_d = ctr + 3;
   it12_d = (int2*)(b + L.o_it12);
@@ -504,6 +511,7 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
   CK(cudaMemcpyAsync(sel_d, L.sel.data(), sizeof(int) * L.sel.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(selrng_d, L.selrng.data(), sizeof(int2) * L.selrng.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemsetAsync(ctr_pairs_d, 0, 16, stream));
+  CK(cudaMemsetAsync(ctr_red_d, 0, 4 * L.sd.size(), stream));
   CK(cudaMemsetAsync(energy_d, 0, 16 * L.sd.size(), stream));
   // parameter-only quantities (scalars, M_n, tables, quadrature grid, surface basis), once per layout
   launch_setup(sys_d, (int)L.sd.size(), Mn_d, rec_a_d, rec_b_d, sect_d, inv_np1_d, rec_a2_d, rec_b2_d, sect2_d,
@@ -640,6 +648,92 @@ int Engine::potentials()
   leave();
   launches += pot_launch_count();
   pot_ready = true;
+  field_ready = false;
+  if (!L.it4.empty()) pair_timed = true;
+  return HSMA_OK;
+}
+
+int Engine::ensure_field_buffers()
+{
+  const size_t need_p = std::max<size_t>(32 * (size_t)L.totPart, 256);
+  const size_t need_e = std::max<size_t>(72 * (size_t)L.totN, 256);
+  if (need_p <= fpart_cap && need_e <= E_cap) {
+    Ec_d = E_d;
+    Er_d = E_d + 3 * L.totN;
+    Et_d = E_d + 6 * L.totN;
+    return HSMA_OK;
+  }
+  CK(cudaStreamSynchronize(stream));
+  if (g_field) cudaGraphExecDestroy(g_field);
+  g_field = nullptr;
+  if (need_p > fpart_cap) {
+    if (fpart_d) cudaFree(fpart_d);
+    fpart_d = nullptr;
+    fpart_cap = 0;
+    cudaError_t e = cudaMalloc(&fpart_d, need_p);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fpart_d = nullptr;
+      return fail(HSMA_E_OOM, "cudaMalloc(%zu) for the field partials failed", need_p);
+    }
+    fpart_cap = need_p;
+  }
+  if (need_e > E_cap) {
+    if (E_d) cudaFree(E_d);
+    E_d = nullptr;
+    E_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&E_d, need_e);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      E_d = nullptr;
+      return fail(HSMA_E_OOM, "cudaMalloc(%zu) for the fields failed", need_e);
+    }
+    E_cap = need_e;
+  }
+  Ec_d = E_d;
+  Er_d = E_d + 3 * L.totN;
+  Et_d = E_d + 6 * L.totN;
+  return HSMA_OK;
+}
+
+void Engine::issue_field()
+{
+  const int nsys = (int)L.sd.size();
+  cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), stream);
+  if (!L.it4.empty()) {
+    cudaEventRecordWithFlags(ev_pair0, stream, cudaEventRecordExternal);
+    if (prec == HSMA_FP64) {
+      const int grid =
+          (int)std::max<size_t>(1, std::min<size_t>(L.it4.size(), (size_t)num_sms * std::max(occ_field64, 1)));
+      launch_field_f64(grid, sys_d, it4_d, (int)L.it4.size(), ctr_pairs_d, src64_d, surf64a_d, surf64b_d,
+                       (dbl4*)fpart_d, stream);
+    } else {
+      const int grid =
+          (int)std::max<size_t>(1, std::min<size_t>(L.it4.size(), (size_t)num_sms * std::max(occ_field[L.cfg], 1)));
+      launch_field_f32(L.cfg, grid, sys_d, it4_d, (int)L.it4.size(), ctr_pairs_d, srchi_d, srclo_d, surfa_d, surfb_d,
+                       boxes_d, (float4*)fpart_d, stream);
+    }
+    cudaEventRecordWithFlags(ev_pair1, stream, cudaEventRecordExternal);
+  }
+  launch_reduce_field(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), (const float4*)fpart_d,
+                      (const dbl4*)fpart_d, prec, q_d, perm_d, r0_d, phic_d, phir_d, phit_d, Ec_d, Er_d, Et_d,
+                      epart_d, energy_d, ctr_red_d, status_d, stream);
+}
+
+int Engine::field()
+{
+  if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
+  if (pot_ready && field_ready) return HSMA_OK;
+  CK(cudaSetDevice(device));
+  int rc = ensure_field_buffers();
+  if (rc) return rc;
+  enter();
+  rc = run_graph(&g_field, &Engine::issue_field);
+  if (rc) return rc;
+  leave();
+  launches += pot_launch_count();
+  pot_ready = true;
+  field_ready = true;
   if (!L.it4.empty()) pair_timed = true;
   return HSMA_OK;
 }
@@ -922,6 +1016,35 @@ int hsma_potential_device(hsma_t* h, double* phi_dev, int what)
   }
   return HSMA_OK;
 }
+
+static const double* pick_field(Engine* e, int what)
+{
+  if (what == HSMA_TOTAL) return e->Et_d;
+  if (what == HSMA_REACTION) return e->Er_d;
+  if (what == HSMA_COULOMB) return e->Ec_d;
+  return nullptr;
+}
+
+static int field_out(hsma_t* h, double* E, int what, bool dev)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  if (h->n < 0) return set_err(h, HSMA_E_STATE, "sources have not been built");
+  if (h->n > 0 && !E) return set_err(h, HSMA_E_INVALID_ARG, "NULL E");
+  if (what != HSMA_TOTAL && what != HSMA_REACTION && what != HSMA_COULOMB)
+    return set_err(h, HSMA_E_INVALID_ARG, "bad 'what'");
+  int rc = h->e->field();
+  if (rc) return from_engine(h, rc);
+  if (h->n > 0) {
+    cudaError_t e = cudaMemcpyAsync(E, pick_field(h->e, what), 24 * h->n,
+                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->e->stream);
+    if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy E"));
+  }
+  if (dev) return HSMA_OK;
+  return from_engine(h, h->e->check_status());
+}
+
+int hsma_field(hsma_t* h, double* E, int what) { return field_out(h, E, what, false); }
+int hsma_field_device(hsma_t* h, double* E_dev, int what) { return field_out(h, E_dev, what, true); }
 
 int hsma_energy(hsma_t* h, double* e_total, double* e_reaction)
 {

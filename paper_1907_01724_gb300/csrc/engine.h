@@ -43,6 +43,7 @@ struct Layout {
   size_t o_dreq = 0, o_ditems = 0, o_dreqit = 0, o_mitems = 0, o_dpart = 0, o_de = 0;
   size_t o_sb = 0, o_coef2 = 0, o_itsb = 0;
   size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_offs = 0, o_cursor = 0, o_boxes = 0, o_itord = 0;
+  size_t o_redctr = 0;
   size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0;
   size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0;
   size_t bytes = 0;
@@ -57,6 +58,7 @@ class Engine {
   int attach(void* ptr, size_t bytes);
   int build(const double* xyz, const double* q, bool device_inputs);
   int potentials();
+  int field();                    // potentials and fields in one pass (lazily allocated buffers)
   int check_status();
   int delta_energy(int64_t k, const double* x_new, double* de);
   int apply_move(int64_t k, const double* x_new);
@@ -75,8 +77,8 @@ class Engine {
   bool use_graphs = true;
   int forced_cfg = -1;
   std::vector<std::pair<int, int>> tuned;  // (size bucket, pair config)
-  std::vector<int> occ_f32;
-  int occ_f64 = 1;
+  std::vector<int> occ_f32, occ_field;
+  int occ_f64 = 1, occ_field64 = 1;
   std::vector<SysSpec> spec;
 
   // layout and workspace
@@ -141,7 +143,15 @@ class Engine {
 
   // state
   bool sources_ready = false, pot_ready = false;
-  cudaGraphExec_t g_build = nullptr, g_pot = nullptr;
+  bool field_ready = false;       // E is current when pot_ready && field_ready
+  cudaGraphExec_t g_build = nullptr, g_pot = nullptr, g_field = nullptr;
+  // field pass buffers, outside the workspace (allocated on the first field request)
+  void* fpart_d = nullptr;        // 32 bytes per (chunk, target) slot
+  size_t fpart_cap = 0;
+  double* E_d = nullptr;          // E_coul, E_rf, E_total: 3 x (3 totN) doubles
+  size_t E_cap = 0;
+  double *Ec_d = nullptr, *Er_d = nullptr, *Et_d = nullptr;
+  int ensure_field_buffers();
   int64_t launches = 0;
   std::string err;
 
@@ -151,6 +161,7 @@ class Engine {
   void carve();
   void issue_build();
   void issue_pot();
+  void issue_field();
   int build_launch_count() const;
   int pot_launch_count() const;
   int run_graph(cudaGraphExec_t* g, void (Engine::*issue)());

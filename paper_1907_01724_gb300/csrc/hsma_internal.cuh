@@ -148,11 +148,29 @@ void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems
                       const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, double* part64,
                       cudaStream_t st);
 // Reduce the pair partials of the launched items to potentials and energies; the energies of
-// system sel[r] are summed from the launch items sel_rng[r] = (first, count).
+// system sel[r] are summed from the launch items sel_rng[r] = (first, count), ranges ascending
+// and contiguous; counter[r] (zero before the launch, zero after it) counts r's finished items.
 void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
                    const float2* part, const double* part64, int prec, const double* q, const int* perm,
                    const double* r0, double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy,
                    unsigned int* counter, int* status, cudaStream_t st);
+
+// ---- fields (k_field.cu): potential and E = -grad phi in one pass over the pair items ----
+int field_f32_occupancy(int cfg);
+int field_f64_occupancy();
+// FP32: two float4 per (chunk, target) slot, (hi, lo) of (phi, Ex, Ey, Ez); FP64: one dbl4
+void launch_field_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
+                      const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
+                      const float4* boxes, float4* fpart, cudaStream_t st);
+void launch_field_f64(int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
+                      const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, dbl4* fpart64,
+                      cudaStream_t st);
+// as launch_reduce, plus the Coulomb, reaction and total fields (3 doubles per charge, input order)
+void launch_reduce_field(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items,
+                         int nitems, const float4* fpart, const dbl4* fpart64, int prec, const double* q,
+                         const int* perm, const double* r0, double* phi_c, double* phi_r, double* phi_t,
+                         double* E_c, double* E_r, double* E_t, double* epart, double* energy, unsigned int* counter,
+                         int* status, cudaStream_t st);
 
 // ---- single-charge moves (k_delta.cu) ----
 // One request: move charge k of system sys to (x, y, z).

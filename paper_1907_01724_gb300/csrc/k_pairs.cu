@@ -214,8 +214,8 @@ void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems
 // ---------------------------------------------------------------------------------------
 // phi_coul = sum of real-chunk partials, phi_rf = Kelvin + surface partials + centre constant,
 // energies E_total = 1/2 sum q (phi_coul + phi_rf), E_RF = 1/2 sum q phi_rf.  Fixed-order
-// block reductions; the last block to finish sums the block partials of every system in
-// order (so the result does not depend on which block ends last).
+// block reductions; the last block of a system to finish (counter[r] per launch-local system
+// r, reset by that block) sums the system's block partials in a fixed order.
 constexpr int kRedLanes = 8;
 constexpr int kRedThreads = kReduceTargetsPerBlock * kRedLanes;
 static_assert(kRedThreads == 256, "reduce block size");
@@ -234,6 +234,7 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
 {
   __shared__ double red[2][kRedThreads / 32];
   __shared__ bool last;
+  __shared__ int s_r;
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int n = S.n;
@@ -308,25 +309,52 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     epart[2 * blockIdx.x] = a;
     epart[2 * blockIdx.x + 1] = b;
     __threadfence();
-    const unsigned prev = atomicAdd(counter, 1u);
-    last = (prev == gridDim.x - 1);
+    // launch-local system r of this block (sel_rng ascending: the last r whose range starts at
+    // or before this block), and whether this block is the last of r's blocks to finish
+    int lo = 0, hi = nsel - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sel_rng[mid].x <= (int)blockIdx.x)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    s_r = lo;
+    const unsigned prev = atomicAdd(&counter[lo], 1u);
+    last = (prev == (unsigned)sel_rng[lo].y - 1u);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // energies of the launched systems: sel[r] owns launch items sel_rng[r] = (first, count)
-  for (int r = threadIdx.x; r < nsel; r += kRedThreads) {
-    const int s = sel[r];
-    const int2 rg = sel_rng[r];
-    double a = 0.0, b = 0.0;
-    for (int k = 0; k < rg.y; ++k) {
-      a += ((volatile double*)epart)[2 * (rg.x + k)];
-      b += ((volatile double*)epart)[2 * (rg.x + k) + 1];
-    }
-    energy[2 * s] = a;
-    energy[2 * s + 1] = b;
+  // energies of system sel[r]: its blocks' partials in a fixed order (strided lanes, xor tree,
+  // warps in order), so the result does not depend on which block finishes last
+  const int r = s_r;
+  const int2 rg = sel_rng[r];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < rg.y; k += kRedThreads) {
+    a += __ldcg(&epart[2 * (rg.x + k)]);
+    b += __ldcg(&epart[2 * (rg.x + k) + 1]);
   }
-  if (threadIdx.x == 0) *counter = 0u;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    red[0][warp] = a;
+    red[1][warp] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double A = 0.0, B = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) {
+      A += red[0][w];
+      B += red[1][w];
+    }
+    energy[2 * sel[r]] = A;
+    energy[2 * sel[r] + 1] = B;
+    counter[r] = 0u;
+  }
 }
 
 void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,

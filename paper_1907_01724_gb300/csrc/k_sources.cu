@@ -513,11 +513,27 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
   const double* base = mom + (size_t)S.mom * mom_stride;
   R U = Num<R>::zero(), V = Num<R>::zero();
   double Rs = 0.0;
-  if (idx < P)
-    for (int b = warp; b < S.mom_blocks; b += kCoefWarps) {
+  if (idx < P) {
+    // two interleaved accumulators per moment, loads issued a step ahead
+    R U1 = Num<R>::zero(), V1 = Num<R>::zero();
+    int b = warp;
+    for (; b + kCoefWarps < S.mom_blocks; b += 2 * kCoefWarps) {
+      const R u0 = Num<R>::ld(base, (long long)b * mom_stride + idx);
+      const R v0 = Num<R>::ld(base, (long long)b * mom_stride + P + idx);
+      const R u1 = Num<R>::ld(base, (long long)(b + kCoefWarps) * mom_stride + idx);
+      const R v1 = Num<R>::ld(base, (long long)(b + kCoefWarps) * mom_stride + P + idx);
+      U = U + u0;
+      V = V + v0;
+      U1 = U1 + u1;
+      V1 = V1 + v1;
+    }
+    if (b < S.mom_blocks) {
       U = U + Num<R>::ld(base, (long long)b * mom_stride + idx);
       V = V + Num<R>::ld(base, (long long)b * mom_stride + P + idx);
     }
+    U = U + U1;
+    V = V + V1;
+  }
   if (it.y == 0 && lane == 0)
     for (int b = warp; b < S.mom_blocks; b += kCoefWarps) Rs += base[(size_t)b * mom_stride + 2 * P];
   su[warp][lane] = U;

@@ -106,3 +106,24 @@ def test_field_is_linear_in_the_charges():
     E2 = oracle.field(P, xyz, q2)["E"]
     E12 = oracle.field(P, xyz, 2.0 * q1 - 0.5 * q2)["E"]
     assert np.linalg.norm(E12 - (2.0 * E1 - 0.5 * E2)) <= 1e-12 * np.linalg.norm(E12)
+
+
+def test_force_is_minus_energy_gradient_within_the_method():
+    """q_k E(x_k) against -dE_total/dx_k by central differences of the whole method: they agree
+    to the method's own accuracy (its discrete Green's function is symmetric only to truncation
+    and quadrature, and the sources move with the charge), ~1e-4 here."""
+    s = inputs.small_system()
+    P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+    E = oracle.field(P, s.xyz, s.q)["E"]
+    rng = np.random.default_rng(0)
+    h = 1e-5
+    for k in rng.choice(len(s.q), 3, replace=False):
+        g = np.zeros(3)
+        for d in range(3):
+            xp = s.xyz.copy()
+            xp[k, d] += h
+            xm = s.xyz.copy()
+            xm[k, d] -= h
+            g[d] = -(oracle.hsma(P, xp, s.q)["E_total"] - oracle.hsma(P, xm, s.q)["E_total"]) / (2 * h)
+        F = s.q[k] * E[k]
+        assert np.linalg.norm(F - g) <= 2e-3 * np.linalg.norm(g), k
