@@ -157,6 +157,14 @@ HSMA_API int hsma_coefficients(hsma_t* h, double* out, int64_t len);
 /* Number of the library's kernel launches issued so far by this handle (for accounting). */
 HSMA_API int64_t hsma_kernel_launches(const hsma_t* h);
 
+/* Scheduling of a build followed by a potential/energy evaluation.  hsma_build_sources copies
+ * the inputs and defers the source kernels to the first call that needs them.  on = 1 (the
+ * default): a potential or energy evaluation right after a build runs the build and the pair
+ * sum as one graph, the real-charge/Kelvin part of the pair sum overlapping the coefficient and
+ * surface kernels; on = 0: separate passes (the pair kernel then runs alone on the GPU, which
+ * is how hsma_last_pair_time times it in isolation).  Results are bitwise the same either way. */
+HSMA_API int hsma_set_overlap(hsma_t* h, int on);
+
 /* Device time in milliseconds of the most recent pair-sum kernel launch of the handle (the
  * potential pass's or, after hsma_field, the field pass's; CUDA events recorded on the
  * handle's stream just before and after that launch).  Synchronises
@@ -223,6 +231,9 @@ HSMA_API int hsma_batch_apply_moves(hsma_batch_t* b, int nreq, const int* sys, c
 
 HSMA_API int64_t hsma_batch_kernel_launches(const hsma_batch_t* b);
 HSMA_API int hsma_batch_last_pair_time(hsma_batch_t* b, float* ms);
+
+/* Build/potential scheduling of the batch (see hsma_set_overlap). */
+HSMA_API int hsma_batch_set_overlap(hsma_batch_t* b, int on);
 
 /* Pair-sum tile configurations (CTA threads x targets per thread).  hsma_batch_set_pair_config
  * forces one (-1 = automatic); hsma_batch_autotune times every configuration on the current

@@ -123,6 +123,7 @@ def _declare(lib):
         "hsma_delta_energy": (ctypes.c_int, [vp, i64, vp, dp]),
         "hsma_apply_move": (ctypes.c_int, [vp, i64, vp]),
         "hsma_kernel_launches": (ctypes.c_int64, [vp]),
+        "hsma_set_overlap": (ctypes.c_int, [vp, ctypes.c_int]),
         "hsma_last_pair_time": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "hsma_coefficients": (ctypes.c_int, [vp, vp, i64]),
         "hsma_batch_create": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, vp, pp, ctypes.POINTER(vp)]),
@@ -141,6 +142,7 @@ def _declare(lib):
         "hsma_batch_delta_energy": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp]),
         "hsma_batch_apply_moves": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp]),
         "hsma_batch_kernel_launches": (ctypes.c_int64, [vp]),
+        "hsma_batch_set_overlap": (ctypes.c_int, [vp, ctypes.c_int]),
         "hsma_batch_last_pair_time": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "hsma_pair_config_count": (ctypes.c_int, []),
         "hsma_pair_config_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),

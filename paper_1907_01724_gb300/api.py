@@ -198,6 +198,10 @@ def hsma_apply_move(h: Handle, k: int, x_new) -> None:
     _check(_native.load().hsma_apply_move(h.ptr, int(k), _dptr(x)), h.ptr)
 
 
+def hsma_set_overlap(h: Handle, on: bool) -> None:
+    _check(_native.load().hsma_set_overlap(h.ptr, 1 if on else 0), h.ptr)
+
+
 def hsma_kernel_launches(h: Handle) -> int:
     return int(_native.load().hsma_kernel_launches(h.ptr))
 

@@ -118,6 +118,9 @@ class Batch:
         self._check(self.lib.hsma_batch_potential(self.ptr, _p(phi), int(what)))
         return phi
 
+    def hsma_batch_set_overlap(self, on: bool):
+        self._check(self.lib.hsma_batch_set_overlap(self.ptr, 1 if on else 0))
+
     def hsma_batch_field(self, what: int = HSMA_TOTAL, out=None):
         if out is not None and _is_torch_cuda(out):
             self._check(self.lib.hsma_batch_field_device(self.ptr, ctypes.c_void_p(out.data_ptr()), int(what)))

@@ -56,6 +56,7 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
     rc = run_graph(&g_build, &Engine::issue_build);
     if (rc) return rc;
     sources_ready = true;
+    build_pending = false;
     std::vector<float> t;
     for (int r = 0; r < reps + 1; ++r) {
       pot_ready = false;
@@ -92,6 +93,7 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
   rc = run_graph(&g_build, &Engine::issue_build);
   if (rc) return rc;
   sources_ready = true;
+  build_pending = false;
   pot_ready = false;
   v_ready = false;
   if (best_out) *best_out = best;
@@ -188,6 +190,7 @@ int hsma_batch_set_max_requests(hsma_batch_t* b, int max_requests)
   b->e->max_requests = max_requests;
   b->e->layout_uploaded = false;
   b->e->sources_ready = false;
+  b->e->build_pending = false;
   b->n.clear();
   return HSMA_OK;
 }
@@ -274,6 +277,13 @@ static int batch_field(hsma_batch_t* b, double* E, int what, bool dev)
   }
   if (dev) return HSMA_OK;
   return bfrom(b, b->e->check_status());
+}
+
+int hsma_batch_set_overlap(hsma_batch_t* b, int on)
+{
+  if (!b) return HSMA_E_INVALID_ARG;
+  b->e->overlap = on != 0;
+  return HSMA_OK;
 }
 
 int hsma_batch_field(hsma_batch_t* b, double* E, int what) { return batch_field(b, E, what, false); }
@@ -365,6 +375,7 @@ int hsma_batch_set_pair_config(hsma_batch_t* b, int cfg)
   b->e->forced_cfg = cfg;
   b->e->layout_uploaded = false;
   b->e->sources_ready = false;
+  b->e->build_pending = false;
   b->n.clear();
   return HSMA_OK;
 }

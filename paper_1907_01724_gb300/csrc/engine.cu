@@ -83,6 +83,7 @@ int Engine::init(int dev, void* user_stream, int precision)
   CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ev_img, cudaEventDisableTiming));
   CK(cudaGetLastError());
   return HSMA_OK;
 }
@@ -131,6 +132,7 @@ Engine::~Engine()
   if (ev_pot1) cudaEventDestroy(ev_pot1);
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
+  if (ev_img) cudaEventDestroy(ev_img);
   if (side) cudaStreamDestroy(side);
   if (ev_in) cudaEventDestroy(ev_in);
   if (ev_out) cudaEventDestroy(ev_out);
@@ -142,7 +144,8 @@ void Engine::drop_graphs()
   if (g_build) cudaGraphExecDestroy(g_build);
   if (g_pot) cudaGraphExecDestroy(g_pot);
   if (g_field) cudaGraphExecDestroy(g_field);
-  g_build = g_pot = g_field = nullptr;
+  if (g_fused) cudaGraphExecDestroy(g_fused);
+  g_build = g_pot = g_field = g_fused = nullptr;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -280,6 +283,11 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   };
   for (auto& it : L.it4) it.w = 0;
   std::stable_sort(L.it4.begin(), L.it4.end(), [&](const int4& x, const int4& y) { return cost(x) > cost(y); });
+  // the overlapped pass launches the real/Kelvin items (which need only the records) apart from
+  // the surface items (which wait for the coefficient chain)
+  L.it4x = L.it4;
+  auto is_rk = [&](const int4& it) { return it.z < L.sd[it.x].ncr + L.sd[it.x].nck; };
+  L.nRK = (int)(std::stable_partition(L.it4x.begin(), L.it4x.end(), is_rk) - L.it4x.begin());
   L.totN = chg;
   L.totM = surf;
   L.totP = coef;
@@ -366,6 +374,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_it3 = take(sizeof(int2) * L.it3.size());
   L.o_it5 = take(sizeof(int2) * L.it5.size());
   L.o_it4 = take(sizeof(int4) * L.it4.size());
+  L.o_it4x = take(sizeof(int4) * L.it4x.size());
   L.sel.resize(nsys);
   L.selrng.resize(nsys);
   for (int s = 0; s < nsys; ++s) {
@@ -448,6 +457,8 @@ void Engine::carve()
   it3_d = (int2*)(b + L.o_it3);
   it5_d = (int2*)(b + L.o_it5);
   it4_d = (int4*)(b + L.o_it4);
+  it4x_d = (int4*)(b + L.o_it4x);
+  ctr_pairs2_d = ctr + 1;
   sel_d = (int*)(b + L.o_sel);
   selrng_d = (int2*)(b + L.o_selrng);
 }
@@ -464,6 +475,7 @@ int Engine::attach(void* ptr, size_t bytes)
   ws_user = ptr != nullptr;
   layout_uploaded = false;
   sources_ready = pot_ready = false;
+  build_pending = false;
   drop_graphs();
   return HSMA_OK;
 }
@@ -504,6 +516,8 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
     CK(cudaMemcpyAsync(it5_d, L.it5.data(), sizeof(int2) * L.it5.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it4.empty())
     CK(cudaMemcpyAsync(it4_d, L.it4.data(), sizeof(int4) * L.it4.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.it4x.empty())
+    CK(cudaMemcpyAsync(it4x_d, L.it4x.data(), sizeof(int4) * L.it4x.size(), cudaMemcpyHostToDevice, stream));
   if (!L.itsb.empty())
     CK(cudaMemcpyAsync(itsb_d, L.itsb.data(), sizeof(int2) * L.itsb.size(), cudaMemcpyHostToDevice, stream));
   if (!L.itord.empty())
@@ -526,6 +540,7 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
   CK(cudaStreamSynchronize(stream));
   layout_uploaded = true;
   sources_ready = pot_ready = false;
+  build_pending = false;
   return HSMA_OK;
 }
 
@@ -593,6 +608,75 @@ void Engine::issue_pot()
 
 int Engine::pot_launch_count() const { return (L.it4.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1); }
 
+void Engine::launch_pair_items(const int4* items, int nitems, unsigned int* counter, int grid, cudaStream_t st,
+                               bool reset)
+{
+  if (nitems <= 0) return;
+  if (reset) cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
+  if (prec == HSMA_FP64)
+    launch_pairs_f64(grid, sys_d, items, nitems, counter, src64_d, surf64a_d, surf64b_d, part64_d, st);
+  else
+    launch_pairs_f32(L.cfg, grid, sys_d, items, nitems, counter, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, part_d,
+                     st);
+}
+
+// Build and potentials in one graph.  The real/Kelvin pair items need only the records, so they
+// start on the second stream right after k_images, beside the moments -> coefficients ->
+// surface chain, with their grid capped at kOverlapShare of the pair slots so that the chain's
+// blocks keep room.  After the chain, the main stream runs the surface items and then a second,
+// full-grid launch on the same real/Kelvin item list and work counter, which drains whatever
+// the first launch has not taken (each item is taken once, by whichever CTA gets it).
+//   side:  k_order_* -> k_images -> k_pairs (real/Kelvin, capped grid)
+//   main:  k_moments -> k_coef_reduce -> k_surface_mat -> [wait records] k_pairs (surface)
+//          -> k_pairs (real/Kelvin, drain)
+//   join:  k_reduce
+constexpr double kOverlapShare = 0.5;
+
+void Engine::issue_fused()
+{
+  if (L.itord.empty()) {
+    issue_build();
+    issue_pot();
+    return;
+  }
+  const int nsys = (int)L.sd.size();
+  const int nS = (int)L.it4x.size() - L.nRK;
+  const int occ = prec == HSMA_FP64 ? std::max(occ_f64, 1) : std::max(occ_f32[L.cfg], 1);
+  const int slots = num_sms * occ;
+  const int grid_rk = std::max(1, std::min(L.nRK, (int)(kOverlapShare * slots)));
+  const int grid_s = std::max(1, std::min(nS, slots));
+  cudaEventRecord(ev_fork, stream);
+  cudaStreamWaitEvent(side, ev_fork, 0);
+  launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, key_d, hist_d, offs_d, cursor_d, perm_d, iperm_d,
+               side);
+  launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d, prec,
+                status_d, side);
+  // the work counter of the real/Kelvin items is reset before ev_img, which the main stream
+  // waits for before its draining launch
+  cudaMemsetAsync(ctr_pairs2_d, 0, sizeof(unsigned int), side);
+  cudaEventRecord(ev_img, side);
+  launch_pair_items(it4x_d, L.nRK, ctr_pairs2_d, grid_rk, side, false);
+  cudaEventRecord(ev_join, side);
+  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, tables(), prec, mom_d, L.mom_stride, stream);
+  launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
+                     stream);
+  launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
+                 surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
+  cudaStreamWaitEvent(stream, ev_img, 0);
+  launch_pair_items(it4x_d + L.nRK, nS, ctr_pairs_d, grid_s, stream, true);
+  launch_pair_items(it4x_d, L.nRK, ctr_pairs2_d, std::max(1, std::min(L.nRK, slots)), stream, false);
+  cudaStreamWaitEvent(stream, ev_join, 0);
+  launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
+                phic_d, phir_d, phit_d, epart_d, energy_d, ctr_red_d, status_d, stream);
+}
+
+int Engine::fused_launch_count() const
+{
+  if (L.itord.empty()) return build_launch_count() + pot_launch_count();
+  return build_launch_count() + (L.nRK > 0 ? 2 : 0) + ((int)L.it4x.size() > L.nRK ? 1 : 0) +
+         (L.it5.empty() ? 0 : 1);
+}
+
 int Engine::run_graph(cudaGraphExec_t* g, void (Engine::*issue)())
 {
   if (!use_graphs) {
@@ -627,13 +711,24 @@ int Engine::build(const double* xyz, const double* q, bool device_inputs)
     CK(cudaMemcpyAsync(xyz_d, xyz, 24 * n, kind, stream));
     CK(cudaMemcpyAsync(q_d, q, 8 * n, kind, stream));
   }
+  leave();
+  sources_ready = true;
+  build_pending = true;
+  pot_ready = false;
+  v_ready = false;
+  return HSMA_OK;
+}
+
+int Engine::ensure_built()
+{
+  if (!build_pending) return HSMA_OK;
+  CK(cudaSetDevice(device));
+  enter();
   int rc = run_graph(&g_build, &Engine::issue_build);
   if (rc) return rc;
   leave();
   launches += build_launch_count();
-  sources_ready = true;
-  pot_ready = false;
-  v_ready = false;
+  build_pending = false;
   return HSMA_OK;
 }
 
@@ -642,14 +737,25 @@ int Engine::potentials()
   if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
   if (pot_ready) return HSMA_OK;
   CK(cudaSetDevice(device));
-  enter();
-  int rc = run_graph(&g_pot, &Engine::issue_pot);
-  if (rc) return rc;
-  leave();
-  launches += pot_launch_count();
+  if (build_pending && overlap) {
+    enter();
+    int rc = run_graph(&g_fused, &Engine::issue_fused);
+    if (rc) return rc;
+    leave();
+    launches += fused_launch_count();
+    build_pending = false;
+  } else {
+    int rc = ensure_built();
+    if (rc) return rc;
+    enter();
+    rc = run_graph(&g_pot, &Engine::issue_pot);
+    if (rc) return rc;
+    leave();
+    launches += pot_launch_count();
+    if (!L.it4.empty()) pair_timed = true;
+  }
   pot_ready = true;
   field_ready = false;
-  if (!L.it4.empty()) pair_timed = true;
   return HSMA_OK;
 }
 
@@ -725,7 +831,9 @@ int Engine::field()
   if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
   if (pot_ready && field_ready) return HSMA_OK;
   CK(cudaSetDevice(device));
-  int rc = ensure_field_buffers();
+  int rc = ensure_built();
+  if (rc) return rc;
+  rc = ensure_field_buffers();
   if (rc) return rc;
   enter();
   rc = run_graph(&g_field, &Engine::issue_field);
@@ -1074,6 +1182,13 @@ int hsma_apply_move(hsma_t* h, int64_t k, const double* x_new)
   return from_engine(h, h->e->apply_move(k, x_new));
 }
 
+int hsma_set_overlap(hsma_t* h, int on)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  h->e->overlap = on != 0;
+  return HSMA_OK;
+}
+
 int64_t hsma_kernel_launches(const hsma_t* h) { return h ? h->e->launches : 0; }
 
 int hsma_coefficients(hsma_t* h, double* out, int64_t len)
@@ -1082,6 +1197,8 @@ int hsma_coefficients(hsma_t* h, double* out, int64_t len)
   if (h->n < 0 || !h->e->sources_ready) return set_err(h, HSMA_E_STATE, "sources have not been built");
   const int P = h->e->L.sd[0].P;
   if (len < P) return set_err(h, HSMA_E_INVALID_ARG, "output shorter than (p+1)^2");
+  int rc = h->e->ensure_built();
+  if (rc) return from_engine(h, rc);
   cudaError_t e = cudaMemcpyAsync(out, h->e->coef_d, 8 * (size_t)P, cudaMemcpyDeviceToHost, h->e->stream);
   if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy coefficients"));
   return from_engine(h, h->e->check_status());
@@ -1130,6 +1247,8 @@ int Engine::delta_batch(const std::vector<DeltaReq>& reqs, double* de_host)
   if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
   int rc = check_moves(*this, reqs);
   if (rc) return rc;
+  rc = ensure_built();
+  if (rc) return rc;
   if (reqs.empty()) return HSMA_OK;
   std::vector<int4> items;
   std::vector<int2> ranges(reqs.size());
@@ -1161,6 +1280,8 @@ int Engine::move_batch(const std::vector<DeltaReq>& reqs)
 {
   if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
   int rc = check_moves(*this, reqs);
+  if (rc) return rc;
+  rc = ensure_built();
   if (rc) return rc;
   if (reqs.empty()) return HSMA_OK;
   std::vector<int2> items;

@@ -29,6 +29,8 @@ struct Layout {
   bool use_sb = false;        // surface synthesis through the basis tables
   int64_t totSB = 0;          // 8-byte slots of all basis tables
   std::vector<int4> it4;
+  std::vector<int4> it4x;     // it4 split: real and Kelvin items first (nRK), then surface items
+  int nRK = 0;
   std::vector<int> sel;       // all systems, in order (energy pass of a full launch)
   std::vector<int2> selrng;   // their reduce-item ranges
   size_t o_sel = 0, o_selrng = 0;
@@ -45,7 +47,7 @@ struct Layout {
   size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_offs = 0, o_cursor = 0, o_boxes = 0, o_itord = 0;
   size_t o_redctr = 0;
   size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0;
-  size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0;
+  size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0, o_it4x = 0;
   size_t bytes = 0;
 };
 
@@ -108,7 +110,12 @@ class Engine {
   float4* boxes_d = nullptr;      // bounding boxes of 32 consecutive sorted records
   int2* itord_d = nullptr;
   cudaStream_t side = nullptr;    // second stream of the build (order + records beside the moments)
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_img = nullptr;
+  // deferred build: build() copies the inputs; the first evaluation runs the build, and a
+  // potential/energy evaluation runs it fused with the pair sum (overlap) in one graph
+  bool build_pending = false;
+  bool overlap = true;
+  int ensure_built();
   double *phic_d = nullptr, *phir_d = nullptr, *phit_d = nullptr, *epart_d = nullptr, *energy_d = nullptr;
   unsigned int *ctr_pairs_d = nullptr, *ctr_red_d = nullptr, *ctr_delta_d = nullptr;
   int* status_d = nullptr;
@@ -129,6 +136,8 @@ class Engine {
   int* sel_d = nullptr;
   int2* selrng_d = nullptr;
   int4* it4_d = nullptr;
+  int4* it4x_d = nullptr;
+  unsigned int* ctr_pairs2_d = nullptr;  // work counter of the overlapped real/Kelvin pair launch
 
   // pair-kernel timing events (recorded around every pair-sum launch)
   cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;
@@ -144,7 +153,7 @@ class Engine {
   // state
   bool sources_ready = false, pot_ready = false;
   bool field_ready = false;       // E is current when pot_ready && field_ready
-  cudaGraphExec_t g_build = nullptr, g_pot = nullptr, g_field = nullptr;
+  cudaGraphExec_t g_build = nullptr, g_pot = nullptr, g_field = nullptr, g_fused = nullptr;
   // field pass buffers, outside the workspace (allocated on the first field request)
   void* fpart_d = nullptr;        // 32 bytes per (chunk, target) slot
   size_t fpart_cap = 0;
@@ -162,6 +171,10 @@ class Engine {
   void issue_build();
   void issue_pot();
   void issue_field();
+  void issue_fused();
+  void launch_pair_items(const int4* items, int nitems, unsigned int* counter, int grid, cudaStream_t st,
+                         bool reset);
+  int fused_launch_count() const;
   int build_launch_count() const;
   int pot_launch_count() const;
   int run_graph(cudaGraphExec_t* g, void (Engine::*issue)());

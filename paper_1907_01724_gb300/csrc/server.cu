@@ -159,6 +159,8 @@ static int rebuild(hsma_server_t* s)
   if (rc) return serr(s, rc, e->err);
   rc = e->build(xyz.data(), q.data(), false);
   if (rc) return serr(s, rc, e->err);
+  rc = e->ensure_built();
+  if (rc) return serr(s, rc, e->err);
   rc = e->ensure_v();
   if (rc) return serr(s, rc, e->err);
   rc = e->check_status();

@@ -202,5 +202,29 @@ def test_kernel_launch_accounting():
     api.hsma_build_sources(h, s.xyz, s.q)
     api.hsma_energy(h)
     # once per layout: k_setup, k_surface_basis; build: k_order_cells, _scan, _scatter, _sort,
-    # k_images, k_moments, k_coef_reduce, k_surface_mat; potentials: k_pairs, k_reduce
-    assert api.hsma_kernel_launches(h) == 12
+    # k_images, k_moments, k_coef_reduce, k_surface_mat; potentials (overlapped with the build):
+    # k_pairs (real/Kelvin items, capped grid), k_pairs (surface items), k_pairs (real/Kelvin
+    # items, draining), k_reduce
+    assert api.hsma_kernel_launches(h) == 14
+    api.hsma_set_overlap(h, False)
+    api.hsma_build_sources(h, s.xyz, s.q)
+    api.hsma_energy(h)
+    # separate passes: the 8 build kernels, then k_pairs and k_reduce
+    assert api.hsma_kernel_launches(h) == 14 + 10
+
+
+@pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
+def test_overlapped_and_separate_passes_agree_bitwise(prec):
+    s = inputs.near_interface_system(kappa_a=2.0)
+    prm = api.hsma_default_params(p=s.p, M=s.M, precision=prec)
+    h = api.hsma_create(s.a, s.eps1, s.eps2, s.kappa, prm)
+    api.hsma_build_sources(h, s.xyz, s.q)
+    phi1 = api.hsma_potential(h)
+    e1 = api.hsma_energy(h)
+    api.hsma_set_overlap(h, False)
+    api.hsma_build_sources(h, s.xyz, s.q)
+    phi0 = api.hsma_potential(h)
+    e0 = api.hsma_energy(h)
+    api.hsma_destroy(h)
+    assert np.array_equal(phi0, phi1)
+    assert e0 == e1
