@@ -55,16 +55,24 @@ def evals(s) -> int:
     return s.n * (2 * s.n - 1 + s.M)
 
 
-def profiled_traffic(kernel_src: str, profile_md: str):
+def kernel_source_sha(paths) -> str:
+    """sha256 of the concatenated sources of a kernel (recorded with each committed ncu summary)."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel_srcs, profile_md: str):
     """DRAM bytes per launch from the committed ncu summary, or None if the kernel's source has
     changed since that capture (the summary records the source hash it was taken with)."""
-    import hashlib
     import re
     try:
         text = open(profile_md).read()
         sha = re.search(r"source_sha256 \([^)]*\): ([0-9a-f]+)", text).group(1)
         traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
-        cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:len(sha)]
+        cur = kernel_source_sha(kernel_srcs)[:len(sha)]
     except (OSError, AttributeError):
         return None
     return traffic if cur == sha else None
@@ -210,6 +218,18 @@ def run_batched(local, stream, gpu_name):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     tot_pairs = sum(pairs(s) for s in systems)
+    # the pair kernel alone (separate passes), for its roofline at this size
+    b.hsma_batch_set_overlap(False)
+    kern = []
+    for _ in range(3):
+        b.hsma_batch_build_sources(n, xyz_d, q_d)
+        b.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
+        kern.append(b.hsma_batch_last_pair_time())
+    b.hsma_batch_set_overlap(True)
+    t_kern = statistics.median(kern) / 1e3
+    props = torch.cuda.get_device_properties(local)
+    peak = props.multi_processor_count * SM_MUFU_PER_CLK * 2070.0e6
+    kern_evals = sum(evals(s) for s in systems) / t_kern
     et, _ = b.hsma_batch_energy()
     # accuracy on a seeded sample against the oracle
     import oracle
@@ -240,6 +260,8 @@ def run_batched(local, stream, gpu_name):
                         "kappa*a~U[0.5,3], eps1 in {1, 78.5}, eps2=78.5, M=1000, p=20",
             "req_per_s": len(systems) * k / t, "pair_evals_per_s": tot_pairs * k / t, "ms_per_batch": t / k * 1e3,
             "pair_config": batch.pair_configs()[cfg], "energy_rel_err_max_vs_oracle_sample": worst,
+            "pair_kernel_alone": {"ms": t_kern * 1e3, "evals_per_s": kern_evals,
+                                  "frac_of_mufu_peak_at_2070MHz": kern_evals / peak},
             "fp64_single_system": {"req_per_s": fp64_req_s, "pair_evals_per_s": fp64_pairs_s,
                                    "sample": "16 seeded systems, one FP64 handle each, host inputs"}}
 
@@ -431,7 +453,8 @@ def run_ours(args):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = sms * SM_MUFU_PER_CLK * sm_max * 1e6
     achieved = ev_per_launch / t_pair
-    traffic = profiled_traffic(os.path.join(ROOT, "paper_1907_01724_gb300", "csrc", "k_pairs.cu"),
+    csrc = os.path.join(ROOT, "paper_1907_01724_gb300", "csrc")
+    traffic = profiled_traffic([os.path.join(csrc, "k_pairs.cu"), os.path.join(csrc, "k_pairs_f32.cuh")],
                                os.path.join(ROOT, "profiles", "k_pairs_f32_N2000x2.md"))
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-eval/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",

@@ -146,7 +146,7 @@ def _declare(lib):
         "hsma_batch_last_pair_time": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "hsma_pair_config_count": (ctypes.c_int, []),
         "hsma_pair_config_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                                                 ctypes.POINTER(ctypes.c_int)]),
+                                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "hsma_batch_set_pair_config": (ctypes.c_int, [vp, ctypes.c_int]),
         "hsma_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_float)]),

@@ -167,13 +167,14 @@ class Batch:
         return int(best.value), float(ms.value)
 
 
-def pair_configs() -> list[tuple[int, int]]:
+def pair_configs() -> list[tuple[int, int, int]]:
+    """(CTA threads, targets per thread, pair items per CTA slot) of every configuration."""
     lib = _native.load()
     out = []
     for i in range(lib.hsma_pair_config_count()):
-        t, k = ctypes.c_int(), ctypes.c_int()
-        lib.hsma_pair_config_info(i, ctypes.byref(t), ctypes.byref(k))
-        out.append((t.value, k.value))
+        t, k, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib.hsma_pair_config_info(i, ctypes.byref(t), ctypes.byref(k), ctypes.byref(m))
+        out.append((t.value, k.value, m.value))
     return out
 
 
@@ -207,7 +208,8 @@ class TuneCache:
     @staticmethod
     def key(n, gpu: str) -> str:
         tot = int(np.sum(n))
-        return f"{gpu}|nsys={len(n)}|log2N={max(tot, 1).bit_length()}"
+        ncfg = _native.load().hsma_pair_config_count()
+        return f"{gpu}|ncfg={ncfg}|nsys={len(n)}|log2N={max(tot, 1).bit_length()}"
 
     def get(self, n, gpu: str):
         return self.data.get(self.key(n, gpu))

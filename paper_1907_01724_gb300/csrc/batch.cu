@@ -360,12 +360,13 @@ int hsma_batch_last_pair_time(hsma_batch_t* b, float* ms)
 
 int hsma_pair_config_count(void) { return hsma::pair_config_count(); }
 
-int hsma_pair_config_info(int idx, int* threads, int* targets_per_thread)
+int hsma_pair_config_info(int idx, int* threads, int* targets_per_thread, int* items_per_slot)
 {
   if (idx < 0 || idx >= hsma::pair_config_count()) return HSMA_E_INVALID_ARG;
   const hsma::PairConfig c = hsma::pair_config(idx);
   if (threads) *threads = c.threads;
   if (targets_per_thread) *targets_per_thread = c.k;
+  if (items_per_slot) *items_per_slot = c.items_per_slot;
   return HSMA_OK;
 }
 

@@ -164,7 +164,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     occ = occ_f32[cfg] > 0 ? occ_f32[cfg] : 1;
   }
   const int slots = num_sms * occ;
-  const double desired = 4.0 * slots;
+  const double desired = (prec == HSMA_FP64 ? 4.0 : (double)pair_config(cfg).items_per_slot) * slots;
   // the pair items and moment blocks of the whole engine are apportioned by each system's share
   // of the work, so a batch of many small systems gets few, larger items per system
   double W = 0.0;

@@ -132,11 +132,13 @@ constexpr int kMomTile = 256;  // largest moment tile (charges per moment block)
 
 // ---- launchers (k_pairs.cu) ----
 struct PairConfig {
-  int threads;  // CTA size
-  int k;        // targets per thread
+  int threads;         // CTA size
+  int k;               // targets per thread
+  int items_per_slot;  // pair items per resident CTA slot of the layout
 };
 int pair_config_count();
 PairConfig pair_config(int idx);
+int pair_kernel_of(int cfg);  // kernel variant (threads, k) of a configuration
 int pairs_f32_occupancy(int cfg);
 int pairs_f64_occupancy();
 constexpr int kF64TargetsPerBlock = 128;

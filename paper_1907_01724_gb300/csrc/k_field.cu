@@ -106,6 +106,18 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
     const int w0 = t0 + warp * 32 * K;
     const FChunk ch = field_chunk(S, it.z);
 
+    // the first source tile is in flight while the targets load
+    const float4* gA = ch.type == 2 ? surf_a + ch.off : src_hi + ch.off;
+    const float4* gB = ch.type == 2 ? surf_b + ch.off : src_lo + ch.off;
+    const int ntiles = (ch.count + NT - 1) / NT;
+    const long long box_kind = S.bb + (ch.type == 1 ? (n + kBox - 1) / kBox : 0);
+
+    if (tid < ch.count) {
+      cp_async16_f(&shA[0][tid], gA + tid);
+      cp_async16_f(&shB[0][tid], gB + tid);
+    }
+    cp_async_commit_f();
+
     float txh[K], tyh[K], tzh[K], txl[K], tyl[K], tzl[K];
     int tix[K];
 #pragma unroll
@@ -136,16 +148,6 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
 #pragma unroll
     for (int k = 0; k < K; ++k) Hp[k] = Lp[k] = Hx[k] = Lx[k] = Hy[k] = Ly[k] = Hz[k] = Lz[k] = 0.f;
 
-    const float4* gA = ch.type == 2 ? surf_a + ch.off : src_hi + ch.off;
-    const float4* gB = ch.type == 2 ? surf_b + ch.off : src_lo + ch.off;
-    const int ntiles = (ch.count + NT - 1) / NT;
-    const long long box_kind = S.bb + (ch.type == 1 ? (n + kBox - 1) / kBox : 0);
-
-    if (tid < ch.count) {
-      cp_async16_f(&shA[0][tid], gA + tid);
-      cp_async16_f(&shB[0][tid], gB + tid);
-    }
-    cp_async_commit_f();
     for (int t = 0; t < ntiles; ++t) {
       const int buf = t & 1;
       if (t + 1 < ntiles) {
@@ -272,7 +274,7 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
 int field_f32_occupancy(int cfg)
 {
   int b = 0;
-  switch (cfg) {
+  switch (pair_kernel_of(cfg)) {
 #define HSMA_FCFG_OCC(i, nt, k) \
   case i: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_field_f32<nt, k>, nt, 0); break;
     HSMA_FIELD_CONFIGS(HSMA_FCFG_OCC)
@@ -288,7 +290,7 @@ void launch_field_f32(int cfg, int grid, const SysDev* sys, const int4* items, i
                       const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
                       const float4* boxes, float4* fpart, cudaStream_t st)
 {
-  switch (cfg) {
+  switch (pair_kernel_of(cfg)) {
 #define HSMA_FCFG_LAUNCH(i, nt, k)                                                                        \
   case i:                                                                                                 \
     k_field_f32<nt, k><<<grid, nt, 0, st>>>(sys, items, nitems, counter, src_hi, src_lo, surf_a, surf_b, boxes, \

@@ -79,24 +79,37 @@ __device__ __forceinline__ ChunkInfo decode_chunk(const SysDev& S, int c)
 // ---------------------------------------------------------------------------------------
 #include "k_pairs_f32.cuh"
 
-// Tile configurations (CTA threads, targets per thread); the autotuner picks one per size class.
+// Tile configurations: kernel variants (CTA threads, targets per thread), each with 4, 2 or 1
+// pair items per resident CTA slot (fewer, larger items have less per-item overhead, more items
+// balance better); the autotuner picks one per size class.
 #define HSMA_PAIR_CONFIGS(X) \
   X(0, 128, 4) X(1, 128, 2) X(2, 256, 2) X(3, 256, 4) X(4, 64, 4) X(5, 128, 1) X(6, 256, 1) X(7, 128, 8) \
   X(8, 64, 2) X(9, 64, 1) X(10, 32, 2) X(11, 32, 4)
 
-static const PairConfig kPairConfigs[] = {
+static const int kPairKernel[][2] = {
 #define HSMA_CFG_ENTRY(i, nt, k) {nt, k},
     HSMA_PAIR_CONFIGS(HSMA_CFG_ENTRY)
 #undef HSMA_CFG_ENTRY
 };
+constexpr int kPairKernels = (int)(sizeof(kPairKernel) / sizeof(kPairKernel[0]));
+static const int kItemsPerSlot[] = {4, 2, 1};
+constexpr int kItemChoices = (int)(sizeof(kItemsPerSlot) / sizeof(kItemsPerSlot[0]));
 
-int pair_config_count() { return (int)(sizeof(kPairConfigs) / sizeof(kPairConfigs[0])); }
-PairConfig pair_config(int idx) { return kPairConfigs[idx]; }
+int pair_config_count() { return kPairKernels * kItemChoices; }
+int pair_kernel_of(int cfg) { return cfg % kPairKernels; }
+PairConfig pair_config(int idx)
+{
+  PairConfig c;
+  c.threads = kPairKernel[idx % kPairKernels][0];
+  c.k = kPairKernel[idx % kPairKernels][1];
+  c.items_per_slot = kItemsPerSlot[idx / kPairKernels];
+  return c;
+}
 
 int pairs_f32_occupancy(int cfg)
 {
   int b = 0;
-  switch (cfg) {
+  switch (pair_kernel_of(cfg)) {
 #define HSMA_CFG_OCC(i, nt, k) \
   case i: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_f32<nt, k>, nt, 0); break;
     HSMA_PAIR_CONFIGS(HSMA_CFG_OCC)
@@ -110,7 +123,7 @@ void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, i
                       const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
                       const float4* boxes, float2* part, cudaStream_t st)
 {
-  switch (cfg) {
+  switch (pair_kernel_of(cfg)) {
 #define HSMA_CFG_LAUNCH(i, nt, k)                                                                          \
   case i:                                                                                                  \
     k_pairs_f32<nt, k><<<grid, nt, 0, st>>>(sys, items, nitems, counter, src_hi, src_lo, surf_a, surf_b, boxes, \

@@ -36,6 +36,18 @@ __global__ __launch_bounds__(NT) void k_pairs_f32(const SysDev* __restrict__ sys
     const int w0 = t0 + warp * 32 * K;  // the warp's targets are [w0, w0 + 32 K)
     const ChunkInfo ch = decode_chunk(S, it.z);
 
+    // the first source tile is in flight while the targets load
+    const float4* gA = ch.type == 2 ? surf_a + ch.off : src_hi + ch.off;
+    const float4* gB = ch.type == 2 ? surf_b + ch.off : src_lo + ch.off;
+    const int ntiles = (ch.count + NT - 1) / NT;
+    const long long box_kind = S.bb + (ch.type == 1 ? (n + kBox - 1) / kBox : 0);
+
+    if (tid < ch.count) {
+      cp_async16(&shA[0][tid], gA + tid);
+      cp_async16(&shB[0][tid], gB + tid);
+    }
+    cp_async_commit();
+
     // targets (a slot past the end repeats the block's first target)
     float txh[K], tyh[K], tzh[K], txl[K], tyl[K], tzl[K];
     int tix[K];
@@ -68,16 +80,6 @@ __global__ __launch_bounds__(NT) void k_pairs_f32(const SysDev* __restrict__ sys
 #pragma unroll
     for (int k = 0; k < K; ++k) H[k] = L[k] = 0.f;
 
-    const float4* gA = ch.type == 2 ? surf_a + ch.off : src_hi + ch.off;
-    const float4* gB = ch.type == 2 ? surf_b + ch.off : src_lo + ch.off;
-    const int ntiles = (ch.count + NT - 1) / NT;
-    const long long box_kind = S.bb + (ch.type == 1 ? (n + kBox - 1) / kBox : 0);
-
-    if (tid < ch.count) {
-      cp_async16(&shA[0][tid], gA + tid);
-      cp_async16(&shB[0][tid], gB + tid);
-    }
-    cp_async_commit();
     for (int t = 0; t < ntiles; ++t) {
       const int buf = t & 1;
       if (t + 1 < ntiles) {
