@@ -418,6 +418,32 @@ __device__ __forceinline__ df dshfl(df v, int o)
   return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
 }
 
+// Adds the (hi, lo) partials of chunks k0, k0 + kFRedLanes, ... < k1 in ascending order, two
+// chunks' loads in flight ahead of the additions.
+__device__ __forceinline__ void sum_field_chunks(const float4* __restrict__ b, long long n, int k0, int k1, df* acc)
+{
+  int k = k0;
+  for (; k + kFRedLanes < k1; k += 2 * kFRedLanes) {
+    const float4 h0 = b[2 * (long long)k * n], l0 = b[2 * (long long)k * n + 1];
+    const float4 h1 = b[2 * (long long)(k + kFRedLanes) * n], l1 = b[2 * (long long)(k + kFRedLanes) * n + 1];
+    acc[0] = acc[0] + df_make(h0.x, l0.x);
+    acc[1] = acc[1] + df_make(h0.y, l0.y);
+    acc[2] = acc[2] + df_make(h0.z, l0.z);
+    acc[3] = acc[3] + df_make(h0.w, l0.w);
+    acc[0] = acc[0] + df_make(h1.x, l1.x);
+    acc[1] = acc[1] + df_make(h1.y, l1.y);
+    acc[2] = acc[2] + df_make(h1.z, l1.z);
+    acc[3] = acc[3] + df_make(h1.w, l1.w);
+  }
+  for (; k < k1; k += kFRedLanes) {
+    const float4 h = b[2 * (long long)k * n], l = b[2 * (long long)k * n + 1];
+    acc[0] = acc[0] + df_make(h.x, l.x);
+    acc[1] = acc[1] + df_make(h.y, l.y);
+    acc[2] = acc[2] + df_make(h.z, l.z);
+    acc[3] = acc[3] + df_make(h.w, l.w);
+  }
+}
+
 __global__ __launch_bounds__(kFRedThreads) void k_reduce_field(
     const SysDev* __restrict__ sys, const int* __restrict__ sel, const int2* __restrict__ sel_rng, int nsel,
     const int2* __restrict__ items, const float4* __restrict__ fpart, const dbl4* __restrict__ fpart64, int prec,
@@ -460,20 +486,8 @@ __global__ __launch_bounds__(kFRedThreads) void k_reduce_field(
     for (int m = 0; m < 4; ++m) cc[m] = rr[m] = df_make(0.f, 0.f);
     if (i < n) {
       const float4* b = fpart + 2 * (S.part + i);
-      for (int k = sub; k < S.ncr; k += kFRedLanes) {
-        const float4 h = b[2 * (long long)k * n], l = b[2 * (long long)k * n + 1];
-        cc[0] = cc[0] + df_make(h.x, l.x);
-        cc[1] = cc[1] + df_make(h.y, l.y);
-        cc[2] = cc[2] + df_make(h.z, l.z);
-        cc[3] = cc[3] + df_make(h.w, l.w);
-      }
-      for (int k = S.ncr + sub; k < nch; k += kFRedLanes) {
-        const float4 h = b[2 * (long long)k * n], l = b[2 * (long long)k * n + 1];
-        rr[0] = rr[0] + df_make(h.x, l.x);
-        rr[1] = rr[1] + df_make(h.y, l.y);
-        rr[2] = rr[2] + df_make(h.z, l.z);
-        rr[3] = rr[3] + df_make(h.w, l.w);
-      }
+      sum_field_chunks(b, n, sub, S.ncr, cc);
+      sum_field_chunks(b, n, S.ncr + sub, nch, rr);
     }
     for (int o = 1; o < kFRedLanes; o <<= 1)
 #pragma unroll

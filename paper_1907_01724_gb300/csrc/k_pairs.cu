@@ -230,8 +230,32 @@ void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems
 // block reductions; the last block of a system to finish (counter[r] per launch-local system
 // r, reset by that block) sums the system's block partials in a fixed order.
 constexpr int kRedLanes = 8;
+// Sum of the (hi, lo) partials of chunks k0, k0 + kRedLanes, ... < k1 in ascending order; the
+// loads are issued four at a time ahead of the additions (a plain loop would wait one L2 round
+// trip per chunk).
+__device__ __forceinline__ df sum_chunks(const float2* __restrict__ b, long long n, int k0, int k1)
+{
+  df acc = df_make(0.f, 0.f);
+  int k = k0;
+  for (; k + 3 * 8 < k1; k += 4 * 8) {
+    const float2 v0 = b[(long long)k * n], v1 = b[(long long)(k + 8) * n];
+    const float2 v2 = b[(long long)(k + 16) * n], v3 = b[(long long)(k + 24) * n];
+    acc = acc + df_make(v0.x, v0.y);
+    acc = acc + df_make(v1.x, v1.y);
+    acc = acc + df_make(v2.x, v2.y);
+    acc = acc + df_make(v3.x, v3.y);
+  }
+  for (; k < k1; k += 8) {
+    const float2 v = b[(long long)k * n];
+    acc = acc + df_make(v.x, v.y);
+  }
+  return acc;
+}
+
+
 constexpr int kRedThreads = kReduceTargetsPerBlock * kRedLanes;
 static_assert(kRedThreads == 256, "reduce block size");
+static_assert(kRedLanes == 8, "sum_chunks strides by 8 lanes");
 
 __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict__ sys, const int* __restrict__ sel,
                                                         const int2* __restrict__ sel_rng, int nsel,
@@ -256,6 +280,15 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   // loads per target are in flight and the order does not depend on scheduling
   const int sub = threadIdx.x % kRedLanes;
   const int i = it.y * kReduceTargetsPerBlock + threadIdx.x / kRedLanes;
+  // the target's input position, charge and the centre constant are loaded first, so their
+  // latency overlaps the partial sums
+  long long o = 0;
+  double qi = 0.0, rc = 0.0;
+  if (i < n && sub == 0) {
+    o = S.chg + perm[S.chg + i];  // partials are in sorted order
+    qi = q[o];
+    rc = r0[it.x];
+  }
   double et = 0.0, er = 0.0;
   double pc = 0.0, pr = 0.0;
   const int nch = S.ncr + S.nck + S.ncs;
@@ -274,14 +307,8 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     df c = df_make(0.f, 0.f), r = df_make(0.f, 0.f);
     if (i < n) {
       const float2* b = part + S.part + i;
-      for (int k = sub; k < S.ncr; k += kRedLanes) {
-        const float2 v = b[(long long)k * n];
-        c = c + df_make(v.x, v.y);
-      }
-      for (int k = S.ncr + sub; k < nch; k += kRedLanes) {
-        const float2 v = b[(long long)k * n];
-        r = r + df_make(v.x, v.y);
-      }
+      c = sum_chunks(b, n, sub, S.ncr);
+      r = sum_chunks(b, n, S.ncr + sub, nch);
     }
     for (int o = 1; o < kRedLanes; o <<= 1) {
       c = c + df_make(__shfl_xor_sync(0xffffffffu, c.hi, o), __shfl_xor_sync(0xffffffffu, c.lo, o));
@@ -293,13 +320,11 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     }
   }
   if (i < n && sub == 0) {
-    pr += r0[it.x];
-    const long long o = S.chg + perm[S.chg + i];  // partials are in sorted order
+    pr += rc;
     phi_c[o] = pc;
     phi_r[o] = pr;
     phi_t[o] = pc + pr;
     if (!isfinite(pc) || !isfinite(pr)) atomicOr(status, kStNonFinite);
-    const double qi = q[o];
     et = 0.5 * qi * (pc + pr);
     er = 0.5 * qi * pr;
   }

@@ -145,6 +145,9 @@ struct Num<double> {
   static __device__ __forceinline__ void st(double* p, long long i, double v) { p[i] = v; }
   static __device__ __forceinline__ double shfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
   static __device__ __forceinline__ double coefv(const double* c, const float2*, long long i) { return c[i]; }
+  static __device__ __forceinline__ double mul_sub(double a, double x, double b, double y) { return a * x - b * y; }
+  static __device__ __forceinline__ double acc(double s, double a, double b) { return a * b + s; }
+  static __device__ __forceinline__ double norm(double x) { return x; }
 };
 template <>
 struct Num<df> {
@@ -187,6 +190,9 @@ struct Num<df> {
     const float2 v = c2[i];
     return df_make(v.x, v.y);
   }
+  static __device__ __forceinline__ df mul_sub(df a, df x, df b, df y) { return df_mul_sub(a, x, b, y); }
+  static __device__ __forceinline__ df acc(df s, df a, df b) { return df_acc(s, a, b); }
+  static __device__ __forceinline__ df norm(df x) { return df_norm(x); }
 };
 
 // Real normalised solid harmonics of one point (u, v, w) (units of a), column m of the
@@ -199,8 +205,8 @@ __device__ __forceinline__ void solid_column(int m, int p, R u, R v, R w, R rho2
   R cr = Num<R>::one(), ci = Num<R>::zero();
   for (int k = 1; k <= m; ++k) {
     const R f = Num<R>::sc(tab, k);
-    const R nr = f * (cr * u - ci * v);
-    const R ni = f * (cr * v + ci * u);
+    const R nr = f * Num<R>::mul_sub(cr, u, ci, v);
+    const R ni = f * Num<R>::mul_sub(cr, v, -ci, u);
     cr = nr;
     ci = ni;
   }
@@ -210,8 +216,8 @@ __device__ __forceinline__ void solid_column(int m, int p, R u, R v, R w, R rho2
   for (int n = m + 1; n <= p; ++n) {
     const int t = n * (n + 1) / 2 + m;
     const R A = Num<R>::ra(tab, t) * w, B = Num<R>::rb(tab, t) * rho2;
-    const R nr = A * pr - B * qr;
-    const R ni = A * pi - B * qi;
+    const R nr = Num<R>::mul_sub(A, pr, B, qr);
+    const R ni = Num<R>::mul_sub(A, pi, B, qi);
     T[n * n + n + m] = nr;
     if (m) T[n * n + n - m] = ni;
     qr = pr;
@@ -232,6 +238,7 @@ __device__ __forceinline__ void split2(double x, float& hi, float& lo)
 constexpr int kMomThreads = 256;  // a moment block holds at most kMomTile <= kMomThreads charges
 constexpr int kMomWarps = kMomThreads / 32;
 static_assert(kMomTile <= kMomThreads, "one charge per thread in the preparation pass");
+static_assert(kOrderBlock % 64 == 0, "k_images splits an order item into 64-thread blocks");
 
 // Kelvin image of one charge (Sec. 2.4): r_K = a^2/r along xhat,
 // q_K = (q/a)[gamma r_K + dbar (R_tau - r_K)/2], strength k q_K/eps1.  r, r_K and the image
@@ -266,22 +273,26 @@ __device__ __forceinline__ KelvinRec kelvin_rec(const SysDev& S, double x, doubl
   return k;
 }
 
-// Pair-sum records in the spatial order of k_order.cu: thread t of item (s, b) handles sorted
-// position i = 256 b + t, i.e. input charge perm[i].  Real record (x, k q/eps1) at src + i and
-// Kelvin record at src + n + i; the FP32 path stores (hi x, hi y, hi z, Q) and
-// (lo x, lo y, lo z, 0) and, per warp (32 consecutive records), the bounding box of the hi
-// coordinates (min, max as two float4) of the real and of the Kelvin records.
-constexpr int kImgThreads = 256;
+// Pair-sum records in the spatial order of k_order.cu: item (s, b) covers sorted positions
+// [kOrderBlock b, kOrderBlock (b + 1)); sorted position i holds input charge perm[i].  Real
+// record (x, k q/eps1) at src + i and Kelvin record at src + n + i; the FP32 path stores
+// (hi x, hi y, hi z, Q) and (lo x, lo y, lo z, 0) and, per warp (32 consecutive records), the
+// bounding box of the hi coordinates (min, max as two float4) of the real and of the Kelvin
+// records.
+// Blocks of 64 threads (four per item): the image geometry is FP64, and on this GPU the FP64 pipe
+// of one SM issues 1.6 operations per clock, so the work is spread over four times as many SMs.
+constexpr int kImgThreads = 64;
+constexpr int kImgSplit = kOrderBlock / kImgThreads;
 __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict__ sys, const int2* __restrict__ items,
                                                         const double* __restrict__ xyz, const double* __restrict__ q,
                                                         const int* __restrict__ perm, float4* __restrict__ src_hi,
                                                         float4* __restrict__ src_lo, dbl4* __restrict__ src64,
                                                         float4* __restrict__ boxes, int prec, int* __restrict__ status)
 {
-  const int2 it = items[blockIdx.x];
+  const int2 it = items[blockIdx.x / kImgSplit];
   const SysDev& S = sys[it.x];
   const int n = S.n;
-  const int i = it.y * kImgThreads + threadIdx.x;
+  const int i = it.y * kOrderBlock + (blockIdx.x % kImgSplit) * kImgThreads + threadIdx.x;
   const int lane = threadIdx.x & 31;
   float bmin[6], bmax[6];
 #pragma unroll
@@ -341,7 +352,8 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
                    cudaStream_t st)
 {
   if (nitems <= 0) return;
-  k_images<<<nitems, kImgThreads, 0, st>>>(sys, items, xyz, q, perm, src_hi, src_lo, src64, boxes, prec, status);
+  k_images<<<nitems * kImgSplit, kImgThreads, 0, st>>>(sys, items, xyz, q, perm, src_hi, src_lo, src64, boxes, prec,
+                                                       status);
 }
 
 // Charge moments of the correction coefficients.  Thread t of a block prepares charge c0 + t
@@ -418,11 +430,11 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
         R u = accU[j], v = accV[j];
         for (int g = 0; g < gcount; ++g) {
           const R t = T[(size_t)g * P + idx];
-          u = cq[g0 + g] * t + u;
-          v = cqc[g0 + g] * t + v;
+          u = Num<R>::acc(u, cq[g0 + g], t);
+          v = Num<R>::acc(v, cqc[g0 + g], t);
         }
-        accU[j] = u;
-        accV[j] = v;
+        accU[j] = Num<R>::norm(u);
+        accV[j] = Num<R>::norm(v);
       }
     }
     __syncthreads();
@@ -514,25 +526,25 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
   R U = Num<R>::zero(), V = Num<R>::zero();
   double Rs = 0.0;
   if (idx < P) {
-    // two interleaved accumulators per moment, loads issued a step ahead
-    R U1 = Num<R>::zero(), V1 = Num<R>::zero();
+    // rows b = warp, warp + kCoefWarps, ... in ascending order, four rows' loads in flight
     int b = warp;
-    for (; b + kCoefWarps < S.mom_blocks; b += 2 * kCoefWarps) {
-      const R u0 = Num<R>::ld(base, (long long)b * mom_stride + idx);
-      const R v0 = Num<R>::ld(base, (long long)b * mom_stride + P + idx);
-      const R u1 = Num<R>::ld(base, (long long)(b + kCoefWarps) * mom_stride + idx);
-      const R v1 = Num<R>::ld(base, (long long)(b + kCoefWarps) * mom_stride + P + idx);
-      U = U + u0;
-      V = V + v0;
-      U1 = U1 + u1;
-      V1 = V1 + v1;
+    for (; b + 3 * kCoefWarps < S.mom_blocks; b += 4 * kCoefWarps) {
+      R u[4], v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        u[k] = Num<R>::ld(base, (long long)(b + k * kCoefWarps) * mom_stride + idx);
+        v[k] = Num<R>::ld(base, (long long)(b + k * kCoefWarps) * mom_stride + P + idx);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        U = U + u[k];
+        V = V + v[k];
+      }
     }
-    if (b < S.mom_blocks) {
+    for (; b < S.mom_blocks; b += kCoefWarps) {
       U = U + Num<R>::ld(base, (long long)b * mom_stride + idx);
       V = V + Num<R>::ld(base, (long long)b * mom_stride + P + idx);
     }
-    U = U + U1;
-    V = V + V1;
   }
   if (it.y == 0 && lane == 0)
     for (int b = warp; b < S.mom_blocks; b += kCoefWarps) Rs += base[(size_t)b * mom_stride + 2 * P];
@@ -672,11 +684,26 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __re
   if (j >= M) return;
   const double* row = sb + S.sb + (long long)j * P;
   R ph = Num<R>::zero(), dph = Num<R>::zero();
-  for (int i = lane; i < P; i += 32) {
-    const R b = Num<R>::ld(row, i);
-    ph = A[i] * b + ph;
-    dph = nA[i] * b + dph;
+  int i = lane;
+  for (; i + 96 < P; i += 128) {  // four row loads in flight ahead of the sums
+    const R b0 = Num<R>::ld(row, i), b1 = Num<R>::ld(row, i + 32);
+    const R b2 = Num<R>::ld(row, i + 64), b3 = Num<R>::ld(row, i + 96);
+    ph = Num<R>::acc(ph, A[i], b0);
+    dph = Num<R>::acc(dph, nA[i], b0);
+    ph = Num<R>::acc(ph, A[i + 32], b1);
+    dph = Num<R>::acc(dph, nA[i + 32], b1);
+    ph = Num<R>::acc(ph, A[i + 64], b2);
+    dph = Num<R>::acc(dph, nA[i + 64], b2);
+    ph = Num<R>::acc(ph, A[i + 96], b3);
+    dph = Num<R>::acc(dph, nA[i + 96], b3);
   }
+  for (; i < P; i += 32) {
+    const R b = Num<R>::ld(row, i);
+    ph = Num<R>::acc(ph, A[i], b);
+    dph = Num<R>::acc(dph, nA[i], b);
+  }
+  ph = Num<R>::norm(ph);
+  dph = Num<R>::norm(dph);
   for (int off = 16; off > 0; off >>= 1) {
     ph = ph + Num<R>::shfl(ph, off);
     dph = dph + Num<R>::shfl(dph, off);
