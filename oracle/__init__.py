@@ -42,6 +42,7 @@ class OracleParams(ctypes.Structure):
         ("coulomb_k", ctypes.c_double),
         ("dipole_form", ctypes.c_int),
         ("nthreads", ctypes.c_int),
+        ("image_rel", ctypes.c_double),
     ]
 
 
@@ -157,7 +158,8 @@ def fibonacci_pair(M: int) -> tuple[int, int]:
 
 
 def make_params(a=1.0, eps1=1.0, eps2=80.0, kappa=1.0, p=20, M=None, F1=None, F2=None, tau=0.1,
-                dy_rel=1e-5, coulomb_k=1.0 / (4.0 * math.pi), dipole_form=1, nthreads=0) -> OracleParams:
+                dy_rel=1e-5, coulomb_k=1.0 / (4.0 * math.pi), dipole_form=1, nthreads=0,
+                image_rel=0.0) -> OracleParams:
     if F2 is None:
         if M is None:
             M = 400
@@ -165,7 +167,8 @@ def make_params(a=1.0, eps1=1.0, eps2=80.0, kappa=1.0, p=20, M=None, F1=None, F2
     elif F1 is None:
         F1 = int(round(F2 * (math.sqrt(5.0) - 1.0) / 2.0))
     return OracleParams(float(a), float(eps1), float(eps2), float(kappa), int(p), int(F1), int(F2),
-                        float(tau), float(dy_rel), float(coulomb_k), int(dipole_form), int(nthreads))
+                        float(tau), float(dy_rel), float(coulomb_k), int(dipole_form), int(nthreads),
+                        float(image_rel))
 
 
 def S_n(n: int, mu: float) -> float:

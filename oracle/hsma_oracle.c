@@ -35,6 +35,12 @@
  *     (the central difference sits inside the integral over that sphere).
  *   - Energy: E_total = 1/2 sum_i q_i [ sum_{j != i} k q_j/(eps1 r_ij) + Phi_RF(x_i) ],
  *     E_RF = 1/2 sum_i q_i Phi_RF(x_i); Neumaier-compensated sums.
+ *   - Images only near the interface (a variant the paper motivates in Sec. 2.3:
+ *     the image terms matter for charges close to the interface): a charge with
+ *     r_i < image_rel R gets no Kelvin image and no line image, and its whole
+ *     reaction potential is the truncated series with the full M_n, i.e.
+ *     hat M'_{n,i} = M_n (c_i = -gamma in the notation below); image_rel = 0 is
+ *     the paper's method (every charge has its image).
  *   - dipole_form = 0 evaluates the three shells as literal point charges (eq.
  *     threeintegrals after quadrature); dipole_form = 1 evaluates the same
  *     difference (1/d_- - 1/d_+)/dy through the exact rewrite
@@ -62,6 +68,7 @@ typedef struct {
     double coulomb_k;  /* 1/(4 pi) in the paper's units */
     int dipole_form;   /* 0 literal shells, 1 fused rewrite */
     int nthreads;      /* OpenMP threads (<= 0: library default) */
+    double image_rel;  /* charges with r_i < image_rel R get no Kelvin image (0: every charge) */
 } oracle_params;
 
 /* ------------------------------------------------------------------------ */
@@ -179,6 +186,12 @@ int oracle_build(const oracle_params* P, int64_t n, const double* xyz, const dou
     for (int64_t i = 0; i < n; ++i) {
         const double* x = xyz + 3 * i;
         double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (P->image_rel > 0.0 && r < P->image_rel * a) {
+            /* no image: the charge's reaction potential is all in the series */
+            if (kel_xyz) { kel_xyz[3 * i] = 0.0; kel_xyz[3 * i + 1] = 0.0; kel_xyz[3 * i + 2] = 0.0; }
+            if (kel_q) kel_q[i] = 0.0;
+            continue;
+        }
         if (r == 0.0) {
             c0 += P->coulomb_k / P->eps1 * q[i] / a * (gamma - 0.5 * dbar);
             if (kel_xyz) { kel_xyz[3 * i] = 0.0; kel_xyz[3 * i + 1] = 0.0; kel_xyz[3 * i + 2] = 0.0; }
@@ -218,13 +231,15 @@ int oracle_build(const oracle_params* P, int64_t n, const double* xyz, const dou
                 const double* x = xyz + 3 * i;
                 double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
                 double pref = P->coulomb_k * q[i] / (P->eps1 * a);
+                int no_image = P->image_rel > 0.0 && r < P->image_rel * a;
                 if (r == 0.0) {
-                    /* limit r_K -> infinity: only n = 0, hat M'_0 = M_0 - gamma + dbar/2 */
-                    phi += pref * (Mn[0] - gamma + 0.5 * dbar);
+                    /* limit r_K -> infinity: only n = 0, hat M'_0 = M_0 - gamma + dbar/2
+                       (M_0 for a charge without image) */
+                    phi += pref * (no_image ? Mn[0] : Mn[0] - gamma + 0.5 * dbar);
                     continue;
                 }
                 double rK = a * a / r;
-                double corr_i = dbar * (Rtau - rK) / (2.0 * rK);
+                double corr_i = no_image ? -gamma : dbar * (Rtau - rK) / (2.0 * rK);
                 double t = (x[0] * y[0] + x[1] * y[1] + x[2] * y[2]) / (r * rho);
                 double u = rho / rK; /* (|y| / r_K,i) */
                 double Pn = 1.0, Pnm1 = 0.0, un = 1.0;

@@ -45,6 +45,10 @@ MUTANTS = {
                                   "er[k] += strength * (up[k] / (dp * dp * dp) - um[k] / (dm * dm * dm));"),
     "field_dipole_fused_shell": ("er[k] += D * (yh[k] / dm3 + up[k] * f);", "er[k] += D * (yh[k] / dp3 + up[k] * f);"),
     "field_dipole_fused_factor": ("double f = 2.0 * (Rtau - xy)", "double f = (Rtau - xy)"),
+    # near-interface-only image variant
+    "variant_corr_sign": ("double corr_i = no_image ? -gamma :", "double corr_i = no_image ? gamma :"),
+    "variant_centre": ("phi += pref * (no_image ? Mn[0] : Mn[0] - gamma + 0.5 * dbar);",
+                       "phi += pref * (no_image ? Mn[0] - gamma : Mn[0] - gamma + 0.5 * dbar);"),
 }
 
 
@@ -126,6 +130,19 @@ def _checks():
                        xyz[0], 1e-4)
     if not np.linalg.norm(E[0] - ref) <= 1e-9 * np.linalg.norm(ref):
         failed.append("kirkwood_field")
+    # near-interface-only images: a charge without image is the truncated Kirkwood series, and a
+    # centre charge without image is Born / Debye-Hueckel
+    P = oracle.make_params(a=1.1, eps1=2.0, eps2=80.0, kappa=1.5, p=10, M=4000, tau=0.1, image_rel=0.7)
+    xyz = np.array([[0.1, -0.2, 0.3], [-0.25, 0.05, 0.2]])
+    q = np.array([1.0, -0.5])
+    r = oracle.hsma(P, xyz, q)
+    ref = [sum(q[j] * kirkwood_rf(xyz[i], xyz[j], 1.1, 2.0, 80.0, 1.5, nmax=10) for j in range(2)) for i in range(2)]
+    if not np.allclose(r["phi_rf"], ref, rtol=1e-9, atol=1e-13):
+        failed.append("variant_series")
+    P = oracle.make_params(a=1.3, eps1=2.0, eps2=80.0, kappa=5.0, p=6, M=400, image_rel=0.5)
+    e = oracle.hsma(P, np.zeros((1, 3)), np.array([1.0]))["E_rf"]
+    if not abs(e - 0.5 * K4PI / 1.3 * (1.0 / (80.0 * (1.0 + 6.5)) - 0.5)) < 1e-9 * abs(e):
+        failed.append("variant_born")
     return failed
 
 
