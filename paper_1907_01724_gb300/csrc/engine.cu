@@ -593,12 +593,12 @@ void Engine::issue_pot()
   cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), stream);
   if (!L.it4.empty()) {
     cudaEventRecordWithFlags(ev_pair0, stream, cudaEventRecordExternal);
+    const PairWork all{it4_d, (int)L.it4.size(), ctr_pairs_d}, none{nullptr, 0, nullptr};
     if (prec == HSMA_FP64)
-      launch_pairs_f64(L.pair_grid, sys_d, it4_d, (int)L.it4.size(), ctr_pairs_d, src64_d, surf64a_d, surf64b_d,
-                       part64_d, stream);
+      launch_pairs_f64(L.pair_grid, sys_d, all, none, src64_d, surf64a_d, surf64b_d, part64_d, stream);
     else
-      launch_pairs_f32(L.cfg, L.pair_grid, sys_d, it4_d, (int)L.it4.size(), ctr_pairs_d, srchi_d, srclo_d, surfa_d,
-                       surfb_d, boxes_d, part_d, stream);
+      launch_pairs_f32(L.cfg, L.pair_grid, sys_d, all, none, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, part_d,
+                       stream);
     cudaEventRecordWithFlags(ev_pair1, stream, cudaEventRecordExternal);
   }
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
@@ -608,27 +608,24 @@ void Engine::issue_pot()
 
 int Engine::pot_launch_count() const { return (L.it4.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1); }
 
-void Engine::launch_pair_items(const int4* items, int nitems, unsigned int* counter, int grid, cudaStream_t st,
-                               bool reset)
+void Engine::launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t st)
 {
-  if (nitems <= 0) return;
-  if (reset) cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
+  if (w1.nitems <= 0 && w2.nitems <= 0) return;
   if (prec == HSMA_FP64)
-    launch_pairs_f64(grid, sys_d, items, nitems, counter, src64_d, surf64a_d, surf64b_d, part64_d, st);
+    launch_pairs_f64(grid, sys_d, w1, w2, src64_d, surf64a_d, surf64b_d, part64_d, st);
   else
-    launch_pairs_f32(L.cfg, grid, sys_d, items, nitems, counter, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, part_d,
-                     st);
+    launch_pairs_f32(L.cfg, grid, sys_d, w1, w2, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, part_d, st);
 }
 
 // Build and potentials in one graph.  The real/Kelvin pair items need only the records, so they
 // start on the second stream right after k_images, beside the moments -> coefficients ->
 // surface chain, with their grid capped at kOverlapShare of the pair slots so that the chain's
-// blocks keep room.  After the chain, the main stream runs the surface items and then a second,
-// full-grid launch on the same real/Kelvin item list and work counter, which drains whatever
-// the first launch has not taken (each item is taken once, by whichever CTA gets it).
+// blocks keep room.  After the chain, the main stream runs one full-grid launch that takes the
+// surface items and then drains whatever real/Kelvin items the first launch has not taken,
+// from the same list and work counter (each item is taken once, by whichever CTA gets it).
 //   side:  k_order_* -> k_images -> k_pairs (real/Kelvin, capped grid)
-//   main:  k_moments -> k_coef_reduce -> k_surface_mat -> [wait records] k_pairs (surface)
-//          -> k_pairs (real/Kelvin, drain)
+//   main:  k_moments -> k_coef_reduce -> k_surface_mat -> [wait records] k_pairs (surface,
+//          then real/Kelvin)
 //   join:  k_reduce
 constexpr double kOverlapShare = 0.5;
 
@@ -644,7 +641,7 @@ void Engine::issue_fused()
   const int occ = prec == HSMA_FP64 ? std::max(occ_f64, 1) : std::max(occ_f32[L.cfg], 1);
   const int slots = num_sms * occ;
   const int grid_rk = std::max(1, std::min(L.nRK, (int)(kOverlapShare * slots)));
-  const int grid_s = std::max(1, std::min(nS, slots));
+  const int grid_s = std::max(1, std::min(nS + L.nRK, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);
   launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, key_d, hist_d, offs_d, cursor_d, perm_d, iperm_d,
@@ -655,16 +652,17 @@ void Engine::issue_fused()
   // waits for before its draining launch
   cudaMemsetAsync(ctr_pairs2_d, 0, sizeof(unsigned int), side);
   cudaEventRecord(ev_img, side);
-  launch_pair_items(it4x_d, L.nRK, ctr_pairs2_d, grid_rk, side, false);
+  const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d}, srf{it4x_d + L.nRK, nS, ctr_pairs_d}, none{nullptr, 0, nullptr};
+  launch_pair_items(rk, none, grid_rk, side);
   cudaEventRecord(ev_join, side);
   launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, tables(), prec, mom_d, L.mom_stride, stream);
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
   launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
                  surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
+  cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), stream);
   cudaStreamWaitEvent(stream, ev_img, 0);
-  launch_pair_items(it4x_d + L.nRK, nS, ctr_pairs_d, grid_s, stream, true);
-  launch_pair_items(it4x_d, L.nRK, ctr_pairs2_d, std::max(1, std::min(L.nRK, slots)), stream, false);
+  launch_pair_items(srf, rk, grid_s, stream);
   cudaStreamWaitEvent(stream, ev_join, 0);
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
                 phic_d, phir_d, phit_d, epart_d, energy_d, ctr_red_d, status_d, stream);
@@ -673,8 +671,7 @@ void Engine::issue_fused()
 int Engine::fused_launch_count() const
 {
   if (L.itord.empty()) return build_launch_count() + pot_launch_count();
-  return build_launch_count() + (L.nRK > 0 ? 2 : 0) + ((int)L.it4x.size() > L.nRK ? 1 : 0) +
-         (L.it5.empty() ? 0 : 1);
+  return build_launch_count() + (L.nRK > 0 ? 1 : 0) + (L.it4x.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1);
 }
 
 int Engine::run_graph(cudaGraphExec_t* g, void (Engine::*issue)())

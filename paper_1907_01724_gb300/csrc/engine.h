@@ -172,8 +172,7 @@ class Engine {
   void issue_pot();
   void issue_field();
   void issue_fused();
-  void launch_pair_items(const int4* items, int nitems, unsigned int* counter, int grid, cudaStream_t st,
-                         bool reset);
+  void launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t st);
   int fused_launch_count() const;
   int build_launch_count() const;
   int pot_launch_count() const;

@@ -143,12 +143,19 @@ int pairs_f32_occupancy(int cfg);
 int pairs_f64_occupancy();
 constexpr int kF64TargetsPerBlock = 128;
 constexpr int kReduceTargetsPerBlock = 32;
-void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
-                      const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
-                      const float4* boxes, float2* part, cudaStream_t st);
-void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
-                      const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, double* part64,
-                      cudaStream_t st);
+// A list of pair work items pulled through an atomic counter (zero before the first launch that
+// uses it); counter == nullptr: no list.
+struct PairWork {
+  const int4* items;
+  int nitems;
+  unsigned int* counter;
+};
+// Persistent pair-sum launches: each CTA takes items of w1 until it is exhausted, then of w2.
+void launch_pairs_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
+                      const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
+                      float2* part, cudaStream_t st);
+void launch_pairs_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, const dbl4* src64,
+                      const dbl4* surf64_a, const double* surf64_b, double* part64, cudaStream_t st);
 // Reduce the pair partials of the launched items to potentials and energies; the energies of
 // system sel[r] are summed from the launch items sel_rng[r] = (first, count), ranges ascending
 // and contiguous; counter[r] (zero before the launch, zero after it) counts r's finished items.

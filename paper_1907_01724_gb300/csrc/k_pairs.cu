@@ -76,6 +76,28 @@ __device__ __forceinline__ ChunkInfo decode_chunk(const SysDev& S, int c)
   return ci;
 }
 
+// Next work item of a persistent CTA (thread 0): items of w1 first, then, when w1 is exhausted,
+// items of w2 (if any).  list = 0 or 1 names the list of the item, 2 means no work left.
+__device__ __forceinline__ void next_pair_item(const PairWork& w1, const PairWork& w2, int list, int& s_item,
+                                               int& s_list)
+{
+  int v = 0;
+  if (list == 0) {
+    v = (int)atomicAdd(w1.counter, 1u);
+    if (v >= w1.nitems) list = 1;
+  }
+  if (list == 1) {
+    if (w2.counter) {
+      v = (int)atomicAdd(w2.counter, 1u);
+      if (v >= w2.nitems) list = 2;
+    } else {
+      list = 2;
+    }
+  }
+  s_item = v;
+  s_list = list;
+}
+
 // ---------------------------------------------------------------------------------------
 #include "k_pairs_f32.cuh"
 
@@ -119,15 +141,14 @@ int pairs_f32_occupancy(int cfg)
   return b;
 }
 
-void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
-                      const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
-                      const float4* boxes, float2* part, cudaStream_t st)
+void launch_pairs_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
+                      const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
+                      float2* part, cudaStream_t st)
 {
   switch (pair_kernel_of(cfg)) {
 #define HSMA_CFG_LAUNCH(i, nt, k)                                                                          \
   case i:                                                                                                  \
-    k_pairs_f32<nt, k><<<grid, nt, 0, st>>>(sys, items, nitems, counter, src_hi, src_lo, surf_a, surf_b, boxes, \
-                                            part);                                                             \
+    k_pairs_f32<nt, k><<<grid, nt, 0, st>>>(sys, w1, w2, src_hi, src_lo, surf_a, surf_b, boxes, part); \
     break;
     HSMA_PAIR_CONFIGS(HSMA_CFG_LAUNCH)
 #undef HSMA_CFG_LAUNCH
@@ -139,25 +160,25 @@ void launch_pairs_f32(int cfg, int grid, const SysDev* sys, const int4* items, i
 // FP64 comparator path: one target per thread, plain staged loads.
 constexpr int kF64Threads = kF64TargetsPerBlock;
 
-__global__ __launch_bounds__(kF64Threads) void k_pairs_f64(const SysDev* __restrict__ sys,
-                                                           const int4* __restrict__ items, int nitems,
-                                                           unsigned int* __restrict__ counter,
-                                                           const dbl4* __restrict__ src64,
+__global__ __launch_bounds__(kF64Threads) void k_pairs_f64(const SysDev* __restrict__ sys, PairWork w1,
+                                                           PairWork w2, const dbl4* __restrict__ src64,
                                                            const dbl4* __restrict__ surf64_a,
                                                            const double* __restrict__ surf64_b,
                                                            double* __restrict__ part64)
 {
   __shared__ dbl4 shA[kF64Threads];
   __shared__ double shB[kF64Threads];
-  __shared__ int s_item;
+  __shared__ int s_item, s_list;
   const int tid = threadIdx.x;
+  int list = 0;
   for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
+    if (tid == 0) next_pair_item(w1, w2, list, s_item, s_list);
     __syncthreads();
     const int item = s_item;
+    list = s_list;
     __syncthreads();
-    if (item >= nitems) break;
-    const int4 it = items[item];
+    if (list > 1) break;
+    const int4 it = (list == 0 ? w1.items : w2.items)[item];
     const SysDev& S = sys[it.x];
     const int n = S.n;
     const int i = it.y * kF64Threads + tid;
@@ -217,11 +238,10 @@ int pairs_f64_occupancy()
   return b;
 }
 
-void launch_pairs_f64(int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
-                      const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, double* part64,
-                      cudaStream_t st)
+void launch_pairs_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, const dbl4* src64,
+                      const dbl4* surf64_a, const double* surf64_b, double* part64, cudaStream_t st)
 {
-  k_pairs_f64<<<grid, kF64Threads, 0, st>>>(sys, items, nitems, counter, src64, surf64_a, surf64_b, part64);
+  k_pairs_f64<<<grid, kF64Threads, 0, st>>>(sys, w1, w2, src64, surf64_a, surf64_b, part64);
 }
 
 // ---------------------------------------------------------------------------------------

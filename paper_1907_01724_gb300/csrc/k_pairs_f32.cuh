@@ -9,8 +9,7 @@
 // form s = (x_hi - y_hi) + (x_lo - y_lo), r^2 = |s|^2, accurate to FP32 rounding at any
 // distance (a charge next to its own Kelvin image).  The decision is uniform over the warp.
 template <int NT, int K>
-__global__ __launch_bounds__(NT) void k_pairs_f32(const SysDev* __restrict__ sys, const int4* __restrict__ items,
-                                                  int nitems, unsigned int* __restrict__ counter,
+__global__ __launch_bounds__(NT) void k_pairs_f32(const SysDev* __restrict__ sys, PairWork w1, PairWork w2,
                                                   const float4* __restrict__ src_hi,
                                                   const float4* __restrict__ src_lo,
                                                   const float4* __restrict__ surf_a,
@@ -20,16 +19,18 @@ __global__ __launch_bounds__(NT) void k_pairs_f32(const SysDev* __restrict__ sys
   static_assert(NT % kBox == 0, "a staged tile holds whole source boxes");
   __shared__ __align__(16) float4 shA[2][NT];
   __shared__ __align__(16) float4 shB[2][NT];
-  __shared__ int s_item;
+  __shared__ int s_item, s_list;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int list = 0;
 
   for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
+    if (tid == 0) next_pair_item(w1, w2, list, s_item, s_list);
     __syncthreads();
     const int item = s_item;
+    list = s_list;
     __syncthreads();
-    if (item >= nitems) break;
-    const int4 it = items[item];
+    if (list > 1) break;
+    const int4 it = (list == 0 ? w1.items : w2.items)[item];
     const SysDev& S = sys[it.x];
     const int n = S.n;
     const int t0 = it.y * (NT * K);

@@ -38,6 +38,30 @@
 
 namespace hsma {
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start while its
+// predecessor in the stream is finishing; it calls grid_dependency_wait() before it reads
+// anything the predecessor writes (a no-op when launched normally).  A predecessor lets its
+// dependent launch early with allow_dependents().
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args)
+{
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------------------------------
 // Per-system scalars, tables and the quadrature grid.  Block s handles system s (thread 0:
 // scalars and M_n; all threads: its Fibonacci points); block 0 also fills the tables.
@@ -368,6 +392,7 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
                                                          Tables tab, double* __restrict__ mom, int mom_stride, int G)
 {
   extern __shared__ double sm[];
+  allow_dependents();
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int n = S.n, P = S.P, p = S.p;
@@ -517,6 +542,8 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
 {
   __shared__ R su[kCoefWarps][kCoefChunk], sv[kCoefWarps][kCoefChunk];
   __shared__ double sr[kCoefWarps];
+  allow_dependents();
+  grid_dependency_wait();  // the moment rows of k_moments
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P;
@@ -581,9 +608,10 @@ void launch_coef_reduce(const SysDev* sys, const int2* items, int nitems, const 
 {
   if (nitems <= 0) return;
   if (prec == HSMA_FP64)
-    k_coef_reduce<double><<<nitems, kCoefWarps * 32, 0, st>>>(sys, items, mom, mom_stride, Mn, coef, coef2, r0);
+    launch_pdl(k_coef_reduce<double>, nitems, kCoefWarps * 32, 0, st, sys, items, mom, mom_stride, Mn, coef, coef2,
+               r0);
   else
-    k_coef_reduce<df><<<nitems, kCoefWarps * 32, 0, st>>>(sys, items, mom, mom_stride, Mn, coef, coef2, r0);
+    launch_pdl(k_coef_reduce<df>, nitems, kCoefWarps * 32, 0, st, sys, items, mom, mom_stride, Mn, coef, coef2, r0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -665,6 +693,7 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __re
                                                               double2* __restrict__ surfqd, int prec)
 {
   extern __shared__ double sm[];
+  grid_dependency_wait();  // the coefficients of k_coef_reduce
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P, M = S.M;
@@ -726,6 +755,7 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface(const SysDev* __restri
                                                           double2* __restrict__ surfqd, int prec)
 {
   extern __shared__ double sm[];
+  grid_dependency_wait();  // the coefficients of k_coef_reduce
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P, p = S.p, M = S.M;
@@ -784,20 +814,20 @@ void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, 
   if (sb) {
     const size_t smem = 2 * (size_t)maxP * sizeof(double);
     if (prec == HSMA_FP64)
-      k_surface_mat<double><<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, coef2, sb, surf_a, surf_b,
-                                                                surf64_a, surf64_b, surfx, surfqd, prec);
+      launch_pdl(k_surface_mat<double>, nitems, kSurfThreads, smem, st, sys, items, coef, coef2, sb, surf_a, surf_b,
+                 surf64_a, surf64_b, surfx, surfqd, prec);
     else
-      k_surface_mat<df><<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, coef2, sb, surf_a, surf_b, surf64_a,
-                                                            surf64_b, surfx, surfqd, prec);
+      launch_pdl(k_surface_mat<df>, nitems, kSurfThreads, smem, st, sys, items, coef, coef2, sb, surf_a, surf_b,
+                 surf64_a, surf64_b, surfx, surfqd, prec);
     return;
   }
   const size_t smem = (size_t)maxP * sizeof(double);
   if (prec == HSMA_FP64)
-    k_surface<double><<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, tab, surf_a, surf_b, surf64_a, surf64_b,
-                                                          surfx, surfqd, prec);
+    launch_pdl(k_surface<double>, nitems, kSurfThreads, smem, st, sys, items, coef, tab, surf_a, surf_b, surf64_a,
+               surf64_b, surfx, surfqd, prec);
   else
-    k_surface<df><<<nitems, kSurfThreads, smem, st>>>(sys, items, coef, tab, surf_a, surf_b, surf64_a, surf64_b,
-                                                      surfx, surfqd, prec);
+    launch_pdl(k_surface<df>, nitems, kSurfThreads, smem, st, sys, items, coef, tab, surf_a, surf_b, surf64_a,
+               surf64_b, surfx, surfqd, prec);
 }
 
 template <class R>
