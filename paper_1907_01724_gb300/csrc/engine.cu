@@ -314,7 +314,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_inv_np1 = take(8 * (size_t)(L.pmax + 1));
   L.o_rec_a2 = take(8 * (size_t)ntri);
   L.o_rec_b2 = take(8 * (size_t)ntri);
-  L.o_sect2 = take(8 * (size_t)(L.pmax + 1));
+  L.o_sect2 = take(8 * 3 * (size_t)(L.pmax + 1));  // sect2, then the Legendre tables
   L.o_xyz = take(24 * L.totN);
   L.o_q = take(8 * L.totN);
   if (prec == HSMA_FP64) {
@@ -554,6 +554,8 @@ Tables Engine::tables() const
   t.rec_a2 = rec_a2_d;
   t.rec_b2 = rec_b2_d;
   t.sect2 = sect2_d;
+  t.leg_a2 = sect2_d + (L.pmax + 1);
+  t.leg_b2 = sect2_d + 2 * (L.pmax + 1);
   t.pmax = L.pmax;
   return t;
 }
@@ -1264,7 +1266,7 @@ int Engine::delta_batch(const std::vector<DeltaReq>& reqs, double* de_host)
   CK(cudaMemcpyAsync(ditems_d, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(dreqit_d, ranges.data(), sizeof(int2) * ranges.size(), cudaMemcpyHostToDevice, stream));
   launch_delta(sys_d, ditems_d, (int)items.size(), dreqit_d, dreq_d, (int)reqs.size(), xyz_d, q_d, perm_d, iperm_d,
-               srchi_d, srclo_d, src64_d, surfx_d, surfqd_d, vsurf_d, Mn_d, inv_np1_d, dpart_d, de_d, ctr_delta_d,
+               srchi_d, srclo_d, src64_d, surfx_d, surfqd_d, vsurf_d, Mn_d, tables(), dpart_d, de_d, ctr_delta_d,
                status_d, stream);
   CK(cudaGetLastError());
   launches += 1;

@@ -93,6 +93,8 @@ struct Tables {
   const float2* rec_a2;   // the same three tables as double-float pairs (hi, lo)
   const float2* rec_b2;
   const float2* sect2;
+  const float2* leg_a2;   // Legendre recurrence (2n+1)/(n+1) and n/(n+1), n <= pmax, as (hi, lo)
+  const float2* leg_b2;   // (stored after sect2 in the same array)
   int pmax;
 };
 
@@ -195,7 +197,7 @@ void launch_surface_potentials(const SysDev* sys, const int2* items, int nitems,
 void launch_delta(const SysDev* sys, const int4* items, int nitems, const int2* req_items, const DeltaReq* reqs,
                   int nreq, const double* xyz, const double* q, const int* perm, const int* iperm,
                   const float4* src_hi, const float4* src_lo, const dbl4* src64, const dbl4* surfx,
-                  const double2* surfqd, const double2* vsurf, const double* Mn, const double* inv_np1, double* dpart,
+                  const double2* surfqd, const double2* vsurf, const double* Mn, Tables tab, double* dpart,
                   double* de, unsigned int* counter, int* status, cudaStream_t st);
 void launch_move(const SysDev* sys, const int2* surf_items, int n_surf_items, const DeltaReq* reqs, int nreq,
                  Tables tab, int maxP, double* xyz, const double* q, const double* Mn, double* coef, float2* coef2,

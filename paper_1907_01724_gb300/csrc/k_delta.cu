@@ -19,6 +19,7 @@
 // range of work items whose partial sums are added in a fixed order by the last block.
 #include <math.h>
 
+#include "df64.cuh"
 #include "hsma_internal.cuh"
 
 namespace hsma {
@@ -152,6 +153,71 @@ __device__ __forceinline__ void charge_series(const SysDev& S, const double* __r
   dphi = pref * sd * S.inv_Rt;
 }
 
+// The same series on the FP32 path, in double-float arithmetic (FP64 runs at ~1/73 of FP32 on
+// this GPU, and the series is ~10 FP64 operations per order and point): per request the block
+// prepares, for the new (side 0) and the old (side 1) position, a_n = k q/(eps1 a)
+// (M_n - gamma - c) u^n and b_n = n a_n (u = r R_tau/a^2) and the unit vector xhat; per point
+// the Legendre recurrence in t = xhat.yhat and the sums run in (hi, lo) pairs.
+struct SeriesShared {
+  df a[2][HSMA_P_MAX + 1];
+  df b[2][HSMA_P_MAX + 1];
+  double hat[2][3];
+};
+
+// All threads of the block call it (it ends with __syncthreads).
+__device__ __forceinline__ void series_prepare(const SysDev& S, const double* __restrict__ Mn, double xn, double yn,
+                                               double zn, double xo, double yo, double zo, double q,
+                                               SeriesShared& sh)
+{
+  const int np = S.p + 1;
+  const int t = threadIdx.x;
+  if (t < 2 * np) {
+    const int side = t / np, n = t - side * np;
+    const double x = side ? xo : xn, y = side ? yo : yn, z = side ? zo : zn;
+    const double r = sqrt(x * x + y * y + z * z);
+    const bool centre = r <= kCentreRel * S.a;
+    const double c = S.dbar * (S.Rt_a * r * S.inv_a - 1.0) * 0.5;
+    const double u = r * S.Rt_a * S.inv_a;
+    double un = 1.0, base = u;
+    for (int e = n; e; e >>= 1) {  // u^n by squaring
+      if (e & 1) un *= base;
+      base *= base;
+    }
+    const double an = S.kc_a * q * (Mn[S.mn + n] - S.gam - c) * (centre ? (n == 0 ? 1.0 : 0.0) : un);
+    sh.a[side][n] = df_from_double(an);
+    sh.b[side][n] = df_from_double((double)n * an);
+    if (n == 0) {
+      const double inv = centre ? 0.0 : 1.0 / r;
+      sh.hat[side][0] = x * inv;
+      sh.hat[side][1] = y * inv;
+      sh.hat[side][2] = z * inv;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void series_eval(const SysDev& S, const SeriesShared& sh, int side, const dbl4& yl,
+                                            const Tables& tab, double& phi, double& dphi)
+{
+  const double tc = (sh.hat[side][0] * yl.x + sh.hat[side][1] * yl.y + sh.hat[side][2] * yl.z) * S.inv_Rt;
+  const df t = df_from_double(tc);
+  df P0 = df_make(1.f, 0.f), P1 = t;
+  df s = sh.a[side][0], sd = df_make(0.f, 0.f);
+  for (int n = 1; n <= S.p; ++n) {
+    s = df_acc(s, sh.a[side][n], P1);
+    sd = df_acc(sd, sh.b[side][n], P1);
+    if (n < S.p) {
+      const float2 la = tab.leg_a2[n], lb = tab.leg_b2[n];
+      const df A = df_make(la.x, la.y) * t;
+      const df P2 = df_mul_sub(A, P1, df_make(lb.x, lb.y), P0);
+      P0 = P1;
+      P1 = P2;
+    }
+  }
+  phi = df_to_double(df_norm(s));
+  dphi = df_to_double(df_norm(sd)) * S.inv_Rt;
+}
+
 // Work item: (request, kind 0 = rows / 1 = surface, block)
 __global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restrict__ sys, const int4* __restrict__ items,
                                                          int nitems, const int2* __restrict__ req_items,
@@ -163,13 +229,15 @@ __global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restric
                                                          const dbl4* __restrict__ src64, const dbl4* __restrict__ surfx,
                                                          const double2* __restrict__ surfqd,
                                                          const double2* __restrict__ vsurf,
-                                                         const double* __restrict__ Mn,
-                                                         const double* __restrict__ inv_np1, double* __restrict__ dpart,
-                                                         double* __restrict__ de, unsigned int* __restrict__ counter,
-                                                         int* __restrict__ status)
+                                                         const double* __restrict__ Mn, Tables tab,
+                                                         double* __restrict__ dpart, double* __restrict__ de,
+                                                         unsigned int* __restrict__ counter, int* __restrict__ status)
 {
   __shared__ double red[kDeltaThreads / 32];
   __shared__ bool last;
+  __shared__ SeriesShared ssh;
+  __shared__ Image s_in, s_io;
+  const double* inv_np1 = tab.inv_np1;
   const int4 it = items[blockIdx.x];
   const DeltaReq R = reqs[it.x];
   const SysDev& S = sys[R.sys];
@@ -179,8 +247,13 @@ __global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restric
   double acc = 0.0;
   const int idx = it.z * kDeltaThreads + threadIdx.x;
   if (it.y == 0) {
-    const Image In = kelvin_image(S, xn, yn, zn, qk);
-    const Image Io = kelvin_image(S, xo, yo, zo, qk);
+    // the moved charge's images (FP64), once per block
+    if (threadIdx.x == 0) {
+      s_in = kelvin_image(S, xn, yn, zn, qk);
+      s_io = kelvin_image(S, xo, yo, zo, qk);
+    }
+    __syncthreads();
+    const Image In = s_in, Io = s_io;
     if (blockIdx.x == req_items[it.x].x && threadIdx.x == 0) {
       const double rn2 = xn * xn + yn * yn + zn * zn;
       if (!(rn2 < S.a * S.a) || !isfinite(rn2)) atomicOr(status, kStBadMove);
@@ -231,6 +304,8 @@ __global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restric
       }
     }
   } else {
+    const bool dfs = S.prec != HSMA_FP64;
+    if (dfs) series_prepare(S, Mn, xn, yn, zn, xo, yo, zo, qk, ssh);
     const int l = idx;
     if (l < S.M) {
       const dbl4 yl = surfx[S.surf + l];
@@ -239,8 +314,13 @@ __global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restric
       double g0n, g1n, g0o, g1o, pn, dpn, po, dpo;
       surf_kernels(S, xn, yn, zn, yl, g0n, g1n);
       surf_kernels(S, xo, yo, zo, yl, g0o, g1o);
-      charge_series(S, Mn, inv_np1, xn, yn, zn, qk, yl, pn, dpn);
-      charge_series(S, Mn, inv_np1, xo, yo, zo, qk, yl, po, dpo);
+      if (dfs) {
+        series_eval(S, ssh, 0, yl, tab, pn, dpn);
+        series_eval(S, ssh, 1, yl, tab, po, dpo);
+      } else {
+        charge_series(S, Mn, inv_np1, xn, yn, zn, qk, yl, pn, dpn);
+        charge_series(S, Mn, inv_np1, xo, yo, zo, qk, yl, po, dpo);
+      }
       const double w4 = yl.w / (4.0 * kPi);
       const double dQ0 = w4 * (dpn - dpo), dD = w4 * (pn - po);
       const double dV0 = qk * (g0n - g0o), dV1 = qk * (g1n - g1o);
@@ -331,24 +411,32 @@ __device__ __forceinline__ void box_grow(float4* box, float x, float y, float z)
 __global__ __launch_bounds__(256) void k_move_surface(const SysDev* __restrict__ sys, const int2* __restrict__ items,
                                                       const DeltaReq* __restrict__ reqs, const double* __restrict__ xyz,
                                                       const double* __restrict__ q, const double* __restrict__ Mn,
-                                                      const double* __restrict__ inv_np1,
-                                                      const dbl4* __restrict__ surfx, double2* __restrict__ surfqd,
+                                                      Tables tab, const dbl4* __restrict__ surfx,
+                                                      double2* __restrict__ surfqd,
                                                       double2* __restrict__ vsurf, int have_v,
                                                       float4* __restrict__ surf_a, float4* __restrict__ surf_b,
                                                       dbl4* __restrict__ surf64_a, double* __restrict__ surf64_b)
 {
+  __shared__ SeriesShared ssh;
   const int2 it = items[blockIdx.x];  // (request, block)
   const DeltaReq R = reqs[it.x];
   const SysDev& S = sys[R.sys];
-  const int l = it.y * 256 + threadIdx.x;
-  if (l >= S.M) return;
   const long long kk = S.chg + R.k;
   const double xo = xyz[3 * kk], yo = xyz[3 * kk + 1], zo = xyz[3 * kk + 2], qk = q[kk];
+  const bool dfs = S.prec != HSMA_FP64;
+  if (dfs) series_prepare(S, Mn, R.x, R.y, R.z, xo, yo, zo, qk, ssh);
+  const int l = it.y * 256 + threadIdx.x;
+  if (l >= S.M) return;
   const long long o = S.surf + l;
   const dbl4 yl = surfx[o];
   double pn, dpn, po, dpo;
-  charge_series(S, Mn, inv_np1, R.x, R.y, R.z, qk, yl, pn, dpn);
-  charge_series(S, Mn, inv_np1, xo, yo, zo, qk, yl, po, dpo);
+  if (dfs) {
+    series_eval(S, ssh, 0, yl, tab, pn, dpn);
+    series_eval(S, ssh, 1, yl, tab, po, dpo);
+  } else {
+    charge_series(S, Mn, tab.inv_np1, R.x, R.y, R.z, qk, yl, pn, dpn);
+    charge_series(S, Mn, tab.inv_np1, xo, yo, zo, qk, yl, po, dpo);
+  }
   const double w4 = yl.w / (4.0 * kPi);
   double2 QD = surfqd[o];
   QD.x += w4 * (dpn - dpo);
@@ -477,13 +565,12 @@ void launch_surface_potentials(const SysDev* sys, const int2* items, int nitems,
 void launch_delta(const SysDev* sys, const int4* items, int nitems, const int2* req_items, const DeltaReq* reqs,
                   int nreq, const double* xyz, const double* q, const int* perm, const int* iperm,
                   const float4* src_hi, const float4* src_lo, const dbl4* src64, const dbl4* surfx,
-                  const double2* surfqd, const double2* vsurf, const double* Mn, const double* inv_np1, double* dpart,
+                  const double2* surfqd, const double2* vsurf, const double* Mn, Tables tab, double* dpart,
                   double* de, unsigned int* counter, int* status, cudaStream_t st)
 {
   if (nitems <= 0) return;
   k_delta<<<nitems, kDeltaThreads, 0, st>>>(sys, items, nitems, req_items, reqs, nreq, xyz, q, perm, iperm, src_hi,
-                                            src_lo, src64, surfx, surfqd, vsurf, Mn, inv_np1, dpart, de, counter,
-                                            status);
+                                            src_lo, src64, surfx, surfqd, vsurf, Mn, tab, dpart, de, counter, status);
 }
 
 void launch_move(const SysDev* sys, const int2* surf_items, int n_surf_items, const DeltaReq* reqs, int nreq,
@@ -494,7 +581,7 @@ void launch_move(const SysDev* sys, const int2* surf_items, int n_surf_items, co
 {
   if (nreq <= 0) return;
   if (n_surf_items > 0)
-    k_move_surface<<<n_surf_items, 256, 0, st>>>(sys, surf_items, reqs, xyz, q, Mn, tab.inv_np1, surfx, surfqd,
+    k_move_surface<<<n_surf_items, 256, 0, st>>>(sys, surf_items, reqs, xyz, q, Mn, tab, surfx, surfqd,
                                                  vsurf, have_v, surf_a, surf_b, surf64_a, surf64_b);
   k_move_charge<<<nreq, 256, 2 * (size_t)maxP * sizeof(double), st>>>(sys, reqs, tab, xyz, q, Mn,
                                                                      coef, coef2, r0, iperm, src_hi, src_lo, src64,

@@ -250,28 +250,31 @@ void launch_pairs_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, con
 // block reductions; the last block of a system to finish (counter[r] per launch-local system
 // r, reset by that block) sums the system's block partials in a fixed order.
 constexpr int kRedLanes = 8;
-// Sum of the (hi, lo) partials of chunks k0, k0 + kRedLanes, ... < k1 in ascending order; the
-// loads are issued four at a time ahead of the additions (a plain loop would wait one L2 round
-// trip per chunk).
-__device__ __forceinline__ df sum_chunks(const float2* __restrict__ b, long long n, int k0, int k1)
+// Sums of the (hi, lo) partials of this lane's chunks k = sub, sub + kRedLanes, ... < nch in
+// ascending order: the real chunks (k < ncr) into c, the others into r.  Eight chunks' loads are
+// issued ahead of their additions, so a target's partials cost one or two L2 round trips
+// instead of one per chunk.
+__device__ __forceinline__ void sum_chunks(const float2* __restrict__ b, long long n, int sub, int ncr, int nch,
+                                           df& c, df& r)
 {
-  df acc = df_make(0.f, 0.f);
-  int k = k0;
-  for (; k + 3 * 8 < k1; k += 4 * 8) {
-    const float2 v0 = b[(long long)k * n], v1 = b[(long long)(k + 8) * n];
-    const float2 v2 = b[(long long)(k + 16) * n], v3 = b[(long long)(k + 24) * n];
-    acc = acc + df_make(v0.x, v0.y);
-    acc = acc + df_make(v1.x, v1.y);
-    acc = acc + df_make(v2.x, v2.y);
-    acc = acc + df_make(v3.x, v3.y);
+  constexpr int kBatch = 8;
+  for (int k0 = sub; k0 < nch; k0 += kBatch * 8) {
+    float2 v[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      const int k = k0 + 8 * j;
+      v[j] = k < nch ? b[(long long)k * n] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      const int k = k0 + 8 * j;
+      if (k < ncr)
+        c = c + df_make(v[j].x, v[j].y);
+      else if (k < nch)
+        r = r + df_make(v[j].x, v[j].y);
+    }
   }
-  for (; k < k1; k += 8) {
-    const float2 v = b[(long long)k * n];
-    acc = acc + df_make(v.x, v.y);
-  }
-  return acc;
 }
-
 
 constexpr int kRedThreads = kReduceTargetsPerBlock * kRedLanes;
 static_assert(kRedThreads == 256, "reduce block size");
@@ -325,11 +328,7 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   } else {
     // the (hi, lo) partials are summed in double-float arithmetic on the FP32 pipes
     df c = df_make(0.f, 0.f), r = df_make(0.f, 0.f);
-    if (i < n) {
-      const float2* b = part + S.part + i;
-      c = sum_chunks(b, n, sub, S.ncr);
-      r = sum_chunks(b, n, S.ncr + sub, nch);
-    }
+    if (i < n) sum_chunks(part + S.part + i, n, sub, S.ncr, nch, c, r);
     for (int o = 1; o < kRedLanes; o <<= 1) {
       c = c + df_make(__shfl_xor_sync(0xffffffffu, c.hi, o), __shfl_xor_sync(0xffffffffu, c.lo, o));
       r = r + df_make(__shfl_xor_sync(0xffffffffu, r.hi, o), __shfl_xor_sync(0xffffffffu, r.lo, o));

@@ -105,6 +105,8 @@ __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__
       sect[m] = (m >= 2) ? sqrt((2.0 * m - 1.0) / (2.0 * m)) : 1.0;
       sect2[m] = pair_of(sect[m]);
       inv_np1[m] = 1.0 / (m + 1.0);
+      sect2[pmax + 1 + m] = pair_of((2.0 * m + 1.0) / (m + 1.0));  // Legendre: P_{n+1} = a P_n t - b P_{n-1}
+      sect2[2 * (pmax + 1) + m] = pair_of((double)m / (m + 1.0));
     }
   }
   for (int s = blockIdx.x; s < nsys; s += gridDim.x) {
@@ -553,24 +555,24 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
   R U = Num<R>::zero(), V = Num<R>::zero();
   double Rs = 0.0;
   if (idx < P) {
-    // rows b = warp, warp + kCoefWarps, ... in ascending order, four rows' loads in flight
-    int b = warp;
-    for (; b + 3 * kCoefWarps < S.mom_blocks; b += 4 * kCoefWarps) {
-      R u[4], v[4];
+    // rows b = warp, warp + kCoefWarps, ... in ascending order, five rows' loads in flight
+    // (1024-thread blocks have 64 registers per thread)
+    constexpr int kRows = 5;
+    for (int b0 = warp; b0 < S.mom_blocks; b0 += kRows * kCoefWarps) {
+      R u[kRows], v[kRows];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        u[k] = Num<R>::ld(base, (long long)(b + k * kCoefWarps) * mom_stride + idx);
-        v[k] = Num<R>::ld(base, (long long)(b + k * kCoefWarps) * mom_stride + P + idx);
+      for (int k = 0; k < kRows; ++k) {
+        const int b = b0 + k * kCoefWarps;
+        u[k] = b < S.mom_blocks ? Num<R>::ld(base, (long long)b * mom_stride + idx) : Num<R>::zero();
+        v[k] = b < S.mom_blocks ? Num<R>::ld(base, (long long)b * mom_stride + P + idx) : Num<R>::zero();
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        U = U + u[k];
-        V = V + v[k];
+      for (int k = 0; k < kRows; ++k) {
+        if (b0 + k * kCoefWarps < S.mom_blocks) {
+          U = U + u[k];
+          V = V + v[k];
+        }
       }
-    }
-    for (; b < S.mom_blocks; b += kCoefWarps) {
-      U = U + Num<R>::ld(base, (long long)b * mom_stride + idx);
-      V = V + Num<R>::ld(base, (long long)b * mom_stride + P + idx);
     }
   }
   if (it.y == 0 && lane == 0)
@@ -712,24 +714,25 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __re
   const int j = it.y * kSurfWarps + warp;
   if (j >= M) return;
   const double* row = sb + S.sb + (long long)j * P;
+  const dbl4 yw = surfx[S.surf + j];  // loaded ahead of the sums
   R ph = Num<R>::zero(), dph = Num<R>::zero();
-  int i = lane;
-  for (; i + 96 < P; i += 128) {  // four row loads in flight ahead of the sums
-    const R b0 = Num<R>::ld(row, i), b1 = Num<R>::ld(row, i + 32);
-    const R b2 = Num<R>::ld(row, i + 64), b3 = Num<R>::ld(row, i + 96);
-    ph = Num<R>::acc(ph, A[i], b0);
-    dph = Num<R>::acc(dph, nA[i], b0);
-    ph = Num<R>::acc(ph, A[i + 32], b1);
-    dph = Num<R>::acc(dph, nA[i + 32], b1);
-    ph = Num<R>::acc(ph, A[i + 64], b2);
-    dph = Num<R>::acc(dph, nA[i + 64], b2);
-    ph = Num<R>::acc(ph, A[i + 96], b3);
-    dph = Num<R>::acc(dph, nA[i + 96], b3);
-  }
-  for (; i < P; i += 32) {
-    const R b = Num<R>::ld(row, i);
-    ph = Num<R>::acc(ph, A[i], b);
-    dph = Num<R>::acc(dph, nA[i], b);
+  // sixteen row loads in flight ahead of their sums (one DRAM round trip per 512 coefficients)
+  constexpr int kRowBatch = 16;
+  for (int i0 = lane; i0 < P; i0 += 32 * kRowBatch) {
+    R bv[kRowBatch];
+#pragma unroll
+    for (int j = 0; j < kRowBatch; ++j) {
+      const int i = i0 + 32 * j;
+      bv[j] = i < P ? Num<R>::ld(row, i) : Num<R>::zero();
+    }
+#pragma unroll
+    for (int j = 0; j < kRowBatch; ++j) {
+      const int i = i0 + 32 * j;
+      if (i < P) {
+        ph = Num<R>::acc(ph, A[i], bv[j]);
+        dph = Num<R>::acc(dph, nA[i], bv[j]);
+      }
+    }
   }
   ph = Num<R>::norm(ph);
   dph = Num<R>::norm(dph);
@@ -738,8 +741,8 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __re
     dph = dph + Num<R>::shfl(dph, off);
   }
   if (lane == 0)
-    surface_records(S, S.surf + j, surfx[S.surf + j], Num<R>::to(ph), Num<R>::to(dph), prec, surf_a, surf_b,
-                    surf64_a, surf64_b, surfqd);
+    surface_records(S, S.surf + j, yw, Num<R>::to(ph), Num<R>::to(dph), prec, surf_a, surf_b, surf64_a, surf64_b,
+                    surfqd);
 }
 
 // Without a basis table (too large for the workspace): lane m runs column m of the recurrence

@@ -263,7 +263,7 @@ static int launch_moves(hsma_server_t* s, const std::vector<int>& ridx, const hs
   SCK(cudaMemcpyAsync(e->ditems_d, s->ditems_h, sizeof(int4) * ni, cudaMemcpyHostToDevice, s->sA));
   SCK(cudaMemcpyAsync(e->dreqit_d, s->dranges_h, sizeof(int2) * nr, cudaMemcpyHostToDevice, s->sA));
   hsma::launch_delta(e->sys_d, e->ditems_d, ni, e->dreqit_d, e->dreq_d, nr, e->xyz_d, e->q_d, e->perm_d, e->iperm_d,
-                     e->srchi_d, e->srclo_d, e->src64_d, e->surfx_d, e->surfqd_d, e->vsurf_d, e->Mn_d, e->inv_np1_d,
+                     e->srchi_d, e->srclo_d, e->src64_d, e->surfx_d, e->surfqd_d, e->vsurf_d, e->Mn_d, e->tables(),
                      e->dpart_d, e->de_d, e->ctr_delta_d, e->status_d, s->sA);
   SCK(cudaGetLastError());
   SCK(cudaMemcpyAsync(s->de_h, e->de_d, 8 * nr, cudaMemcpyDeviceToHost, s->sA));
