@@ -238,9 +238,9 @@ HSMA_API int hsma_batch_set_overlap(hsma_batch_t* b, int on);
 /* Pair-sum tile configurations: CTA threads x targets per thread, and the number of pair work
  * items per resident CTA slot the layout aims for (any pointer may be NULL).
  * hsma_batch_set_pair_config forces one (-1 = automatic); hsma_batch_autotune times every
- * configuration on the current sources (reps potential passes each: pair sum and reduction,
- * CUDA events) and keeps the fastest for this size class; *best and *best_ms (nullable)
- * receive the choice and its time. */
+ * configuration on the current inputs (reps runs each, CUDA events: the overlapped build +
+ * potential step, or with overlap off the potential pass alone) and keeps the fastest for this
+ * size class; *best and *best_ms (nullable) receive the choice and its time. */
 HSMA_API int hsma_pair_config_count(void);
 HSMA_API int hsma_pair_config_info(int idx, int* threads, int* targets_per_thread, int* items_per_slot);
 HSMA_API int hsma_batch_set_pair_config(hsma_batch_t* b, int cfg);

@@ -209,7 +209,7 @@ class TuneCache:
     def key(n, gpu: str) -> str:
         tot = int(np.sum(n))
         ncfg = _native.load().hsma_pair_config_count()
-        return f"{gpu}|ncfg={ncfg}|nsys={len(n)}|log2N={max(tot, 1).bit_length()}"
+        return f"{gpu}|ncfg={ncfg}|step|nsys={len(n)}|log2N={max(tot, 1).bit_length()}"
 
     def get(self, n, gpu: str):
         return self.data.get(self.key(n, gpu))

@@ -18,10 +18,12 @@ struct hsma_batch_t {
 
 namespace hsma {
 
-// Time every pair configuration on the current sources (the potentials pass: pair sum plus the
-// reduction of its partials, whose count the configuration sets) and keep the fastest for this
-// size class.  The inputs (xyz, q) sit before every configuration-dependent buffer of the
-// workspace, so each configuration rebuilds its sources from them in place.
+// Time every pair configuration on the current inputs and keep the fastest for this size class:
+// with overlap on, the overlapped build + potential step that a build followed by an evaluation
+// runs (the configuration sets the pair items that overlap the coefficient chain); with overlap
+// off, the potential pass alone (pair sum plus the reduction of its partials).  The inputs (xyz,
+// q) sit before every configuration-dependent buffer of the workspace, so each configuration
+// rebuilds its sources from them in place.
 int Engine::autotune(int reps, int* best_out, float* best_ms_out)
 {
   if (prec == HSMA_FP64) return fail(HSMA_E_INVALID_ARG, "autotuning applies to the FP32 pair sum");
@@ -60,11 +62,23 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
     std::vector<float> t;
     for (int r = 0; r < reps + 1; ++r) {
       pot_ready = false;
-      rc = potentials();
-      if (rc) return rc;
       float ms = 0.f;
-      rc = last_pot_time(&ms);
-      if (rc) return rc;
+      if (overlap) {
+        build_pending = true;
+        cudaError_t e = cudaEventRecord(ev_tune0, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord (autotune)");
+        rc = potentials();
+        if (rc) return rc;
+        e = cudaEventRecord(ev_tune1, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev_tune1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev_tune0, ev_tune1);
+        if (e != cudaSuccess) return cuda_fail(e, "timing (autotune)");
+      } else {
+        rc = potentials();
+        if (rc) return rc;
+        rc = last_pot_time(&ms);
+        if (rc) return rc;
+      }
       if (r > 0) t.push_back(ms);
     }
     std::sort(t.begin(), t.end());

@@ -80,6 +80,8 @@ int Engine::init(int dev, void* user_stream, int precision)
   CK(cudaEventCreate(&ev_pair0));
   CK(cudaEventCreate(&ev_pair1));
   CK(cudaEventCreate(&ev_pot1));
+  CK(cudaEventCreate(&ev_tune0));
+  CK(cudaEventCreate(&ev_tune1));
   CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
@@ -130,6 +132,8 @@ Engine::~Engine()
   if (ev_pair0) cudaEventDestroy(ev_pair0);
   if (ev_pair1) cudaEventDestroy(ev_pair1);
   if (ev_pot1) cudaEventDestroy(ev_pot1);
+  if (ev_tune0) cudaEventDestroy(ev_tune0);
+  if (ev_tune1) cudaEventDestroy(ev_tune1);
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
   if (ev_img) cudaEventDestroy(ev_img);
@@ -653,6 +657,7 @@ void Engine::issue_fused()
   // the work counter of the real/Kelvin items is reset before ev_img, which the main stream
   // waits for before its draining launch
   cudaMemsetAsync(ctr_pairs2_d, 0, sizeof(unsigned int), side);
+  cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), side);
   cudaEventRecord(ev_img, side);
   const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d}, srf{it4x_d + L.nRK, nS, ctr_pairs_d}, none{nullptr, 0, nullptr};
   launch_pair_items(rk, none, grid_rk, side);
@@ -662,7 +667,6 @@ void Engine::issue_fused()
                      stream);
   launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
                  surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
-  cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), stream);
   cudaStreamWaitEvent(stream, ev_img, 0);
   launch_pair_items(srf, rk, grid_s, stream);
   cudaStreamWaitEvent(stream, ev_join, 0);

@@ -142,6 +142,7 @@ class Engine {
   // pair-kernel timing events (recorded around every pair-sum launch)
   cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;
   cudaEvent_t ev_pot1 = nullptr;  // after the reduction (pair sum + reduction = potentials pass)
+  cudaEvent_t ev_tune0 = nullptr, ev_tune1 = nullptr;  // autotuner: around an overlapped step
   // ordering with the caller's legacy default stream when the handle owns its stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   void enter();

@@ -38,29 +38,6 @@
 
 namespace hsma {
 
-// Programmatic dependent launch: a kernel launched with launch_pdl may start while its
-// predecessor in the stream is finishing; it calls grid_dependency_wait() before it reads
-// anything the predecessor writes (a no-op when launched normally).  A predecessor lets its
-// dependent launch early with allow_dependents().
-__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
-                       Args... args)
-{
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
 
 // ---------------------------------------------------------------------------------------
 // Per-system scalars, tables and the quadrature grid.  Block s handles system s (thread 0:
