@@ -135,6 +135,7 @@ template <class R>
 struct Num;
 template <>
 struct Num<double> {
+  static constexpr bool is_df = false;
   static __device__ __forceinline__ double from(double x) { return x; }
   static __device__ __forceinline__ double from_int(int n) { return (double)n; }
   static __device__ __forceinline__ double to(double x) { return x; }
@@ -154,6 +155,7 @@ struct Num<double> {
 };
 template <>
 struct Num<df> {
+  static constexpr bool is_df = true;
   static __device__ __forceinline__ df from(double x) { return df_from_double(x); }
   static __device__ __forceinline__ df from_int(int n) { return df_make((float)n, 0.f); }
   static __device__ __forceinline__ double to(df x) { return df_to_double(x); }
@@ -240,6 +242,9 @@ __device__ __forceinline__ void split2(double x, float& hi, float& lo)
 
 constexpr int kMomThreads = 256;  // a moment block holds at most kMomTile <= kMomThreads charges
 constexpr int kMomWarps = kMomThreads / 32;
+// Slots of the recurrence tables (a_nm, b_nm over the triangle n <= pmax, and the sectoral
+// factors) that k_moments keeps in shared memory when they take at most kMomTableSlots slots.
+constexpr size_t kMomTableSlots = 4096;
 static_assert(kMomTile <= kMomThreads, "one charge per thread in the preparation pass");
 static_assert(kOrderBlock % 64 == 0, "k_images splits an order item into 64-thread blocks");
 
@@ -390,6 +395,34 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
   R* cqc = cq + kMomThreads;
   double* red = reinterpret_cast<double*>(cqc + kMomThreads);  // [kMomWarps]
 
+  // the recurrence tables in shared memory when they are small (a global load per recurrence
+  // step otherwise); visible after the __syncthreads that follows the preparation pass
+  Tables tsh = tab;
+  {
+    const int pm = tab.pmax;
+    const int ntri = (pm + 1) * (pm + 2) / 2;
+    if (2 * (size_t)ntri + pm + 1 <= kMomTableSlots) {
+      double* tb = red + kMomWarps;
+      const double* ga = sizeof(R) == 8 && Num<R>::is_df ? reinterpret_cast<const double*>(tab.rec_a2) : tab.rec_a;
+      const double* gb = sizeof(R) == 8 && Num<R>::is_df ? reinterpret_cast<const double*>(tab.rec_b2) : tab.rec_b;
+      const double* gs = sizeof(R) == 8 && Num<R>::is_df ? reinterpret_cast<const double*>(tab.sect2) : tab.sect;
+      for (int i = tid; i < ntri; i += kMomThreads) {
+        tb[i] = ga[i];
+        tb[ntri + i] = gb[i];
+      }
+      for (int i = tid; i <= pm; i += kMomThreads) tb[2 * ntri + i] = gs[i];
+      if (Num<R>::is_df) {
+        tsh.rec_a2 = reinterpret_cast<const float2*>(tb);
+        tsh.rec_b2 = reinterpret_cast<const float2*>(tb + ntri);
+        tsh.sect2 = reinterpret_cast<const float2*>(tb + 2 * ntri);
+      } else {
+        tsh.rec_a = tb;
+        tsh.rec_b = tb + ntri;
+        tsh.sect = tb + 2 * ntri;
+      }
+    }
+  }
+
   double r0 = 0.0;
   if (tid < cnt) {
     const long long gi = S.chg + c0 + tid;
@@ -424,7 +457,7 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
     const int gcount = min(G, cnt - g0);
     if (tg < gcount) {
       const int c = g0 + tg;
-      solid_column<R>(tm, p, cu[c], cv[c], cw[c], cr2[c], tab, T + (size_t)tg * P);
+      solid_column<R>(tm, p, cu[c], cv[c], cw[c], cr2[c], tsh, T + (size_t)tg * P);
     }
     __syncthreads();
 #pragma unroll
@@ -455,11 +488,17 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
 
 // Charges per moment group: at most one solid-harmonic column per thread (G (p+1) <= 256) and
 // the group's G P values within the shared-memory budget.
+static size_t moment_table_slots(int pmax)
+{
+  const size_t s = 2 * (size_t)(pmax + 1) * (pmax + 2) / 2 + (size_t)(pmax + 1);
+  return s <= kMomTableSlots ? s : 0;
+}
+
 int moment_smem_group(int maxP)
 {
   int pmax = (int)std::lround(std::sqrt((double)maxP)) - 1;
   if (pmax < 0) pmax = 0;
-  const size_t fixed = (6 * (size_t)kMomThreads + kMomWarps) * sizeof(double);
+  const size_t fixed = (6 * (size_t)kMomThreads + kMomWarps + moment_table_slots(pmax)) * sizeof(double);
   const size_t budget = 192 * 1024;
   int G = kMomThreads / (pmax + 1);
   const int Gs = (int)((budget - fixed) / ((size_t)maxP * sizeof(double)));
@@ -470,7 +509,11 @@ int moment_smem_group(int maxP)
 
 static size_t moment_smem_bytes(int maxP)
 {
-  return ((size_t)moment_smem_group(maxP) * maxP + 6 * (size_t)kMomThreads + kMomWarps) * sizeof(double);
+  int pmax = (int)std::lround(std::sqrt((double)maxP)) - 1;
+  if (pmax < 0) pmax = 0;
+  return ((size_t)moment_smem_group(maxP) * maxP + 6 * (size_t)kMomThreads + kMomWarps +
+          moment_table_slots(pmax)) *
+         sizeof(double);
 }
 
 template <int MAXJ>
