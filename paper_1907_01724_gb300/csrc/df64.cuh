@@ -108,4 +108,24 @@ __device__ __forceinline__ df df_acc(df acc, df a, df b)
 
 __device__ __forceinline__ df df_norm(df x) { return fast_two_sum(x.hi, x.lo); }
 
+// 1/b: the correctly rounded FP32 reciprocal of the high part, then one Newton step for
+// f(y) = 1/y - b in double-float, y <- y + y (1 - b y), which squares the 2^-24 relative error.
+__device__ __forceinline__ df df_recip(df b)
+{
+  const float y = __frcp_rn(b.hi);
+  const df yd = df_make(y, 0.f);
+  const df e = df_make(1.f, 0.f) - b * yd;
+  return yd + e * yd;
+}
+
+// sqrt(a), a > 0: the FP32 square root of the high part, then one Newton (Heron) step in
+// double-float, s <- s + (a - s^2) / (2 s).
+__device__ __forceinline__ df df_sqrt(df a)
+{
+  const float s = sqrtf(a.hi);
+  const df sd = df_make(s, 0.f);
+  const df r = a - two_prod(s, s);
+  return sd + r * df_make(0.5f / s, 0.f);
+}
+
 }  // namespace hsma

@@ -68,6 +68,7 @@ int Engine::init(int dev, void* user_stream, int precision)
   static bool attrs_done[64] = {false};
   if (device >= 0 && device < 64 && !attrs_done[device]) {
     init_source_kernels();
+    init_order_kernels();
     init_delta_kernels();
     attrs_done[device] = true;
   }
@@ -83,11 +84,23 @@ int Engine::init(int dev, void* user_stream, int precision)
   CK(cudaEventCreate(&ev_tune0));
   CK(cudaEventCreate(&ev_tune1));
   CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+  {
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    prio_hi = greatest;
+    prio_mid = std::min(greatest + 1, least);
+  }
   CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ev_img, cudaEventDisableTiming));
   CK(cudaGetLastError());
   return HSMA_OK;
+}
+
+int& launch_priority()
+{
+  static thread_local int p = 0;
+  return p;
 }
 
 void Engine::enter()
@@ -361,8 +374,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_iperm = take(4 * (size_t)L.totN);
   L.o_key = take(4 * (size_t)L.totN);
   L.o_hist = take(4 * (size_t)nsys * kOrderCells);
-  L.o_offs = take(4 * (size_t)nsys * kOrderCells);
-  L.o_cursor = take(4 * (size_t)nsys * kOrderCells);
+  L.o_sortscr = take(8 * (size_t)L.totN);
   L.o_boxes = take(2 * sizeof(float4) * (size_t)L.totBoxes);
   L.o_itord = take(sizeof(int2) * L.itord.size());
   L.o_r0 = take(8 * (size_t)nsys);
@@ -441,8 +453,7 @@ void Engine::carve()
   iperm_d = (int*)(b + L.o_iperm);
   key_d = (int*)(b + L.o_key);
   hist_d = (int*)(b + L.o_hist);
-  offs_d = (int*)(b + L.o_offs);
-  cursor_d = (int*)(b + L.o_cursor);
+  sortscr_d = (int*)(b + L.o_sortscr);
   boxes_d = (float4*)(b + L.o_boxes);
   itord_d = (int2*)(b + L.o_itord);
   r0_d = (double*)(b + L.o_r0);
@@ -531,6 +542,7 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
   CK(cudaMemsetAsync(ctr_pairs_d, 0, 16, stream));
   CK(cudaMemsetAsync(ctr_red_d, 0, 4 * L.sd.size(), stream));
   CK(cudaMemsetAsync(energy_d, 0, 16 * L.sd.size(), stream));
+  CK(cudaMemsetAsync(hist_d, 0, 4 * L.sd.size() * kOrderCells, stream));
   // parameter-only quantities (scalars, M_n, tables, quadrature grid, surface basis), once per layout
   launch_setup(sys_d, (int)L.sd.size(), Mn_d, rec_a_d, rec_b_d, sect_d, inv_np1_d, rec_a2_d, rec_b2_d, sect2_d,
                L.pmax, surfx_d, stream);
@@ -573,8 +585,9 @@ void Engine::issue_build()
   if (order) {
     cudaEventRecord(ev_fork, stream);
     cudaStreamWaitEvent(side, ev_fork, 0);
-    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, key_d, hist_d, offs_d, cursor_d, perm_d, iperm_d,
-                 side);
+    PriorityScope ps(prio_hi);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, key_d, hist_d, sortscr_d, perm_d, iperm_d, nullptr,
+                 0, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d, prec,
                   status_d, side);
     cudaEventRecord(ev_join, side);
@@ -589,8 +602,8 @@ void Engine::issue_build()
 
 int Engine::build_launch_count() const
 {
-  // order: 4 kernels (k_order_cells, _scan, _scatter, _sort) and k_images
-  return (L.itord.empty() ? 0 : 5) + (L.it12.empty() ? 0 : 1) + (L.it2r.empty() ? 0 : 1) + (L.it3.empty() ? 0 : 1);
+  // order: 2 kernels (k_order_keys, k_order_sort) and k_images
+  return (L.itord.empty() ? 0 : 3) + (L.it12.empty() ? 0 : 1) + (L.it2r.empty() ? 0 : 1) + (L.it3.empty() ? 0 : 1);
 }
 
 void Engine::issue_pot()
@@ -650,18 +663,23 @@ void Engine::issue_fused()
   const int grid_s = std::max(1, std::min(nS + L.nRK, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);
-  launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, key_d, hist_d, offs_d, cursor_d, perm_d, iperm_d,
-               side);
-  launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d, prec,
-                status_d, side);
-  // the work counter of the real/Kelvin items is reset before ev_img, which the main stream
-  // waits for before its draining launch
-  cudaMemsetAsync(ctr_pairs2_d, 0, sizeof(unsigned int), side);
-  cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), side);
-  cudaEventRecord(ev_img, side);
+  // launch priorities: the order and the records (short, and the capped real/Kelvin launch
+  // waits for them) first, the moments -> coefficients -> surface chain next, the capped
+  // launch last, so that its CTAs take only what the chains leave free; k_order_keys also
+  // zeroes both pair work counters (ctr_pairs_d and ctr_pairs2_d, adjacent), which the main
+  // stream's launch uses only after ev_img
   const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d}, srf{it4x_d + L.nRK, nS, ctr_pairs_d}, none{nullptr, 0, nullptr};
+  {
+    PriorityScope ps(prio_hi);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
+                 ctr_pairs_d, 2, side);
+    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d, prec,
+                  status_d, side);
+  }
+  cudaEventRecord(ev_img, side);
   launch_pair_items(rk, none, grid_rk, side);
   cudaEventRecord(ev_join, side);
+  PriorityScope ps(prio_mid);
   launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, tables(), prec, mom_d, L.mom_stride, stream);
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
@@ -693,7 +711,7 @@ int Engine::run_graph(cudaGraphExec_t* g, void (Engine::*issue)())
     (this->*issue)();
     cudaError_t e = cudaStreamEndCapture(stream, &graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(g, graph, 0);
+    e = cudaGraphInstantiate(g, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
       *g = nullptr;

@@ -44,7 +44,7 @@ struct Layout {
   int max_req = 1, ditem_cap = 1, mitem_cap = 1;
   size_t o_dreq = 0, o_ditems = 0, o_dreqit = 0, o_mitems = 0, o_dpart = 0, o_de = 0;
   size_t o_sb = 0, o_coef2 = 0, o_itsb = 0;
-  size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_offs = 0, o_cursor = 0, o_boxes = 0, o_itord = 0;
+  size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_sortscr = 0, o_boxes = 0, o_itord = 0;
   size_t o_redctr = 0;
   size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0;
   size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0, o_it4x = 0;
@@ -106,11 +106,15 @@ class Engine {
   double* sb_d = nullptr;         // auxiliary-sphere solid-harmonic tables
   int2* itsb_d = nullptr;
   int *perm_d = nullptr, *iperm_d = nullptr;  // spatial order (sorted position <-> input index)
-  int *key_d = nullptr, *hist_d = nullptr, *offs_d = nullptr, *cursor_d = nullptr;
+  int* key_d = nullptr;            // cell key of every charge
+  int* hist_d = nullptr;           // cell histogram per system (zero between builds)
+  int* sortscr_d = nullptr;        // scratch of the order's sort (2 ints per charge)
   float4* boxes_d = nullptr;      // bounding boxes of 32 consecutive sorted records
   int2* itord_d = nullptr;
   cudaStream_t side = nullptr;    // second stream of the build (order + records beside the moments)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_img = nullptr;
+  int prio_hi = 0, prio_mid = 0;  // greatest stream priority of the device and the next one
+                                  // (launch priorities of the overlapped step, issue_fused)
   // deferred build: build() copies the inputs; the first evaluation runs the build, and a
   // potential/energy evaluation runs it fused with the pair sum (overlap) in one graph
   bool build_pending = false;

@@ -45,21 +45,50 @@ constexpr double kCentreRel = 1e-12;
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
+// Launch priority (a stream-priority value, 0 = the default, lower = more urgent) that the
+// launchers below give their kernels; the engine sets it around each launcher call, so that in
+// the overlapped step the work that gates the pair sum is dispatched before the pair sum of the
+// real and Kelvin records, which runs beside it.  Graphs are instantiated to honour it.
+int& launch_priority();
+struct PriorityScope {
+  int saved;
+  explicit PriorityScope(int p) : saved(launch_priority()) { launch_priority() = p; }
+  ~PriorityScope() { launch_priority() = saved; }
+};
+
+// Kernel launch with the current launch priority and, when pdl is set, programmatic dependent
+// launch.
 template <typename... KArgs, typename... Args>
-inline void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
-                       Args... args)
+inline void launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, bool pdl,
+                     Args... args)
 {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[2];
+  unsigned na = 0;
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (launch_priority() != 0) {
+    attr[na].id = cudaLaunchAttributePriority;
+    attr[na].val.priority = launch_priority();
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = na;
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args)
+{
+  launch_k(kern, grid, block, smem, st, true, args...);
 }
 
 // Per-system descriptor, resident on the device.  The host fills the inputs and the layout
@@ -98,11 +127,17 @@ struct SysDev {
 // Spatial order (k_order.cu): charges sorted by the Morton index of their cell on a 16^3 grid
 // over [-a, a]^3 (input index inside a cell).  perm[chg + i] = input index of sorted position
 // i, iperm its inverse.  Pair-sum records, pair partials and move work use sorted positions.
+// launch_order writes the cell keys and the cell histogram (items = (system, block of
+// kOrderBlock charges)), then sorts each system in one block; its first kernel also zeroes the
+// nreset counters at ctr_reset.  hist (kOrderCells ints per system) must be zero on entry and
+// is zero again on exit; scr is scratch of 2 ints per charge (used for systems of more than
+// 4096 charges).
 constexpr int kOrderGrid = 16;
 constexpr int kOrderCells = kOrderGrid * kOrderGrid * kOrderGrid;
-constexpr int kOrderBlock = 256;  // charges per k_order / k_images work item
+constexpr int kOrderBlock = 256;  // charges per k_order_keys / k_images work item
+void init_order_kernels();  // one-time function attributes (call outside stream capture)
 void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, int* key, int* hist,
-                  int* offs, int* cursor, int* perm, int* iperm, cudaStream_t st);
+                  int* scr, int* perm, int* iperm, unsigned int* ctr_reset, int nreset, cudaStream_t st);
 // Boxes of 32 consecutive sorted records: a warp's targets and a box farther apart than
 // kNearRel a use plain FP32 coordinates in the pair sum, nearer ones the hi/lo-split form.
 constexpr int kBox = 32;

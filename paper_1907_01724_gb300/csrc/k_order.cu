@@ -5,11 +5,15 @@
 // is deterministic.  Consecutive charges in this order are close in space: a warp's targets
 // and a 32-source sub-tile each occupy a small box, and the pair kernel evaluates the pairs of
 // well-separated boxes with plain FP32 coordinates, keeping the hi/lo-split form for near ones.
-//   k_order_cells    cell key per charge, histogram per system (integer atomics: exact)
-//   k_order_scan     exclusive scan of each system's histogram (one block per system)
-//   k_order_scatter  charge -> slot of its cell (atomic cursor: any order inside a cell)
-//   k_order_sort     sort every cell's slots by input index (insertion sort; cells are small)
-//                    and write the inverse permutation
+//   k_order_keys   cell key per charge and the cell histogram of its system (global integer
+//                  atomics; many small blocks: the key is FP64 arithmetic, which this GPU
+//                  issues at a low rate per SM)
+//   k_order_sort   one block per system: exclusive scan of the histogram, scatter to the cells
+//                  (atomic cursor in shared memory: any order inside a cell), then every slot
+//                  finds its place in its cell by counting the cell's smaller input indices (the
+//                  rank; cells hold a few charges), which gives perm and iperm; it leaves the
+//                  histogram zeroed for the next build (zeroed once when the workspace is laid out)
+// Two kernels and no memsets: the order is on the critical path of the overlapped step.
 #include "hsma_internal.cuh"
 
 namespace hsma {
@@ -33,10 +37,12 @@ __device__ __forceinline__ int cell_key(const SysDev& S, double x, double y, dou
   return (int)(spread3((unsigned)ix) | (spread3((unsigned)iy) << 1) | (spread3((unsigned)iz) << 2));
 }
 
-__global__ __launch_bounds__(kOrderBlock) void k_order_cells(const SysDev* __restrict__ sys, const int2* __restrict__ items,
-                                                     const double* __restrict__ xyz, int* __restrict__ key,
-                                                     int* __restrict__ hist)
+__global__ __launch_bounds__(kOrderBlock) void k_order_keys(const SysDev* __restrict__ sys, const int2* __restrict__ items,
+                                                            const double* __restrict__ xyz, int* __restrict__ key,
+                                                            int* __restrict__ hist, unsigned int* __restrict__ ctr_reset,
+                                                            int nreset)
 {
+  if (blockIdx.x == 0 && (int)threadIdx.x < nreset) ctr_reset[threadIdx.x] = 0u;
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int i = it.y * kOrderBlock + threadIdx.x;
@@ -47,96 +53,120 @@ __global__ __launch_bounds__(kOrderBlock) void k_order_cells(const SysDev* __res
   atomicAdd(&hist[(size_t)it.x * kOrderCells + k], 1);
 }
 
-// exclusive scan of kOrderCells counts with 1024 threads (4 cells per thread)
-__global__ __launch_bounds__(1024) void k_order_scan(int nsys, const int* __restrict__ hist, int* __restrict__ offs,
-                                                     int* __restrict__ cursor)
+// One block per system.  s_cell holds the first sorted position of every cell (exclusive scan
+// of the histogram), then (after the scatter) the end of every cell.  The scattered slots
+// (input index and cell) live in shared memory when the system has at most kOrderSmemN charges,
+// else in the scratch buffer scr (2 ints per charge); the keys of the first kKeyRegs
+// kSortThreads charges are held in registers between the two passes that use them.
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kOrderSmemN = 4096;
+constexpr int kKeyRegs = kOrderSmemN / kSortThreads;
+static_assert(kOrderCells % kSortThreads == 0, "cells split evenly over the sort block");
+
+__global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __restrict__ sys,
+                                                             const int* __restrict__ key, int* __restrict__ hist,
+                                                             int* __restrict__ scr, int* __restrict__ perm,
+                                                             int* __restrict__ iperm)
 {
-  __shared__ int warp_sums[32];
-  const int s = blockIdx.x;
-  if (s >= nsys) return;
-  const int* h = hist + (size_t)s * kOrderCells;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  constexpr int per = kOrderCells / 1024;
-  int local[per];
+  __shared__ int s_cell[kOrderCells];
+  __shared__ int s_wsum[kSortWarps];
+  extern __shared__ int s_slot[];
+  const SysDev& S = sys[blockIdx.x];
+  const int n = S.n;
+  const long long c0 = S.chg;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int* slot = n <= kOrderSmemN ? s_slot : scr + 2 * c0;  // [n] input index, then [n] cell
+  int* skey = slot + (n <= kOrderSmemN ? kOrderSmemN : n);
+  int* h = hist + (size_t)blockIdx.x * kOrderCells;
+
+  // the keys (loads in flight beside the scan)
+  int kr[kKeyRegs];
+#pragma unroll
+  for (int j = 0; j < kKeyRegs; ++j) {
+    const int i = tid + j * kSortThreads;
+    kr[j] = i < n ? key[c0 + i] : 0;
+  }
+
+  // exclusive scan: thread t owns cells [t per, (t + 1) per); the histogram is zeroed behind it
+  constexpr int per = kOrderCells / kSortThreads;
+  int cnt[per];
   int sum = 0;
 #pragma unroll
   for (int j = 0; j < per; ++j) {
-    local[j] = h[t * per + j];
-    sum += local[j];
+    cnt[j] = h[tid * per + j];
+    sum += cnt[j];
   }
+#pragma unroll
+  for (int j = 0; j < per; ++j) h[tid * per + j] = 0;
   int incl = sum;
+#pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int v = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += v;
   }
-  if (lane == 31) warp_sums[warp] = incl;
+  if (lane == 31) s_wsum[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    int w = warp_sums[lane];
+    int w = lane < kSortWarps ? s_wsum[lane] : 0;
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, w, o);
       if (lane >= o) w += v;
     }
-    warp_sums[lane] = w;
+    if (lane < kSortWarps) s_wsum[lane] = w;
   }
   __syncthreads();
-  int run = incl - sum + (warp > 0 ? warp_sums[warp - 1] : 0);
+  int run = incl - sum + (warp > 0 ? s_wsum[warp - 1] : 0);
 #pragma unroll
   for (int j = 0; j < per; ++j) {
-    offs[(size_t)s * kOrderCells + t * per + j] = run;
-    cursor[(size_t)s * kOrderCells + t * per + j] = run;
-    run += local[j];
+    s_cell[tid * per + j] = run;
+    run += cnt[j];
   }
-}
+  __syncthreads();
 
-__global__ __launch_bounds__(kOrderBlock) void k_order_scatter(const SysDev* __restrict__ sys, const int2* __restrict__ items,
-                                                       const int* __restrict__ key, int* __restrict__ cursor,
-                                                       int* __restrict__ perm)
-{
-  const int2 it = items[blockIdx.x];
-  const SysDev& S = sys[it.x];
-  const int i = it.y * kOrderBlock + threadIdx.x;
-  if (i >= S.n) return;
-  const int pos = atomicAdd(&cursor[(size_t)it.x * kOrderCells + key[S.chg + i]], 1);
-  perm[S.chg + pos] = i;
-}
-
-// one thread per cell: insertion sort of the cell's slots by input index, then the inverse map
-__global__ __launch_bounds__(256) void k_order_sort(const SysDev* __restrict__ sys, int nsys,
-                                                    const int* __restrict__ hist, const int* __restrict__ offs,
-                                                    int* __restrict__ perm, int* __restrict__ iperm)
-{
-  const long long gid = (long long)blockIdx.x * 256 + threadIdx.x;
-  const int s = (int)(gid / kOrderCells);
-  const int c = (int)(gid % kOrderCells);
-  if (s >= nsys) return;
-  const SysDev& S = sys[s];
-  const int cnt = hist[(size_t)s * kOrderCells + c];
-  if (cnt == 0) return;
-  int* seg = perm + S.chg + offs[(size_t)s * kOrderCells + c];
-  for (int a = 1; a < cnt; ++a) {
-    const int v = seg[a];
-    int b = a - 1;
-    while (b >= 0 && seg[b] > v) {
-      seg[b + 1] = seg[b];
-      --b;
+  // scatter
+#pragma unroll
+  for (int j = 0; j < kKeyRegs; ++j) {
+    const int i = tid + j * kSortThreads;
+    if (i < n) {
+      const int p = atomicAdd(&s_cell[kr[j]], 1);
+      slot[p] = i;
+      skey[p] = kr[j];
     }
-    seg[b + 1] = v;
   }
-  const int base = offs[(size_t)s * kOrderCells + c];
-  for (int a = 0; a < cnt; ++a) iperm[S.chg + seg[a]] = base + a;
+  for (int i = tid + kKeyRegs * kSortThreads; i < n; i += kSortThreads) {
+    const int k = key[c0 + i];
+    const int p = atomicAdd(&s_cell[k], 1);
+    slot[p] = i;
+    skey[p] = k;
+  }
+  __syncthreads();
+
+  // slot a of cell k (which spans [end of cell k - 1, end of cell k)) goes to the cell's start
+  // plus the number of the cell's input indices below its own
+  for (int a = tid; a < n; a += kSortThreads) {
+    const int v = slot[a], k = skey[a];
+    const int b0 = k ? s_cell[k - 1] : 0, e = s_cell[k];
+    int p = b0;
+    for (int b = b0; b < e; ++b) p += slot[b] < v;
+    perm[c0 + p] = v;
+    iperm[c0 + v] = p;
+  }
+}
+
+void init_order_kernels()
+{
+  cudaFuncSetAttribute(k_order_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * sizeof(int) * kOrderSmemN);
 }
 
 void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, int* key, int* hist,
-                  int* offs, int* cursor, int* perm, int* iperm, cudaStream_t st)
+                  int* scr, int* perm, int* iperm, unsigned int* ctr_reset, int nreset, cudaStream_t st)
 {
   if (nitems <= 0 || nsys <= 0) return;
-  cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)nsys * kOrderCells, st);
-  k_order_cells<<<nitems, kOrderBlock, 0, st>>>(sys, items, xyz, key, hist);
-  k_order_scan<<<nsys, 1024, 0, st>>>(nsys, hist, offs, cursor);
-  k_order_scatter<<<nitems, kOrderBlock, 0, st>>>(sys, items, key, cursor, perm);
-  const long long cells = (long long)nsys * kOrderCells;
-  k_order_sort<<<(int)((cells + 255) / 256), 256, 0, st>>>(sys, nsys, hist, offs, perm, iperm);
+  launch_k(k_order_keys, nitems, kOrderBlock, 0, st, false, sys, items, xyz, key, hist, ctr_reset, nreset);
+  launch_k(k_order_sort, nsys, kSortThreads, 2 * sizeof(int) * kOrderSmemN, st, false, sys, (const int*)key, hist, scr,
+           perm, iperm);
 }
 
 }  // namespace hsma

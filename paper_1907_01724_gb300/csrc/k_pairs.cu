@@ -148,7 +148,7 @@ void launch_pairs_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWor
   switch (pair_kernel_of(cfg)) {
 #define HSMA_CFG_LAUNCH(i, nt, k)                                                                          \
   case i:                                                                                                  \
-    k_pairs_f32<nt, k><<<grid, nt, 0, st>>>(sys, w1, w2, src_hi, src_lo, surf_a, surf_b, boxes, part); \
+    launch_k(k_pairs_f32<nt, k>, grid, nt, 0, st, false, sys, w1, w2, src_hi, src_lo, surf_a, surf_b, boxes, part); \
     break;
     HSMA_PAIR_CONFIGS(HSMA_CFG_LAUNCH)
 #undef HSMA_CFG_LAUNCH
@@ -241,7 +241,7 @@ int pairs_f64_occupancy()
 void launch_pairs_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, const dbl4* src64,
                       const dbl4* surf64_a, const double* surf64_b, double* part64, cudaStream_t st)
 {
-  k_pairs_f64<<<grid, kF64Threads, 0, st>>>(sys, w1, w2, src64, surf64_a, surf64_b, part64);
+  launch_k(k_pairs_f64, grid, kF64Threads, 0, st, false, sys, w1, w2, src64, surf64_a, surf64_b, part64);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -303,19 +303,19 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   // loads per target are in flight and the order does not depend on scheduling
   const int sub = threadIdx.x % kRedLanes;
   const int i = it.y * kReduceTargetsPerBlock + threadIdx.x / kRedLanes;
-  // the target's input position, charge and the centre constant are loaded first, so their
-  // latency overlaps the partial sums
+  // the target's input position, charge and the centre constant are loaded first (by every
+  // lane of the target: one broadcast load), so their latency overlaps the partial sums
   long long o = 0;
-  double qi = 0.0, rc = 0.0;
-  if (i < n && sub == 0) {
+  double qi = 0.0;
+  const double rc = r0[it.x];
+  if (i < n) {
     o = S.chg + perm[S.chg + i];  // partials are in sorted order
     qi = q[o];
-    rc = r0[it.x];
   }
   double et = 0.0, er = 0.0;
-  double pc = 0.0, pr = 0.0;
   const int nch = S.ncr + S.nck + S.ncs;
   if (prec == HSMA_FP64) {
+    double pc = 0.0, pr = 0.0;
     if (i < n) {
       const double* b = part64 + S.part + i;
       for (int c = sub; c < S.ncr; c += kRedLanes) pc += b[(long long)c * n];
@@ -325,31 +325,48 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
       pc += __shfl_xor_sync(0xffffffffu, pc, o);
       pr += __shfl_xor_sync(0xffffffffu, pr, o);
     }
+    if (i < n && sub == 0) {
+      pr += rc;
+      phi_c[o] = pc;
+      phi_r[o] = pr;
+      phi_t[o] = pc + pr;
+      if (!isfinite(pc) || !isfinite(pr)) atomicOr(status, kStNonFinite);
+      et = 0.5 * qi * (pc + pr);
+      er = 0.5 * qi * pr;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      et += __shfl_xor_sync(0xffffffffu, et, o);
+      er += __shfl_xor_sync(0xffffffffu, er, o);
+    }
   } else {
-    // the (hi, lo) partials are summed in double-float arithmetic on the FP32 pipes
+    // the (hi, lo) partials, the centre constant and the energy terms in double-float
+    // arithmetic on the FP32 pipes; FP64 only to convert (this GPU issues FP64 at a small
+    // fraction of the FP32 rate), and the three conversions of a target spread over its lanes.  The
+    // xor butterfly leaves the same sums in all kRedLanes lanes (df addition is commutative).
     df c = df_make(0.f, 0.f), r = df_make(0.f, 0.f);
     if (i < n) sum_chunks(part + S.part + i, n, sub, S.ncr, nch, c, r);
     for (int o = 1; o < kRedLanes; o <<= 1) {
       c = c + df_make(__shfl_xor_sync(0xffffffffu, c.hi, o), __shfl_xor_sync(0xffffffffu, c.lo, o));
       r = r + df_make(__shfl_xor_sync(0xffffffffu, r.hi, o), __shfl_xor_sync(0xffffffffu, r.lo, o));
     }
-    if (sub == 0) {
-      pc = df_to_double(c);
-      pr = df_to_double(r);
+    r = r + df_from_double(rc);
+    const df t = c + r;
+    if (i < n && sub < 3) {
+      double* dst = sub == 0 ? phi_c : (sub == 1 ? phi_r : phi_t);
+      dst[o] = df_to_double(sub == 0 ? c : (sub == 1 ? r : t));
+      if (sub == 0 && !(isfinite(c.hi) && isfinite(r.hi))) atomicOr(status, kStNonFinite);
     }
-  }
-  if (i < n && sub == 0) {
-    pr += rc;
-    phi_c[o] = pc;
-    phi_r[o] = pr;
-    phi_t[o] = pc + pr;
-    if (!isfinite(pc) || !isfinite(pr)) atomicOr(status, kStNonFinite);
-    et = 0.5 * qi * (pc + pr);
-    er = 0.5 * qi * pr;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    et += __shfl_xor_sync(0xffffffffu, et, o);
-    er += __shfl_xor_sync(0xffffffffu, er, o);
+    const df hq = df_from_double(0.5 * qi);
+    df ect = i < n && sub == 0 ? hq * t : df_make(0.f, 0.f);
+    df ecr = i < n && sub == 0 ? hq * r : df_make(0.f, 0.f);
+    for (int o = 16; o > 0; o >>= 1) {
+      ect = ect + df_make(__shfl_xor_sync(0xffffffffu, ect.hi, o), __shfl_xor_sync(0xffffffffu, ect.lo, o));
+      ecr = ecr + df_make(__shfl_xor_sync(0xffffffffu, ecr.hi, o), __shfl_xor_sync(0xffffffffu, ecr.lo, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      et = df_to_double(ect);
+      er = df_to_double(ecr);
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
@@ -420,8 +437,8 @@ void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int n
                    unsigned int* counter, int* status, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  k_reduce<<<nitems, kRedThreads, 0, st>>>(sys, sel, sel_rng, nsel, items, part, part64, prec, q, perm, r0, phi_c,
-                                           phi_r, phi_t, epart, energy, counter, status);
+  launch_k(k_reduce, nitems, kRedThreads, 0, st, false, sys, sel, sel_rng, nsel, items, part, part64, prec, q, perm, r0,
+           phi_c, phi_r, phi_t, epart, energy, counter, status);
 }
 
 }  // namespace hsma

@@ -311,13 +311,19 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
   if (i < n) {
     const long long gi = S.chg + perm[S.chg + i];
     const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
-    const KelvinRec k = kelvin_rec(S, x, y, z, qi);
-    if (!(k.r < S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) atomicOr(status, kStOutside);
     const long long sr = S.src + i, sk = S.src + n + i;
     if (prec == HSMA_FP64) {
+      const KelvinRec k = kelvin_rec(S, x, y, z, qi);
+      if (!(k.r < S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) atomicOr(status, kStOutside);
       src64[sr] = make_dbl4(x, y, z, S.kc * qi);
       src64[sk] = make_dbl4(k.kx, k.ky, k.kz, k.QK);
     } else {
+      // the Kelvin point in double-float arithmetic from the exact-ish r^2 (FP64 square root and
+      // division cost hundreds of cycles here): s = (a/r)^2 = a^2 (1/r^2), r_K xhat = s x,
+      // r_K = a sqrt(s); the (hi, lo) result is the record's split directly
+      const double r2d = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+      if (!(r2d < S.a * S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi))
+        atomicOr(status, kStOutside);
       float hx, hy, hz, lx, ly, lz;
       split2(x, hx, lx);
       split2(y, hy, ly);
@@ -327,14 +333,26 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
       bmin[0] = bmax[0] = hx;
       bmin[1] = bmax[1] = hy;
       bmin[2] = bmax[2] = hz;
-      split2(k.kx, hx, lx);
-      split2(k.ky, hy, ly);
-      split2(k.kz, hz, lz);
-      src_hi[sk] = make_float4(hx, hy, hz, (float)k.QK);
-      src_lo[sk] = make_float4(lx, ly, lz, 0.f);
-      bmin[3] = bmax[3] = hx;
-      bmin[4] = bmax[4] = hy;
-      bmin[5] = bmax[5] = hz;
+      // centre test as in kelvin_rec and k_moments (on r = sqrt(r^2)); the square root is taken
+      // only for charges that can pass it
+      const double rc = kCentreRel * S.a;
+      if (r2d <= 4.0 * rc * rc && sqrt(r2d) <= rc) {
+        // image at infinity (its constant potential is added by k_moments): a zero-strength
+        // record, left out of the box
+        src_hi[sk] = make_float4((float)(1e15 * S.a), 0.f, 0.f, 0.f);
+        src_lo[sk] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        const df da = df_from_double(S.a);
+        const df s = (da * da) * df_recip(df_from_double(r2d));
+        const df kx = s * df_make(hx, lx), ky = s * df_make(hy, ly), kz = s * df_make(hz, lz);
+        const double rK = df_to_double(da * df_sqrt(s));
+        const double QK = S.kc * (qi * S.inv_a * (S.gam * rK + S.dbar * (S.Rtau - rK) * 0.5));
+        src_hi[sk] = make_float4(kx.hi, ky.hi, kz.hi, (float)QK);
+        src_lo[sk] = make_float4(kx.lo, ky.lo, kz.lo, 0.f);
+        bmin[3] = bmax[3] = kx.hi;
+        bmin[4] = bmax[4] = ky.hi;
+        bmin[5] = bmax[5] = kz.hi;
+      }
     }
   }
   if (prec != HSMA_FP64) {
@@ -360,8 +378,8 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
                    cudaStream_t st)
 {
   if (nitems <= 0) return;
-  k_images<<<nitems * kImgSplit, kImgThreads, 0, st>>>(sys, items, xyz, q, perm, src_hi, src_lo, src64, boxes, prec,
-                                                       status);
+  launch_k(k_images, nitems * kImgSplit, kImgThreads, 0, st, false, sys, items, xyz, q, perm, src_hi, src_lo, src64,
+           boxes, prec, status);
 }
 
 // Charge moments of the correction coefficients.  Thread t of a block prepares charge c0 + t
@@ -523,9 +541,9 @@ static void launch_mom(const SysDev* sys, const int2* items, int nitems, int max
   const int G = moment_smem_group(maxP);
   const size_t smem = moment_smem_bytes(maxP);
   if (prec == HSMA_FP64)
-    k_moments<MAXJ, double><<<nitems, kMomThreads, smem, st>>>(sys, items, xyz, q, tab, mom, mom_stride, G);
+    launch_k(k_moments<MAXJ, double>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, tab, mom, mom_stride, G);
   else
-    k_moments<MAXJ, df><<<nitems, kMomThreads, smem, st>>>(sys, items, xyz, q, tab, mom, mom_stride, G);
+    launch_k(k_moments<MAXJ, df>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, tab, mom, mom_stride, G);
 }
 
 void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,

@@ -201,16 +201,16 @@ def test_kernel_launch_accounting():
     h = api.hsma_create(s.a, s.eps1, s.eps2, s.kappa, prm)
     api.hsma_build_sources(h, s.xyz, s.q)
     api.hsma_energy(h)
-    # once per layout: k_setup, k_surface_basis; build: k_order_cells, _scan, _scatter, _sort,
-    # k_images, k_moments, k_coef_reduce, k_surface_mat; potentials (overlapped with the build):
-    # k_pairs (real/Kelvin items, capped grid), k_pairs (surface items, then the real/Kelvin
-    # items left), k_reduce
-    assert api.hsma_kernel_launches(h) == 13
+    # once per layout: k_setup, k_surface_basis; build: k_order_keys, k_order_sort, k_images,
+    # k_moments, k_coef_reduce, k_surface_mat; potentials (overlapped with the build): k_pairs
+    # (real/Kelvin items, capped grid), k_pairs (surface items, then the real/Kelvin items
+    # left), k_reduce
+    assert api.hsma_kernel_launches(h) == 11
     api.hsma_set_overlap(h, False)
     api.hsma_build_sources(h, s.xyz, s.q)
     api.hsma_energy(h)
-    # separate passes: the 8 build kernels, then k_pairs and k_reduce
-    assert api.hsma_kernel_launches(h) == 13 + 10
+    # separate passes: the 6 build kernels, then k_pairs and k_reduce
+    assert api.hsma_kernel_launches(h) == 11 + 8
 
 
 @pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
