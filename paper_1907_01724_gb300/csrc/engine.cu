@@ -327,11 +327,11 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_Mn = take(8 * L.totMn);
   L.o_rec_a = take(8 * (size_t)ntri);
   L.o_rec_b = take(8 * (size_t)ntri);
-  L.o_sect = take(8 * (size_t)(L.pmax + 1));
+  L.o_sect = take(8 * 2 * (size_t)(L.pmax + 1));  // sect, then sprod
   L.o_inv_np1 = take(8 * (size_t)(L.pmax + 1));
   L.o_rec_a2 = take(8 * (size_t)ntri);
   L.o_rec_b2 = take(8 * (size_t)ntri);
-  L.o_sect2 = take(8 * 3 * (size_t)(L.pmax + 1));  // sect2, then the Legendre tables
+  L.o_sect2 = take(8 * 4 * (size_t)(L.pmax + 1));  // sect2, the Legendre tables, sprod2
   L.o_xyz = take(24 * L.totN);
   L.o_q = take(8 * L.totN);
   if (prec == HSMA_FP64) {
@@ -572,6 +572,8 @@ Tables Engine::tables() const
   t.sect2 = sect2_d;
   t.leg_a2 = sect2_d + (L.pmax + 1);
   t.leg_b2 = sect2_d + 2 * (L.pmax + 1);
+  t.sprod = sect_d + (L.pmax + 1);
+  t.sprod2 = sect2_d + 3 * (L.pmax + 1);
   t.pmax = L.pmax;
   return t;
 }

@@ -154,6 +154,8 @@ struct Tables {
   const float2* sect2;
   const float2* leg_a2;   // Legendre recurrence (2n+1)/(n+1) and n/(n+1), n <= pmax, as (hi, lo)
   const float2* leg_b2;   // (stored after sect2 in the same array)
+  const double* sprod;    // sectoral normalisation prod_{k <= m} sect[k] (stored after sect)
+  const float2* sprod2;   // the same as (hi, lo) (stored after leg_b2)
   int pmax;
 };
 

@@ -84,6 +84,10 @@ __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__
       inv_np1[m] = 1.0 / (m + 1.0);
       sect2[pmax + 1 + m] = pair_of((2.0 * m + 1.0) / (m + 1.0));  // Legendre: P_{n+1} = a P_n t - b P_{n-1}
       sect2[2 * (pmax + 1) + m] = pair_of((double)m / (m + 1.0));
+      double sp = 1.0;
+      for (int k = 2; k <= m; ++k) sp *= sqrt((2.0 * k - 1.0) / (2.0 * k));
+      sect[pmax + 1 + m] = sp;
+      sect2[3 * (pmax + 1) + m] = pair_of(sp);
     }
   }
   for (int s = blockIdx.x; s < nsys; s += gridDim.x) {
@@ -230,6 +234,55 @@ __device__ __forceinline__ void solid_column(int m, int p, R u, R v, R w, R rho2
     pr = nr;
     pi = ni;
   }
+}
+
+// The columns m1 = j and m2 = p - j (j <= p/2) of one point, for the moment kernel: one thread
+// per column pair keeps every lane of a warp busy for about 2p steps (one thread per column
+// leaves the warp waiting for its longest sectoral and vertical chains).  The sectoral
+// values are T_mm = sprod_m (u + i v)^m, with the power carried from m1 to m2; below the
+// diagonal the vertical recurrence is real, T_nm = Q_n T_mm with Q_m = 1, Q_{m-1} = 0,
+// Q_n = a_nm w Q_{n-1} - b_nm rho^2 Q_{n-2}.  ra, rb, sp: a_nm, b_nm (index n(n+1)/2 + m)
+// and sprod in the arithmetic R.
+template <class R>
+__device__ __forceinline__ void solid_vertical(int m, int p, R w, R rho2, R cr, R ci, const R* __restrict__ ra,
+                                               const R* __restrict__ rb, R* __restrict__ T)
+{
+  T[m * m + 2 * m] = cr;
+  if (m) T[m * m] = ci;
+  R q1 = Num<R>::one(), q2 = Num<R>::zero();
+  int t = (m + 1) * (m + 2) / 2 + m;  // table index of (n, m), n = m + 1
+  int i0 = (m + 1) * (m + 2);         // coefficient index of (n, 0)
+  for (int n = m + 1; n <= p; ++n) {
+    const R A = ra[t] * w, B = rb[t] * rho2;
+    const R qn = Num<R>::mul_sub(A, q1, B, q2);
+    T[i0 + m] = qn * cr;
+    if (m) T[i0 - m] = qn * ci;
+    q2 = q1;
+    q1 = qn;
+    t += n + 1;
+    i0 += 2 * n + 2;
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void solid_pair(int j, int p, R u, R v, R w, R rho2, const R* __restrict__ ra,
+                                           const R* __restrict__ rb, const R* __restrict__ sp, R* __restrict__ T)
+{
+  const int m1 = j, m2 = p - j;
+  R zr = Num<R>::one(), zi = Num<R>::zero();
+  R c1r = Num<R>::one(), c1i = Num<R>::zero();
+  for (int k = 1; k <= m2; ++k) {
+    const R nr = Num<R>::mul_sub(zr, u, zi, v);
+    const R ni = Num<R>::mul_sub(zr, v, -zi, u);
+    zr = nr;
+    zi = ni;
+    if (k == m1) {
+      c1r = sp[m1] * zr;
+      c1i = sp[m1] * zi;
+    }
+  }
+  solid_vertical<R>(m1, p, w, rho2, c1r, c1i, ra, rb, T);
+  if (m2 != m1) solid_vertical<R>(m2, p, w, rho2, sp[m2] * zr, sp[m2] * zi, ra, rb, T);
 }
 
 // Split a double into an FP32 high part and the FP32-rounded residual (x ~ hi + lo).
@@ -385,9 +438,10 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
 // Charge moments of the correction coefficients.  Thread t of a block prepares charge c0 + t
 // (FP64): the centre constant of a charge at the centre, and its moment inputs u, v, w = x/a,
 // rho^2, q and q c in the moment arithmetic R (shared memory), so the moment phase runs on R
-// alone: per group of G charges, thread t computes column m = t mod (p+1) of charge t / (p+1)
-// (solid_column), then thread t accumulates coefficients t + j kMomThreads over the group.
-// Moments are stored as R values in 8-byte slots; slot 2P holds the block's centre constant.
+// alone: per group of G charges, thread t computes the column pair j = t mod (p/2 + 1) of
+// charge t / (p/2 + 1) (solid_pair), then thread t accumulates coefficients t + j kMomThreads
+// over the group.  Moments are stored as R values in 8-byte slots; slot 2P holds the block's
+// centre constant.
 template <int MAXJ, class R>
 __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restrict__ sys, const int2* __restrict__ items,
                                                          const double* __restrict__ xyz, const double* __restrict__ q,
@@ -415,29 +469,22 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
 
   // the recurrence tables in shared memory when they are small (a global load per recurrence
   // step otherwise); visible after the __syncthreads that follows the preparation pass
-  Tables tsh = tab;
+  const R* ra = Num<R>::is_df ? reinterpret_cast<const R*>(tab.rec_a2) : reinterpret_cast<const R*>(tab.rec_a);
+  const R* rb = Num<R>::is_df ? reinterpret_cast<const R*>(tab.rec_b2) : reinterpret_cast<const R*>(tab.rec_b);
+  const R* sp = Num<R>::is_df ? reinterpret_cast<const R*>(tab.sprod2) : reinterpret_cast<const R*>(tab.sprod);
   {
     const int pm = tab.pmax;
     const int ntri = (pm + 1) * (pm + 2) / 2;
     if (2 * (size_t)ntri + pm + 1 <= kMomTableSlots) {
-      double* tb = red + kMomWarps;
-      const double* ga = sizeof(R) == 8 && Num<R>::is_df ? reinterpret_cast<const double*>(tab.rec_a2) : tab.rec_a;
-      const double* gb = sizeof(R) == 8 && Num<R>::is_df ? reinterpret_cast<const double*>(tab.rec_b2) : tab.rec_b;
-      const double* gs = sizeof(R) == 8 && Num<R>::is_df ? reinterpret_cast<const double*>(tab.sect2) : tab.sect;
+      R* tb = reinterpret_cast<R*>(red + kMomWarps);
       for (int i = tid; i < ntri; i += kMomThreads) {
-        tb[i] = ga[i];
-        tb[ntri + i] = gb[i];
+        tb[i] = ra[i];
+        tb[ntri + i] = rb[i];
       }
-      for (int i = tid; i <= pm; i += kMomThreads) tb[2 * ntri + i] = gs[i];
-      if (Num<R>::is_df) {
-        tsh.rec_a2 = reinterpret_cast<const float2*>(tb);
-        tsh.rec_b2 = reinterpret_cast<const float2*>(tb + ntri);
-        tsh.sect2 = reinterpret_cast<const float2*>(tb + 2 * ntri);
-      } else {
-        tsh.rec_a = tb;
-        tsh.rec_b = tb + ntri;
-        tsh.sect = tb + 2 * ntri;
-      }
+      for (int i = tid; i <= pm; i += kMomThreads) tb[2 * ntri + i] = sp[i];
+      ra = tb;
+      rb = tb + ntri;
+      sp = tb + 2 * ntri;
     }
   }
 
@@ -455,27 +502,32 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
     cq[tid] = Num<R>::from(qi);
     cqc[tid] = Num<R>::from(qi * (dbar * (S.Rt_a * (r * inv_a) - 1.0) * 0.5));
   }
-  // block sum of the centre-charge constants (fixed order)
-  for (int o = 16; o > 0; o >>= 1) r0 += __shfl_xor_sync(0xffffffffu, r0, o);
-  if (lane == 0) red[warp] = r0;
-  __syncthreads();
+  // block sum of the centre-charge constants (fixed order), reduced only when some charge of
+  // the tile sits at the centre (FP64 shuffles in every warp cost more than the tile's prep)
   double* out = mom + (size_t)(S.mom + it.y) * mom_stride;
-  if (tid == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kMomWarps; ++w) s += red[w];
-    out[2 * P] = s;
+  if (__syncthreads_or(r0 != 0.0)) {
+    for (int o = 16; o > 0; o >>= 1) r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+    if (lane == 0) red[warp] = r0;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kMomWarps; ++w) s += red[w];
+      out[2 * P] = s;
+    }
+  } else if (tid == 0) {
+    out[2 * P] = 0.0;
   }
   // charge moments U_nm, V_nm
   R accU[MAXJ], accV[MAXJ];
 #pragma unroll
   for (int j = 0; j < MAXJ; ++j) accU[j] = accV[j] = Num<R>::zero();
-  const int ncol = p + 1;
-  const int tg = tid / ncol, tm = tid - tg * ncol;
+  const int npair = p / 2 + 1;
+  const int tg = tid / npair, tj = tid - tg * npair;
   for (int g0 = 0; g0 < cnt; g0 += G) {
     const int gcount = min(G, cnt - g0);
     if (tg < gcount) {
       const int c = g0 + tg;
-      solid_column<R>(tm, p, cu[c], cv[c], cw[c], cr2[c], tsh, T + (size_t)tg * P);
+      solid_pair<R>(tj, p, cu[c], cv[c], cw[c], cr2[c], ra, rb, sp, T + (size_t)tg * P);
     }
     __syncthreads();
 #pragma unroll
@@ -504,8 +556,8 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
   }
 }
 
-// Charges per moment group: at most one solid-harmonic column per thread (G (p+1) <= 256) and
-// the group's G P values within the shared-memory budget.
+// Charges per moment group: at most one solid-harmonic column pair per thread
+// (G (p/2 + 1) <= 256) and the group's G P values within the shared-memory budget.
 static size_t moment_table_slots(int pmax)
 {
   const size_t s = 2 * (size_t)(pmax + 1) * (pmax + 2) / 2 + (size_t)(pmax + 1);
@@ -518,7 +570,7 @@ int moment_smem_group(int maxP)
   if (pmax < 0) pmax = 0;
   const size_t fixed = (6 * (size_t)kMomThreads + kMomWarps + moment_table_slots(pmax)) * sizeof(double);
   const size_t budget = 192 * 1024;
-  int G = kMomThreads / (pmax + 1);
+  int G = kMomThreads / (pmax / 2 + 1);
   const int Gs = (int)((budget - fixed) / ((size_t)maxP * sizeof(double)));
   if (G > Gs) G = Gs;
   if (G < 1) G = 1;
