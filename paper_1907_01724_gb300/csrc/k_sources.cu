@@ -785,10 +785,28 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __re
                                                               double2* __restrict__ surfqd, int prec)
 {
   extern __shared__ double sm[];
-  grid_dependency_wait();  // the coefficients of k_coef_reduce
+  __shared__ R s_ph[kSurfWarps], s_dph[kSurfWarps];
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P, M = S.M;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = it.y * kSurfWarps + warp;
+  const bool live = j < M;
+  // the basis row (a layout constant) and, in warp 0, the block's points are loaded before the
+  // wait for the coefficients: sixteen row loads per lane in flight (512 coefficients)
+  const double* row = sb + S.sb + (long long)(live ? j : 0) * P;
+  constexpr int kRowBatch = 16;
+  R bv[kRowBatch];
+#pragma unroll
+  for (int k = 0; k < kRowBatch; ++k) {
+    const int i = lane + 32 * k;
+    bv[k] = live && i < P ? Num<R>::ld(row, i) : Num<R>::zero();
+  }
+  const int jl = it.y * kSurfWarps + lane;  // warp 0: the point of lane l < kSurfWarps
+  dbl4 yw = make_dbl4(0.0, 0.0, 0.0, 0.0);
+  if (warp == 0 && lane < kSurfWarps && jl < M) yw = surfx[S.surf + jl];
+
+  grid_dependency_wait();  // the coefficients of k_coef_reduce
   R* A = reinterpret_cast<R*>(sm);  // [P] A'_nm
   R* nA = A + P;                    // [P] n A'_nm
   for (int i = threadIdx.x; i < P; i += kSurfThreads) {
@@ -800,28 +818,22 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __re
     nA[i] = Num<R>::from_int(nn) * c;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = it.y * kSurfWarps + warp;
-  if (j >= M) return;
-  const double* row = sb + S.sb + (long long)j * P;
-  const dbl4 yw = surfx[S.surf + j];  // loaded ahead of the sums
   R ph = Num<R>::zero(), dph = Num<R>::zero();
-  // sixteen row loads in flight ahead of their sums (one DRAM round trip per 512 coefficients)
-  constexpr int kRowBatch = 16;
-  for (int i0 = lane; i0 < P; i0 += 32 * kRowBatch) {
-    R bv[kRowBatch];
+  for (int i0 = 0;;) {
 #pragma unroll
-    for (int j = 0; j < kRowBatch; ++j) {
-      const int i = i0 + 32 * j;
-      bv[j] = i < P ? Num<R>::ld(row, i) : Num<R>::zero();
-    }
-#pragma unroll
-    for (int j = 0; j < kRowBatch; ++j) {
-      const int i = i0 + 32 * j;
+    for (int k = 0; k < kRowBatch; ++k) {
+      const int i = i0 + lane + 32 * k;
       if (i < P) {
-        ph = Num<R>::acc(ph, A[i], bv[j]);
-        dph = Num<R>::acc(dph, nA[i], bv[j]);
+        ph = Num<R>::acc(ph, A[i], bv[k]);
+        dph = Num<R>::acc(dph, nA[i], bv[k]);
       }
+    }
+    i0 += 32 * kRowBatch;
+    if (i0 >= P) break;
+#pragma unroll
+    for (int k = 0; k < kRowBatch; ++k) {
+      const int i = i0 + lane + 32 * k;
+      bv[k] = live && i < P ? Num<R>::ld(row, i) : Num<R>::zero();
     }
   }
   ph = Num<R>::norm(ph);
@@ -830,9 +842,16 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __re
     ph = ph + Num<R>::shfl(ph, off);
     dph = dph + Num<R>::shfl(dph, off);
   }
-  if (lane == 0)
-    surface_records(S, S.surf + j, yw, Num<R>::to(ph), Num<R>::to(dph), prec, surf_a, surf_b, surf64_a, surf64_b,
-                    surfqd);
+  if (lane == 0) {
+    s_ph[warp] = ph;
+    s_dph[warp] = dph;
+  }
+  __syncthreads();
+  // the records of the block's points from one warp (lane l: point l), so that their FP64
+  // arithmetic issues once per block rather than once per point
+  if (warp == 0 && lane < kSurfWarps && jl < M)
+    surface_records(S, S.surf + jl, yw, Num<R>::to(s_ph[lane]), Num<R>::to(s_dph[lane]), prec, surf_a, surf_b,
+                    surf64_a, surf64_b, surfqd);
 }
 
 // Without a basis table (too large for the workspace): lane m runs column m of the recurrence
