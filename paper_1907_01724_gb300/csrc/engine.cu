@@ -691,7 +691,8 @@ void Engine::issue_fused()
   launch_pair_items(srf, rk, grid_s, stream);
   cudaStreamWaitEvent(stream, ev_join, 0);
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
-                phic_d, phir_d, phit_d, epart_d, energy_d, ctr_red_d, status_d, stream);
+                phic_d, phir_d, phit_d, epart_d, energy_d, ctr_red_d, status_d, stream,
+                true);
 }
 
 int Engine::fused_launch_count() const

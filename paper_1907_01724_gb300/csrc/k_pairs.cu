@@ -312,6 +312,9 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     o = S.chg + perm[S.chg + i];  // partials are in sorted order
     qi = q[o];
   }
+  // (launched as a programmatic dependent of the pair kernel: everything above reads data that
+  // the pair sum does not write; the partials below wait for it)
+  grid_dependency_wait();
   double et = 0.0, er = 0.0;
   const int nch = S.ncr + S.nck + S.ncs;
   if (prec == HSMA_FP64) {
@@ -434,10 +437,10 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
 void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
                    const float2* part, const double* part64, int prec, const double* q, const int* perm,
                    const double* r0, double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy,
-                   unsigned int* counter, int* status, cudaStream_t st)
+                   unsigned int* counter, int* status, cudaStream_t st, bool pdl)
 {
   if (nitems <= 0) return;
-  launch_k(k_reduce, nitems, kRedThreads, 0, st, false, sys, sel, sel_rng, nsel, items, part, part64, prec, q, perm, r0,
+  launch_k(k_reduce, nitems, kRedThreads, 0, st, pdl, sys, sel, sel_rng, nsel, items, part, part64, prec, q, perm, r0,
            phi_c, phi_r, phi_t, epart, energy, counter, status);
 }
 

@@ -141,6 +141,7 @@ template <>
 struct Num<double> {
   static constexpr bool is_df = false;
   static __device__ __forceinline__ double from(double x) { return x; }
+  static __device__ __forceinline__ double from_df(df x) { return df_to_double(x); }
   static __device__ __forceinline__ double from_int(int n) { return (double)n; }
   static __device__ __forceinline__ double to(double x) { return x; }
   static __device__ __forceinline__ double zero() { return 0.0; }
@@ -161,6 +162,7 @@ template <>
 struct Num<df> {
   static constexpr bool is_df = true;
   static __device__ __forceinline__ df from(double x) { return df_from_double(x); }
+  static __device__ __forceinline__ df from_df(df x) { return x; }
   static __device__ __forceinline__ df from_int(int n) { return df_make((float)n, 0.f); }
   static __device__ __forceinline__ double to(df x) { return df_to_double(x); }
   static __device__ __forceinline__ df zero() { return df_make(0.f, 0.f); }
@@ -467,6 +469,16 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
   R* cqc = cq + kMomThreads;
   double* red = reinterpret_cast<double*>(cqc + kMomThreads);  // [kMomWarps]
 
+  // the tile's charges are loaded first (the longest chain of dependent loads: item, system,
+  // charges), the recurrence tables beside them
+  double x = 0.0, y = 0.0, z = 0.0, qi = 0.0;
+  if (tid < cnt) {
+    const long long gi = S.chg + c0 + tid;
+    x = xyz[3 * gi];
+    y = xyz[3 * gi + 1];
+    z = xyz[3 * gi + 2];
+    qi = q[gi];
+  }
   // the recurrence tables in shared memory when they are small (a global load per recurrence
   // step otherwise); visible after the __syncthreads that follows the preparation pass
   const R* ra = Num<R>::is_df ? reinterpret_cast<const R*>(tab.rec_a2) : reinterpret_cast<const R*>(tab.rec_a);
@@ -478,10 +490,11 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
     if (2 * (size_t)ntri + pm + 1 <= kMomTableSlots) {
       R* tb = reinterpret_cast<R*>(red + kMomWarps);
       for (int i = tid; i < ntri; i += kMomThreads) {
-        tb[i] = ra[i];
-        tb[ntri + i] = rb[i];
+        const R va = ra[i], vb = rb[i], vs = i <= pm ? sp[i] : Num<R>::zero();
+        tb[i] = va;
+        tb[ntri + i] = vb;
+        if (i <= pm) tb[2 * ntri + i] = vs;
       }
-      for (int i = tid; i <= pm; i += kMomThreads) tb[2 * ntri + i] = sp[i];
       ra = tb;
       rb = tb + ntri;
       sp = tb + 2 * ntri;
@@ -490,17 +503,34 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
 
   double r0 = 0.0;
   if (tid < cnt) {
-    const long long gi = S.chg + c0 + tid;
-    const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
-    const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
-    if (r <= kCentreRel * S.a) r0 += S.kc_a * qi * (S.gam - 0.5 * dbar);
-    const double ux = x * inv_a, uy = y * inv_a, uz = z * inv_a;
-    cu[tid] = Num<R>::from(ux);
-    cv[tid] = Num<R>::from(uy);
-    cw[tid] = Num<R>::from(uz);
-    cr2[tid] = Num<R>::from(ux * ux + uy * uy + uz * uz);
-    cq[tid] = Num<R>::from(qi);
-    cqc[tid] = Num<R>::from(qi * (dbar * (S.Rt_a * (r * inv_a) - 1.0) * 0.5));
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+    const double rc = kCentreRel * S.a;
+    if (r2 <= 4.0 * rc * rc && sqrt(r2) <= rc) r0 += S.kc_a * qi * (S.gam - 0.5 * dbar);
+    if (Num<R>::is_df) {
+      // u, v, w, rho^2 and q c in double-float from the split inputs (four FP64 conversions
+      // per charge; this GPU issues FP64 arithmetic at a small fraction of the FP32 rate)
+      const df ia = df_from_double(inv_a);
+      const df u = df_from_double(x) * ia, v = df_from_double(y) * ia, w = df_from_double(z) * ia;
+      const df rho2 = u * u + v * v + w * w;
+      const df qd = df_from_double(qi);
+      const df rr = rho2.hi > 0.f ? df_sqrt(rho2) : df_make(0.f, 0.f);
+      const df c = df_from_double(0.5 * dbar) * (df_from_double(S.Rt_a) * rr - df_make(1.f, 0.f));
+      cu[tid] = Num<R>::from_df(u);
+      cv[tid] = Num<R>::from_df(v);
+      cw[tid] = Num<R>::from_df(w);
+      cr2[tid] = Num<R>::from_df(rho2);
+      cq[tid] = Num<R>::from_df(qd);
+      cqc[tid] = Num<R>::from_df(qd * c);
+    } else {
+      const double r = sqrt(r2);
+      const double ux = x * inv_a, uy = y * inv_a, uz = z * inv_a;
+      cu[tid] = Num<R>::from(ux);
+      cv[tid] = Num<R>::from(uy);
+      cw[tid] = Num<R>::from(uz);
+      cr2[tid] = Num<R>::from(ux * ux + uy * uy + uz * uz);
+      cq[tid] = Num<R>::from(qi);
+      cqc[tid] = Num<R>::from(qi * (dbar * (S.Rt_a * (r * inv_a) - 1.0) * 0.5));
+    }
   }
   // block sum of the centre-charge constants (fixed order), reduced only when some charge of
   // the tile sits at the centre (FP64 shuffles in every warp cost more than the tile's prep)
