@@ -375,6 +375,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_key = take(4 * (size_t)L.totN);
   L.o_hist = take(4 * (size_t)nsys * kOrderCells);
   L.o_sortscr = take(8 * (size_t)L.totN);
+  L.o_xs = take(prec == HSMA_FP64 ? 0 : 32 * (size_t)L.totN);
   L.o_boxes = take(2 * sizeof(float4) * (size_t)L.totBoxes);
   L.o_itord = take(sizeof(int2) * L.itord.size());
   L.o_r0 = take(8 * (size_t)nsys);
@@ -454,6 +455,7 @@ void Engine::carve()
   key_d = (int*)(b + L.o_key);
   hist_d = (int*)(b + L.o_hist);
   sortscr_d = (int*)(b + L.o_sortscr);
+  xs_d = prec == HSMA_FP64 ? nullptr : (float4*)(b + L.o_xs);
   boxes_d = (float4*)(b + L.o_boxes);
   itord_d = (int2*)(b + L.o_itord);
   r0_d = (double*)(b + L.o_r0);
@@ -588,10 +590,10 @@ void Engine::issue_build()
     cudaEventRecord(ev_fork, stream);
     cudaStreamWaitEvent(side, ev_fork, 0);
     PriorityScope ps(prio_hi);
-    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, key_d, hist_d, sortscr_d, perm_d, iperm_d, nullptr,
-                 0, side);
-    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d, prec,
-                  status_d, side);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
+                 xs_d, status_d, nullptr, 0, side);
+    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
+                  prec, status_d, side);
     cudaEventRecord(ev_join, side);
   }
   launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, tables(), prec, mom_d, L.mom_stride, stream);
@@ -673,10 +675,10 @@ void Engine::issue_fused()
   const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d}, srf{it4x_d + L.nRK, nS, ctr_pairs_d}, none{nullptr, 0, nullptr};
   {
     PriorityScope ps(prio_hi);
-    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
-                 ctr_pairs_d, 2, side);
-    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d, prec,
-                  status_d, side);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
+                 xs_d, status_d, ctr_pairs_d, 2, side);
+    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
+                  prec, status_d, side);
   }
   cudaEventRecord(ev_img, side);
   launch_pair_items(rk, none, grid_rk, side);

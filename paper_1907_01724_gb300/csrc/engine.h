@@ -44,7 +44,7 @@ struct Layout {
   int max_req = 1, ditem_cap = 1, mitem_cap = 1;
   size_t o_dreq = 0, o_ditems = 0, o_dreqit = 0, o_mitems = 0, o_dpart = 0, o_de = 0;
   size_t o_sb = 0, o_coef2 = 0, o_itsb = 0;
-  size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_sortscr = 0, o_boxes = 0, o_itord = 0;
+  size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_sortscr = 0, o_xs = 0, o_boxes = 0, o_itord = 0;
   size_t o_redctr = 0;
   size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0;
   size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0, o_it4x = 0;
@@ -109,6 +109,7 @@ class Engine {
   int* key_d = nullptr;            // cell key of every charge
   int* hist_d = nullptr;           // cell histogram per system (zero between builds)
   int* sortscr_d = nullptr;        // scratch of the order's sort (2 ints per charge)
+  float4* xs_d = nullptr;          // FP32 path: (hi, lo) split of the inputs (k_order_keys)
   float4* boxes_d = nullptr;      // bounding boxes of 32 consecutive sorted records
   int2* itord_d = nullptr;
   cudaStream_t side = nullptr;    // second stream of the build (order + records beside the moments)

@@ -122,6 +122,11 @@ struct SysDev {
   float dc2;          // squared near distance of the FP32 pair-sum box test, (kNearRel a)^2
   long long sb;       // offset (8-byte slots) of its auxiliary-sphere solid-harmonic table (M x P)
   long long bb;       // first 32-record box of this system (real boxes, then Kelvin boxes)
+  // double-float (hi, lo) constants of the FP32 path's record arithmetic (k_setup): k/eps1, a,
+  // a^2, and q_K = q (qk1 r_K + qk0) with qk1 = (k/(eps1 a)) (gamma - dbar/2),
+  // qk0 = (k/(eps1 a)) dbar R_tau / 2; rc2 = (2 kCentreRel a)^2 (FP32)
+  float2 f_kc, f_a, f_a2, f_qk1, f_qk0;
+  float f_rc2;
 };
 
 // Spatial order (k_order.cu): charges sorted by the Morton index of their cell on a 16^3 grid
@@ -136,8 +141,12 @@ constexpr int kOrderGrid = 16;
 constexpr int kOrderCells = kOrderGrid * kOrderGrid * kOrderGrid;
 constexpr int kOrderBlock = 256;  // charges per k_order_keys / k_images work item
 void init_order_kernels();  // one-time function attributes (call outside stream capture)
-void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, int* key, int* hist,
-                  int* scr, int* perm, int* iperm, unsigned int* ctr_reset, int nreset, cudaStream_t st);
+// xs (FP32 path, else null): 2 float4 per charge in input order, the (hi, lo) split of
+// (x, y, z, q): xs[2 g] = hi parts, xs[2 g + 1] = lo parts.  status: kStOutside for a charge at
+// |x| >= a or with a non-finite coordinate or charge.
+void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, const double* q,
+                  int* key, int* hist, int* scr, int* perm, int* iperm, float4* xs, int* status,
+                  unsigned int* ctr_reset, int nreset, cudaStream_t st);
 // Boxes of 32 consecutive sorted records: a warp's targets and a box farther apart than
 // kNearRel a use plain FP32 coordinates in the pair sum, nearer ones the hi/lo-split form.
 constexpr int kBox = 32;
@@ -169,8 +178,8 @@ constexpr int kCoefChunk = 32;  // coefficients per k_coef_reduce block
 // Records at sorted positions (items = (system, block of kOrderBlock sorted positions)); the
 // FP32 path also writes the boxes (2 float4 per box: min and max of the hi coordinates).
 void launch_images(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
-                   const int* perm, float4* src_hi, float4* src_lo, dbl4* src64, float4* boxes, int prec, int* status,
-                   cudaStream_t st);
+                   const float4* xs, const int* perm, float4* src_hi, float4* src_lo, dbl4* src64, float4* boxes,
+                   int prec, int* status, cudaStream_t st);
 void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
                     Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st);
 int moment_smem_group(int maxP);

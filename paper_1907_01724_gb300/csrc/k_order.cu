@@ -6,8 +6,10 @@
 // and a 32-source sub-tile each occupy a small box, and the pair kernel evaluates the pairs of
 // well-separated boxes with plain FP32 coordinates, keeping the hi/lo-split form for near ones.
 //   k_order_keys   cell key per charge and the cell histogram of its system (global integer
-//                  atomics; many small blocks: the key is FP64 arithmetic, which this GPU
-//                  issues at a low rate per SM)
+//                  atomics), the check that the charge lies inside the cavity and, for the FP32
+//                  path, the (hi, lo) split of its coordinates and charge (64-thread blocks: this
+//                  is the FP64 arithmetic of the build's record chain, which this GPU issues at
+//                  a low rate per SM, so it is spread over many SMs)
 //   k_order_sort   one block per system: exclusive scan of the histogram, scatter to the cells
 //                  (atomic cursor in shared memory: any order inside a cell), then every slot
 //                  finds its place in its cell by counting the cell's smaller input indices (the
@@ -37,20 +39,37 @@ __device__ __forceinline__ int cell_key(const SysDev& S, double x, double y, dou
   return (int)(spread3((unsigned)ix) | (spread3((unsigned)iy) << 1) | (spread3((unsigned)iz) << 2));
 }
 
-__global__ __launch_bounds__(kOrderBlock) void k_order_keys(const SysDev* __restrict__ sys, const int2* __restrict__ items,
-                                                            const double* __restrict__ xyz, int* __restrict__ key,
-                                                            int* __restrict__ hist, unsigned int* __restrict__ ctr_reset,
-                                                            int nreset)
+__device__ __forceinline__ float2 split_pair(double x)
+{
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+constexpr int kKeyThreads = 64;
+constexpr int kKeySplit = kOrderBlock / kKeyThreads;
+__global__ __launch_bounds__(kKeyThreads) void k_order_keys(const SysDev* __restrict__ sys, const int2* __restrict__ items,
+                                                            const double* __restrict__ xyz, const double* __restrict__ q,
+                                                            int* __restrict__ key, int* __restrict__ hist,
+                                                            float4* __restrict__ xs, int* __restrict__ status,
+                                                            unsigned int* __restrict__ ctr_reset, int nreset)
 {
   if (blockIdx.x == 0 && (int)threadIdx.x < nreset) ctr_reset[threadIdx.x] = 0u;
-  const int2 it = items[blockIdx.x];
+  const int2 it = items[blockIdx.x / kKeySplit];
   const SysDev& S = sys[it.x];
-  const int i = it.y * kOrderBlock + threadIdx.x;
+  const int i = it.y * kOrderBlock + (blockIdx.x % kKeySplit) * kKeyThreads + threadIdx.x;
   if (i >= S.n) return;
   const long long g = S.chg + i;
-  const int k = cell_key(S, xyz[3 * g], xyz[3 * g + 1], xyz[3 * g + 2]);
+  const double x = xyz[3 * g], y = xyz[3 * g + 1], z = xyz[3 * g + 2], qg = q[g];
+  const int k = cell_key(S, x, y, z);
   key[g] = k;
   atomicAdd(&hist[(size_t)it.x * kOrderCells + k], 1);
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+  if (!(r2 < S.a * S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qg)) atomicOr(status, kStOutside);
+  if (xs) {
+    const float2 sx = split_pair(x), sy = split_pair(y), sz = split_pair(z), sq = split_pair(qg);
+    xs[2 * g] = make_float4(sx.x, sy.x, sz.x, sq.x);
+    xs[2 * g + 1] = make_float4(sx.y, sy.y, sz.y, sq.y);
+  }
 }
 
 // One block per system.  s_cell holds the first sorted position of every cell (exclusive scan
@@ -160,11 +179,13 @@ void init_order_kernels()
   cudaFuncSetAttribute(k_order_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * sizeof(int) * kOrderSmemN);
 }
 
-void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, int* key, int* hist,
-                  int* scr, int* perm, int* iperm, unsigned int* ctr_reset, int nreset, cudaStream_t st)
+void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, const double* q,
+                  int* key, int* hist, int* scr, int* perm, int* iperm, float4* xs, int* status,
+                  unsigned int* ctr_reset, int nreset, cudaStream_t st)
 {
   if (nitems <= 0 || nsys <= 0) return;
-  launch_k(k_order_keys, nitems, kOrderBlock, 0, st, false, sys, items, xyz, key, hist, ctr_reset, nreset);
+  launch_k(k_order_keys, nitems * kKeySplit, kKeyThreads, 0, st, false, sys, items, xyz, q, key, hist, xs, status,
+           ctr_reset, nreset);
   launch_k(k_order_sort, nsys, kSortThreads, 2 * sizeof(int) * kOrderSmemN, st, false, sys, (const int*)key, hist, scr,
            perm, iperm);
 }

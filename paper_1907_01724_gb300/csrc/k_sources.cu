@@ -105,6 +105,12 @@ __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__
       d.kc_a = d.kc / d.a;
       d.Rt_a = d.Rtau / d.a;
       d.inv_Rt = 1.0 / d.Rtau;
+      d.f_kc = pair_of(d.kc);
+      d.f_a = pair_of(d.a);
+      d.f_a2 = pair_of(d.a * d.a);
+      d.f_qk1 = pair_of(d.kc_a * (d.gam - 0.5 * d.dbar));
+      d.f_qk0 = pair_of(d.kc_a * d.dbar * d.Rtau * 0.5);
+      d.f_rc2 = (float)(4.0 * (kCentreRel * d.a) * (kCentreRel * d.a));
       double t = d.mu;
       for (int n = 0; n <= d.p; ++n) {
         Mn[d.mn + n] = -((1.0 - d.eps) * (n + 1) + t) / ((1.0 + d.eps) * n + 1.0 + t);
@@ -342,15 +348,17 @@ __device__ __forceinline__ KelvinRec kelvin_rec(const SysDev& S, double x, doubl
 // (hi x, hi y, hi z, Q) and (lo x, lo y, lo z, 0) and, per warp (32 consecutive records), the
 // bounding box of the hi coordinates (min, max as two float4) of the real and of the Kelvin
 // records.
-// Blocks of 64 threads (four per item): the image geometry is FP64, and on this GPU the FP64 pipe
-// of one SM issues 1.6 operations per clock, so the work is spread over four times as many SMs.
+// Blocks of 64 threads (four per item): small blocks find room beside the moment kernel; the
+// FP64 path's image geometry is FP64, which this GPU issues at a low rate per SM, so it is
+// spread over four times as many SMs.
 constexpr int kImgThreads = 64;
 constexpr int kImgSplit = kOrderBlock / kImgThreads;
 __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict__ sys, const int2* __restrict__ items,
                                                         const double* __restrict__ xyz, const double* __restrict__ q,
-                                                        const int* __restrict__ perm, float4* __restrict__ src_hi,
-                                                        float4* __restrict__ src_lo, dbl4* __restrict__ src64,
-                                                        float4* __restrict__ boxes, int prec, int* __restrict__ status)
+                                                        const float4* __restrict__ xs, const int* __restrict__ perm,
+                                                        float4* __restrict__ src_hi, float4* __restrict__ src_lo,
+                                                        dbl4* __restrict__ src64, float4* __restrict__ boxes, int prec,
+                                                        int* __restrict__ status)
 {
   const int2 it = items[blockIdx.x / kImgSplit];
   const SysDev& S = sys[it.x];
@@ -365,44 +373,38 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
   }
   if (i < n) {
     const long long gi = S.chg + perm[S.chg + i];
-    const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
     const long long sr = S.src + i, sk = S.src + n + i;
     if (prec == HSMA_FP64) {
+      const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
       const KelvinRec k = kelvin_rec(S, x, y, z, qi);
       if (!(k.r < S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) atomicOr(status, kStOutside);
       src64[sr] = make_dbl4(x, y, z, S.kc * qi);
       src64[sk] = make_dbl4(k.kx, k.ky, k.kz, k.QK);
     } else {
-      // the Kelvin point in double-float arithmetic from the exact-ish r^2 (FP64 square root and
-      // division cost hundreds of cycles here): s = (a/r)^2 = a^2 (1/r^2), r_K xhat = s x,
-      // r_K = a sqrt(s); the (hi, lo) result is the record's split directly
-      const double r2d = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
-      if (!(r2d < S.a * S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi))
-        atomicOr(status, kStOutside);
-      float hx, hy, hz, lx, ly, lz;
-      split2(x, hx, lx);
-      split2(y, hy, ly);
-      split2(z, hz, lz);
-      src_hi[sr] = make_float4(hx, hy, hz, (float)(S.kc * qi));
-      src_lo[sr] = make_float4(lx, ly, lz, 0.f);
-      bmin[0] = bmax[0] = hx;
-      bmin[1] = bmax[1] = hy;
-      bmin[2] = bmax[2] = hz;
-      // centre test as in kelvin_rec and k_moments (on r = sqrt(r^2)); the square root is taken
-      // only for charges that can pass it
-      const double rc = kCentreRel * S.a;
-      if (r2d <= 4.0 * rc * rc && sqrt(r2d) <= rc) {
+      // from the (hi, lo) split of k_order_keys, in double-float arithmetic on the FP32 pipes
+      // (FP64 only for a charge within 2 kCentreRel a of the centre): r^2, s = a^2 / r^2,
+      // the Kelvin point s x (its (hi, lo) pair is the record's split), r_K = a sqrt(s) and
+      // q_K = q (qk1 r_K + qk0)
+      const float4 h = xs[2 * gi], l = xs[2 * gi + 1];
+      const df X = df_make(h.x, l.x), Y = df_make(h.y, l.y), Z = df_make(h.z, l.z), Q = df_make(h.w, l.w);
+      src_hi[sr] = make_float4(h.x, h.y, h.z, (df_make(S.f_kc.x, S.f_kc.y) * Q).hi);
+      src_lo[sr] = make_float4(l.x, l.y, l.z, 0.f);
+      bmin[0] = bmax[0] = h.x;
+      bmin[1] = bmax[1] = h.y;
+      bmin[2] = bmax[2] = h.z;
+      const df r2 = X * X + Y * Y + Z * Z;
+      // centre test as in kelvin_rec and k_moments, on r = sqrt(r^2) (to within the rounding of r^2)
+      if (r2.hi <= S.f_rc2 && sqrt(df_to_double(r2)) <= kCentreRel * S.a) {
         // image at infinity (its constant potential is added by k_moments): a zero-strength
         // record, left out of the box
         src_hi[sk] = make_float4((float)(1e15 * S.a), 0.f, 0.f, 0.f);
         src_lo[sk] = make_float4(0.f, 0.f, 0.f, 0.f);
       } else {
-        const df da = df_from_double(S.a);
-        const df s = (da * da) * df_recip(df_from_double(r2d));
-        const df kx = s * df_make(hx, lx), ky = s * df_make(hy, ly), kz = s * df_make(hz, lz);
-        const double rK = df_to_double(da * df_sqrt(s));
-        const double QK = S.kc * (qi * S.inv_a * (S.gam * rK + S.dbar * (S.Rtau - rK) * 0.5));
-        src_hi[sk] = make_float4(kx.hi, ky.hi, kz.hi, (float)QK);
+        const df s = df_make(S.f_a2.x, S.f_a2.y) * df_recip(r2);
+        const df kx = s * X, ky = s * Y, kz = s * Z;
+        const df rK = df_make(S.f_a.x, S.f_a.y) * df_sqrt(s);
+        const df QK = Q * (df_make(S.f_qk1.x, S.f_qk1.y) * rK + df_make(S.f_qk0.x, S.f_qk0.y));
+        src_hi[sk] = make_float4(kx.hi, ky.hi, kz.hi, QK.hi);
         src_lo[sk] = make_float4(kx.lo, ky.lo, kz.lo, 0.f);
         bmin[3] = bmax[3] = kx.hi;
         bmin[4] = bmax[4] = ky.hi;
@@ -429,12 +431,12 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
 }
 
 void launch_images(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
-                   const int* perm, float4* src_hi, float4* src_lo, dbl4* src64, float4* boxes, int prec, int* status,
-                   cudaStream_t st)
+                   const float4* xs, const int* perm, float4* src_hi, float4* src_lo, dbl4* src64, float4* boxes,
+                   int prec, int* status, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  launch_k(k_images, nitems * kImgSplit, kImgThreads, 0, st, false, sys, items, xyz, q, perm, src_hi, src_lo, src64,
-           boxes, prec, status);
+  launch_k(k_images, nitems * kImgSplit, kImgThreads, 0, st, false, sys, items, xyz, q, xs, perm, src_hi, src_lo,
+           src64, boxes, prec, status);
 }
 
 // Charge moments of the correction coefficients.  Thread t of a block prepares charge c0 + t
@@ -450,7 +452,6 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
                                                          Tables tab, double* __restrict__ mom, int mom_stride, int G)
 {
   extern __shared__ double sm[];
-  allow_dependents();
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int n = S.n, P = S.P, p = S.p;
@@ -576,6 +577,9 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
     }
     __syncthreads();
   }
+  // the coefficient kernel may launch once every moment block is here: earlier, its CTAs would
+  // hold SM resources (waiting) that the order and the records need beside this kernel
+  allow_dependents();
 #pragma unroll
   for (int j = 0; j < MAXJ; ++j) {
     const int idx = tid + j * kMomThreads;
@@ -664,8 +668,8 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
 {
   __shared__ R su[kCoefWarps][kCoefChunk], sv[kCoefWarps][kCoefChunk];
   __shared__ double sr[kCoefWarps];
-  allow_dependents();
   grid_dependency_wait();  // the moment rows of k_moments
+  allow_dependents();      // (the surface kernel's CTAs wait only while this kernel works)
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P;
