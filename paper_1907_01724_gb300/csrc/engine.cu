@@ -616,7 +616,8 @@ void Engine::issue_pot()
   cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), stream);
   if (!L.it4.empty()) {
     cudaEventRecordWithFlags(ev_pair0, stream, cudaEventRecordExternal);
-    const PairWork all{it4_d, (int)L.it4.size(), ctr_pairs_d}, none{nullptr, 0, nullptr};
+    const int nit = (int)L.it4.size();
+    const PairWork all{it4_d, nit, ctr_pairs_d, std::min(L.pair_grid, nit)}, none{nullptr, 0, nullptr, 0};
     if (prec == HSMA_FP64)
       launch_pairs_f64(L.pair_grid, sys_d, all, none, src64_d, surf64a_d, surf64b_d, part64_d, stream);
     else
@@ -672,7 +673,8 @@ void Engine::issue_fused()
   // launch last, so that its CTAs take only what the chains leave free; k_order_keys also
   // zeroes both pair work counters (ctr_pairs_d and ctr_pairs2_d, adjacent), which the main
   // stream's launch uses only after ev_img
-  const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d}, srf{it4x_d + L.nRK, nS, ctr_pairs_d}, none{nullptr, 0, nullptr};
+  const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d, std::min(grid_rk, L.nRK)};
+  const PairWork srf{it4x_d + L.nRK, nS, ctr_pairs_d, std::min(grid_s, nS)}, none{nullptr, 0, nullptr, 0};
   {
     PriorityScope ps(prio_hi);
     launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,

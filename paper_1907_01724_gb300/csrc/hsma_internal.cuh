@@ -215,12 +215,15 @@ int pairs_f32_occupancy(int cfg);
 int pairs_f64_occupancy();
 constexpr int kF64TargetsPerBlock = 128;
 constexpr int kReduceTargetsPerBlock = 32;
-// A list of pair work items pulled through an atomic counter (zero before the first launch that
-// uses it); counter == nullptr: no list.
+// A list of pair work items.  Items [0, first) are the first items of CTAs 0 .. first - 1 of the
+// launch that has the list as w1 (no atomic: a grid-wide first fetch from one counter serialises
+// thousands of atomics); the rest are pulled through an atomic counter (zero before the first
+// launch that uses it) as first + counter.  counter == nullptr: no list.
 struct PairWork {
   const int4* items;
   int nitems;
   unsigned int* counter;
+  int first;
 };
 // Persistent pair-sum launches: each CTA takes items of w1 until it is exhausted, then of w2.
 void launch_pairs_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,

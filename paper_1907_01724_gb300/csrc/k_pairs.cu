@@ -76,19 +76,26 @@ __device__ __forceinline__ ChunkInfo decode_chunk(const SysDev& S, int c)
   return ci;
 }
 
-// Next work item of a persistent CTA (thread 0): items of w1 first, then, when w1 is exhausted,
-// items of w2 (if any).  list = 0 or 1 names the list of the item, 2 means no work left.
-__device__ __forceinline__ void next_pair_item(const PairWork& w1, const PairWork& w2, int list, int& s_item,
-                                               int& s_list)
+// Next work item of a persistent CTA (thread 0): items of w1 first (the CTA's own item of the
+// static round on its first fetch, then the counter), then, when w1 is exhausted, items of w2
+// (if any).  list = 0 or 1 names the list of the item, 2 means no work left.
+__device__ __forceinline__ void next_pair_item(const PairWork& w1, const PairWork& w2, int list, bool first_fetch,
+                                               int& s_item, int& s_list)
 {
   int v = 0;
   if (list == 0) {
-    v = (int)atomicAdd(w1.counter, 1u);
-    if (v >= w1.nitems) list = 1;
+    if (first_fetch && (int)blockIdx.x < w1.first) {
+      v = (int)blockIdx.x;
+    } else if (w1.first < w1.nitems) {
+      v = w1.first + (int)atomicAdd(w1.counter, 1u);
+      if (v >= w1.nitems) list = 1;
+    } else {
+      list = 1;
+    }
   }
   if (list == 1) {
-    if (w2.counter) {
-      v = (int)atomicAdd(w2.counter, 1u);
+    if (w2.counter && w2.first < w2.nitems) {
+      v = w2.first + (int)atomicAdd(w2.counter, 1u);
       if (v >= w2.nitems) list = 2;
     } else {
       list = 2;
@@ -171,8 +178,10 @@ __global__ __launch_bounds__(kF64Threads) void k_pairs_f64(const SysDev* __restr
   __shared__ int s_item, s_list;
   const int tid = threadIdx.x;
   int list = 0;
+  bool first_fetch = true;
   for (;;) {
-    if (tid == 0) next_pair_item(w1, w2, list, s_item, s_list);
+    if (tid == 0) next_pair_item(w1, w2, list, first_fetch, s_item, s_list);
+    first_fetch = false;
     __syncthreads();
     const int item = s_item;
     list = s_list;

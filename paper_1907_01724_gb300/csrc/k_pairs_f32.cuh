@@ -22,9 +22,11 @@ __global__ __launch_bounds__(NT) void k_pairs_f32(const SysDev* __restrict__ sys
   __shared__ int s_item, s_list;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int list = 0;
+  bool first_fetch = true;
 
   for (;;) {
-    if (tid == 0) next_pair_item(w1, w2, list, s_item, s_list);
+    if (tid == 0) next_pair_item(w1, w2, list, first_fetch, s_item, s_list);
+    first_fetch = false;
     __syncthreads();
     const int item = s_item;
     list = s_list;

@@ -312,7 +312,8 @@ static int launch_energy(hsma_server_t* s, EnergySlot& sl, int chain)
     const int occ = e->prec == HSMA_FP64 ? e->occ_f64 : e->occ_f32[e->L.cfg];
     const int cap = std::max(1, (int)std::floor(s->sm_frac * e->num_sms * std::max(occ, 1)));
     const int grid = std::max(1, std::min((int)it4.size(), cap));
-    const hsma::PairWork w{sl.items_d, (int)it4.size(), sl.ctr_d}, none{nullptr, 0, nullptr};
+    const hsma::PairWork w{sl.items_d, (int)it4.size(), sl.ctr_d, std::min(grid, (int)it4.size())},
+        none{nullptr, 0, nullptr, 0};
     if (e->prec == HSMA_FP64)
       hsma::launch_pairs_f64(grid, e->sys_d, w, none, e->src64_d, e->surf64a_d, e->surf64b_d, e->part64_d, sl.st);
     else
