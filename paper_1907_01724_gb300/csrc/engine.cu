@@ -312,7 +312,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.totMom = mom;
   L.totPart = part;
   L.totBoxes = boxes;
-  L.mom_stride = (int)align_up(2 * (size_t)L.maxP + 1, 2);
+  L.mom_stride = (int)align_up((size_t)L.maxP + 1, 2);
   L.pair_grid = (int)std::max<size_t>(1, std::min<size_t>(L.it4.size(), (size_t)slots));
 
   // workspace plan
@@ -596,7 +596,7 @@ void Engine::issue_build()
                   prec, status_d, side);
     cudaEventRecord(ev_join, side);
   }
-  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, tables(), prec, mom_d, L.mom_stride, stream);
+  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, Mn_d, tables(), prec, mom_d, L.mom_stride, stream);
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
   launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
@@ -686,7 +686,7 @@ void Engine::issue_fused()
   launch_pair_items(rk, none, grid_rk, side);
   cudaEventRecord(ev_join, side);
   PriorityScope ps(prio_mid);
-  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, tables(), prec, mom_d, L.mom_stride, stream);
+  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, Mn_d, tables(), prec, mom_d, L.mom_stride, stream);
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
   launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,

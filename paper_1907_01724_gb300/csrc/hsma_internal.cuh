@@ -180,8 +180,10 @@ constexpr int kCoefChunk = 32;  // coefficients per k_coef_reduce block
 void launch_images(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
                    const float4* xs, const int* perm, float4* src_hi, float4* src_lo, dbl4* src64, float4* boxes,
                    int prec, int* status, cudaStream_t st);
+// Moment rows: per block, sum_i q_i (M_n - gamma - c_i) T_nm(x_i/a) for the P coefficients
+// (slots 0 .. P-1) and the block's centre constant (slot P).
 void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
-                    Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st);
+                    const double* Mn, Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st);
 int moment_smem_group(int maxP);
 // Moments are stored in the moment arithmetic (FP64 path: double; FP32 path: FP32 (hi, lo)
 // pairs), one 8-byte slot each; the coefficients as double (coef) and as (hi, lo) pairs (coef2).

@@ -26,9 +26,10 @@
 //         = (k/(eps1 a)) [ (M_n - gamma) U_nm - V_nm ],
 //   U_nm = sum_i q_i T_nm(x_i/a),  V_nm = sum_i q_i c_i T_nm(x_i/a),
 //   c_i = dbar (R_tau - r_K,i)/(2 r_K,i) = dbar (R_tau r_i/a^2 - 1)/2,
-// which is the per-charge hat M'_{n,i} = M_n - gamma - c_i of Sec. 2.4 split into two
-// charge moments.  Coefficient index: idx(n, m) = n^2 + n + m, m in [-n, n]; m < 0 holds
-// the sine part of order |m|.
+// which is the per-charge hat M'_{n,i} = M_n - gamma - c_i of Sec. 2.4; the moment kernel forms
+// the weights q_i hat M'_{n,i} once per (n, charge) and accumulates one sum per coefficient.
+// Coefficient index: idx(n, m) = n^2 + n + m, m in [-n, n]; m < 0 holds the sine part of order
+// |m|.
 #include <math.h>
 
 #include <cmath>
@@ -439,17 +440,18 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
            src64, boxes, prec, status);
 }
 
-// Charge moments of the correction coefficients.  Thread t of a block prepares charge c0 + t
-// (FP64): the centre constant of a charge at the centre, and its moment inputs u, v, w = x/a,
-// rho^2, q and q c in the moment arithmetic R (shared memory), so the moment phase runs on R
-// alone: per group of G charges, thread t computes the column pair j = t mod (p/2 + 1) of
-// charge t / (p/2 + 1) (solid_pair), then thread t accumulates coefficients t + j kMomThreads
-// over the group.  Moments are stored as R values in 8-byte slots; slot 2P holds the block's
-// centre constant.
+// Charge moments of the correction coefficients.  Thread t of a block prepares charge c0 + t:
+// the centre constant of a charge at the centre, and its moment inputs u, v, w = x/a, rho^2, q
+// and q c in the moment arithmetic R (shared memory), so the moment phase runs on R alone: per
+// group of G charges, the weights q (M_n - gamma) - q c of every (charge, n), thread t computes
+// the column pair j = t mod (p/2 + 1) of charge t / (p/2 + 1) (solid_pair), then thread t
+// accumulates coefficients t + j kMomThreads over the group.  Rows are stored as R values in
+// 8-byte slots; slot P holds the block's centre constant.
 template <int MAXJ, class R>
 __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restrict__ sys, const int2* __restrict__ items,
                                                          const double* __restrict__ xyz, const double* __restrict__ q,
-                                                         Tables tab, double* __restrict__ mom, int mom_stride, int G)
+                                                         const double* __restrict__ Mn, Tables tab,
+                                                         double* __restrict__ mom, int mom_stride, int G)
 {
   extern __shared__ double sm[];
   const int2 it = items[blockIdx.x];
@@ -469,6 +471,9 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
   R* cq = cr2 + kMomThreads;
   R* cqc = cq + kMomThreads;
   double* red = reinterpret_cast<double*>(cqc + kMomThreads);  // [kMomWarps]
+  const int np1 = tab.pmax + 1;
+  R* mg = reinterpret_cast<R*>(red + kMomWarps);  // [pmax + 1] M_n - gamma
+  R* wq = mg + np1;                               // [G][pmax + 1] q (M_n - gamma - c) of the group
 
   // the tile's charges are loaded first (the longest chain of dependent loads: item, system,
   // charges), the recurrence tables beside them
@@ -489,7 +494,7 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
     const int pm = tab.pmax;
     const int ntri = (pm + 1) * (pm + 2) / 2;
     if (2 * (size_t)ntri + pm + 1 <= kMomTableSlots) {
-      R* tb = reinterpret_cast<R*>(red + kMomWarps);
+      R* tb = wq + (size_t)G * np1;
       for (int i = tid; i < ntri; i += kMomThreads) {
         const R va = ra[i], vb = rb[i], vs = i <= pm ? sp[i] : Num<R>::zero();
         tb[i] = va;
@@ -533,6 +538,7 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
       cqc[tid] = Num<R>::from(qi * (dbar * (S.Rt_a * (r * inv_a) - 1.0) * 0.5));
     }
   }
+  if (tid <= p) mg[tid] = Num<R>::from(Mn[S.mn + tid] - S.gam);
   // block sum of the centre-charge constants (fixed order), reduced only when some charge of
   // the tile sits at the centre (FP64 shuffles in every warp cost more than the tile's prep)
   double* out = mom + (size_t)(S.mom + it.y) * mom_stride;
@@ -543,19 +549,33 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
     if (tid == 0) {
       double s = 0.0;
       for (int w = 0; w < kMomWarps; ++w) s += red[w];
-      out[2 * P] = s;
+      out[P] = s;
     }
   } else if (tid == 0) {
-    out[2 * P] = 0.0;
+    out[P] = 0.0;
   }
-  // charge moments U_nm, V_nm
-  R accU[MAXJ], accV[MAXJ];
+  // the block's rows of A'_nm / (k/(eps1 a)) = sum_i q_i (M_n - gamma - c_i) T_nm(x_i)
+  // (the moments (M_n - gamma) U_nm - V_nm with one accumulation per coefficient and charge:
+  // the weight of (n, charge) is formed once per group)
+  R acc[MAXJ];
+  int nidx[MAXJ];
 #pragma unroll
-  for (int j = 0; j < MAXJ; ++j) accU[j] = accV[j] = Num<R>::zero();
+  for (int j = 0; j < MAXJ; ++j) {
+    acc[j] = Num<R>::zero();
+    const int idx = tid + j * kMomThreads;
+    int nn = (int)sqrtf((float)idx);
+    while (nn * nn > idx) --nn;
+    while ((nn + 1) * (nn + 1) <= idx) ++nn;
+    nidx[j] = nn;
+  }
   const int npair = p / 2 + 1;
   const int tg = tid / npair, tj = tid - tg * npair;
   for (int g0 = 0; g0 < cnt; g0 += G) {
     const int gcount = min(G, cnt - g0);
+    for (int k = tid; k < gcount * (p + 1); k += kMomThreads) {
+      const int g = k / (p + 1), nn = k - g * (p + 1);
+      wq[g * np1 + nn] = Num<R>::mul_sub(cq[g0 + g], mg[nn], Num<R>::one(), cqc[g0 + g]);
+    }
     if (tg < gcount) {
       const int c = g0 + tg;
       solid_pair<R>(tj, p, cu[c], cv[c], cw[c], cr2[c], ra, rb, sp, T + (size_t)tg * P);
@@ -565,14 +585,9 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
     for (int j = 0; j < MAXJ; ++j) {
       const int idx = tid + j * kMomThreads;
       if (idx < P) {
-        R u = accU[j], v = accV[j];
-        for (int g = 0; g < gcount; ++g) {
-          const R t = T[(size_t)g * P + idx];
-          u = Num<R>::acc(u, cq[g0 + g], t);
-          v = Num<R>::acc(v, cqc[g0 + g], t);
-        }
-        accU[j] = Num<R>::norm(u);
-        accV[j] = Num<R>::norm(v);
+        R u = acc[j];
+        for (int g = 0; g < gcount; ++g) u = Num<R>::acc(u, wq[g * np1 + nidx[j]], T[(size_t)g * P + idx]);
+        acc[j] = Num<R>::norm(u);
       }
     }
     __syncthreads();
@@ -583,10 +598,7 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
 #pragma unroll
   for (int j = 0; j < MAXJ; ++j) {
     const int idx = tid + j * kMomThreads;
-    if (idx < P) {
-      Num<R>::st(out, idx, accU[j]);
-      Num<R>::st(out, P + idx, accV[j]);
-    }
+    if (idx < P) Num<R>::st(out, idx, acc[j]);
   }
 }
 
@@ -602,10 +614,10 @@ int moment_smem_group(int maxP)
 {
   int pmax = (int)std::lround(std::sqrt((double)maxP)) - 1;
   if (pmax < 0) pmax = 0;
-  const size_t fixed = (6 * (size_t)kMomThreads + kMomWarps + moment_table_slots(pmax)) * sizeof(double);
+  const size_t fixed = (6 * (size_t)kMomThreads + kMomWarps + (pmax + 1) + moment_table_slots(pmax)) * sizeof(double);
   const size_t budget = 192 * 1024;
   int G = kMomThreads / (pmax / 2 + 1);
-  const int Gs = (int)((budget - fixed) / ((size_t)maxP * sizeof(double)));
+  const int Gs = (int)((budget - fixed) / (((size_t)maxP + pmax + 1) * sizeof(double)));
   if (G > Gs) G = Gs;
   if (G < 1) G = 1;
   return G;
@@ -615,49 +627,51 @@ static size_t moment_smem_bytes(int maxP)
 {
   int pmax = (int)std::lround(std::sqrt((double)maxP)) - 1;
   if (pmax < 0) pmax = 0;
-  return ((size_t)moment_smem_group(maxP) * maxP + 6 * (size_t)kMomThreads + kMomWarps +
+  return ((size_t)moment_smem_group(maxP) * (maxP + pmax + 1) + 6 * (size_t)kMomThreads + kMomWarps + (pmax + 1) +
           moment_table_slots(pmax)) *
          sizeof(double);
 }
 
 template <int MAXJ>
 static void launch_mom(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
-                       Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
+                       const double* Mn, Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
 {
   const int G = moment_smem_group(maxP);
   const size_t smem = moment_smem_bytes(maxP);
   if (prec == HSMA_FP64)
-    launch_k(k_moments<MAXJ, double>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, tab, mom, mom_stride, G);
+    launch_k(k_moments<MAXJ, double>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, Mn, tab, mom, mom_stride,
+             G);
   else
-    launch_k(k_moments<MAXJ, df>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, tab, mom, mom_stride, G);
+    launch_k(k_moments<MAXJ, df>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, Mn, tab, mom, mom_stride, G);
 }
 
 void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
-                    Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
+                    const double* Mn, Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
 {
   if (nitems <= 0) return;
   const int J = (maxP + kMomThreads - 1) / kMomThreads;
   if (J <= 1)
-    launch_mom<1>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
+    launch_mom<1>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 2)
-    launch_mom<2>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
+    launch_mom<2>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 4)
-    launch_mom<4>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
+    launch_mom<4>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 8)
-    launch_mom<8>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
+    launch_mom<8>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 16)
-    launch_mom<16>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
+    launch_mom<16>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else
-    launch_mom<26>(sys, items, nitems, maxP, xyz, q, tab, prec, mom, mom_stride, st);
+    launch_mom<26>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
 }
 
 // ---------------------------------------------------------------------------------------
-// hat A'_nm = (k/(eps1 a)) [(M_n - gamma) U_nm - V_nm].  A block owns kCoefChunk coefficients
-// (one per lane); its kCoefWarps warps split the moment blocks (warp w takes blocks w,
-// w + kCoefWarps, ...), and warp 0 adds the warp sums in order, so the result does not depend
-// on scheduling.  Sums run in the moment arithmetic R; the coefficient is formed in FP64 and
-// also stored as an FP32 (hi, lo) pair for the FP32 path's surface synthesis.
-constexpr int kCoefWarps = 32;
+// hat A'_nm = (k/(eps1 a)) [(M_n - gamma) U_nm - V_nm] = (k/(eps1 a)) sum over the moment rows
+// (each row holds sum_i q_i (M_n - gamma - c_i) T_nm(x_i/a) over its block's charges).  A block
+// owns kCoefChunk coefficients (one per lane); its kCoefWarps warps split the rows (warp w takes
+// rows w, w + kCoefWarps, ...), and warp 0 adds the warp sums in order, so the result does not
+// depend on scheduling.  Sums run in the moment arithmetic R; the coefficient is formed in FP64
+// and also stored as an FP32 (hi, lo) pair for the FP32 path's surface synthesis.
+constexpr int kCoefWarps = 8;
 template <class R>
 __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* __restrict__ sys,
                                                                  const int2* __restrict__ items,
@@ -666,65 +680,53 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
                                                                  double* __restrict__ coef, float2* __restrict__ coef2,
                                                                  double* __restrict__ r0)
 {
-  __shared__ R su[kCoefWarps][kCoefChunk], sv[kCoefWarps][kCoefChunk];
+  __shared__ R su[kCoefWarps][kCoefChunk];
   __shared__ double sr[kCoefWarps];
-  grid_dependency_wait();  // the moment rows of k_moments
-  allow_dependents();      // (the surface kernel's CTAs wait only while this kernel works)
+  // the item and its system are read before the wait for the moment rows
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
-  const int P = S.P;
+  const int P = S.P, nb = S.mom_blocks;
+  const double kc_a = S.kc_a;
+  const double* base = mom + (size_t)S.mom * mom_stride;
+  grid_dependency_wait();  // the moment rows of k_moments
+  allow_dependents();      // (the surface kernel's CTAs wait only while this kernel works)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int idx = it.y * kCoefChunk + lane;
-  const double* base = mom + (size_t)S.mom * mom_stride;
-  R U = Num<R>::zero(), V = Num<R>::zero();
+  R U = Num<R>::zero();
   double Rs = 0.0;
   if (idx < P) {
-    // rows b = warp, warp + kCoefWarps, ... in ascending order, five rows' loads in flight
-    // (1024-thread blocks have 64 registers per thread)
-    constexpr int kRows = 5;
-    for (int b0 = warp; b0 < S.mom_blocks; b0 += kRows * kCoefWarps) {
-      R u[kRows], v[kRows];
+    // rows b = warp, warp + kCoefWarps, ... in ascending order, twelve rows' loads in flight
+    constexpr int kRows = 12;
+    for (int b0 = warp; b0 < nb; b0 += kRows * kCoefWarps) {
+      R u[kRows];
 #pragma unroll
       for (int k = 0; k < kRows; ++k) {
         const int b = b0 + k * kCoefWarps;
-        u[k] = b < S.mom_blocks ? Num<R>::ld(base, (long long)b * mom_stride + idx) : Num<R>::zero();
-        v[k] = b < S.mom_blocks ? Num<R>::ld(base, (long long)b * mom_stride + P + idx) : Num<R>::zero();
+        u[k] = b < nb ? Num<R>::ld(base, (long long)b * mom_stride + idx) : Num<R>::zero();
       }
 #pragma unroll
-      for (int k = 0; k < kRows; ++k) {
-        if (b0 + k * kCoefWarps < S.mom_blocks) {
-          U = U + u[k];
-          V = V + v[k];
-        }
-      }
+      for (int k = 0; k < kRows; ++k)
+        if (b0 + k * kCoefWarps < nb) U = U + u[k];
     }
   }
   if (it.y == 0 && lane == 0)
-    for (int b = warp; b < S.mom_blocks; b += kCoefWarps) Rs += base[(size_t)b * mom_stride + 2 * P];
+    for (int b = warp; b < nb; b += kCoefWarps) Rs += base[(size_t)b * mom_stride + P];
   su[warp][lane] = U;
-  sv[warp][lane] = V;
   if (lane == 0) sr[warp] = Rs;
   __syncthreads();
   if (warp == 0) {
     U = Num<R>::zero();
-    V = Num<R>::zero();
-#pragma unroll 4
-    for (int w = 0; w < kCoefWarps; ++w) {
-      U = U + su[w][lane];
-      V = V + sv[w][lane];
-    }
+#pragma unroll
+    for (int w = 0; w < kCoefWarps; ++w) U = U + su[w][lane];
     if (idx < P) {
-      int nn = (int)sqrtf((float)idx);
-      while (nn * nn > idx) --nn;
-      while ((nn + 1) * (nn + 1) <= idx) ++nn;
-      const double c = S.kc_a * ((Mn[S.mn + nn] - S.gam) * Num<R>::to(U) - Num<R>::to(V));
+      const double c = kc_a * Num<R>::to(U);
       coef[S.coef + idx] = c;
       coef2[S.coef + idx] = pair_of(c);
     }
     if (it.y == 0 && lane == 0) {
-      double s = 0.0;
-      for (int w = 0; w < kCoefWarps; ++w) s += sr[w];
-      r0[it.x] = s;
+      double t = 0.0;
+      for (int w = 0; w < kCoefWarps; ++w) t += sr[w];
+      r0[it.x] = t;
     }
   }
 }
