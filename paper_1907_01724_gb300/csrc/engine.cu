@@ -192,7 +192,11 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     totn_all += ns[s];
     maxP_all = std::max(maxP_all, (spec[s].p + 1) * (spec[s].p + 1));
   }
-  const int G = moment_smem_group(maxP_all);
+  // charges per moment group: the largest group when the moment blocks fit in about one wave,
+  // half-size shared memory (two blocks per SM) when there are many waves
+  int G = moment_smem_group(maxP_all, 1);
+  if (totn_all > 4 * (int64_t)num_sms * G) G = moment_smem_group(maxP_all, 2);
+  L.momG = G;
   L.sd.resize(nsys);
   int64_t chg = 0, surf = 0, coef = 0, mn = 0, mom = 0, part = 0, boxes = 0;
   int k5 = 0;
@@ -596,7 +600,8 @@ void Engine::issue_build()
                   prec, status_d, side);
     cudaEventRecord(ev_join, side);
   }
-  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, Mn_d, tables(), prec, mom_d, L.mom_stride, stream);
+  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
+                 L.mom_stride, stream);
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
   launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
@@ -686,7 +691,8 @@ void Engine::issue_fused()
   launch_pair_items(rk, none, grid_rk, side);
   cudaEventRecord(ev_join, side);
   PriorityScope ps(prio_mid);
-  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, xyz_d, q_d, Mn_d, tables(), prec, mom_d, L.mom_stride, stream);
+  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
+                 L.mom_stride, stream);
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
   launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,

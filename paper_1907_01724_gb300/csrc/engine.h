@@ -26,6 +26,7 @@ struct Layout {
   std::vector<int2> itsb;     // (representative system, point block) of every surface-basis table
   std::vector<int2> itord;    // (system, block of kOrderBlock charges): spatial order and records
   int64_t totBoxes = 0;       // 32-record boxes (real + Kelvin) of all systems
+  int momG = 1;               // charges per moment group (k_moments)
   bool use_sb = false;        // surface synthesis through the basis tables
   int64_t totSB = 0;          // 8-byte slots of all basis tables
   std::vector<int4> it4;

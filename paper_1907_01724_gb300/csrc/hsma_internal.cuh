@@ -182,9 +182,11 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
                    int prec, int* status, cudaStream_t st);
 // Moment rows: per block, sum_i q_i (M_n - gamma - c_i) T_nm(x_i/a) for the P coefficients
 // (slots 0 .. P-1) and the block's centre constant (slot P).
-void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
-                    const double* Mn, Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st);
-int moment_smem_group(int maxP);
+// G: charges per moment group (moment_smem_group; the layout's tiles are multiples of it).
+void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const double* xyz,
+                    const double* q, const double* Mn, Tables tab, int prec, double* mom, int mom_stride,
+                    cudaStream_t st);
+int moment_smem_group(int maxP, int blocks_per_sm);
 // Moments are stored in the moment arithmetic (FP64 path: double; FP32 path: FP32 (hi, lo)
 // pairs), one 8-byte slot each; the coefficients as double (coef) and as (hi, lo) pairs (coef2).
 void launch_coef_reduce(const SysDev* sys, const int2* items, int nitems, const double* mom, int mom_stride,

@@ -610,34 +610,37 @@ static size_t moment_table_slots(int pmax)
   return s <= kMomTableSlots ? s : 0;
 }
 
-int moment_smem_group(int maxP)
+// blocks_per_sm = 2 halves the budget, so that two blocks (20 warps) share an SM: more warps to
+// hide the dependent double-float chains when there are many more blocks than SMs.
+int moment_smem_group(int maxP, int blocks_per_sm)
 {
   int pmax = (int)std::lround(std::sqrt((double)maxP)) - 1;
   if (pmax < 0) pmax = 0;
   const size_t fixed = (6 * (size_t)kMomThreads + kMomWarps + (pmax + 1) + moment_table_slots(pmax)) * sizeof(double);
-  const size_t budget = 192 * 1024;
+  const size_t budget = blocks_per_sm >= 2 ? 112 * 1024 : 192 * 1024;
   int G = kMomThreads / (pmax / 2 + 1);
-  const int Gs = (int)((budget - fixed) / (((size_t)maxP + pmax + 1) * sizeof(double)));
+  const size_t per = ((size_t)maxP + pmax + 1) * sizeof(double);
+  const int Gs = budget > fixed ? (int)((budget - fixed) / per) : 0;
   if (G > Gs) G = Gs;
   if (G < 1) G = 1;
   return G;
 }
 
-static size_t moment_smem_bytes(int maxP)
+static size_t moment_smem_bytes(int maxP, int G)
 {
   int pmax = (int)std::lround(std::sqrt((double)maxP)) - 1;
   if (pmax < 0) pmax = 0;
-  return ((size_t)moment_smem_group(maxP) * (maxP + pmax + 1) + 6 * (size_t)kMomThreads + kMomWarps + (pmax + 1) +
+  return ((size_t)G * (maxP + pmax + 1) + 6 * (size_t)kMomThreads + kMomWarps + (pmax + 1) +
           moment_table_slots(pmax)) *
          sizeof(double);
 }
 
 template <int MAXJ>
-static void launch_mom(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
-                       const double* Mn, Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
+static void launch_mom(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const double* xyz,
+                       const double* q, const double* Mn, Tables tab, int prec, double* mom, int mom_stride,
+                       cudaStream_t st)
 {
-  const int G = moment_smem_group(maxP);
-  const size_t smem = moment_smem_bytes(maxP);
+  const size_t smem = moment_smem_bytes(maxP, G);
   if (prec == HSMA_FP64)
     launch_k(k_moments<MAXJ, double>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, Mn, tab, mom, mom_stride,
              G);
@@ -645,23 +648,24 @@ static void launch_mom(const SysDev* sys, const int2* items, int nitems, int max
     launch_k(k_moments<MAXJ, df>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, Mn, tab, mom, mom_stride, G);
 }
 
-void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, const double* xyz, const double* q,
+void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const double* xyz,
+                    const double* q,
                     const double* Mn, Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
 {
   if (nitems <= 0) return;
   const int J = (maxP + kMomThreads - 1) / kMomThreads;
   if (J <= 1)
-    launch_mom<1>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<1>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 2)
-    launch_mom<2>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<2>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 4)
-    launch_mom<4>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<4>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 8)
-    launch_mom<8>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<8>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 16)
-    launch_mom<16>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<16>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else
-    launch_mom<26>(sys, items, nitems, maxP, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<26>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
 }
 
 // ---------------------------------------------------------------------------------------
