@@ -321,6 +321,22 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     o = S.chg + perm[S.chg + i];  // partials are in sorted order
     qi = q[o];
   }
+  // launch-local system r of this block (sel_rng ascending: the last r whose range starts at or
+  // before this block), found by thread 0 before the wait
+  int r_blk = 0, cnt_blk = 0;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nsel - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sel_rng[mid].x <= (int)blockIdx.x)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    r_blk = lo;
+    cnt_blk = sel_rng[lo].y;
+    s_r = lo;
+  }
   // (launched as a programmatic dependent of the pair kernel: everything above reads data that
   // the pair sum does not write; the partials below wait for it)
   grid_dependency_wait();
@@ -395,19 +411,9 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     epart[2 * blockIdx.x] = a;
     epart[2 * blockIdx.x + 1] = b;
     __threadfence();
-    // launch-local system r of this block (sel_rng ascending: the last r whose range starts at
-    // or before this block), and whether this block is the last of r's blocks to finish
-    int lo = 0, hi = nsel - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (sel_rng[mid].x <= (int)blockIdx.x)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    s_r = lo;
-    const unsigned prev = atomicAdd(&counter[lo], 1u);
-    last = (prev == (unsigned)sel_rng[lo].y - 1u);
+    // whether this block is the last of its system's blocks to finish
+    const unsigned prev = atomicAdd(&counter[r_blk], 1u);
+    last = (prev == (unsigned)cnt_blk - 1u);
   }
   __syncthreads();
   if (!last) return;
