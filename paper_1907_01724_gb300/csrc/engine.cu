@@ -140,6 +140,7 @@ Engine::~Engine()
   if (device >= 0) cudaSetDevice(device);
   drop_graphs();
   if (ws_owned && ws) cudaFree(ws);
+  if (energy_h) cudaFreeHost(energy_h);
   if (fpart_d) cudaFree(fpart_d);
   if (E_d) cudaFree(E_d);
   if (ev_pair0) cudaEventDestroy(ev_pair0);
@@ -789,7 +790,24 @@ int Engine::potentials()
     if (!L.it4.empty()) pair_timed = true;
   }
   pot_ready = true;
+  ++pot_epoch;
   field_ready = false;
+  return HSMA_OK;
+}
+
+// Enqueue the copy of every system's energies to the pinned mirror (after a potential pass on the
+// engine's stream); valid once the stream has been synchronised.
+int Engine::stage_energies()
+{
+  const size_t need = 16 * std::max<size_t>(L.sd.size(), 1);
+  if (need > energy_h_cap) {
+    if (energy_h) cudaFreeHost(energy_h);
+    energy_h = nullptr;
+    energy_h_cap = 0;
+    CK(cudaHostAlloc((void**)&energy_h, need, cudaHostAllocDefault));
+    energy_h_cap = need;
+  }
+  CK(cudaMemcpyAsync(energy_h, energy_d, 16 * L.sd.size(), cudaMemcpyDeviceToHost, stream));
   return HSMA_OK;
 }
 
@@ -875,6 +893,7 @@ int Engine::field()
   leave();
   launches += pot_launch_count();
   pot_ready = true;
+  ++pot_epoch;
   field_ready = true;
   if (!L.it4.empty()) pair_timed = true;
   return HSMA_OK;

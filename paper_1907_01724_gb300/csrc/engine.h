@@ -159,6 +159,12 @@ class Engine {
 
   // state
   bool sources_ready = false, pot_ready = false;
+  // energies of the last potential pass staged in pinned host memory by a host-output potential
+  // call (batch API), so that an energy call right after it needs no second GPU round trip
+  double* energy_h = nullptr;
+  size_t energy_h_cap = 0;
+  uint64_t pot_epoch = 0, energy_h_epoch = ~uint64_t(0);
+  int stage_energies();
   bool field_ready = false;       // E is current when pot_ready && field_ready
   cudaGraphExec_t g_build = nullptr, g_pot = nullptr, g_field = nullptr, g_fused = nullptr;
   // field pass buffers, outside the workspace (allocated on the first field request)
