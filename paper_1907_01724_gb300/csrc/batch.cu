@@ -262,22 +262,22 @@ static int batch_pot(hsma_batch_t* b, double* phi, int what, bool dev)
   int64_t tot = 0;
   for (auto v : b->n) tot += v;
   if (tot > 0 && !phi) return berr(b, HSMA_E_INVALID_ARG, "NULL phi");
+  if (!dev) {
+    const int rs = b->e->ensure_host_stage(tot);
+    if (rs) return bfrom(b, rs);
+  }
   int rc = b->e->potentials();
   if (rc) return bfrom(b, rc);
-  if (tot > 0) {
-    cudaError_t e = cudaMemcpyAsync(phi, src, 8 * tot, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                    b->e->stream);
-    if (e != cudaSuccess) return bfrom(b, b->e->cuda_fail(e, "copy phi"));
+  if (dev) {
+    if (tot > 0) {
+      cudaError_t e = cudaMemcpyAsync(phi, src, 8 * tot, cudaMemcpyDeviceToDevice, b->e->stream);
+      if (e != cudaSuccess) return bfrom(b, b->e->cuda_fail(e, "copy phi"));
+    }
+    return HSMA_OK;
   }
-  if (dev) return HSMA_OK;
-  // the energies ride along with the host copy (hsma_batch_energy then reads them without a
-  // second round trip)
-  rc = b->e->stage_energies();
-  if (rc) return bfrom(b, rc);
-  rc = b->e->check_status();
-  if (rc) return bfrom(b, rc);
-  b->e->energy_h_epoch = b->e->pot_epoch;
-  return HSMA_OK;
+  // through pinned staging, with the energies (hsma_batch_energy then reads them without a
+  // second round trip) and the status in the same round trip
+  return bfrom(b, b->e->copy_to_host(src, tot, phi));
 }
 
 static int batch_field(hsma_batch_t* b, double* E, int what, bool dev)

@@ -141,6 +141,7 @@ Engine::~Engine()
   drop_graphs();
   if (ws_owned && ws) cudaFree(ws);
   if (energy_h) cudaFreeHost(energy_h);
+  if (host_stage) cudaFreeHost(host_stage);
   if (fpart_d) cudaFree(fpart_d);
   if (E_d) cudaFree(E_d);
   if (ev_pair0) cudaEventDestroy(ev_pair0);
@@ -799,15 +800,31 @@ int Engine::potentials()
 // engine's stream); valid once the stream has been synchronised.
 int Engine::stage_energies()
 {
-  const size_t need = 16 * std::max<size_t>(L.sd.size(), 1);
-  if (need > energy_h_cap) {
+  if (16 * L.sd.size() > energy_h_cap) return fail(HSMA_E_STATE, "energy staging buffer not allocated");
+  CK(cudaMemcpyAsync(energy_h, energy_d, 16 * L.sd.size(), cudaMemcpyDeviceToHost, stream));
+  return HSMA_OK;
+}
+
+// The pinned staging buffers of copy_to_host and stage_energies; allocated before the call
+// enqueues any work (an allocation is no place between an enqueued copy and its wait).
+int Engine::ensure_host_stage(int64_t count)
+{
+  const size_t need_e = 16 * std::max<size_t>(L.sd.size(), 1);
+  if (need_e > energy_h_cap) {
     if (energy_h) cudaFreeHost(energy_h);
     energy_h = nullptr;
     energy_h_cap = 0;
-    CK(cudaHostAlloc((void**)&energy_h, need, cudaHostAllocDefault));
-    energy_h_cap = need;
+    CK(cudaHostAlloc((void**)&energy_h, need_e, cudaHostAllocDefault));
+    energy_h_cap = need_e;
   }
-  CK(cudaMemcpyAsync(energy_h, energy_d, 16 * L.sd.size(), cudaMemcpyDeviceToHost, stream));
+  const size_t need = 8 * (size_t)std::max<int64_t>(count, 0) + 256;
+  if (need > host_stage_cap) {
+    if (host_stage) cudaFreeHost(host_stage);
+    host_stage = nullptr;
+    host_stage_cap = 0;
+    CK(cudaHostAlloc((void**)&host_stage, need, cudaHostAllocDefault));
+    host_stage_cap = need;
+  }
   return HSMA_OK;
 }
 
@@ -904,6 +921,32 @@ int Engine::check_status()
   int st = 0;
   CK(cudaMemcpyAsync(&st, status_d, sizeof(int), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
+  return decode_status(st);
+}
+
+// Copy count doubles from the device to caller host memory through a pinned staging buffer,
+// with the energies (pinned mirror) and the status word in the same round trip, then decode the
+// status: one stream synchronisation instead of one per pageable copy.
+int Engine::copy_to_host(const double* src_d, int64_t count, double* dst_h)
+{
+  if (8 * (size_t)std::max<int64_t>(count, 0) + 256 > host_stage_cap)
+    return fail(HSMA_E_STATE, "host staging buffer not allocated");
+  int* st_h = reinterpret_cast<int*>(host_stage);
+  double* vals = reinterpret_cast<double*>(host_stage + 256);
+  if (count > 0) CK(cudaMemcpyAsync(vals, src_d, 8 * (size_t)count, cudaMemcpyDeviceToHost, stream));
+  int rc = stage_energies();
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(st_h, status_d, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  rc = decode_status(*st_h);
+  if (rc) return rc;
+  if (count > 0) std::memcpy(dst_h, vals, 8 * (size_t)count);
+  energy_h_epoch = pot_epoch;
+  return HSMA_OK;
+}
+
+int Engine::decode_status(int st)
+{
   if (st) {
     CK(cudaMemsetAsync(status_d, 0, sizeof(int), stream));
     pot_ready = false;

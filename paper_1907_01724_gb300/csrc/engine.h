@@ -165,6 +165,12 @@ class Engine {
   size_t energy_h_cap = 0;
   uint64_t pot_epoch = 0, energy_h_epoch = ~uint64_t(0);
   int stage_energies();
+  // pinned staging of a host-output potential copy and of the status word: one round trip
+  char* host_stage = nullptr;
+  size_t host_stage_cap = 0;
+  int ensure_host_stage(int64_t count);  // call before enqueueing the work whose results are copied
+  int copy_to_host(const double* src_d, int64_t count, double* dst_h);
+  int decode_status(int st);
   bool field_ready = false;       // E is current when pot_ready && field_ready
   cudaGraphExec_t g_build = nullptr, g_pot = nullptr, g_field = nullptr, g_fused = nullptr;
   // field pass buffers, outside the workspace (allocated on the first field request)
