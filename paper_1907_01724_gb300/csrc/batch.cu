@@ -326,11 +326,9 @@ int hsma_batch_energy(hsma_batch_t* b, double* e_total, double* e_reaction)
   std::vector<double> en(2 * ns);
   if (b->e->energy_h && b->e->energy_h_epoch == b->e->pot_epoch) {
     // staged by the host-output potential call of this very pass (its status already checked)
-    std::memcpy(en.data(), b->e->energy_h, 16 * ns);
+    b->e->energies_from(b->e->energy_h, b->e->energy_h_parts, en.data());
   } else {
-    cudaError_t e = cudaMemcpyAsync(en.data(), b->e->energy_d, 16 * ns, cudaMemcpyDeviceToHost, b->e->stream);
-    if (e != cudaSuccess) return bfrom(b, b->e->cuda_fail(e, "copy energy"));
-    rc = b->e->check_status();
+    rc = b->e->read_energies(en.data());
     if (rc) return bfrom(b, rc);
   }
   for (size_t s = 0; s < ns; ++s) {

@@ -633,7 +633,7 @@ void Engine::issue_pot()
     cudaEventRecordWithFlags(ev_pair1, stream, cudaEventRecordExternal);
   }
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
-                phic_d, phir_d, phit_d, epart_d, energy_d, ctr_red_d, status_d, stream);
+                phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, stream);
   if (!L.it4.empty()) cudaEventRecordWithFlags(ev_pot1, stream, cudaEventRecordExternal);
 }
 
@@ -703,8 +703,7 @@ void Engine::issue_fused()
   launch_pair_items(srf, rk, grid_s, stream);
   cudaStreamWaitEvent(stream, ev_join, 0);
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
-                phic_d, phir_d, phit_d, epart_d, energy_d, ctr_red_d, status_d, stream,
-                true);
+                phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, stream, true);
 }
 
 int Engine::fused_launch_count() const
@@ -792,6 +791,7 @@ int Engine::potentials()
   }
   pot_ready = true;
   ++pot_epoch;
+  energy_parts = true;  // the potential passes leave the energies as per-block terms (epart)
   field_ready = false;
   return HSMA_OK;
 }
@@ -800,8 +800,45 @@ int Engine::potentials()
 // engine's stream); valid once the stream has been synchronised.
 int Engine::stage_energies()
 {
-  if (16 * L.sd.size() > energy_h_cap) return fail(HSMA_E_STATE, "energy staging buffer not allocated");
-  CK(cudaMemcpyAsync(energy_h, energy_d, 16 * L.sd.size(), cudaMemcpyDeviceToHost, stream));
+  const size_t bytes = energy_parts ? 16 * L.it5.size() : 16 * L.sd.size();
+  if (bytes > energy_h_cap) return fail(HSMA_E_STATE, "energy staging buffer not allocated");
+  if (bytes)
+    CK(cudaMemcpyAsync(energy_h, energy_parts ? epart_d : energy_d, bytes, cudaMemcpyDeviceToHost, stream));
+  energy_h_parts = energy_parts;
+  return HSMA_OK;
+}
+
+// Every system's (E_total, E_rf) from the raw energies of a pass: the per-block terms of the
+// potential passes summed per system in block order, or the device-completed pairs.
+void Engine::energies_from(const double* raw, bool parts, double* out) const
+{
+  for (size_t s = 0; s < L.sd.size(); ++s) {
+    if (!parts) {
+      out[2 * s] = raw[2 * s];
+      out[2 * s + 1] = raw[2 * s + 1];
+      continue;
+    }
+    double a = 0.0, b = 0.0;
+    const int b0 = L.sd[s].k5_first, nb = L.sd[s].k5_count;
+    for (int k = 0; k < nb; ++k) {
+      a += raw[2 * (b0 + k)];
+      b += raw[2 * (b0 + k) + 1];
+    }
+    out[2 * s] = a;
+    out[2 * s + 1] = b;
+  }
+}
+
+// Energies of the current potentials into out (2 per system), with the status check.
+int Engine::read_energies(double* out)
+{
+  const bool parts = energy_parts;
+  const size_t n = parts ? 2 * L.it5.size() : 2 * L.sd.size();
+  std::vector<double> raw(std::max<size_t>(n, 1));
+  if (n) CK(cudaMemcpyAsync(raw.data(), parts ? epart_d : energy_d, 8 * n, cudaMemcpyDeviceToHost, stream));
+  const int rc = check_status();
+  if (rc) return rc;
+  energies_from(raw.data(), parts, out);
   return HSMA_OK;
 }
 
@@ -809,7 +846,7 @@ int Engine::stage_energies()
 // enqueues any work (an allocation is no place between an enqueued copy and its wait).
 int Engine::ensure_host_stage(int64_t count)
 {
-  const size_t need_e = 16 * std::max<size_t>(L.sd.size(), 1);
+  const size_t need_e = 16 * std::max<size_t>(std::max(L.sd.size(), L.it5.size()), 1);
   if (need_e > energy_h_cap) {
     if (energy_h) cudaFreeHost(energy_h);
     energy_h = nullptr;
@@ -911,6 +948,7 @@ int Engine::field()
   launches += pot_launch_count();
   pot_ready = true;
   ++pot_epoch;
+  energy_parts = false;  // the field pass completes the energies on the device
   field_ready = true;
   if (!L.it4.empty()) pair_timed = true;
   return HSMA_OK;
@@ -1257,9 +1295,7 @@ int hsma_energy(hsma_t* h, double* e_total, double* e_reaction)
   int rc = h->e->potentials();
   if (rc) return from_engine(h, rc);
   double en[2] = {0.0, 0.0};
-  cudaError_t e = cudaMemcpyAsync(en, h->e->energy_d, 16, cudaMemcpyDeviceToHost, h->e->stream);
-  if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy energy"));
-  rc = h->e->check_status();
+  rc = h->e->read_energies(en);
   if (rc) return from_engine(h, rc);
   if (e_total) *e_total = en[0];
   if (e_reaction) *e_reaction = en[1];

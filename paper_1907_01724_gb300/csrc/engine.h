@@ -165,6 +165,10 @@ class Engine {
   size_t energy_h_cap = 0;
   uint64_t pot_epoch = 0, energy_h_epoch = ~uint64_t(0);
   int stage_energies();
+  bool energy_parts = false;   // the current energies are per-block terms (epart), not energy_d
+  bool energy_h_parts = false; // what the pinned mirror holds
+  void energies_from(const double* raw, bool parts, double* out) const;
+  int read_energies(double* out);
   // pinned staging of a host-output potential copy and of the status word: one round trip
   char* host_stage = nullptr;
   size_t host_stage_cap = 0;

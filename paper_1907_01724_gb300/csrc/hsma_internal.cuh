@@ -239,6 +239,9 @@ void launch_pairs_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, con
 // system sel[r] are summed from the launch items sel_rng[r] = (first, count), ranges ascending
 // and contiguous; counter[r] (zero before the launch, zero after it) counts r's finished items.
 // pdl: launched as a programmatic dependent of the pair kernel that precedes it in the stream.
+// energy == nullptr: only the per-block energy terms (epart, two doubles per launch item) are
+// written; the reader sums them (Engine::read_energies), which spares every block the fence and
+// atomic of the last-block completion.
 void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
                    const float2* part, const double* part64, int prec, const double* q, const int* perm,
                    const double* r0, double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy,

@@ -410,10 +410,13 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     }
     epart[2 * blockIdx.x] = a;
     epart[2 * blockIdx.x + 1] = b;
-    __threadfence();
-    // whether this block is the last of its system's blocks to finish
-    const unsigned prev = atomicAdd(&counter[r_blk], 1u);
-    last = (prev == (unsigned)cnt_blk - 1u);
+    last = false;
+    if (energy) {
+      __threadfence();
+      // whether this block is the last of its system's blocks to finish
+      const unsigned prev = atomicAdd(&counter[r_blk], 1u);
+      last = (prev == (unsigned)cnt_blk - 1u);
+    }
   }
   __syncthreads();
   if (!last) return;
