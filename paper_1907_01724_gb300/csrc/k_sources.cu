@@ -302,7 +302,7 @@ __device__ __forceinline__ void split2(double x, float& hi, float& lo)
 }
 
 
-constexpr int kMomThreads = 320;  // a moment block holds at most kMomTile <= kMomThreads charges
+constexpr int kMomThreads = 352;  // a moment block holds at most kMomTile <= kMomThreads charges
 constexpr int kMomWarps = kMomThreads / 32;
 // Slots of the recurrence tables (a_nm, b_nm over the triangle n <= pmax, and the sectoral
 // factors) that k_moments keeps in shared memory when they take at most kMomTableSlots slots.
