@@ -443,10 +443,10 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
 // Charge moments of the correction coefficients.  Thread t of a block prepares charge c0 + t:
 // the centre constant of a charge at the centre, and its moment inputs u, v, w = x/a, rho^2, q
 // and q c in the moment arithmetic R (shared memory), so the moment phase runs on R alone: per
-// group of G charges, the weights q (M_n - gamma) - q c of every (charge, n), thread t computes
-// the column pair j = t mod (p/2 + 1) of charge t / (p/2 + 1) (solid_pair), then thread t
-// accumulates coefficients t + j kMomThreads over the group.  Rows are stored as R values in
-// 8-byte slots; slot P holds the block's centre constant.
+// group of G <= 32 charges, the weights q (M_n - gamma) - q c of every (charge, n), warp w
+// computes the column pairs j = w, w + kMomWarps, ... of every charge (lane = charge;
+// solid_pair), then thread t accumulates coefficients t + j kMomThreads over the group.  Rows
+// are stored as R values in 8-byte slots; slot P holds the block's centre constant.
 template <int MAXJ, class R>
 __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restrict__ sys, const int2* __restrict__ items,
                                                          const double* __restrict__ xyz, const double* __restrict__ q,
@@ -568,17 +568,19 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
     while ((nn + 1) * (nn + 1) <= idx) ++nn;
     nidx[j] = nn;
   }
+  // warp w computes the column pairs j = w, w + kMomWarps, ... and lane l charge l of the group
+  // (G <= 32): the lanes of a warp run the same chains, without divergence
   const int npair = p / 2 + 1;
-  const int tg = tid / npair, tj = tid - tg * npair;
   for (int g0 = 0; g0 < cnt; g0 += G) {
     const int gcount = min(G, cnt - g0);
     for (int k = tid; k < gcount * (p + 1); k += kMomThreads) {
       const int g = k / (p + 1), nn = k - g * (p + 1);
       wq[g * np1 + nn] = Num<R>::mul_sub(cq[g0 + g], mg[nn], Num<R>::one(), cqc[g0 + g]);
     }
-    if (tg < gcount) {
-      const int c = g0 + tg;
-      solid_pair<R>(tj, p, cu[c], cv[c], cw[c], cr2[c], ra, rb, sp, T + (size_t)tg * P);
+    if (lane < gcount) {
+      const int c = g0 + lane;
+      for (int j = warp; j < npair; j += kMomWarps)
+        solid_pair<R>(j, p, cu[c], cv[c], cw[c], cr2[c], ra, rb, sp, T + (size_t)lane * P);
     }
     __syncthreads();
 #pragma unroll
@@ -602,8 +604,8 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
   }
 }
 
-// Charges per moment group: at most one solid-harmonic column pair per thread
-// (G (p/2 + 1) <= 256) and the group's G P values within the shared-memory budget.
+// Charges per moment group: at most 32 (a warp's lanes) and the group's G (P + pmax + 1) values
+// within the shared-memory budget.
 static size_t moment_table_slots(int pmax)
 {
   const size_t s = 2 * (size_t)(pmax + 1) * (pmax + 2) / 2 + (size_t)(pmax + 1);
@@ -618,7 +620,7 @@ int moment_smem_group(int maxP, int blocks_per_sm)
   if (pmax < 0) pmax = 0;
   const size_t fixed = (6 * (size_t)kMomThreads + kMomWarps + (pmax + 1) + moment_table_slots(pmax)) * sizeof(double);
   const size_t budget = blocks_per_sm >= 2 ? 112 * 1024 : 192 * 1024;
-  int G = kMomThreads / (pmax / 2 + 1);
+  int G = 32;  // one warp lane per charge of the group
   const size_t per = ((size_t)maxP + pmax + 1) * sizeof(double);
   const int Gs = budget > fixed ? (int)((budget - fixed) / per) : 0;
   if (G > Gs) G = Gs;
