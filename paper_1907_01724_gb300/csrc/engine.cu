@@ -164,7 +164,8 @@ void Engine::drop_graphs()
   if (g_pot) cudaGraphExecDestroy(g_pot);
   if (g_field) cudaGraphExecDestroy(g_field);
   if (g_fused) cudaGraphExecDestroy(g_fused);
-  g_build = g_pot = g_field = g_fused = nullptr;
+  if (g_field_fused) cudaGraphExecDestroy(g_field_fused);
+  g_build = g_pot = g_field = g_fused = g_field_fused = nullptr;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -877,7 +878,8 @@ int Engine::ensure_field_buffers()
   }
   CK(cudaStreamSynchronize(stream));
   if (g_field) cudaGraphExecDestroy(g_field);
-  g_field = nullptr;
+  if (g_field_fused) cudaGraphExecDestroy(g_field_fused);
+  g_field = g_field_fused = nullptr;
   if (need_p > fpart_cap) {
     if (fpart_d) cudaFree(fpart_d);
     fpart_d = nullptr;
@@ -908,28 +910,76 @@ int Engine::ensure_field_buffers()
   return HSMA_OK;
 }
 
+int Engine::field_slots() const
+{
+  return num_sms * std::max(prec == HSMA_FP64 ? occ_field64 : occ_field[L.cfg], 1);
+}
+
+void Engine::launch_field_items(PairWork w1, PairWork w2, int grid, cudaStream_t st)
+{
+  if (w1.nitems <= 0 && w2.nitems <= 0) return;
+  if (prec == HSMA_FP64)
+    launch_field_f64(grid, sys_d, w1, w2, src64_d, surf64a_d, surf64b_d, (dbl4*)fpart_d, st);
+  else
+    launch_field_f32(L.cfg, grid, sys_d, w1, w2, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, (float4*)fpart_d, st);
+}
+
+void Engine::launch_field_reduce(cudaStream_t st)
+{
+  launch_reduce_field(sys_d, sel_d, selrng_d, (int)L.sd.size(), it5_d, (int)L.it5.size(), (const float4*)fpart_d,
+                      (const dbl4*)fpart_d, prec, q_d, perm_d, r0_d, phic_d, phir_d, phit_d, Ec_d, Er_d, Et_d,
+                      epart_d, energy_d, ctr_red_d, status_d, st);
+}
+
 void Engine::issue_field()
 {
-  const int nsys = (int)L.sd.size();
   cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), stream);
   if (!L.it4.empty()) {
     cudaEventRecordWithFlags(ev_pair0, stream, cudaEventRecordExternal);
-    if (prec == HSMA_FP64) {
-      const int grid =
-          (int)std::max<size_t>(1, std::min<size_t>(L.it4.size(), (size_t)num_sms * std::max(occ_field64, 1)));
-      launch_field_f64(grid, sys_d, it4_d, (int)L.it4.size(), ctr_pairs_d, src64_d, surf64a_d, surf64b_d,
-                       (dbl4*)fpart_d, stream);
-    } else {
-      const int grid =
-          (int)std::max<size_t>(1, std::min<size_t>(L.it4.size(), (size_t)num_sms * std::max(occ_field[L.cfg], 1)));
-      launch_field_f32(L.cfg, grid, sys_d, it4_d, (int)L.it4.size(), ctr_pairs_d, srchi_d, srclo_d, surfa_d, surfb_d,
-                       boxes_d, (float4*)fpart_d, stream);
-    }
+    const int nit = (int)L.it4.size();
+    const int grid = std::max(1, std::min(nit, field_slots()));
+    const PairWork all{it4_d, nit, ctr_pairs_d, std::min(grid, nit)}, none{nullptr, 0, nullptr, 0};
+    launch_field_items(all, none, grid, stream);
     cudaEventRecordWithFlags(ev_pair1, stream, cudaEventRecordExternal);
   }
-  launch_reduce_field(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), (const float4*)fpart_d,
-                      (const dbl4*)fpart_d, prec, q_d, perm_d, r0_d, phic_d, phir_d, phit_d, Ec_d, Er_d, Et_d,
-                      epart_d, energy_d, ctr_red_d, status_d, stream);
+  launch_field_reduce(stream);
+}
+
+// Build and field pass in one graph, as issue_fused does for the potentials: the field items of
+// the real/Kelvin records on the second stream right after the records (grid capped at
+// kOverlapShare of the slots), the surface items and the rest after the moment chain.
+void Engine::issue_field_fused()
+{
+  const int nsys = (int)L.sd.size();
+  const int nS = (int)L.it4x.size() - L.nRK;
+  const int slots = field_slots();
+  const int grid_rk = std::max(1, std::min(L.nRK, (int)(kOverlapShare * slots)));
+  const int grid_s = std::max(1, std::min(nS + L.nRK, slots));
+  cudaEventRecord(ev_fork, stream);
+  cudaStreamWaitEvent(side, ev_fork, 0);
+  const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d, std::min(grid_rk, L.nRK)};
+  const PairWork srf{it4x_d + L.nRK, nS, ctr_pairs_d, std::min(grid_s, nS)}, none{nullptr, 0, nullptr, 0};
+  {
+    PriorityScope ps(prio_hi);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
+                 xs_d, status_d, ctr_pairs_d, 2, side);
+    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
+                  prec, status_d, side);
+  }
+  cudaEventRecord(ev_img, side);
+  launch_field_items(rk, none, grid_rk, side);
+  cudaEventRecord(ev_join, side);
+  PriorityScope ps(prio_mid);
+  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
+                 L.mom_stride, stream);
+  launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
+                     stream);
+  launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
+                 surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
+  cudaStreamWaitEvent(stream, ev_img, 0);
+  launch_field_items(srf, rk, grid_s, stream);
+  cudaStreamWaitEvent(stream, ev_join, 0);
+  launch_field_reduce(stream);
 }
 
 int Engine::field()
@@ -937,20 +987,29 @@ int Engine::field()
   if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
   if (pot_ready && field_ready) return HSMA_OK;
   CK(cudaSetDevice(device));
-  int rc = ensure_built();
+  int rc = ensure_field_buffers();
   if (rc) return rc;
-  rc = ensure_field_buffers();
-  if (rc) return rc;
-  enter();
-  rc = run_graph(&g_field, &Engine::issue_field);
-  if (rc) return rc;
-  leave();
-  launches += pot_launch_count();
+  if (build_pending && overlap && !L.itord.empty()) {
+    enter();
+    rc = run_graph(&g_field_fused, &Engine::issue_field_fused);
+    if (rc) return rc;
+    leave();
+    launches += build_launch_count() + (L.nRK > 0 ? 1 : 0) + (L.it4x.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1);
+    build_pending = false;
+  } else {
+    rc = ensure_built();
+    if (rc) return rc;
+    enter();
+    rc = run_graph(&g_field, &Engine::issue_field);
+    if (rc) return rc;
+    leave();
+    launches += pot_launch_count();
+    if (!L.it4.empty()) pair_timed = true;
+  }
   pot_ready = true;
   ++pot_epoch;
   energy_parts = false;  // the field pass completes the energies on the device
   field_ready = true;
-  if (!L.it4.empty()) pair_timed = true;
   return HSMA_OK;
 }
 

@@ -176,7 +176,7 @@ class Engine {
   int copy_to_host(const double* src_d, int64_t count, double* dst_h);
   int decode_status(int st);
   bool field_ready = false;       // E is current when pot_ready && field_ready
-  cudaGraphExec_t g_build = nullptr, g_pot = nullptr, g_field = nullptr, g_fused = nullptr;
+  cudaGraphExec_t g_build = nullptr, g_pot = nullptr, g_field = nullptr, g_fused = nullptr, g_field_fused = nullptr;
   // field pass buffers, outside the workspace (allocated on the first field request)
   void* fpart_d = nullptr;        // 32 bytes per (chunk, target) slot
   size_t fpart_cap = 0;
@@ -196,6 +196,10 @@ class Engine {
   void issue_field();
   void issue_fused();
   void launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t st);
+  int field_slots() const;
+  void launch_field_items(PairWork w1, PairWork w2, int grid, cudaStream_t st);
+  void launch_field_reduce(cudaStream_t st);
+  void issue_field_fused();
   int fused_launch_count() const;
   int build_launch_count() const;
   int pot_launch_count() const;

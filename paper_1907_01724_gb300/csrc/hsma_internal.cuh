@@ -229,6 +229,35 @@ struct PairWork {
   unsigned int* counter;
   int first;
 };
+// An item from the counter of w, or -1 when none is left (a plain read first: a list that is
+// already exhausted costs no atomic, so CTAs that find no work do not queue on the counter).
+__device__ __forceinline__ int pull_pair_item(const PairWork& w)
+{
+  if (!w.counter || w.first >= w.nitems) return -1;
+  if (w.first + (int)__ldcg(w.counter) >= w.nitems) return -1;
+  const int v = w.first + (int)atomicAdd(w.counter, 1u);
+  return v < w.nitems ? v : -1;
+}
+
+// Next work item of a persistent CTA (thread 0): items of w1 first (the CTA's own item of the
+// static round on its first fetch, then the counter), then, when w1 is exhausted, items of w2
+// (if any).  list = 0 or 1 names the list of the item, 2 means no work left.
+__device__ __forceinline__ void next_pair_item(const PairWork& w1, const PairWork& w2, int list,
+                                               bool first_fetch, int& s_item, int& s_list)
+{
+  int v = 0;
+  if (list == 0) {
+    v = first_fetch && (int)blockIdx.x < w1.first ? (int)blockIdx.x : pull_pair_item(w1);
+    if (v < 0) list = 1;
+  }
+  if (list == 1) {
+    v = pull_pair_item(w2);
+    if (v < 0) list = 2;
+  }
+  s_item = v;
+  s_list = list;
+}
+
 // Persistent pair-sum launches: each CTA takes items of w1 until it is exhausted, then of w2.
 void launch_pairs_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
                       const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
@@ -251,13 +280,13 @@ void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int n
 // ---- fields (k_field.cu): potential and E = -grad phi in one pass over the pair items ----
 int field_f32_occupancy(int cfg);
 int field_f64_occupancy();
-// FP32: two float4 per (chunk, target) slot, (hi, lo) of (phi, Ex, Ey, Ez); FP64: one dbl4
-void launch_field_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
-                      const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
-                      const float4* boxes, float4* fpart, cudaStream_t st);
-void launch_field_f64(int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
-                      const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, dbl4* fpart64,
-                      cudaStream_t st);
+// FP32: two float4 per (chunk, target) slot, (hi, lo) of (phi, Ex, Ey, Ez); FP64: one dbl4.
+// Work lists as for the pair kernels (w1, then w2).
+void launch_field_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
+                      const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
+                      float4* fpart, cudaStream_t st);
+void launch_field_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, const dbl4* src64,
+                      const dbl4* surf64_a, const double* surf64_b, dbl4* fpart64, cudaStream_t st);
 // as launch_reduce, plus the Coulomb, reaction and total fields (3 doubles per charge, input order)
 void launch_reduce_field(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items,
                          int nitems, const float4* fpart, const dbl4* fpart64, int prec, const double* q,

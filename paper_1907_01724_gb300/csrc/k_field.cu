@@ -79,8 +79,7 @@ __device__ __forceinline__ void fold(float& H, float& L, float b)
 }
 
 template <int NT, int K>
-__global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys, const int4* __restrict__ items,
-                                                  int nitems, unsigned int* __restrict__ counter,
+__global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys, PairWork w1, PairWork w2,
                                                   const float4* __restrict__ src_hi,
                                                   const float4* __restrict__ src_lo,
                                                   const float4* __restrict__ surf_a,
@@ -90,16 +89,20 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
   static_assert(NT % kBox == 0, "a staged tile holds whole source boxes");
   __shared__ __align__(16) float4 shA[2][NT];
   __shared__ __align__(16) float4 shB[2][NT];
-  __shared__ int s_item;
+  __shared__ int s_item, s_list;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int list = 0;
+  bool first_fetch = true;
 
   for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
+    if (tid == 0) next_pair_item(w1, w2, list, first_fetch, s_item, s_list);
+    first_fetch = false;
     __syncthreads();
     const int item = s_item;
+    list = s_list;
     __syncthreads();
-    if (item >= nitems) break;
-    const int4 it = items[item];
+    if (list > 1) break;
+    const int4 it = (list == 0 ? w1.items : w2.items)[item];
     const SysDev& S = sys[it.x];
     const int n = S.n;
     const int t0 = it.y * (NT * K);
@@ -286,15 +289,15 @@ int field_f32_occupancy(int cfg)
 
 int field_f64_occupancy();
 
-void launch_field_f32(int cfg, int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
-                      const float4* src_hi, const float4* src_lo, const float4* surf_a, const float4* surf_b,
-                      const float4* boxes, float4* fpart, cudaStream_t st)
+void launch_field_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
+                      const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
+                      float4* fpart, cudaStream_t st)
 {
   switch (pair_kernel_of(cfg)) {
 #define HSMA_FCFG_LAUNCH(i, nt, k)                                                                        \
   case i:                                                                                                 \
-    k_field_f32<nt, k><<<grid, nt, 0, st>>>(sys, items, nitems, counter, src_hi, src_lo, surf_a, surf_b, boxes, \
-                                            fpart);                                                       \
+    launch_k(k_field_f32<nt, k>, grid, nt, 0, st, false, sys, w1, w2, src_hi, src_lo, surf_a, surf_b, boxes, \
+             fpart);                                                                                     \
     break;
     HSMA_FIELD_CONFIGS(HSMA_FCFG_LAUNCH)
 #undef HSMA_FCFG_LAUNCH
@@ -306,25 +309,27 @@ void launch_field_f32(int cfg, int grid, const SysDev* sys, const int4* items, i
 // FP64 comparator: one target per thread, plain staged loads.
 constexpr int kF64FThreads = kF64TargetsPerBlock;
 
-__global__ __launch_bounds__(kF64FThreads) void k_field_f64(const SysDev* __restrict__ sys,
-                                                            const int4* __restrict__ items, int nitems,
-                                                            unsigned int* __restrict__ counter,
-                                                            const dbl4* __restrict__ src64,
+__global__ __launch_bounds__(kF64FThreads) void k_field_f64(const SysDev* __restrict__ sys, PairWork w1,
+                                                            PairWork w2, const dbl4* __restrict__ src64,
                                                             const dbl4* __restrict__ surf64_a,
                                                             const double* __restrict__ surf64_b,
                                                             dbl4* __restrict__ fpart64)
 {
   __shared__ dbl4 shA[kF64FThreads];
   __shared__ double shB[kF64FThreads];
-  __shared__ int s_item;
+  __shared__ int s_item, s_list;
   const int tid = threadIdx.x;
+  int list = 0;
+  bool first_fetch = true;
   for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
+    if (tid == 0) next_pair_item(w1, w2, list, first_fetch, s_item, s_list);
+    first_fetch = false;
     __syncthreads();
     const int item = s_item;
+    list = s_list;
     __syncthreads();
-    if (item >= nitems) break;
-    const int4 it = items[item];
+    if (list > 1) break;
+    const int4 it = (list == 0 ? w1.items : w2.items)[item];
     const SysDev& S = sys[it.x];
     const int n = S.n;
     const int i = it.y * kF64FThreads + tid;
@@ -398,11 +403,10 @@ int field_f64_occupancy()
   return b;
 }
 
-void launch_field_f64(int grid, const SysDev* sys, const int4* items, int nitems, unsigned int* counter,
-                      const dbl4* src64, const dbl4* surf64_a, const double* surf64_b, dbl4* fpart64,
-                      cudaStream_t st)
+void launch_field_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, const dbl4* src64,
+                      const dbl4* surf64_a, const double* surf64_b, dbl4* fpart64, cudaStream_t st)
 {
-  k_field_f64<<<grid, kF64FThreads, 0, st>>>(sys, items, nitems, counter, src64, surf64_a, surf64_b, fpart64);
+  launch_k(k_field_f64, grid, kF64FThreads, 0, st, false, sys, w1, w2, src64, surf64_a, surf64_b, fpart64);
 }
 
 // ---------------------------------------------------------------------------------------
