@@ -461,7 +461,7 @@ def run_ours(args):
     peak = sms * SM_MUFU_PER_CLK * sm_max * 1e6
     achieved = ev_per_launch / t_pair
     csrc = os.path.join(ROOT, "paper_1907_01724_gb300", "csrc")
-    traffic = profiled_traffic([os.path.join(csrc, "k_pairs.cu"), os.path.join(csrc, "k_pairs_f32.cuh")],
+    traffic = profiled_traffic([os.path.join(csrc, f) for f in ("k_pairs.cu", "k_pairs_f32.cuh", "pair_work.cuh")],
                                os.path.join(ROOT, "profiles", "k_pairs_f32_N2000x2.md"))
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-eval/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
