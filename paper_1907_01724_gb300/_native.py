@@ -29,6 +29,16 @@ _lock = threading.Lock()
 _lib = None
 
 
+
+def host_ptr(a) -> ctypes.c_void_p:
+    """Address of a host array's data as a ctypes argument.  A writable buffer's address comes
+    from a ctypes view of it (a fraction of the cost of ndarray.ctypes, which matters on the
+    per-call path); read-only and empty arrays take ndarray.ctypes."""
+    try:
+        return ctypes.c_void_p(ctypes.addressof(ctypes.c_char.from_buffer(a)))
+    except (TypeError, ValueError, BufferError):
+        return ctypes.c_void_p(a.ctypes.data)
+
 def _nvcc() -> str:
     for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
         if c and os.path.exists(c):

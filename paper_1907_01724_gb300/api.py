@@ -60,8 +60,7 @@ def _host_f64(x, shape=None):
     return a
 
 
-def _dptr(a: np.ndarray):
-    return ctypes.c_void_p(a.ctypes.data)
+_dptr = _native.host_ptr
 
 
 def _is_torch_cuda(x) -> bool:

@@ -19,8 +19,7 @@ def _arr(x, dtype):
     return np.ascontiguousarray(np.asarray(x, dtype=dtype))
 
 
-def _p(a: np.ndarray):
-    return ctypes.c_void_p(a.ctypes.data)
+_p = _native.host_ptr
 
 
 def _is_torch_cuda(x) -> bool:
@@ -81,7 +80,7 @@ class Batch:
     def _ensure_workspace(self, n):
         if not self.use_torch_workspace:
             return
-        key = tuple(int(v) for v in n)
+        key = tuple(n.tolist())
         if getattr(self, "_ws_key", None) == key:
             return
         need = self.hsma_batch_workspace_size(n)

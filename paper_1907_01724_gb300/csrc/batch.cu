@@ -262,22 +262,26 @@ static int batch_pot(hsma_batch_t* b, double* phi, int what, bool dev)
   int64_t tot = 0;
   for (auto v : b->n) tot += v;
   if (tot > 0 && !phi) return berr(b, HSMA_E_INVALID_ARG, "NULL phi");
+  // a pass run by this call writes the result straight to the caller's device array, or (host
+  // output) to pinned staging together with the energy terms (hsma_batch_energy then reads them
+  // without a second round trip); a pass already run: copies
+  hsma::OutDesc od{dev && tot > 0 ? phi : nullptr, nullptr, Engine::out_lane(what), 0};
   if (!dev) {
     const int rs = b->e->ensure_host_stage(tot);
     if (rs) return bfrom(b, rs);
+    od = b->e->host_outputs(tot, what);
   }
-  int rc = b->e->potentials();
+  bool wrote = false;
+  int rc = b->e->potentials(od, &wrote);
   if (rc) return bfrom(b, rc);
   if (dev) {
-    if (tot > 0) {
+    if (tot > 0 && !wrote) {
       cudaError_t e = cudaMemcpyAsync(phi, src, 8 * tot, cudaMemcpyDeviceToDevice, b->e->stream);
       if (e != cudaSuccess) return bfrom(b, b->e->cuda_fail(e, "copy phi"));
     }
     return HSMA_OK;
   }
-  // through pinned staging, with the energies (hsma_batch_energy then reads them without a
-  // second round trip) and the status in the same round trip
-  return bfrom(b, b->e->copy_to_host(src, tot, phi));
+  return bfrom(b, b->e->copy_to_host(src, tot, phi, wrote));
 }
 
 static int batch_field(hsma_batch_t* b, double* E, int what, bool dev)
@@ -324,13 +328,9 @@ int hsma_batch_energy(hsma_batch_t* b, double* e_total, double* e_reaction)
   if (rc) return bfrom(b, rc);
   const size_t ns = b->e->spec.size();
   std::vector<double> en(2 * ns);
-  if (b->e->energy_h && b->e->energy_h_epoch == b->e->pot_epoch) {
-    // staged by the host-output potential call of this very pass (its status already checked)
-    b->e->energies_from(b->e->energy_h, b->e->energy_h_parts, en.data());
-  } else {
-    rc = b->e->read_energies(en.data());
-    if (rc) return bfrom(b, rc);
-  }
+  // from the pinned mirror when a host-output call of this pass staged it (status checked)
+  rc = b->e->read_energies(en.data());
+  if (rc) return bfrom(b, rc);
   for (size_t s = 0; s < ns; ++s) {
     if (e_total) e_total[s] = en[2 * s];
     if (e_reaction) e_reaction[s] = en[2 * s + 1];

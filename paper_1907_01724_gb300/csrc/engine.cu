@@ -392,6 +392,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_epart = take(16 * L.it5.size());
   L.o_energy = take(16 * (size_t)nsys);
   L.o_ctr = take(16);
+  L.o_outdesc = take(sizeof(OutDesc));
   L.o_redctr = take(4 * (size_t)nsys);
   L.o_it12 = take(sizeof(int2) * L.it12.size());
   L.o_it2r = take(sizeof(int2) * L.it2r.size());
@@ -475,6 +476,7 @@ void Engine::carve()
   ctr_pairs_d = ctr;
   ctr_red_d = (unsigned int*)(b + L.o_redctr);
   status_d = (int*)(ctr + 2);
+  outdesc_d = (OutDesc*)(b + L.o_outdesc);
   ctr_delta_d = ctr + 3;
   it12_d = (int2*)(b + L.o_it12);
   it2r_d = (int2*)(b + L.o_it2r);
@@ -552,6 +554,8 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
   CK(cudaMemsetAsync(ctr_red_d, 0, 4 * L.sd.size(), stream));
   CK(cudaMemsetAsync(energy_d, 0, 16 * L.sd.size(), stream));
   CK(cudaMemsetAsync(hist_d, 0, 4 * L.sd.size() * kOrderCells, stream));
+  CK(cudaMemsetAsync(outdesc_d, 0, sizeof(OutDesc), stream));
+  out_cur = OutDesc{nullptr, nullptr, 0, 0};
   // parameter-only quantities (scalars, M_n, tables, quadrature grid, surface basis), once per layout
   launch_setup(sys_d, (int)L.sd.size(), Mn_d, rec_a_d, rec_b_d, sect_d, inv_np1_d, rec_a2_d, rec_b2_d, sect2_d,
                L.pmax, surfx_d, stream);
@@ -634,7 +638,7 @@ void Engine::issue_pot()
     cudaEventRecordWithFlags(ev_pair1, stream, cudaEventRecordExternal);
   }
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
-                phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, stream);
+                phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, outdesc_d, stream);
   if (!L.it4.empty()) cudaEventRecordWithFlags(ev_pot1, stream, cudaEventRecordExternal);
 }
 
@@ -704,7 +708,7 @@ void Engine::issue_fused()
   launch_pair_items(srf, rk, grid_s, stream);
   cudaStreamWaitEvent(stream, ev_join, 0);
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
-                phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, stream, true);
+                phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, outdesc_d, stream, true);
 }
 
 int Engine::fused_launch_count() const
@@ -768,11 +772,26 @@ int Engine::ensure_built()
   return HSMA_OK;
 }
 
-int Engine::potentials()
+// Destinations of the next potential pass (OutDesc): rewritten on the device only when they
+// change (a pageable source: the copy has taken it when the call returns).
+int Engine::set_outputs(const OutDesc& od)
 {
+  if (od.phi == out_cur.phi && od.epart == out_cur.epart && od.what == out_cur.what) return HSMA_OK;
+  out_cur = od;
+  CK(cudaMemcpyAsync(outdesc_d, &out_cur, sizeof(OutDesc), cudaMemcpyHostToDevice, stream));
+  return HSMA_OK;
+}
+
+int Engine::potentials(const OutDesc& od, bool* wrote)
+{
+  if (wrote) *wrote = false;
   if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
   if (pot_ready) return HSMA_OK;
   CK(cudaSetDevice(device));
+  {
+    const int rs = set_outputs(od);
+    if (rs) return rs;
+  }
   if (build_pending && overlap) {
     enter();
     int rc = run_graph(&g_fused, &Engine::issue_fused);
@@ -794,6 +813,7 @@ int Engine::potentials()
   ++pot_epoch;
   energy_parts = true;  // the potential passes leave the energies as per-block terms (epart)
   field_ready = false;
+  if (wrote) *wrote = true;
   return HSMA_OK;
 }
 
@@ -831,15 +851,20 @@ void Engine::energies_from(const double* raw, bool parts, double* out) const
 }
 
 // Energies of the current potentials into out (2 per system), with the status check.
+// Energies of the current pass through the pinned mirror (one round trip with the status);
+// later reads of the same pass take the mirror without a copy.
 int Engine::read_energies(double* out)
 {
-  const bool parts = energy_parts;
-  const size_t n = parts ? 2 * L.it5.size() : 2 * L.sd.size();
-  std::vector<double> raw(std::max<size_t>(n, 1));
-  if (n) CK(cudaMemcpyAsync(raw.data(), parts ? epart_d : energy_d, 8 * n, cudaMemcpyDeviceToHost, stream));
-  const int rc = check_status();
-  if (rc) return rc;
-  energies_from(raw.data(), parts, out);
+  if (!(energy_h && energy_h_epoch == pot_epoch)) {
+    int rc = ensure_host_stage(0);
+    if (rc) return rc;
+    rc = stage_energies();
+    if (rc) return rc;
+    rc = check_status();
+    if (rc) return rc;
+    energy_h_epoch = pot_epoch;
+  }
+  energies_from(energy_h, energy_h_parts, out);
   return HSMA_OK;
 }
 
@@ -852,16 +877,18 @@ int Engine::ensure_host_stage(int64_t count)
     if (energy_h) cudaFreeHost(energy_h);
     energy_h = nullptr;
     energy_h_cap = 0;
-    CK(cudaHostAlloc((void**)&energy_h, need_e, cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&energy_h, need_e, cudaHostAllocMapped));
     energy_h_cap = need_e;
+    CK(cudaHostGetDevicePointer((void**)&energy_h_dev, energy_h, 0));
   }
   const size_t need = 8 * (size_t)std::max<int64_t>(count, 0) + 256;
   if (need > host_stage_cap) {
     if (host_stage) cudaFreeHost(host_stage);
     host_stage = nullptr;
     host_stage_cap = 0;
-    CK(cudaHostAlloc((void**)&host_stage, need, cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&host_stage, need, cudaHostAllocMapped));
     host_stage_cap = need;
+    CK(cudaHostGetDevicePointer((void**)&host_stage_dev, host_stage, 0));
   }
   return HSMA_OK;
 }
@@ -1015,24 +1042,39 @@ int Engine::field()
 
 int Engine::check_status()
 {
-  int st = 0;
-  CK(cudaMemcpyAsync(&st, status_d, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  // the status word through pinned memory (a pageable copy costs a driver-staged round trip)
+  int rc = ensure_host_stage(0);
+  if (rc) return rc;
+  int* st_h = reinterpret_cast<int*>(host_stage);
+  CK(cudaMemcpyAsync(st_h, status_d, sizeof(int), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
-  return decode_status(st);
+  return decode_status(*st_h);
 }
 
 // Copy count doubles from the device to caller host memory through a pinned staging buffer,
 // with the energies (pinned mirror) and the status word in the same round trip, then decode the
 // status: one stream synchronisation instead of one per pageable copy.
-int Engine::copy_to_host(const double* src_d, int64_t count, double* dst_h)
+int Engine::out_lane(int what) { return what == HSMA_COULOMB ? 0 : (what == HSMA_REACTION ? 1 : 2); }
+
+OutDesc Engine::host_outputs(int64_t count, int what) const
+{
+  return OutDesc{count > 0 ? host_stage_dev + 32 : nullptr, energy_h_dev, out_lane(what), 0};
+}
+
+int Engine::copy_to_host(const double* src_d, int64_t count, double* dst_h, bool written)
 {
   if (8 * (size_t)std::max<int64_t>(count, 0) + 256 > host_stage_cap)
     return fail(HSMA_E_STATE, "host staging buffer not allocated");
   int* st_h = reinterpret_cast<int*>(host_stage);
   double* vals = reinterpret_cast<double*>(host_stage + 256);
-  if (count > 0) CK(cudaMemcpyAsync(vals, src_d, 8 * (size_t)count, cudaMemcpyDeviceToHost, stream));
-  int rc = stage_energies();
-  if (rc) return rc;
+  if (written) {
+    energy_h_parts = true;  // the potential pass wrote its per-block energy terms
+  } else {
+    if (count > 0) CK(cudaMemcpyAsync(vals, src_d, 8 * (size_t)count, cudaMemcpyDeviceToHost, stream));
+    const int rs = stage_energies();
+    if (rs) return rs;
+  }
+  int rc = 0;
   CK(cudaMemcpyAsync(st_h, status_d, sizeof(int), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
   rc = decode_status(*st_h);
@@ -1293,13 +1335,12 @@ int hsma_potential(hsma_t* h, double* phi, int what)
   if (h->n > 0 && !phi) return set_err(h, HSMA_E_INVALID_ARG, "NULL phi");
   const double* src = pick_phi(h->e, what);
   if (!src) return set_err(h, HSMA_E_INVALID_ARG, "bad 'what'");
-  int rc = h->e->potentials();
+  int rc = h->e->ensure_host_stage(h->n);
   if (rc) return from_engine(h, rc);
-  if (h->n > 0) {
-    cudaError_t e = cudaMemcpyAsync(phi, src, 8 * h->n, cudaMemcpyDeviceToHost, h->e->stream);
-    if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy phi"));
-  }
-  return from_engine(h, h->e->check_status());
+  bool wrote = false;
+  rc = h->e->potentials(h->e->host_outputs(h->n, what), &wrote);
+  if (rc) return from_engine(h, rc);
+  return from_engine(h, h->e->copy_to_host(src, h->n, phi, wrote));
 }
 
 int hsma_potential_device(hsma_t* h, double* phi_dev, int what)
@@ -1309,9 +1350,11 @@ int hsma_potential_device(hsma_t* h, double* phi_dev, int what)
   if (h->n > 0 && !phi_dev) return set_err(h, HSMA_E_INVALID_ARG, "NULL phi");
   const double* src = pick_phi(h->e, what);
   if (!src) return set_err(h, HSMA_E_INVALID_ARG, "bad 'what'");
-  int rc = h->e->potentials();
+  bool wrote = false;
+  const hsma::OutDesc od{h->n > 0 ? phi_dev : nullptr, nullptr, Engine::out_lane(what), 0};
+  int rc = h->e->potentials(od, &wrote);
   if (rc) return from_engine(h, rc);
-  if (h->n > 0) {
+  if (h->n > 0 && !wrote) {
     cudaError_t e = cudaMemcpyAsync(phi_dev, src, 8 * h->n, cudaMemcpyDeviceToDevice, h->e->stream);
     if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy phi"));
   }

@@ -47,7 +47,7 @@ struct Layout {
   size_t o_sb = 0, o_coef2 = 0, o_itsb = 0;
   size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_sortscr = 0, o_xs = 0, o_boxes = 0, o_itord = 0;
   size_t o_redctr = 0;
-  size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0;
+  size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0, o_outdesc = 0;
   size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0, o_it4x = 0;
   size_t bytes = 0;
 };
@@ -60,7 +60,12 @@ class Engine {
   int set_sizes(const std::vector<int64_t>& ns);
   int attach(void* ptr, size_t bytes);
   int build(const double* xyz, const double* q, bool device_inputs);
-  int potentials();
+  // a potential pass if the potentials are not current; od: where it also writes its results
+  // (OutDesc), *wrote: whether a pass ran (and so wrote them)
+  int potentials(const OutDesc& od = OutDesc{nullptr, nullptr, 0, 0}, bool* wrote = nullptr);
+  int set_outputs(const OutDesc& od);
+  OutDesc* outdesc_d = nullptr;
+  OutDesc out_cur{nullptr, nullptr, 0, 0};  // what outdesc_d holds
   int field();                    // potentials and fields in one pass (lazily allocated buffers)
   int check_status();
   int delta_energy(int64_t k, const double* x_new, double* de);
@@ -173,7 +178,13 @@ class Engine {
   char* host_stage = nullptr;
   size_t host_stage_cap = 0;
   int ensure_host_stage(int64_t count);  // call before enqueueing the work whose results are copied
-  int copy_to_host(const double* src_d, int64_t count, double* dst_h);
+  double* host_stage_dev = nullptr;  // device addresses of the pinned buffers (kernel writes)
+  double* energy_h_dev = nullptr;
+  // the results of a host-output call: written: the pass just run wrote the values and the
+  // energy terms into the pinned buffers itself (OutDesc from host_outputs), else copied here
+  int copy_to_host(const double* src_d, int64_t count, double* dst_h, bool written = false);
+  OutDesc host_outputs(int64_t count, int what) const;
+  static int out_lane(int what);  // HSMA_TOTAL / HSMA_REACTION / HSMA_COULOMB -> OutDesc::what
   int decode_status(int st);
   bool field_ready = false;       // E is current when pot_ready && field_ready
   cudaGraphExec_t g_build = nullptr, g_pot = nullptr, g_field = nullptr, g_fused = nullptr, g_field_fused = nullptr;

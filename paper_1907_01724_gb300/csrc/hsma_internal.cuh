@@ -234,11 +234,20 @@ void launch_pairs_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, con
 // energy == nullptr: only the per-block energy terms (epart, two doubles per launch item) are
 // written; the reader sums them (Engine::read_energies), which spares every block the fence and
 // atomic of the last-block completion.
+// Where a potential pass also writes its results for the caller, read by k_reduce from device
+// memory (so that a captured graph serves any destination): the selected potential in input order
+// (device memory, or pinned host memory) and the per-block energy terms (pinned host memory);
+// null pointers: nowhere.
+struct OutDesc {
+  double* phi;
+  double* epart;
+  int what;  // 0 Coulomb, 1 reaction, 2 total
+  int pad;
+};
 void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
                    const float2* part, const double* part64, int prec, const double* q, const int* perm,
                    const double* r0, double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy,
-                   unsigned int* counter, int* status, cudaStream_t st,
-                   bool pdl = false);
+                   unsigned int* counter, int* status, const OutDesc* out, cudaStream_t st, bool pdl = false);
 
 // ---- fields (k_field.cu): potential and E = -grad phi in one pass over the pair items ----
 int field_f32_occupancy(int cfg);

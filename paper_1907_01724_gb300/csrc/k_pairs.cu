@@ -270,7 +270,7 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
                                                         double* __restrict__ phi_c, double* __restrict__ phi_r,
                                                         double* __restrict__ phi_t, double* __restrict__ epart,
                                                         double* __restrict__ energy, unsigned int* __restrict__ counter,
-                                                        int* __restrict__ status)
+                                                        int* __restrict__ status, const OutDesc* __restrict__ out)
 {
   __shared__ double red[2][kRedThreads / 32];
   __shared__ bool last;
@@ -292,6 +292,8 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     o = S.chg + perm[S.chg + i];  // partials are in sorted order
     qi = q[o];
   }
+  // the caller's destinations (written by the host before the launch)
+  const OutDesc od = out ? *out : OutDesc{nullptr, nullptr, 0, 0};
   // launch-local system r of this block (sel_rng ascending: the last r whose range starts at or
   // before this block), found by thread 0 before the wait
   int r_blk = 0, cnt_blk = 0;
@@ -329,6 +331,7 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
       phi_c[o] = pc;
       phi_r[o] = pr;
       phi_t[o] = pc + pr;
+      if (od.phi) od.phi[o] = od.what == 0 ? pc : (od.what == 1 ? pr : pc + pr);
       if (!isfinite(pc) || !isfinite(pr)) atomicOr(status, kStNonFinite);
       et = 0.5 * qi * (pc + pr);
       er = 0.5 * qi * pr;
@@ -352,7 +355,9 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     const df t = c + r;
     if (i < n && sub < 3) {
       double* dst = sub == 0 ? phi_c : (sub == 1 ? phi_r : phi_t);
-      dst[o] = df_to_double(sub == 0 ? c : (sub == 1 ? r : t));
+      const double v = df_to_double(sub == 0 ? c : (sub == 1 ? r : t));
+      dst[o] = v;
+      if (od.phi && sub == od.what) od.phi[o] = v;
       if (sub == 0 && !(isfinite(c.hi) && isfinite(r.hi))) atomicOr(status, kStNonFinite);
     }
     const df hq = df_from_double(0.5 * qi);
@@ -381,6 +386,10 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     }
     epart[2 * blockIdx.x] = a;
     epart[2 * blockIdx.x + 1] = b;
+    if (od.epart) {
+      od.epart[2 * blockIdx.x] = a;
+      od.epart[2 * blockIdx.x + 1] = b;
+    }
     last = false;
     if (energy) {
       __threadfence();
@@ -426,11 +435,11 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
 void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
                    const float2* part, const double* part64, int prec, const double* q, const int* perm,
                    const double* r0, double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy,
-                   unsigned int* counter, int* status, cudaStream_t st, bool pdl)
+                   unsigned int* counter, int* status, const OutDesc* out, cudaStream_t st, bool pdl)
 {
   if (nitems <= 0) return;
   launch_k(k_reduce, nitems, kRedThreads, 0, st, pdl, sys, sel, sel_rng, nsel, items, part, part64, prec, q, perm, r0,
-           phi_c, phi_r, phi_t, epart, energy, counter, status);
+           phi_c, phi_r, phi_t, epart, energy, counter, status, out);
 }
 
 }  // namespace hsma

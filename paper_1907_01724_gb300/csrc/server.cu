@@ -324,7 +324,7 @@ static int launch_energy(hsma_server_t* s, EnergySlot& sl, int chain)
   if (!it5.empty()) {
     hsma::launch_reduce(e->sys_d, sl.sel_d, sl.selrng_d, 1, sl.it5_d, (int)it5.size(), e->part_d, e->part64_d, e->prec,
                         e->q_d, e->perm_d, e->r0_d, e->phic_d, e->phir_d, e->phit_d, sl.epart_d, e->energy_d, sl.ctr_d + 1,
-                        e->status_d, sl.st);
+                        e->status_d, nullptr, sl.st);
     e->launches += 1;
   }
   SCK(cudaGetLastError());

@@ -20,8 +20,7 @@ RESULT = np.dtype([("id", "i8"), ("status", "i4"), ("pad", "i4"), ("value", "f8"
 assert REQUEST.itemsize == 64 and RESULT.itemsize == 40
 
 
-def _p(a: np.ndarray):
-    return ctypes.c_void_p(a.ctypes.data)
+_p = _native.host_ptr
 
 
 class Server:

@@ -1,0 +1,98 @@
+"""Where a potential pass writes its results: straight into the caller's array (device output) or
+pinned staging (host output) when the call runs the pass, by copies when the potentials are
+already current; a later pass that asks for no output must leave earlier destinations alone."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_01724_gb300 import api, batch, inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def systems():
+    rng = np.random.default_rng(31)
+    return [inputs.System(xyz=inputs.uniform_ball(rng, n, 1.0), q=rng.choice([-1.0, 1.0], size=n), a=1.0, eps1=1.0,
+                          eps2=78.5, kappa=1.0, p=12, M=400, tau=0.1) for n in (700, 129)]
+
+
+def refs(sy):
+    out = []
+    for s in sy:
+        P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+        out.append(oracle.hsma(P, s.xyz, s.q))
+    return out
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
+def test_device_and_host_outputs_alternate(prec):
+    tol = 1e-6 if prec == api.HSMA_FP32 else 1e-12
+    sy = systems()
+    ref = refs(sy)
+    n, xyz, q = batch.concat(sy)
+    tot = int(n.sum())
+    key = {api.HSMA_TOTAL: "phi", api.HSMA_REACTION: "phi_rf", api.HSMA_COULOMB: "phi_coul"}
+    want = {w: np.concatenate([r[k] for r in ref]) for w, k in key.items()}
+    b = batch.from_systems(sy, precision=prec)
+    A = torch.full((tot,), -7.0, dtype=torch.float64, device="cuda")
+    B = torch.full((tot,), -7.0, dtype=torch.float64, device="cuda")
+    # the pass runs in this call and writes A itself
+    b.hsma_batch_build_sources(n, xyz, q)
+    b.hsma_batch_potential(api.HSMA_REACTION, out=A)
+    torch.cuda.synchronize()
+    a1 = A.cpu().numpy()
+    assert rel(a1, want[api.HSMA_REACTION]) <= tol
+    # potentials current: copies, into B, another quantity
+    b.hsma_batch_potential(api.HSMA_COULOMB, out=B)
+    torch.cuda.synchronize()
+    assert rel(B.cpu().numpy(), want[api.HSMA_COULOMB]) <= tol
+    # a new pass that asks for no output (energies) must not touch A or B
+    A.fill_(-7.0)
+    B.fill_(-7.0)
+    b.hsma_batch_build_sources(n, xyz, q)
+    et, _ = b.hsma_batch_energy()
+    torch.cuda.synchronize()
+    assert np.all(A.cpu().numpy() == -7.0) and np.all(B.cpu().numpy() == -7.0)
+    for k, (s, r) in enumerate(zip(sy, ref)):
+        scale = max(abs(r["E_total"]), 0.5 * np.sum(np.abs(s.q * r["phi"])))
+        assert abs(et[k] - r["E_total"]) <= tol * scale
+    # host output of a fresh pass, then device output of the next, then host again
+    for w in (api.HSMA_TOTAL, api.HSMA_COULOMB):
+        b.hsma_batch_build_sources(n, xyz, q)
+        h = b.hsma_batch_potential(w)
+        assert rel(h, want[w]) <= tol
+        e1 = b.hsma_batch_energy()
+        b.hsma_batch_build_sources(n, xyz, q)
+        b.hsma_batch_potential(w, out=B)
+        torch.cuda.synchronize()
+        assert np.array_equal(B.cpu().numpy(), h)
+        assert np.array_equal(np.asarray(b.hsma_batch_energy()), np.asarray(e1))
+    assert np.all(A.cpu().numpy() == -7.0)
+
+
+def test_single_handle_outputs():
+    s = systems()[0]
+    ref = refs([s])[0]
+    prm = api.hsma_default_params(p=s.p, M=s.M, tau=s.tau)
+    h = api.hsma_create(s.a, s.eps1, s.eps2, s.kappa, prm)
+    api.hsma_build_sources(h, s.xyz, s.q)
+    out = torch.full((s.n,), -7.0, dtype=torch.float64, device="cuda")
+    api.hsma_potential(h, api.HSMA_TOTAL, out=out)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), ref["phi"]) <= 1e-6
+    host = api.hsma_potential(h, api.HSMA_TOTAL)
+    assert np.array_equal(host, out.cpu().numpy())
+    out.fill_(-7.0)
+    api.hsma_build_sources(h, s.xyz, s.q)
+    host2 = api.hsma_potential(h, api.HSMA_REACTION)
+    assert rel(host2, ref["phi_rf"]) <= 1e-6
+    et, er = api.hsma_energy(h)
+    assert abs(et - ref["E_total"]) <= 1e-6 * max(abs(ref["E_total"]), 0.5 * np.sum(np.abs(s.q * ref["phi"])))
+    torch.cuda.synchronize()
+    assert np.all(out.cpu().numpy() == -7.0)
+    api.hsma_destroy(h)
