@@ -95,6 +95,10 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
   const int n = S.n;
   const long long c0 = S.chg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // k_images, a programmatic dependent of this kernel, is dispatched right away and waits for
+  // this grid (a programmatic launch of this kernel after k_order_keys put both blocks on one
+  // SM beside a moment block: 3 us slower)
+  allow_dependents();
   int* slot = n <= kOrderSmemN ? s_slot : scr + 2 * c0;  // [n] input index, then [n] cell
   int* skey = slot + (n <= kOrderSmemN ? kOrderSmemN : n);
   int* h = hist + (size_t)blockIdx.x * kOrderCells;

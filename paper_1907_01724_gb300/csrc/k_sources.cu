@@ -361,50 +361,63 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
                                                         dbl4* __restrict__ src64, float4* __restrict__ boxes, int prec,
                                                         int* __restrict__ status)
 {
+  // the item and the system's constants are loaded while k_order_sort runs (this kernel is
+  // its programmatic dependent; a copy, so the loads precede the wait), perm after it
   const int2 it = items[blockIdx.x / kImgSplit];
-  const SysDev& S = sys[it.x];
+  const SysDev S = sys[it.x];
   const int n = S.n;
   const int i = it.y * kOrderBlock + (blockIdx.x % kImgSplit) * kImgThreads + threadIdx.x;
   const int lane = threadIdx.x & 31;
+  grid_dependency_wait();
   float bmin[6], bmax[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     bmin[d] = 3.0e38f;
     bmax[d] = -3.0e38f;
   }
-  if (i < n) {
-    const long long gi = S.chg + perm[S.chg + i];
-    const long long sr = S.src + i, sk = S.src + n + i;
-    if (prec == HSMA_FP64) {
+  if (prec == HSMA_FP64) {
+    if (i < n) {
+      const long long gi = S.chg + perm[S.chg + i];
       const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
       const KelvinRec k = kelvin_rec(S, x, y, z, qi);
       if (!(k.r < S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) atomicOr(status, kStOutside);
-      src64[sr] = make_dbl4(x, y, z, S.kc * qi);
-      src64[sk] = make_dbl4(k.kx, k.ky, k.kz, k.QK);
-    } else {
-      // from the (hi, lo) split of k_order_keys, in double-float arithmetic on the FP32 pipes
-      // (FP64 only for a charge within 2 kCentreRel a of the centre): r^2, s = a^2 / r^2,
-      // the Kelvin point s x (its (hi, lo) pair is the record's split), r_K = a sqrt(s) and
-      // q_K = q (qk1 r_K + qk0)
-      const float4 h = xs[2 * gi], l = xs[2 * gi + 1];
-      const df X = df_make(h.x, l.x), Y = df_make(h.y, l.y), Z = df_make(h.z, l.z), Q = df_make(h.w, l.w);
+      src64[S.src + i] = make_dbl4(x, y, z, S.kc * qi);
+      src64[S.src + n + i] = make_dbl4(k.kx, k.ky, k.kz, k.QK);
+    }
+  } else {
+    // from the (hi, lo) split of k_order_keys, in double-float arithmetic on the FP32 pipes
+    // (FP64 only for a charge within 2 kCentreRel a of the centre): r^2, s = a^2 / r^2, the
+    // Kelvin point s x (its (hi, lo) pair is the record's split), r_K = a sqrt(s) and
+    // q_K = q (qk1 r_K + qk0).  Lanes past the end repeat the last charge without storing
+    // anything, so that the warp does not diverge (a warp with a diverged tail was seen to end
+    // several microseconds after the others).
+    const bool on = i < n;
+    const int ic = on ? i : n - 1;
+    const long long gi = S.chg + perm[S.chg + ic];
+    const long long sr = S.src + ic, sk = S.src + n + ic;
+    const float4 h = xs[2 * gi], l = xs[2 * gi + 1];
+    const df X = df_make(h.x, l.x), Y = df_make(h.y, l.y), Z = df_make(h.z, l.z), Q = df_make(h.w, l.w);
+    if (on) {
       src_hi[sr] = make_float4(h.x, h.y, h.z, (df_make(S.f_kc.x, S.f_kc.y) * Q).hi);
       src_lo[sr] = make_float4(l.x, l.y, l.z, 0.f);
       bmin[0] = bmax[0] = h.x;
       bmin[1] = bmax[1] = h.y;
       bmin[2] = bmax[2] = h.z;
-      const df r2 = X * X + Y * Y + Z * Z;
-      // centre test as in kelvin_rec and k_moments, on r = sqrt(r^2) (to within the rounding of r^2)
-      if (r2.hi <= S.f_rc2 && sqrt(df_to_double(r2)) <= kCentreRel * S.a) {
+    }
+    const df r2 = X * X + Y * Y + Z * Z;
+    // centre test as in kelvin_rec and k_moments, on r = sqrt(r^2) (to within the rounding of r^2)
+    const bool centre = r2.hi <= S.f_rc2 && sqrt(df_to_double(r2)) <= kCentreRel * S.a;
+    const df s = df_make(S.f_a2.x, S.f_a2.y) * df_recip(r2);
+    const df kx = s * X, ky = s * Y, kz = s * Z;
+    const df rK = df_make(S.f_a.x, S.f_a.y) * df_sqrt(s);
+    const df QK = Q * (df_make(S.f_qk1.x, S.f_qk1.y) * rK + df_make(S.f_qk0.x, S.f_qk0.y));
+    if (on) {
+      if (centre) {
         // image at infinity (its constant potential is added by k_moments): a zero-strength
         // record, left out of the box
         src_hi[sk] = make_float4((float)(1e15 * S.a), 0.f, 0.f, 0.f);
         src_lo[sk] = make_float4(0.f, 0.f, 0.f, 0.f);
       } else {
-        const df s = df_make(S.f_a2.x, S.f_a2.y) * df_recip(r2);
-        const df kx = s * X, ky = s * Y, kz = s * Z;
-        const df rK = df_make(S.f_a.x, S.f_a.y) * df_sqrt(s);
-        const df QK = Q * (df_make(S.f_qk1.x, S.f_qk1.y) * rK + df_make(S.f_qk0.x, S.f_qk0.y));
         src_hi[sk] = make_float4(kx.hi, ky.hi, kz.hi, QK.hi);
         src_lo[sk] = make_float4(kx.lo, ky.lo, kz.lo, 0.f);
         bmin[3] = bmax[3] = kx.hi;
@@ -436,7 +449,7 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
                    int prec, int* status, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  launch_k(k_images, nitems * kImgSplit, kImgThreads, 0, st, false, sys, items, xyz, q, xs, perm, src_hi, src_lo,
+  launch_k(k_images, nitems * kImgSplit, kImgThreads, 0, st, true, sys, items, xyz, q, xs, perm, src_hi, src_lo,
            src64, boxes, prec, status);
 }
 
