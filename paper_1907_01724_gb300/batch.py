@@ -47,6 +47,7 @@ class Batch:
         self.use_torch_workspace = use_torch_workspace
         self.workspace = None
         self.n = None
+        self._ntot = 0
         if max_requests != 1:
             self.hsma_batch_set_max_requests(max_requests)
 
@@ -108,12 +109,13 @@ class Batch:
             qq = _arr(q, np.float64)
             self._check(self.lib.hsma_batch_build_sources(self.ptr, _p(n), _p(x), _p(qq)))
         self.n = n
+        self._ntot = int(n.sum())
 
     def hsma_batch_potential(self, what: int = HSMA_TOTAL, out=None):
         if out is not None and _is_torch_cuda(out):
             self._check(self.lib.hsma_batch_potential_device(self.ptr, ctypes.c_void_p(out.data_ptr()), int(what)))
             return out
-        phi = np.empty(int(self.n.sum()), dtype=np.float64)
+        phi = np.empty(self._ntot, dtype=np.float64)
         self._check(self.lib.hsma_batch_potential(self.ptr, _p(phi), int(what)))
         return phi
 
@@ -124,15 +126,15 @@ class Batch:
         if out is not None and _is_torch_cuda(out):
             self._check(self.lib.hsma_batch_field_device(self.ptr, ctypes.c_void_p(out.data_ptr()), int(what)))
             return out
-        E = np.empty((int(self.n.sum()), 3), dtype=np.float64)
+        E = np.empty((self._ntot, 3), dtype=np.float64)
         self._check(self.lib.hsma_batch_field(self.ptr, _p(E), int(what)))
         return E
 
     def hsma_batch_energy(self):
-        et = np.empty(self.nsys)
-        er = np.empty(self.nsys)
-        self._check(self.lib.hsma_batch_energy(self.ptr, _p(et), _p(er)))
-        return et, er
+        e = np.empty((2, self.nsys))  # (E_total, E_rf) rows: one buffer, one address lookup
+        p = _p(e).value
+        self._check(self.lib.hsma_batch_energy(self.ptr, ctypes.c_void_p(p), ctypes.c_void_p(p + 8 * self.nsys)))
+        return e[0], e[1]
 
     def hsma_batch_delta_energy(self, sys, k, x_new):
         sys = _arr(sys, np.int32)

@@ -219,13 +219,8 @@ static int batch_build(hsma_batch_t* b, const int64_t* n, const double* xyz, con
   if (!dev) {
     int64_t off = 0;
     for (size_t s = 0; s < ns.size(); ++s) {
-      const double a = b->e->spec[s].a;
-      for (int64_t i = off; i < off + ns[s]; ++i) {
-        const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-        if (!(x * x + y * y + z * z < a * a) || !std::isfinite(q[i]) || !std::isfinite(x) || !std::isfinite(y) ||
-            !std::isfinite(z))
-          return berr(b, HSMA_E_OUTSIDE, "a charge lies outside its cavity (|x| >= a) or is not finite");
-      }
+      if (!hsma::charges_inside(xyz + 3 * off, q + off, ns[s], b->e->spec[s].a))
+        return berr(b, HSMA_E_OUTSIDE, "a charge lies outside its cavity (|x| >= a) or is not finite");
       off += ns[s];
     }
   }

@@ -1296,13 +1296,8 @@ static int build_common(hsma_t* h, int64_t n, const double* xyz, const double* q
   if (n < 0 || n > (int64_t)INT32_MAX / 4) return set_err(h, HSMA_E_INVALID_ARG, "n out of range");
   if (n > 0 && (!xyz || !q)) return set_err(h, HSMA_E_INVALID_ARG, "NULL xyz or q");
   if (!dev) {
-    const double a = h->e->spec[0].a;
-    for (int64_t i = 0; i < n; ++i) {
-      const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-      const double r2 = x * x + y * y + z * z;
-      if (!(r2 < a * a) || !std::isfinite(q[i]) || !std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z))
-        return set_err(h, HSMA_E_OUTSIDE, "a charge lies outside the cavity (|x| >= a) or is not finite");
-    }
+    if (!hsma::charges_inside(xyz, q, n, h->e->spec[0].a))
+      return set_err(h, HSMA_E_OUTSIDE, "a charge lies outside the cavity (|x| >= a) or is not finite");
   }
   int rc = h->e->set_sizes({n});
   if (rc) return from_engine(h, rc);

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1907_01724_gb300 import api, inputs
+from paper_1907_01724_gb300 import api, batch, inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -228,3 +228,36 @@ def test_overlapped_and_separate_passes_agree_bitwise(prec):
     api.hsma_destroy(h)
     assert np.array_equal(phi0, phi1)
     assert e0 == e1
+
+
+@pytest.mark.parametrize("bad", ["nan_x", "inf_z", "inf_q", "nan_q", "on_sphere", "last_of_many"])
+def test_host_inputs_checked_at_build(bad):
+    """The host-input builds reject a charge at |x| >= a or a non-finite coordinate or charge
+    (HSMA_E_OUTSIDE = -2), single handle and batch, wherever it sits in the array."""
+    rng = np.random.default_rng(5)
+    xyz = inputs.uniform_ball(rng, 300, 0.9)
+    q = rng.choice([-1.0, 1.0], size=300)
+    k = 299 if bad == "last_of_many" else 17
+    if bad == "nan_x":
+        xyz[k, 0] = np.nan
+    elif bad == "inf_z":
+        xyz[k, 2] = -np.inf
+    elif bad == "inf_q":
+        q[k] = np.inf
+    elif bad == "nan_q":
+        q[k] = np.nan
+    elif bad == "on_sphere":
+        xyz[k] = (0.0, 1.0, 0.0)
+    else:
+        xyz[k] = (0.6, 0.6, 0.6)
+    prm = api.hsma_default_params(p=8, M=100)
+    h = api.hsma_create(1.0, 1.0, 80.0, 1.0, prm)
+    with pytest.raises(api.HsmaError) as e:
+        api.hsma_build_sources(h, xyz, q)
+    assert e.value.code == -2
+    api.hsma_destroy(h)
+    good = inputs.uniform_ball(rng, 50, 0.9)
+    b = batch.Batch([1.0, 1.0], [1.0, 1.0], [80.0, 80.0], [1.0, 1.0], prm)
+    with pytest.raises(api.HsmaError) as e:
+        b.hsma_batch_build_sources([50, 300], np.concatenate([good, xyz]), np.concatenate([np.ones(50), q]))
+    assert e.value.code == -2
