@@ -260,7 +260,7 @@ static int batch_pot(hsma_batch_t* b, double* phi, int what, bool dev)
   // a pass run by this call writes the result straight to the caller's device array, or (host
   // output) to pinned staging together with the energy terms (hsma_batch_energy then reads them
   // without a second round trip); a pass already run: copies
-  hsma::OutDesc od{dev && tot > 0 ? phi : nullptr, nullptr, Engine::out_lane(what), 0};
+  hsma::OutDesc od{dev && tot > 0 ? phi : nullptr, nullptr, nullptr, Engine::out_lane(what), 0};
   if (!dev) {
     const int rs = b->e->ensure_host_stage(tot);
     if (rs) return bfrom(b, rs);

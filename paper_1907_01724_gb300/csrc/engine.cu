@@ -555,7 +555,7 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
   CK(cudaMemsetAsync(energy_d, 0, 16 * L.sd.size(), stream));
   CK(cudaMemsetAsync(hist_d, 0, 4 * L.sd.size() * kOrderCells, stream));
   CK(cudaMemsetAsync(outdesc_d, 0, sizeof(OutDesc), stream));
-  out_cur = OutDesc{nullptr, nullptr, 0, 0};
+  out_cur = OutDesc{nullptr, nullptr, nullptr, 0, 0};
   // parameter-only quantities (scalars, M_n, tables, quadrature grid, surface basis), once per layout
   launch_setup(sys_d, (int)L.sd.size(), Mn_d, rec_a_d, rec_b_d, sect_d, inv_np1_d, rec_a2_d, rec_b2_d, sect2_d,
                L.pmax, surfx_d, stream);
@@ -776,7 +776,8 @@ int Engine::ensure_built()
 // change (a pageable source: the copy has taken it when the call returns).
 int Engine::set_outputs(const OutDesc& od)
 {
-  if (od.phi == out_cur.phi && od.epart == out_cur.epart && od.what == out_cur.what) return HSMA_OK;
+  if (od.phi == out_cur.phi && od.epart == out_cur.epart && od.status == out_cur.status && od.what == out_cur.what)
+    return HSMA_OK;
   out_cur = od;
   CK(cudaMemcpyAsync(outdesc_d, &out_cur, sizeof(OutDesc), cudaMemcpyHostToDevice, stream));
   return HSMA_OK;
@@ -1056,9 +1057,13 @@ int Engine::check_status()
 // status: one stream synchronisation instead of one per pageable copy.
 int Engine::out_lane(int what) { return what == HSMA_COULOMB ? 0 : (what == HSMA_REACTION ? 1 : 2); }
 
-OutDesc Engine::host_outputs(int64_t count, int what) const
+// Pinned staging of a host-output pass: values at byte 256, the status bytes at byte 16 (zeroed
+// here: the staging buffer is written only by passes that a host-output call waits for).
+OutDesc Engine::host_outputs(int64_t count, int what)
 {
-  return OutDesc{count > 0 ? host_stage_dev + 32 : nullptr, energy_h_dev, out_lane(what), 0};
+  std::memset(host_stage + 16, 0, kStBits);
+  return OutDesc{count > 0 ? host_stage_dev + 32 : nullptr, energy_h_dev,
+                 reinterpret_cast<unsigned char*>(host_stage_dev) + 16, out_lane(what), 0};
 }
 
 int Engine::copy_to_host(const double* src_d, int64_t count, double* dst_h, bool written)
@@ -1067,17 +1072,23 @@ int Engine::copy_to_host(const double* src_d, int64_t count, double* dst_h, bool
     return fail(HSMA_E_STATE, "host staging buffer not allocated");
   int* st_h = reinterpret_cast<int*>(host_stage);
   double* vals = reinterpret_cast<double*>(host_stage + 256);
+  int st = 0;
   if (written) {
-    energy_h_parts = true;  // the potential pass wrote its per-block energy terms
+    // the pass wrote the values, its per-block energy terms and its status bytes
+    energy_h_parts = true;
+    CK(cudaStreamSynchronize(stream));
+    const unsigned char* sb = reinterpret_cast<const unsigned char*>(host_stage) + 16;
+    for (int b = 0; b < kStBits; ++b)
+      if (sb[b]) st |= 1 << b;
   } else {
     if (count > 0) CK(cudaMemcpyAsync(vals, src_d, 8 * (size_t)count, cudaMemcpyDeviceToHost, stream));
     const int rs = stage_energies();
     if (rs) return rs;
+    CK(cudaMemcpyAsync(st_h, status_d, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    st = *st_h;
   }
-  int rc = 0;
-  CK(cudaMemcpyAsync(st_h, status_d, sizeof(int), cudaMemcpyDeviceToHost, stream));
-  CK(cudaStreamSynchronize(stream));
-  rc = decode_status(*st_h);
+  const int rc = decode_status(st);
   if (rc) return rc;
   if (count > 0) std::memcpy(dst_h, vals, 8 * (size_t)count);
   energy_h_epoch = pot_epoch;
@@ -1346,7 +1357,7 @@ int hsma_potential_device(hsma_t* h, double* phi_dev, int what)
   const double* src = pick_phi(h->e, what);
   if (!src) return set_err(h, HSMA_E_INVALID_ARG, "bad 'what'");
   bool wrote = false;
-  const hsma::OutDesc od{h->n > 0 ? phi_dev : nullptr, nullptr, Engine::out_lane(what), 0};
+  const hsma::OutDesc od{h->n > 0 ? phi_dev : nullptr, nullptr, nullptr, Engine::out_lane(what), 0};
   int rc = h->e->potentials(od, &wrote);
   if (rc) return from_engine(h, rc);
   if (h->n > 0 && !wrote) {

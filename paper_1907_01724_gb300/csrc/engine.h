@@ -80,10 +80,10 @@ class Engine {
   int build(const double* xyz, const double* q, bool device_inputs);
   // a potential pass if the potentials are not current; od: where it also writes its results
   // (OutDesc), *wrote: whether a pass ran (and so wrote them)
-  int potentials(const OutDesc& od = OutDesc{nullptr, nullptr, 0, 0}, bool* wrote = nullptr);
+  int potentials(const OutDesc& od = OutDesc{nullptr, nullptr, nullptr, 0, 0}, bool* wrote = nullptr);
   int set_outputs(const OutDesc& od);
   OutDesc* outdesc_d = nullptr;
-  OutDesc out_cur{nullptr, nullptr, 0, 0};  // what outdesc_d holds
+  OutDesc out_cur{nullptr, nullptr, nullptr, 0, 0};  // what outdesc_d holds
   int field();                    // potentials and fields in one pass (lazily allocated buffers)
   int check_status();
   int delta_energy(int64_t k, const double* x_new, double* de);
@@ -201,7 +201,7 @@ class Engine {
   // the results of a host-output call: written: the pass just run wrote the values and the
   // energy terms into the pinned buffers itself (OutDesc from host_outputs), else copied here
   int copy_to_host(const double* src_d, int64_t count, double* dst_h, bool written = false);
-  OutDesc host_outputs(int64_t count, int what) const;
+  OutDesc host_outputs(int64_t count, int what);
   static int out_lane(int what);  // HSMA_TOTAL / HSMA_REACTION / HSMA_COULOMB -> OutDesc::what
   int decode_status(int st);
   bool field_ready = false;       // E is current when pot_ready && field_ready

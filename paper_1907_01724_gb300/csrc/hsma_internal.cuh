@@ -236,14 +236,18 @@ void launch_pairs_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, con
 // atomic of the last-block completion.
 // Where a potential pass also writes its results for the caller, read by k_reduce from device
 // memory (so that a captured graph serves any destination): the selected potential in input order
-// (device memory, or pinned host memory) and the per-block energy terms (pinned host memory);
-// null pointers: nowhere.
+// (device memory, or pinned host memory), the per-block energy terms (pinned host memory) and the
+// pass's status flags, one byte per flag bit (pinned host memory, zeroed by the host before the
+// pass; bytes, so that blocks setting different flags never overwrite one another); null
+// pointers: nowhere.
 struct OutDesc {
   double* phi;
   double* epart;
+  unsigned char* status;
   int what;  // 0 Coulomb, 1 reaction, 2 total
   int pad;
 };
+constexpr int kStBits = 4;  // status flag bits mirrored by OutDesc::status
 void launch_reduce(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items, int nitems,
                    const float2* part, const double* part64, int prec, const double* q, const int* perm,
                    const double* r0, double* phi_c, double* phi_r, double* phi_t, double* epart, double* energy,

@@ -77,7 +77,7 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
     qi = q[o];
   }
   // the caller's destinations (written by the host before the launch)
-  const OutDesc od = out ? *out : OutDesc{nullptr, nullptr, 0, 0};
+  const OutDesc od = out ? *out : OutDesc{nullptr, nullptr, nullptr, 0, 0};
   // launch-local system r of this block (sel_rng ascending: the last r whose range starts at or
   // before this block), found by thread 0 before the wait
   int r_blk = 0, cnt_blk = 0;
@@ -97,6 +97,12 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   // (launched as a programmatic dependent of the pair kernel: everything above reads data that
   // the pair sum does not write; the partials below wait for it)
   grid_dependency_wait();
+  if (od.status && blockIdx.x == 0 && threadIdx.x == 0) {
+    // the flags of the pass's earlier kernels (all complete here), for the caller's host copy
+    const int st = __ldcg(status);
+    for (int b = 0; b < kStBits; ++b)
+      if (st & (1 << b)) od.status[b] = 1;
+  }
   double et = 0.0, er = 0.0;
   const int nch = S.ncr + S.nck + S.ncs;
   if (prec == HSMA_FP64) {
@@ -116,7 +122,10 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
       phi_r[o] = pr;
       phi_t[o] = pc + pr;
       if (od.phi) od.phi[o] = od.what == 0 ? pc : (od.what == 1 ? pr : pc + pr);
-      if (!isfinite(pc) || !isfinite(pr)) atomicOr(status, kStNonFinite);
+      if (!isfinite(pc) || !isfinite(pr)) {
+        atomicOr(status, kStNonFinite);
+        if (od.status) od.status[1] = 1;
+      }
       et = 0.5 * qi * (pc + pr);
       er = 0.5 * qi * pr;
     }
@@ -142,7 +151,10 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
       const double v = df_to_double(sub == 0 ? c : (sub == 1 ? r : t));
       dst[o] = v;
       if (od.phi && sub == od.what) od.phi[o] = v;
-      if (sub == 0 && !(isfinite(c.hi) && isfinite(r.hi))) atomicOr(status, kStNonFinite);
+      if (sub == 0 && !(isfinite(c.hi) && isfinite(r.hi))) {
+        atomicOr(status, kStNonFinite);
+        if (od.status) od.status[1] = 1;
+      }
     }
     const df hq = df_from_double(0.5 * qi);
     df ect = i < n && sub == 0 ? hq * t : df_make(0.f, 0.f);
