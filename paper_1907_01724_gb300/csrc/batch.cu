@@ -287,16 +287,18 @@ static int batch_field(hsma_batch_t* b, double* E, int what, bool dev)
   int64_t tot = 0;
   for (auto v : b->n) tot += v;
   if (tot > 0 && !E) return berr(b, HSMA_E_INVALID_ARG, "NULL E");
-  int rc = b->e->field();
+  // host output through the pinned staging (with the energies and the status, one round trip)
+  int rc = dev ? HSMA_OK : b->e->ensure_host_stage(3 * tot);
+  if (rc) return bfrom(b, rc);
+  rc = b->e->field();
   if (rc) return bfrom(b, rc);
   const double* src = what == HSMA_TOTAL ? b->e->Et_d : (what == HSMA_REACTION ? b->e->Er_d : b->e->Ec_d);
+  if (!dev) return bfrom(b, b->e->copy_to_host(src, 3 * tot, E));
   if (tot > 0) {
-    cudaError_t e = cudaMemcpyAsync(E, src, 24 * tot, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                    b->e->stream);
+    cudaError_t e = cudaMemcpyAsync(E, src, 24 * tot, cudaMemcpyDeviceToDevice, b->e->stream);
     if (e != cudaSuccess) return bfrom(b, b->e->cuda_fail(e, "copy E"));
   }
-  if (dev) return HSMA_OK;
-  return bfrom(b, b->e->check_status());
+  return HSMA_OK;
 }
 
 int hsma_batch_set_overlap(hsma_batch_t* b, int on)

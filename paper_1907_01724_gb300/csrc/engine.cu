@@ -1382,15 +1382,16 @@ static int field_out(hsma_t* h, double* E, int what, bool dev)
   if (h->n > 0 && !E) return set_err(h, HSMA_E_INVALID_ARG, "NULL E");
   if (what != HSMA_TOTAL && what != HSMA_REACTION && what != HSMA_COULOMB)
     return set_err(h, HSMA_E_INVALID_ARG, "bad 'what'");
-  int rc = h->e->field();
+  int rc = dev ? HSMA_OK : h->e->ensure_host_stage(3 * h->n);
   if (rc) return from_engine(h, rc);
+  rc = h->e->field();
+  if (rc) return from_engine(h, rc);
+  if (!dev) return from_engine(h, h->e->copy_to_host(pick_field(h->e, what), 3 * h->n, E));
   if (h->n > 0) {
-    cudaError_t e = cudaMemcpyAsync(E, pick_field(h->e, what), 24 * h->n,
-                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->e->stream);
+    cudaError_t e = cudaMemcpyAsync(E, pick_field(h->e, what), 24 * h->n, cudaMemcpyDeviceToDevice, h->e->stream);
     if (e != cudaSuccess) return from_engine(h, h->e->cuda_fail(e, "copy E"));
   }
-  if (dev) return HSMA_OK;
-  return from_engine(h, h->e->check_status());
+  return HSMA_OK;
 }
 
 int hsma_field(hsma_t* h, double* E, int what) { return field_out(h, E, what, false); }
