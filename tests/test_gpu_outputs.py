@@ -96,3 +96,51 @@ def test_single_handle_outputs():
     torch.cuda.synchronize()
     assert np.all(out.cpu().numpy() == -7.0)
     api.hsma_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
+def test_call_sequences_after_host_outputs(prec):
+    """Builds, host and device potentials of different quantities, fields and energies in
+    sequence: whatever the caller asks next gets the results of the current positions (the
+    pinned staging of a host-output pass is never mistaken for a later pass's values)."""
+    tol = 1e-6 if prec == api.HSMA_FP32 else 1e-12
+    sy = systems()
+    n, xyz, q = batch.concat(sy)
+    rng = np.random.default_rng(77)
+    xyz2 = xyz.copy()
+    xyz2[::7] *= 0.97  # moved charges (still inside)
+    sy2 = [inputs.System(xyz=xyz2[a:a + s.n], q=s.q, a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M,
+                         tau=s.tau) for s, a in zip(sy, np.cumsum([0] + [s.n for s in sy])[:-1])]
+    r1, r2 = refs(sy), refs(sy2)
+    phi1 = np.concatenate([r["phi"] for r in r1])
+    phi2 = np.concatenate([r["phi"] for r in r2])
+    rf2 = np.concatenate([r["phi_rf"] for r in r2])
+    b = batch.from_systems(sy, precision=prec)
+    b.hsma_batch_build_sources(n, xyz, q)
+    assert rel(b.hsma_batch_potential(), phi1) <= tol
+    b.hsma_batch_build_sources(n, xyz2, q)
+    assert rel(b.hsma_batch_potential(), phi2) <= tol
+    et, _ = b.hsma_batch_energy()
+    for k, (s, r) in enumerate(zip(sy2, r2)):
+        scale = max(abs(r["E_total"]), 0.5 * np.sum(np.abs(s.q * r["phi"])))
+        assert abs(et[k] - r["E_total"]) <= tol * scale
+    # another quantity of the early pass, then a field request, then potentials again
+    b.hsma_batch_build_sources(n, xyz, q)
+    b.hsma_batch_build_sources(n, xyz2, q)
+    assert rel(b.hsma_batch_potential(api.HSMA_REACTION), rf2) <= tol
+    assert rel(b.hsma_batch_potential(), phi2) <= tol
+    b.hsma_batch_build_sources(n, xyz, q)
+    E = b.hsma_batch_field()
+    off = 0
+    for s in sy:
+        P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+        assert rel(E[off:off + s.n], oracle.field(P, s.xyz, s.q)["E"]) <= tol
+        off += s.n
+    assert rel(b.hsma_batch_potential(), phi1) <= tol
+    # energies only, after two builds
+    b.hsma_batch_build_sources(n, xyz2, q)
+    b.hsma_batch_build_sources(n, xyz2, q)
+    et, _ = b.hsma_batch_energy()
+    for k, (s, r) in enumerate(zip(sy2, r2)):
+        scale = max(abs(r["E_total"]), 0.5 * np.sum(np.abs(s.q * r["phi"])))
+        assert abs(et[k] - r["E_total"]) <= tol * scale
