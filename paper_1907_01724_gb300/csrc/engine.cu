@@ -644,13 +644,13 @@ void Engine::issue_pot()
 
 int Engine::pot_launch_count() const { return (L.it4.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1); }
 
-void Engine::launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t st)
+void Engine::launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t st, bool pdl)
 {
   if (w1.nitems <= 0 && w2.nitems <= 0) return;
   if (prec == HSMA_FP64)
-    launch_pairs_f64(grid, sys_d, w1, w2, src64_d, surf64a_d, surf64b_d, part64_d, st);
+    launch_pairs_f64(grid, sys_d, w1, w2, src64_d, surf64a_d, surf64b_d, part64_d, st, pdl);
   else
-    launch_pairs_f32(L.cfg, grid, sys_d, w1, w2, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, part_d, st);
+    launch_pairs_f32(L.cfg, grid, sys_d, w1, w2, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, part_d, st, pdl);
 }
 
 // Build and potentials in one graph.  The real/Kelvin pair items need only the records, so they
@@ -700,12 +700,14 @@ void Engine::issue_fused()
   PriorityScope ps(prio_mid);
   launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
                  L.mom_stride, stream);
+  // the records are joined before the coefficients (done by then), so that the main stream's
+  // pair launch has a single dependency and starts as a programmatic dependent of the surface
+  cudaStreamWaitEvent(stream, ev_img, 0);
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
   launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
                  surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
-  cudaStreamWaitEvent(stream, ev_img, 0);
-  launch_pair_items(srf, rk, grid_s, stream);
+  launch_pair_items(srf, rk, grid_s, stream, true);
   cudaStreamWaitEvent(stream, ev_join, 0);
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
                 phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, outdesc_d, stream, true);
@@ -943,13 +945,14 @@ int Engine::field_slots() const
   return num_sms * std::max(prec == HSMA_FP64 ? occ_field64 : occ_field[L.cfg], 1);
 }
 
-void Engine::launch_field_items(PairWork w1, PairWork w2, int grid, cudaStream_t st)
+void Engine::launch_field_items(PairWork w1, PairWork w2, int grid, cudaStream_t st, bool pdl)
 {
   if (w1.nitems <= 0 && w2.nitems <= 0) return;
   if (prec == HSMA_FP64)
-    launch_field_f64(grid, sys_d, w1, w2, src64_d, surf64a_d, surf64b_d, (dbl4*)fpart_d, st);
+    launch_field_f64(grid, sys_d, w1, w2, src64_d, surf64a_d, surf64b_d, (dbl4*)fpart_d, st, pdl);
   else
-    launch_field_f32(L.cfg, grid, sys_d, w1, w2, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, (float4*)fpart_d, st);
+    launch_field_f32(L.cfg, grid, sys_d, w1, w2, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, (float4*)fpart_d, st,
+                     pdl);
 }
 
 void Engine::launch_field_reduce(cudaStream_t st)
@@ -1000,12 +1003,12 @@ void Engine::issue_field_fused()
   PriorityScope ps(prio_mid);
   launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
                  L.mom_stride, stream);
+  cudaStreamWaitEvent(stream, ev_img, 0);  // (as in issue_fused)
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
   launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
                  surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
-  cudaStreamWaitEvent(stream, ev_img, 0);
-  launch_field_items(srf, rk, grid_s, stream);
+  launch_field_items(srf, rk, grid_s, stream, true);
   cudaStreamWaitEvent(stream, ev_join, 0);
   launch_field_reduce(stream);
 }

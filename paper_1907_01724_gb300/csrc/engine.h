@@ -224,9 +224,9 @@ class Engine {
   void issue_pot();
   void issue_field();
   void issue_fused();
-  void launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t st);
+  void launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t st, bool pdl = false);
   int field_slots() const;
-  void launch_field_items(PairWork w1, PairWork w2, int grid, cudaStream_t st);
+  void launch_field_items(PairWork w1, PairWork w2, int grid, cudaStream_t st, bool pdl = false);
   void launch_field_reduce(cudaStream_t st);
   void issue_field_fused();
   int fused_launch_count() const;

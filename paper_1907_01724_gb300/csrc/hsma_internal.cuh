@@ -222,11 +222,14 @@ int pairs_f64_occupancy();
 constexpr int kF64TargetsPerBlock = 128;
 constexpr int kReduceTargetsPerBlock = 32;
 // Persistent pair-sum launches: each CTA takes items of w1 until it is exhausted, then of w2.
+// pdl: launched as a programmatic dependent of the stream's previous kernel (the kernels wait
+// for it before touching any work).
 void launch_pairs_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
                       const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
-                      float2* part, cudaStream_t st);
+                      float2* part, cudaStream_t st, bool pdl = false);
 void launch_pairs_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, const dbl4* src64,
-                      const dbl4* surf64_a, const double* surf64_b, double* part64, cudaStream_t st);
+                      const dbl4* surf64_a, const double* surf64_b, double* part64, cudaStream_t st,
+                      bool pdl = false);
 // Reduce the pair partials of the launched items to potentials and energies; the energies of
 // system sel[r] are summed from the launch items sel_rng[r] = (first, count), ranges ascending
 // and contiguous; counter[r] (zero before the launch, zero after it) counts r's finished items.
@@ -260,9 +263,10 @@ int field_f64_occupancy();
 // Work lists as for the pair kernels (w1, then w2).
 void launch_field_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
                       const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
-                      float4* fpart, cudaStream_t st);
+                      float4* fpart, cudaStream_t st, bool pdl = false);
 void launch_field_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, const dbl4* src64,
-                      const dbl4* surf64_a, const double* surf64_b, dbl4* fpart64, cudaStream_t st);
+                      const dbl4* surf64_a, const double* surf64_b, dbl4* fpart64, cudaStream_t st,
+                      bool pdl = false);
 // as launch_reduce, plus the Coulomb, reaction and total fields (3 doubles per charge, input order)
 void launch_reduce_field(const SysDev* sys, const int* sel, const int2* sel_rng, int nsel, const int2* items,
                          int nitems, const float4* fpart, const dbl4* fpart64, int prec, const double* q,

@@ -93,6 +93,7 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int list = 0;
   bool first_fetch = true;
+  grid_dependency_wait();  // (a programmatic launch: the records and counters of the pass)
 
   for (;;) {
     if (tid == 0) next_pair_item(w1, w2, list, first_fetch, s_item, s_list);
@@ -291,12 +292,12 @@ int field_f64_occupancy();
 
 void launch_field_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
                       const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
-                      float4* fpart, cudaStream_t st)
+                      float4* fpart, cudaStream_t st, bool pdl)
 {
   switch (pair_kernel_of(cfg)) {
 #define HSMA_FCFG_LAUNCH(i, nt, k)                                                                        \
   case i:                                                                                                 \
-    launch_k(k_field_f32<nt, k>, grid, nt, 0, st, false, sys, w1, w2, src_hi, src_lo, surf_a, surf_b, boxes, \
+    launch_k(k_field_f32<nt, k>, grid, nt, 0, st, pdl, sys, w1, w2, src_hi, src_lo, surf_a, surf_b, boxes, \
              fpart);                                                                                     \
     break;
     HSMA_FIELD_CONFIGS(HSMA_FCFG_LAUNCH)
@@ -321,6 +322,7 @@ __global__ __launch_bounds__(kF64FThreads) void k_field_f64(const SysDev* __rest
   const int tid = threadIdx.x;
   int list = 0;
   bool first_fetch = true;
+  grid_dependency_wait();  // (a programmatic launch: the records and counters of the pass)
   for (;;) {
     if (tid == 0) next_pair_item(w1, w2, list, first_fetch, s_item, s_list);
     first_fetch = false;
@@ -404,9 +406,9 @@ int field_f64_occupancy()
 }
 
 void launch_field_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, const dbl4* src64,
-                      const dbl4* surf64_a, const double* surf64_b, dbl4* fpart64, cudaStream_t st)
+                      const dbl4* surf64_a, const double* surf64_b, dbl4* fpart64, cudaStream_t st, bool pdl)
 {
-  launch_k(k_field_f64, grid, kF64FThreads, 0, st, false, sys, w1, w2, src64, surf64_a, surf64_b, fpart64);
+  launch_k(k_field_f64, grid, kF64FThreads, 0, st, pdl, sys, w1, w2, src64, surf64_a, surf64_b, fpart64);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -121,12 +121,12 @@ int pairs_f32_occupancy(int cfg)
 
 void launch_pairs_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
                       const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
-                      float2* part, cudaStream_t st)
+                      float2* part, cudaStream_t st, bool pdl)
 {
   switch (pair_kernel_of(cfg)) {
 #define HSMA_CFG_LAUNCH(i, nt, k)                                                                          \
   case i:                                                                                                  \
-    launch_k(k_pairs_f32<nt, k>, grid, nt, 0, st, false, sys, w1, w2, src_hi, src_lo, surf_a, surf_b, boxes, part); \
+    launch_k(k_pairs_f32<nt, k>, grid, nt, 0, st, pdl, sys, w1, w2, src_hi, src_lo, surf_a, surf_b, boxes, part); \
     break;
     HSMA_PAIR_CONFIGS(HSMA_CFG_LAUNCH)
 #undef HSMA_CFG_LAUNCH
@@ -150,6 +150,7 @@ __global__ __launch_bounds__(kF64Threads) void k_pairs_f64(const SysDev* __restr
   const int tid = threadIdx.x;
   int list = 0;
   bool first_fetch = true;
+  grid_dependency_wait();  // (a programmatic launch: the records and counters of the pass)
   for (;;) {
     if (tid == 0) next_pair_item(w1, w2, list, first_fetch, s_item, s_list);
     first_fetch = false;
@@ -219,9 +220,9 @@ int pairs_f64_occupancy()
 }
 
 void launch_pairs_f64(int grid, const SysDev* sys, PairWork w1, PairWork w2, const dbl4* src64,
-                      const dbl4* surf64_a, const double* surf64_b, double* part64, cudaStream_t st)
+                      const dbl4* surf64_a, const double* surf64_b, double* part64, cudaStream_t st, bool pdl)
 {
-  launch_k(k_pairs_f64, grid, kF64Threads, 0, st, false, sys, w1, w2, src64, surf64_a, surf64_b, part64);
+  launch_k(k_pairs_f64, grid, kF64Threads, 0, st, pdl, sys, w1, w2, src64, surf64_a, surf64_b, part64);
 }
 
 }  // namespace hsma

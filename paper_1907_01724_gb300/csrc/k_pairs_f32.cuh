@@ -23,6 +23,7 @@ __global__ __launch_bounds__(NT) void k_pairs_f32(const SysDev* __restrict__ sys
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int list = 0;
   bool first_fetch = true;
+  grid_dependency_wait();  // (a programmatic launch: the records and counters of the pass)
 
   for (;;) {
     if (tid == 0) next_pair_item(w1, w2, list, first_fetch, s_item, s_list);
