@@ -1,17 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 HSMA hot path (arXiv:1907.01724, Algorithm 1 steps 4-5).
 
-Workload (default): two cavities of N = 2000 unit charges, 25% within 0.05a of the interface,
-eps1 = 1, eps2 = 80, kappa a in {0.5, 2}, M = 1000 points per shell, p = 20, FP32 pair sums
-with FP64 coefficient/surface/reduction steps.  Both cavities form one batch: one step = the
-whole hot path for both (per-system scalars, Kelvin images, correction coefficients, surface
-images, the tiled pair sum, the FP64 potential/energy reduction) as two CUDA-graph launches.
+Headline workload: one cavity of N = 20000 unit charges uniform in a = 1, eps1 = eps2 = 78.5,
+kappa a = 3, M = 2000 points per shell, p = 30 (the largest single-system workload).  One step =
+the whole hot path (spatial order and Kelvin images, correction coefficients, surface images,
+the tiled pair sum, the potential/energy reduction) as one CUDA-graph launch.  FP32 pair sums;
+the moments, coefficients, surface synthesis and reductions in double-float arithmetic
+(~2^-46 relative), the geometry of the records in FP64.
 
 Metric: Coulomb pair-evaluations per second, counting per cavity N (2N - 1 + 3M) pairs (every
 charge against the other real charges, the N Kelvin images and the 3M surface images of
-eq. phicorrfinall).  Inputs are seeded synthetic data (random charges in the ball, the
-paper's workload type).  L2 is flushed (256 MB write) before every timed step, outside the
-timed events.
+eq. phicorrfinall).  Inputs are seeded synthetic data (random charges in the ball, the paper's
+workload type).  L2 is flushed (256 MB write) before every timed step, outside the timed events.
+
+Sections: the near-interface workload (two cavities of N = 2000, 25% within 0.05a of the
+interface, M = 1000, p = 20), fields, the batched workload (512 cavities) and the serving loop.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs its own independent cavities (weak scaling, no collective on
@@ -38,9 +41,16 @@ from paper_1907_01724_gb300 import inputs  # noqa: E402
 
 SM_MUFU_PER_CLK = 16  # rsqrt results per SM per clock (one pair evaluation each)
 METRIC = "Coulomb pair-evals/s at rel err <=1e-6 vs FP64"
+DTYPE = "f32 pair sums; double-float (~2^-46) moments, coefficients, surface and reductions; f64 geometry"
 
 
 def workload(rank: int):
+    """The headline workload: one cavity, N = 20000 uniform, eps1 = eps2 = 78.5, kappa a = 3,
+    M = 2000, p = 30."""
+    return [inputs.primitive_system(seed_offset=1000 * rank)]
+
+
+def near_interface_workload(rank: int):
     off = 1000 * rank
     return [inputs.near_interface_system(kappa_a=0.5, seed_offset=off),
             inputs.near_interface_system(kappa_a=2.0, seed_offset=off)]
@@ -80,11 +90,32 @@ def profiled_traffic(kernel_srcs, profile_md: str):
 
 def config_dict(systems, n_gpus):
     s = systems[0]
-    return {"workload": f"2 cavities N={s.n} (25% within 0.05a of the interface), eps1=1, eps2=80, "
-                        f"kappa*a in {{0.5,2}}, M={s.M}, p={s.p}, tau=0.1, FP32 pair sums",
-            "systems_per_gpu": len(systems), "N": s.n, "M": s.M, "p": s.p,
+    return {"workload": f"1 cavity N={s.n} uniform in a=1, eps1=eps2=78.5, kappa*a=3, M={s.M}, p={s.p}, "
+                        f"tau=0.1, FP32 pair sums",
+            "systems_per_gpu": len(systems), "N": s.n, "M": s.M, "p": s.p, "kappa_a": s.kappa * s.a,
+            "eps1": s.eps1, "eps2": s.eps2,
             "pairs_per_step_per_gpu": int(sum(pairs(x) for x in systems)),
             "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{n_gpus}"}
+
+
+def affinity():
+    """Host cores this process may run on: count and the mask as ranges."""
+    try:
+        cpus = sorted(os.sched_getaffinity(0))
+    except AttributeError:
+        cpus = list(range(os.cpu_count() or 1))
+    rng, start, prev = [], None, None
+    for c in cpus:
+        if start is None:
+            start = prev = c
+        elif c == prev + 1:
+            prev = c
+        else:
+            rng.append(f"{start}-{prev}" if prev > start else f"{start}")
+            start = prev = c
+    if start is not None:
+        rng.append(f"{start}-{prev}" if prev > start else f"{start}")
+    return len(cpus), ",".join(rng)
 
 
 class Clocks:
@@ -169,9 +200,13 @@ def aggregate(world: int, local_seconds: float, local_units: float, device: str 
     return units / t_max, t_max, units
 
 
-def oracle_run(systems, budget_s: float = 10.0, max_rounds: int = 50):
-    """FP64 oracle over the whole workload, repeated until about budget_s of CPU work."""
+def oracle_run(systems, budget_s: float = 10.0, max_rounds: int = 50, nthreads: int = 0):
+    """FP64 oracle over the whole workload (build + potentials + energies of every system),
+    repeated until about budget_s of CPU work; nthreads OpenMP threads (0 = one per core of the
+    affinity mask).  Returns the results of the first round, pair-evals/s, seconds, rounds and
+    the threads used."""
     import oracle
+    th = nthreads if nthreads > 0 else affinity()[0]
     t0 = time.perf_counter()
     done = 0
     rounds = 0
@@ -179,7 +214,8 @@ def oracle_run(systems, budget_s: float = 10.0, max_rounds: int = 50):
     while True:
         out = []
         for s in systems:
-            P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+            P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau,
+                                   nthreads=th)
             out.append(oracle.hsma(P, s.xyz, s.q))
             done += pairs(s)
         refs = refs or out
@@ -187,7 +223,138 @@ def oracle_run(systems, budget_s: float = 10.0, max_rounds: int = 50):
         el = time.perf_counter() - t0
         if el >= budget_s or rounds >= max_rounds:
             break
-    return refs, done / el, el, rounds, oracle.threads()
+    return refs, done / el, el, rounds, th
+
+
+def cpu_baselines(systems, quick: bool):
+    """The oracle timed on the host cores on the same workload: every core of the affinity mask
+    (repeated to about 8 s), then one thread (one pass over the whole workload)."""
+    ncores, mask = affinity()
+    refs, rate, el, rounds, th = oracle_run(systems, budget_s=0.0 if quick else 8.0, max_rounds=1 if quick else 20)
+    cpu = {"value": rate, "unit": "pair-evals/s", "cores": th, "kind": "oracle",
+           "sample": f"whole workload (build + potentials + energies) x{rounds}, {el:.1f} s",
+           "affinity": {"cores": ncores, "mask": mask}}
+    if not quick:
+        _, rate1, el1, rounds1, _ = oracle_run(systems, budget_s=0.0, max_rounds=1, nthreads=1)
+        cpu["single_thread"] = {"value": rate1, "unit": "pair-evals/s", "cores": 1,
+                                "sample": f"whole workload x{rounds1}, {el1:.1f} s"}
+    return refs, cpu
+
+
+def accuracy(systems, refs, phi, et):
+    """Norm-wise potential errors, pointwise maxima and energy errors against the oracle."""
+    out = {"phi_rel_l2_max": 0.0, "phi_pointwise_abs_over_max": 0.0, "energy_rel_max": 0.0,
+           "reference": "FP64 oracle"}
+    off = 0
+    for s, r, e in zip(systems, refs, et):
+        p = phi[off:off + s.n]
+        off += s.n
+        d = np.abs(p - r["phi"])
+        scale = max(abs(r["E_total"]), 0.5 * float(np.sum(np.abs(s.q * r["phi"]))))
+        out["phi_rel_l2_max"] = max(out["phi_rel_l2_max"], float(np.linalg.norm(d) / np.linalg.norm(r["phi"])))
+        out["phi_pointwise_abs_over_max"] = max(out["phi_pointwise_abs_over_max"],
+                                                float(d.max() / np.abs(r["phi"]).max()))
+        out["energy_rel_max"] = max(out["energy_rel_max"], abs(e - r["E_total"]) / scale)
+    return out
+
+
+def timed_steps(step, stream, flush, k):
+    """k steps, L2 flushed before each (outside the events), CUDA events on the work stream;
+    returns the total seconds."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for i in range(k):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(c) for a, c in ev) / 1e3
+
+
+def pair_kernel_alone(b, step, flush, reps):
+    """The pair kernel timed alone: in the timed steps it overlaps the coefficient chain, so it
+    is timed in separate passes (same items, bitwise the same results), CUDA events around each
+    launch on its stream; mean seconds per launch."""
+    b.hsma_batch_set_overlap(False)
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        step()
+        ms.append(b.hsma_batch_last_pair_time())
+    b.hsma_batch_set_overlap(True)
+    return statistics.mean(ms) / 1e3, len(ms)
+
+
+def e2e_run(b, n, xyz, q, units_per_step, world, k):
+    """End to end through the C ABI with pinned host buffers: the H2D copy of the inputs, the
+    step, and the D2H read of the potentials and energies inside the timed region."""
+    import torch
+
+    from paper_1907_01724_gb300 import api
+    xyz_h = torch.tensor(xyz).pin_memory().numpy()
+    q_h = torch.tensor(q).pin_memory().numpy()
+
+    def e2e_step():
+        b.hsma_batch_build_sources(n, xyz_h, q_h)
+        b.hsma_batch_potential(api.HSMA_TOTAL)
+        b.hsma_batch_energy()
+
+    for _ in range(3):
+        e2e_step()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        e2e_step()
+    torch.cuda.synchronize()
+    te = allreduce(world, time.perf_counter() - t0, "max")
+    return {"value": allreduce(world, float(units_per_step * k), "sum") / te,
+            "unit": "pair-evals/s", "h2d_bytes_per_step": int(32 * n.sum()),
+            "d2h_bytes_per_step": int(8 * n.sum() + 16 * len(n)), "steps": k,
+            "ms_per_step": te / k * 1e3}
+
+
+def run_near_interface(local, stream, gpu_name, steps):
+    """The near-interface workload (two cavities of N = 2000, 25% within 0.05a of the interface,
+    M = 1000, p = 20): whole-path steps, the pair kernel alone, end to end, accuracy."""
+    import torch
+
+    from paper_1907_01724_gb300 import api, batch
+    systems = near_interface_workload(0)
+    refs, _, _, _, _ = oracle_run(systems, budget_s=0.0, max_rounds=1)
+    n, xyz, q = batch.concat(systems)
+    b = batch.from_systems(systems, precision=api.HSMA_FP32, device=local, stream=stream)
+    cfg = batch.autotuned(b, n, xyz, q, gpu=gpu_name, reps=5)
+    dev = torch.device(f"cuda:{local}")
+    xyz_d = torch.tensor(xyz, device=dev)
+    q_d = torch.tensor(q, device=dev)
+    phi_d = torch.empty(int(n.sum()), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        b.hsma_batch_build_sources(n, xyz_d, q_d)
+        b.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
+
+    for _ in range(20):
+        step()
+    torch.cuda.synchronize()
+    acc = accuracy(systems, refs, b.hsma_batch_potential(api.HSMA_TOTAL), b.hsma_batch_energy()[0])
+    k = max(200, steps)
+    t = timed_steps(step, stream, flush, k)
+    units = sum(pairs(s) for s in systems)
+    t_pair, nrep = pair_kernel_alone(b, step, flush, 100)
+    props = torch.cuda.get_device_properties(local)
+    peak = props.multi_processor_count * SM_MUFU_PER_CLK * 2070.0e6
+    e2e = e2e_run(b, n, xyz, q, units, 1, max(50, steps // 4))
+    return {"workload": "2 cavities N=2000 (25% within 0.05a of the interface), eps1=1, eps2=80, "
+                        "kappa*a in {0.5,2}, M=1000, p=20, tau=0.1, FP32 pair sums",
+            "value": units * k / t, "unit": "pair-evals/s", "ms_per_step": t / k * 1e3, "steps": k,
+            "pair_kernel_alone": {"ms": t_pair * 1e3, "launches": nrep,
+                                  "frac_of_mufu_peak_at_2070MHz": units / t_pair / peak,
+                                  "frac_kernel_evals": sum(evals(s) for s in systems) / t_pair / peak},
+            "e2e": e2e, "pair_config": batch.pair_configs()[cfg], "accuracy_vs_oracle": acc,
+            "l2": "flushed before every timed step (256 MB write)"}
 
 
 def run_batched(local, stream, gpu_name):
@@ -267,7 +434,7 @@ def run_batched(local, stream, gpu_name):
 
 
 def run_field(local, stream, systems, gpu_name):
-    """Fields and potentials in one pass (hsma_batch_field) on the headline workload: build +
+    """Fields and potentials in one pass (hsma_batch_field) on the near-interface workload: build +
     field per step, the field pass's pair-evals/s, its kernel alone, and E against the oracle."""
     import torch
 
@@ -313,7 +480,7 @@ def run_field(local, stream, systems, gpu_name):
         off += s.n
     tk = statistics.mean(kern) / 1e3
     ev_per_launch = sum(evals(s) for s in systems)
-    return {"workload": "the headline workload, fields and potentials in one pass (build + field per step)",
+    return {"workload": "the near-interface workload, fields and potentials in one pass (build + field per step)",
             "pair_evals_per_s": sum(pairs(s) for s in systems) * k / t, "ms_per_step": t / k * 1e3, "steps": k,
             "field_kernel_ms": tk * 1e3, "field_kernel_evals_per_s": ev_per_launch / tk,
             "pair_config": batch.pair_configs()[cfg], "E_rel_l2_max_vs_oracle": worst,
@@ -388,11 +555,9 @@ def run_ours(args):
     cpu = None
     refs = None
     if rank == 0:
-        refs, cpu_rate, cpu_s, rounds, threads = oracle_run(systems, budget_s=0.0 if args.no_cpu_baseline else 10.0,
-                                                            max_rounds=1 if args.no_cpu_baseline else 50)
-        if world == 1:
-            cpu = {"value": cpu_rate, "unit": "pair-evals/s", "cores": threads, "kind": "oracle",
-                   "sample": f"full workload (both cavities, build + potentials + energy) x{rounds}, {cpu_s:.1f} s"}
+        refs, cpu = cpu_baselines(systems, quick=args.no_cpu_baseline or world > 1)
+        if world > 1:
+            cpu = None
 
     n, xyz, q = batch.concat(systems)
     b = batch.from_systems(systems, precision=api.HSMA_FP32, device=local, stream=stream)
@@ -403,73 +568,54 @@ def run_ours(args):
     phi_d = torch.empty(int(n.sum()), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def step(bb):
-        bb.hsma_batch_build_sources(n, xyz_d, q_d)
-        bb.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
+    def step():
+        b.hsma_batch_build_sources(n, xyz_d, q_d)
+        b.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
 
     for _ in range(args.warmup):
-        step(b)
+        step()
     torch.cuda.synchronize()
     acc = None
     if refs is not None:
-        phi = b.hsma_batch_potential(api.HSMA_TOTAL)
-        et, _ = b.hsma_batch_energy()
-        errs, off = [], 0
-        for s, r, e in zip(systems, refs, et):
-            p = phi[off:off + s.n]
-            off += s.n
-            scale = max(abs(r["E_total"]), 0.5 * float(np.sum(np.abs(s.q * r["phi"]))))
-            errs.append((np.linalg.norm(p - r["phi"]) / np.linalg.norm(r["phi"]), abs(e - r["E_total"]) / scale))
-        acc = {"phi_rel_l2_max": max(x[0] for x in errs), "energy_rel_max": max(x[1] for x in errs),
-               "reference": "FP64 oracle"}
+        acc = accuracy(systems, refs, b.hsma_batch_potential(api.HSMA_TOTAL), b.hsma_batch_energy()[0])
 
+    units = sum(pairs(s) for s in systems)
     launches0 = b.hsma_batch_kernel_launches()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    pair_ms = []
     clocks = Clocks(local)
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        step(b)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    t_local = timed_steps(step, stream, flush, args.steps)
     clk = clocks.stop()
     barrier(world)
     launches = b.hsma_batch_kernel_launches() - launches0
-    t_local = sum(a.elapsed_time(c) for a, c in ev) / 1e3
-    value, t_max, total_pairs = aggregate(world, t_local, float(sum(pairs(s) for s in systems) * args.steps))
+    value, t_max, total_pairs = aggregate(world, t_local, float(units * args.steps))
 
-    # the pair kernel alone: in the timed steps it overlaps the coefficient chain, so it is timed
-    # in separate passes (same items, bitwise the same results), events around each launch
-    b.hsma_batch_set_overlap(False)
-    for k in range(max(20, min(200, args.steps // 10))):
-        flush.zero_()
-        step(b)
-        pair_ms.append(b.hsma_batch_last_pair_time())
-    b.hsma_batch_set_overlap(True)
-
-    # dominant kernel alone: evaluations per launch / event-timed launch duration
-    ev_per_launch = sum(evals(s) for s in systems)
-    t_pair = statistics.mean(pair_ms) / 1e3
+    # dominant kernel alone: algorithmic pairs per launch (N (2N - 1 + 3M) per cavity) / the
+    # event-timed launch duration
+    t_pair, nrep = pair_kernel_alone(b, step, flush, max(20, min(200, args.steps)))
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = sms * SM_MUFU_PER_CLK * sm_max * 1e6
-    achieved = ev_per_launch / t_pair
+    achieved = units / t_pair
+    ev_per_launch = sum(evals(s) for s in systems)
     csrc = os.path.join(ROOT, "paper_1907_01724_gb300", "csrc")
-    traffic = profiled_traffic([os.path.join(csrc, f) for f in ("k_pairs.cu", "k_pairs_f32.cuh", "pair_work.cuh")],
-                               os.path.join(ROOT, "profiles", "k_pairs_f32_N2000x2.md"))
+    traffic = profiled_traffic([os.path.join(csrc, f) for f in ("k_pairs.cu", "k_pairs_f32.cuh", "pair_work.cuh", "fp32_pair.cuh")],
+                               os.path.join(ROOT, "profiles", "k_pairs_f32_N20000_M2000_p30.md"))
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-eval/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
             "kernel": "k_pairs_f32",
+            "work_unit": "pairs N(2N-1+3M) per cavity per launch (a surface point's monopole and two dipole "
+                         "charges count 3)",
             "peak_basis": f"{sms} SMs x {SM_MUFU_PER_CLK} MUFU rsqrt/clk x {sm_max:.0f} MHz (max SM clock)",
+            "frac_kernel_evals": ev_per_launch / t_pair / peak,
+            "kernel_evals_note": "N(2N-1+M) evaluations per cavity: one rsqrt per pair, a surface point's "
+                                 "monopole and dipole share one",
             "pair_kernel_ms": t_pair * 1e3, "pair_config": batch.pair_configs()[cfg],
-            "evals_per_launch": ev_per_launch,
-            "timing": f"{len(pair_ms)} launches in separate passes (L2 flushed before each step), CUDA events "
+            "pairs_per_launch": units,
+            "timing": f"{nrep} launches in separate passes (L2 flushed before each step), CUDA events "
                       "on the launch stream; in the timed steps the kernel runs overlapped with the "
                       "coefficient chain"}
     if clk.get("sm_mhz"):
@@ -478,58 +624,36 @@ def run_ours(args):
     # plain FP64 path on the same GPU (comparator)
     b64 = batch.from_systems(systems, precision=api.HSMA_FP64, device=local, stream=stream)
     b64.hsma_batch_build_sources(n, xyz, q)
-    step(b64)
-    torch.cuda.synchronize()
-    k64 = max(3, min(30, args.steps // 50))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(k64):
-        step(b64)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t64 = e0.elapsed_time(e1) / 1e3
-    fp64 = {"value": sum(pairs(s) for s in systems) * k64 / t64, "unit": "pair-evals/s",
-            "ms_per_step": t64 / k64 * 1e3, "steps": k64}
 
-    # end to end through the C ABI with pinned host buffers: H2D of inputs, D2H of potentials
-    # and energies inside the timed region
-    xyz_h = torch.tensor(xyz).pin_memory().numpy()
-    q_h = torch.tensor(q).pin_memory().numpy()
+    def step64():
+        b64.hsma_batch_build_sources(n, xyz_d, q_d)
+        b64.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
 
-    def e2e_step():
-        b.hsma_batch_build_sources(n, xyz_h, q_h)
-        b.hsma_batch_potential(api.HSMA_TOTAL)
-        b.hsma_batch_energy()
-
-    for _ in range(3):
-        e2e_step()
-    ke = max(10, args.steps // 4)
-    barrier(world)
+    step64()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(ke):
-        e2e_step()
-    torch.cuda.synchronize()
-    te = allreduce(world, time.perf_counter() - t0, "max")
-    e2e = {"value": allreduce(world, float(sum(pairs(s) for s in systems) * ke), "sum") / te,
-           "unit": "pair-evals/s", "h2d_bytes_per_step": int(32 * n.sum()),
-           "d2h_bytes_per_step": int(8 * n.sum() + 16 * len(systems)), "steps": ke,
-           "ms_per_step": te / ke * 1e3}
+    k64 = 3
+    t64 = timed_steps(step64, stream, flush, k64)
+    fp64 = {"value": units * k64 / t64, "unit": "pair-evals/s", "ms_per_step": t64 / k64 * 1e3, "steps": k64}
+    del b64
 
-    batched = serving = fieldres = None
+    e2e = e2e_run(b, n, xyz, q, units, world, max(10, args.steps))
+
+    near = batched = serving = fieldres = None
     if rank == 0 and world == 1 and not args.no_extras:
-        fieldres = run_field(local, stream, systems, gpu_name)
+        near = run_near_interface(local, stream, gpu_name, args.steps)
+        fieldres = run_field(local, stream, near_interface_workload(0), gpu_name)
         batched = run_batched(local, stream, gpu_name)
         serving = run_serving(local)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair sums (f64 coefficients/reduction)",
-                "data": "synthetic (seeded random charges in the ball, 25% near the interface)",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
+                "data": "synthetic (seeded random charges uniform in the ball)",
                 "config": config_dict(systems, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches), "accuracy_vs_oracle": acc, "fp64_path": fp64,
-                "field": fieldres, "batched": batched, "serving": serving, "impl": "ours"}
+                "near_interface": near, "field": fieldres, "batched": batched, "serving": serving,
+                "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -543,27 +667,33 @@ def run_reference(args):
         return
     import oracle
     systems = workload(0)
+    th, mask = affinity()
+
+    def one_step():
+        for s in systems:
+            P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau,
+                                   nthreads=th)
+            oracle.hsma(P, s.xyz, s.q)
+
     # warm-up: one full pass (also measures the cost of a step)
     t0 = time.perf_counter()
-    for s in systems:
-        P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
-        oracle.hsma(P, s.xyz, s.q)
+    one_step()
     t_step = time.perf_counter() - t0
     k = int(max(1, min(args.steps, math.ceil(60.0 / max(t_step, 1e-3)))))
     t0 = time.perf_counter()
     for _ in range(k):
-        for s in systems:
-            P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
-            oracle.hsma(P, s.xyz, s.q)
+        one_step()
     el = time.perf_counter() - t0
     value = sum(pairs(s) for s in systems) * k / el
     line = {"metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": k,
             "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": el / k * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded random charges in the ball, 25% near the interface)",
+            "data": "synthetic (seeded random charges uniform in the ball)",
             "config": config_dict(systems, 1), "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": "pair-evals/s", "kind": "oracle", "cores": oracle.threads(),
-                             "sample": f"full workload (both cavities) x{k} steps, bounded to about 60 s"},
+            "cpu_baseline": {"value": value, "unit": "pair-evals/s", "kind": "oracle", "cores": th,
+                             "affinity": {"cores": th, "mask": mask},
+                             "sample": f"whole workload (build + potentials + energies) x{k} steps, "
+                                       "bounded to about 60 s"},
             "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -571,12 +701,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sections")
-    ap.add_argument("--only", choices=["batched", "serving", "field"], help="run one extra section alone (profiling)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the near-interface, field, batched and "
+                                                             "serving sections")
+    ap.add_argument("--only", choices=["batched", "serving", "field", "near", "pairs"],
+                    help="run one section alone (profiling); 'pairs': the headline workload's pair kernel "
+                         "in separate passes (--steps launches)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.only:
@@ -584,10 +717,15 @@ def main():
         torch.cuda.set_device(0)
         st = torch.cuda.Stream()
         torch.cuda.set_stream(st)
+        name = torch.cuda.get_device_name(0)
         if args.only == "batched":
-            out = run_batched(0, st, torch.cuda.get_device_name(0))
+            out = run_batched(0, st, name)
         elif args.only == "field":
-            out = run_field(0, st, workload(0), torch.cuda.get_device_name(0))
+            out = run_field(0, st, near_interface_workload(0), name)
+        elif args.only == "near":
+            out = run_near_interface(0, st, name, args.steps)
+        elif args.only == "pairs":
+            out = run_pairs_only(0, st, name, args.steps, args.warmup)
         else:
             out = run_serving(0)
         print(json.dumps(out), flush=True)
@@ -595,6 +733,32 @@ def main():
         run_reference(args)
     else:
         run_ours(args)
+
+
+def run_pairs_only(local, stream, gpu_name, steps, warmup):
+    """The headline workload with the build and the pair sum in separate passes: warmup + steps
+    potential passes (for profiling the pair kernel; the launch list shows one k_pairs_f32 per
+    pass)."""
+    import torch
+
+    from paper_1907_01724_gb300 import api, batch
+    systems = workload(0)
+    n, xyz, q = batch.concat(systems)
+    b = batch.from_systems(systems, precision=api.HSMA_FP32, device=local, stream=stream)
+    cfg = batch.autotuned(b, n, xyz, q, gpu=gpu_name, reps=5)
+    b.hsma_batch_set_overlap(False)
+    xyz_d = torch.tensor(xyz, device=f"cuda:{local}")
+    q_d = torch.tensor(q, device=f"cuda:{local}")
+    phi_d = torch.empty(int(n.sum()), dtype=torch.float64, device=f"cuda:{local}")
+    ms = []
+    for i in range(warmup + steps):
+        b.hsma_batch_build_sources(n, xyz_d, q_d)
+        b.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
+        if i >= warmup:
+            ms.append(b.hsma_batch_last_pair_time())
+    torch.cuda.synchronize()
+    return {"workload": config_dict(systems, 1)["workload"], "pair_config": batch.pair_configs()[cfg],
+            "pair_kernel_ms_mean": statistics.mean(ms) if ms else None, "launches": len(ms)}
 
 
 if __name__ == "__main__":
