@@ -26,3 +26,19 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    # pointwise errors of the parity checks, reported beside the norm-wise bar they passed
+    try:
+        from pointwise import RECORDS
+    except Exception:
+        return
+    if not RECORDS:
+        return
+    tr = terminalreporter
+    tr.section("pointwise potential errors of the parity checks (norm-wise is the asserted bar)")
+    for r in RECORDS:
+        tr.write_line(f"{r['case']:<48s} n={r['n']:<6d} normwise={r['normwise']:.2e} "
+                      f"pointwise_rel_max={r['pointwise_rel_max']:.2e} "
+                      f"pointwise_abs/max|phi|={r['pointwise_abs_over_max']:.2e}")

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from paper_1907_01724_gb300 import api, batch, inputs
+from pointwise import record_pointwise
 
 pytestmark = pytest.mark.gpu
 
@@ -32,6 +33,10 @@ def check(s, prec, ref=None, tol=None, **kw):
     r = api.solve(s, precision=prec, **kw)
     e_phi = rel(r.phi, ref["phi"])
     e_rf = rel(r.phi_rf, ref["phi_rf"])
+    # the pointwise errors are reported beside the norm-wise ones (the pointwise relative error is
+    # ill-conditioned where a potential nearly cancels, so it is recorded, not asserted)
+    record_pointwise(f"{s.name or 'N%d' % s.n} {'fp32' if prec == api.HSMA_FP32 else 'fp64'}", prec, r.phi,
+                     ref["phi"], e_phi)
     scale_t = max(abs(ref["E_total"]), 0.5 * np.sum(np.abs(s.q * ref["phi"])), 1e-300)
     scale_r = max(abs(ref["E_rf"]), 0.5 * np.sum(np.abs(s.q * ref["phi_rf"])), 1e-300)
     e_E = abs(r.E_total - ref["E_total"]) / scale_t
