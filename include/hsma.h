@@ -49,8 +49,10 @@ extern "C" {
 #define HSMA_E_NONFINITE (-8)     /* non-finite potential (e.g. coincident charges) */
 
 /* precision of the pair sums */
-#define HSMA_FP32 0   /* FP32 pair sums (hi/lo split coordinates, compensated accumulation);
-                         FP64 coefficient, surface and reduction steps */
+#define HSMA_FP32 0   /* FP32 pair sums (hi/lo split coordinates near, compensated partials);
+                         moments, coefficients, surface synthesis and reductions in
+                         double-float arithmetic (FP32 pairs, ~2^-46 relative); record
+                         geometry in FP64 */
 #define HSMA_FP64 1   /* FP64 everywhere */
 
 /* which potential hsma_potential returns */
@@ -312,9 +314,9 @@ HSMA_API int hsma_server_positions(hsma_server_t* s, int c, double* xyz_out, int
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free Coulomb sum.  The paper has no counterpart: this is a service for callers
- * that may not allocate device memory (code running while a larger application captures a
- * CUDA graph, allocator or memory-pool callbacks, real-time loops with a fixed memory
- * budget).  It computes phi[i] = k_over_eps1 * sum_{j != i} q[j] / |x_i - x_j| for n charges
+ * that may not allocate device memory (code inside allocator or memory-pool callbacks, where
+ * an allocation would re-enter the allocator; plugins whose host application owns and
+ * accounts for all device memory; real-time loops with a fixed memory budget).  It computes phi[i] = k_over_eps1 * sum_{j != i} q[j] / |x_i - x_j| for n charges
  * with the library's FP32 tiled pair sum (hi/lo split coordinates, compensated partials;
  * the same numbers as hsma_potential(..., HSMA_COULOMB) up to the FP32 tolerance).
  *   xyz_dev (n,3), q_dev (n): device inputs; phi_dev (n): device output; stream: a
@@ -324,8 +326,12 @@ HSMA_API int hsma_server_positions(hsma_server_t* s, int c, double* xyz_out, int
  * partial sums and counters) is a static device array that every GPU loading the library
  * keeps until the process exits.  The first call on a device looks up that array's address
  * (cudaGetSymbolAddress, with the device current): make that first call before any stream
- * capture.  All calls share the array: calls that may overlap on the GPU (different streams
- * without ordering, or several host threads) race and must be serialised by the caller. */
+ * capture.  The address is kept for the life of the process and does not survive
+ * cudaDeviceReset (do not call this entry point again after a reset).  All calls share the
+ * array, which keeps the last call's contents (the call clears its completion counters
+ * itself): calls that may overlap on the GPU (different streams without ordering, or several
+ * host threads) race and must be serialised by the caller.  A CUDA error left pending by
+ * earlier work is returned as HSMA_E_CUDA before anything is launched, and left pending. */
 #define HSMA_NOALLOC_MAX_N 32768
 HSMA_API int hsma_coulomb_potential_noalloc(int64_t n, const double* xyz_dev, const double* q_dev,
                                             double k_over_eps1, double* phi_dev, void* stream);

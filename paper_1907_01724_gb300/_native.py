@@ -20,7 +20,7 @@ INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_HERE, "_build")
 LIB = os.path.join(BUILD, "libhsma.so")
 SOURCES = ["k_order.cu", "k_sources.cu", "k_pairs.cu", "k_reduce.cu", "k_field.cu", "k_delta.cu", "engine.cu", "batch.cu", "server.cu", "noalloc.cu"]
-HEADERS = ["hsma_internal.cuh", "engine.h", "df64.cuh", "k_pairs_f32.cuh", "pair_work.cuh"]
+HEADERS = ["hsma_internal.cuh", "engine.h", "df64.cuh", "k_pairs_f32.cuh", "pair_work.cuh", "fp32_pair.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 LINK_FLAGS = ["-Xlinker", "--exclude-libs,ALL", "-Xcompiler", "-fPIC"]

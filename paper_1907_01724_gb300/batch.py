@@ -207,16 +207,22 @@ class TuneCache:
             self.data = {}
 
     @staticmethod
-    def key(n, gpu: str) -> str:
+    def key(n, gpu: str, params=None) -> str:
+        """Size class (number of systems, log2 of the total charge count) and everything else that
+        changes the pair work of a step: the truncation order, the quadrature (M, F1, F2), the
+        precision, and the library's set of tile configurations."""
         tot = int(np.sum(n))
         ncfg = _native.load().hsma_pair_config_count()
-        return f"{gpu}|ncfg={ncfg}|step|nsys={len(n)}|log2N={max(tot, 1).bit_length()}"
+        k = f"{gpu}|ncfg={ncfg}|step|nsys={len(n)}|log2N={max(tot, 1).bit_length()}"
+        if params is not None:
+            k += f"|p={params.p}|M={params.M}|F={params.F1},{params.F2}|prec={params.precision}"
+        return k
 
-    def get(self, n, gpu: str):
-        return self.data.get(self.key(n, gpu))
+    def get(self, n, gpu: str, params=None):
+        return self.data.get(self.key(n, gpu, params))
 
-    def put(self, n, gpu: str, cfg: int, ms: float):
-        self.data[self.key(n, gpu)] = {"cfg": int(cfg), "ms": float(ms)}
+    def put(self, n, gpu: str, cfg: int, ms: float, params=None):
+        self.data[self.key(n, gpu, params)] = {"cfg": int(cfg), "ms": float(ms)}
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         tmp = self.path + f".{os.getpid()}"
         with open(tmp, "w") as f:
@@ -227,7 +233,7 @@ class TuneCache:
 def autotuned(batch: Batch, n, xyz, q, gpu: str = "", reps: int = 5, cache: TuneCache | None = None) -> int:
     """Build, then use the cached tile configuration for this size class or autotune and cache it."""
     cache = cache or TuneCache()
-    hit = cache.get(n, gpu)
+    hit = cache.get(n, gpu, batch.params)
     if hit is not None:
         batch.hsma_batch_set_pair_config(hit["cfg"])
         batch.hsma_batch_build_sources(n, xyz, q)
@@ -236,5 +242,5 @@ def autotuned(batch: Batch, n, xyz, q, gpu: str = "", reps: int = 5, cache: Tune
     cfg, ms = batch.hsma_batch_autotune(reps)
     batch.hsma_batch_set_pair_config(cfg)
     batch.hsma_batch_build_sources(n, xyz, q)
-    cache.put(n, gpu, cfg, ms)
+    cache.put(n, gpu, cfg, ms, batch.params)
     return cfg

@@ -1107,7 +1107,6 @@ int Engine::decode_status(int st)
       sources_ready = false;
       return fail(HSMA_E_OUTSIDE, "a charge lies outside the cavity (|x| >= a) or is not finite");
     }
-    if (st & kStTimeout) return fail(HSMA_E_TIMEOUT, "a bounded device wait gave up");
     if (st & kStBadMove) return fail(HSMA_E_OUTSIDE, "moved charge outside the cavity");
     if (st & kStNonFinite)
       return fail(HSMA_E_NONFINITE, "non-finite potential (coincident charges?)");

@@ -27,11 +27,11 @@ __host__ __device__ __forceinline__ dbl4 make_dbl4(double x, double y, double z,
   return r;
 }
 
-// Status bits written by kernels (the host maps them to HSMA_E_* codes).
+// Status bits written by kernels (the host maps them to HSMA_E_* codes).  No kernel of the
+// library waits on another CTA or on the host, so none has a timeout status.
 enum : int {
   kStOutside = 1,    // a charge at |x| >= a or with a non-finite coordinate
   kStNonFinite = 2,  // a non-finite potential
-  kStTimeout = 4,    // a bounded device wait gave up
   kStBadMove = 8,    // delta-energy move target outside the cavity
 };
 

@@ -20,36 +20,13 @@
 #include <math.h>
 
 #include "df64.cuh"
+#include "fp32_pair.cuh"
 #include "hsma_internal.cuh"
 
 namespace hsma {
 
 constexpr int kDeltaThreads = kDeltaBlock;
 
-__device__ __forceinline__ float rsqrt_f(float x)
-{
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ void split2d(double x, float& hi, float& lo)
-{
-  hi = __double2float_rn(x);
-  lo = __double2float_rn(x - (double)hi);
-}
-
-// hi/lo distance^-1 between two split points (see k_pairs.cu)
-__device__ __forceinline__ float inv_hilo(float ax, float ay, float az, float alx, float aly, float alz, float bx,
-                                          float by, float bz, float blx, float bly, float blz)
-{
-  const float dx = ax - bx, dy = ay - by, dz = az - bz;
-  const float ex = (alx - blx) + dx, ey = (aly - bly) + dy, ez = (alz - blz) + dz;
-  float r2 = ex * ex;
-  r2 = fmaf(ey, ey, r2);
-  r2 = fmaf(ez, ez, r2);
-  return rsqrt_f(r2);
-}
 
 // Kelvin image of a charge (position x, charge q): position, strength k q_K/eps1, or the centre
 // constant when |x| <= kCentreRel a.  Same separately rounded operations as k_images_moments.
@@ -274,8 +251,8 @@ __global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restric
         acc += 0.5 * qj * (img_pot(In, rj.x, rj.y, rj.z) - img_pot(Io, rj.x, rj.y, rj.z));
       } else {
         float nh[3], nl[3], oh[3], ol[3];
-        split2d(xn, nh[0], nl[0]); split2d(yn, nh[1], nl[1]); split2d(zn, nh[2], nl[2]);
-        split2d(xo, oh[0], ol[0]); split2d(yo, oh[1], ol[1]); split2d(zo, oh[2], ol[2]);
+        split_hilo(xn, nh[0], nl[0]); split_hilo(yn, nh[1], nl[1]); split_hilo(zn, nh[2], nl[2]);
+        split_hilo(xo, oh[0], ol[0]); split_hilo(yo, oh[1], ol[1]); split_hilo(zo, oh[2], ol[2]);
         const float4 rh = src_hi[S.src + j], rl = src_lo[S.src + j];
         const float4 kh = src_hi[S.src + S.n + j], kl = src_lo[S.src + S.n + j];
         float t = rh.w * (inv_hilo(nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], rh.x, rh.y, rh.z, rl.x, rl.y, rl.z) -
@@ -290,14 +267,14 @@ __global__ __launch_bounds__(kDeltaThreads) void k_delta(const SysDev* __restric
         if (In.centre) {
           pn = In.C;
         } else {
-          split2d(In.x, ih[0], il[0]); split2d(In.y, ih[1], il[1]); split2d(In.z, ih[2], il[2]);
+          split_hilo(In.x, ih[0], il[0]); split_hilo(In.y, ih[1], il[1]); split_hilo(In.z, ih[2], il[2]);
           jh[0] = rh.x; jh[1] = rh.y; jh[2] = rh.z; jl[0] = rl.x; jl[1] = rl.y; jl[2] = rl.z;
           pn = In.Q * (double)inv_hilo(jh[0], jh[1], jh[2], jl[0], jl[1], jl[2], ih[0], ih[1], ih[2], il[0], il[1], il[2]);
         }
         if (Io.centre) {
           po = Io.C;
         } else {
-          split2d(Io.x, ih[0], il[0]); split2d(Io.y, ih[1], il[1]); split2d(Io.z, ih[2], il[2]);
+          split_hilo(Io.x, ih[0], il[0]); split_hilo(Io.y, ih[1], il[1]); split_hilo(Io.z, ih[2], il[2]);
           po = Io.Q * (double)inv_hilo(rh.x, rh.y, rh.z, rl.x, rl.y, rl.z, ih[0], ih[1], ih[2], il[0], il[1], il[2]);
         }
         acc += 0.5 * qj * (pn - po);
@@ -538,12 +515,12 @@ __global__ __launch_bounds__(256) void k_move_charge(const SysDev* __restrict__ 
       src64[sk] = make_dbl4(In.x, In.y, In.z, In.Q);
     } else {
       float hx, hy, hz, lx, ly, lz;
-      split2d(R.x, hx, lx); split2d(R.y, hy, ly); split2d(R.z, hz, lz);
+      split_hilo(R.x, hx, lx); split_hilo(R.y, hy, ly); split_hilo(R.z, hz, lz);
       src_hi[sr] = make_float4(hx, hy, hz, (float)(S.kc * qk));
       src_lo[sr] = make_float4(lx, ly, lz, 0.f);
       const long long b = S.bb + ks / kBox, bk = b + (S.n + kBox - 1) / kBox;
       box_grow(boxes + 2 * b, hx, hy, hz);
-      split2d(In.x, hx, lx); split2d(In.y, hy, ly); split2d(In.z, hz, lz);
+      split_hilo(In.x, hx, lx); split_hilo(In.y, hy, ly); split_hilo(In.z, hz, lz);
       src_hi[sk] = make_float4(hx, hy, hz, (float)In.Q);
       src_lo[sk] = make_float4(lx, ly, lz, 0.f);
       box_grow(boxes + 2 * bk, hx, hy, hz);

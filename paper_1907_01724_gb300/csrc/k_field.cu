@@ -17,28 +17,11 @@
 #include <math.h>
 
 #include "df64.cuh"
+#include "fp32_pair.cuh"
 #include "hsma_internal.cuh"
 
 namespace hsma {
 
-__device__ __forceinline__ float rsqrt_sfu(float x)
-{
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ void cp_async16_f(void* smem, const void* gmem)
-{
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_f() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_f()
-{
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 struct FChunk {
   int type;       // 0 real, 1 Kelvin, 2 surface
@@ -117,10 +100,10 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
     const long long box_kind = S.bb + (ch.type == 1 ? (n + kBox - 1) / kBox : 0);
 
     if (tid < ch.count) {
-      cp_async16_f(&shA[0][tid], gA + tid);
-      cp_async16_f(&shB[0][tid], gB + tid);
+      cp_async16(&shA[0][tid], gA + tid);
+      cp_async16(&shB[0][tid], gB + tid);
     }
-    cp_async_commit_f();
+    cp_async_commit();
 
     float txh[K], tyh[K], tzh[K], txl[K], tyl[K], tzl[K];
     int tix[K];
@@ -157,13 +140,13 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
       if (t + 1 < ntiles) {
         const int s = (t + 1) * NT + tid;
         if (s < ch.count) {
-          cp_async16_f(&shA[buf ^ 1][tid], gA + s);
-          cp_async16_f(&shB[buf ^ 1][tid], gB + s);
+          cp_async16(&shA[buf ^ 1][tid], gA + s);
+          cp_async16(&shB[buf ^ 1][tid], gB + s);
         }
-        cp_async_commit_f();
-        cp_async_wait_f<1>();
+        cp_async_commit();
+        cp_async_wait<1>();
       } else {
-        cp_async_wait_f<0>();
+        cp_async_wait<0>();
       }
       __syncthreads();
       const int cnt = min(NT, ch.count - t * NT);
@@ -183,7 +166,7 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
             float r2 = dx * dx;
             r2 = fmaf(dy, dy, r2);
             r2 = fmaf(dz, dz, r2);
-            const float inv = rsqrt_sfu(r2);
+            const float inv = rsqrt_mufu(r2);
             const float inv2 = inv * inv;
             float dot = dx * y.x;
             dot = fmaf(dy, y.y, dot);
@@ -217,7 +200,7 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
                 float r2 = dx * dx;
                 r2 = fmaf(dy, dy, r2);
                 r2 = fmaf(dz, dz, r2);
-                const float inv = rsqrt_sfu(r2);
+                const float inv = rsqrt_mufu(r2);
                 const float qi = h.w * inv;
                 ap[k] += qi;
                 const float c = qi * (inv * inv);
@@ -238,7 +221,7 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
                 float r2 = ex * ex;
                 r2 = fmaf(ey, ey, r2);
                 r2 = fmaf(ez, ez, r2);
-                float inv = rsqrt_sfu(r2);
+                float inv = rsqrt_mufu(r2);
                 if (self) inv = (sbase + s == tix[k]) ? 0.f : inv;
                 const float qi = h.w * inv;
                 ap[k] += qi;

@@ -16,6 +16,7 @@
 //                  rank; cells hold a few charges), which gives perm and iperm; it leaves the
 //                  histogram zeroed for the next build (zeroed once when the workspace is laid out)
 // Two kernels and no memsets: the order is on the critical path of the overlapped step.
+#include "fp32_pair.cuh"
 #include "hsma_internal.cuh"
 
 namespace hsma {
@@ -37,12 +38,6 @@ __device__ __forceinline__ int cell_key(const SysDev& S, double x, double y, dou
   iy = min(max(iy, 0), kOrderGrid - 1);
   iz = min(max(iz, 0), kOrderGrid - 1);
   return (int)(spread3((unsigned)ix) | (spread3((unsigned)iy) << 1) | (spread3((unsigned)iz) << 2));
-}
-
-__device__ __forceinline__ float2 split_pair(double x)
-{
-  const float hi = __double2float_rn(x);
-  return make_float2(hi, __double2float_rn(x - (double)hi));
 }
 
 constexpr int kKeyThreads = 64;

@@ -24,28 +24,10 @@
 #include <math.h>
 
 #include "df64.cuh"
+#include "fp32_pair.cuh"
 #include "hsma_internal.cuh"
 
 namespace hsma {
-
-__device__ __forceinline__ float rsqrt_mufu(float x)
-{
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 struct ChunkInfo {
   int type;       // 0 real, 1 Kelvin, 2 surface

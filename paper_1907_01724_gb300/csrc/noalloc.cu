@@ -1,8 +1,9 @@
 // Coulomb part of the pair sum for callers that cannot allocate device memory.
 //
-// Some callers may not call cudaMalloc at all: code running while a larger application
-// captures a CUDA graph, inside a custom allocator or memory-pool callback, or in a real-time
-// loop whose memory budget is fixed up front.  For them this entry point computes
+// Some callers may not call cudaMalloc at all: code running inside a custom allocator or
+// memory-pool callback (a nested allocation would re-enter the allocator), a plugin whose host
+// application owns and accounts for all device memory, or a real-time loop whose memory budget
+// is fixed up front.  For them this entry point computes
 //   phi_i = k_over_eps1 * sum_{j != i} q_j / |x_i - x_j|
 // with the tiled FP32 pair-sum kernel of the library (hi/lo split coordinates, one MUFU rsqrt
 // per pair, compensated tile partials), but its scratch memory (the per-chunk partial sums and
@@ -12,6 +13,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "fp32_pair.cuh"
 #include "hsma_internal.cuh"
 
 namespace hsma {
@@ -32,18 +34,6 @@ struct __align__(256) NoAllocScratch {
 };
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-__device__ __forceinline__ float na_rsqrt(float x)
-{
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ void na_split(double x, float& hi, float& lo)
-{
-  hi = __double2float_rn(x);
-  lo = __double2float_rn(x - (double)hi);
-}
 
 // One block per (target block, source chunk).  The last block of a target block to finish
 // adds the chunk partials of its targets in chunk order (FP64) and writes phi.
@@ -64,9 +54,9 @@ __global__ __launch_bounds__(kNaThreads) void k_coulomb_noalloc(int n, const dou
     const int i = t0 + k * kNaThreads + tid;
     const int ii = i < n ? i : t0;
     ti[k] = i;
-    na_split(xyz[3 * (size_t)ii], th[k][0], tl[k][0]);
-    na_split(xyz[3 * (size_t)ii + 1], th[k][1], tl[k][1]);
-    na_split(xyz[3 * (size_t)ii + 2], th[k][2], tl[k][2]);
+    split_hilo(xyz[3 * (size_t)ii], th[k][0], tl[k][0]);
+    split_hilo(xyz[3 * (size_t)ii + 1], th[k][1], tl[k][1]);
+    split_hilo(xyz[3 * (size_t)ii + 2], th[k][2], tl[k][2]);
   }
   float H[kNaK], L[kNaK];
 #pragma unroll
@@ -77,9 +67,9 @@ __global__ __launch_bounds__(kNaThreads) void k_coulomb_noalloc(int n, const dou
     if (tid < cnt) {
       const size_t j = (size_t)(ts + tid);
       float hx, hy, hz, lx, ly, lz;
-      na_split(xyz[3 * j], hx, lx);
-      na_split(xyz[3 * j + 1], hy, ly);
-      na_split(xyz[3 * j + 2], hz, lz);
+      split_hilo(xyz[3 * j], hx, lx);
+      split_hilo(xyz[3 * j + 1], hy, ly);
+      split_hilo(xyz[3 * j + 2], hz, lz);
       sh[tid] = make_float4(hx, hy, hz, (float)(kfac * q[j]));
       sl[tid] = make_float4(lx, ly, lz, 0.f);
     }
@@ -96,7 +86,7 @@ __global__ __launch_bounds__(kNaThreads) void k_coulomb_noalloc(int n, const dou
         float r2 = ex * ex;
         r2 = fmaf(ey, ey, r2);
         r2 = fmaf(ez, ez, r2);
-        float inv = na_rsqrt(r2);
+        float inv = rsqrt_mufu(r2);
         inv = (ts + s == ti[k]) ? 0.f : inv;
         acc[k] = fmaf(h.w, inv, acc[k]);
       }
@@ -131,7 +121,9 @@ __global__ __launch_bounds__(kNaThreads) void k_coulomb_noalloc(int n, const dou
   }
 }
 
-// Device address of the scratch array, looked up once per device (with that device current).
+// Device address of the scratch array, looked up once per device (with that device current) and
+// kept for the life of the process: it does not survive cudaDeviceReset, after which this entry
+// point must not be called again in the same process.
 std::mutex g_na_mutex;
 void* g_na_addr[64] = {nullptr};
 
@@ -145,6 +137,9 @@ extern "C" int hsma_coulomb_potential_noalloc(int64_t n, const double* xyz_dev, 
   if (n < 0 || n > kNaMaxN) return HSMA_E_INVALID_ARG;
   if (n == 0) return HSMA_OK;
   if (!xyz_dev || !q_dev || !phi_dev || !std::isfinite(k_over_eps1)) return HSMA_E_INVALID_ARG;
+  // an error left pending by earlier, unrelated work is the caller's: it is reported as such and
+  // left in place (nothing is launched), so the checks below see only this call's own errors
+  if (cudaPeekAtLastError() != cudaSuccess) return HSMA_E_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     cudaGetLastError();
@@ -169,10 +164,10 @@ extern "C" int hsma_coulomb_potential_noalloc(int64_t n, const double* xyz_dev, 
   const int nchunks = (int)((n + kNaChunk - 1) / kNaChunk);
   // the completion counters must start at zero; the partials are overwritten before use
   if (cudaMemsetAsync(scr->done, 0, sizeof(unsigned int) * ntb, st) != cudaSuccess) {
-    cudaGetLastError();
+    cudaGetLastError();  // (this call's own error: none was pending on entry)
     return HSMA_E_CUDA;
   }
   k_coulomb_noalloc<<<ntb * nchunks, kNaThreads, 0, st>>>((int)n, xyz_dev, q_dev, k_over_eps1, phi_dev, scr);
-  if (cudaGetLastError() != cudaSuccess) return HSMA_E_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return HSMA_E_CUDA;  // the launch's own error
   return HSMA_OK;
 }
