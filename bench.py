@@ -613,7 +613,7 @@ def run_ours(args):
             "frac_kernel_evals": ev_per_launch / t_pair / peak,
             "kernel_evals_note": "N(2N-1+M) evaluations per cavity: one rsqrt per pair, a surface point's "
                                  "monopole and dipole share one",
-            "pair_kernel_ms": t_pair * 1e3, "pair_config": batch.pair_configs()[cfg],
+            "pair_kernel_ms": t_pair * 1e3, "pair_config": batch.pair_configs()[cfg], "pair_config_index": cfg,
             "pairs_per_launch": units,
             "timing": f"{nrep} launches in separate passes (L2 flushed before each step), CUDA events "
                       "on the launch stream; in the timed steps the kernel runs overlapped with the "
@@ -707,6 +707,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the near-interface, field, batched and "
                                                              "serving sections")
+    ap.add_argument("--pair-config", type=int, default=-1,
+                    help="with --only pairs: this tile configuration (index of batch.pair_configs()) instead "
+                         "of the autotuned one")
     ap.add_argument("--only", choices=["batched", "serving", "field", "near", "pairs"],
                     help="run one section alone (profiling); 'pairs': the headline workload's pair kernel "
                          "in separate passes (--steps launches)")
@@ -725,7 +728,7 @@ def main():
         elif args.only == "near":
             out = run_near_interface(0, st, name, args.steps)
         elif args.only == "pairs":
-            out = run_pairs_only(0, st, name, args.steps, args.warmup)
+            out = run_pairs_only(0, st, name, args.steps, args.warmup, args.pair_config)
         else:
             out = run_serving(0)
         print(json.dumps(out), flush=True)
@@ -735,7 +738,7 @@ def main():
         run_ours(args)
 
 
-def run_pairs_only(local, stream, gpu_name, steps, warmup):
+def run_pairs_only(local, stream, gpu_name, steps, warmup, pair_config=-1):
     """The headline workload with the build and the pair sum in separate passes: warmup + steps
     potential passes (for profiling the pair kernel; the launch list shows one k_pairs_f32 per
     pass)."""
@@ -745,7 +748,11 @@ def run_pairs_only(local, stream, gpu_name, steps, warmup):
     systems = workload(0)
     n, xyz, q = batch.concat(systems)
     b = batch.from_systems(systems, precision=api.HSMA_FP32, device=local, stream=stream)
-    cfg = batch.autotuned(b, n, xyz, q, gpu=gpu_name, reps=5)
+    if pair_config >= 0:
+        cfg = pair_config
+        b.hsma_batch_set_pair_config(cfg)
+    else:
+        cfg = batch.autotuned(b, n, xyz, q, gpu=gpu_name, reps=5)
     b.hsma_batch_set_overlap(False)
     xyz_d = torch.tensor(xyz, device=f"cuda:{local}")
     q_d = torch.tensor(q, device=f"cuda:{local}")
@@ -758,6 +765,7 @@ def run_pairs_only(local, stream, gpu_name, steps, warmup):
             ms.append(b.hsma_batch_last_pair_time())
     torch.cuda.synchronize()
     return {"workload": config_dict(systems, 1)["workload"], "pair_config": batch.pair_configs()[cfg],
+            "pair_config_index": cfg,
             "pair_kernel_ms_mean": statistics.mean(ms) if ms else None, "launches": len(ms)}
 
 
