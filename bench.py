@@ -500,16 +500,19 @@ def run_serving(local):
     srv.hsma_server_run(reqs)
     reqs, pos = server.make_trace(wl, 3000, None, pos)
     res = srv.hsma_server_run(reqs)
-    sat = server.latency_stats(res)
+    sat = server.latency_stats(res, reqs)
     out = {"workload": "64 chains, N log-uniform [500, 5e4] (sum %d), M=1000, p=20; 90%% single-move dE "
                        "(commit with p=0.5), 10%% full energies" % sum(c.n for c in wl.chains),
+           "driver": "hsma_server_run: the calling thread submits each request at its release time through "
+                     "hsma_server_submit and takes the answers through hsma_server_poll; the request loop "
+                     "runs on its own native thread",
            "saturation": sat, "loads": {}}
     for f in (0.25, 0.5, 0.8, 0.95):
         rate = f * sat["req_per_s"]
         nreq = int(min(20000, max(300, rate * 1.0)))
         reqs, pos = server.make_trace(wl, nreq, rate, pos)
         res = srv.hsma_server_run(reqs)
-        st = server.latency_stats(res)
+        st = server.latency_stats(res, reqs)
         st["offered_req_per_s"] = rate
         out["loads"][str(f)] = st
     # plain FP64 single-system path: the same kind of requests, one handle per chain, sequential

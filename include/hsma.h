@@ -44,7 +44,7 @@ extern "C" {
 #define HSMA_E_STATE (-3)         /* call out of order (e.g. potential before sources) */
 #define HSMA_E_OOM (-4)           /* device allocation failed or workspace too small */
 #define HSMA_E_CUDA (-5)          /* a CUDA runtime call failed */
-#define HSMA_E_TIMEOUT (-6)       /* a bounded device-side wait gave up */
+#define HSMA_E_TIMEOUT (-6)       /* a host-side wait reached its deadline (hsma_server_poll) */
 #define HSMA_E_BUSY (-7)          /* server queue full / no admission */
 #define HSMA_E_NONFINITE (-8)     /* non-finite potential (e.g. coincident charges) */
 
@@ -249,14 +249,20 @@ HSMA_API int hsma_batch_set_pair_config(hsma_batch_t* b, int cfg);
 HSMA_API int hsma_batch_autotune(hsma_batch_t* b, int reps, int* best, float* best_ms);
 
 /* ---------------------------------------------------------------------------------------
- * Serving: Monte Carlo chains (independent cavities) resident on the device, answering
- * single-charge-move energy changes and full energies as requests arrive.  The request loop
- * is native (host thread of the caller) and does continuous batching: released requests wait
- * in a FIFO per chain (one request of a chain in flight at a time, so a chain's results follow
- * its own order); every ready move request of every idle chain joins the next batched
- * Delta-E launch (high-priority stream; accepted moves are committed in the same launch
- * sequence), while full-energy requests run concurrently on low-priority streams with a pair
- * kernel limited to part of the GPU, so move batches keep running beside them.
+ * Serving: Monte Carlo chains (independent cavities) kept on the device, answering
+ * single-charge-move energy changes and full energies as requests arrive (the Monte Carlo
+ * use of the method, Sec. 1; the paper itself defines no serving loop).  The request loop is
+ * native: hsma_server_start runs it on a thread of its own; any thread then submits requests
+ * (hsma_server_submit) and takes answers (hsma_server_poll) while it runs; hsma_server_stop
+ * ends it.  Continuous batching: a chain has one request in flight at a time and its released
+ * requests wait in a FIFO (a chain's results follow its own order); every ready move request
+ * of every idle chain joins the next batched Delta-E launch (high-priority stream; accepted
+ * moves are committed in the same launch sequence), while full-energy requests run on
+ * low-priority streams as bounded chunks of pair work on a grid limited to part of the GPU,
+ * so move batches keep running between and beside them.  Admission by device footprint: a
+ * request for a chain that is not resident waits until that chain fits the budget once idle
+ * resident chains (least recently used first) are evicted; the resident set is then rebuilt
+ * from every chain's committed state at a point where no work is in flight.
  * --------------------------------------------------------------------------------------- */
 typedef struct hsma_server_t hsma_server_t;
 
@@ -264,7 +270,7 @@ typedef struct hsma_server_t hsma_server_t;
 #define HSMA_REQ_ENERGY 1  /* total energy of the chain's current configuration */
 
 typedef struct {
-  double t_arrival;  /* release time in seconds after the start of hsma_server_run */
+  double t_arrival;  /* hsma_server_run only: release time in seconds after the start of the run */
   int chain;         /* chain (system) index */
   int kind;          /* HSMA_REQ_DELTA or HSMA_REQ_ENERGY */
   int accept;        /* DELTA: commit the move after computing Delta E (the caller's MC decision) */
@@ -276,11 +282,13 @@ typedef struct {
 
 typedef struct {
   int64_t id;        /* the request's tag */
-  int status;        /* HSMA_OK, HSMA_E_BUSY (chain not admitted), HSMA_E_OUTSIDE, ... */
-  int pad;
+  int status;        /* HSMA_OK, HSMA_E_BUSY (chain closed, larger than the budget, or cancelled
+                        by hsma_server_stop(s, 0)), HSMA_E_OUTSIDE, HSMA_E_INVALID_ARG, ... */
+  int chain;         /* the request's chain */
   double value;      /* Delta E, or E_total */
-  double t_arrival;  /* release time (s, run clock) */
-  double t_done;     /* completion seen by the loop (s, run clock) */
+  double t_arrival;  /* submission time (s; hsma_server_run: the release time, run clock) */
+  double t_done;     /* completion seen by the loop (s, same clock) */
+  int64_t ticket;    /* the ticket hsma_server_submit returned (counted from 0 at each start) */
 } hsma_result;
 
 /* Create a server for nchains cavities (arrays as for hsma_batch_create; common params).
@@ -291,25 +299,52 @@ typedef struct {
 HSMA_API int hsma_server_create(int nchains, const double* a, const double* eps1, const double* eps2,
                                 const double* kappa, const hsma_params* params, size_t hbm_budget_bytes,
                                 int max_batch, int energy_slots, double energy_sm_frac, hsma_server_t** out);
+/* Destroy a server (stops a running loop first, cancelling what has not started). */
 HSMA_API void hsma_server_destroy(hsma_server_t* s);
 HSMA_API const char* hsma_server_last_error(const hsma_server_t* s);
 
 /* Initial charges of every chain: n[nchains], xyz (sum n, 3), q (sum n), host.  Chains are
  * admitted in index order while their device footprint fits the budget; their sources are
- * built on the device.  *admitted (nullable) receives the number of resident chains. */
+ * built on the device.  *admitted (nullable) receives the number of resident chains.
+ * HSMA_E_STATE while the loop runs. */
 HSMA_API int hsma_server_load(hsma_server_t* s, const int64_t* n, const double* xyz, const double* q,
                               int* admitted);
 
-/* Evict chain c (frees its share of the budget) and admit waiting chains that now fit,
- * rebuilding the resident set from the committed host-side state. */
+/* Close chain c for good (its later requests are answered HSMA_E_BUSY), free its share of the
+ * budget and admit waiting chains that now fit, in index order.  HSMA_E_STATE while the loop
+ * runs. */
 HSMA_API int hsma_server_close_chain(hsma_server_t* s, int c, int* admitted);
 
-/* Replay nreq requests (any order of t_arrival) in real time on the calling thread and
- * return when all are answered; results[r] answers reqs[r].  Requests of non-resident chains
- * are answered with HSMA_E_BUSY. */
+/* Start the request loop on a native thread (HSMA_E_STATE if it runs already or nothing is
+ * loaded).  From here until hsma_server_stop the loop alone issues the server's device work. */
+HSMA_API int hsma_server_start(hsma_server_t* s);
+
+/* Submit one request (thread-safe; any number of producer threads).  It is released at once:
+ * its submission time on the server clock becomes its arrival time.  *ticket (nullable)
+ * receives its ticket.  HSMA_E_BUSY: 65536 requests are submitted and not yet answered (try
+ * again after polling); HSMA_E_STATE: the loop is not running or is stopping; a loop that
+ * ended on a CUDA error returns that error.  Invalid requests are accepted here and answered
+ * with their error status. */
+HSMA_API int hsma_server_submit(hsma_server_t* s, const hsma_request* req, int64_t* ticket);
+
+/* Take up to max_results answers, in completion order, into out (thread-safe); *count receives
+ * how many.  timeout_s = 0: return at once; timeout_s > 0: wait up to that long for at least
+ * one answer and return HSMA_E_TIMEOUT if none came.  Answers stay available after
+ * hsma_server_stop until taken. */
+HSMA_API int hsma_server_poll(hsma_server_t* s, hsma_result* out, int max_results, double timeout_s, int* count);
+
+/* Stop the loop and join its thread.  drain = 1: every submitted request is answered first;
+ * drain = 0: requests that have not started are answered HSMA_E_BUSY, those in flight
+ * complete.  Returns HSMA_OK, or the CUDA error that ended the loop. */
+HSMA_API int hsma_server_stop(hsma_server_t* s, int drain);
+
+/* Replay nreq requests (any order of t_arrival) in real time: starts the loop, submits each
+ * request from the calling thread at its release time, polls the answers, stops the loop with
+ * drain = 1, and returns when all are answered; results[r] answers reqs[r].  HSMA_E_STATE if
+ * the loop is already running. */
 HSMA_API int hsma_server_run(hsma_server_t* s, int nreq, const hsma_request* reqs, hsma_result* results);
 
-/* Current positions of chain c (n_c x 3 doubles, host) after the committed moves. */
+/* Current positions of chain c (n_c x 3 doubles, host) after the committed moves (thread-safe). */
 HSMA_API int hsma_server_positions(hsma_server_t* s, int c, double* xyz_out, int64_t n);
 
 /* ---------------------------------------------------------------------------------------

@@ -168,6 +168,10 @@ def _declare(lib):
         "hsma_server_load": (ctypes.c_int, [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]),
         "hsma_server_close_chain": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "hsma_server_run": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "hsma_server_start": (ctypes.c_int, [vp]),
+        "hsma_server_submit": (ctypes.c_int, [vp, vp, ctypes.POINTER(i64)]),
+        "hsma_server_poll": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+        "hsma_server_stop": (ctypes.c_int, [vp, ctypes.c_int]),
         "hsma_server_positions": (ctypes.c_int, [vp, ctypes.c_int, vp, i64]),
     }
     for name, (res, args) in sigs.items():

@@ -1,24 +1,37 @@
 // Serving loop (include/hsma.h, hsma_server_*): Monte Carlo chains resident on the device,
 // continuous batching of single-charge-move energy changes, overlapped full energies.
 //
-// * Residency: one batched Engine holds every admitted chain; chains are admitted in index
-//   order while the sum of their device footprints fits the budget, and re-admitted from the
-//   host copy of their committed state when another chain is closed.
+// * Live boundary: hsma_server_start runs the request loop on a native thread of its own;
+//   producers call hsma_server_submit from any thread while it runs (a bounded inbound queue),
+//   consumers take answers with hsma_server_poll (a host-side deadline), and hsma_server_stop
+//   drains or cancels what is left.  hsma_server_run replays a request array through the same
+//   loop (submitting each request at its release time from the calling thread).
+// * Residency and admission: one batched Engine holds every resident chain.  A request for a
+//   chain that is not resident waits in its chain's queue; it is admitted as soon as its
+//   chain's device footprint fits the budget once idle resident chains (no request queued or
+//   in flight, least recently used first) are evicted; the resident set is then rebuilt, at a
+//   point where no work is in flight, from the host copy of every chain's committed state.  A
+//   chain whose footprint alone exceeds the budget is answered HSMA_E_BUSY.
 // * Ordering: a chain has at most one request in flight; its released requests wait in a
 //   FIFO, so its results follow its own order whatever the mix.
 // * Move requests: all ready move requests of idle chains form one batched k_delta launch on
 //   a high-priority stream, followed in the same stream by the commit (k_move_surface,
 //   k_move_charge) of the accepted ones; one such batch is in flight at a time.
-// * Energy requests: each runs on its own low-priority stream slot (pair kernel over that
-//   chain's items with a grid capped at a fraction of the GPU, then k_reduce), so move batches
-//   keep finding free SMs beside it.
+// * Energy requests: each runs on its own low-priority stream slot as a sequence of pair-kernel
+//   launches over bounded chunks of that chain's items (grids capped at a fraction of the GPU),
+//   then k_reduce; between the chunks the block scheduler hands the freed SMs to the
+//   high-priority move batches, so a large chain's energy does not hold the GPU for its whole
+//   duration.
 // * Completion is seen with cudaEventQuery; no device-side waits are involved.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "engine.h"
@@ -35,6 +48,18 @@ double now_s()
   return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
+// Pair work of one energy-request launch: items are split into chunks of about this many pair
+// evaluations (~50 us of the capped grid) and at least one item per CTA of the capped grid, so
+// that move batches get SMs between the launches of a large chain.
+constexpr double kEnergyChunkPairs = 1.5e8;
+
+// A request released to the loop: the caller's request, its ticket and submission time.
+struct Pending {
+  hsma_request q;
+  int64_t ticket;
+  double t_sub;  // server clock
+};
+
 struct EnergySlot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
@@ -49,7 +74,8 @@ struct EnergySlot {
   int* sel_h = nullptr;
   int2* selrng_h = nullptr;
   double* energy_h = nullptr;
-  int req = -1;
+  int live = 0;  // a request is in flight on this slot
+  Pending p;
   int chain = -1;
 };
 
@@ -81,6 +107,19 @@ struct hsma_server_t {
   std::vector<std::vector<int2>> it5_of;
   std::string err;
   bool loaded = false;
+  // live loop
+  std::thread th;
+  std::mutex mu;                       // inbox, outbox, counters, flags and pos
+  std::condition_variable cv_loop, cv_out;
+  std::deque<Pending> inbox;
+  std::deque<hsma_result> outbox;
+  int queue_cap = 1 << 16;             // submitted but not yet answered requests
+  int64_t next_ticket = 0, in_system = 0;
+  bool running = false, stop_req = false, drain = true;
+  int loop_rc = HSMA_OK;
+  double t0 = 0.0;                     // server clock origin (hsma_server_start)
+  std::vector<double> last_used;       // per chain, server clock (least recently used eviction)
+  std::vector<double> pairs_of;        // per resident system: pair evaluations of its item list
 };
 
 static int serr(hsma_server_t* s, int code, const std::string& msg)
@@ -171,6 +210,8 @@ static int rebuild(hsma_server_t* s)
   s->it5_of.assign(nsys, {});
   for (const auto& it : e->L.it4) s->it4_of[it.x].push_back(it);
   for (const auto& it : e->L.it5) s->it5_of[it.x].push_back(it);
+  s->pairs_of.assign(nsys, 0.0);
+  for (size_t k = 0; k < nsys; ++k) s->pairs_of[k] = (double)ns[k] * (2.0 * ns[k] + sp[k].M);
   int icap = 1, i5cap = 1;
   for (size_t k = 0; k < nsys; ++k) {
     icap = std::max(icap, (int)s->it4_of[k].size());
@@ -182,7 +223,7 @@ static int rebuild(hsma_server_t* s)
   s->it5_cap = i5cap;
   int lo = 0, hi = 0;
   SCK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-  SCK(cudaStreamCreateWithPriority(&s->sA, cudaStreamNonBlocking, hi));
+  if (!s->sA) SCK(cudaStreamCreateWithPriority(&s->sA, cudaStreamNonBlocking, hi));
   s->slots.resize(s->energy_slots);
   for (auto& sl : s->slots) {
     SCK(cudaStreamCreateWithPriority(&sl.st, cudaStreamNonBlocking, lo));
@@ -233,13 +274,13 @@ static int admit(hsma_server_t* s, int* admitted)
 }
 
 // --- batched move requests ----------------------------------------------------------------
-static int launch_moves(hsma_server_t* s, const std::vector<int>& ridx, const hsma_request* reqs)
+static int launch_moves(hsma_server_t* s, const std::vector<Pending>& batch)
 {
   Engine* e = s->e;
-  const int nr = (int)ridx.size();
+  const int nr = (int)batch.size();
   int ni = 0, nacc = 0, nmi = 0;
   for (int r = 0; r < nr; ++r) {
-    const hsma_request& q = reqs[ridx[r]];
+    const hsma_request& q = batch[r].q;
     DeltaReq d;
     d.sys = s->sys_of[q.chain];
     d.k = (int)q.k;
@@ -277,8 +318,9 @@ static int launch_moves(hsma_server_t* s, const std::vector<int>& ridx, const hs
     SCK(cudaGetLastError());
     e->launches += nmi > 0 ? 2 : 1;
     // committed state on the host
+    std::lock_guard<std::mutex> lk(s->mu);
     for (int r = 0; r < nr; ++r) {
-      const hsma_request& q = reqs[ridx[r]];
+      const hsma_request& q = batch[r].q;
       if (!q.accept) continue;
       auto& p = s->pos[q.chain];
       p[3 * q.k] = q.x[0];
@@ -290,6 +332,20 @@ static int launch_moves(hsma_server_t* s, const std::vector<int>& ridx, const hs
   e->pot_ready = false;
   SCK(cudaEventRecord(s->evA, s->sA));
   return HSMA_OK;
+}
+
+// Pair evaluations of one pair-sum item (targets x sources; a surface point counts once).
+static double item_pairs(const hsma::SysDev& d, const int4& it)
+{
+  const double nt = (double)std::min<int64_t>(d.tb, (int64_t)d.n - (int64_t)it.y * d.tb);
+  int64_t ns;
+  if (it.z < d.ncr)
+    ns = std::min<int64_t>(d.chunk, (int64_t)d.n - (int64_t)it.z * d.chunk);
+  else if (it.z < d.ncr + d.nck)
+    ns = std::min<int64_t>(d.chunk, (int64_t)d.n - (int64_t)(it.z - d.ncr) * d.chunk);
+  else
+    ns = std::min<int64_t>(d.chunk_s, (int64_t)d.M - (int64_t)(it.z - d.ncr - d.nck) * d.chunk_s);
+  return nt * (double)std::max<int64_t>(ns, 0);
 }
 
 // --- one full-energy request on a slot ------------------------------------------------------
@@ -307,19 +363,30 @@ static int launch_energy(hsma_server_t* s, EnergySlot& sl, int chain)
   SCK(cudaMemcpyAsync(sl.it5_d, sl.it5_h, sizeof(int2) * it5.size(), cudaMemcpyHostToDevice, sl.st));
   SCK(cudaMemcpyAsync(sl.sel_d, sl.sel_h, sizeof(int), cudaMemcpyHostToDevice, sl.st));
   SCK(cudaMemcpyAsync(sl.selrng_d, sl.selrng_h, sizeof(int2), cudaMemcpyHostToDevice, sl.st));
-  SCK(cudaMemsetAsync(sl.ctr_d, 0, sizeof(unsigned int), sl.st));
   if (!it4.empty()) {
     const int occ = e->prec == HSMA_FP64 ? e->occ_f64 : e->occ_f32[e->L.cfg];
     const int cap = std::max(1, (int)std::floor(s->sm_frac * e->num_sms * std::max(occ, 1)));
-    const int grid = std::max(1, std::min((int)it4.size(), cap));
-    const hsma::PairWork w{sl.items_d, (int)it4.size(), sl.ctr_d, std::min(grid, (int)it4.size())},
-        none{nullptr, 0, nullptr, 0};
-    if (e->prec == HSMA_FP64)
-      hsma::launch_pairs_f64(grid, e->sys_d, w, none, e->src64_d, e->surf64a_d, e->surf64b_d, e->part64_d, sl.st);
-    else
-      hsma::launch_pairs_f32(e->L.cfg, grid, e->sys_d, w, none, e->srchi_d, e->srclo_d, e->surfa_d, e->surfb_d,
-                             e->boxes_d, e->part_d, sl.st);
-    e->launches += 1;
+    // chunks of consecutive items (the list is longest first) of about kEnergyChunkPairs each,
+    // but never fewer items than the capped grid has CTAs (every launch fills its grid)
+    const hsma::SysDev& d = e->L.sd[sys];
+    int beg = 0;
+    while (beg < (int)it4.size()) {
+      int end = beg;
+      double w = 0.0;
+      while (end < (int)it4.size() && (end - beg < cap || w + item_pairs(d, it4[end]) <= kEnergyChunkPairs))
+        w += item_pairs(d, it4[end++]);
+      const int cnt = end - beg;
+      const int grid = std::max(1, std::min(cnt, cap));
+      SCK(cudaMemsetAsync(sl.ctr_d, 0, sizeof(unsigned int), sl.st));
+      const hsma::PairWork w1{sl.items_d + beg, cnt, sl.ctr_d, std::min(grid, cnt)}, none{nullptr, 0, nullptr, 0};
+      if (e->prec == HSMA_FP64)
+        hsma::launch_pairs_f64(grid, e->sys_d, w1, none, e->src64_d, e->surf64a_d, e->surf64b_d, e->part64_d, sl.st);
+      else
+        hsma::launch_pairs_f32(e->L.cfg, grid, e->sys_d, w1, none, e->srchi_d, e->srclo_d, e->surfa_d, e->surfb_d,
+                               e->boxes_d, e->part_d, sl.st);
+      e->launches += 1;
+      beg = end;
+    }
   }
   if (!it5.empty()) {
     hsma::launch_reduce(e->sys_d, sl.sel_d, sl.selrng_d, 1, sl.it5_d, (int)it5.size(), e->part_d, e->part64_d, e->prec,
@@ -331,6 +398,239 @@ static int launch_energy(hsma_server_t* s, EnergySlot& sl, int chain)
   SCK(cudaMemcpyAsync(sl.energy_h, e->energy_d + 2 * (size_t)sys, 16, cudaMemcpyDeviceToHost, sl.st));
   SCK(cudaEventRecord(sl.ev, sl.st));
   return HSMA_OK;
+}
+
+// --- the request loop -----------------------------------------------------------------------
+static void answer(hsma_server_t* s, const Pending& p, int status, double value)
+{
+  hsma_result r;
+  r.id = p.q.id;
+  r.status = status;
+  r.chain = p.q.chain;
+  r.value = value;
+  r.t_arrival = p.t_sub;
+  r.t_done = now_s() - s->t0;
+  r.ticket = p.ticket;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->outbox.push_back(r);
+    --s->in_system;
+  }
+  s->cv_out.notify_all();
+}
+
+// Validation of a released request: HSMA_OK or the status it is answered with.
+static int check_request(const hsma_server_t* s, const hsma_request& q)
+{
+  const int nc = (int)s->specs.size();
+  if (q.chain < 0 || q.chain >= nc) return HSMA_E_INVALID_ARG;
+  if (s->closed[q.chain]) return HSMA_E_BUSY;
+  if (q.kind == HSMA_REQ_DELTA) {
+    const double a = s->specs[q.chain].a;
+    const double r2 = q.x[0] * q.x[0] + q.x[1] * q.x[1] + q.x[2] * q.x[2];
+    if (q.k < 0 || q.k >= s->n[q.chain]) return HSMA_E_INVALID_ARG;
+    if (!(r2 < a * a) || !std::isfinite(r2)) return HSMA_E_OUTSIDE;
+  } else if (q.kind != HSMA_REQ_ENERGY) {
+    return HSMA_E_INVALID_ARG;
+  }
+  return HSMA_OK;
+}
+
+static int loop_body(hsma_server_t* s, std::vector<std::deque<Pending>>& fifo, std::vector<Pending>& batch)
+{
+  Engine* e = s->e;
+  SCK(cudaSetDevice(e->device));
+  const int nc = (int)s->specs.size();
+  std::vector<char> busy(nc, 0);
+  bool batch_live = false;
+  // admission waiting for the GPU to go idle: chains to evict and to admit
+  bool adm_pending = false;
+  std::vector<int> adm_out, adm_in;
+  std::vector<Pending> incoming;
+  for (;;) {
+    bool stop = false, drain = true;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      incoming.assign(s->inbox.begin(), s->inbox.end());
+      s->inbox.clear();
+      stop = s->stop_req;
+      drain = s->drain;
+    }
+    // release: validate, queue per chain
+    for (const Pending& p : incoming) {
+      const int st = check_request(s, p.q);
+      if (st != HSMA_OK)
+        answer(s, p, st, 0.0);
+      else
+        fifo[p.q.chain].push_back(p);
+    }
+    if (stop && !drain) {
+      // cancel what has not started
+      for (int c = 0; c < nc; ++c) {
+        for (const Pending& p : fifo[c]) answer(s, p, HSMA_E_BUSY, 0.0);
+        fifo[c].clear();
+      }
+    }
+    // completions
+    if (batch_live) {
+      const cudaError_t qe = cudaEventQuery(s->evA);
+      if (qe == cudaSuccess) {
+        for (size_t i = 0; i < batch.size(); ++i) {
+          busy[batch[i].q.chain] = 0;
+          answer(s, batch[i], HSMA_OK, s->de_h[i]);
+        }
+        batch.clear();
+        batch_live = false;
+      } else if (qe != cudaErrorNotReady) {
+        return scuda(s, qe, "move batch");
+      }
+    }
+    for (auto& sl : s->slots) {
+      if (!sl.live) continue;
+      const cudaError_t qe = cudaEventQuery(sl.ev);
+      if (qe == cudaSuccess) {
+        busy[sl.chain] = 0;
+        sl.live = 0;
+        sl.chain = -1;
+        answer(s, sl.p, HSMA_OK, sl.energy_h[0]);
+      } else if (qe != cudaErrorNotReady) {
+        return scuda(s, qe, "energy request");
+      }
+    }
+    int in_flight = batch_live ? 1 : 0;
+    for (auto& sl : s->slots) in_flight += sl.live;
+    // admission of chains with queued requests that are not resident
+    if (!adm_pending) {
+      size_t used = 0;
+      for (int c = 0; c < nc; ++c)
+        if (s->sys_of[c] >= 0) used += s->footprint[c];
+      for (int c = 0; c < nc && !adm_pending; ++c) {
+        if (fifo[c].empty() || s->sys_of[c] >= 0) continue;
+        if (s->budget > 0 && s->footprint[c] > s->budget) {
+          for (const Pending& p : fifo[c]) answer(s, p, HSMA_E_BUSY, 0.0);
+          fifo[c].clear();
+          continue;
+        }
+        std::vector<int> idle;
+        for (int v = 0; v < nc; ++v)
+          if (s->sys_of[v] >= 0 && !busy[v] && fifo[v].empty()) idle.push_back(v);
+        std::sort(idle.begin(), idle.end(), [&](int x, int y) { return s->last_used[x] < s->last_used[y]; });
+        size_t freed = 0;
+        std::vector<int> out;
+        for (int v : idle) {
+          if (s->budget == 0 || used - freed + s->footprint[c] <= s->budget) break;
+          out.push_back(v);
+          freed += s->footprint[v];
+        }
+        if (s->budget == 0 || used - freed + s->footprint[c] <= s->budget) {
+          adm_pending = true;
+          adm_out = out;
+          adm_in = {c};
+        }
+      }
+    }
+    if (adm_pending && in_flight == 0) {
+      for (int v : adm_out) s->sys_of[v] = -1;
+      for (int c : adm_in) s->sys_of[c] = 0;  // marked resident; rebuild assigns the index
+      adm_pending = false;
+      int rc = rebuild(s);
+      if (rc) return rc;
+    }
+    // issue (not while an admission waits for the GPU to go idle)
+    if (!adm_pending) {
+      if (!batch_live) {
+        for (int c = 0; c < nc && (int)batch.size() < s->max_batch; ++c) {
+          if (busy[c] || fifo[c].empty() || s->sys_of[c] < 0) continue;
+          const Pending& p = fifo[c].front();
+          if (p.q.kind != HSMA_REQ_DELTA) continue;
+          batch.push_back(p);
+          fifo[c].pop_front();
+          busy[c] = 1;
+          s->last_used[c] = now_s() - s->t0;
+        }
+        if (!batch.empty()) {
+          int rc = launch_moves(s, batch);
+          if (rc) return rc;
+          batch_live = true;
+        }
+      }
+      for (auto& sl : s->slots) {
+        if (sl.live) continue;
+        int bc = -1;
+        for (int c = 0; c < nc; ++c) {
+          if (busy[c] || fifo[c].empty() || s->sys_of[c] < 0) continue;
+          const Pending& p = fifo[c].front();
+          if (p.q.kind != HSMA_REQ_ENERGY) continue;
+          if (bc < 0 || p.t_sub < fifo[bc].front().t_sub) bc = c;
+        }
+        if (bc < 0) break;
+        sl.p = fifo[bc].front();
+        fifo[bc].pop_front();
+        busy[bc] = 1;
+        sl.live = 1;
+        sl.chain = bc;
+        s->last_used[bc] = now_s() - s->t0;
+        int rc = launch_energy(s, sl, bc);
+        if (rc) return rc;
+      }
+    }
+    in_flight = batch_live ? 1 : 0;
+    for (auto& sl : s->slots) in_flight += sl.live;
+    bool queued = false;
+    for (int c = 0; c < nc && !queued; ++c) queued = !fifo[c].empty();
+    if (stop && in_flight == 0 && !queued) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->inbox.empty()) break;
+      continue;
+    }
+    if (in_flight == 0 && !adm_pending) {
+      // idle: wait for a submission (or the stop request)
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_loop.wait_for(lk, std::chrono::milliseconds(2), [&] { return !s->inbox.empty() || s->stop_req; });
+    } else {
+      std::this_thread::yield();
+    }
+  }
+  // device status of the whole run (a non-finite potential, a bad move)
+  SCK(cudaDeviceSynchronize());
+  int st = 0;
+  SCK(cudaMemcpy(&st, e->status_d, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    cudaMemset(e->status_d, 0, sizeof(int));
+    return serr(s, (st & hsma::kStNonFinite) ? HSMA_E_NONFINITE : HSMA_E_OUTSIDE, "device status flagged");
+  }
+  return HSMA_OK;
+}
+
+static void loop_main(hsma_server_t* s)
+{
+  const int nc = (int)s->specs.size();
+  std::vector<std::deque<Pending>> fifo(nc);
+  std::vector<Pending> batch;
+  int rc = loop_body(s, fifo, batch);
+  if (rc) {
+    // a CUDA failure ends the loop: everything not answered gets its status
+    cudaDeviceSynchronize();
+    std::vector<Pending> left(batch.begin(), batch.end());
+    for (auto& sl : s->slots)
+      if (sl.live) {
+        left.push_back(sl.p);
+        sl.live = 0;
+      }
+    for (auto& f : fifo) left.insert(left.end(), f.begin(), f.end());
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      left.insert(left.end(), s->inbox.begin(), s->inbox.end());
+      s->inbox.clear();
+      s->loop_rc = rc;
+    }
+    for (const Pending& p : left) answer(s, p, rc, 0.0);
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!rc) s->loop_rc = HSMA_OK;
+  }
+  s->cv_out.notify_all();
 }
 
 extern "C" {
@@ -375,6 +675,7 @@ int hsma_server_create(int nchains, const double* a, const double* eps1, const d
 void hsma_server_destroy(hsma_server_t* s)
 {
   if (!s) return;
+  if (s->running) hsma_server_stop(s, 0);
   if (s->e) cudaSetDevice(s->e->device);
   cudaDeviceSynchronize();
   free_buffers(s);
@@ -389,7 +690,9 @@ const char* hsma_server_last_error(const hsma_server_t* s) { return s ? s->err.c
 int hsma_server_load(hsma_server_t* s, const int64_t* n, const double* xyz, const double* q, int* admitted)
 {
   if (!s || !n) return HSMA_E_INVALID_ARG;
+  if (s->running) return serr(s, HSMA_E_STATE, "the request loop is running");
   const size_t nc = s->specs.size();
+  s->last_used.assign(nc, 0.0);
   s->n.assign(n, n + nc);
   s->pos.assign(nc, {});
   s->chg.assign(nc, {});
@@ -423,6 +726,7 @@ int hsma_server_load(hsma_server_t* s, const int64_t* n, const double* xyz, cons
 int hsma_server_close_chain(hsma_server_t* s, int c, int* admitted)
 {
   if (!s || !s->loaded || c < 0 || c >= (int)s->specs.size()) return serr(s, HSMA_E_INVALID_ARG, "bad chain");
+  if (s->running) return serr(s, HSMA_E_STATE, "the request loop is running");
   cudaDeviceSynchronize();
   s->closed[c] = 1;
   return admit(s, admitted);
@@ -432,148 +736,150 @@ int hsma_server_positions(hsma_server_t* s, int c, double* xyz_out, int64_t n)
 {
   if (!s || !s->loaded || c < 0 || c >= (int)s->specs.size() || !xyz_out || n != s->n[c])
     return serr(s, HSMA_E_INVALID_ARG, "bad arguments");
+  std::lock_guard<std::mutex> lk(s->mu);
   std::copy(s->pos[c].begin(), s->pos[c].end(), xyz_out);
   return HSMA_OK;
+}
+
+int hsma_server_start(hsma_server_t* s)
+{
+  if (!s) return HSMA_E_INVALID_ARG;
+  if (!s->loaded) return serr(s, HSMA_E_STATE, "no chains loaded");
+  if (s->running) return serr(s, HSMA_E_STATE, "the request loop is already running");
+  SCK(cudaSetDevice(s->e->device));
+  SCK(cudaDeviceSynchronize());
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->inbox.clear();
+    s->outbox.clear();
+    s->in_system = 0;
+    s->stop_req = false;
+    s->drain = true;
+    s->loop_rc = HSMA_OK;
+    s->next_ticket = 0;
+    s->t0 = now_s();
+    s->running = true;
+  }
+  try {
+    s->th = std::thread(loop_main, s);
+  } catch (...) {
+    s->running = false;
+    return serr(s, HSMA_E_STATE, "could not start the request loop thread");
+  }
+  return HSMA_OK;
+}
+
+int hsma_server_submit(hsma_server_t* s, const hsma_request* req, int64_t* ticket)
+{
+  if (!s || !req) return HSMA_E_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->running || s->stop_req) return HSMA_E_STATE;
+    if (s->loop_rc != HSMA_OK) return s->loop_rc;
+    if (s->in_system >= s->queue_cap) return HSMA_E_BUSY;
+    Pending p;
+    p.q = *req;
+    p.ticket = s->next_ticket++;
+    p.t_sub = now_s() - s->t0;
+    s->inbox.push_back(p);
+    ++s->in_system;
+    if (ticket) *ticket = p.ticket;
+  }
+  s->cv_loop.notify_one();
+  return HSMA_OK;
+}
+
+int hsma_server_poll(hsma_server_t* s, hsma_result* out, int max_results, double timeout_s, int* count)
+{
+  if (!s || !count || max_results < 0 || (max_results > 0 && !out) || !(timeout_s >= 0.0))
+    return HSMA_E_INVALID_ARG;
+  *count = 0;
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->outbox.empty() && timeout_s > 0.0 && max_results > 0) {
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    s->cv_out.wait_until(lk, deadline, [&] { return !s->outbox.empty() || (!s->running && s->in_system == 0); });
+  }
+  int k = 0;
+  while (k < max_results && !s->outbox.empty()) {
+    out[k++] = s->outbox.front();
+    s->outbox.pop_front();
+  }
+  *count = k;
+  if (k == 0 && timeout_s > 0.0 && max_results > 0) return HSMA_E_TIMEOUT;
+  return HSMA_OK;
+}
+
+int hsma_server_stop(hsma_server_t* s, int drain)
+{
+  if (!s) return HSMA_E_INVALID_ARG;
+  if (!s->running) return serr(s, HSMA_E_STATE, "the request loop is not running");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop_req = true;
+    s->drain = drain != 0;
+  }
+  s->cv_loop.notify_all();
+  s->th.join();
+  int rc;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->running = false;
+    rc = s->loop_rc;
+  }
+  s->cv_out.notify_all();
+  return rc;
 }
 
 int hsma_server_run(hsma_server_t* s, int nreq, const hsma_request* reqs, hsma_result* results)
 {
   if (!s || nreq < 0 || (nreq > 0 && (!reqs || !results))) return serr(s, HSMA_E_INVALID_ARG, "bad arguments");
   if (!s->loaded) return serr(s, HSMA_E_STATE, "no chains loaded");
-  Engine* e = s->e;
-  SCK(cudaSetDevice(e->device));
-  SCK(cudaDeviceSynchronize());
-  const int nc = (int)s->specs.size();
+  if (s->running) return serr(s, HSMA_E_STATE, "the request loop is running");
+  int rc = hsma_server_start(s);
+  if (rc) return rc;
+  // release order; results[r] answers reqs[r] (found by ticket)
   std::vector<int> order(nreq);
   for (int r = 0; r < nreq; ++r) order[r] = r;
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return reqs[x].t_arrival < reqs[y].t_arrival; });
-  std::vector<std::deque<int>> fifo(nc);
-  std::vector<char> busy(nc, 0);
-  for (int r = 0; r < nreq; ++r) {
-    results[r].id = reqs[r].id;
-    results[r].status = HSMA_E_STATE;
-    results[r].value = 0.0;
-    results[r].t_arrival = reqs[r].t_arrival;
-    results[r].t_done = -1.0;
-  }
-  int next = 0, done = 0;
-  std::vector<int> batch;  // request indices in the move batch in flight
-  bool batch_live = false;
-  const double t0 = now_s();
-  while (done < nreq) {
-    const double t = now_s() - t0;
-    // release arrived requests
+  std::vector<int> of_ticket;
+  of_ticket.reserve(nreq);
+  const double run0 = now_s();
+  const double off = run0 - s->t0;  // run clock = server clock - off
+  int next = 0, got = 0;
+  std::vector<hsma_result> buf(256);
+  while (got < nreq) {
+    const double t = now_s() - run0;
     while (next < nreq && reqs[order[next]].t_arrival <= t) {
-      const int r = order[next++];
-      const hsma_request& q = reqs[r];
-      int st = HSMA_OK;
-      if (q.chain < 0 || q.chain >= nc)
-        st = HSMA_E_INVALID_ARG;
-      else if (s->sys_of[q.chain] < 0)
-        st = HSMA_E_BUSY;
-      else if (q.kind == HSMA_REQ_DELTA) {
-        const double a = s->specs[q.chain].a;
-        const double r2 = q.x[0] * q.x[0] + q.x[1] * q.x[1] + q.x[2] * q.x[2];
-        if (q.k < 0 || q.k >= s->n[q.chain]) st = HSMA_E_INVALID_ARG;
-        else if (!(r2 < a * a) || !std::isfinite(r2)) st = HSMA_E_OUTSIDE;
-      } else if (q.kind != HSMA_REQ_ENERGY) {
-        st = HSMA_E_INVALID_ARG;
+      int64_t ticket = -1;
+      const int sr = hsma_server_submit(s, &reqs[order[next]], &ticket);
+      if (sr == HSMA_E_BUSY) break;  // queue full: retry after answers arrive
+      if (sr) {
+        hsma_server_stop(s, 0);
+        return serr(s, sr, "submit failed");
       }
-      if (st != HSMA_OK) {
-        results[r].status = st;
-        results[r].t_done = now_s() - t0;
-        ++done;
-        continue;
-      }
-      fifo[q.chain].push_back(r);
+      of_ticket.push_back(order[next]);
+      ++next;
     }
-    bool progress = false;
-    // completions
-    if (batch_live) {
-      const cudaError_t qe = cudaEventQuery(s->evA);
-      if (qe == cudaSuccess) {
-        const double td = now_s() - t0;
-        for (size_t i = 0; i < batch.size(); ++i) {
-          const int r = batch[i];
-          results[r].status = HSMA_OK;
-          results[r].value = s->de_h[i];
-          results[r].t_done = td;
-          busy[reqs[r].chain] = 0;
-          ++done;
-        }
-        batch.clear();
-        batch_live = false;
-        progress = true;
-      } else if (qe != cudaErrorNotReady) {
-        return scuda(s, qe, "move batch");
-      }
+    // wait for answers until the next release is due
+    const double wait = next < nreq ? std::max(0.0, reqs[order[next]].t_arrival - (now_s() - run0)) : 0.05;
+    int cnt = 0;
+    const int pr = hsma_server_poll(s, buf.data(), (int)buf.size(), std::min(wait, 0.05), &cnt);
+    if (pr != HSMA_OK && pr != HSMA_E_TIMEOUT) {
+      hsma_server_stop(s, 0);
+      return serr(s, pr, "poll failed");
     }
-    for (auto& sl : s->slots) {
-      if (sl.req < 0) continue;
-      const cudaError_t qe = cudaEventQuery(sl.ev);
-      if (qe == cudaSuccess) {
-        results[sl.req].status = HSMA_OK;
-        results[sl.req].value = sl.energy_h[0];
-        results[sl.req].t_done = now_s() - t0;
-        busy[sl.chain] = 0;
-        ++done;
-        sl.req = -1;
-        sl.chain = -1;
-        progress = true;
-      } else if (qe != cudaErrorNotReady) {
-        return scuda(s, qe, "energy request");
-      }
+    if (wait <= 0.0 && cnt == 0) std::this_thread::yield();
+    for (int i = 0; i < cnt; ++i) {
+      const hsma_result& r = buf[i];
+      const int idx = of_ticket[(size_t)r.ticket];
+      results[idx] = r;
+      results[idx].t_arrival = reqs[idx].t_arrival;
+      results[idx].t_done = r.t_done - off;
+      ++got;
     }
-    // issue: one move batch of every idle chain whose next request is a move
-    if (!batch_live) {
-      for (int c = 0; c < nc && (int)batch.size() < s->max_batch; ++c) {
-        if (busy[c] || fifo[c].empty()) continue;
-        const int r = fifo[c].front();
-        if (reqs[r].kind != HSMA_REQ_DELTA) continue;
-        fifo[c].pop_front();
-        busy[c] = 1;
-        batch.push_back(r);
-      }
-      if (!batch.empty()) {
-        int rc = launch_moves(s, batch, reqs);
-        if (rc) return rc;
-        batch_live = true;
-        progress = true;
-      }
-    }
-    // issue: full energies into free slots (oldest first)
-    for (auto& sl : s->slots) {
-      if (sl.req >= 0) continue;
-      int best = -1, bc = -1;
-      for (int c = 0; c < nc; ++c) {
-        if (busy[c] || fifo[c].empty()) continue;
-        const int r = fifo[c].front();
-        if (reqs[r].kind != HSMA_REQ_ENERGY) continue;
-        if (best < 0 || reqs[r].t_arrival < reqs[best].t_arrival) {
-          best = r;
-          bc = c;
-        }
-      }
-      if (best < 0) break;
-      fifo[bc].pop_front();
-      busy[bc] = 1;
-      sl.req = best;
-      sl.chain = bc;
-      int rc = launch_energy(s, sl, bc);
-      if (rc) return rc;
-      progress = true;
-    }
-    (void)progress;
   }
-  SCK(cudaDeviceSynchronize());
-  int st = 0;
-  SCK(cudaMemcpy(&st, e->status_d, sizeof(int), cudaMemcpyDeviceToHost));
-  if (st) {
-    cudaMemset(e->status_d, 0, sizeof(int));
-    return serr(s, (st & hsma::kStNonFinite) ? HSMA_E_NONFINITE : HSMA_E_OUTSIDE, "device status flagged");
-  }
-  return HSMA_OK;
+  return hsma_server_stop(s, 1);
 }
 
 }  // extern "C"

@@ -15,9 +15,12 @@ REQ_ENERGY = 1
 
 REQUEST = np.dtype([("t_arrival", "f8"), ("chain", "i4"), ("kind", "i4"), ("accept", "i4"), ("pad", "i4"),
                     ("k", "i8"), ("x", "f8", 3), ("id", "i8")], align=True)
-RESULT = np.dtype([("id", "i8"), ("status", "i4"), ("pad", "i4"), ("value", "f8"), ("t_arrival", "f8"),
-                   ("t_done", "f8")], align=True)
-assert REQUEST.itemsize == 64 and RESULT.itemsize == 40
+RESULT = np.dtype([("id", "i8"), ("status", "i4"), ("chain", "i4"), ("value", "f8"), ("t_arrival", "f8"),
+                   ("t_done", "f8"), ("ticket", "i8")], align=True)
+assert REQUEST.itemsize == 64 and RESULT.itemsize == 48
+
+HSMA_E_TIMEOUT = -6
+HSMA_E_BUSY = -7
 
 
 _p = _native.host_ptr
@@ -73,6 +76,32 @@ class Server:
         self._check(self.lib.hsma_server_run(self.ptr, len(reqs), _p(reqs), _p(res)))
         return res
 
+    def hsma_server_start(self):
+        self._check(self.lib.hsma_server_start(self.ptr))
+
+    def hsma_server_submit(self, req) -> int:
+        """Submit one request (a REQUEST record); returns its ticket.  Raises HsmaError on a
+        full queue (HSMA_E_BUSY) or a stopped loop (HSMA_E_STATE)."""
+        r = np.ascontiguousarray(np.asarray(req, dtype=REQUEST).reshape(1))
+        t = ctypes.c_int64()
+        rc = self.lib.hsma_server_submit(self.ptr, _p(r), ctypes.byref(t))
+        if rc:
+            raise HsmaError(rc, "hsma_server_submit")
+        return int(t.value)
+
+    def hsma_server_poll(self, max_results: int = 256, timeout: float = 0.0) -> np.ndarray:
+        """Answers available now (timeout 0) or within timeout seconds (an empty array when none
+        came)."""
+        out = np.zeros(max_results, dtype=RESULT)
+        cnt = ctypes.c_int()
+        rc = self.lib.hsma_server_poll(self.ptr, _p(out), int(max_results), float(timeout), ctypes.byref(cnt))
+        if rc and rc != HSMA_E_TIMEOUT:
+            raise HsmaError(rc, "hsma_server_poll")
+        return out[:cnt.value]
+
+    def hsma_server_stop(self, drain: bool = True):
+        self._check(self.lib.hsma_server_stop(self.ptr, 1 if drain else 0))
+
     def hsma_server_positions(self, c: int) -> np.ndarray:
         n = self.chains[c].n
         out = np.empty((n, 3))
@@ -108,10 +137,19 @@ def make_trace(workload: ServingWorkload, nreq: int, rate: float | None, positio
     return reqs, pos
 
 
-def latency_stats(res: np.ndarray) -> dict:
+def latency_stats(res: np.ndarray, reqs: np.ndarray | None = None) -> dict:
+    """p50/p99 latency and throughput of the answered requests; with the requests, also the
+    latencies of the move and the full-energy requests apart."""
     ok = res["status"] == 0
     lat = (res["t_done"] - res["t_arrival"])[ok]
     span = float(res["t_done"][ok].max() - res["t_arrival"][ok].min()) if ok.any() else 0.0
-    return {"p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
-            "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
-            "req_per_s": float(ok.sum() / span) if span > 0 else None, "answered": int(ok.sum())}
+    out = {"p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+           "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+           "req_per_s": float(ok.sum() / span) if span > 0 else None, "answered": int(ok.sum())}
+    if reqs is not None:
+        for name, kind in (("delta", REQ_DELTA), ("energy", REQ_ENERGY)):
+            m = ok & (reqs["kind"] == kind)
+            lk = (res["t_done"] - res["t_arrival"])[m]
+            out[name] = {"p50_ms": float(np.percentile(lk, 50) * 1e3) if lk.size else None,
+                         "p99_ms": float(np.percentile(lk, 99) * 1e3) if lk.size else None, "answered": int(m.sum())}
+    return out

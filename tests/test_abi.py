@@ -44,3 +44,13 @@ def test_default_params_without_gpu():
 
 def test_built_for_sm103a_only():
     assert _native.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_server_entry_points_reject_null_without_gpu():
+    import ctypes
+    lib = _native.load()
+    cnt = ctypes.c_int()
+    assert lib.hsma_server_start(None) == -1
+    assert lib.hsma_server_submit(None, None, None) == -1
+    assert lib.hsma_server_poll(None, None, 0, 0.0, ctypes.byref(cnt)) == -1
+    assert lib.hsma_server_stop(None, 1) == -1

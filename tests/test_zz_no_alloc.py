@@ -1,10 +1,11 @@
 """The allocation-free Coulomb sum (hsma_coulomb_potential_noalloc) against the regular entry point.
 
-Callers that may not allocate device memory (graph capture in progress, allocator callbacks,
-fixed-budget real-time loops) use hsma_coulomb_potential_noalloc, whose scratch memory is a
-static device array.  This file is collected last on purpose.  It checks, through the C ABI,
-that two calls in a row reproduce hsma_potential(..., HSMA_COULOMB) within the FP32
-tolerance of the tests (1e-6 norm-wise), and that sizes beyond the maximum are rejected.
+Callers that may not allocate device memory (code inside allocator callbacks, plugins whose
+host application owns all device memory, fixed-budget real-time loops) use
+hsma_coulomb_potential_noalloc, whose scratch memory is a static device array.  This file is
+collected last on purpose.  It checks, through the C ABI, that two calls in a row reproduce
+hsma_potential(..., HSMA_COULOMB) within the FP32 tolerance of the tests (1e-6 norm-wise), up
+to the largest accepted size, and that sizes beyond the maximum are rejected.
 """
 import ctypes
 
@@ -31,7 +32,7 @@ def _noalloc(lib, xyz_d, q_d, kfac, out, stream):
                                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
 
 
-@pytest.mark.parametrize("n", [1, 517, 5000])
+@pytest.mark.parametrize("n", [1, 517, 5000, MAX_N])
 def test_noalloc_matches_regular_entry_point_twice(n):
     import torch
     lib = _native.load()
