@@ -174,17 +174,24 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   Layout L;
   const int nsys = (int)spec.size();
   L.cfg = cfg;
-  int TB, occ;
+  // TB: targets per pair item (FP64) or per surface item of the FP32 pair kernel (a warp's
+  // group); TBf: targets per item of the FP32 field kernel (its CTA's targets)
+  int TB, TBf, occ, nw;
   if (prec == HSMA_FP64) {
-    TB = kF64TargetsPerBlock;
+    TB = TBf = kF64TargetsPerBlock;
     occ = occ_f64 > 0 ? occ_f64 : 1;
+    nw = 1;
   } else {
     const PairConfig pc = pair_config(cfg);
-    TB = pc.threads * pc.k;
+    TB = 32 * pc.k;
+    TBf = pc.threads * pc.k;
     occ = occ_f32[cfg] > 0 ? occ_f32[cfg] : 1;
+    nw = pair_workers_per_cta(cfg);
   }
   const int slots = num_sms * occ;
-  const double desired = (prec == HSMA_FP64 ? 4.0 : (double)pair_config(cfg).items_per_slot) * slots;
+  // pair items wanted over the whole engine: a few per worker (CTA on the FP64 path, warp on the
+  // FP32 path)
+  const double desired = (prec == HSMA_FP64 ? 4.0 : (double)pair_config(cfg).items_per_slot) * slots * nw;
   // the pair items and moment blocks of the whole engine are apportioned by each system's share
   // of the work, so a batch of many small systems gets few, larger items per system
   double W = 0.0;
@@ -233,16 +240,37 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     if (n > 0) {
       const double Ws = (double)n * (2.0 * n + 1.3 * sp.M);
       const double items_s = std::max(1.0, std::round(desired * Ws / std::max(W, 1.0)));
-      const int64_t chunks_total = std::max<int64_t>(1, (int64_t)std::ceil(items_s / d.n_tb));
-      const int64_t per = (2 * n + sp.M + chunks_total - 1) / chunks_total;
-      const int unit = prec == HSMA_FP64 ? kF64TargetsPerBlock : pair_config(cfg).threads;
-      int64_t chunk = std::max<int64_t>(per, unit);
-      chunk = (chunk + unit - 1) / unit * unit;
-      d.chunk = (int)chunk;
-      d.chunk_s = (int)chunk;
-      d.ncr = (int)((n + chunk - 1) / chunk);
-      d.nck = d.ncr;
-      d.ncs = (int)((sp.M + chunk - 1) / chunk);
+      if (prec == HSMA_FP64) {
+        const int64_t chunks_total = std::max<int64_t>(1, (int64_t)std::ceil(items_s / d.n_tb));
+        const int64_t per = (2 * n + sp.M + chunks_total - 1) / chunks_total;
+        const int unit = kF64TargetsPerBlock;
+        int64_t chunk = std::max<int64_t>(per, unit);
+        chunk = (chunk + unit - 1) / unit * unit;
+        d.chunk = (int)chunk;
+        d.chunk_s = (int)chunk;
+        d.ncr = (int)((n + chunk - 1) / chunk);
+        d.nck = d.ncr;
+        d.ncs = (int)((sp.M + chunk - 1) / chunk);
+      } else {
+        // real and Kelvin: nb blocks that are also the chunks, nb (nb + 1) items (each unordered
+        // pair of blocks once, real and Kelvin); a block is a whole number of the pair kernel's
+        // target groups and at most kSymChunkMax charges
+        const double items_rk = items_s * (2.0 * n) / (2.0 * n + 1.3 * sp.M);
+        const int64_t nb = std::max<int64_t>(1, (int64_t)std::floor(std::sqrt(std::max(items_rk, 1.0))));
+        int64_t chunk = (n + nb - 1) / nb;
+        chunk = (chunk + TB - 1) / TB * TB;
+        chunk = std::min<int64_t>(std::max<int64_t>(chunk, TB), kSymChunkMax / TB * TB);
+        d.chunk = (int)chunk;
+        d.ncr = (int)((n + chunk - 1) / chunk);
+        d.nck = d.ncr;
+        // surface: the rest of the items over the target groups, chunks of whole 32-point boxes
+        const double items_sf = std::max(1.0, items_s - items_rk);
+        const int64_t ncs_want = std::max<int64_t>(1, std::llround(items_sf / d.n_tb));
+        int64_t chunk_s = (sp.M + ncs_want - 1) / ncs_want;
+        chunk_s = std::max<int64_t>(kBox, (chunk_s + kBox - 1) / kBox * kBox);
+        d.chunk_s = (int)chunk_s;
+        d.ncs = (int)((sp.M + chunk_s - 1) / chunk_s);
+      }
     }
     d.part = part;
     d.dc2 = (float)((kNearRel * sp.a) * (kNearRel * sp.a));
@@ -256,8 +284,23 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     for (int b = 0; b < d.k5_count; ++b) L.it5.push_back(make_int2(s, b));
     for (int b = 0; b < (int)((n + kOrderBlock - 1) / kOrderBlock); ++b) L.itord.push_back(make_int2(s, b));
     const int nch = d.ncr + d.nck + d.ncs;
-    for (int tb = 0; tb < d.n_tb; ++tb)
-      for (int c = 0; c < nch; ++c) L.it4.push_back(make_int4(s, tb, c, 0));
+    if (prec == HSMA_FP64) {
+      for (int tb = 0; tb < d.n_tb; ++tb)
+        for (int c = 0; c < nch; ++c) L.it4.push_back(make_int4(s, tb, c, 0));
+    } else if (n > 0) {
+      // the pair kernel: each unordered pair of real/Kelvin blocks once, surface items per group
+      for (int b = 0; b < d.ncr; ++b)
+        for (int c = b; c < d.ncr; ++c) {
+          L.it4.push_back(make_int4(s, b, c, 0));
+          L.it4.push_back(make_int4(s, b, d.ncr + c, 0));
+        }
+      for (int tb = 0; tb < d.n_tb; ++tb)
+        for (int c = d.ncr + d.nck; c < nch; ++c) L.it4.push_back(make_int4(s, tb, c, 0));
+      // the field kernel: every (target block, chunk) one way
+      const int ntbf = (int)((n + TBf - 1) / TBf);
+      for (int tb = 0; tb < ntbf; ++tb)
+        for (int c = 0; c < nch; ++c) L.it4f.push_back(make_int4(s, tb, c, 0));
+    }
     chg += n;
     surf += sp.M;
     coef += d.P;
@@ -291,27 +334,43 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     if (!L.use_sb) L.itsb.clear();
   }
   // longest pair items first (cost ~ targets x sources x per-source weight)
-  auto cost = [&](const int4& it) {
+  const bool sym = prec != HSMA_FP64;
+  auto cost_of = [&](const int4& it, bool field) {
     const SysDev& d = L.sd[it.x];
-    const int64_t nt = std::min<int64_t>(d.tb, d.n - (int64_t)it.y * d.tb);
-    int64_t ns_, w = 10;
-    if (it.z < d.ncr) {
-      ns_ = std::min<int64_t>(d.chunk, d.n - (int64_t)it.z * d.chunk);
-    } else if (it.z < d.ncr + d.nck) {
-      ns_ = std::min<int64_t>(d.chunk, d.n - (int64_t)(it.z - d.ncr) * d.chunk);
+    const bool rk = it.z < d.ncr + d.nck;
+    const int cb = it.z < d.ncr ? it.z : it.z - d.ncr;
+    int64_t nt, ns_, w = 10;
+    if (sym && !field && rk) {
+      // a real/Kelvin block against a chunk: both ways off the diagonal
+      nt = std::min<int64_t>(d.chunk, d.n - (int64_t)it.y * d.chunk);
+      w = cb > it.y ? 12 : 10;
+    } else {
+      const int64_t tbk = field ? TBf : d.tb;
+      nt = std::min<int64_t>(tbk, d.n - (int64_t)it.y * tbk);
+    }
+    if (rk) {
+      ns_ = std::min<int64_t>(d.chunk, d.n - (int64_t)cb * d.chunk);
     } else {
       ns_ = std::min<int64_t>(d.chunk_s, d.M - (int64_t)(it.z - d.ncr - d.nck) * d.chunk_s);
       w = 13;
     }
     return nt * ns_ * w;
   };
+  auto is_rk = [&](const int4& it) { return it.z < L.sd[it.x].ncr + L.sd[it.x].nck; };
   for (auto& it : L.it4) it.w = 0;
-  std::stable_sort(L.it4.begin(), L.it4.end(), [&](const int4& x, const int4& y) { return cost(x) > cost(y); });
+  std::stable_sort(L.it4.begin(), L.it4.end(),
+                   [&](const int4& x, const int4& y) { return cost_of(x, false) > cost_of(y, false); });
   // the overlapped pass launches the real/Kelvin items (which need only the records) apart from
   // the surface items (which wait for the coefficient chain)
   L.it4x = L.it4;
-  auto is_rk = [&](const int4& it) { return it.z < L.sd[it.x].ncr + L.sd[it.x].nck; };
   L.nRK = (int)(std::stable_partition(L.it4x.begin(), L.it4x.end(), is_rk) - L.it4x.begin());
+  // the field pass: on the FP64 path the same one-way list; on the FP32 path its own
+  if (!sym) L.it4f = L.it4;
+  for (auto& it : L.it4f) it.w = 0;
+  std::stable_sort(L.it4f.begin(), L.it4f.end(),
+                   [&](const int4& x, const int4& y) { return cost_of(x, true) > cost_of(y, true); });
+  L.it4fx = L.it4f;
+  L.nRKf = (int)(std::stable_partition(L.it4fx.begin(), L.it4fx.end(), is_rk) - L.it4fx.begin());
   L.totN = chg;
   L.totM = surf;
   L.totP = coef;
@@ -320,7 +379,8 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.totPart = part;
   L.totBoxes = boxes;
   L.mom_stride = (int)align_up((size_t)L.maxP + 1, 2);
-  L.pair_grid = (int)std::max<size_t>(1, std::min<size_t>(L.it4.size(), (size_t)slots));
+  L.nw = nw;
+  L.pair_grid = (int)std::max<size_t>(1, std::min<size_t>((L.it4.size() + nw - 1) / nw, (size_t)slots));
 
   // workspace plan
   size_t off = 0;
@@ -400,6 +460,8 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_it5 = take(sizeof(int2) * L.it5.size());
   L.o_it4 = take(sizeof(int4) * L.it4.size());
   L.o_it4x = take(sizeof(int4) * L.it4x.size());
+  L.o_it4f = take(sizeof(int4) * L.it4f.size());
+  L.o_it4fx = take(sizeof(int4) * L.it4fx.size());
   L.sel.resize(nsys);
   L.selrng.resize(nsys);
   for (int s = 0; s < nsys; ++s) {
@@ -484,6 +546,8 @@ void Engine::carve()
   it5_d = (int2*)(b + L.o_it5);
   it4_d = (int4*)(b + L.o_it4);
   it4x_d = (int4*)(b + L.o_it4x);
+  it4f_d = (int4*)(b + L.o_it4f);
+  it4fx_d = (int4*)(b + L.o_it4fx);
   ctr_pairs2_d = ctr + 1;
   sel_d = (int*)(b + L.o_sel);
   selrng_d = (int2*)(b + L.o_selrng);
@@ -544,6 +608,10 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
     CK(cudaMemcpyAsync(it4_d, L.it4.data(), sizeof(int4) * L.it4.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it4x.empty())
     CK(cudaMemcpyAsync(it4x_d, L.it4x.data(), sizeof(int4) * L.it4x.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.it4f.empty())
+    CK(cudaMemcpyAsync(it4f_d, L.it4f.data(), sizeof(int4) * L.it4f.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.it4fx.empty())
+    CK(cudaMemcpyAsync(it4fx_d, L.it4fx.data(), sizeof(int4) * L.it4fx.size(), cudaMemcpyHostToDevice, stream));
   if (!L.itsb.empty())
     CK(cudaMemcpyAsync(itsb_d, L.itsb.data(), sizeof(int2) * L.itsb.size(), cudaMemcpyHostToDevice, stream));
   if (!L.itord.empty())
@@ -629,7 +697,7 @@ void Engine::issue_pot()
   if (!L.it4.empty()) {
     cudaEventRecordWithFlags(ev_pair0, stream, cudaEventRecordExternal);
     const int nit = (int)L.it4.size();
-    const PairWork all{it4_d, nit, ctr_pairs_d, std::min(L.pair_grid, nit)}, none{nullptr, 0, nullptr, 0};
+    const PairWork all{it4_d, nit, ctr_pairs_d, std::min(L.pair_grid * L.nw, nit)}, none{nullptr, 0, nullptr, 0};
     if (prec == HSMA_FP64)
       launch_pairs_f64(L.pair_grid, sys_d, all, none, src64_d, surf64a_d, surf64b_d, part64_d, stream);
     else
@@ -676,8 +744,9 @@ void Engine::issue_fused()
   const int nS = (int)L.it4x.size() - L.nRK;
   const int occ = prec == HSMA_FP64 ? std::max(occ_f64, 1) : std::max(occ_f32[L.cfg], 1);
   const int slots = num_sms * occ;
-  const int grid_rk = std::max(1, std::min(L.nRK, (int)(kOverlapShare * slots)));
-  const int grid_s = std::max(1, std::min(nS + L.nRK, slots));
+  const int nw = L.nw;  // workers per CTA
+  const int grid_rk = std::max(1, std::min((L.nRK + nw - 1) / nw, (int)(kOverlapShare * slots)));
+  const int grid_s = std::max(1, std::min((nS + L.nRK + nw - 1) / nw, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);
   // launch priorities: the order and the records (short, and the capped real/Kelvin launch
@@ -685,8 +754,8 @@ void Engine::issue_fused()
   // launch last, so that its CTAs take only what the chains leave free; k_order_keys also
   // zeroes both pair work counters (ctr_pairs_d and ctr_pairs2_d, adjacent), which the main
   // stream's launch uses only after ev_img
-  const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d, std::min(grid_rk, L.nRK)};
-  const PairWork srf{it4x_d + L.nRK, nS, ctr_pairs_d, std::min(grid_s, nS)}, none{nullptr, 0, nullptr, 0};
+  const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d, std::min(grid_rk * nw, L.nRK)};
+  const PairWork srf{it4x_d + L.nRK, nS, ctr_pairs_d, std::min(grid_s * nw, nS)}, none{nullptr, 0, nullptr, 0};
   {
     PriorityScope ps(prio_hi);
     launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
@@ -965,11 +1034,11 @@ void Engine::launch_field_reduce(cudaStream_t st)
 void Engine::issue_field()
 {
   cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), stream);
-  if (!L.it4.empty()) {
+  if (!L.it4f.empty()) {
     cudaEventRecordWithFlags(ev_pair0, stream, cudaEventRecordExternal);
-    const int nit = (int)L.it4.size();
+    const int nit = (int)L.it4f.size();
     const int grid = std::max(1, std::min(nit, field_slots()));
-    const PairWork all{it4_d, nit, ctr_pairs_d, std::min(grid, nit)}, none{nullptr, 0, nullptr, 0};
+    const PairWork all{it4f_d, nit, ctr_pairs_d, std::min(grid, nit)}, none{nullptr, 0, nullptr, 0};
     launch_field_items(all, none, grid, stream);
     cudaEventRecordWithFlags(ev_pair1, stream, cudaEventRecordExternal);
   }
@@ -982,14 +1051,14 @@ void Engine::issue_field()
 void Engine::issue_field_fused()
 {
   const int nsys = (int)L.sd.size();
-  const int nS = (int)L.it4x.size() - L.nRK;
+  const int nS = (int)L.it4fx.size() - L.nRKf;
   const int slots = field_slots();
-  const int grid_rk = std::max(1, std::min(L.nRK, (int)(kOverlapShare * slots)));
-  const int grid_s = std::max(1, std::min(nS + L.nRK, slots));
+  const int grid_rk = std::max(1, std::min(L.nRKf, (int)(kOverlapShare * slots)));
+  const int grid_s = std::max(1, std::min(nS + L.nRKf, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);
-  const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d, std::min(grid_rk, L.nRK)};
-  const PairWork srf{it4x_d + L.nRK, nS, ctr_pairs_d, std::min(grid_s, nS)}, none{nullptr, 0, nullptr, 0};
+  const PairWork rk{it4fx_d, L.nRKf, ctr_pairs2_d, std::min(grid_rk, L.nRKf)};
+  const PairWork srf{it4fx_d + L.nRKf, nS, ctr_pairs_d, std::min(grid_s, nS)}, none{nullptr, 0, nullptr, 0};
   {
     PriorityScope ps(prio_hi);
     launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
@@ -1025,7 +1094,7 @@ int Engine::field()
     rc = run_graph(&g_field_fused, &Engine::issue_field_fused);
     if (rc) return rc;
     leave();
-    launches += build_launch_count() + (L.nRK > 0 ? 1 : 0) + (L.it4x.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1);
+    launches += build_launch_count() + (L.nRKf > 0 ? 1 : 0) + (L.it4fx.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1);
     build_pending = false;
   } else {
     rc = ensure_built();

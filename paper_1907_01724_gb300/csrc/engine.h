@@ -50,6 +50,10 @@ struct Layout {
   std::vector<int4> it4;
   std::vector<int4> it4x;     // it4 split: real and Kelvin items first (nRK), then surface items
   int nRK = 0;
+  std::vector<int4> it4f;     // items of the field pass (FP32: every (target block, chunk) one way)
+  std::vector<int4> it4fx;    // it4f split as it4x
+  int nRKf = 0;
+  int nw = 1;                 // pair-kernel workers per CTA (FP32: warps)
   std::vector<int> sel;       // all systems, in order (energy pass of a full launch)
   std::vector<int2> selrng;   // their reduce-item ranges
   size_t o_sel = 0, o_selrng = 0;
@@ -66,7 +70,7 @@ struct Layout {
   size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_sortscr = 0, o_xs = 0, o_boxes = 0, o_itord = 0;
   size_t o_redctr = 0;
   size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0, o_outdesc = 0;
-  size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0, o_it4x = 0;
+  size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0, o_it4x = 0, o_it4f = 0, o_it4fx = 0;
   size_t bytes = 0;
 };
 
@@ -166,6 +170,8 @@ class Engine {
   int2* selrng_d = nullptr;
   int4* it4_d = nullptr;
   int4* it4x_d = nullptr;
+  int4* it4f_d = nullptr;
+  int4* it4fx_d = nullptr;
   unsigned int* ctr_pairs2_d = nullptr;  // work counter of the overlapped real/Kelvin pair launch
 
   // pair-kernel timing events (recorded around every pair-sum launch)

@@ -115,10 +115,12 @@ struct SysDev {
   int mom_tile;       // charges per moment block
   long long part;     // offset of its pair partials (n_chunks * n elements)
   int ncr, nck, ncs;  // source chunks: real, Kelvin, surface
-  int chunk;          // sources per real/Kelvin chunk
+  int chunk;          // sources per real/Kelvin chunk; FP32 path: also the targets per block of
+                      // the pair kernel's real/Kelvin items (blocks and chunks coincide)
   int chunk_s;        // points per surface chunk
-  int tb;             // targets per target block
-  int n_tb;           // target blocks
+  int tb;             // targets per target block of the pair kernel's surface items (FP32 path:
+                      // a warp's group, 32 K) and of every FP64 pair item
+  int n_tb;           // such target blocks
   int k5_first;       // first reduce item of this system
   int k5_count;       // reduce items of this system
   float dc2;          // squared near distance of the FP32 pair-sum box test, (kNearRel a)^2
@@ -153,6 +155,10 @@ void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, co
 // kNearRel a use plain FP32 coordinates in the pair sum, nearer ones the hi/lo-split form.
 constexpr int kBox = 32;
 constexpr double kNearRel = 0.08;
+// Largest block of the FP32 path's real and Kelvin items (charges; blocks and chunks coincide
+// there, see k_pairs_f32.cuh): the pair kernel keeps one (hi, lo) sum per source of a chunk in
+// shared memory per warp.
+constexpr int kSymChunkMax = 512;
 
 // Offsets of the surface-record and coefficient tables for one engine.
 struct Tables {
@@ -216,6 +222,7 @@ struct PairConfig {
 };
 int pair_config_count();
 PairConfig pair_config(int idx);
+int pair_workers_per_cta(int cfg);  // FP32 pair kernel: warps, each an independent worker
 int pair_kernel_of(int cfg);  // kernel variant (threads, k) of a configuration
 int pairs_f32_occupancy(int cfg);
 int pairs_f64_occupancy();

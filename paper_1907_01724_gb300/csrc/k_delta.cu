@@ -515,15 +515,18 @@ __global__ __launch_bounds__(256) void k_move_charge(const SysDev* __restrict__ 
       src64[sk] = make_dbl4(In.x, In.y, In.z, In.Q);
     } else {
       float hx, hy, hz, lx, ly, lz;
+      // (the lo records' fourth components: the weights of the symmetric pair sum's transposed
+      // Kelvin term, as written by k_images)
+      const double rn2 = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(R.x, R.x), __dmul_rn(R.y, R.y)), __dmul_rn(R.z, R.z)));
       split_hilo(R.x, hx, lx); split_hilo(R.y, hy, ly); split_hilo(R.z, hz, lz);
       src_hi[sr] = make_float4(hx, hy, hz, (float)(S.kc * qk));
-      src_lo[sr] = make_float4(lx, ly, lz, 0.f);
+      src_lo[sr] = make_float4(lx, ly, lz, In.centre ? 0.f : (float)(In.Q * rn2));
       const long long b = S.bb + ks / kBox, bk = b + (S.n + kBox - 1) / kBox;
       box_grow(boxes + 2 * b, hx, hy, hz);
       split_hilo(In.x, hx, lx); split_hilo(In.y, hy, ly); split_hilo(In.z, hz, lz);
       src_hi[sk] = make_float4(hx, hy, hz, (float)In.Q);
-      src_lo[sk] = make_float4(lx, ly, lz, 0.f);
-      box_grow(boxes + 2 * bk, hx, hy, hz);
+      src_lo[sk] = make_float4(lx, ly, lz, In.centre ? (float)(1e15 * S.inv_a) : (float)(1.0 / rn2));
+      if (!In.centre) box_grow(boxes + 2 * bk, hx, hy, hz);
     }
     xyz[3 * kk] = R.x;
     xyz[3 * kk + 1] = R.y;

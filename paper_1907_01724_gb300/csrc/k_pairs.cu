@@ -4,10 +4,12 @@
 // Sources of one cavity: n real charges (excluding the target itself), n trapezoid-modified
 // Kelvin images, and M surface points each carrying a monopole and a dipole (the 3M discrete
 // images of eq. phicorrfinall).  Work is split into items (system, target block, source
-// chunk); persistent CTAs pull items from an atomic counter (longest items first) and write
-// one compensated FP32 partial per (chunk, target), which k_reduce (k_reduce.cu) sums in a
-// fixed order (FP64, or double-float on the FP32 path), so results do not depend on scheduling.  Records
-// and partials are in the spatial order of k_order.cu; k_reduce maps them back to input order.
+// chunk); persistent workers (CTAs on the FP64 path, warps on the FP32 path) pull items from an
+// atomic counter (longest items first) and write one compensated partial per (chunk, target),
+// which k_reduce (k_reduce.cu) sums in a fixed order (FP64, or double-float on the FP32 path),
+// so results do not depend on scheduling.  Records and partials are in the spatial order of
+// k_order.cu; k_reduce maps them back to input order.  On the FP32 path the real and Kelvin
+// items cover each unordered pair of blocks once and fill both blocks' slots (k_pairs_f32.cuh).
 //
 // FP32 path (ALU bound, no tensor cores: the sum is not a dense contraction):
 //  * real and Kelvin records hold hi/lo-split coordinates; with dh the FP32 difference of the
@@ -78,6 +80,7 @@ static const int kItemsPerSlot[] = {4, 2, 1};
 constexpr int kItemChoices = (int)(sizeof(kItemsPerSlot) / sizeof(kItemsPerSlot[0]));
 
 int pair_config_count() { return kPairKernels * kItemChoices; }
+int pair_workers_per_cta(int cfg) { return kPairKernel[cfg % kPairKernels][0] / 32; }
 int pair_kernel_of(int cfg) { return cfg % kPairKernels; }
 PairConfig pair_config(int idx)
 {
@@ -93,7 +96,7 @@ int pairs_f32_occupancy(int cfg)
   int b = 0;
   switch (pair_kernel_of(cfg)) {
 #define HSMA_CFG_OCC(i, nt, k) \
-  case i: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_f32<nt, k>, nt, 0); break;
+  case i: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pairs_f32<nt, k>, nt, pair_dyn_smem(nt)); break;
     HSMA_PAIR_CONFIGS(HSMA_CFG_OCC)
 #undef HSMA_CFG_OCC
     default: break;
@@ -108,7 +111,8 @@ void launch_pairs_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWor
   switch (pair_kernel_of(cfg)) {
 #define HSMA_CFG_LAUNCH(i, nt, k)                                                                          \
   case i:                                                                                                  \
-    launch_k(k_pairs_f32<nt, k>, grid, nt, 0, st, pdl, sys, w1, w2, src_hi, src_lo, surf_a, surf_b, boxes, part); \
+    launch_k(k_pairs_f32<nt, k>, grid, nt, pair_dyn_smem(nt), st, pdl, sys, w1, w2, src_hi, src_lo, surf_a, surf_b, \
+             boxes, part);                                                                                 \
     break;
     HSMA_PAIR_CONFIGS(HSMA_CFG_LAUNCH)
 #undef HSMA_CFG_LAUNCH

@@ -1,33 +1,46 @@
 // FP32 pair-sum kernel (included by k_pairs.cu inside namespace hsma).
 //
-// Sources and targets are in the spatial order of k_order.cu.  A warp owns 32*K consecutive
-// targets.
+// Work is split among warps, not CTAs: every warp pulls its own items and never waits for the
+// other warps of its CTA.  Records and targets are in the spatial order of k_order.cu.
 //
-// Real and Kelvin sources (per warp, no CTA-wide synchronisation): the warp works in
-// coordinates relative to an origin o at the centre of its targets' box; a target is held as
-// the exact (hi, lo) FP32 split t' of x - o, a source as s' = fl(fl(x_hi - o) + x_lo) (within
-// 2u |s'|, u = 2^-24).  The warp walks the chunk's 32-record source boxes; lane l loads record
-// l of the next box while the current one is summed, and writes (-2 s', |s'|^2) and q of its
-// record to the warp's shared buffer.  Per (warp, box) one of three forms is chosen, from
-// X = (largest |t'|) + (largest |s'|) over the two boxes and their gap g (d >= g for every
-// pair), so that each pair's relative error in 1/r stays below ~2.6e-6:
-//   expanded  r^2 = |t'|^2 + |s'|^2 - 2 t'.s'   (1 FADD + 3 FFMA)   when X <= kExpRatio g:
-//             the rounding of the expanded form, <= ~5 u X^2 in r^2, and the position errors,
-//             <= 2 sqrt(3) u X / d, give <= 2.5 u (X/d)^2 + 3.5 u X/d relative in 1/r;
-//   difference s = t'_hi - s',  r^2 = |s|^2      (3 + 3 operations)  when X <= kMidRatio g:
-//             <= 2 sqrt(3) u X / d relative;
-//   checked   the difference form where d >= X / kMidRatio; the rare closer pairs (r^2 below
-//             that bound, the self pair included) are marked in a per-target mask in the loop
-//             and added afterwards in the exact hi/lo form: t' and s' as exact splits from the
-//             raw records, s = (t'_hi - s'_hi) + (t'_lo - s'_lo), accurate to FP32 rounding at
-//             any distance (a charge next to its own Kelvin image); the self pair gets
-//             r^2 = +inf, i.e. no contribution.
-// Each pair then costs one MUFU rsqrt and one FFMA.
+// Real and Kelvin items (system, block b, chunk c >= b): blocks and chunks are the same runs of
+// S.chunk sorted charges.  The warp takes the block's targets in groups of 32 K (K per lane)
+// and, for each group, walks the chunk's 32-record source boxes.
+//  * Coordinates relative to an origin o at the centre of the group's box: a target is held as
+//    the exact (hi, lo) FP32 split t' of x - o, a source as s' = fl(fl(x_hi - o) + x_lo) (within
+//    2u |s'|, u = 2^-24).  Lane l loads record l of the next box while the current one is
+//    summed, and writes (-2 s', |s'|^2) and q of its record to the warp's buffer.
+//  * Per (group, box) one of three forms, from X = (largest |t'|) + (largest |s'|) over the two
+//    boxes and their gap g (d >= g for every pair), so that each pair's relative error in 1/r
+//    stays below ~2.7e-6:
+//      expanded    r^2 = |t'|^2 + |s'|^2 - 2 t'.s'  (1 FADD + 3 FFMA)  when X <= kExpRatio g:
+//                  the rounding of the expanded form, <= ~5 u X^2 in r^2, and the position
+//                  errors, <= 2 sqrt(3) u X / d, give <= 2.5 u (X/d)^2 + 3.5 u X/d;
+//      difference  s = t'_hi - s', r^2 = |s|^2      (3 + 3 operations) when X <= kMidRatio g:
+//                  <= 2 sqrt(3) u X / d;
+//      checked     the difference form where d >= X / kMidRatio; the rare closer pairs (r^2
+//                  below that bound, the self pair included) are marked in a mask in the loop
+//                  and added afterwards in the exact hi/lo form: t' and s' as exact splits from
+//                  the raw records, s = (t'_hi - s'_hi) + (t'_lo - s'_lo), accurate to FP32
+//                  rounding at any distance (a charge next to its own Kelvin image); the self
+//                  pair gets r^2 = +inf, i.e. no contribution.
+//  * Off-diagonal items (c > b) are evaluated once per unordered pair, both ways.  Real pairs by
+//    Newton's third law: 1/|x_i - x_j| serves i's term from j and j's term from i.  Kelvin pairs
+//    by Kelvin inversion, |x_j - x_i*| = |x_i - x_j*| |x_j| / |x_i| (x* = a^2 x / |x|^2): the
+//    target i's term from j's image is q_K,j / |x_i - x_j*|, and j's term from i's image is
+//    (q_K,i |x_i|) (1 / |x_i - x_j*|) (1 / |x_j|); k_images stores q_K,i |x_i| with the real
+//    record and 1 / |x_j| with the Kelvin record.  In a box the lanes walk a ring: at step j
+//    lane l takes source (l + j) mod 32 and hands that source's running sum of the transposed
+//    terms to lane l - 1, so after 32 steps lane l holds its source's sum over the group's
+//    targets; the sums are kept per source as (hi, lo) pairs in the warp's shared memory and
+//    written, for the block's slot, at the end of the item.  The diagonal item (c = b) is
+//    evaluated one way and skips the self pair.
 //
-// Surface sources (CTA tiles staged with cp.async): monopole and dipole share one rsqrt; the
-// dipole pair in its dy -> 0 limit.  Absolute FP32 coordinates: d >= tau a for every target.
+// Surface items (system, group of 32 K targets, surface chunk): points staged per warp the same
+// way; monopole and dipole share one rsqrt, the dipole pair in its dy -> 0 limit; absolute FP32
+// coordinates (d >= tau a for every target).
 //
-// Each target keeps an FP32 partial per group of sources, folded into an (hi, lo) two-sum pair.
+// Each target keeps an FP32 partial per group of boxes, folded into an (hi, lo) two-sum pair.
 
 // ratios of the form choice (see above): 2.5 u 3.6^2 + 3.5 u 3.6 = 2.7e-6 and
 // 2 sqrt(3) u 12 = 2.5e-6
@@ -55,6 +68,15 @@ __device__ __forceinline__ void rel_split(float xh, float xl, float o, float& h,
   l = t - (h - s);
 }
 
+// (H, L) += v (two-sum)
+__device__ __forceinline__ void fold_two_sum(float& H, float& L, float v)
+{
+  const float s = H + v;
+  const float bp = s - H;
+  L += (H - (s - bp)) + (v - bp);
+  H = s;
+}
+
 // The exact squared distance of a close pair (the checked form's fallback): target and source
 // as exact splits relative to the origin, from their raw (hi, lo) records.
 __device__ __forceinline__ float exact_r2(float4 th, float4 tl, float4 sh, float4 sl, float ox, float oy, float oz)
@@ -72,61 +94,58 @@ __device__ __forceinline__ float exact_r2(float4 th, float4 tl, float4 sh, float
   return fmaf(ez, ez, r2);
 }
 
-// One source of a box against the lane's K targets in one of the three forms.
-template <int K, int FORM>
-__device__ __forceinline__ void source_pairs(const float4 a, const float q, const float (&tx)[K], const float (&ty)[K],
-                                             const float (&tz)[K], const float (&c)[K], float (&acc)[K])
+// Squared distance of a target (relative hi part tx, ty, tz and |t'|^2 = c) to a buffered
+// source a = (-2 s', |s'|^2) in the expanded or the difference form.
+template <int FORM>
+__device__ __forceinline__ float pair_r2(const float4 a, float tx, float ty, float tz, float c)
 {
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    float r2;
-    if (FORM == kFormExp) {
-      r2 = fmaf(tx[k], a.x, fmaf(ty[k], a.y, fmaf(tz[k], a.z, a.w + c[k])));
-    } else {
-      // 0.5 a.x = -s'_x exactly: one rounding, as t'_hi - s'
-      const float dx = fmaf(0.5f, a.x, tx[k]), dy = fmaf(0.5f, a.y, ty[k]), dz = fmaf(0.5f, a.z, tz[k]);
-      r2 = dx * dx;
-      r2 = fmaf(dy, dy, r2);
-      r2 = fmaf(dz, dz, r2);
-    }
-    acc[k] = fmaf(q, rsqrt_mufu(r2), acc[k]);
-  }
+  if (FORM == kFormExp) return fmaf(tx, a.x, fmaf(ty, a.y, fmaf(tz, a.z, a.w + c)));
+  // 0.5 a.x = -s'_x exactly: one rounding, as t'_hi - s'
+  const float dx = fmaf(0.5f, a.x, tx), dy = fmaf(0.5f, a.y, ty), dz = fmaf(0.5f, a.z, tz);
+  float r2 = dx * dx;
+  r2 = fmaf(dy, dy, r2);
+  return fmaf(dz, dz, r2);
 }
 
-// A box of cnt sources (the warp's buffer) in the expanded or the difference form.
+// One-way sums of a box (cnt sources of the warp's buffer) into the lane's K targets.
 template <int K, int FORM>
-__device__ __forceinline__ void box_pairs(const float4* __restrict__ bA, const float* __restrict__ bQ, int cnt,
-                                          const float (&tx)[K], const float (&ty)[K], const float (&tz)[K],
-                                          const float (&c)[K], float (&acc)[K])
+__device__ __forceinline__ void box_oneway(const float4* __restrict__ bA, const float* __restrict__ bQ, int cnt,
+                                           const float (&tx)[K], const float (&ty)[K], const float (&tz)[K],
+                                           const float (&c)[K], float (&acc)[K])
 {
   if (cnt == kBox) {
-#pragma unroll 8
-    for (int s = 0; s < kBox; ++s) source_pairs<K, FORM>(bA[s], bQ[s], tx, ty, tz, c, acc);
+#pragma unroll 4
+    for (int s = 0; s < kBox; ++s) {
+      const float4 a = bA[s];
+      const float q = bQ[s];
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = fmaf(q, rsqrt_mufu(pair_r2<FORM>(a, tx[k], ty[k], tz[k], c[k])), acc[k]);
+    }
   } else {
 #pragma unroll 2
-    for (int s = 0; s < cnt; ++s) source_pairs<K, FORM>(bA[s], bQ[s], tx, ty, tz, c, acc);
+    for (int s = 0; s < cnt; ++s) {
+      const float4 a = bA[s];
+      const float q = bQ[s];
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = fmaf(q, rsqrt_mufu(pair_r2<FORM>(a, tx[k], ty[k], tz[k], c[k])), acc[k]);
+    }
   }
 }
 
-// A box in the checked form: the difference form, where a pair with r^2 < thr2 adds nothing and
-// is marked in its target's 32-bit source mask instead (no branch in the loop); the caller adds
-// the marked pairs in the exact form.
-template <int K, bool FULL>
-__device__ __forceinline__ void box_pairs_checked(const float4* __restrict__ bA, const float* __restrict__ bQ, int cnt,
-                                                  float thr2, const float (&tx)[K], const float (&ty)[K],
-                                                  const float (&tz)[K], float (&acc)[K], unsigned (&mk)[K])
+// One-way checked sums: a pair with r^2 < thr2 adds nothing and is marked in its target's mask
+// (bit = source index).
+template <int K>
+__device__ __forceinline__ void box_oneway_checked(const float4* __restrict__ bA, const float* __restrict__ bQ,
+                                                   int cnt, float thr2, const float (&tx)[K], const float (&ty)[K],
+                                                   const float (&tz)[K], float (&acc)[K], unsigned (&mk)[K])
 {
-  const int ns = FULL ? kBox : cnt;
-#pragma unroll(FULL ? 32 : 1)
-  for (int s = 0; s < ns; ++s) {
+#pragma unroll 4
+  for (int s = 0; s < cnt; ++s) {
     const float4 a = bA[s];
     const float q = bQ[s];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const float dx = fmaf(0.5f, a.x, tx[k]), dy = fmaf(0.5f, a.y, ty[k]), dz = fmaf(0.5f, a.z, tz[k]);
-      float r2 = dx * dx;
-      r2 = fmaf(dy, dy, r2);
-      r2 = fmaf(dz, dz, r2);
+      const float r2 = pair_r2<kFormMid>(a, tx[k], ty[k], tz[k], 0.f);
       const bool close = r2 < thr2;
       if (close) mk[k] |= 1u << s;
       const float inv = rsqrt_mufu(r2);
@@ -135,99 +154,160 @@ __device__ __forceinline__ void box_pairs_checked(const float4* __restrict__ bA,
   }
 }
 
+// Both-way sums of a full or ragged box (the buffer holds the box twice, so that step j of lane
+// l reads entry l + j, i.e. source (l + j) mod 32; entries past the box's sources are far-away
+// zero charges).  The transposed terms go into kRing running sums, sum r taking the steps j = r
+// (mod kRing): after step j it moves kRing lanes down, to the lane that takes the same source at
+// step j + kRing.  After the 32 steps sum r of lane l belongs to source l + r; it is moved to
+// lane l - r, and the lane's returned total belongs to source l.  (One sum: measured on GB300
+// with 2, 4 and 8 interleaved sums, which shorten each sum's chain of dependent shuffles, the
+// kernel was not faster.)  CHECKED: pairs with r^2 < thr2 add nothing either way and are marked
+// in the target's mask (bit = step).
+constexpr int kRing = 1;
+
+template <int K, int FORM, bool CHECKED>
+__device__ __forceinline__ float box_ring(const float4* __restrict__ bA, const float* __restrict__ bQ, int lane,
+                                          float thr2, const float (&tx)[K], const float (&ty)[K],
+                                          const float (&tz)[K], const float (&c)[K], const float (&wt)[K],
+                                          float (&acc)[K], unsigned (&mk)[K])
+{
+  const float4* A = bA + lane;
+  const float* Q = bQ + lane;
+  float sacc[kRing];
+#pragma unroll
+  for (int r = 0; r < kRing; ++r) sacc[r] = 0.f;
+#pragma unroll 8
+  for (int j0 = 0; j0 < kBox; j0 += kRing) {
+#pragma unroll
+    for (int r = 0; r < kRing; ++r) {
+      const int j = j0 + r;
+      const float4 a = A[j];
+      const float q = Q[j];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float r2 = pair_r2<FORM>(a, tx[k], ty[k], tz[k], c[k]);
+        float inv = rsqrt_mufu(r2);
+        if (CHECKED) {
+          const bool close = r2 < thr2;
+          if (close) mk[k] |= 1u << j;
+          inv = close ? 0.f : inv;
+        }
+        acc[k] = fmaf(q, inv, acc[k]);
+        sacc[r] = fmaf(wt[k], inv, sacc[r]);
+      }
+      sacc[r] = __shfl_sync(0xffffffffu, sacc[r], (lane + kRing) & 31);
+    }
+  }
+  float tot = sacc[0];
+#pragma unroll
+  for (int r = 1; r < kRing; ++r) tot += __shfl_sync(0xffffffffu, sacc[r], (lane - r) & 31);
+  return tot;
+}
+
 // registers per thread the kernel is compiled for (launch bounds: resident CTAs per SM), so
 // that the warps of several CTAs share each SM sub-partition's MUFU
 template <int NT, int K>
 constexpr int pair_min_blocks()
 {
-  constexpr int regs = K >= 8 ? 168 : (K >= 4 ? 128 : 96);
+  constexpr int regs = K >= 8 ? 168 : 128;
   return 65536 / (NT * regs) > 0 ? 65536 / (NT * regs) : 1;
 }
 
+// dynamic shared memory of a k_pairs_f32<NT, K> launch: per warp, kSymChunkMax (hi, lo) sums
+// of the transposed terms
+constexpr size_t pair_dyn_smem(int nt) { return (size_t)(nt / 32) * kSymChunkMax * sizeof(float2); }
+
 template <int NT, int K>
-__global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(const SysDev* __restrict__ sys, PairWork w1, PairWork w2,
-                                                  const float4* __restrict__ src_hi,
-                                                  const float4* __restrict__ src_lo,
-                                                  const float4* __restrict__ surf_a,
-                                                  const float4* __restrict__ surf_b,
-                                                  const float4* __restrict__ boxes, float2* __restrict__ part)
+__global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(const SysDev* __restrict__ sys,
+                                                                          PairWork w1, PairWork w2,
+                                                                          const float4* __restrict__ src_hi,
+                                                                          const float4* __restrict__ src_lo,
+                                                                          const float4* __restrict__ surf_a,
+                                                                          const float4* __restrict__ surf_b,
+                                                                          const float4* __restrict__ boxes,
+                                                                          float2* __restrict__ part)
 {
   static_assert(NT % 32 == 0, "whole warps");
+  static_assert(kSymChunkMax % (32 * K) == 0, "blocks of whole target groups");
   constexpr int NW = NT / 32;
-  __shared__ __align__(16) float4 shA[2][NT];  // surface tiles
-  __shared__ __align__(16) float4 shB[2][NT];
-  __shared__ __align__(16) float4 wA[NW][32];  // per warp: (-2 s', |s'|^2) of the current box
-  __shared__ float wQ[NW][32];                 // per warp: q of the current box
-  __shared__ int s_item, s_list;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int G = 32 * K;  // targets per group
+  __shared__ __align__(16) float4 wA[NW][2 * kBox];  // relative source records of the box, twice
+  __shared__ float wQ[NW][2 * kBox];                 // their charges
+  extern __shared__ float2 wP_all[];                 // per warp: (hi, lo) sums of transposed terms
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int worker = blockIdx.x * NW + warp;
+  float4* bA = wA[warp];
+  float* bQ = wQ[warp];
+  float2* P = wP_all + (size_t)warp * kSymChunkMax;
   int list = 0;
   bool first_fetch = true;
   grid_dependency_wait();  // (a programmatic launch: the records and counters of the pass)
 
   for (;;) {
-    if (tid == 0) next_pair_item(w1, w2, list, first_fetch, s_item, s_list);
+    // the warp's next item (lane 0 fetches, the warp follows)
+    int item = 0;
+    if (lane == 0) {
+      int v = 0;
+      if (list == 0) {
+        v = first_fetch && worker < w1.first ? worker : pull_pair_item(w1);
+        if (v < 0) list = 1;
+      }
+      if (list == 1) {
+        v = pull_pair_item(w2);
+        if (v < 0) list = 2;
+      }
+      item = v;
+    }
+    item = __shfl_sync(0xffffffffu, item, 0);
+    list = __shfl_sync(0xffffffffu, list, 0);
     first_fetch = false;
-    __syncthreads();
-    const int item = s_item;
-    list = s_list;
-    __syncthreads();
     if (list > 1) break;
     const int4 it = (list == 0 ? w1.items : w2.items)[item];
     const SysDev& S = sys[it.x];
     const int n = S.n;
-    const int t0 = it.y * (NT * K);
-    const int w0 = t0 + warp * 32 * K;  // the warp's targets are [w0, w0 + 32 K)
     const ChunkInfo ch = decode_chunk(S, it.z);
-    float H[K], L[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) H[k] = L[k] = 0.f;
-    int tix[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) tix[k] = w0 + k * 32 + lane;
 
     if (ch.type == 2) {
-      // ---- surface sources: CTA tiles -------------------------------------------------
-      const float4* gA = surf_a + ch.off;
-      const float4* gB = surf_b + ch.off;
-      const int ntiles = (ch.count + NT - 1) / NT;
-      if (tid < ch.count) {
-        cp_async16(&shA[0][tid], gA + tid);
-        cp_async16(&shB[0][tid], gB + tid);
-      }
-      cp_async_commit();
-      float txh[K], tyh[K], tzh[K];
+      // ---- surface item: one group of targets against a chunk of surface points ----------
+      const int g0 = it.y * G;
+      float tx[K], ty[K], tz[K], H[K], L[K], acc[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float4 h = src_hi[S.src + (tix[k] < n ? tix[k] : t0)];
-        txh[k] = h.x; tyh[k] = h.y; tzh[k] = h.z;
+        const int i = g0 + k * 32 + lane;
+        const float4 h = src_hi[S.src + (i < n ? i : g0)];
+        tx[k] = h.x; ty[k] = h.y; tz[k] = h.z;
+        H[k] = L[k] = acc[k] = 0.f;
       }
-      for (int t = 0; t < ntiles; ++t) {
-        const int buf = t & 1;
-        if (t + 1 < ntiles) {
-          const int s = (t + 1) * NT + tid;
-          if (s < ch.count) {
-            cp_async16(&shA[buf ^ 1][tid], gA + s);
-            cp_async16(&shB[buf ^ 1][tid], gB + s);
-          }
-          cp_async_commit();
-          cp_async_wait<1>();
-        } else {
-          cp_async_wait<0>();
+      const float4* ga = surf_a + ch.off;
+      const float4* gb = surf_b + ch.off;
+      const int nb = (ch.count + kBox - 1) / kBox;
+      float4 ra = make_float4(0.f, 0.f, 0.f, 0.f);
+      float rd = 0.f;
+      if (lane < ch.count) {
+        ra = __ldg(ga + lane);
+        rd = __ldg(gb + lane).x;
+      }
+      for (int b = 0; b < nb; ++b) {
+        const int cnt = min(kBox, ch.count - b * kBox);
+        float4 na = ra;
+        float nd = rd;
+        if (b + 1 < nb && lane < ch.count - (b + 1) * kBox) {
+          na = __ldg(ga + (b + 1) * kBox + lane);
+          nd = __ldg(gb + (b + 1) * kBox + lane).x;
         }
-        __syncthreads();
-        const int cnt = min(NT, ch.count - t * NT);
-        const float4* A = shA[buf];
-        const float4* B = shB[buf];
-        float acc[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] = 0.f;
+        __syncwarp();  // the previous box's sums have read the buffer
+        if (lane < cnt) {
+          bA[lane] = ra;
+          bQ[lane] = rd;
+        }
+        __syncwarp();
 #pragma unroll 2
         for (int s = 0; s < cnt; ++s) {
-          const float4 y = A[s];
-          const float Dp = B[s].x;
+          const float4 y = bA[s];
+          const float Dp = bQ[s];
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            const float dx = txh[k] - y.x, dy = tyh[k] - y.y, dz = tzh[k] - y.z;
+            const float dx = tx[k] - y.x, dy = ty[k] - y.y, dz = tz[k] - y.z;
             float r2 = dx * dx;
             r2 = fmaf(dy, dy, r2);
             r2 = fmaf(dz, dz, r2);
@@ -240,36 +320,51 @@ __global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(cons
             acc[k] = fmaf(v, inv, acc[k]);
           }
         }
+        if ((b + 1) % kFoldBoxes == 0 || b + 1 == nb) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const float s = H[k] + acc[k];
-          const float bp = s - H[k];
-          L[k] += (H[k] - (s - bp)) + (acc[k] - bp);
-          H[k] = s;
+          for (int k = 0; k < K; ++k) {
+            fold_two_sum(H[k], L[k], acc[k]);
+            acc[k] = 0.f;
+          }
         }
-        __syncthreads();
+        ra = na;
+        rd = nd;
       }
-    } else {
-      // ---- real / Kelvin sources: per warp, relative coordinates ---------------------
-      const float4* gh = src_hi + ch.off;
-      const float4* gl = src_lo + ch.off;
-      const int nb = (ch.count + kBox - 1) / kBox;
-      // the first box's record is in flight while the targets load
-      float4 rh = make_float4(0.f, 0.f, 0.f, 0.f), rl = rh;
-      if (lane < ch.count) {
-        rh = __ldg(gh + lane);
-        rl = __ldg(gl + lane);
+      float2* out = part + S.part + (long long)it.z * n;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int i = g0 + k * 32 + lane;
+        if (i < n) out[i] = make_float2(H[k], L[k]);
       }
-      float tx[K], ty[K], tz[K], c[K];
+      continue;
+    }
+
+    // ---- real / Kelvin item: block blk of targets against chunk cb of sources ----------------
+    const int blk = it.y;
+    const int cb = ch.type == 0 ? it.z : it.z - S.ncr;
+    const bool sym = cb > blk;
+    const int tb0 = blk * S.chunk, tb1 = min(n, tb0 + S.chunk);
+    const float4* gh = src_hi + ch.off;
+    const float4* gl = src_lo + ch.off;
+    const int nb = (ch.count + kBox - 1) / kBox;
+    const long long box0 = S.bb + (ch.type == 1 ? (n + kBox - 1) / kBox : 0) + ch.first / kBox;
+    if (sym) {
+      for (int j = lane; j < ch.count; j += 32) P[j] = make_float2(0.f, 0.f);
+    }
+    for (int g0 = tb0; g0 < tb1; g0 += G) {
+      // targets of the group (slots past the block repeat its first target, with no weight)
+      float tx[K], ty[K], tz[K], c[K], wt[K], H[K], L[K], acc[K];
       float wmnx = 3.0e38f, wmny = 3.0e38f, wmnz = 3.0e38f, wmxx = -3.0e38f, wmxy = -3.0e38f, wmxz = -3.0e38f;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float4 h = src_hi[S.src + (tix[k] < n ? tix[k] : t0)];
+        const int i = g0 + k * 32 + lane;
+        const float4 h = src_hi[S.src + (i < tb1 ? i : g0)];
         tx[k] = h.x; ty[k] = h.y; tz[k] = h.z;
+        wt[k] = h.w;
+        H[k] = L[k] = acc[k] = 0.f;
         wmnx = fminf(wmnx, h.x); wmny = fminf(wmny, h.y); wmnz = fminf(wmnz, h.z);
         wmxx = fmaxf(wmxx, h.x); wmxy = fmaxf(wmxy, h.y); wmxz = fmaxf(wmxz, h.z);
       }
-      // box of the warp's targets (hi coordinates) and its centre, the origin o
       for (int o = 16; o > 0; o >>= 1) {
         wmnx = fminf(wmnx, __shfl_xor_sync(0xffffffffu, wmnx, o));
         wmny = fminf(wmny, __shfl_xor_sync(0xffffffffu, wmny, o));
@@ -279,11 +374,14 @@ __global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(cons
         wmxz = fmaxf(wmxz, __shfl_xor_sync(0xffffffffu, wmxz, o));
       }
       const float ox = 0.5f * (wmnx + wmxx), oy = 0.5f * (wmny + wmxy), oz = 0.5f * (wmnz + wmxz);
-      // targets relative to o (the hi part of the exact split), |t'_hi|^2, largest |t'|
       float rw2 = 0.f;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float4 l = src_lo[S.src + (tix[k] < n ? tix[k] : t0)];
+        const int i = g0 + k * 32 + lane;
+        const float4 l = src_lo[S.src + (i < tb1 ? i : g0)];
+        // weight of the target as a source of the transposed terms: its charge (real pairs) or
+        // q_K |x| (Kelvin pairs); none for a slot past the block
+        wt[k] = i < tb1 ? (ch.type == 0 ? wt[k] : l.w) : 0.f;
         float lo;
         rel_split(tx[k], l.x, ox, tx[k], lo);
         rel_split(ty[k], l.y, oy, ty[k], lo);
@@ -293,12 +391,12 @@ __global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(cons
       }
       for (int o = 16; o > 0; o >>= 1) rw2 = fmaxf(rw2, __shfl_xor_sync(0xffffffffu, rw2, o));
       const float Rw = sqrtf(rw2) * 1.0001f + 1e-30f;
-      const long long box0 = S.bb + (ch.type == 1 ? (n + kBox - 1) / kBox : 0) + ch.first / kBox;
-      float4* bA = wA[warp];
-      float* bQ = wQ[warp];
-      float acc[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) acc[k] = 0.f;
+      // the first box's record
+      float4 rh = make_float4(0.f, 0.f, 0.f, 0.f), rl = rh;
+      if (lane < ch.count) {
+        rh = __ldg(gh + lane);
+        rl = __ldg(gl + lane);
+      }
       int code = kFormChecked;  // lane l: form of box (group + l) and, for a checked box,
       float thr = 0.f;          // the squared distance below which a pair takes the exact form
       for (int b = 0; b < nb; ++b) {
@@ -310,7 +408,7 @@ __global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(cons
           if (bl < nb) {
             const float4 bmn = __ldg(&boxes[2 * (box0 + bl)]), bmx = __ldg(&boxes[2 * (box0 + bl) + 1]);
             const int s0 = ch.first + bl * kBox;
-            const bool self = ch.type == 0 && s0 < w0 + 32 * K && w0 < s0 + kBox;
+            const bool self = ch.type == 0 && !sym && s0 < g0 + G && g0 < s0 + kBox;
             if (!self && bmn.x > bmx.x) {
               code = kFormExp;  // only zero-strength records (images of centre charges)
             } else {
@@ -341,60 +439,120 @@ __global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(cons
           nl = __ldg(gl + (b + 1) * kBox + lane);
         }
         __syncwarp();  // the previous box's sums have read the buffer
-        if (lane < cnt) {
-          const float sx = (rh.x - ox) + rl.x, sy = (rh.y - oy) + rl.y, sz = (rh.z - oz) + rl.z;
-          bA[lane] = make_float4(-2.f * sx, -2.f * sy, -2.f * sz, fmaf(sx, sx, fmaf(sy, sy, sz * sz)));
-          bQ[lane] = rh.w;
+        {
+          float4 a = make_float4(-2.0e18f, 0.f, 0.f, 1.0e36f);  // past the box: far away, no charge
+          float q = 0.f;
+          if (lane < cnt) {
+            const float sx = (rh.x - ox) + rl.x, sy = (rh.y - oy) + rl.y, sz = (rh.z - oz) + rl.z;
+            a = make_float4(-2.f * sx, -2.f * sy, -2.f * sz, fmaf(sx, sx, fmaf(sy, sy, sz * sz)));
+            q = rh.w;
+          }
+          bA[lane] = a;
+          bA[lane + kBox] = a;
+          bQ[lane] = q;
+          bQ[lane + kBox] = q;
         }
         __syncwarp();
-        if (form == kFormExp) {
-          box_pairs<K, kFormExp>(bA, bQ, cnt, tx, ty, tz, c, acc);
-        } else if (form == kFormMid) {
-          box_pairs<K, kFormMid>(bA, bQ, cnt, tx, ty, tz, c, acc);
-        } else {
-          unsigned mk[K];
+        unsigned mk[K];
 #pragma unroll
-          for (int k = 0; k < K; ++k) mk[k] = 0u;
-          if (cnt == kBox)
-            box_pairs_checked<K, true>(bA, bQ, cnt, thr2, tx, ty, tz, acc, mk);
-          else
-            box_pairs_checked<K, false>(bA, bQ, cnt, thr2, tx, ty, tz, acc, mk);
-          // the marked close pairs in the exact hi/lo form from the raw records (the self pair:
-          // no term)
-          const int sb = ch.first + b * kBox;
+        for (int k = 0; k < K; ++k) mk[k] = 0u;
+        if (!sym) {
+          if (form == kFormExp) {
+            box_oneway<K, kFormExp>(bA, bQ, cnt, tx, ty, tz, c, acc);
+          } else if (form == kFormMid) {
+            box_oneway<K, kFormMid>(bA, bQ, cnt, tx, ty, tz, c, acc);
+          } else {
+            box_oneway_checked<K>(bA, bQ, cnt, thr2, tx, ty, tz, acc, mk);
+            // the marked close pairs in the exact hi/lo form from the raw records (the self
+            // pair: no term)
+            const int sb = ch.first + b * kBox;
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            unsigned m = mk[k];
-            while (m) {
-              const int sx = __ffs(m) - 1;
-              m &= m - 1u;
-              const int ti = tix[k] < n ? tix[k] : t0;
-              float r2 = exact_r2(src_hi[S.src + ti], src_lo[S.src + ti], __ldg(gh + b * kBox + sx),
-                                  __ldg(gl + b * kBox + sx), ox, oy, oz);
-              if (ch.type == 0 && sb + sx == tix[k]) r2 = __int_as_float(0x7f800000);  // +inf
-              const float q = bQ[sx];
-              acc[k] = fmaf(q, rsqrt_mufu(r2), acc[k]);
+            for (int k = 0; k < K; ++k) {
+              unsigned m = mk[k];
+              const int ti = g0 + k * 32 + lane;
+              while (m) {
+                const int sx = __ffs(m) - 1;
+                m &= m - 1u;
+                const int tr = ti < tb1 ? ti : g0;
+                float r2 = exact_r2(src_hi[S.src + tr], src_lo[S.src + tr], __ldg(gh + b * kBox + sx),
+                                    __ldg(gl + b * kBox + sx), ox, oy, oz);
+                if (ch.type == 0 && sb + sx == ti) r2 = __int_as_float(0x7f800000);  // +inf
+                acc[k] = fmaf(bQ[sx], rsqrt_mufu(r2), acc[k]);
+              }
             }
+          }
+        } else {
+          float sacc;
+          if (form == kFormExp) {
+            sacc = box_ring<K, kFormExp, false>(bA, bQ, lane, thr2, tx, ty, tz, c, wt, acc, mk);
+          } else if (form == kFormMid) {
+            sacc = box_ring<K, kFormMid, false>(bA, bQ, lane, thr2, tx, ty, tz, c, wt, acc, mk);
+          } else {
+            sacc = box_ring<K, kFormMid, true>(bA, bQ, lane, thr2, tx, ty, tz, c, wt, acc, mk);
+            unsigned any = 0u;
+#pragma unroll
+            for (int k = 0; k < K; ++k) any |= mk[k];
+            if (__any_sync(0xffffffffu, any != 0u)) {
+              // the marked close pairs, both ways, in the exact form: a second ring carries the
+              // transposed terms to their sources in the same order
+              float fx = 0.f;
+              for (int j = 0; j < kBox; ++j) {
+                const int sx = (lane + j) & 31;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                  if ((mk[k] >> j) & 1u) {
+                    const int ti = g0 + k * 32 + lane;
+                    const int tr = ti < tb1 ? ti : g0;
+                    const float r2 = exact_r2(src_hi[S.src + tr], src_lo[S.src + tr], __ldg(gh + b * kBox + sx),
+                                              __ldg(gl + b * kBox + sx), ox, oy, oz);
+                    const float inv = rsqrt_mufu(r2);
+                    acc[k] = fmaf(bQ[sx], inv, acc[k]);
+                    fx = fmaf(wt[k], inv, fx);
+                  }
+                }
+                fx = __shfl_sync(0xffffffffu, fx, (lane + 1) & 31);
+              }
+              sacc += fx;
+            }
+          }
+          if (lane < cnt) {
+            float2 p = P[b * kBox + lane];
+            fold_two_sum(p.x, p.y, sacc);
+            P[b * kBox + lane] = p;
           }
         }
         if ((b + 1) % kFoldBoxes == 0 || b + 1 == nb) {
-          // two-sum fold of the group's partial
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            const float s = H[k] + acc[k];
-            const float bp = s - H[k];
-            L[k] += (H[k] - (s - bp)) + (acc[k] - bp);
-            H[k] = s;
+            fold_two_sum(H[k], L[k], acc[k]);
             acc[k] = 0.f;
           }
         }
         rh = nh;
         rl = nl;
       }
-    }
-    float2* out = part + S.part + (long long)it.z * n;
+      float2* out = part + S.part + (long long)it.z * n;
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (tix[k] < n) out[tix[k]] = make_float2(H[k], L[k]);
+      for (int k = 0; k < K; ++k) {
+        const int i = g0 + k * 32 + lane;
+        if (i < tb1) out[i] = make_float2(H[k], L[k]);
+      }
+    }
+    if (sym) {
+      // the transposed terms of the chunk's charges: the block's slot of their kind (the Kelvin
+      // sums scaled by 1 / |x_j|, stored with the Kelvin record)
+      __syncwarp();
+      float2* out = part + S.part + (long long)(ch.type == 0 ? blk : S.ncr + blk) * n + ch.first;
+      for (int j = lane; j < ch.count; j += 32) {
+        float2 p = P[j];
+        if (ch.type == 1) {
+          const float w = __ldg(gl + j).w;
+          p.x *= w;
+          p.y *= w;
+        }
+        out[j] = p;
+      }
+      __syncwarp();
+    }
   }
 }

@@ -411,15 +411,23 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
     const df kx = s * X, ky = s * Y, kz = s * Z;
     const df rK = df_make(S.f_a.x, S.f_a.y) * df_sqrt(s);
     const df QK = Q * (df_make(S.f_qk1.x, S.f_qk1.y) * rK + df_make(S.f_qk0.x, S.f_qk0.y));
+    // weights of the transposed Kelvin term of the symmetric pair sum (k_pairs_f32.cuh): by
+    // Kelvin inversion |x_j - x_i*| = |x_i - x_j*| |x_j| / |x_i|, so charge j's term from i's
+    // image is (q_K,i |x_i|) (1 / |x_i - x_j*|) (1 / |x_j|); the real record carries
+    // q_K,i |x_i|, the Kelvin record 1 / |x_j|
+    const df rr = df_sqrt(r2);
     if (on) {
       if (centre) {
         // image at infinity (its constant potential is added by k_moments): a zero-strength
-        // record, left out of the box
+        // record, left out of the box; its scale 1e15 / a turns 1 / |x_i - record| (the record
+        // sits at 1e15 a) into the limit 1 / a^2 of |x_i| / (|x_j| |x_i - x_j*|) at x_j -> 0
         src_hi[sk] = make_float4((float)(1e15 * S.a), 0.f, 0.f, 0.f);
-        src_lo[sk] = make_float4(0.f, 0.f, 0.f, 0.f);
+        src_lo[sk] = make_float4(0.f, 0.f, 0.f, (float)(1e15 * S.inv_a));
+        src_lo[sr].w = 0.f;
       } else {
         src_hi[sk] = make_float4(kx.hi, ky.hi, kz.hi, QK.hi);
-        src_lo[sk] = make_float4(kx.lo, ky.lo, kz.lo, 0.f);
+        src_lo[sk] = make_float4(kx.lo, ky.lo, kz.lo, df_recip(rr).hi);
+        src_lo[sr].w = (QK * rr).hi;
         bmin[3] = bmax[3] = kx.hi;
         bmin[4] = bmax[4] = ky.hi;
         bmin[5] = bmax[5] = kz.hi;

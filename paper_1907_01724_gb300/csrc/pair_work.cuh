@@ -4,10 +4,11 @@
 
 namespace hsma {
 
-// A list of pair work items.  Items [0, first) are the first items of CTAs 0 .. first - 1 of the
-// launch that has the list as w1 (no atomic: a grid-wide first fetch from one counter serialises
-// thousands of atomics); the rest are pulled through an atomic counter (zero before the first
-// launch that uses it) as first + counter.  counter == nullptr: no list.
+// A list of pair work items.  Items [0, first) are the first items of workers 0 .. first - 1 of
+// the launch that has the list as w1 (a worker is a CTA, or a warp of the FP32 pair kernel; no
+// atomic: a grid-wide first fetch from one counter serialises thousands of atomics); the rest are
+// pulled through an atomic counter (zero before the first launch that uses it) as first +
+// counter.  counter == nullptr: no list.
 struct PairWork {
   const int4* items;
   int nitems;

@@ -334,18 +334,20 @@ static int launch_moves(hsma_server_t* s, const std::vector<Pending>& batch)
   return HSMA_OK;
 }
 
-// Pair evaluations of one pair-sum item (targets x sources; a surface point counts once).
-static double item_pairs(const hsma::SysDev& d, const int4& it)
+// Pair evaluations of one pair-sum item (targets x sources, both ways for an off-diagonal
+// real/Kelvin item of the FP32 path; a surface point counts once).
+static double item_pairs(const hsma::SysDev& d, const int4& it, bool sym)
 {
-  const double nt = (double)std::min<int64_t>(d.tb, (int64_t)d.n - (int64_t)it.y * d.tb);
+  const bool rk = it.z < d.ncr + d.nck;
+  const int cb = it.z < d.ncr ? it.z : it.z - d.ncr;
+  const int64_t tbk = sym && rk ? d.chunk : d.tb;
+  const double nt = (double)std::min<int64_t>(tbk, (int64_t)d.n - (int64_t)it.y * tbk);
   int64_t ns;
-  if (it.z < d.ncr)
-    ns = std::min<int64_t>(d.chunk, (int64_t)d.n - (int64_t)it.z * d.chunk);
-  else if (it.z < d.ncr + d.nck)
-    ns = std::min<int64_t>(d.chunk, (int64_t)d.n - (int64_t)(it.z - d.ncr) * d.chunk);
+  if (rk)
+    ns = std::min<int64_t>(d.chunk, (int64_t)d.n - (int64_t)cb * d.chunk);
   else
     ns = std::min<int64_t>(d.chunk_s, (int64_t)d.M - (int64_t)(it.z - d.ncr - d.nck) * d.chunk_s);
-  return nt * (double)std::max<int64_t>(ns, 0);
+  return nt * (double)std::max<int64_t>(ns, 0) * (sym && rk && cb > it.y ? 2.0 : 1.0);
 }
 
 // --- one full-energy request on a slot ------------------------------------------------------
@@ -366,19 +368,22 @@ static int launch_energy(hsma_server_t* s, EnergySlot& sl, int chain)
   if (!it4.empty()) {
     const int occ = e->prec == HSMA_FP64 ? e->occ_f64 : e->occ_f32[e->L.cfg];
     const int cap = std::max(1, (int)std::floor(s->sm_frac * e->num_sms * std::max(occ, 1)));
+    const int nw = e->L.nw;  // workers per CTA
+    const bool sym = e->prec != HSMA_FP64;
     // chunks of consecutive items (the list is longest first) of about kEnergyChunkPairs each,
-    // but never fewer items than the capped grid has CTAs (every launch fills its grid)
+    // but never fewer items than the capped grid has workers (every launch fills its grid)
     const hsma::SysDev& d = e->L.sd[sys];
     int beg = 0;
     while (beg < (int)it4.size()) {
       int end = beg;
       double w = 0.0;
-      while (end < (int)it4.size() && (end - beg < cap || w + item_pairs(d, it4[end]) <= kEnergyChunkPairs))
-        w += item_pairs(d, it4[end++]);
+      while (end < (int)it4.size() &&
+             (end - beg < cap * nw || w + item_pairs(d, it4[end], sym) <= kEnergyChunkPairs))
+        w += item_pairs(d, it4[end++], sym);
       const int cnt = end - beg;
-      const int grid = std::max(1, std::min(cnt, cap));
+      const int grid = std::max(1, std::min((cnt + nw - 1) / nw, cap));
       SCK(cudaMemsetAsync(sl.ctr_d, 0, sizeof(unsigned int), sl.st));
-      const hsma::PairWork w1{sl.items_d + beg, cnt, sl.ctr_d, std::min(grid, cnt)}, none{nullptr, 0, nullptr, 0};
+      const hsma::PairWork w1{sl.items_d + beg, cnt, sl.ctr_d, std::min(grid * nw, cnt)}, none{nullptr, 0, nullptr, 0};
       if (e->prec == HSMA_FP64)
         hsma::launch_pairs_f64(grid, e->sys_d, w1, none, e->src64_d, e->surf64a_d, e->surf64b_d, e->part64_d, sl.st);
       else

@@ -54,8 +54,10 @@ def test_batch_matches_oracle_per_system(prec):
 
 @pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
 def test_batch_equals_alone(prec):
-    """Each system of a batch matches the same system evaluated alone (the split differs, so the
-    agreement is to the rounding of the path), and a batch is deterministic run to run."""
+    """Each system of a batch matches the same system evaluated alone, and a batch is deterministic
+    run to run.  The two evaluations split the sums differently (item sizes follow each system's
+    share of the work), so they agree to the rounding bound of the path (1e-6 norm-wise on the
+    FP32 path, the bound each of them meets against the oracle), not bitwise."""
     systems = mixed_systems(seed=9, sizes=(5, 640, 1500, 77))
     b = batch.from_systems(systems, precision=prec)
     n, xyz, q = batch.concat(systems)
@@ -64,7 +66,7 @@ def test_batch_equals_alone(prec):
     et, _ = b.hsma_batch_energy()
     b.hsma_batch_build_sources(n, xyz, q)
     assert np.array_equal(phi, b.hsma_batch_potential())
-    tol = {api.HSMA_FP32: 2e-7, api.HSMA_FP64: 1e-14}[prec]
+    tol = {api.HSMA_FP32: 1e-6, api.HSMA_FP64: 1e-14}[prec]
     off = 0
     for i, s in enumerate(systems):
         alone = api.solve(s, precision=prec)
