@@ -616,6 +616,11 @@ def run_ours(args):
             "frac_kernel_evals": ev_per_launch / t_pair / peak,
             "kernel_evals_note": "N(2N-1+M) evaluations per cavity: one rsqrt per pair, a surface point's "
                                  "monopole and dipole share one",
+            "unique_rsqrt_per_launch": sum(s.n * s.n + s.n * s.M for s in systems),
+            "frac_unique_rsqrt": sum(s.n * s.n + s.n * s.M for s in systems) / t_pair / peak,
+            "unique_rsqrt_note": "the rsqrt evaluations the kernel needs: real and Kelvin pairs once per unordered "
+                                 "pair (Newton's third law; Kelvin inversion), N(N-1)/2 + N(N+1)/2 + NM per cavity "
+                                 "(+ ~1% for the one-way diagonal blocks): the MUFU's own utilisation",
             "pair_kernel_ms": t_pair * 1e3, "pair_config": batch.pair_configs()[cfg], "pair_config_index": cfg,
             "pairs_per_launch": units,
             "timing": f"{nrep} launches in separate passes (L2 flushed before each step), CUDA events "
@@ -713,9 +718,10 @@ def main():
     ap.add_argument("--pair-config", type=int, default=-1,
                     help="with --only pairs: this tile configuration (index of batch.pair_configs()) instead "
                          "of the autotuned one")
-    ap.add_argument("--only", choices=["batched", "serving", "field", "near", "pairs"],
+    ap.add_argument("--only", choices=["batched", "serving", "field", "near", "pairs", "steps", "near_steps"],
                     help="run one section alone (profiling); 'pairs': the headline workload's pair kernel "
-                         "in separate passes (--steps launches)")
+                         "in separate passes (--steps launches); 'steps' / 'near_steps': --warmup + --steps "
+                         "whole-path steps of the headline / near-interface workload and nothing else")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.only:
@@ -732,6 +738,9 @@ def main():
             out = run_near_interface(0, st, name, args.steps)
         elif args.only == "pairs":
             out = run_pairs_only(0, st, name, args.steps, args.warmup, args.pair_config)
+        elif args.only in ("steps", "near_steps"):
+            wl = workload(0) if args.only == "steps" else near_interface_workload(0)
+            out = run_steps_only(0, st, name, wl, args.steps, args.warmup, args.pair_config)
         else:
             out = run_serving(0)
         print(json.dumps(out), flush=True)
@@ -770,6 +779,30 @@ def run_pairs_only(local, stream, gpu_name, steps, warmup, pair_config=-1):
     return {"workload": config_dict(systems, 1)["workload"], "pair_config": batch.pair_configs()[cfg],
             "pair_config_index": cfg,
             "pair_kernel_ms_mean": statistics.mean(ms) if ms else None, "launches": len(ms)}
+
+
+def run_steps_only(local, stream, gpu_name, systems, steps, warmup, pair_config=-1):
+    """warmup + steps whole-path steps (build + potentials, the overlapped graph) of a workload,
+    device inputs, nothing else (for launch lists); the tile configuration given or autotuned."""
+    import torch
+
+    from paper_1907_01724_gb300 import api, batch
+    n, xyz, q = batch.concat(systems)
+    b = batch.from_systems(systems, precision=api.HSMA_FP32, device=local, stream=stream)
+    if pair_config >= 0:
+        cfg = pair_config
+        b.hsma_batch_set_pair_config(cfg)
+    else:
+        cfg = batch.autotuned(b, n, xyz, q, gpu=gpu_name, reps=5)
+    xyz_d = torch.tensor(xyz, device=f"cuda:{local}")
+    q_d = torch.tensor(q, device=f"cuda:{local}")
+    phi_d = torch.empty(int(n.sum()), dtype=torch.float64, device=f"cuda:{local}")
+    for _ in range(warmup + steps):
+        b.hsma_batch_build_sources(n, xyz_d, q_d)
+        b.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
+    torch.cuda.synchronize()
+    return {"systems": len(systems), "N": [s.n for s in systems], "pair_config": batch.pair_configs()[cfg],
+            "pair_config_index": cfg, "steps": steps, "warmup": warmup}
 
 
 if __name__ == "__main__":

@@ -26,6 +26,12 @@ def case():
     near = inputs.near_interface_system(kappa_a=2.0)
     systems.append(inputs.System(xyz=near.xyz, q=near.q, a=near.a, eps1=near.eps1, eps2=near.eps2, kappa=near.kappa,
                                  p=12, M=400, tau=0.1))
+    # several blocks with a centre charge (image at infinity: exactly at the centre, and inside the
+    # centre threshold), so that the both-way Kelvin terms of centre charges are exercised
+    for c in ([0.0, 0.0, 0.0], [1e-13, -2e-13, 0.0]):
+        xyz = np.concatenate([inputs.uniform_ball(rng, 1299, 1.0), [c]])
+        systems.append(inputs.System(xyz=xyz, q=inputs.neutral_charges(rng, 1300), a=1.0, eps1=2.0, eps2=78.5,
+                                     kappa=1.0, p=12, M=400, tau=0.1))
     refs = []
     for s in systems:
         r = oracle.hsma(P_of(s), s.xyz, s.q)
