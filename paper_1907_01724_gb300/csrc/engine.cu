@@ -207,7 +207,17 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   int G = moment_smem_group(maxP_all, 1);
   if (totn_all > 4 * (int64_t)num_sms * G) G = moment_smem_group(maxP_all, 2);
   L.momG = G;
+  // FP32 moment units (k_moment_units): a warp per (tile of kg groups of 32 charges, column
+  // pair), kg chosen so that a launch has about 96 units per SM (a few per resident warp) or,
+  // for small engines, one group per tile
+  int kg = 1;
+  if (prec != HSMA_FP64) {
+    int64_t U1 = 0;
+    for (int s = 0; s < nsys; ++s) U1 += (ns[s] + 31) / 32 * moment_unit_pairs(spec[s].p);
+    kg = (int)std::max<int64_t>(1, U1 / (96 * (int64_t)num_sms));
+  }
   L.sd.resize(nsys);
+  int64_t zoff = 0;
   int64_t chg = 0, surf = 0, coef = 0, mn = 0, mom = 0, part = 0, boxes = 0;
   int k5 = 0;
   L.maxP = 1;
@@ -224,9 +234,12 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     d.prec = prec;
     d.chg = chg; d.src = 2 * chg; d.surf = surf; d.coef = coef; d.mn = mn;
     d.mom = mom;
-    // charges per moment block: enough blocks to cover the SMs twice over the whole engine,
-    // a multiple of the moment group G (charges whose solid harmonics a block forms at once)
-    {
+    // FP64 path: charges per moment block, enough blocks to cover the SMs twice over the whole
+    // engine, a multiple of the moment group G (charges whose solid harmonics a block forms at
+    // once); FP32 path: kg groups of 32 charges per moment row
+    if (prec != HSMA_FP64) {
+      d.mom_tile = 32 * kg;
+    } else {
       const double share = (double)n / std::max<double>((double)totn_all, 1.0);
       const int64_t want_blocks = std::max<int64_t>(1, (int64_t)std::llround(2.0 * num_sms * share));
       int64_t tile = (n + want_blocks - 1) / want_blocks;
@@ -235,6 +248,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
       d.mom_tile = (int)tile;
     }
     d.mom_blocks = (int)((n + d.mom_tile - 1) / d.mom_tile);
+    d.mzo = zoff;  // FP32 path (zoff advances with the unit items below)
     d.tb = TB;
     d.n_tb = (int)((n + TB - 1) / TB);
     if (n > 0) {
@@ -278,7 +292,15 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     d.k5_first = k5;
     d.k5_count = (int)((n + kReduceTargetsPerBlock - 1) / kReduceTargetsPerBlock);
     L.sd[s] = d;
-    for (int b = 0; b < d.mom_blocks; ++b) L.it12.push_back(make_int2(s, b));
+    if (prec == HSMA_FP64) {
+      for (int b = 0; b < d.mom_blocks; ++b) L.it12.push_back(make_int2(s, b));
+    } else {
+      for (int b = 0; b < (int)((n + kMomPrepThreads - 1) / kMomPrepThreads); ++b) L.it12.push_back(make_int2(s, b));
+      // (tiles < 2^24 for n <= 2^29 charges, pairs <= HSMA_P_MAX/2 + 1 < 2^7: fits an int)
+      for (int t = 0; t < d.mom_blocks; ++t)
+        for (int j = 0; j < moment_unit_pairs(sp.p); ++j) L.itmu.push_back(make_int2(s, (t << 7) | j));
+      zoff += (int64_t)(sp.p + 1) * n;
+    }
     for (int c = 0; c < (d.P + kCoefChunk - 1) / kCoefChunk; ++c) L.it2r.push_back(make_int2(s, c));
     for (int b = 0; b < (sp.M + kSurfPointsPerBlock - 1) / kSurfPointsPerBlock; ++b) L.it3.push_back(make_int2(s, b));
     for (int b = 0; b < d.k5_count; ++b) L.it5.push_back(make_int2(s, b));
@@ -371,11 +393,17 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
                    [&](const int4& x, const int4& y) { return cost_of(x, true) > cost_of(y, true); });
   L.it4fx = L.it4f;
   L.nRKf = (int)(std::stable_partition(L.it4fx.begin(), L.it4fx.end(), is_rk) - L.it4fx.begin());
+  {
+    int64_t maxn = 0;
+    for (const auto& d : L.sd) maxn = std::max<int64_t>(maxn, d.n);
+    L.order_smem_n = order_smem_charges(maxn);
+  }
   L.totN = chg;
   L.totM = surf;
   L.totP = coef;
   L.totMn = mn;
   L.totMom = mom;
+  L.totZ = zoff;
   L.totPart = part;
   L.totBoxes = boxes;
   L.mom_stride = (int)align_up((size_t)L.maxP + 1, 2);
@@ -399,6 +427,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_rec_a2 = take(8 * (size_t)ntri);
   L.o_rec_b2 = take(8 * (size_t)ntri);
   L.o_sect2 = take(8 * 4 * (size_t)(L.pmax + 1));  // sect2, the Legendre tables, sprod2
+  L.o_mtab = take(8 * 2 * (size_t)ntri);
   L.o_xyz = take(24 * L.totN);
   L.o_q = take(8 * L.totN);
   if (prec == HSMA_FP64) {
@@ -433,6 +462,13 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_dpart = take(8 * (size_t)L.ditem_cap);
   L.o_de = take(8 * (size_t)L.max_req);
   L.o_mom = take(8 * (size_t)L.totMom * L.mom_stride);
+  if (prec != HSMA_FP64) {
+    L.o_mgeo = take(16 * (size_t)L.totN);
+    L.o_mz = take(16 * (size_t)L.totZ);
+    L.o_mwq = take(8 * (size_t)L.totZ);
+    L.o_mcen = take(8 * (size_t)L.totN);
+    L.o_itmu = take(sizeof(int2) * L.itmu.size());
+  }
   L.o_coef = take(8 * L.totP);
   L.o_coef2 = take(8 * L.totP);
   L.o_sb = take(L.use_sb ? 8 * (size_t)L.totSB : 0);
@@ -486,6 +522,7 @@ void Engine::carve()
   rec_a2_d = (float2*)(b + L.o_rec_a2);
   rec_b2_d = (float2*)(b + L.o_rec_b2);
   sect2_d = (float2*)(b + L.o_sect2);
+  mtab_d = (float2*)(b + L.o_mtab);
   xyz_d = (double*)(b + L.o_xyz);
   q_d = (double*)(b + L.o_q);
   if (prec == HSMA_FP64) {
@@ -516,6 +553,18 @@ void Engine::carve()
   dpart_d = (double*)(b + L.o_dpart);
   de_d = (double*)(b + L.o_de);
   mom_d = (double*)(b + L.o_mom);
+  if (prec != HSMA_FP64) {
+    mgeo_d = (float4*)(b + L.o_mgeo);
+    mz_d = (float4*)(b + L.o_mz);
+    mwq_d = (float2*)(b + L.o_mwq);
+    mcen_d = (double*)(b + L.o_mcen);
+    itmu_d = (int2*)(b + L.o_itmu);
+  } else {
+    mgeo_d = mz_d = nullptr;
+    mwq_d = nullptr;
+    mcen_d = nullptr;
+    itmu_d = nullptr;
+  }
   coef_d = (double*)(b + L.o_coef);
   coef2_d = (float2*)(b + L.o_coef2);
   sb_d = L.use_sb ? (double*)(b + L.o_sb) : nullptr;
@@ -598,6 +647,8 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
   CK(cudaMemcpyAsync(sys_d, L.sd.data(), sizeof(SysDev) * L.sd.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it12.empty())
     CK(cudaMemcpyAsync(it12_d, L.it12.data(), sizeof(int2) * L.it12.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.itmu.empty())
+    CK(cudaMemcpyAsync(itmu_d, L.itmu.data(), sizeof(int2) * L.itmu.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it2r.empty())
     CK(cudaMemcpyAsync(it2r_d, L.it2r.data(), sizeof(int2) * L.it2r.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it3.empty())
@@ -626,7 +677,7 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
   out_cur = OutDesc{nullptr, nullptr, nullptr, 0, 0};
   // parameter-only quantities (scalars, M_n, tables, quadrature grid, surface basis), once per layout
   launch_setup(sys_d, (int)L.sd.size(), Mn_d, rec_a_d, rec_b_d, sect_d, inv_np1_d, rec_a2_d, rec_b2_d, sect2_d,
-               L.pmax, surfx_d, stream);
+               mtab_d, L.pmax, surfx_d, stream);
   CK(cudaGetLastError());
   launches += 1;
   if (L.use_sb && !L.itsb.empty()) {
@@ -655,8 +706,22 @@ Tables Engine::tables() const
   t.leg_b2 = sect2_d + 2 * (L.pmax + 1);
   t.sprod = sect_d + (L.pmax + 1);
   t.sprod2 = sect2_d + 3 * (L.pmax + 1);
+  t.mbeta2 = mtab_d;
+  t.mnrm2 = mtab_d + (L.pmax + 1) * (L.pmax + 2) / 2;
   t.pmax = L.pmax;
   return t;
+}
+
+void Engine::issue_moments()
+{
+  if (prec == HSMA_FP64) {
+    launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
+                   L.mom_stride, stream);
+    return;
+  }
+  launch_moment_prep(sys_d, it12_d, (int)L.it12.size(), xyz_d, q_d, Mn_d, mgeo_d, mz_d, mwq_d, mcen_d, stream);
+  launch_moment_units(sys_d, itmu_d, (int)L.itmu.size(), mgeo_d, mz_d, mwq_d, mcen_d, tables(), mom_d,
+                      L.mom_stride, stream);
 }
 
 void Engine::issue_build()
@@ -670,13 +735,12 @@ void Engine::issue_build()
     cudaStreamWaitEvent(side, ev_fork, 0);
     PriorityScope ps(prio_hi);
     launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
-                 xs_d, status_d, nullptr, 0, side);
+                 xs_d, status_d, nullptr, 0, L.order_smem_n, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
                   prec, status_d, side);
     cudaEventRecord(ev_join, side);
   }
-  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
-                 L.mom_stride, stream);
+  issue_moments();
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
   launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
@@ -687,7 +751,8 @@ void Engine::issue_build()
 int Engine::build_launch_count() const
 {
   // order: 2 kernels (k_order_keys, k_order_sort) and k_images
-  return (L.itord.empty() ? 0 : 3) + (L.it12.empty() ? 0 : 1) + (L.it2r.empty() ? 0 : 1) + (L.it3.empty() ? 0 : 1);
+  return (L.itord.empty() ? 0 : 3) + (L.it12.empty() ? 0 : 1) + (L.itmu.empty() ? 0 : 1) +
+         (L.it2r.empty() ? 0 : 1) + (L.it3.empty() ? 0 : 1);
 }
 
 void Engine::issue_pot()
@@ -759,7 +824,7 @@ void Engine::issue_fused()
   {
     PriorityScope ps(prio_hi);
     launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
-                 xs_d, status_d, ctr_pairs_d, 2, side);
+                 xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
                   prec, status_d, side);
   }
@@ -767,8 +832,7 @@ void Engine::issue_fused()
   launch_pair_items(rk, none, grid_rk, side);
   cudaEventRecord(ev_join, side);
   PriorityScope ps(prio_mid);
-  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
-                 L.mom_stride, stream);
+  issue_moments();
   // the records are joined before the coefficients (done by then), so that the main stream's
   // pair launch has a single dependency and starts as a programmatic dependent of the surface
   cudaStreamWaitEvent(stream, ev_img, 0);
@@ -1062,7 +1126,7 @@ void Engine::issue_field_fused()
   {
     PriorityScope ps(prio_hi);
     launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
-                 xs_d, status_d, ctr_pairs_d, 2, side);
+                 xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
                   prec, status_d, side);
   }
@@ -1070,8 +1134,7 @@ void Engine::issue_field_fused()
   launch_field_items(rk, none, grid_rk, side);
   cudaEventRecord(ev_join, side);
   PriorityScope ps(prio_mid);
-  launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
-                 L.mom_stride, stream);
+  issue_moments();
   cudaStreamWaitEvent(stream, ev_img, 0);  // (as in issue_fused)
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);

@@ -44,7 +44,10 @@ struct Layout {
   std::vector<int2> itsb;     // (representative system, point block) of every surface-basis table
   std::vector<int2> itord;    // (system, block of kOrderBlock charges): spatial order and records
   int64_t totBoxes = 0;       // 32-record boxes (real + Kelvin) of all systems
-  int momG = 1;               // charges per moment group (k_moments)
+  int momG = 1;               // charges per moment group (k_moments, FP64 path)
+  std::vector<int2> itmu;     // FP32 path: moment units (system, tile << 7 | column pair); it12
+                              // then holds the prep items (system, block of kMomPrepThreads)
+  int64_t totZ = 0;           // FP32 path: slots of the (p+1) x n moment tables of all systems
   bool use_sb = false;        // surface synthesis through the basis tables
   int64_t totSB = 0;          // 8-byte slots of all basis tables
   std::vector<int4> it4;
@@ -54,13 +57,15 @@ struct Layout {
   std::vector<int4> it4fx;    // it4f split as it4x
   int nRKf = 0;
   int nw = 1;                 // pair-kernel workers per CTA (FP32: warps)
+  int order_smem_n = 4096;    // charges k_order_sort keeps in shared memory (order_smem_charges)
   std::vector<int> sel;       // all systems, in order (energy pass of a full launch)
   std::vector<int2> selrng;   // their reduce-item ranges
   size_t o_sel = 0, o_selrng = 0;
   int cfg = 0, maxP = 1, pmax = 0, mom_stride = 3, pair_grid = 1;
   int64_t totN = 0, totM = 0, totP = 0, totMn = 0, totMom = 0, totPart = 0;
   size_t o_sys = 0, o_Mn = 0, o_rec_a = 0, o_rec_b = 0, o_sect = 0, o_inv_np1 = 0, o_xyz = 0, o_q = 0;
-  size_t o_rec_a2 = 0, o_rec_b2 = 0, o_sect2 = 0;
+  size_t o_rec_a2 = 0, o_rec_b2 = 0, o_sect2 = 0, o_mtab = 0;
+  size_t o_mgeo = 0, o_mz = 0, o_mwq = 0, o_mcen = 0, o_itmu = 0;
   size_t o_src64 = 0, o_surf64a = 0, o_surf64b = 0, o_part64 = 0;
   size_t o_srchi = 0, o_srclo = 0, o_surfa = 0, o_surfb = 0, o_part = 0;
   size_t o_surfx = 0, o_surfqd = 0, o_vsurf = 0;
@@ -123,6 +128,12 @@ class Engine {
   SysDev* sys_d = nullptr;
   double *Mn_d = nullptr, *rec_a_d = nullptr, *rec_b_d = nullptr, *sect_d = nullptr, *inv_np1_d = nullptr;
   float2 *rec_a2_d = nullptr, *rec_b2_d = nullptr, *sect2_d = nullptr;
+  float2* mtab_d = nullptr;        // rescaled moment chain: beta_nm, then e_nm sprod_m
+  // FP32 path: per-charge moment inputs (k_moment_prep) and the moment units
+  float4 *mgeo_d = nullptr, *mz_d = nullptr;
+  float2* mwq_d = nullptr;
+  double* mcen_d = nullptr;
+  int2* itmu_d = nullptr;
   double *xyz_d = nullptr, *q_d = nullptr;
   float4 *srchi_d = nullptr, *srclo_d = nullptr, *surfa_d = nullptr, *surfb_d = nullptr;
   dbl4 *src64_d = nullptr, *surf64a_d = nullptr;
@@ -226,6 +237,7 @@ class Engine {
 
  private:
   void carve();
+  void issue_moments();  // the moment rows (FP64: k_moments; FP32: k_moment_prep, k_moment_units)
   void issue_build();
   void issue_pot();
   void issue_field();

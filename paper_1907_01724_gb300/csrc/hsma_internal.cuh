@@ -110,9 +110,11 @@ struct SysDev {
   long long surf;     // offset of its M surface records
   long long coef;     // offset of its P = (p+1)^2 correction coefficients
   long long mn;       // offset of its p+1 Kirkwood coefficients M_n
-  long long mom;      // index of its first moment block
-  int mom_blocks;     // moment blocks (K12 CTAs) of this system
-  int mom_tile;       // charges per moment block
+  long long mom;      // index of its first moment row
+  int mom_blocks;     // moment rows of this system (FP64 path: one per k_moments block; FP32
+                      // path: one per tile of k_moment_units)
+  int mom_tile;       // charges per moment row
+  long long mzo;      // FP32 path: offset of its (p+1) x n moment tables (powers, weights)
   long long part;     // offset of its pair partials (n_chunks * n elements)
   int ncr, nck, ncs;  // source chunks: real, Kelvin, surface
   int chunk;          // sources per real/Kelvin chunk; FP32 path: also the targets per block of
@@ -145,12 +147,16 @@ constexpr int kOrderGrid = 16;
 constexpr int kOrderCells = kOrderGrid * kOrderGrid * kOrderGrid;
 constexpr int kOrderBlock = 256;  // charges per k_order_keys / k_images work item
 void init_order_kernels();  // one-time function attributes (call outside stream capture)
+// Charges of a system that k_order_sort sorts in shared memory at most (larger ones use the
+// scratch buffer), and the per-launch capacity for an engine whose largest system has max_n.
+constexpr int kOrderSmemMaxN = 24576;
+int order_smem_charges(int64_t max_n);
 // xs (FP32 path, else null): 2 float4 per charge in input order, the (hi, lo) split of
 // (x, y, z, q): xs[2 g] = hi parts, xs[2 g + 1] = lo parts.  status: kStOutside for a charge at
 // |x| >= a or with a non-finite coordinate or charge.
 void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, const double* q,
                   int* key, int* hist, int* scr, int* perm, int* iperm, float4* xs, int* status,
-                  unsigned int* ctr_reset, int nreset, cudaStream_t st);
+                  unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st);
 // Boxes of 32 consecutive sorted records: a warp's targets and a box farther apart than
 // kNearRel a use plain FP32 coordinates in the pair sum, nearer ones the hi/lo-split form.
 constexpr int kBox = 32;
@@ -173,6 +179,8 @@ struct Tables {
   const float2* leg_b2;   // (stored after sect2 in the same array)
   const double* sprod;    // sectoral normalisation prod_{k <= m} sect[k] (stored after sect)
   const float2* sprod2;   // the same as (hi, lo) (stored after leg_b2)
+  const float2* mbeta2;   // rescaled column chain of k_moment_units: beta_nm (index n(n+1)/2 + m)
+  const float2* mnrm2;    // and its factor e_nm sprod_m back to T_nm (k_setup)
   int pmax;
 };
 
@@ -181,7 +189,8 @@ void init_source_kernels();  // one-time function attributes (call outside strea
 // Parameter-only work, once per layout: derived scalars, M_n, recurrence tables and the
 // Fibonacci points/weights of every system (written to surfx).
 void launch_setup(SysDev* sys, int nsys, double* Mn, double* rec_a, double* rec_b, double* sect, double* inv_np1,
-                  float2* rec_a2, float2* rec_b2, float2* sect2, int pmax, dbl4* surfx, cudaStream_t st);
+                  float2* rec_a2, float2* rec_b2, float2* sect2, float2* mtab, int pmax, dbl4* surfx,
+                  cudaStream_t st);
 constexpr int kCoefChunk = 32;  // coefficients per k_coef_reduce block
 // Records at sorted positions (items = (system, block of kOrderBlock sorted positions)); the
 // FP32 path also writes the boxes (2 float4 per box: min and max of the hi coordinates).
@@ -194,6 +203,22 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
 void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const double* xyz,
                     const double* q, const double* Mn, Tables tab, int prec, double* mom, int mom_stride,
                     cudaStream_t st);
+// FP32 path, in two kernels.  k_moment_prep (items = (system, block of kMomPrepThreads charges)):
+// per charge its double-float moment inputs -- geo = (2w hi, 2w lo, rho^2 hi, rho^2 lo), the
+// powers (u + i v)^m (mz, (re hi, re lo, im hi, im lo)) and the weights q (M_n - gamma - c)
+// (mwq) for m, n = 0..p at mzo + (m or n) n_sys + i -- and its centre constant (mcen, FP64).
+// k_moment_units (units = (system, tile << 7 | column pair j), one warp each): row mom + tile of
+// the moments of the columns m = j and p - j over the tile's charges, and slot P (the centre
+// constants) for j = 0.  A programmatic dependent of the prep; its dependent may start at its end.
+constexpr int kMomPrepThreads = 128;
+constexpr int kMomUnitWarps = 8;
+constexpr int kMomUnitSteps = 8;  // chain steps per warp reduction (16 values)
+inline int moment_unit_pairs(int p) { return p / 2 + 1; }
+void launch_moment_prep(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
+                        const double* Mn, float4* geo, float4* mz, float2* mwq, double* mcen, cudaStream_t st);
+void launch_moment_units(const SysDev* sys, const int2* units, int nunits, const float4* geo,
+                         const float4* mz, const float2* mwq, const double* mcen, Tables tab, double* mom,
+                         int mom_stride, cudaStream_t st);
 int moment_smem_group(int maxP, int blocks_per_sm);
 // Moments are stored in the moment arithmetic (FP64 path: double; FP32 path: FP32 (hi, lo)
 // pairs), one 8-byte slot each; the coefficients as double (coef) and as (hi, lo) pairs (coef2).

@@ -16,6 +16,8 @@
 //                  rank; cells hold a few charges), which gives perm and iperm; it leaves the
 //                  histogram zeroed for the next build (zeroed once when the workspace is laid out)
 // Two kernels and no memsets: the order is on the critical path of the overlapped step.
+#include <algorithm>
+
 #include "fp32_pair.cuh"
 #include "hsma_internal.cuh"
 
@@ -69,19 +71,19 @@ __global__ __launch_bounds__(kKeyThreads) void k_order_keys(const SysDev* __rest
 
 // One block per system.  s_cell holds the first sorted position of every cell (exclusive scan
 // of the histogram), then (after the scatter) the end of every cell.  The scattered slots
-// (input index and cell) live in shared memory when the system has at most kOrderSmemN charges,
-// else in the scratch buffer scr (2 ints per charge); the keys of the first kKeyRegs
-// kSortThreads charges are held in registers between the two passes that use them.
+// (input index and cell) live in shared memory when the system has at most smem_n charges (the
+// launch's dynamic shared memory, sized by the engine for its largest system up to
+// kOrderSmemMaxN), else in the scratch buffer scr (2 ints per charge); the keys of the first
+// kKeyRegs kSortThreads charges are held in registers between the two passes that use them.
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kOrderSmemN = 4096;
-constexpr int kKeyRegs = kOrderSmemN / kSortThreads;
+constexpr int kKeyRegs = 4096 / kSortThreads;
 static_assert(kOrderCells % kSortThreads == 0, "cells split evenly over the sort block");
 
 __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __restrict__ sys,
                                                              const int* __restrict__ key, int* __restrict__ hist,
                                                              int* __restrict__ scr, int* __restrict__ perm,
-                                                             int* __restrict__ iperm)
+                                                             int* __restrict__ iperm, int smem_n)
 {
   __shared__ int s_cell[kOrderCells];
   __shared__ int s_wsum[kSortWarps];
@@ -94,8 +96,8 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
   // this grid (a programmatic launch of this kernel after k_order_keys put both blocks on one
   // SM beside a moment block: 3 us slower)
   allow_dependents();
-  int* slot = n <= kOrderSmemN ? s_slot : scr + 2 * c0;  // [n] input index, then [n] cell
-  int* skey = slot + (n <= kOrderSmemN ? kOrderSmemN : n);
+  int* slot = n <= smem_n ? s_slot : scr + 2 * c0;  // [n] input index, then [n] cell
+  int* skey = slot + (n <= smem_n ? smem_n : n);
   int* h = hist + (size_t)blockIdx.x * kOrderCells;
 
   // the keys (loads in flight beside the scan)
@@ -175,18 +177,24 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
 
 void init_order_kernels()
 {
-  cudaFuncSetAttribute(k_order_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * sizeof(int) * kOrderSmemN);
+  cudaFuncSetAttribute(k_order_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * sizeof(int) * kOrderSmemMaxN);
+}
+
+int order_smem_charges(int64_t max_n)
+{
+  int64_t c = std::max<int64_t>(4096, (max_n + 1023) / 1024 * 1024);
+  return (int)std::min<int64_t>(c, kOrderSmemMaxN);
 }
 
 void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, const double* q,
                   int* key, int* hist, int* scr, int* perm, int* iperm, float4* xs, int* status,
-                  unsigned int* ctr_reset, int nreset, cudaStream_t st)
+                  unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st)
 {
   if (nitems <= 0 || nsys <= 0) return;
   launch_k(k_order_keys, nitems * kKeySplit, kKeyThreads, 0, st, false, sys, items, xyz, q, key, hist, xs, status,
            ctr_reset, nreset);
-  launch_k(k_order_sort, nsys, kSortThreads, 2 * sizeof(int) * kOrderSmemN, st, false, sys, (const int*)key, hist, scr,
-           perm, iperm);
+  launch_k(k_order_sort, nsys, kSortThreads, 2 * sizeof(int) * (size_t)smem_n, st, false, sys, (const int*)key, hist,
+           scr, perm, iperm, smem_n);
 }
 
 }  // namespace hsma

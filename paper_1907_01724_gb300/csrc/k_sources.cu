@@ -55,10 +55,24 @@ __device__ __forceinline__ float2 pair_of(double x)
   return make_float2(hi, __double2float_rn(x - (double)hi));
 }
 
+// Vertical recurrence coefficients of the normalised solid harmonics below the diagonal:
+// T_nm = a_nm w T_{n-1,m} - b_nm rho^2 T_{n-2,m} (a_{m+1,m} = sqrt(2m+1), b_{m+1,m} = 0).
+__device__ __forceinline__ void rec_coef(int n, int m, double& A, double& B)
+{
+  A = 0.0;
+  B = 0.0;
+  if (n == m + 1) {
+    A = sqrt(2.0 * m + 1.0);
+  } else if (n >= m + 2) {
+    A = (2.0 * n - 1.0) / sqrt((double)(n - m) * (double)(n + m));
+    B = sqrt(((double)(n + m - 1) * (double)(n - m - 1)) / ((double)(n + m) * (double)(n - m)));
+  }
+}
+
 __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__ Mn, double* __restrict__ rec_a,
                         double* __restrict__ rec_b, double* __restrict__ sect, double* __restrict__ inv_np1,
                         float2* __restrict__ rec_a2, float2* __restrict__ rec_b2, float2* __restrict__ sect2,
-                        int pmax, dbl4* __restrict__ surfx)
+                        float2* __restrict__ mtab, int pmax, dbl4* __restrict__ surfx)
 {
   if (blockIdx.x == 0) {
     const int ntri = (pmax + 1) * (pmax + 2) / 2;
@@ -67,17 +81,29 @@ __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__
       while (n * (n + 1) / 2 > t) --n;
       while ((n + 1) * (n + 2) / 2 <= t) ++n;
       const int m = t - n * (n + 1) / 2;
-      double A = 0.0, B = 0.0;
-      if (n == m + 1) {
-        A = sqrt(2.0 * m + 1.0);
-      } else if (n >= m + 2) {
-        A = (2.0 * n - 1.0) / sqrt((double)(n - m) * (double)(n + m));
-        B = sqrt(((double)(n + m - 1) * (double)(n - m - 1)) / ((double)(n + m) * (double)(n - m)));
-      }
+      double A, B;
+      rec_coef(n, m, A, B);
       rec_a[t] = A;
       rec_b[t] = B;
       rec_a2[t] = pair_of(A);
       rec_b2[t] = pair_of(B);
+      // the rescaled column chain of k_moment_units: with e_nm = prod_{k=m+1..n} a_km / 2,
+      // S_n = T_nm / (e_nm sprod_m z^m) obeys S_n = 2 w S_{n-1} - beta_nm rho^2 S_{n-2},
+      // beta_nm = 4 b_nm / (a_nm a_{n-1,m}), S_m = 1 (no table factor left in the chain)
+      double e = 1.0, sp = 1.0, Ak, Bk;
+      for (int k = m + 1; k <= n; ++k) {
+        rec_coef(k, m, Ak, Bk);
+        e *= 0.5 * Ak;
+      }
+      for (int k = 2; k <= m; ++k) sp *= sqrt((2.0 * k - 1.0) / (2.0 * k));
+      double beta = 0.0;
+      if (n >= m + 2) {
+        double A1, B1;
+        rec_coef(n - 1, m, A1, B1);
+        beta = 4.0 * B / (A * A1);
+      }
+      mtab[t] = pair_of(beta);
+      mtab[ntri + t] = pair_of(e * sp);
     }
     for (int m = threadIdx.x; m <= pmax; m += blockDim.x) {
       sect[m] = (m >= 2) ? sqrt((2.0 * m - 1.0) / (2.0 * m)) : 1.0;
@@ -133,10 +159,11 @@ __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__
 }
 
 void launch_setup(SysDev* sys, int nsys, double* Mn, double* rec_a, double* rec_b, double* sect, double* inv_np1,
-                  float2* rec_a2, float2* rec_b2, float2* sect2, int pmax, dbl4* surfx, cudaStream_t st)
+                  float2* rec_a2, float2* rec_b2, float2* sect2, float2* mtab, int pmax, dbl4* surfx, cudaStream_t st)
 {
   const int blocks = nsys < 4096 ? (nsys > 0 ? nsys : 1) : 4096;
-  k_setup<<<blocks, 256, 0, st>>>(sys, nsys, Mn, rec_a, rec_b, sect, inv_np1, rec_a2, rec_b2, sect2, pmax, surfx);
+  k_setup<<<blocks, 256, 0, st>>>(sys, nsys, Mn, rec_a, rec_b, sect, inv_np1, rec_a2, rec_b2, sect2, mtab, pmax,
+                                  surfx);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -461,6 +488,27 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
            src64, boxes, prec, status);
 }
 
+// Moment inputs of one charge in double-float: u, v, w = x/a, rho^2 = |x|^2/a^2, q and q c with
+// c = dbar (R_tau r/a^2 - 1)/2, from the split FP64 inputs (four FP64 conversions per charge;
+// this GPU issues FP64 arithmetic at a small fraction of the FP32 rate).
+struct MomentInputs {
+  df u, v, w, rho2, q, qc;
+};
+__device__ __forceinline__ MomentInputs moment_inputs_df(const SysDev& S, double x, double y, double z, double qi)
+{
+  MomentInputs r;
+  const df ia = df_from_double(S.inv_a);
+  r.u = df_from_double(x) * ia;
+  r.v = df_from_double(y) * ia;
+  r.w = df_from_double(z) * ia;
+  r.rho2 = r.u * r.u + r.v * r.v + r.w * r.w;
+  r.q = df_from_double(qi);
+  const df rr = r.rho2.hi > 0.f ? df_sqrt(r.rho2) : df_make(0.f, 0.f);
+  const df c = df_from_double(0.5 * S.dbar) * (df_from_double(S.Rt_a) * rr - df_make(1.f, 0.f));
+  r.qc = r.q * c;
+  return r;
+}
+
 // Charge moments of the correction coefficients.  Thread t of a block prepares charge c0 + t:
 // the centre constant of a charge at the centre, and its moment inputs u, v, w = x/a, rho^2, q
 // and q c in the moment arithmetic R (shared memory), so the moment phase runs on R alone: per
@@ -484,6 +532,7 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   static_assert(sizeof(R) == sizeof(double), "moment arithmetic uses 8-byte values");
+  static_assert(!Num<R>::is_df, "the FP32 path forms its moments in k_moment_units");
   R* T = reinterpret_cast<R*>(sm);  // [G][P]
   R* cu = T + (size_t)G * P;        // per charge of the tile: u, v, w, rho^2, q, q c
   R* cv = cu + kMomThreads;
@@ -533,31 +582,14 @@ __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restric
     const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
     const double rc = kCentreRel * S.a;
     if (r2 <= 4.0 * rc * rc && sqrt(r2) <= rc) r0 += S.kc_a * qi * (S.gam - 0.5 * dbar);
-    if (Num<R>::is_df) {
-      // u, v, w, rho^2 and q c in double-float from the split inputs (four FP64 conversions
-      // per charge; this GPU issues FP64 arithmetic at a small fraction of the FP32 rate)
-      const df ia = df_from_double(inv_a);
-      const df u = df_from_double(x) * ia, v = df_from_double(y) * ia, w = df_from_double(z) * ia;
-      const df rho2 = u * u + v * v + w * w;
-      const df qd = df_from_double(qi);
-      const df rr = rho2.hi > 0.f ? df_sqrt(rho2) : df_make(0.f, 0.f);
-      const df c = df_from_double(0.5 * dbar) * (df_from_double(S.Rt_a) * rr - df_make(1.f, 0.f));
-      cu[tid] = Num<R>::from_df(u);
-      cv[tid] = Num<R>::from_df(v);
-      cw[tid] = Num<R>::from_df(w);
-      cr2[tid] = Num<R>::from_df(rho2);
-      cq[tid] = Num<R>::from_df(qd);
-      cqc[tid] = Num<R>::from_df(qd * c);
-    } else {
-      const double r = sqrt(r2);
-      const double ux = x * inv_a, uy = y * inv_a, uz = z * inv_a;
-      cu[tid] = Num<R>::from(ux);
-      cv[tid] = Num<R>::from(uy);
-      cw[tid] = Num<R>::from(uz);
-      cr2[tid] = Num<R>::from(ux * ux + uy * uy + uz * uz);
-      cq[tid] = Num<R>::from(qi);
-      cqc[tid] = Num<R>::from(qi * (dbar * (S.Rt_a * (r * inv_a) - 1.0) * 0.5));
-    }
+    const double r = sqrt(r2);
+    const double ux = x * inv_a, uy = y * inv_a, uz = z * inv_a;
+    cu[tid] = Num<R>::from(ux);
+    cv[tid] = Num<R>::from(uy);
+    cw[tid] = Num<R>::from(uz);
+    cr2[tid] = Num<R>::from(ux * ux + uy * uy + uz * uz);
+    cq[tid] = Num<R>::from(qi);
+    cqc[tid] = Num<R>::from(qi * (dbar * (S.Rt_a * (r * inv_a) - 1.0) * 0.5));
   }
   if (tid <= p) mg[tid] = Num<R>::from(Mn[S.mn + tid] - S.gam);
   // block sum of the centre-charge constants (fixed order), reduced only when some charge of
@@ -664,11 +696,9 @@ static void launch_mom(const SysDev* sys, const int2* items, int nitems, int max
                        cudaStream_t st)
 {
   const size_t smem = moment_smem_bytes(maxP, G);
-  if (prec == HSMA_FP64)
-    launch_k(k_moments<MAXJ, double>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, Mn, tab, mom, mom_stride,
-             G);
-  else
-    launch_k(k_moments<MAXJ, df>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, Mn, tab, mom, mom_stride, G);
+  (void)prec;  // FP64 only (the FP32 path: launch_moment_prep, launch_moment_units)
+  launch_k(k_moments<MAXJ, double>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, Mn, tab, mom, mom_stride,
+           G);
 }
 
 void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const double* xyz,
@@ -689,6 +719,214 @@ void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, 
     launch_mom<16>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
   else
     launch_mom<26>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+}
+
+// ---------------------------------------------------------------------------------------
+// FP32 path: the moment rows in double-float, lane = charge.  The unnormalised column chains
+// share nothing between charges, so a warp takes 32 charges of one column pair and forms the
+// 32 charges' terms of each coefficient side by side, then sums them across the lanes with a
+// transposed warp reduction; no shared memory and no block barrier, every lane busy.
+//
+// k_moment_prep, one thread per charge: the inputs that every column of the charge reuses.
+__global__ __launch_bounds__(kMomPrepThreads) void k_moment_prep(const SysDev* __restrict__ sys,
+                                                                 const int2* __restrict__ items,
+                                                                 const double* __restrict__ xyz,
+                                                                 const double* __restrict__ q,
+                                                                 const double* __restrict__ Mn,
+                                                                 float4* __restrict__ geo, float4* __restrict__ mz,
+                                                                 float2* __restrict__ mwq, double* __restrict__ mcen)
+{
+  static_assert(kMomPrepThreads > HSMA_P_MAX, "one thread per degree for M_n - gamma");
+  __shared__ df smg[kMomPrepThreads];  // M_n - gamma
+  const int2 it = items[blockIdx.x];
+  const SysDev& S = sys[it.x];
+  const int ns = S.n, p = S.p;
+  const int i = it.y * kMomPrepThreads + threadIdx.x;
+  if ((int)threadIdx.x <= p) smg[threadIdx.x] = df_from_double(Mn[S.mn + threadIdx.x] - S.gam);
+  // every block of the grid is resident once this is reached: the unit kernel's blocks may
+  // start (they wait for this grid's writes before reading them)
+  allow_dependents();
+  __syncthreads();
+  if (i >= ns) return;
+  const long long gi = S.chg + i;
+  const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
+  // the centre constant of a charge whose image is at infinity (as in k_moments and kelvin_rec)
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+  const double rc = kCentreRel * S.a;
+  mcen[gi] = (r2 <= 4.0 * rc * rc && sqrt(r2) <= rc) ? S.kc_a * qi * (S.gam - 0.5 * S.dbar) : 0.0;
+  const MomentInputs mi = moment_inputs_df(S, x, y, z, qi);
+  geo[gi] = make_float4(2.f * mi.w.hi, 2.f * mi.w.lo, mi.rho2.hi, mi.rho2.lo);
+  const long long zb = S.mzo + i;
+  df zr = df_make(1.f, 0.f), zi = df_make(0.f, 0.f);
+  for (int m = 0; m <= p; ++m) {
+    mz[zb + (long long)m * ns] = make_float4(zr.hi, zr.lo, zi.hi, zi.lo);
+    const df nr = df_mul_sub(zr, mi.u, zi, mi.v);
+    const df ni = df_mul_sub(zr, mi.v, -zi, mi.u);
+    zr = nr;
+    zi = ni;
+  }
+  for (int n = 0; n <= p; ++n) {
+    const df wq = df_mul_sub(mi.q, smg[n], df_make(1.f, 0.f), mi.qc);
+    mwq[zb + (long long)n * ns] = make_float2(wq.hi, wq.lo);
+  }
+}
+
+// a + b with the low parts summed, not renormalised (the caller renormalises once)
+__device__ __forceinline__ df df_add_lazy(df a, df b)
+{
+  const df s = two_sum(a.hi, b.hi);
+  return df_make(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ df shfl_xor_df(df v, int o)
+{
+  return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
+// One level of the transposed reduction: lanes with bit H of the lane set keep the upper half
+// of the H-pair window of v and send the lower half to the partner lane ^ H (and vice versa).
+template <int H>
+__device__ __forceinline__ void treduce_level(df* v, bool upper)
+{
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const df keep = upper ? v[H + k] : v[k];
+    const df send = upper ? v[k] : v[H + k];
+    v[k] = df_add_lazy(keep, shfl_xor_df(send, 2 * H));
+  }
+}
+
+// Sum over the 32 lanes of each of the 16 values v[0..15] of a lane: afterwards lane l holds
+// the sum of value (l >> 1) & 15 (lanes l and l ^ 1 the same) in v[0], renormalised.  Fixed
+// order: the result does not depend on scheduling.
+__device__ __forceinline__ df warp_treduce16(df* v, int lane)
+{
+  treduce_level<8>(v, (lane & 16) != 0);
+  treduce_level<4>(v, (lane & 8) != 0);
+  treduce_level<2>(v, (lane & 4) != 0);
+  treduce_level<1>(v, (lane & 2) != 0);
+  return df_norm(df_add_lazy(v[0], shfl_xor_df(v[0], 1)));
+}
+
+// k_moment_units: the unit's steps are the column m1 = j (n = m1..p), then the column m2 = p - j
+// (n = m2..p) unless it is the same column; a batch of kMomUnitSteps steps gives 16 values per
+// lane (real and sine parts) that warp_treduce16 sums over the lanes, and the running sum of a
+// batch's values over the tile's groups of 32 charges stays in the warp's shared memory (lane l:
+// value (l >> 1) & 15).  The chain runs on S_n = T_nm / (e_nm sprod_m z^m) (k_setup), the step's
+// term is q (M_n - gamma - c) S_n z^m, and the row value is that sum times e_nm sprod_m (mnrm2).
+constexpr int kMomUnitMaxBatches = (HSMA_P_MAX + 2 + kMomUnitSteps - 1) / kMomUnitSteps;
+__global__ __launch_bounds__(kMomUnitWarps * 32) void k_moment_units(
+    const SysDev* __restrict__ sys, const int2* __restrict__ units, int nunits, const float4* __restrict__ geo,
+    const float4* __restrict__ mz, const float2* __restrict__ mwq, const double* __restrict__ mcen, Tables tab,
+    double* __restrict__ mom, int mom_stride)
+{
+  constexpr int ST = kMomUnitSteps;
+  __shared__ float2 sacc[kMomUnitWarps][kMomUnitMaxBatches][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int u = blockIdx.x * kMomUnitWarps + warp;
+  if (u >= nunits) return;
+  const int2 it = units[u];
+  const SysDev& S = sys[it.x];
+  const int ns = S.n, p = S.p;
+  const int tile = it.y >> 7, j = it.y & 127;
+  const int m1 = j, m2 = p - j;
+  const int L1 = p - m1 + 1;
+  const int L = m2 != m1 ? p + 2 : L1;
+  const int nbat = (L + ST - 1) / ST;
+  const int cb = tile * S.mom_tile, ce = min(ns, cb + S.mom_tile);
+  const float2* __restrict__ beta = tab.mbeta2;
+  float2* acc = &sacc[warp][0][lane];  // acc[32 b]: batch b
+  for (int b = 0; b < nbat; ++b) acc[32 * b] = make_float2(0.f, 0.f);
+  grid_dependency_wait();  // the prep's tables
+
+  double cen = 0.0;
+  for (int c0 = cb; c0 < ce; c0 += 32) {
+    const int i = c0 + lane;
+    const bool live = i < ce;
+    const long long zb = S.mzo + i;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 g = live ? geo[S.chg + i] : zero4;
+    const float4 z1 = live ? mz[zb + (long long)m1 * ns] : zero4;
+    const float4 z2 = live ? mz[zb + (long long)m2 * ns] : zero4;
+    if (j == 0 && live) cen += mcen[S.chg + i];
+    const df W = df_make(g.x, g.y), R2 = df_make(g.z, g.w);
+    df qa = df_make(0.f, 0.f), qb = df_make(0.f, 0.f);  // S_{n-1}, S_{n-2}
+#pragma unroll 1
+    for (int b = 0; b < nbat; ++b) {
+      df v[2 * ST];
+#pragma unroll
+      for (int k = 0; k < ST; ++k) {
+        const int s = b * ST + k;
+        v[2 * k] = df_make(0.f, 0.f);
+        v[2 * k + 1] = df_make(0.f, 0.f);
+        if (s < L) {
+          const bool second = s >= L1;
+          const int m = second ? m2 : m1;
+          const int n = second ? m2 + (s - L1) : m1 + s;
+          df cur;
+          if (n == m) {
+            cur = df_make(1.f, 0.f);
+            qa = df_make(0.f, 0.f);
+          } else {
+            const float2 bt = beta[n * (n + 1) / 2 + m];
+            cur = df_mul_sub(W, qa, df_make(bt.x, bt.y) * R2, qb);
+          }
+          qb = qa;
+          qa = cur;
+          const float2 wv = live ? mwq[zb + (long long)n * ns] : make_float2(0.f, 0.f);
+          const float4 zz = second ? z2 : z1;
+          const df t = df_make(wv.x, wv.y) * cur;
+          v[2 * k] = t * df_make(zz.x, zz.y);
+          v[2 * k + 1] = t * df_make(zz.z, zz.w);
+        }
+      }
+      const df r = warp_treduce16(v, lane);
+      const float2 a = acc[32 * b];
+      const df sum = df_make(a.x, a.y) + r;
+      acc[32 * b] = make_float2(sum.hi, sum.lo);
+    }
+  }
+  // the coefficient kernel may launch once every unit is here
+  allow_dependents();
+  double* out = mom + (size_t)(S.mom + tile) * mom_stride;
+  if ((lane & 1) == 0) {
+    const int part = (lane >> 1) & 1;  // 0: cosine (real) part, 1: sine part
+    for (int b = 0; b < nbat; ++b) {
+      const int s = b * ST + (lane >> 2);
+      if (s < L) {
+        const bool second = s >= L1;
+        const int m = second ? m2 : m1;
+        const int n = second ? m2 + (s - L1) : m1 + s;
+        if (!(part && m == 0)) {
+          const float2 f = tab.mnrm2[n * (n + 1) / 2 + m];
+          const float2 a = acc[32 * b];
+          const df val = df_make(a.x, a.y) * df_make(f.x, f.y);
+          reinterpret_cast<float2*>(out)[n * n + n + (part ? -m : m)] = make_float2(val.hi, val.lo);
+        }
+      }
+    }
+  }
+  if (j == 0) {
+    for (int o = 16; o > 0; o >>= 1) cen += __shfl_xor_sync(0xffffffffu, cen, o);
+    if (lane == 0) out[S.P] = cen;
+  }
+}
+
+void launch_moment_prep(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
+                        const double* Mn, float4* geo, float4* mz, float2* mwq, double* mcen, cudaStream_t st)
+{
+  if (nitems <= 0) return;
+  launch_k(k_moment_prep, nitems, kMomPrepThreads, 0, st, false, sys, items, xyz, q, Mn, geo, mz, mwq, mcen);
+}
+
+void launch_moment_units(const SysDev* sys, const int2* units, int nunits, const float4* geo,
+                         const float4* mz, const float2* mwq, const double* mcen, Tables tab, double* mom,
+                         int mom_stride, cudaStream_t st)
+{
+  if (nunits <= 0) return;
+  const int grid = (nunits + kMomUnitWarps - 1) / kMomUnitWarps;
+  launch_pdl(k_moment_units, grid, kMomUnitWarps * 32, 0, st, sys, units, nunits, geo, mz, mwq, mcen, tab, mom,
+             mom_stride);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1006,22 +1244,22 @@ void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, 
 }
 
 template <class R>
-static void moment_attrs()
+static void surface_attrs()
 {
-  cudaFuncSetAttribute(k_moments<1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_moments<2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_moments<4, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_moments<8, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_moments<16, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_moments<26, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_surface<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
   cudaFuncSetAttribute(k_surface_mat<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
 }
 
 void init_source_kernels()
 {
-  moment_attrs<double>();
-  moment_attrs<df>();
+  cudaFuncSetAttribute(k_moments<1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<4, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<8, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<16, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_moments<26, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  surface_attrs<double>();
+  surface_attrs<df>();
 }
 
 }  // namespace hsma

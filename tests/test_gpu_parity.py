@@ -207,15 +207,15 @@ def test_kernel_launch_accounting():
     api.hsma_build_sources(h, s.xyz, s.q)
     api.hsma_energy(h)
     # once per layout: k_setup, k_surface_basis; build: k_order_keys, k_order_sort, k_images,
-    # k_moments, k_coef_reduce, k_surface_mat; potentials (overlapped with the build): k_pairs
-    # (real/Kelvin items, capped grid), k_pairs (surface items, then the real/Kelvin items
-    # left), k_reduce
-    assert api.hsma_kernel_launches(h) == 11
+    # k_moment_prep, k_moment_units, k_coef_reduce, k_surface_mat; potentials (overlapped with
+    # the build): k_pairs (real/Kelvin items, capped grid), k_pairs (surface items, then the
+    # real/Kelvin items left), k_reduce
+    assert api.hsma_kernel_launches(h) == 12
     api.hsma_set_overlap(h, False)
     api.hsma_build_sources(h, s.xyz, s.q)
     api.hsma_energy(h)
-    # separate passes: the 6 build kernels, then k_pairs and k_reduce
-    assert api.hsma_kernel_launches(h) == 11 + 8
+    # separate passes: the 7 build kernels, then k_pairs and k_reduce
+    assert api.hsma_kernel_launches(h) == 12 + 9
 
 
 @pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
