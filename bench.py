@@ -65,6 +65,11 @@ def evals(s) -> int:
     return s.n * (2 * s.n - 1 + s.M)
 
 
+# the sources of the FP32 pair kernel, in the order its committed ncu summary hashes them
+PAIR_KERNEL_SOURCES = ("k_pairs.cu", "k_pairs_f32.cuh", "pair_work.cuh", "fp32_pair.cuh", "df64.cuh",
+                       "hsma_internal.cuh")
+
+
 def kernel_source_sha(paths) -> str:
     """sha256 of the concatenated sources of a kernel (recorded with each committed ncu summary)."""
     import hashlib
@@ -605,7 +610,7 @@ def run_ours(args):
     achieved = units / t_pair
     ev_per_launch = sum(evals(s) for s in systems)
     csrc = os.path.join(ROOT, "paper_1907_01724_gb300", "csrc")
-    traffic = profiled_traffic([os.path.join(csrc, f) for f in ("k_pairs.cu", "k_pairs_f32.cuh", "pair_work.cuh", "fp32_pair.cuh")],
+    traffic = profiled_traffic([os.path.join(csrc, f) for f in PAIR_KERNEL_SOURCES],
                                os.path.join(ROOT, "profiles", "k_pairs_f32_N20000_M2000_p30.md"))
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-eval/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",

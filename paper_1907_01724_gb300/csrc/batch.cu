@@ -23,7 +23,47 @@ namespace hsma {
 // runs (the configuration sets the pair items that overlap the coefficient chain); with overlap
 // off, the potential pass alone (pair sum plus the reduction of its partials).  The inputs (xyz,
 // q) sit before every configuration-dependent buffer of the workspace, so each configuration
-// rebuilds its sources from them in place.
+// rebuilds its sources from them in place.  A sweep takes the median of reps steps per
+// configuration; the kTuneFinal fastest are then timed again in interleaved rounds (one step of
+// each per round, 2 reps rounds), so that a drift of the clocks over the sweep does not decide
+// between configurations a few percent apart.
+constexpr int kTuneFinal = 3;
+
+int Engine::tune_time_config(int c, int steps, std::vector<float>& t)
+{
+  forced_cfg = c;
+  layout_uploaded = false;
+  const std::vector<int64_t> ns = cur_ns;
+  int rc = set_sizes(ns);
+  if (rc) return rc;
+  rc = run_graph(&g_build, &Engine::issue_build);
+  if (rc) return rc;
+  sources_ready = true;
+  build_pending = false;
+  for (int r = 0; r < steps + 1; ++r) {
+    pot_ready = false;
+    float ms = 0.f;
+    if (overlap) {
+      build_pending = true;
+      cudaError_t e = cudaEventRecord(ev_tune0, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord (autotune)");
+      rc = potentials();
+      if (rc) return rc;
+      e = cudaEventRecord(ev_tune1, stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev_tune1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev_tune0, ev_tune1);
+      if (e != cudaSuccess) return cuda_fail(e, "timing (autotune)");
+    } else {
+      rc = potentials();
+      if (rc) return rc;
+      rc = last_pot_time(&ms);
+      if (rc) return rc;
+    }
+    if (r > 0) t.push_back(ms);  // the first step after a rebuild is a warm-up
+  }
+  return HSMA_OK;
+}
+
 int Engine::autotune(int reps, int* best_out, float* best_ms_out)
 {
   if (prec == HSMA_FP64) return fail(HSMA_E_INVALID_ARG, "autotuning applies to the FP32 pair sum");
@@ -47,45 +87,36 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
     ws_cap = need;
     ws_owned = true;
   }
-  int best = -1;
-  float best_ms = 0.f;
   const int saved_forced = forced_cfg;
-  for (int c = 0; c < pair_config_count(); ++c) {
-    forced_cfg = c;
-    layout_uploaded = false;
-    int rc = set_sizes(ns);
-    if (rc) return rc;
-    rc = run_graph(&g_build, &Engine::issue_build);
-    if (rc) return rc;
-    sources_ready = true;
-    build_pending = false;
-    std::vector<float> t;
-    for (int r = 0; r < reps + 1; ++r) {
-      pot_ready = false;
-      float ms = 0.f;
-      if (overlap) {
-        build_pending = true;
-        cudaError_t e = cudaEventRecord(ev_tune0, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord (autotune)");
-        rc = potentials();
-        if (rc) return rc;
-        e = cudaEventRecord(ev_tune1, stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev_tune1);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev_tune0, ev_tune1);
-        if (e != cudaSuccess) return cuda_fail(e, "timing (autotune)");
-      } else {
-        rc = potentials();
-        if (rc) return rc;
-        rc = last_pot_time(&ms);
-        if (rc) return rc;
-      }
-      if (r > 0) t.push_back(ms);
-    }
+  auto median = [](std::vector<float>& t) {
     std::sort(t.begin(), t.end());
-    const float med = t[t.size() / 2];
-    if (best < 0 || med < best_ms) {
-      best = c;
-      best_ms = med;
+    return t[t.size() / 2];
+  };
+  std::vector<std::pair<float, int>> sweep;
+  for (int c = 0; c < pair_config_count(); ++c) {
+    std::vector<float> t;
+    int rc = tune_time_config(c, reps, t);
+    if (rc) return rc;
+    sweep.emplace_back(median(t), c);
+  }
+  std::sort(sweep.begin(), sweep.end());
+  const int nfin = std::min<int>(kTuneFinal, (int)sweep.size());
+  std::vector<std::vector<float>> tf(nfin);
+  for (int round = 0; round < 2 * reps && nfin > 1; ++round)
+    for (int k = 0; k < nfin; ++k) {
+      int rc = tune_time_config(sweep[k].second, 1, tf[k]);
+      if (rc) return rc;
+    }
+  int best = sweep[0].second;
+  float best_ms = sweep[0].first;
+  if (nfin > 1) {
+    best_ms = -1.f;
+    for (int k = 0; k < nfin; ++k) {
+      const float med = median(tf[k]);
+      if (best_ms < 0.f || med < best_ms) {
+        best = sweep[k].second;
+        best_ms = med;
+      }
     }
   }
   forced_cfg = saved_forced;

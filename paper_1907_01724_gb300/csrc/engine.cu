@@ -295,7 +295,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     if (prec == HSMA_FP64) {
       for (int b = 0; b < d.mom_blocks; ++b) L.it12.push_back(make_int2(s, b));
     } else {
-      for (int b = 0; b < (int)((n + kMomPrepThreads - 1) / kMomPrepThreads); ++b) L.it12.push_back(make_int2(s, b));
+      for (int b = 0; b < (int)((n + kMomPrepCharges - 1) / kMomPrepCharges); ++b) L.it12.push_back(make_int2(s, b));
       // (tiles < 2^24 for n <= 2^29 charges, pairs <= HSMA_P_MAX/2 + 1 < 2^7: fits an int)
       for (int t = 0; t < d.mom_blocks; ++t)
         for (int j = 0; j < moment_unit_pairs(sp.p); ++j) L.itmu.push_back(make_int2(s, (t << 7) | j));
@@ -354,6 +354,22 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     L.totSB = off_sb;
     L.use_sb = 8 * (size_t)off_sb <= kMaxSurfBasisBytes;
     if (!L.use_sb) L.itsb.clear();
+    // with the basis, the per-step surface kernel takes surf_pw points per warp: as many as keep
+    // at least four blocks per SM (fewer, larger blocks amortise the coefficient staging; more
+    // blocks finish sooner when the launch is short of them)
+    if (L.use_sb) {
+      int64_t totM = 0;
+      for (int s = 0; s < nsys; ++s) totM += spec[s].M;
+      L.surf_pw = 1;
+      for (int pw : {4, 2})
+        if (totM / (kSurfMatWarps * pw) >= 4 * (int64_t)num_sms) {
+          L.surf_pw = pw;
+          break;
+        }
+      const int pts = kSurfMatWarps * L.surf_pw;
+      for (int s = 0; s < nsys; ++s)
+        for (int b = 0; b < (spec[s].M + pts - 1) / pts; ++b) L.it3m.push_back(make_int2(s, b));
+    }
   }
   // longest pair items first (cost ~ targets x sources x per-source weight)
   const bool sym = prec != HSMA_FP64;
@@ -427,7 +443,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_rec_a2 = take(8 * (size_t)ntri);
   L.o_rec_b2 = take(8 * (size_t)ntri);
   L.o_sect2 = take(8 * 4 * (size_t)(L.pmax + 1));  // sect2, the Legendre tables, sprod2
-  L.o_mtab = take(8 * 2 * (size_t)ntri);
+  L.o_mtab = take(8 * ((size_t)moment_beta_slots(L.pmax) + (size_t)ntri));
   L.o_xyz = take(24 * L.totN);
   L.o_q = take(8 * L.totN);
   if (prec == HSMA_FP64) {
@@ -493,6 +509,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_it12 = take(sizeof(int2) * L.it12.size());
   L.o_it2r = take(sizeof(int2) * L.it2r.size());
   L.o_it3 = take(sizeof(int2) * L.it3.size());
+  L.o_it3m = take(sizeof(int2) * L.it3m.size());
   L.o_it5 = take(sizeof(int2) * L.it5.size());
   L.o_it4 = take(sizeof(int4) * L.it4.size());
   L.o_it4x = take(sizeof(int4) * L.it4x.size());
@@ -592,6 +609,7 @@ void Engine::carve()
   it12_d = (int2*)(b + L.o_it12);
   it2r_d = (int2*)(b + L.o_it2r);
   it3_d = (int2*)(b + L.o_it3);
+  it3m_d = (int2*)(b + L.o_it3m);
   it5_d = (int2*)(b + L.o_it5);
   it4_d = (int4*)(b + L.o_it4);
   it4x_d = (int4*)(b + L.o_it4x);
@@ -653,6 +671,8 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
     CK(cudaMemcpyAsync(it2r_d, L.it2r.data(), sizeof(int2) * L.it2r.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it3.empty())
     CK(cudaMemcpyAsync(it3_d, L.it3.data(), sizeof(int2) * L.it3.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.it3m.empty())
+    CK(cudaMemcpyAsync(it3m_d, L.it3m.data(), sizeof(int2) * L.it3m.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it5.empty())
     CK(cudaMemcpyAsync(it5_d, L.it5.data(), sizeof(int2) * L.it5.size(), cudaMemcpyHostToDevice, stream));
   if (!L.it4.empty())
@@ -707,7 +727,7 @@ Tables Engine::tables() const
   t.sprod = sect_d + (L.pmax + 1);
   t.sprod2 = sect2_d + 3 * (L.pmax + 1);
   t.mbeta2 = mtab_d;
-  t.mnrm2 = mtab_d + (L.pmax + 1) * (L.pmax + 2) / 2;
+  t.mnrm2 = mtab_d + moment_beta_slots(L.pmax);
   t.pmax = L.pmax;
   return t;
 }
@@ -743,8 +763,9 @@ void Engine::issue_build()
   issue_moments();
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
-  launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
-                 surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
+  launch_surface(sys_d, L.use_sb ? it3m_d : it3_d, (int)(L.use_sb ? L.it3m.size() : L.it3.size()), L.maxP,
+                 L.surf_pw, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d, surf64a_d, surf64b_d, surfx_d,
+                 surfqd_d, prec, stream);
   if (order) cudaStreamWaitEvent(stream, ev_join, 0);
 }
 
@@ -787,16 +808,18 @@ void Engine::launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t 
 }
 
 // Build and potentials in one graph.  The real/Kelvin pair items need only the records, so they
-// start on the second stream right after k_images, beside the moments -> coefficients ->
-// surface chain, with their grid capped at kOverlapShare of the pair slots so that the chain's
-// blocks keep room.  After the chain, the main stream runs one full-grid launch that takes the
-// surface items and then drains whatever real/Kelvin items the first launch has not taken,
-// from the same list and work counter (each item is taken once, by whichever CTA gets it).
-//   side:  k_order_* -> k_images -> k_pairs (real/Kelvin, capped grid)
-//   main:  k_moments -> k_coef_reduce -> k_surface_mat -> [wait records] k_pairs (surface,
-//          then real/Kelvin)
+// start on the second stream right after k_images, beside the moment -> coefficient -> surface
+// chain, on a full grid at the lowest launch priority: the chain's kernels (small blocks, higher
+// priority) are dispatched first whenever they have blocks waiting, and the pair CTAs take
+// every slot the chain leaves free.  (A grid capped to keep slots for the chain leaves SMs idle
+// while the chain's kernels are short of blocks; it was slower on every workload measured.)
+// After the chain, the main stream runs one full-grid launch that takes the surface items and
+// then drains whatever real/Kelvin items the first launch has not taken, from the same list and
+// work counter (each item is taken once, by whichever CTA gets it).
+//   side:  k_order_* -> k_images -> k_pairs (real/Kelvin)
+//   main:  k_moment_prep -> k_moment_units -> k_coef_reduce -> k_surface_mat -> [wait records]
+//          k_pairs (surface, then real/Kelvin)
 //   join:  k_reduce
-constexpr double kOverlapShare = 0.5;
 
 void Engine::issue_fused()
 {
@@ -810,13 +833,13 @@ void Engine::issue_fused()
   const int occ = prec == HSMA_FP64 ? std::max(occ_f64, 1) : std::max(occ_f32[L.cfg], 1);
   const int slots = num_sms * occ;
   const int nw = L.nw;  // workers per CTA
-  const int grid_rk = std::max(1, std::min((L.nRK + nw - 1) / nw, (int)(kOverlapShare * slots)));
+  const int grid_rk = std::max(1, std::min((L.nRK + nw - 1) / nw, slots));
   const int grid_s = std::max(1, std::min((nS + L.nRK + nw - 1) / nw, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);
-  // launch priorities: the order and the records (short, and the capped real/Kelvin launch
-  // waits for them) first, the moments -> coefficients -> surface chain next, the capped
-  // launch last, so that its CTAs take only what the chains leave free; k_order_keys also
+  // launch priorities: the order and the records (short, and the real/Kelvin launch waits for
+  // them) first, the moment -> coefficient -> surface chain next, the real/Kelvin launch last,
+  // so that its CTAs take only what the chains leave free; k_order_keys also
   // zeroes both pair work counters (ctr_pairs_d and ctr_pairs2_d, adjacent), which the main
   // stream's launch uses only after ev_img
   const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d, std::min(grid_rk * nw, L.nRK)};
@@ -838,8 +861,9 @@ void Engine::issue_fused()
   cudaStreamWaitEvent(stream, ev_img, 0);
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
-  launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
-                 surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
+  launch_surface(sys_d, L.use_sb ? it3m_d : it3_d, (int)(L.use_sb ? L.it3m.size() : L.it3.size()), L.maxP,
+                 L.surf_pw, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d, surf64a_d, surf64b_d, surfx_d,
+                 surfqd_d, prec, stream);
   launch_pair_items(srf, rk, grid_s, stream, true);
   cudaStreamWaitEvent(stream, ev_join, 0);
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
@@ -1110,14 +1134,14 @@ void Engine::issue_field()
 }
 
 // Build and field pass in one graph, as issue_fused does for the potentials: the field items of
-// the real/Kelvin records on the second stream right after the records (grid capped at
-// kOverlapShare of the slots), the surface items and the rest after the moment chain.
+// the real/Kelvin records on the second stream right after the records (full grid, lowest
+// priority), the surface items and the rest after the moment chain.
 void Engine::issue_field_fused()
 {
   const int nsys = (int)L.sd.size();
   const int nS = (int)L.it4fx.size() - L.nRKf;
   const int slots = field_slots();
-  const int grid_rk = std::max(1, std::min(L.nRKf, (int)(kOverlapShare * slots)));
+  const int grid_rk = std::max(1, std::min(L.nRKf, slots));
   const int grid_s = std::max(1, std::min(nS + L.nRKf, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);
@@ -1138,8 +1162,9 @@ void Engine::issue_field_fused()
   cudaStreamWaitEvent(stream, ev_img, 0);  // (as in issue_fused)
   launch_coef_reduce(sys_d, it2r_d, (int)L.it2r.size(), mom_d, L.mom_stride, Mn_d, coef_d, coef2_d, r0_d, prec,
                      stream);
-  launch_surface(sys_d, it3_d, (int)L.it3.size(), L.maxP, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d,
-                 surf64a_d, surf64b_d, surfx_d, surfqd_d, prec, stream);
+  launch_surface(sys_d, L.use_sb ? it3m_d : it3_d, (int)(L.use_sb ? L.it3m.size() : L.it3.size()), L.maxP,
+                 L.surf_pw, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d, surf64a_d, surf64b_d, surfx_d,
+                 surfqd_d, prec, stream);
   launch_field_items(srf, rk, grid_s, stream, true);
   cudaStreamWaitEvent(stream, ev_join, 0);
   launch_field_reduce(stream);

@@ -41,12 +41,14 @@ int tune_bucket(int64_t total_n, int nsys);
 struct Layout {
   std::vector<SysDev> sd;
   std::vector<int2> it12, it2r, it3, it5;
+  std::vector<int2> it3m;     // (system, block of kSurfMatWarps surf_pw points) of k_surface_mat
+  int surf_pw = 1;            // surface points per warp of k_surface_mat (with the basis)
   std::vector<int2> itsb;     // (representative system, point block) of every surface-basis table
   std::vector<int2> itord;    // (system, block of kOrderBlock charges): spatial order and records
   int64_t totBoxes = 0;       // 32-record boxes (real + Kelvin) of all systems
   int momG = 1;               // charges per moment group (k_moments, FP64 path)
   std::vector<int2> itmu;     // FP32 path: moment units (system, tile << 7 | column pair); it12
-                              // then holds the prep items (system, block of kMomPrepThreads)
+                              // then holds the prep items (system, block of kMomPrepCharges)
   int64_t totZ = 0;           // FP32 path: slots of the (p+1) x n moment tables of all systems
   bool use_sb = false;        // surface synthesis through the basis tables
   int64_t totSB = 0;          // 8-byte slots of all basis tables
@@ -75,6 +77,7 @@ struct Layout {
   size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_sortscr = 0, o_xs = 0, o_boxes = 0, o_itord = 0;
   size_t o_redctr = 0;
   size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0, o_outdesc = 0;
+  size_t o_it3m = 0;
   size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0, o_it4x = 0, o_it4f = 0, o_it4fx = 0;
   size_t bytes = 0;
 };
@@ -99,6 +102,7 @@ class Engine {
   int apply_move(int64_t k, const double* x_new);
   int choose_config(const std::vector<int64_t>& ns) const;
   int autotune(int reps, int* best, float* best_ms);
+  int tune_time_config(int c, int steps, std::vector<float>& t);  // (autotune) steps timed after a rebuild
   int fail(int code, const char* fmt, ...);
   int cuda_fail(cudaError_t e, const char* what);
   void drop_graphs();
@@ -176,7 +180,7 @@ class Engine {
   // batched moves: reqs are (system, k, new position); de receives one double per request
   int delta_batch(const std::vector<DeltaReq>& reqs, double* de_host);
   int move_batch(const std::vector<DeltaReq>& reqs);
-  int2 *it12_d = nullptr, *it2r_d = nullptr, *it3_d = nullptr, *it5_d = nullptr;
+  int2 *it12_d = nullptr, *it2r_d = nullptr, *it3_d = nullptr, *it5_d = nullptr, *it3m_d = nullptr;
   int* sel_d = nullptr;
   int2* selrng_d = nullptr;
   int4* it4_d = nullptr;

@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
+
 namespace hsma {
 
 // 1/sqrt(x) by one MUFU instruction (rsqrt.approx, ~2^-22.9 relative; flushes subnormals).
@@ -27,12 +29,8 @@ __device__ __forceinline__ void cp_async_wait()
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// x = hi + lo to ~2^-48 relative: hi = fl32(x), lo = fl32(x - hi).
-__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo)
-{
-  hi = __double2float_rn(x);
-  lo = __double2float_rn(x - (double)hi);
-}
+// x = hi + lo to ~2^-48 relative: hi = fl32(x), lo = fl32(x - hi) (split_double, df64.cuh).
+__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) { split_double(x, hi, lo); }
 __device__ __forceinline__ float2 split_pair(double x)
 {
   float2 r;

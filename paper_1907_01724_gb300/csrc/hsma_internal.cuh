@@ -133,6 +133,8 @@ struct SysDev {
   // qk0 = (k/(eps1 a)) dbar R_tau / 2; rc2 = (2 kCentreRel a)^2 (FP32)
   float2 f_kc, f_a, f_a2, f_qk1, f_qk0;
   float f_rc2;
+  // and of the FP32 moment inputs: 1/a, dbar/2, R_tau/a
+  float2 f_inv_a, f_hdbar, f_Rt_a;
 };
 
 // Spatial order (k_order.cu): charges sorted by the Morton index of their cell on a 16^3 grid
@@ -203,7 +205,7 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
 void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const double* xyz,
                     const double* q, const double* Mn, Tables tab, int prec, double* mom, int mom_stride,
                     cudaStream_t st);
-// FP32 path, in two kernels.  k_moment_prep (items = (system, block of kMomPrepThreads charges)):
+// FP32 path, in two kernels.  k_moment_prep (items = (system, block of kMomPrepCharges charges)):
 // per charge its double-float moment inputs -- geo = (2w hi, 2w lo, rho^2 hi, rho^2 lo), the
 // powers (u + i v)^m (mz, (re hi, re lo, im hi, im lo)) and the weights q (M_n - gamma - c)
 // (mwq) for m, n = 0..p at mzo + (m or n) n_sys + i -- and its centre constant (mcen, FP64).
@@ -211,9 +213,17 @@ void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, 
 // the moments of the columns m = j and p - j over the tile's charges, and slot P (the centre
 // constants) for j = 0.  A programmatic dependent of the prep; its dependent may start at its end.
 constexpr int kMomPrepThreads = 128;
-constexpr int kMomUnitWarps = 8;
+constexpr int kMomPrepSplit = 4;  // threads per charge
+constexpr int kMomPrepCharges = kMomPrepThreads / kMomPrepSplit;
+constexpr int kMomUnitWarps = 4;  // small blocks: the units of a launch spread evenly over the SMs
 constexpr int kMomUnitSteps = 8;  // chain steps per warp reduction (16 values)
 inline int moment_unit_pairs(int p) { return p / 2 + 1; }
+// Slots of the beta_nm table (mbeta2): rows n <= pmax + kMomUnitSteps, so that a chain may step
+// past its last degree inside a batch without a bounds test; the mnrm2 table follows it.
+__host__ __device__ constexpr int moment_beta_slots(int pmax)
+{
+  return (pmax + 1 + kMomUnitSteps) * (pmax + 2 + kMomUnitSteps) / 2;
+}
 void launch_moment_prep(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
                         const double* Mn, float4* geo, float4* mz, float2* mwq, double* mcen, cudaStream_t st);
 void launch_moment_units(const SysDev* sys, const int2* units, int nunits, const float4* geo,
@@ -230,10 +240,13 @@ void launch_surface_basis(const SysDev* sys, const int2* items, int nitems, Tabl
                           int prec, cudaStream_t st);
 // Surface records from the coefficients: with the basis table sb (a GEMV per point), or, when
 // sb is null, by running the solid-harmonic recurrence at every point.
-void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, const double* coef,
+// pw: surface points per warp of k_surface_mat (1, 2 or 4; items of kSurfWarps pw points) when
+// the basis table sb is given.
+void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, int pw, const double* coef,
                     const float2* coef2, const double* sb, Tables tab, float4* surf_a, float4* surf_b,
                     dbl4* surf64_a, double* surf64_b, dbl4* surfx, double2* surfqd, int prec, cudaStream_t st);
-constexpr int kSurfPointsPerBlock = 8;
+constexpr int kSurfPointsPerBlock = 8;  // points per block of k_surface and k_surface_basis
+constexpr int kSurfMatWarps = 8;        // warps per block of k_surface_mat (1, 2 or 4 points each)
 // Largest total size of the surface-basis tables of one engine; beyond it the surface step runs
 // the recurrence at every point instead.
 constexpr size_t kMaxSurfBasisBytes = size_t(4) << 30;

@@ -499,8 +499,9 @@ __global__ __launch_bounds__(256) void k_move_charge(const SysDev* __restrict__ 
     const double mg = Mn[S.mn + n] - S.gam;
     const double c = coef[S.coef + idx] + S.kc / a * qk * ((mg - cn) * Tn[idx] - (mg - co) * To[idx]);
     coef[S.coef + idx] = c;
-    const float ch = __double2float_rn(c);
-    coef2[S.coef + idx] = make_float2(ch, __double2float_rn(c - (double)ch));
+    float ch, cl;
+    split_double(c, ch, cl);
+    coef2[S.coef + idx] = make_float2(ch, cl);
   }
   if (threadIdx.x == 0) {
     const Image In = kelvin_image(S, R.x, R.y, R.z, qk);

@@ -13,36 +13,38 @@ namespace hsma {
 // energies E_total = 1/2 sum q (phi_coul + phi_rf), E_RF = 1/2 sum q phi_rf.  Fixed-order
 // block reductions; the last block of a system to finish (counter[r] per launch-local system
 // r, reset by that block) sums the system's block partials in a fixed order.
-constexpr int kRedLanes = 8;
-// Sums of the (hi, lo) partials of this lane's chunks k = sub, sub + kRedLanes, ... < nch in
-// ascending order: the real chunks (k < ncr) into c, the others into r.  Eight chunks' loads are
-// issued ahead of their additions, so a target's partials cost one or two L2 round trips
-// instead of one per chunk.
+constexpr int kRedLanes = 4;
+// Sum of the (hi, lo) partials of chunks k = k0, k0 + kRedLanes, ... < k1 in ascending order
+// into acc: kRedBatch chunks' loads are issued ahead of their additions, so a target's
+// partials cost a few L2 round trips instead of one per chunk (slots past k1 add zero).
+constexpr int kRedBatch = 8;
+__device__ __forceinline__ void sum_range(const float2* __restrict__ b, long long n, int k0, int k1, df& acc)
+{
+  for (; k0 < k1; k0 += kRedBatch * kRedLanes) {
+    float2 v[kRedBatch];
+#pragma unroll
+    for (int j = 0; j < kRedBatch; ++j) {
+      const int k = k0 + kRedLanes * j;
+      v[j] = k < k1 ? b[(long long)k * n] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < kRedBatch; ++j) acc = acc + df_make(v[j].x, v[j].y);
+  }
+}
+// This lane's chunks (k = sub mod kRedLanes): the real chunks (k < ncr) into c, the others into
+// r.  (Four lanes per target: the lanes' shared work per target -- the butterfly, the
+// conversions and the energy terms -- is paid by half as many lanes as with eight.)
 __device__ __forceinline__ void sum_chunks(const float2* __restrict__ b, long long n, int sub, int ncr, int nch,
                                            df& c, df& r)
 {
-  constexpr int kBatch = 8;
-  for (int k0 = sub; k0 < nch; k0 += kBatch * 8) {
-    float2 v[kBatch];
-#pragma unroll
-    for (int j = 0; j < kBatch; ++j) {
-      const int k = k0 + 8 * j;
-      v[j] = k < nch ? b[(long long)k * n] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int j = 0; j < kBatch; ++j) {
-      const int k = k0 + 8 * j;
-      if (k < ncr)
-        c = c + df_make(v[j].x, v[j].y);
-      else if (k < nch)
-        r = r + df_make(v[j].x, v[j].y);
-    }
-  }
+  sum_range(b, n, sub, ncr, c);
+  const int k2 = ncr + ((sub - ncr) % kRedLanes + kRedLanes) % kRedLanes;  // first k >= ncr, k = sub mod lanes
+  sum_range(b, n, k2, nch, r);
 }
 
 constexpr int kRedThreads = kReduceTargetsPerBlock * kRedLanes;
-static_assert(kRedThreads == 256, "reduce block size");
-static_assert(kRedLanes == 8, "sum_chunks strides by 8 lanes");
+static_assert(kRedThreads == 128, "reduce block size");
+static_assert(kRedLanes >= 3, "lanes 0, 1, 2 of a target write phi_c, phi_r, phi_t");
 
 __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict__ sys, const int* __restrict__ sel,
                                                         const int2* __restrict__ sel_rng, int nsel,
@@ -57,6 +59,7 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
                                                         int* __restrict__ status, const OutDesc* __restrict__ out)
 {
   __shared__ double red[2][kRedThreads / 32];
+  __shared__ float2 red2[2][kRedThreads / 32];
   __shared__ bool last;
   __shared__ int s_r;
   const int2 it = items[blockIdx.x];
@@ -156,7 +159,8 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
         if (od.status) od.status[1] = 1;
       }
     }
-    const df hq = df_from_double(0.5 * qi);
+    // q/2 split exactly (halving a split is exact away from underflow)
+    const df q1 = df_from_double(qi), hq = df_make(0.5f * q1.hi, 0.5f * q1.lo);
     df ect = i < n && sub == 0 ? hq * t : df_make(0.f, 0.f);
     df ecr = i < n && sub == 0 ? hq * r : df_make(0.f, 0.f);
     for (int o = 16; o > 0; o >>= 1) {
@@ -164,21 +168,32 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
       ecr = ecr + df_make(__shfl_xor_sync(0xffffffffu, ecr.hi, o), __shfl_xor_sync(0xffffffffu, ecr.lo, o));
     }
     if ((threadIdx.x & 31) == 0) {
-      et = df_to_double(ect);
-      er = df_to_double(ecr);
+      red2[0][threadIdx.x >> 5] = make_float2(ect.hi, ect.lo);
+      red2[1][threadIdx.x >> 5] = make_float2(ecr.hi, ecr.lo);
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
+  if (lane == 0 && prec == HSMA_FP64) {
     red[0][warp] = et;
     red[1][warp] = er;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
-    for (int w = 0; w < kRedThreads / 32; ++w) {
-      a += red[0][w];
-      b += red[1][w];
+    if (prec == HSMA_FP64) {
+      for (int w = 0; w < kRedThreads / 32; ++w) {
+        a += red[0][w];
+        b += red[1][w];
+      }
+    } else {
+      // the warps' double-float sums in order, one conversion per block
+      df A = df_make(0.f, 0.f), B = df_make(0.f, 0.f);
+      for (int w = 0; w < kRedThreads / 32; ++w) {
+        A = A + df_make(red2[0][w].x, red2[0][w].y);
+        B = B + df_make(red2[1][w].x, red2[1][w].y);
+      }
+      a = df_to_double(A);
+      b = df_to_double(B);
     }
     epart[2 * blockIdx.x] = a;
     epart[2 * blockIdx.x + 1] = b;
@@ -201,29 +216,59 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce(const SysDev* __restrict
   // warps in order), so the result does not depend on which block finishes last
   const int r = s_r;
   const int2 rg = sel_rng[r];
-  double a = 0.0, b = 0.0;
+  if (prec == HSMA_FP64) {
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < rg.y; k += kRedThreads) {
+      a += __ldcg(&epart[2 * (rg.x + k)]);
+      b += __ldcg(&epart[2 * (rg.x + k) + 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+      red[0][warp] = a;
+      red[1][warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double A = 0.0, B = 0.0;
+      for (int w = 0; w < kRedThreads / 32; ++w) {
+        A += red[0][w];
+        B += red[1][w];
+      }
+      energy[2 * sel[r]] = A;
+      energy[2 * sel[r] + 1] = B;
+      counter[r] = 0u;
+    }
+    return;
+  }
+  // FP32 path: the block partials in double-float (the FP64 additions of one block would queue
+  // on its SM's FP64 unit at the end of the pass)
+  df a = df_make(0.f, 0.f), b = df_make(0.f, 0.f);
   for (int k = threadIdx.x; k < rg.y; k += kRedThreads) {
-    a += __ldcg(&epart[2 * (rg.x + k)]);
-    b += __ldcg(&epart[2 * (rg.x + k) + 1]);
+    a = a + df_from_double(__ldcg(&epart[2 * (rg.x + k)]));
+    b = b + df_from_double(__ldcg(&epart[2 * (rg.x + k) + 1]));
   }
   for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
+    a = a + df_make(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
+    b = b + df_make(__shfl_xor_sync(0xffffffffu, b.hi, o), __shfl_xor_sync(0xffffffffu, b.lo, o));
   }
   __syncthreads();
   if (lane == 0) {
-    red[0][warp] = a;
-    red[1][warp] = b;
+    red2[0][warp] = make_float2(a.hi, a.lo);
+    red2[1][warp] = make_float2(b.hi, b.lo);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double A = 0.0, B = 0.0;
+    df A = df_make(0.f, 0.f), B = df_make(0.f, 0.f);
     for (int w = 0; w < kRedThreads / 32; ++w) {
-      A += red[0][w];
-      B += red[1][w];
+      A = A + df_make(red2[0][w].x, red2[0][w].y);
+      B = B + df_make(red2[1][w].x, red2[1][w].y);
     }
-    energy[2 * sel[r]] = A;
-    energy[2 * sel[r] + 1] = B;
+    energy[2 * sel[r]] = df_to_double(A);
+    energy[2 * sel[r] + 1] = df_to_double(B);
     counter[r] = 0u;
   }
 }

@@ -51,8 +51,9 @@ namespace hsma {
 // phi = pi jj F1/F2 (+ pi for odd j), weight w = (2 pi R_tau^2/F2)(1 + cos(pi z)).
 __device__ __forceinline__ float2 pair_of(double x)
 {
-  const float hi = __double2float_rn(x);
-  return make_float2(hi, __double2float_rn(x - (double)hi));
+  float2 r;
+  split_double(x, r.x, r.y);
+  return r;
 }
 
 // Vertical recurrence coefficients of the normalised solid harmonics below the diagonal:
@@ -87,23 +88,27 @@ __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__
       rec_b[t] = B;
       rec_a2[t] = pair_of(A);
       rec_b2[t] = pair_of(B);
-      // the rescaled column chain of k_moment_units: with e_nm = prod_{k=m+1..n} a_km / 2,
-      // S_n = T_nm / (e_nm sprod_m z^m) obeys S_n = 2 w S_{n-1} - beta_nm rho^2 S_{n-2},
-      // beta_nm = 4 b_nm / (a_nm a_{n-1,m}), S_m = 1 (no table factor left in the chain)
-      double e = 1.0, sp = 1.0, Ak, Bk;
-      for (int k = m + 1; k <= n; ++k) {
-        rec_coef(k, m, Ak, Bk);
-        e *= 0.5 * Ak;
-      }
+    }
+    // the rescaled column chain of k_moment_units, one column per thread: with
+    // e_nm = prod_{k=m+1..n} a_km / 2, S_n = T_nm / (e_nm sprod_m z^m) obeys
+    // S_n = 2 w S_{n-1} - beta_nm rho^2 S_{n-2}, beta_nm = 4 b_nm / (a_nm a_{n-1,m}), S_m = 1
+    // (no table factor left in the chain)
+    // (beta rows past pmax, up to pmax + kMomUnitSteps, only feed chain steps whose values are
+    // discarded)
+    const int nbeta = moment_beta_slots(pmax);
+    for (int m = threadIdx.x; m <= pmax; m += blockDim.x) {
+      double sp = 1.0;
       for (int k = 2; k <= m; ++k) sp *= sqrt((2.0 * k - 1.0) / (2.0 * k));
-      double beta = 0.0;
-      if (n >= m + 2) {
-        double A1, B1;
-        rec_coef(n - 1, m, A1, B1);
-        beta = 4.0 * B / (A * A1);
+      double e = 1.0, Aprev = 0.0;
+      for (int n = m; n <= pmax + kMomUnitSteps; ++n) {
+        double A, B;
+        rec_coef(n, m, A, B);
+        if (n > m) e *= 0.5 * A;
+        const int t = n * (n + 1) / 2 + m;
+        mtab[t] = pair_of(n >= m + 2 ? 4.0 * B / (A * Aprev) : 0.0);
+        if (n <= pmax) mtab[nbeta + t] = pair_of(e * sp);
+        Aprev = A;
       }
-      mtab[t] = pair_of(beta);
-      mtab[ntri + t] = pair_of(e * sp);
     }
     for (int m = threadIdx.x; m <= pmax; m += blockDim.x) {
       sect[m] = (m >= 2) ? sqrt((2.0 * m - 1.0) / (2.0 * m)) : 1.0;
@@ -138,6 +143,9 @@ __global__ void k_setup(SysDev* __restrict__ sys, int nsys, double* __restrict__
       d.f_qk1 = pair_of(d.kc_a * (d.gam - 0.5 * d.dbar));
       d.f_qk0 = pair_of(d.kc_a * d.dbar * d.Rtau * 0.5);
       d.f_rc2 = (float)(4.0 * (kCentreRel * d.a) * (kCentreRel * d.a));
+      d.f_inv_a = pair_of(d.inv_a);
+      d.f_hdbar = pair_of(0.5 * d.dbar);
+      d.f_Rt_a = pair_of(d.Rt_a);
       double t = d.mu;
       for (int n = 0; n <= d.p; ++n) {
         Mn[d.mn + n] = -((1.0 - d.eps) * (n + 1) + t) / ((1.0 + d.eps) * n + 1.0 + t);
@@ -321,12 +329,6 @@ __device__ __forceinline__ void solid_pair(int j, int p, R u, R v, R w, R rho2, 
   if (m2 != m1) solid_vertical<R>(m2, p, w, rho2, sp[m2] * zr, sp[m2] * zi, ra, rb, T);
 }
 
-// Split a double into an FP32 high part and the FP32-rounded residual (x ~ hi + lo).
-__device__ __forceinline__ void split2(double x, float& hi, float& lo)
-{
-  hi = __double2float_rn(x);
-  lo = __double2float_rn(x - (double)hi);
-}
 
 
 constexpr int kMomThreads = 352;  // a moment block holds at most kMomTile <= kMomThreads charges
@@ -489,22 +491,22 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
 }
 
 // Moment inputs of one charge in double-float: u, v, w = x/a, rho^2 = |x|^2/a^2, q and q c with
-// c = dbar (R_tau r/a^2 - 1)/2, from the split FP64 inputs (four FP64 conversions per charge;
+// c = dbar (R_tau r/a^2 - 1)/2, from the (hi, lo) splits of x, y, z, q (FP32 arithmetic only:
 // this GPU issues FP64 arithmetic at a small fraction of the FP32 rate).
 struct MomentInputs {
   df u, v, w, rho2, q, qc;
 };
-__device__ __forceinline__ MomentInputs moment_inputs_df(const SysDev& S, double x, double y, double z, double qi)
+__device__ __forceinline__ MomentInputs moment_inputs_df(const SysDev& S, df x, df y, df z, df qi)
 {
   MomentInputs r;
-  const df ia = df_from_double(S.inv_a);
-  r.u = df_from_double(x) * ia;
-  r.v = df_from_double(y) * ia;
-  r.w = df_from_double(z) * ia;
+  const df ia = df_make(S.f_inv_a.x, S.f_inv_a.y);
+  r.u = x * ia;
+  r.v = y * ia;
+  r.w = z * ia;
   r.rho2 = r.u * r.u + r.v * r.v + r.w * r.w;
-  r.q = df_from_double(qi);
+  r.q = qi;
   const df rr = r.rho2.hi > 0.f ? df_sqrt(r.rho2) : df_make(0.f, 0.f);
-  const df c = df_from_double(0.5 * S.dbar) * (df_from_double(S.Rt_a) * rr - df_make(1.f, 0.f));
+  const df c = df_make(S.f_hdbar.x, S.f_hdbar.y) * (df_make(S.f_Rt_a.x, S.f_Rt_a.y) * rr - df_make(1.f, 0.f));
   r.qc = r.q * c;
   return r;
 }
@@ -727,7 +729,10 @@ void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, 
 // 32 charges' terms of each coefficient side by side, then sums them across the lanes with a
 // transposed warp reduction; no shared memory and no block barrier, every lane busy.
 //
-// k_moment_prep, one thread per charge: the inputs that every column of the charge reuses.
+// k_moment_prep, a quad of kMomPrepSplit lanes per charge: the inputs that every column of the
+// charge reuses.  Quad lane k splits input k of the charge (x, y, z, q; split_double) and the
+// quad shares the splits; then lane k writes the powers z^m and the weights of degree n for
+// m, n = k mod 4 (z^m = z^k (z^4)^s), a quarter of the sequential chain of complex products.
 __global__ __launch_bounds__(kMomPrepThreads) void k_moment_prep(const SysDev* __restrict__ sys,
                                                                  const int2* __restrict__ items,
                                                                  const double* __restrict__ xyz,
@@ -737,35 +742,63 @@ __global__ __launch_bounds__(kMomPrepThreads) void k_moment_prep(const SysDev* _
                                                                  float2* __restrict__ mwq, double* __restrict__ mcen)
 {
   static_assert(kMomPrepThreads > HSMA_P_MAX, "one thread per degree for M_n - gamma");
+  static_assert(kMomPrepSplit == 4, "a quad per charge: x, y, z, q and z^k, k < 4");
   __shared__ df smg[kMomPrepThreads];  // M_n - gamma
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int ns = S.n, p = S.p;
-  const int i = it.y * kMomPrepThreads + threadIdx.x;
+  const int lane = threadIdx.x & 31, sub = lane & 3, quad = lane & ~3;
+  const int i = it.y * kMomPrepCharges + (int)threadIdx.x / kMomPrepSplit;
+  const bool live = i < ns;
+  const long long gi = S.chg + (live ? i : 0);
+  double xin = 0.0;
+  if (live) xin = sub < 3 ? xyz[3 * gi + sub] : q[gi];
   if ((int)threadIdx.x <= p) smg[threadIdx.x] = df_from_double(Mn[S.mn + threadIdx.x] - S.gam);
   // every block of the grid is resident once this is reached: the unit kernel's blocks may
   // start (they wait for this grid's writes before reading them)
   allow_dependents();
+  const df dv = df_from_double(xin);
+  df in[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    in[k] = df_make(__shfl_sync(0xffffffffu, dv.hi, quad + k), __shfl_sync(0xffffffffu, dv.lo, quad + k));
+  const double qv = __shfl_sync(0xffffffffu, xin, quad + 3);
   __syncthreads();
-  if (i >= ns) return;
-  const long long gi = S.chg + i;
-  const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
-  // the centre constant of a charge whose image is at infinity (as in k_moments and kelvin_rec)
-  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
-  const double rc = kCentreRel * S.a;
-  mcen[gi] = (r2 <= 4.0 * rc * rc && sqrt(r2) <= rc) ? S.kc_a * qi * (S.gam - 0.5 * S.dbar) : 0.0;
-  const MomentInputs mi = moment_inputs_df(S, x, y, z, qi);
-  geo[gi] = make_float4(2.f * mi.w.hi, 2.f * mi.w.lo, mi.rho2.hi, mi.rho2.lo);
-  const long long zb = S.mzo + i;
+  if (!live) return;
+  const MomentInputs mi = moment_inputs_df(S, in[0], in[1], in[2], in[3]);
+  if (sub == 0) {
+    // the centre constant of a charge whose image is at infinity, by the FP32 path's centre
+    // test of k_images on the same splits (FP64 only near the centre)
+    const df r2 = in[0] * in[0] + in[1] * in[1] + in[2] * in[2];
+    const bool centre = r2.hi <= S.f_rc2 && sqrt(df_to_double(r2)) <= kCentreRel * S.a;
+    mcen[gi] = centre ? S.kc_a * qv * (S.gam - 0.5 * S.dbar) : 0.0;
+    geo[gi] = make_float4(2.f * mi.w.hi, 2.f * mi.w.lo, mi.rho2.hi, mi.rho2.lo);
+  }
+  // z^2, z^4 and z^sub
+  const df uv = mi.u * mi.v;
+  const df u2r = df_mul_sub(mi.u, mi.u, mi.v, mi.v), u2i = df_make(2.f * uv.hi, 2.f * uv.lo);
+  const df rs = u2r * u2i;
+  const df u4r = df_mul_sub(u2r, u2r, u2i, u2i), u4i = df_make(2.f * rs.hi, 2.f * rs.lo);
   df zr = df_make(1.f, 0.f), zi = df_make(0.f, 0.f);
-  for (int m = 0; m <= p; ++m) {
+  if (sub == 1) {
+    zr = mi.u;
+    zi = mi.v;
+  } else if (sub == 2) {
+    zr = u2r;
+    zi = u2i;
+  } else if (sub == 3) {
+    zr = df_mul_sub(u2r, mi.u, u2i, mi.v);
+    zi = df_mul_sub(u2r, mi.v, -u2i, mi.u);
+  }
+  const long long zb = S.mzo + i;
+  for (int m = sub; m <= p; m += kMomPrepSplit) {
     mz[zb + (long long)m * ns] = make_float4(zr.hi, zr.lo, zi.hi, zi.lo);
-    const df nr = df_mul_sub(zr, mi.u, zi, mi.v);
-    const df ni = df_mul_sub(zr, mi.v, -zi, mi.u);
+    const df nr = df_mul_sub(zr, u4r, zi, u4i);
+    const df ni = df_mul_sub(zr, u4i, -zi, u4r);
     zr = nr;
     zi = ni;
   }
-  for (int n = 0; n <= p; ++n) {
+  for (int n = sub; n <= p; n += kMomPrepSplit) {
     const df wq = df_mul_sub(mi.q, smg[n], df_make(1.f, 0.f), mi.qc);
     mwq[zb + (long long)n * ns] = make_float2(wq.hi, wq.lo);
   }
@@ -808,19 +841,74 @@ __device__ __forceinline__ df warp_treduce16(df* v, int lane)
   return df_norm(df_add_lazy(v[0], shfl_xor_df(v[0], 1)));
 }
 
-// k_moment_units: the unit's steps are the column m1 = j (n = m1..p), then the column m2 = p - j
-// (n = m2..p) unless it is the same column; a batch of kMomUnitSteps steps gives 16 values per
-// lane (real and sine parts) that warp_treduce16 sums over the lanes, and the running sum of a
-// batch's values over the tile's groups of 32 charges stays in the warp's shared memory (lane l:
-// value (l >> 1) & 15).  The chain runs on S_n = T_nm / (e_nm sprod_m z^m) (k_setup), the step's
-// term is q (M_n - gamma - c) S_n z^m, and the row value is that sum times e_nm sprod_m (mnrm2).
-constexpr int kMomUnitMaxBatches = (HSMA_P_MAX + 2 + kMomUnitSteps - 1) / kMomUnitSteps;
-__global__ __launch_bounds__(kMomUnitWarps * 32) void k_moment_units(
+// Steps n = n0 .. n0 + NS - 1 of one column chain for the lane's charge: values 2k, 2k + 1 are
+// the real and sine parts of q (M_n - gamma - c) S_n z^m for n = n0 + k (zero past n = p and for
+// a dead lane), then the chain advances, S_{n+1} = 2 w S_n - beta_{n+1,m} rho^2 S_{n-1}.  On
+// entry qa = S_n0, qb = S_{n0-1}, tb = table index of (n0 + 1, m), wp = the weight of degree n0
+// (next degree: + ns).  A chain may run up to NS - 1 steps past p (beta is padded for that).
+template <int NS>
+__device__ __forceinline__ void moment_chain_steps(df W, df R2, df& qa, df& qb, int n0, int p, int& tb,
+                                                   const float2* __restrict__ beta,
+                                                   const float2* __restrict__ wp, long long ns, bool live,
+                                                   float4 z, df* v)
+{
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int n = n0 + k;
+    const float2 wv = (live && n <= p) ? wp[k * ns] : make_float2(0.f, 0.f);
+    const df t = df_mul_lazy(df_make(wv.x, wv.y), qa);
+    v[2 * k] = df_mul_lazy(t, df_make(z.x, z.y));
+    v[2 * k + 1] = df_mul_lazy(t, df_make(z.z, z.w));
+    const float2 bt = beta[tb];
+    const df nx = df_mul_sub(W, qa, df_mul_lazy(df_make(bt.x, bt.y), R2), qb);
+    qb = qa;
+    qa = nx;
+    tb += n + 2;
+  }
+}
+
+// k_moment_units: the unit's columns m1 = j and m2 = p - j (n = m..p each; one column when they
+// coincide) in batches of kMomUnitSteps steps, 16 values per lane that warp_treduce16 sums over
+// the lanes.  The first nA batches take 4 steps of each column (the shorter column m2 is done
+// after them), the next nB batches 8 steps of column m1 alone: every step of a batch has a
+// fixed column and degree offset, with no per-step selection.  The running sum of a batch's
+// values over the tile's groups of 32 charges stays in the warp's shared memory (lane l: value
+// (l >> 1) & 15).  The chain runs on S_n = T_nm / (e_nm sprod_m z^m) (k_setup), and the row value
+// is the sum times e_nm sprod_m (mnrm2).
+constexpr int kMomUnitMaxBatches = 11;  // nA + nB for every p <= HSMA_P_MAX and pair j
+static_assert(HSMA_P_MAX <= 80, "kMomUnitMaxBatches is the largest nA + nB for p <= 80");
+struct MomentUnitShape {
+  int m1, m2, nA, nB;
+};
+__device__ __forceinline__ MomentUnitShape moment_unit_shape(int p, int j)
+{
+  MomentUnitShape u;
+  u.m1 = j;
+  u.m2 = p - j;
+  const int L1 = p - u.m1 + 1, L2 = u.m2 != u.m1 ? p - u.m2 + 1 : 0;
+  u.nA = (L2 + 3) / 4;
+  const int R = L1 - 4 * u.nA;
+  u.nB = R > 0 ? (R + 7) / 8 : 0;
+  return u;
+}
+// column and degree of value k (0..7 steps) of batch b
+__device__ __forceinline__ void moment_unit_value(const MomentUnitShape& u, int b, int k, int& m, int& n)
+{
+  if (b < u.nA) {
+    m = k < 4 ? u.m1 : u.m2;
+    n = m + 4 * b + (k & 3);
+  } else {
+    m = u.m1;
+    n = u.m1 + 4 * u.nA + 8 * (b - u.nA) + k;
+  }
+}
+
+__global__ __launch_bounds__(kMomUnitWarps * 32, 24 / kMomUnitWarps) void k_moment_units(
     const SysDev* __restrict__ sys, const int2* __restrict__ units, int nunits, const float4* __restrict__ geo,
     const float4* __restrict__ mz, const float2* __restrict__ mwq, const double* __restrict__ mcen, Tables tab,
     double* __restrict__ mom, int mom_stride)
 {
-  constexpr int ST = kMomUnitSteps;
+  static_assert(kMomUnitSteps == 8, "mode A: 4 + 4 steps, mode B: 8 steps");
   __shared__ float2 sacc[kMomUnitWarps][kMomUnitMaxBatches][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int u = blockIdx.x * kMomUnitWarps + warp;
@@ -829,10 +917,8 @@ __global__ __launch_bounds__(kMomUnitWarps * 32) void k_moment_units(
   const SysDev& S = sys[it.x];
   const int ns = S.n, p = S.p;
   const int tile = it.y >> 7, j = it.y & 127;
-  const int m1 = j, m2 = p - j;
-  const int L1 = p - m1 + 1;
-  const int L = m2 != m1 ? p + 2 : L1;
-  const int nbat = (L + ST - 1) / ST;
+  const MomentUnitShape sh = moment_unit_shape(p, j);
+  const int nbat = sh.nA + sh.nB;
   const int cb = tile * S.mom_tile, ce = min(ns, cb + S.mom_tile);
   const float2* __restrict__ beta = tab.mbeta2;
   float2* acc = &sacc[warp][0][lane];  // acc[32 b]: batch b
@@ -846,44 +932,35 @@ __global__ __launch_bounds__(kMomUnitWarps * 32) void k_moment_units(
     const long long zb = S.mzo + i;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 g = live ? geo[S.chg + i] : zero4;
-    const float4 z1 = live ? mz[zb + (long long)m1 * ns] : zero4;
-    const float4 z2 = live ? mz[zb + (long long)m2 * ns] : zero4;
+    const float4 z1 = live ? mz[zb + (long long)sh.m1 * ns] : zero4;
+    const float4 z2 = live && sh.nA > 0 ? mz[zb + (long long)sh.m2 * ns] : zero4;
     if (j == 0 && live) cen += mcen[S.chg + i];
     const df W = df_make(g.x, g.y), R2 = df_make(g.z, g.w);
-    df qa = df_make(0.f, 0.f), qb = df_make(0.f, 0.f);  // S_{n-1}, S_{n-2}
+    // chain states: S_n, S_{n-1} at the next step's degree, and that degree's table index + 1 row
+    df qa1 = df_make(1.f, 0.f), qb1 = df_make(0.f, 0.f), qa2 = df_make(1.f, 0.f), qb2 = df_make(0.f, 0.f);
+    int tb1 = (sh.m1 + 1) * (sh.m1 + 2) / 2 + sh.m1, tb2 = (sh.m2 + 1) * (sh.m2 + 2) / 2 + sh.m2;
+    const float2* wp1 = mwq + zb + (long long)sh.m1 * ns;
+    const float2* wp2 = mwq + zb + (long long)sh.m2 * ns;
 #pragma unroll 1
-    for (int b = 0; b < nbat; ++b) {
-      df v[2 * ST];
-#pragma unroll
-      for (int k = 0; k < ST; ++k) {
-        const int s = b * ST + k;
-        v[2 * k] = df_make(0.f, 0.f);
-        v[2 * k + 1] = df_make(0.f, 0.f);
-        if (s < L) {
-          const bool second = s >= L1;
-          const int m = second ? m2 : m1;
-          const int n = second ? m2 + (s - L1) : m1 + s;
-          df cur;
-          if (n == m) {
-            cur = df_make(1.f, 0.f);
-            qa = df_make(0.f, 0.f);
-          } else {
-            const float2 bt = beta[n * (n + 1) / 2 + m];
-            cur = df_mul_sub(W, qa, df_make(bt.x, bt.y) * R2, qb);
-          }
-          qb = qa;
-          qa = cur;
-          const float2 wv = live ? mwq[zb + (long long)n * ns] : make_float2(0.f, 0.f);
-          const float4 zz = second ? z2 : z1;
-          const df t = df_make(wv.x, wv.y) * cur;
-          v[2 * k] = t * df_make(zz.x, zz.y);
-          v[2 * k + 1] = t * df_make(zz.z, zz.w);
-        }
-      }
+    for (int b = 0; b < sh.nA; ++b) {
+      df v[16];
+      moment_chain_steps<4>(W, R2, qa1, qb1, sh.m1 + 4 * b, p, tb1, beta, wp1 + 4LL * b * ns, ns, live, z1, v);
+      moment_chain_steps<4>(W, R2, qa2, qb2, sh.m2 + 4 * b, p, tb2, beta, wp2 + 4LL * b * ns, ns, live, z2, v + 8);
       const df r = warp_treduce16(v, lane);
       const float2 a = acc[32 * b];
       const df sum = df_make(a.x, a.y) + r;
       acc[32 * b] = make_float2(sum.hi, sum.lo);
+    }
+    const int n1 = sh.m1 + 4 * sh.nA;
+#pragma unroll 1
+    for (int b = 0; b < sh.nB; ++b) {
+      df v[16];
+      moment_chain_steps<8>(W, R2, qa1, qb1, n1 + 8 * b, p, tb1, beta, wp1 + (4LL * sh.nA + 8LL * b) * ns, ns,
+                            live, z1, v);
+      const df r = warp_treduce16(v, lane);
+      const float2 a = acc[32 * (sh.nA + b)];
+      const df sum = df_make(a.x, a.y) + r;
+      acc[32 * (sh.nA + b)] = make_float2(sum.hi, sum.lo);
     }
   }
   // the coefficient kernel may launch once every unit is here
@@ -892,17 +969,13 @@ __global__ __launch_bounds__(kMomUnitWarps * 32) void k_moment_units(
   if ((lane & 1) == 0) {
     const int part = (lane >> 1) & 1;  // 0: cosine (real) part, 1: sine part
     for (int b = 0; b < nbat; ++b) {
-      const int s = b * ST + (lane >> 2);
-      if (s < L) {
-        const bool second = s >= L1;
-        const int m = second ? m2 : m1;
-        const int n = second ? m2 + (s - L1) : m1 + s;
-        if (!(part && m == 0)) {
-          const float2 f = tab.mnrm2[n * (n + 1) / 2 + m];
-          const float2 a = acc[32 * b];
-          const df val = df_make(a.x, a.y) * df_make(f.x, f.y);
-          reinterpret_cast<float2*>(out)[n * n + n + (part ? -m : m)] = make_float2(val.hi, val.lo);
-        }
+      int m, n;
+      moment_unit_value(sh, b, lane >> 2, m, n);
+      if (n <= p && !(part && m == 0)) {
+        const float2 f = tab.mnrm2[n * (n + 1) / 2 + m];
+        const float2 a = acc[32 * b];
+        const df val = df_make(a.x, a.y) * df_make(f.x, f.y);
+        reinterpret_cast<float2*>(out)[n * n + n + (part ? -m : m)] = make_float2(val.hi, val.lo);
       }
     }
   }
@@ -936,7 +1009,7 @@ void launch_moment_units(const SysDev* sys, const int2* units, int nunits, const
 // rows w, w + kCoefWarps, ...), and warp 0 adds the warp sums in order, so the result does not
 // depend on scheduling.  Sums run in the moment arithmetic R; the coefficient is formed in FP64
 // and also stored as an FP32 (hi, lo) pair for the FP32 path's surface synthesis.
-constexpr int kCoefWarps = 8;
+constexpr int kCoefWarps = 32;
 template <class R>
 __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* __restrict__ sys,
                                                                  const int2* __restrict__ items,
@@ -947,13 +1020,14 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
 {
   __shared__ R su[kCoefWarps][kCoefChunk];
   __shared__ double sr[kCoefWarps];
+  __shared__ float2 srd[kCoefWarps];
   // the item and its system are read before the wait for the moment rows
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P, nb = S.mom_blocks;
   const double kc_a = S.kc_a;
   const double* base = mom + (size_t)S.mom * mom_stride;
-  grid_dependency_wait();  // the moment rows of k_moments
+  grid_dependency_wait();  // the moment rows
   allow_dependents();      // (the surface kernel's CTAs wait only while this kernel works)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int idx = it.y * kCoefChunk + lane;
@@ -974,10 +1048,31 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
         if (b0 + k * kCoefWarps < nb) U = U + u[k];
     }
   }
-  if (it.y == 0 && lane == 0)
-    for (int b = warp; b < nb; b += kCoefWarps) Rs += base[(size_t)b * mom_stride + P];
+  // the rows' centre constants (block 0): thread t takes rows t, t + kCoefWarps 32, ... (all
+  // loads of the block in flight at once), then a fixed-order reduction over the lanes and the
+  // warps; the FP32 path sums in double-float (FP64 additions of a whole block would queue on one
+  // SM's FP64 unit)
+  df Rsd = df_make(0.f, 0.f);
+  if (it.y == 0) {
+    for (int b = threadIdx.x; b < nb; b += kCoefWarps * 32) {
+      const double v = base[(size_t)b * mom_stride + P];
+      if (Num<R>::is_df)
+        Rsd = Rsd + df_from_double(v);
+      else
+        Rs += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      if (Num<R>::is_df)
+        Rsd = Rsd + df_make(__shfl_xor_sync(0xffffffffu, Rsd.hi, o), __shfl_xor_sync(0xffffffffu, Rsd.lo, o));
+      else
+        Rs += __shfl_xor_sync(0xffffffffu, Rs, o);
+    }
+  }
   su[warp][lane] = U;
-  if (lane == 0) sr[warp] = Rs;
+  if (lane == 0) {
+    sr[warp] = Rs;
+    srd[warp] = make_float2(Rsd.hi, Rsd.lo);
+  }
   __syncthreads();
   if (warp == 0) {
     U = Num<R>::zero();
@@ -989,9 +1084,15 @@ __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* _
       coef2[S.coef + idx] = pair_of(c);
     }
     if (it.y == 0 && lane == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kCoefWarps; ++w) t += sr[w];
-      r0[it.x] = t;
+      if (Num<R>::is_df) {
+        df t = df_make(0.f, 0.f);
+        for (int w = 0; w < kCoefWarps; ++w) t = t + df_make(srd[w].x, srd[w].y);
+        r0[it.x] = df_to_double(t);
+      } else {
+        double t = 0.0;
+        for (int w = 0; w < kCoefWarps; ++w) t += sr[w];
+        r0[it.x] = t;
+      }
     }
   }
 }
@@ -1015,6 +1116,7 @@ void launch_coef_reduce(const SysDev* sys, const int2* items, int nitems, const 
 constexpr int kSurfThreads = 256;
 constexpr int kSurfWarps = kSurfThreads / 32;
 static_assert(kSurfWarps == kSurfPointsPerBlock, "one warp per surface point");
+static_assert(kSurfWarps == kSurfMatWarps, "k_surface_mat blocks of kSurfMatWarps warps");
 
 __device__ __forceinline__ void surface_records(const SysDev& S, long long o, const dbl4& yw, double ph, double dph,
                                                 int prec, float4* __restrict__ surf_a, float4* __restrict__ surf_b,
@@ -1071,9 +1173,47 @@ void launch_surface_basis(const SysDev* sys, const int2* items, int nitems, Tabl
   k_surface_basis<<<nitems, kSurfThreads, 0, st>>>(sys, items, tab, surfx, sb, prec);
 }
 
-// Per step, with the basis: one warp per point, lanes stride the coefficients (R arithmetic),
-// fixed-order shuffle tree.
-template <class R>
+// One level of a transposed reduction over the lanes (R arithmetic): lanes with lane bit OFF set
+// keep the upper half of the 2H-value window of v and send the lower half to the partner lane
+// ^ OFF, the others the reverse.
+template <int H, int OFF, class R>
+__device__ __forceinline__ void treduce_level_r(R* v, int lane)
+{
+  const bool upper = (lane & OFF) != 0;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const R keep = upper ? v[H + k] : v[k];
+    const R send = upper ? v[k] : v[H + k];
+    v[k] = keep + Num<R>::shfl(send, OFF);
+  }
+}
+
+// Per step, with the basis: a warp takes PW points (1, 2 or 4), lanes stride the coefficients
+// (R arithmetic, PW independent sums of Phi and of n Phi per lane), and the 2 PW sums are added
+// over the lanes by one transposed reduction (lane l: sum (l >> (5 - log2(2 PW))) mod 2 PW, in a
+// fixed order).  The block stages the coefficients once for its kSurfWarps PW points, and warp 0
+// forms the records of all of them (lane = point).  Several points per warp amortise the
+// staging and the reduction when there are many blocks; one point per warp gives the most
+// blocks (lowest latency) when there are few.
+template <int V, class R>
+__device__ __forceinline__ void treduce_r(R* v, int lane)
+{
+  static_assert(V == 2 || V == 4 || V == 8, "2, 4 or 8 sums");
+  if (V == 8) {
+    treduce_level_r<4, 16>(v, lane);
+    treduce_level_r<2, 8>(v, lane);
+    treduce_level_r<1, 4>(v, lane);
+  } else if (V == 4) {
+    treduce_level_r<2, 16>(v, lane);
+    treduce_level_r<1, 8>(v, lane);
+  } else {
+    treduce_level_r<1, 16>(v, lane);
+  }
+#pragma unroll
+  for (int off = 32 / V / 2; off > 0; off >>= 1) v[0] = v[0] + Num<R>::shfl(v[0], off);
+}
+
+template <int PW, class R>
 __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __restrict__ sys,
                                                               const int2* __restrict__ items,
                                                               const double* __restrict__ coef,
@@ -1085,27 +1225,35 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __re
                                                               const dbl4* __restrict__ surfx,
                                                               double2* __restrict__ surfqd, int prec)
 {
+  constexpr int PTS = kSurfWarps * PW;  // points per block
   extern __shared__ double sm[];
-  __shared__ R s_ph[kSurfWarps], s_dph[kSurfWarps];
+  __shared__ R s_sum[kSurfWarps][2 * PW];  // per warp: Phi of its points, then n Phi
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int P = S.P, M = S.M;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = it.y * kSurfWarps + warp;
-  const bool live = j < M;
-  // the basis row (a layout constant) and, in warp 0, the block's points are loaded before the
-  // wait for the coefficients: sixteen row loads per lane in flight (512 coefficients)
-  const double* row = sb + S.sb + (long long)(live ? j : 0) * P;
-  constexpr int kRowBatch = 16;
-  R bv[kRowBatch];
+  const int j0 = it.y * PTS + warp * PW;
+  // the basis rows (a layout constant) and, in warp 0, the block's points are loaded before the
+  // wait for the coefficients: kRowBatch row loads per point and lane in flight
+  constexpr int kRowBatch = 16 / PW;
+  const double* row[PW];
+  bool live[PW];
 #pragma unroll
-  for (int k = 0; k < kRowBatch; ++k) {
-    const int i = lane + 32 * k;
-    bv[k] = live && i < P ? Num<R>::ld(row, i) : Num<R>::zero();
+  for (int t = 0; t < PW; ++t) {
+    live[t] = j0 + t < M;
+    row[t] = sb + S.sb + (long long)(live[t] ? j0 + t : 0) * P;
   }
-  const int jl = it.y * kSurfWarps + lane;  // warp 0: the point of lane l < kSurfWarps
+  R bv[PW][kRowBatch];
+#pragma unroll
+  for (int t = 0; t < PW; ++t)
+#pragma unroll
+    for (int k = 0; k < kRowBatch; ++k) {
+      const int i = lane + 32 * k;
+      bv[t][k] = live[t] && i < P ? Num<R>::ld(row[t], i) : Num<R>::zero();
+    }
+  const int jl = it.y * PTS + lane;  // warp 0: the point of lane l < PTS
   dbl4 yw = make_dbl4(0.0, 0.0, 0.0, 0.0);
-  if (warp == 0 && lane < kSurfWarps && jl < M) yw = surfx[S.surf + jl];
+  if (warp == 0 && lane < PTS && jl < M) yw = surfx[S.surf + jl];
 
   grid_dependency_wait();  // the coefficients of k_coef_reduce
   R* A = reinterpret_cast<R*>(sm);  // [P] A'_nm
@@ -1119,40 +1267,45 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface_mat(const SysDev* __re
     nA[i] = Num<R>::from_int(nn) * c;
   }
   __syncthreads();
-  R ph = Num<R>::zero(), dph = Num<R>::zero();
+  R v[2 * PW];
+#pragma unroll
+  for (int t = 0; t < 2 * PW; ++t) v[t] = Num<R>::zero();
   for (int i0 = 0;;) {
 #pragma unroll
     for (int k = 0; k < kRowBatch; ++k) {
       const int i = i0 + lane + 32 * k;
       if (i < P) {
-        ph = Num<R>::acc(ph, A[i], bv[k]);
-        dph = Num<R>::acc(dph, nA[i], bv[k]);
+        const R a = A[i], na = nA[i];
+#pragma unroll
+        for (int t = 0; t < PW; ++t) {
+          v[t] = Num<R>::acc(v[t], a, bv[t][k]);
+          v[PW + t] = Num<R>::acc(v[PW + t], na, bv[t][k]);
+        }
       }
     }
     i0 += 32 * kRowBatch;
     if (i0 >= P) break;
 #pragma unroll
-    for (int k = 0; k < kRowBatch; ++k) {
-      const int i = i0 + lane + 32 * k;
-      bv[k] = live && i < P ? Num<R>::ld(row, i) : Num<R>::zero();
-    }
+    for (int t = 0; t < PW; ++t)
+#pragma unroll
+      for (int k = 0; k < kRowBatch; ++k) {
+        const int i = i0 + lane + 32 * k;
+        bv[t][k] = live[t] && i < P ? Num<R>::ld(row[t], i) : Num<R>::zero();
+      }
   }
-  ph = Num<R>::norm(ph);
-  dph = Num<R>::norm(dph);
-  for (int off = 16; off > 0; off >>= 1) {
-    ph = ph + Num<R>::shfl(ph, off);
-    dph = dph + Num<R>::shfl(dph, off);
-  }
-  if (lane == 0) {
-    s_ph[warp] = ph;
-    s_dph[warp] = dph;
-  }
+#pragma unroll
+  for (int t = 0; t < 2 * PW; ++t) v[t] = Num<R>::norm(v[t]);
+  treduce_r<2 * PW>(v, lane);
+  constexpr int sh = PW == 4 ? 2 : (PW == 2 ? 3 : 4);  // lane l holds sum (l >> sh) mod 2 PW
+  if ((lane & ((1 << sh) - 1)) == 0) s_sum[warp][lane >> sh] = Num<R>::norm(v[0]);
   __syncthreads();
   // the records of the block's points from one warp (lane l: point l), so that their FP64
   // arithmetic issues once per block rather than once per point
-  if (warp == 0 && lane < kSurfWarps && jl < M)
-    surface_records(S, S.surf + jl, yw, Num<R>::to(s_ph[lane]), Num<R>::to(s_dph[lane]), prec, surf_a, surf_b,
+  if (warp == 0 && lane < PTS && jl < M) {
+    const int w = lane / PW, t = lane % PW;
+    surface_records(S, S.surf + jl, yw, Num<R>::to(s_sum[w][t]), Num<R>::to(s_sum[w][PW + t]), prec, surf_a, surf_b,
                     surf64_a, surf64_b, surfqd);
+  }
 }
 
 // Without a basis table (too large for the workspace): lane m runs column m of the recurrence
@@ -1219,19 +1372,36 @@ __global__ __launch_bounds__(kSurfThreads) void k_surface(const SysDev* __restri
   if (lane == 0) surface_records(S, o, yw, ph, dph, prec, surf_a, surf_b, surf64_a, surf64_b, surfqd);
 }
 
-void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, const double* coef,
+template <int PW>
+static void launch_surface_mat(const int2* items, int nitems, size_t smem, const SysDev* sys, const double* coef,
+                               const float2* coef2, const double* sb, float4* surf_a, float4* surf_b,
+                               dbl4* surf64_a, double* surf64_b, dbl4* surfx, double2* surfqd, int prec,
+                               cudaStream_t st)
+{
+  if (prec == HSMA_FP64)
+    launch_pdl(k_surface_mat<PW, double>, nitems, kSurfThreads, smem, st, sys, items, coef, coef2, sb, surf_a, surf_b,
+               surf64_a, surf64_b, surfx, surfqd, prec);
+  else
+    launch_pdl(k_surface_mat<PW, df>, nitems, kSurfThreads, smem, st, sys, items, coef, coef2, sb, surf_a, surf_b,
+               surf64_a, surf64_b, surfx, surfqd, prec);
+}
+
+void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, int pw, const double* coef,
                     const float2* coef2, const double* sb, Tables tab, float4* surf_a, float4* surf_b,
                     dbl4* surf64_a, double* surf64_b, dbl4* surfx, double2* surfqd, int prec, cudaStream_t st)
 {
   if (nitems <= 0) return;
   if (sb) {
     const size_t smem = 2 * (size_t)maxP * sizeof(double);
-    if (prec == HSMA_FP64)
-      launch_pdl(k_surface_mat<double>, nitems, kSurfThreads, smem, st, sys, items, coef, coef2, sb, surf_a, surf_b,
-                 surf64_a, surf64_b, surfx, surfqd, prec);
+    if (pw == 4)
+      launch_surface_mat<4>(items, nitems, smem, sys, coef, coef2, sb, surf_a, surf_b, surf64_a, surf64_b, surfx,
+                            surfqd, prec, st);
+    else if (pw == 2)
+      launch_surface_mat<2>(items, nitems, smem, sys, coef, coef2, sb, surf_a, surf_b, surf64_a, surf64_b, surfx,
+                            surfqd, prec, st);
     else
-      launch_pdl(k_surface_mat<df>, nitems, kSurfThreads, smem, st, sys, items, coef, coef2, sb, surf_a, surf_b,
-                 surf64_a, surf64_b, surfx, surfqd, prec);
+      launch_surface_mat<1>(items, nitems, smem, sys, coef, coef2, sb, surf_a, surf_b, surf64_a, surf64_b, surfx,
+                            surfqd, prec, st);
     return;
   }
   const size_t smem = (size_t)maxP * sizeof(double);
@@ -1247,7 +1417,9 @@ template <class R>
 static void surface_attrs()
 {
   cudaFuncSetAttribute(k_surface<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-  cudaFuncSetAttribute(k_surface_mat<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+  cudaFuncSetAttribute(k_surface_mat<1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+  cudaFuncSetAttribute(k_surface_mat<2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+  cudaFuncSetAttribute(k_surface_mat<4, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
 }
 
 void init_source_kernels()
