@@ -278,7 +278,7 @@ def timed_steps(step, stream, flush, k):
 
 
 def pair_kernel_alone(b, step, flush, reps):
-    """The pair kernel timed alone: in the timed steps it overlaps the coefficient chain, so it
+    """The pair kernel timed alone: in the timed steps it runs in one graph with the build, so it
     is timed in separate passes (same items, bitwise the same results), CUDA events around each
     launch on its stream; mean seconds per launch."""
     b.hsma_batch_set_overlap(False)
@@ -358,7 +358,8 @@ def run_near_interface(local, stream, gpu_name, steps):
             "pair_kernel_alone": {"ms": t_pair * 1e3, "launches": nrep,
                                   "frac_of_mufu_peak_at_2070MHz": units / t_pair / peak,
                                   "frac_kernel_evals": sum(evals(s) for s in systems) / t_pair / peak},
-            "e2e": e2e, "pair_config": batch.pair_configs()[cfg], "accuracy_vs_oracle": acc,
+            "e2e": e2e, "pair_config": batch.pair_configs()[cfg], "pair_schedule": b.hsma_batch_pair_schedule(),
+            "accuracy_vs_oracle": acc,
             "l2": "flushed before every timed step (256 MB write)"}
 
 
@@ -431,7 +432,8 @@ def run_batched(local, stream, gpu_name):
     return {"workload": f"{len(systems)} cavities, N log-uniform [100, 1e4] (sum {int(n.sum())}), a~U[0.8,1.5], "
                         "kappa*a~U[0.5,3], eps1 in {1, 78.5}, eps2=78.5, M=1000, p=20",
             "req_per_s": len(systems) * k / t, "pair_evals_per_s": tot_pairs * k / t, "ms_per_batch": t / k * 1e3,
-            "pair_config": batch.pair_configs()[cfg], "energy_rel_err_max_vs_oracle_sample": worst,
+            "pair_config": batch.pair_configs()[cfg], "pair_schedule": b.hsma_batch_pair_schedule(),
+            "energy_rel_err_max_vs_oracle_sample": worst,
             "pair_kernel_alone": {"ms": t_kern * 1e3, "evals_per_s": kern_evals,
                                   "frac_of_mufu_peak_at_2070MHz": kern_evals / peak},
             "fp64_single_system": {"req_per_s": fp64_req_s, "pair_evals_per_s": fp64_pairs_s,
@@ -465,8 +467,8 @@ def run_field(local, stream, systems, gpu_name):
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     t = sum(a.elapsed_time(c) for a, c in ev) / 1e3
-    # the field kernel alone: in the timed steps it overlaps the coefficient chain, so it is timed
-    # in separate passes (same items), events around each launch
+    # the field kernel alone: in the timed steps it runs in one graph with the build, so it is
+    # timed in separate passes (same items), events around each launch
     b.hsma_batch_set_overlap(False)
     kern = []
     for _ in range(50):
@@ -627,10 +629,11 @@ def run_ours(args):
                                  "pair (Newton's third law; Kelvin inversion), N(N-1)/2 + N(N+1)/2 + NM per cavity "
                                  "(+ ~1% for the one-way diagonal blocks): the MUFU's own utilisation",
             "pair_kernel_ms": t_pair * 1e3, "pair_config": batch.pair_configs()[cfg], "pair_config_index": cfg,
+            "pair_schedule": b.hsma_batch_pair_schedule(),
             "pairs_per_launch": units,
             "timing": f"{nrep} launches in separate passes (L2 flushed before each step), CUDA events "
-                      "on the launch stream; in the timed steps the kernel runs overlapped with the "
-                      "coefficient chain"}
+                      "on the launch stream; in the timed steps the kernel runs in one graph with the "
+                      "build (order and records beside the coefficient chain, then the pair sum)"}
     if clk.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / (sms * SM_MUFU_PER_CLK * clk["sm_mhz"] * 1e6)
 
@@ -721,8 +724,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the near-interface, field, batched and "
                                                              "serving sections")
     ap.add_argument("--pair-config", type=int, default=-1,
-                    help="with --only pairs: this tile configuration (index of batch.pair_configs()) instead "
-                         "of the autotuned one")
+                    help="with --only pairs / steps / near_steps: this tile configuration (index of "
+                         "batch.pair_configs()) instead of the autotuned one")
+    ap.add_argument("--pair-schedule", type=int, default=-1, choices=[-1, 0, 1],
+                    help="with --only steps / near_steps and --pair-config: the real/Kelvin pair schedule "
+                         "(1 beside the coefficient chain, 0 after it; -1 the library's default)")
     ap.add_argument("--only", choices=["batched", "serving", "field", "near", "pairs", "steps", "near_steps"],
                     help="run one section alone (profiling); 'pairs': the headline workload's pair kernel "
                          "in separate passes (--steps launches); 'steps' / 'near_steps': --warmup + --steps "
@@ -745,7 +751,7 @@ def main():
             out = run_pairs_only(0, st, name, args.steps, args.warmup, args.pair_config)
         elif args.only in ("steps", "near_steps"):
             wl = workload(0) if args.only == "steps" else near_interface_workload(0)
-            out = run_steps_only(0, st, name, wl, args.steps, args.warmup, args.pair_config)
+            out = run_steps_only(0, st, name, wl, args.steps, args.warmup, args.pair_config, args.pair_schedule)
         else:
             out = run_serving(0)
         print(json.dumps(out), flush=True)
@@ -786,9 +792,10 @@ def run_pairs_only(local, stream, gpu_name, steps, warmup, pair_config=-1):
             "pair_kernel_ms_mean": statistics.mean(ms) if ms else None, "launches": len(ms)}
 
 
-def run_steps_only(local, stream, gpu_name, systems, steps, warmup, pair_config=-1):
-    """warmup + steps whole-path steps (build + potentials, the overlapped graph) of a workload,
-    device inputs, nothing else (for launch lists); the tile configuration given or autotuned."""
+def run_steps_only(local, stream, gpu_name, systems, steps, warmup, pair_config=-1, pair_schedule=-1):
+    """warmup + steps whole-path steps (build + potentials in one graph) of a workload,
+    device inputs, nothing else (for launch lists); the tile configuration and pair schedule
+    given or autotuned."""
     import torch
 
     from paper_1907_01724_gb300 import api, batch
@@ -797,6 +804,7 @@ def run_steps_only(local, stream, gpu_name, systems, steps, warmup, pair_config=
     if pair_config >= 0:
         cfg = pair_config
         b.hsma_batch_set_pair_config(cfg)
+        b.hsma_batch_set_pair_schedule(pair_schedule)
     else:
         cfg = batch.autotuned(b, n, xyz, q, gpu=gpu_name, reps=5)
     xyz_d = torch.tensor(xyz, device=f"cuda:{local}")
@@ -807,7 +815,8 @@ def run_steps_only(local, stream, gpu_name, systems, steps, warmup, pair_config=
         b.hsma_batch_potential(api.HSMA_TOTAL, out=phi_d)
     torch.cuda.synchronize()
     return {"systems": len(systems), "N": [s.n for s in systems], "pair_config": batch.pair_configs()[cfg],
-            "pair_config_index": cfg, "steps": steps, "warmup": warmup}
+            "pair_config_index": cfg, "pair_schedule": b.hsma_batch_pair_schedule(), "steps": steps,
+            "warmup": warmup}
 
 
 if __name__ == "__main__":

@@ -162,9 +162,11 @@ HSMA_API int64_t hsma_kernel_launches(const hsma_t* h);
 /* Scheduling of a build followed by a potential/energy evaluation.  hsma_build_sources copies
  * the inputs and defers the source kernels to the first call that needs them.  on = 1 (the
  * default): a potential or energy evaluation right after a build runs the build and the pair
- * sum as one graph, the real-charge/Kelvin part of the pair sum overlapping the coefficient and
- * surface kernels; on = 0: separate passes (the pair kernel then runs alone on the GPU, which
- * is how hsma_last_pair_time times it in isolation).  Results are bitwise the same either way. */
+ * sum as one graph (the spatial order and the image records beside the coefficient and surface
+ * kernels; a single cavity also runs the real-charge/Kelvin part of the pair sum beside them,
+ * see hsma_batch_set_pair_schedule); on = 0: separate passes (the pair kernel then runs alone
+ * on the GPU, which is how hsma_last_pair_time times it in isolation).  Results are bitwise
+ * the same either way. */
 HSMA_API int hsma_set_overlap(hsma_t* h, int on);
 
 /* Device time in milliseconds of the most recent pair-sum kernel launch of the handle (the
@@ -237,12 +239,26 @@ HSMA_API int hsma_batch_last_pair_time(hsma_batch_t* b, float* ms);
 /* Build/potential scheduling of the batch (see hsma_set_overlap). */
 HSMA_API int hsma_batch_set_overlap(hsma_batch_t* b, int on);
 
+/* Where the graph of a build followed by a potential/energy evaluation (overlap on) runs the
+ * pair sum of the real charges and Kelvin images, which needs only the image records:
+ * mode = 1 in a launch of its own right after the records, beside the coefficient and surface
+ * kernels (a full grid at the lowest launch priority); mode = 0 in one launch with the surface
+ * images after those kernels; mode = -1 (the default) the autotuned choice for this size class
+ * if there is one (hsma_batch_autotune times both), else 1 for up to 8 cavities and 0 for
+ * more.  Results are bitwise the same either way; the choice takes effect at the next build
+ * (as hsma_batch_set_pair_config does).  HSMA_E_INVALID_ARG for another mode.
+ * hsma_batch_pair_schedule writes the schedule of the current layout (0 or 1) to *mode. */
+HSMA_API int hsma_batch_set_pair_schedule(hsma_batch_t* b, int mode);
+HSMA_API int hsma_batch_pair_schedule(const hsma_batch_t* b, int* mode);
+
 /* Pair-sum tile configurations: CTA threads x targets per thread, and the number of pair work
  * items per resident CTA slot the layout aims for (any pointer may be NULL).
  * hsma_batch_set_pair_config forces one (-1 = automatic); hsma_batch_autotune times every
- * configuration on the current inputs (reps runs each, CUDA events: the overlapped build +
- * potential step, or with overlap off the potential pass alone) and keeps the fastest for this
- * size class; *best and *best_ms (nullable) receive the choice and its time. */
+ * configuration on the current inputs (reps runs each, CUDA events: the build + potential step
+ * in one graph, or with overlap off the potential pass alone; the three fastest again in
+ * interleaved rounds; then, with overlap on and no forced schedule, the winner with both pair
+ * schedules of hsma_batch_set_pair_schedule) and keeps the fastest for this size class;
+ * *best and *best_ms (nullable) receive the configuration and its time. */
 HSMA_API int hsma_pair_config_count(void);
 HSMA_API int hsma_pair_config_info(int idx, int* threads, int* targets_per_thread, int* items_per_slot);
 HSMA_API int hsma_batch_set_pair_config(hsma_batch_t* b, int cfg);

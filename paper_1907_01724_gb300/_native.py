@@ -153,6 +153,8 @@ def _declare(lib):
         "hsma_batch_apply_moves": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp]),
         "hsma_batch_kernel_launches": (ctypes.c_int64, [vp]),
         "hsma_batch_set_overlap": (ctypes.c_int, [vp, ctypes.c_int]),
+        "hsma_batch_set_pair_schedule": (ctypes.c_int, [vp, ctypes.c_int]),
+        "hsma_batch_pair_schedule": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
         "hsma_batch_last_pair_time": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "hsma_pair_config_count": (ctypes.c_int, []),
         "hsma_pair_config_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),

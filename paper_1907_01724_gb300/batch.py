@@ -161,6 +161,14 @@ class Batch:
     def hsma_batch_set_pair_config(self, cfg: int):
         self._check(self.lib.hsma_batch_set_pair_config(self.ptr, int(cfg)))
 
+    def hsma_batch_set_pair_schedule(self, mode: int):
+        self._check(self.lib.hsma_batch_set_pair_schedule(self.ptr, int(mode)))
+
+    def hsma_batch_pair_schedule(self) -> int:
+        mode = ctypes.c_int()
+        self._check(self.lib.hsma_batch_pair_schedule(self.ptr, ctypes.byref(mode)))
+        return int(mode.value)
+
     def hsma_batch_autotune(self, reps: int = 5):
         best = ctypes.c_int()
         ms = ctypes.c_float()
@@ -221,8 +229,8 @@ class TuneCache:
     def get(self, n, gpu: str, params=None):
         return self.data.get(self.key(n, gpu, params))
 
-    def put(self, n, gpu: str, cfg: int, ms: float, params=None):
-        self.data[self.key(n, gpu, params)] = {"cfg": int(cfg), "ms": float(ms)}
+    def put(self, n, gpu: str, cfg: int, ms: float, params=None, schedule: int = -1):
+        self.data[self.key(n, gpu, params)] = {"cfg": int(cfg), "ms": float(ms), "schedule": int(schedule)}
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         tmp = self.path + f".{os.getpid()}"
         with open(tmp, "w") as f:
@@ -231,16 +239,18 @@ class TuneCache:
 
 
 def autotuned(batch: Batch, n, xyz, q, gpu: str = "", reps: int = 5, cache: TuneCache | None = None) -> int:
-    """Build, then use the cached tile configuration for this size class or autotune and cache it."""
+    """Build, then use the cached tile configuration and pair schedule for this size class or
+    autotune and cache them."""
     cache = cache or TuneCache()
     hit = cache.get(n, gpu, batch.params)
     if hit is not None:
         batch.hsma_batch_set_pair_config(hit["cfg"])
+        batch.hsma_batch_set_pair_schedule(hit.get("schedule", -1))
         batch.hsma_batch_build_sources(n, xyz, q)
         return hit["cfg"]
     batch.hsma_batch_build_sources(n, xyz, q)
     cfg, ms = batch.hsma_batch_autotune(reps)
     batch.hsma_batch_set_pair_config(cfg)
     batch.hsma_batch_build_sources(n, xyz, q)
-    cache.put(n, gpu, cfg, ms, batch.params)
+    cache.put(n, gpu, cfg, ms, batch.params, schedule=batch.hsma_batch_pair_schedule())
     return cfg

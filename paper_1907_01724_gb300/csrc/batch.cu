@@ -26,12 +26,15 @@ namespace hsma {
 // rebuilds its sources from them in place.  A sweep takes the median of reps steps per
 // configuration; the kTuneFinal fastest are then timed again in interleaved rounds (one step of
 // each per round, 2 reps rounds), so that a drift of the clocks over the sweep does not decide
-// between configurations a few percent apart.
+// between configurations a few percent apart.  With overlap on, the winner is then timed with
+// both schedules of the real/Kelvin pair items (beside the moment chain or after it, see
+// issue_fused) in interleaved rounds, and the faster schedule is kept with it.
 constexpr int kTuneFinal = 3;
 
-int Engine::tune_time_config(int c, int steps, std::vector<float>& t)
+int Engine::tune_time_config(int c, int side_mode, int steps, std::vector<float>& t)
 {
   forced_cfg = c;
+  forced_side = side_mode;
   layout_uploaded = false;
   const std::vector<int64_t> ns = cur_ns;
   int rc = set_sizes(ns);
@@ -87,7 +90,8 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
     ws_cap = need;
     ws_owned = true;
   }
-  const int saved_forced = forced_cfg;
+  const int saved_forced = forced_cfg, saved_side = forced_side;
+  const int side0 = choose_side(ns);  // the schedule of the sweep (forced, tuned or default)
   auto median = [](std::vector<float>& t) {
     std::sort(t.begin(), t.end());
     return t[t.size() / 2];
@@ -95,7 +99,7 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
   std::vector<std::pair<float, int>> sweep;
   for (int c = 0; c < pair_config_count(); ++c) {
     std::vector<float> t;
-    int rc = tune_time_config(c, reps, t);
+    int rc = tune_time_config(c, side0, reps, t);
     if (rc) return rc;
     sweep.emplace_back(median(t), c);
   }
@@ -104,7 +108,7 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
   std::vector<std::vector<float>> tf(nfin);
   for (int round = 0; round < 2 * reps && nfin > 1; ++round)
     for (int k = 0; k < nfin; ++k) {
-      int rc = tune_time_config(sweep[k].second, 1, tf[k]);
+      int rc = tune_time_config(sweep[k].second, side0, 1, tf[k]);
       if (rc) return rc;
     }
   int best = sweep[0].second;
@@ -119,7 +123,21 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
       }
     }
   }
+  // the schedule of the real/Kelvin items for the winner (only a forced schedule is kept as is)
+  int best_side = side0;
+  if (overlap && saved_side < 0) {
+    std::vector<float> ts[2];
+    for (int round = 0; round < 2 * reps; ++round)
+      for (int sd = 0; sd < 2; ++sd) {
+        int rc = tune_time_config(best, sd, 1, ts[sd]);
+        if (rc) return rc;
+      }
+    const float m0 = median(ts[0]), m1 = median(ts[1]);
+    best_side = m1 <= m0 ? 1 : 0;
+    best_ms = std::min(m0, m1);
+  }
   forced_cfg = saved_forced;
+  forced_side = saved_side;
   const int bucket = tune_bucket([&] {
     int64_t s = 0;
     for (auto v : ns) s += v;
@@ -127,11 +145,12 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
   }(), (int)ns.size());
   bool found = false;
   for (auto& e : tuned)
-    if (e.first == bucket) {
-      e.second = best;
+    if (e.bucket == bucket) {
+      e.cfg = best;
+      e.side = best_side;
       found = true;
     }
-  if (!found) tuned.emplace_back(bucket, best);
+  if (!found) tuned.push_back(Tuned{bucket, best, best_side});
   layout_uploaded = false;
   int rc = set_sizes(ns);
   if (rc) return rc;
@@ -336,6 +355,26 @@ int hsma_batch_set_overlap(hsma_batch_t* b, int on)
 {
   if (!b) return HSMA_E_INVALID_ARG;
   b->e->overlap = on != 0;
+  return HSMA_OK;
+}
+
+int hsma_batch_set_pair_schedule(hsma_batch_t* b, int mode)
+{
+  if (!b || mode < -1 || mode > 1) return berr(b, HSMA_E_INVALID_ARG, "bad schedule");
+  if (b->e->forced_side != mode) {
+    b->e->forced_side = mode;
+    b->e->layout_uploaded = false;  // the next call rebuilds the layout and its graphs
+    b->e->sources_ready = false;
+    b->e->build_pending = false;
+    b->n.clear();
+  }
+  return HSMA_OK;
+}
+
+int hsma_batch_pair_schedule(const hsma_batch_t* b, int* mode)
+{
+  if (!b || !mode) return HSMA_E_INVALID_ARG;
+  *mode = b->e->have_layout ? b->e->rk_side : b->e->choose_side(b->e->cur_ns);
   return HSMA_OK;
 }
 

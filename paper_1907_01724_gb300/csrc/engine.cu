@@ -642,6 +642,7 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
   if (have_layout && ns == cur_ns && layout_uploaded) return HSMA_OK;
   const int cfg = prec == HSMA_FP64 ? 0 : choose_config(ns);
   L = make_layout(ns, cfg);
+  rk_side = prec == HSMA_FP64 ? 1 : choose_side(ns);
   cur_ns = ns;
   have_layout = true;
   if (L.bytes > ws_cap) {
@@ -807,20 +808,24 @@ void Engine::launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t 
     launch_pairs_f32(L.cfg, grid, sys_d, w1, w2, srchi_d, srclo_d, surfa_d, surfb_d, boxes_d, part_d, st, pdl);
 }
 
-// Build and potentials in one graph.  The real/Kelvin pair items need only the records, so they
-// start on the second stream right after k_images, beside the moment -> coefficient -> surface
-// chain, on a full grid at the lowest launch priority: the chain's kernels (small blocks, higher
-// priority) are dispatched first whenever they have blocks waiting, and the pair CTAs take
-// every slot the chain leaves free.  (A grid capped to keep slots for the chain leaves SMs idle
-// while the chain's kernels are short of blocks; it was slower on every workload measured.)
-// After the chain, the main stream runs one full-grid launch that takes the surface items and
-// then drains whatever real/Kelvin items the first launch has not taken, from the same list and
-// work counter (each item is taken once, by whichever CTA gets it).
-//   side:  k_order_* -> k_images -> k_pairs (real/Kelvin)
-//   main:  k_moment_prep -> k_moment_units -> k_coef_reduce -> k_surface_mat -> [wait records]
-//          k_pairs (surface, then real/Kelvin)
-//   join:  k_reduce
-
+// Build and potentials in one graph: the order and the records on the second stream beside the
+// moment -> coefficient -> surface chain, then the pair sum and the reduction.  The real/Kelvin
+// pair items need only the records; where they run is the layout's schedule (rk_side):
+//   1: side:  k_order_keys -> k_order_sort -> k_images -> k_pairs (real/Kelvin, full grid, lowest
+//             launch priority)
+//      main:  k_moment_prep -> k_moment_units -> k_coef_reduce -> k_surface_mat -> k_pairs
+//             (surface items, then the real/Kelvin items the first launch has not taken) -> join
+//             -> k_reduce
+//   0: side:  k_order_keys -> k_order_sort -> k_images
+//      main:  the same chain -> [wait records] k_pairs (surface items, then every real/Kelvin
+//             item) -> k_reduce
+// With 1 the real/Kelvin sum fills the SMs that the chain's latency-bound kernels leave idle,
+// but its persistent CTAs also hold every SM's registers once the moment units drain, so the
+// coefficient and surface kernels may wait for the whole real/Kelvin sum: faster for one or two
+// cavities (0.333 against 0.349 ms at N = 20000; 66 against 72 us for two cavities of N = 2000),
+// slower for a batch of 512 (7.1 against 6.2 ms).  The autotuner times both for a size class.
+// Either way each item is evaluated once, from the same lists and work counters, so results are
+// bitwise the same.
 void Engine::issue_fused()
 {
   if (L.itord.empty()) {
@@ -833,16 +838,17 @@ void Engine::issue_fused()
   const int occ = prec == HSMA_FP64 ? std::max(occ_f64, 1) : std::max(occ_f32[L.cfg], 1);
   const int slots = num_sms * occ;
   const int nw = L.nw;  // workers per CTA
+  const bool side_rk = rk_side != 0 && L.nRK > 0;
   const int grid_rk = std::max(1, std::min((L.nRK + nw - 1) / nw, slots));
   const int grid_s = std::max(1, std::min((nS + L.nRK + nw - 1) / nw, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);
-  // launch priorities: the order and the records (short, and the real/Kelvin launch waits for
-  // them) first, the moment -> coefficient -> surface chain next, the real/Kelvin launch last,
-  // so that its CTAs take only what the chains leave free; k_order_keys also
-  // zeroes both pair work counters (ctr_pairs_d and ctr_pairs2_d, adjacent), which the main
-  // stream's launch uses only after ev_img
-  const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d, std::min(grid_rk * nw, L.nRK)};
+  // launch priorities: the order and the records first, the moment chain next, a real/Kelvin
+  // launch beside the chain last, so that its CTAs take only what the chains leave free;
+  // k_order_keys also zeroes both pair work counters (ctr_pairs_d and ctr_pairs2_d, adjacent),
+  // which the pair launches use only after ev_img.  The items a launch takes statically (one
+  // per worker, `first`) belong to the launch that has the list as its first list.
+  const PairWork rk{it4x_d, L.nRK, ctr_pairs2_d, side_rk ? std::min(grid_rk * nw, L.nRK) : 0};
   const PairWork srf{it4x_d + L.nRK, nS, ctr_pairs_d, std::min(grid_s * nw, nS)}, none{nullptr, 0, nullptr, 0};
   {
     PriorityScope ps(prio_hi);
@@ -852,8 +858,10 @@ void Engine::issue_fused()
                   prec, status_d, side);
   }
   cudaEventRecord(ev_img, side);
-  launch_pair_items(rk, none, grid_rk, side);
-  cudaEventRecord(ev_join, side);
+  if (side_rk) {
+    launch_pair_items(rk, none, grid_rk, side);
+    cudaEventRecord(ev_join, side);
+  }
   PriorityScope ps(prio_mid);
   issue_moments();
   // the records are joined before the coefficients (done by then), so that the main stream's
@@ -865,7 +873,7 @@ void Engine::issue_fused()
                  L.surf_pw, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d, surf64a_d, surf64b_d, surfx_d,
                  surfqd_d, prec, stream);
   launch_pair_items(srf, rk, grid_s, stream, true);
-  cudaStreamWaitEvent(stream, ev_join, 0);
+  if (side_rk) cudaStreamWaitEvent(stream, ev_join, 0);
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
                 phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, outdesc_d, stream, true);
 }
@@ -873,7 +881,8 @@ void Engine::issue_fused()
 int Engine::fused_launch_count() const
 {
   if (L.itord.empty()) return build_launch_count() + pot_launch_count();
-  return build_launch_count() + (L.nRK > 0 ? 1 : 0) + (L.it4x.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1);
+  return build_launch_count() + (rk_side != 0 && L.nRK > 0 ? 1 : 0) + (L.it4x.empty() ? 0 : 1) +
+         (L.it5.empty() ? 0 : 1);
 }
 
 int Engine::run_graph(cudaGraphExec_t* g, void (Engine::*issue)())
@@ -1133,19 +1142,19 @@ void Engine::issue_field()
   launch_field_reduce(stream);
 }
 
-// Build and field pass in one graph, as issue_fused does for the potentials: the field items of
-// the real/Kelvin records on the second stream right after the records (full grid, lowest
-// priority), the surface items and the rest after the moment chain.
+// Build and field pass in one graph, as issue_fused does for the potentials (the same
+// schedule of the real/Kelvin field items: beside the moment chain or after it).
 void Engine::issue_field_fused()
 {
   const int nsys = (int)L.sd.size();
   const int nS = (int)L.it4fx.size() - L.nRKf;
   const int slots = field_slots();
+  const bool side_rk = rk_side != 0 && L.nRKf > 0;
   const int grid_rk = std::max(1, std::min(L.nRKf, slots));
   const int grid_s = std::max(1, std::min(nS + L.nRKf, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);
-  const PairWork rk{it4fx_d, L.nRKf, ctr_pairs2_d, std::min(grid_rk, L.nRKf)};
+  const PairWork rk{it4fx_d, L.nRKf, ctr_pairs2_d, side_rk ? std::min(grid_rk, L.nRKf) : 0};
   const PairWork srf{it4fx_d + L.nRKf, nS, ctr_pairs_d, std::min(grid_s, nS)}, none{nullptr, 0, nullptr, 0};
   {
     PriorityScope ps(prio_hi);
@@ -1155,8 +1164,10 @@ void Engine::issue_field_fused()
                   prec, status_d, side);
   }
   cudaEventRecord(ev_img, side);
-  launch_field_items(rk, none, grid_rk, side);
-  cudaEventRecord(ev_join, side);
+  if (side_rk) {
+    launch_field_items(rk, none, grid_rk, side);
+    cudaEventRecord(ev_join, side);
+  }
   PriorityScope ps(prio_mid);
   issue_moments();
   cudaStreamWaitEvent(stream, ev_img, 0);  // (as in issue_fused)
@@ -1166,7 +1177,7 @@ void Engine::issue_field_fused()
                  L.surf_pw, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d, surf64a_d, surf64b_d, surfx_d,
                  surfqd_d, prec, stream);
   launch_field_items(srf, rk, grid_s, stream, true);
-  cudaStreamWaitEvent(stream, ev_join, 0);
+  if (side_rk) cudaStreamWaitEvent(stream, ev_join, 0);
   launch_field_reduce(stream);
 }
 
@@ -1182,7 +1193,8 @@ int Engine::field()
     rc = run_graph(&g_field_fused, &Engine::issue_field_fused);
     if (rc) return rc;
     leave();
-    launches += build_launch_count() + (L.nRKf > 0 ? 1 : 0) + (L.it4fx.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1);
+    launches += build_launch_count() + (rk_side != 0 && L.nRKf > 0 ? 1 : 0) + (L.it4fx.empty() ? 0 : 1) +
+                (L.it5.empty() ? 0 : 1);
     build_pending = false;
   } else {
     rc = ensure_built();
@@ -1280,8 +1292,22 @@ int Engine::choose_config(const std::vector<int64_t>& ns) const
   for (auto v : ns) tot += v;
   const int bucket = tune_bucket(tot, (int)ns.size());
   for (const auto& e : tuned)
-    if (e.first == bucket) return e.second;
+    if (e.bucket == bucket) return e.cfg;
   return 0;
+}
+
+// Schedule of the real/Kelvin pair items in the fused graph: forced, else the size class's
+// tuned choice, else beside the moment chain for a few cavities and after it for many (the
+// faster one on the single-cavity and two-cavity workloads and on a batch of 512 measured).
+int Engine::choose_side(const std::vector<int64_t>& ns) const
+{
+  if (forced_side >= 0) return forced_side;
+  int64_t tot = 0;
+  for (auto v : ns) tot += v;
+  const int bucket = tune_bucket(tot, (int)ns.size());
+  for (const auto& e : tuned)
+    if (e.bucket == bucket) return e.side;
+  return ns.size() <= 8 ? 1 : 0;
 }
 
 int tune_bucket(int64_t total_n, int nsys)

@@ -101,8 +101,9 @@ class Engine {
   int delta_energy(int64_t k, const double* x_new, double* de);
   int apply_move(int64_t k, const double* x_new);
   int choose_config(const std::vector<int64_t>& ns) const;
+  int choose_side(const std::vector<int64_t>& ns) const;
   int autotune(int reps, int* best, float* best_ms);
-  int tune_time_config(int c, int steps, std::vector<float>& t);  // (autotune) steps timed after a rebuild
+  int tune_time_config(int c, int side, int steps, std::vector<float>& t);  // (autotune) steps after a rebuild
   int fail(int code, const char* fmt, ...);
   int cuda_fail(cudaError_t e, const char* what);
   void drop_graphs();
@@ -115,7 +116,15 @@ class Engine {
   bool own_stream = false;
   bool use_graphs = true;
   int forced_cfg = -1;
-  std::vector<std::pair<int, int>> tuned;  // (size bucket, pair config)
+  // where the fused build + potential graph runs the real/Kelvin pair items: 1 = a launch of
+  // their own beside the moment chain, 0 = with the surface items after it (issue_fused);
+  // forced_side >= 0 forces it, otherwise the tuned choice of the size class or a default
+  int forced_side = -1;
+  int rk_side = 1;  // the current layout's choice
+  struct Tuned {
+    int bucket, cfg, side;
+  };
+  std::vector<Tuned> tuned;  // autotuned choices per size class
   std::vector<int> occ_f32, occ_field;
   int occ_f64 = 1, occ_field64 = 1;
   std::vector<SysSpec> spec;

@@ -135,3 +135,31 @@ def test_autotune_picks_a_valid_config_and_stays_accurate():
         ref = oracle_of(s)
         assert np.linalg.norm(phi[off:off + s.n] - ref["phi"]) / np.linalg.norm(ref["phi"]) <= 1e-6
         off += s.n
+
+
+@pytest.mark.parametrize("nsys", [1, 3])
+def test_pair_schedules_agree_bitwise(nsys):
+    """The real/Kelvin pair items beside the coefficient chain (schedule 1) or after it (0): the
+    same items from the same work lists, so potentials, energies and fields are bitwise equal."""
+    systems = mixed_systems(seed=9, sizes=(1500, 700, 2100)[:nsys])
+    n, xyz, q = batch.concat(systems)
+    out = []
+    for mode in (1, 0):
+        b = batch.from_systems(systems)
+        b.hsma_batch_set_pair_schedule(mode)
+        b.hsma_batch_build_sources(n, xyz, q)
+        phi = b.hsma_batch_potential()
+        assert b.hsma_batch_pair_schedule() == mode
+        e, _ = b.hsma_batch_energy()
+        b.hsma_batch_build_sources(n, xyz, q)
+        E = b.hsma_batch_field()
+        out.append((phi, e, E))
+    for a, c in zip(out[0], out[1]):
+        assert np.array_equal(a, c)
+
+
+def test_pair_schedule_rejects_bad_modes():
+    b = batch.from_systems(mixed_systems(seed=9, sizes=(100,)))
+    for mode in (-2, 2):
+        with pytest.raises(api.HsmaError):
+            b.hsma_batch_set_pair_schedule(mode)

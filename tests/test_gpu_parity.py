@@ -207,9 +207,10 @@ def test_kernel_launch_accounting():
     api.hsma_build_sources(h, s.xyz, s.q)
     api.hsma_energy(h)
     # once per layout: k_setup, k_surface_basis; build: k_order_keys, k_order_sort, k_images,
-    # k_moment_prep, k_moment_units, k_coef_reduce, k_surface_mat; potentials (overlapped with
-    # the build): k_pairs (real/Kelvin items, capped grid), k_pairs (surface items, then the
-    # real/Kelvin items left), k_reduce
+    # k_moment_prep, k_moment_units, k_coef_reduce, k_surface_mat; potentials (the build and
+    # the pass in one graph; a single cavity's default schedule): k_pairs (real/Kelvin items,
+    # beside the coefficient chain), k_pairs (surface items, then the real/Kelvin items left),
+    # k_reduce
     assert api.hsma_kernel_launches(h) == 12
     api.hsma_set_overlap(h, False)
     api.hsma_build_sources(h, s.xyz, s.q)
