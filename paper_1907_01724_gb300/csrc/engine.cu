@@ -811,8 +811,8 @@ void Engine::launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t 
 // Build and potentials in one graph: the order and the records on the second stream beside the
 // moment -> coefficient -> surface chain, then the pair sum and the reduction.  The real/Kelvin
 // pair items need only the records; where they run is the layout's schedule (rk_side):
-//   1: side:  k_order_keys -> k_order_sort -> k_images -> k_pairs (real/Kelvin, full grid, lowest
-//             launch priority)
+//   1: side:  k_order_keys -> k_order_sort -> k_images -> k_pairs (real/Kelvin, all CTA slots but
+//             one per SM, lowest launch priority)
 //      main:  k_moment_prep -> k_moment_units -> k_coef_reduce -> k_surface_mat -> k_pairs
 //             (surface items, then the real/Kelvin items the first launch has not taken) -> join
 //             -> k_reduce
@@ -820,10 +820,11 @@ void Engine::launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t 
 //      main:  the same chain -> [wait records] k_pairs (surface items, then every real/Kelvin
 //             item) -> k_reduce
 // With 1 the real/Kelvin sum fills the SMs that the chain's latency-bound kernels leave idle,
-// but its persistent CTAs also hold every SM's registers once the moment units drain, so the
-// coefficient and surface kernels may wait for the whole real/Kelvin sum: faster for one or two
-// cavities (0.333 against 0.349 ms at N = 20000; 66 against 72 us for two cavities of N = 2000),
-// slower for a batch of 512 (7.1 against 6.2 ms).  The autotuner times both for a size class.
+// but its persistent CTAs hold their SMs' registers until the real/Kelvin items run out, so the
+// launch leaves one CTA slot per SM for the coefficient and surface kernels; still, these may
+// wait for the whole real/Kelvin sum: (1) is faster for one or two cavities (0.326 against 0.349
+// ms at N = 20000; 66 against 72 us for two cavities of N = 2000), (0) for a batch of 512 (6.2
+// against 7.1 ms).  The autotuner times both for a size class.
 // Either way each item is evaluated once, from the same lists and work counters, so results are
 // bitwise the same.
 void Engine::issue_fused()
@@ -839,7 +840,10 @@ void Engine::issue_fused()
   const int slots = num_sms * occ;
   const int nw = L.nw;  // workers per CTA
   const bool side_rk = rk_side != 0 && L.nRK > 0;
-  const int grid_rk = std::max(1, std::min((L.nRK + nw - 1) / nw, slots));
+  // the side launch leaves one CTA slot per SM (when there are at least four) to the chain's
+  // kernels, which then run beside it instead of after it: 0.326 against 0.334 ms per headline
+  // step; two slots per SM: 0.342
+  const int grid_rk = std::max(1, std::min((L.nRK + nw - 1) / nw, occ >= 4 ? slots - num_sms : slots));
   const int grid_s = std::max(1, std::min((nS + L.nRK + nw - 1) / nw, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);

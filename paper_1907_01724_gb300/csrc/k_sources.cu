@@ -1009,7 +1009,7 @@ void launch_moment_units(const SysDev* sys, const int2* units, int nunits, const
 // rows w, w + kCoefWarps, ...), and warp 0 adds the warp sums in order, so the result does not
 // depend on scheduling.  Sums run in the moment arithmetic R; the coefficient is formed in FP64
 // and also stored as an FP32 (hi, lo) pair for the FP32 path's surface synthesis.
-constexpr int kCoefWarps = 32;
+constexpr int kCoefWarps = 8;  // 256-thread blocks: they fit beside a pair launch that leaves a CTA slot free
 template <class R>
 __global__ __launch_bounds__(kCoefWarps * 32) void k_coef_reduce(const SysDev* __restrict__ sys,
                                                                  const int2* __restrict__ items,
