@@ -4,9 +4,11 @@
 // hsma_t handle is an engine with one system).  It lays every system's arrays out in one
 // device workspace, builds the work lists of the kernels (longest pair items first), and
 // records the two device phases as CUDA graphs:
-//   build:     k_moments -> k_coef_reduce -> k_surface_mat, beside k_order_* -> k_images (Sec. 2.3-2.4)
-//   potential: reset counter -> k_pairs -> k_reduce                      (Algorithm 1 step 5)
-// Graphs are re-recorded whenever the layout (sizes) or workspace changes.
+//   build:     moment rows (FP32 path: k_moment_prep -> k_moment_units; FP64 path: k_moments)
+//              -> k_coef_reduce -> k_surface_mat, beside k_order_* -> k_images     (Sec. 2.3-2.4)
+//   potential: k_pairs -> k_reduce                                     (Algorithm 1 step 5)
+// or, for an evaluation right after a build, both in one graph (issue_fused).  Graphs are
+// re-recorded whenever the layout (sizes, tile configuration, pair schedule) or workspace changes.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -202,8 +204,8 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     totn_all += ns[s];
     maxP_all = std::max(maxP_all, (spec[s].p + 1) * (spec[s].p + 1));
   }
-  // charges per moment group: the largest group when the moment blocks fit in about one wave,
-  // half-size shared memory (two blocks per SM) when there are many waves
+  // FP64 path (k_moments): charges per moment group, the largest group when the moment blocks
+  // fit in about one wave, half-size shared memory (two blocks per SM) when there are many waves
   int G = moment_smem_group(maxP_all, 1);
   if (totn_all > 4 * (int64_t)num_sms * G) G = moment_smem_group(maxP_all, 2);
   L.momG = G;

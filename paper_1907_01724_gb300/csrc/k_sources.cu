@@ -5,7 +5,9 @@
 //   k_surface_basis    (once per layout) solid harmonics of the auxiliary-sphere points
 //   k_images           trapezoid-modified Kelvin images q_K at r_K (Sec. 2.4) and the pair-sum
 //                      records, in spatial order, with the bounding box of every 32 records
-//   k_moments          charge moments of the truncated correction coefficients
+//   k_moment_prep,     charge moments of the truncated correction coefficients: FP32 path (a
+//   k_moment_units     warp per 32 charges and column pair, double-float)
+//   k_moments          the same on the FP64 path (a block per tile of charges, FP64)
 //   k_coef_reduce      correction coefficients hat A_nm (eq. phim)
 //   k_surface_mat      Phi_corr and dPhi_corr/dr at the Fibonacci points and the monopole /
 //                      dipole surface images (eqs. GreenSecond, approxG, threeintegrals,
@@ -434,7 +436,8 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
       bmin[2] = bmax[2] = h.z;
     }
     const df r2 = X * X + Y * Y + Z * Z;
-    // centre test as in kelvin_rec and k_moments, on r = sqrt(r^2) (to within the rounding of r^2)
+    // centre test of the FP32 path (k_moment_prep makes the same one), on r = sqrt(r^2) (to
+    // within the rounding of r^2)
     const bool centre = r2.hi <= S.f_rc2 && sqrt(df_to_double(r2)) <= kCentreRel * S.a;
     const df s = df_make(S.f_a2.x, S.f_a2.y) * df_recip(r2);
     const df kx = s * X, ky = s * Y, kz = s * Z;
@@ -447,7 +450,7 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
     const df rr = df_sqrt(r2);
     if (on) {
       if (centre) {
-        // image at infinity (its constant potential is added by k_moments): a zero-strength
+        // image at infinity (its constant potential is added by the moment rows): a zero-strength
         // record, left out of the box; its scale 1e15 / a turns 1 / |x_i - record| (the record
         // sits at 1e15 a) into the limit 1 / a^2 of |x_i| / (|x_j| |x_i - x_j*|) at x_j -> 0
         src_hi[sk] = make_float4((float)(1e15 * S.a), 0.f, 0.f, 0.f);

@@ -163,3 +163,28 @@ def test_pair_schedule_rejects_bad_modes():
     for mode in (-2, 2):
         with pytest.raises(api.HsmaError):
             b.hsma_batch_set_pair_schedule(mode)
+
+
+def test_large_batch_tiles_and_surface_blocks_match_oracle():
+    """A batch large enough that the moment units take several 32-charge groups per row (kg > 1:
+    more than ~96 units per SM) and the surface kernel four points per warp (at least four
+    blocks of 32 points per SM): per-system potentials and energies against the oracle."""
+    rng = np.random.default_rng(13)
+    systems = []
+    for i in range(52):
+        n = int(rng.integers(1700, 1900)) // 2 * 2
+        a = float(rng.uniform(0.8, 1.5))
+        systems.append(inputs.System(a, 1.0 if i % 2 else 78.5, 78.5, float(rng.uniform(0.5, 3.0)) / a, 20, 400,
+                                     inputs.uniform_ball(rng, n, a), inputs.neutral_charges(rng, n)))
+    n, xyz, q = batch.concat(systems)
+    b = batch.from_systems(systems)
+    b.hsma_batch_build_sources(n, xyz, q)
+    phi = b.hsma_batch_potential()
+    et, _ = b.hsma_batch_energy()
+    off = 0
+    for k, s in enumerate(systems):
+        ref = oracle_of(s)
+        assert np.linalg.norm(phi[off:off + s.n] - ref["phi"]) / np.linalg.norm(ref["phi"]) <= 1e-6, k
+        scale = max(abs(ref["E_total"]), 0.5 * np.sum(np.abs(s.q * ref["phi"])))
+        assert abs(et[k] - ref["E_total"]) <= 1e-6 * scale, k
+        off += s.n
