@@ -107,8 +107,10 @@ HSMA_API int hsma_attach_workspace(hsma_t* h, void* device_ptr, size_t bytes);
 /* Build the source set of eq. phirffinall for n charges (Sec. 2.4, Algorithm 1 step 4):
  * trapezoid-modified Kelvin images (one per charge), the truncated correction
  * coefficients, and the 3M monopole/dipole surface images on R_tau.  xyz: host (n,3),
- * q: host (n).  Every |x_i| must be < a (else HSMA_E_OUTSIDE).  n >= 0.
- * Asynchronous with respect to the host once the inputs are copied. */
+ * q: host (n).  n >= 0.  Every |x_i| must be < a with finite coordinates and charges: the
+ * first kernel of the pass checks every charge on the device (host and device inputs alike),
+ * and the evaluation that runs the pass (hsma_potential, hsma_energy, hsma_field) returns
+ * HSMA_E_OUTSIDE.  Asynchronous with respect to the host once the inputs are copied. */
 HSMA_API int hsma_build_sources(hsma_t* h, int64_t n, const double* xyz, const double* q);
 
 /* Same as hsma_build_sources with inputs already resident on the device. */
@@ -207,7 +209,8 @@ HSMA_API int hsma_batch_attach_workspace(hsma_batch_t* b, void* device_ptr, size
 HSMA_API int hsma_batch_set_max_requests(hsma_batch_t* b, int max_requests);
 
 /* Build all sources (Sec. 2.4) for n[nsys] charges per system: xyz (sum n, 3) and q (sum n),
- * host or device memory respectively. */
+ * host or device memory respectively.  A charge outside its cavity or a non-finite value is
+ * reported as HSMA_E_OUTSIDE by the evaluation that runs the pass (see hsma_build_sources). */
 HSMA_API int hsma_batch_build_sources(hsma_batch_t* b, const int64_t* n, const double* xyz, const double* q);
 HSMA_API int hsma_batch_build_sources_device(hsma_batch_t* b, const int64_t* n, const double* xyz_dev,
                                              const double* q_dev);

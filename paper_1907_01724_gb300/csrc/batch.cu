@@ -266,14 +266,8 @@ static int batch_build(hsma_batch_t* b, const int64_t* n, const double* xyz, con
   if (!sizes_ok(b, n, &tot)) return berr(b, HSMA_E_INVALID_ARG, "bad sizes");
   if (tot > 0 && (!xyz || !q)) return berr(b, HSMA_E_INVALID_ARG, "NULL xyz or q");
   std::vector<int64_t> ns(n, n + b->e->spec.size());
-  if (!dev) {
-    int64_t off = 0;
-    for (size_t s = 0; s < ns.size(); ++s) {
-      if (!hsma::charges_inside(xyz + 3 * off, q + off, ns[s], b->e->spec[s].a))
-        return berr(b, HSMA_E_OUTSIDE, "a charge lies outside its cavity (|x| >= a) or is not finite");
-      off += ns[s];
-    }
-  }
+  // (every charge is checked by the pass's first kernel, k_order_keys, for host and device
+  // inputs alike: the evaluation that runs the pass returns HSMA_E_OUTSIDE)
   int rc = b->e->set_sizes(ns);
   if (rc) return bfrom(b, rc);
   b->n = ns;

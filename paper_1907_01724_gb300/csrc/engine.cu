@@ -1497,10 +1497,8 @@ static int build_common(hsma_t* h, int64_t n, const double* xyz, const double* q
   if (!h) return HSMA_E_INVALID_ARG;
   if (n < 0 || n > (int64_t)INT32_MAX / 4) return set_err(h, HSMA_E_INVALID_ARG, "n out of range");
   if (n > 0 && (!xyz || !q)) return set_err(h, HSMA_E_INVALID_ARG, "NULL xyz or q");
-  if (!dev) {
-    if (!hsma::charges_inside(xyz, q, n, h->e->spec[0].a))
-      return set_err(h, HSMA_E_OUTSIDE, "a charge lies outside the cavity (|x| >= a) or is not finite");
-  }
+  // (every charge is checked by the pass's first kernel, k_order_keys, for host and device
+  // inputs alike: the evaluation that runs the pass returns HSMA_E_OUTSIDE)
   int rc = h->e->set_sizes({n});
   if (rc) return from_engine(h, rc);
   h->n = n;

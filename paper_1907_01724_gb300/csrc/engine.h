@@ -5,27 +5,11 @@
 #include <utility>
 #include <vector>
 
-#include <cfloat>
 #include <cmath>
 
 #include "hsma_internal.cuh"
 
 namespace hsma {
-
-// Whether charges [0, n) lie strictly inside the sphere of radius a with finite charges: one
-// pass without early exit (branch-free, so it runs at memory speed; a non-finite coordinate
-// fails r^2 < a^2).
-inline bool charges_inside(const double* xyz, const double* q, int64_t n, double a)
-{
-  const double a2 = a * a;
-  int bad = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-    const double r2 = x * x + y * y + z * z;
-    bad |= !(r2 < a2) | !(std::fabs(q[i]) <= DBL_MAX);
-  }
-  return !bad;
-}
 
 // Host description of one system (Sec. 2.1 inputs plus the numerical parameters).
 struct SysSpec {

@@ -135,8 +135,9 @@ def test_errors_are_reported():
     with pytest.raises(api.HsmaError) as e:
         api.hsma_potential(h)
     assert e.value.code == -3
+    api.hsma_build_sources(h, np.array([[0.0, 0.0, 1.0]]), np.array([1.0]))  # checked on the device
     with pytest.raises(api.HsmaError) as e:
-        api.hsma_build_sources(h, np.array([[0.0, 0.0, 1.0]]), np.array([1.0]))
+        api.hsma_potential(h)
     assert e.value.code == -2
     api.hsma_build_sources(h, np.array([[0.1, 0.2, 0.3], [0.1, 0.2, 0.3]]), np.array([1.0, -1.0]))
     with pytest.raises(api.HsmaError) as e:
@@ -237,9 +238,10 @@ def test_overlapped_and_separate_passes_agree_bitwise(prec):
 
 
 @pytest.mark.parametrize("bad", ["nan_x", "inf_z", "inf_q", "nan_q", "on_sphere", "last_of_many"])
-def test_host_inputs_checked_at_build(bad):
-    """The host-input builds reject a charge at |x| >= a or a non-finite coordinate or charge
-    (HSMA_E_OUTSIDE = -2), single handle and batch, wherever it sits in the array."""
+def test_host_inputs_checked_on_the_device(bad):
+    """A charge at |x| >= a or a non-finite coordinate or charge in host inputs is found by the
+    pass's first kernel and reported by the evaluation (HSMA_E_OUTSIDE = -2), single handle and
+    batch, wherever it sits in the array; a corrected build then evaluates normally."""
     rng = np.random.default_rng(5)
     xyz = inputs.uniform_ball(rng, 300, 0.9)
     q = rng.choice([-1.0, 1.0], size=300)
@@ -258,12 +260,17 @@ def test_host_inputs_checked_at_build(bad):
         xyz[k] = (0.6, 0.6, 0.6)
     prm = api.hsma_default_params(p=8, M=100)
     h = api.hsma_create(1.0, 1.0, 80.0, 1.0, prm)
+    api.hsma_build_sources(h, xyz, q)
     with pytest.raises(api.HsmaError) as e:
-        api.hsma_build_sources(h, xyz, q)
+        api.hsma_energy(h)
     assert e.value.code == -2
+    xyz_ok = inputs.uniform_ball(rng, 300, 0.9)
+    api.hsma_build_sources(h, xyz_ok, np.abs(q) if np.all(np.isfinite(q)) else np.ones(300))
+    assert np.all(np.isfinite(api.hsma_potential(h)))
     api.hsma_destroy(h)
     good = inputs.uniform_ball(rng, 50, 0.9)
     b = batch.Batch([1.0, 1.0], [1.0, 1.0], [80.0, 80.0], [1.0, 1.0], prm)
+    b.hsma_batch_build_sources([50, 300], np.concatenate([good, xyz]), np.concatenate([np.ones(50), q]))
     with pytest.raises(api.HsmaError) as e:
-        b.hsma_batch_build_sources([50, 300], np.concatenate([good, xyz]), np.concatenate([np.ones(50), q]))
+        b.hsma_batch_potential()
     assert e.value.code == -2
