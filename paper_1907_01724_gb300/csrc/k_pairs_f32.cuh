@@ -23,7 +23,11 @@
 //                  and added afterwards in the exact hi/lo form: t' and s' as exact splits from
 //                  the raw records, s = (t'_hi - s'_hi) + (t'_lo - s'_lo), accurate to FP32
 //                  rounding at any distance (a charge next to its own Kelvin image); the self
-//                  pair gets r^2 = +inf, i.e. no contribution.
+//                  pair gets r^2 = +inf, i.e. no contribution.  The box's sources are split
+//                  once, by the lanes that hold their records, into the warp's shared memory,
+//                  and each lane splits its targets once per box, so a marked pair costs no
+//                  global load (near the interface most boxes of a block and its own images'
+//                  chunk have marked pairs).
 //  * Off-diagonal items (c > b) are evaluated once per unordered pair, both ways.  Real pairs by
 //    Newton's third law: 1/|x_i - x_j| serves i's term from j and j's term from i.  Kelvin pairs
 //    by Kelvin inversion, |x_j - x_i*| = |x_i - x_j*| |x_j| / |x_i| (x* = a^2 x / |x|^2): the
@@ -77,21 +81,38 @@ __device__ __forceinline__ void fold_two_sum(float& H, float& L, float v)
   H = s;
 }
 
-// The exact squared distance of a close pair (the checked form's fallback): target and source
-// as exact splits relative to the origin, from their raw (hi, lo) records.
-__device__ __forceinline__ float exact_r2(float4 th, float4 tl, float4 sh, float4 sl, float ox, float oy, float oz)
+// The exact form of a close pair (the checked form's fallback): coordinates as exact (hi, lo)
+// splits relative to the origin, from their raw (hi, lo) records; e = (xh, xl, yh, yl, zh, zl).
+__device__ __forceinline__ void exact_split(float4 h, float4 l, float ox, float oy, float oz, float (&e)[6])
 {
-  float txh, txl, tyh, tyl, tzh, tzl, sxh, sxl, syh, syl, szh, szl;
-  rel_split(th.x, tl.x, ox, txh, txl);
-  rel_split(th.y, tl.y, oy, tyh, tyl);
-  rel_split(th.z, tl.z, oz, tzh, tzl);
-  rel_split(sh.x, sl.x, ox, sxh, sxl);
-  rel_split(sh.y, sl.y, oy, syh, syl);
-  rel_split(sh.z, sl.z, oz, szh, szl);
-  const float ex = (txh - sxh) + (txl - sxl), ey = (tyh - syh) + (tyl - syl), ez = (tzh - szh) + (tzl - szl);
+  rel_split(h.x, l.x, ox, e[0], e[1]);
+  rel_split(h.y, l.y, oy, e[2], e[3]);
+  rel_split(h.z, l.z, oz, e[4], e[5]);
+}
+
+// squared distance of a target and a source from their exact splits: the differences of the hi
+// and of the lo parts, summed per coordinate, accurate to FP32 rounding at any distance
+__device__ __forceinline__ float exact_r2(const float (&t)[6], float sxh, float sxl, float syh, float syl,
+                                          float szh, float szl)
+{
+  const float ex = (t[0] - sxh) + (t[1] - sxl), ey = (t[2] - syh) + (t[3] - syl), ez = (t[4] - szh) + (t[5] - szl);
   float r2 = ex * ex;
   r2 = fmaf(ey, ey, r2);
   return fmaf(ez, ez, r2);
+}
+
+// Lane l writes the exact split of its record (rh, rl) of the current box to column l of E (for
+// l < cnt; the other columns are never read: past the box no pair is marked), then the warp syncs.
+__device__ __forceinline__ void stage_exact_sources(float (*E)[kBox], int lane, int cnt, float4 rh, float4 rl,
+                                                    float ox, float oy, float oz)
+{
+  if (lane < cnt) {
+    float e[6];
+    exact_split(rh, rl, ox, oy, oz, e);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) E[c][lane] = e[c];
+  }
+  __syncwarp();
 }
 
 // Squared distance of a target (relative hi part tx, ty, tz and |t'|^2 = c) to a buffered
@@ -233,11 +254,13 @@ __global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(cons
   constexpr int G = 32 * K;  // targets per group
   __shared__ __align__(16) float4 wA[NW][2 * kBox];  // relative source records of the box, twice
   __shared__ float wQ[NW][2 * kBox];                 // their charges
+  __shared__ float wE[NW][6][kBox];                  // exact splits of a checked box's sources
   extern __shared__ float2 wP_all[];                 // per warp: (hi, lo) sums of transposed terms
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int worker = blockIdx.x * NW + warp;
   float4* bA = wA[warp];
   float* bQ = wQ[warp];
+  float(*bE)[kBox] = wE[warp];
   float2* P = wP_all + (size_t)warp * kSymChunkMax;
   int list = 0;
   bool first_fetch = true;
@@ -463,21 +486,29 @@ __global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(cons
             box_oneway<K, kFormMid>(bA, bQ, cnt, tx, ty, tz, c, acc);
           } else {
             box_oneway_checked<K>(bA, bQ, cnt, thr2, tx, ty, tz, acc, mk);
-            // the marked close pairs in the exact hi/lo form from the raw records (the self
-            // pair: no term)
-            const int sb = ch.first + b * kBox;
+            // the marked close pairs in the exact form (the self pair: no term); each lane
+            // splits its own record of the box and its targets once
+            unsigned any = 0u;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-              unsigned m = mk[k];
-              const int ti = g0 + k * 32 + lane;
-              while (m) {
-                const int sx = __ffs(m) - 1;
-                m &= m - 1u;
+            for (int k = 0; k < K; ++k) any |= mk[k];
+            if (__any_sync(0xffffffffu, any != 0u)) {
+              stage_exact_sources(bE, lane, cnt, rh, rl, ox, oy, oz);
+              const int sb = ch.first + b * kBox;
+#pragma unroll
+              for (int k = 0; k < K; ++k) {
+                unsigned m = mk[k];
+                if (!__any_sync(0xffffffffu, m != 0u)) continue;
+                const int ti = g0 + k * 32 + lane;
                 const int tr = ti < tb1 ? ti : g0;
-                float r2 = exact_r2(src_hi[S.src + tr], src_lo[S.src + tr], __ldg(gh + b * kBox + sx),
-                                    __ldg(gl + b * kBox + sx), ox, oy, oz);
-                if (ch.type == 0 && sb + sx == ti) r2 = __int_as_float(0x7f800000);  // +inf
-                acc[k] = fmaf(bQ[sx], rsqrt_mufu(r2), acc[k]);
+                float te[6];
+                exact_split(src_hi[S.src + tr], src_lo[S.src + tr], ox, oy, oz, te);
+                while (m) {
+                  const int sx = __ffs(m) - 1;
+                  m &= m - 1u;
+                  float r2 = exact_r2(te, bE[0][sx], bE[1][sx], bE[2][sx], bE[3][sx], bE[4][sx], bE[5][sx]);
+                  if (ch.type == 0 && sb + sx == ti) r2 = __int_as_float(0x7f800000);  // +inf
+                  acc[k] = fmaf(bQ[sx], rsqrt_mufu(r2), acc[k]);
+                }
               }
             }
           }
@@ -493,26 +524,36 @@ __global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(cons
 #pragma unroll
             for (int k = 0; k < K; ++k) any |= mk[k];
             if (__any_sync(0xffffffffu, any != 0u)) {
-              // the marked close pairs, both ways, in the exact form: a second ring carries the
-              // transposed terms to their sources in the same order
-              float fx = 0.f;
-              for (int j = 0; j < kBox; ++j) {
-                const int sx = (lane + j) & 31;
+              // the marked close pairs, both ways, in the exact form.  Per target slot k a second
+              // ring carries the transposed terms to their sources: it visits only the steps
+              // where some lane has a marked pair, rotating the running sums by the steps between
+              // them (lane l's sum belongs to source l + jc), and ends aligned (lane l: source l).
+              stage_exact_sources(bE, lane, cnt, rh, rl, ox, oy, oz);
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
+              for (int k = 0; k < K; ++k) {
+                unsigned u = __reduce_or_sync(0xffffffffu, mk[k]);
+                if (u == 0u) continue;
+                const int ti = g0 + k * 32 + lane;
+                const int tr = ti < tb1 ? ti : g0;
+                float te[6];
+                exact_split(src_hi[S.src + tr], src_lo[S.src + tr], ox, oy, oz, te);
+                float fx = 0.f;
+                int jc = 0;
+                while (u) {
+                  const int j = __ffs(u) - 1;
+                  u &= u - 1u;
+                  fx = __shfl_sync(0xffffffffu, fx, (lane + j - jc) & 31);
+                  jc = j;
                   if ((mk[k] >> j) & 1u) {
-                    const int ti = g0 + k * 32 + lane;
-                    const int tr = ti < tb1 ? ti : g0;
-                    const float r2 = exact_r2(src_hi[S.src + tr], src_lo[S.src + tr], __ldg(gh + b * kBox + sx),
-                                              __ldg(gl + b * kBox + sx), ox, oy, oz);
-                    const float inv = rsqrt_mufu(r2);
+                    const int sx = (lane + j) & 31;
+                    const float inv =
+                        rsqrt_mufu(exact_r2(te, bE[0][sx], bE[1][sx], bE[2][sx], bE[3][sx], bE[4][sx], bE[5][sx]));
                     acc[k] = fmaf(bQ[sx], inv, acc[k]);
                     fx = fmaf(wt[k], inv, fx);
                   }
                 }
-                fx = __shfl_sync(0xffffffffu, fx, (lane + 1) & 31);
+                sacc += __shfl_sync(0xffffffffu, fx, (lane + 32 - jc) & 31);
               }
-              sacc += fx;
             }
           }
           if (lane < cnt) {
