@@ -235,6 +235,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     d.p = sp.p; d.P = (sp.p + 1) * (sp.p + 1); d.M = sp.M; d.F1 = sp.F1; d.F2 = sp.F2;
     d.n = (int)n;
     d.prec = prec;
+    d.sort_parts = order_sort_parts(n);
     d.chg = chg; d.src = 2 * chg; d.surf = surf; d.coef = coef; d.mn = mn;
     d.mom = mom;
     // FP64 path: charges per moment block, enough blocks to cover the SMs twice over the whole
@@ -308,6 +309,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     for (int b = 0; b < (sp.M + kSurfPointsPerBlock - 1) / kSurfPointsPerBlock; ++b) L.it3.push_back(make_int2(s, b));
     for (int b = 0; b < d.k5_count; ++b) L.it5.push_back(make_int2(s, b));
     for (int b = 0; b < (int)((n + kOrderBlock - 1) / kOrderBlock); ++b) L.itord.push_back(make_int2(s, b));
+    for (int b = 0; b < d.sort_parts; ++b) L.itsort.push_back(make_int2(s, b));
     const int nch = d.ncr + d.nck + d.ncs;
     if (prec == HSMA_FP64) {
       for (int tb = 0; tb < d.n_tb; ++tb)
@@ -425,8 +427,11 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.it4fx = L.it4f;
   L.nRKf = (int)(std::stable_partition(L.it4fx.begin(), L.it4fx.end(), is_rk) - L.it4fx.begin());
   {
+    // a sort block's share: all of a one-block system, else twice the mean share of its blocks
+    // (a denser run of cells spills to the scratch buffer)
     int64_t maxn = 0;
-    for (const auto& d : L.sd) maxn = std::max<int64_t>(maxn, d.n);
+    for (const auto& d : L.sd)
+      maxn = std::max<int64_t>(maxn, d.sort_parts == 1 ? d.n : (2 * (int64_t)d.n + d.sort_parts - 1) / d.sort_parts);
     L.order_smem_n = order_smem_charges(maxn);
   }
   L.totN = chg;
@@ -507,11 +512,12 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_perm = take(4 * (size_t)L.totN);
   L.o_iperm = take(4 * (size_t)L.totN);
   L.o_key = take(4 * (size_t)L.totN);
-  L.o_hist = take(4 * (size_t)nsys * kOrderCells);
+  L.o_hist = take(4 * (size_t)nsys * (kOrderCells + 1));
   L.o_sortscr = take(8 * (size_t)L.totN);
   L.o_xs = take(prec == HSMA_FP64 ? 0 : 32 * (size_t)L.totN);
   L.o_boxes = take(2 * sizeof(float4) * (size_t)L.totBoxes);
   L.o_itord = take(sizeof(int2) * L.itord.size());
+  L.o_itsort = take(sizeof(int2) * L.itsort.size());
   L.o_r0 = take(8 * (size_t)nsys);
   L.o_phic = take(8 * L.totN);
   L.o_phir = take(8 * L.totN);
@@ -609,6 +615,7 @@ void Engine::carve()
   xs_d = prec == HSMA_FP64 ? nullptr : (float4*)(b + L.o_xs);
   boxes_d = (float4*)(b + L.o_boxes);
   itord_d = (int2*)(b + L.o_itord);
+  itsort_d = (int2*)(b + L.o_itsort);
   r0_d = (double*)(b + L.o_r0);
   phic_d = (double*)(b + L.o_phic);
   phir_d = (double*)(b + L.o_phir);
@@ -703,12 +710,14 @@ int Engine::set_sizes(const std::vector<int64_t>& ns)
     CK(cudaMemcpyAsync(itsb_d, L.itsb.data(), sizeof(int2) * L.itsb.size(), cudaMemcpyHostToDevice, stream));
   if (!L.itord.empty())
     CK(cudaMemcpyAsync(itord_d, L.itord.data(), sizeof(int2) * L.itord.size(), cudaMemcpyHostToDevice, stream));
+  if (!L.itsort.empty())
+    CK(cudaMemcpyAsync(itsort_d, L.itsort.data(), sizeof(int2) * L.itsort.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(sel_d, L.sel.data(), sizeof(int) * L.sel.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(selrng_d, L.selrng.data(), sizeof(int2) * L.selrng.size(), cudaMemcpyHostToDevice, stream));
   CK(cudaMemsetAsync(ctr_pairs_d, 0, 16, stream));
   CK(cudaMemsetAsync(ctr_red_d, 0, 4 * L.sd.size(), stream));
   CK(cudaMemsetAsync(energy_d, 0, 16 * L.sd.size(), stream));
-  CK(cudaMemsetAsync(hist_d, 0, 4 * L.sd.size() * kOrderCells, stream));
+  CK(cudaMemsetAsync(hist_d, 0, 4 * L.sd.size() * (kOrderCells + 1), stream));
   CK(cudaMemsetAsync(outdesc_d, 0, sizeof(OutDesc), stream));
   out_cur = OutDesc{nullptr, nullptr, nullptr, 0, 0};
   // parameter-only quantities (scalars, M_n, tables, quadrature grid, surface basis), once per layout
@@ -770,8 +779,8 @@ void Engine::issue_build()
     cudaEventRecord(ev_fork, stream);
     cudaStreamWaitEvent(side, ev_fork, 0);
     PriorityScope ps(prio_hi);
-    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
-                 xs_d, status_d, nullptr, 0, L.order_smem_n, side);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), xyz_d, q_d, key_d,
+                 hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, nullptr, 0, L.order_smem_n, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
                   prec, status_d, side);
     cudaEventRecord(ev_join, side);
@@ -871,8 +880,8 @@ void Engine::issue_fused()
   const PairWork srf{it4x_d + L.nRK, nS, ctr_pairs_d, std::min(grid_s * nw, nS)}, none{nullptr, 0, nullptr, 0};
   {
     PriorityScope ps(prio_hi);
-    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
-                 xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), xyz_d, q_d, key_d,
+                 hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
                   prec, status_d, side);
   }
@@ -1177,8 +1186,8 @@ void Engine::issue_field_fused()
   const PairWork srf{it4fx_d + L.nRKf, nS, ctr_pairs_d, std::min(grid_s, nS)}, none{nullptr, 0, nullptr, 0};
   {
     PriorityScope ps(prio_hi);
-    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), xyz_d, q_d, key_d, hist_d, sortscr_d, perm_d, iperm_d,
-                 xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), xyz_d, q_d, key_d,
+                 hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
                   prec, status_d, side);
   }

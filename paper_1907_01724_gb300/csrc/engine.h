@@ -29,6 +29,7 @@ struct Layout {
   int surf_pw = 1;            // surface points per warp of k_surface_mat (with the basis)
   std::vector<int2> itsb;     // (representative system, point block) of every surface-basis table
   std::vector<int2> itord;    // (system, block of kOrderBlock charges): spatial order and records
+  std::vector<int2> itsort;   // (system, part): the blocks of k_order_sort
   int64_t totBoxes = 0;       // 32-record boxes (real + Kelvin) of all systems
   int momG = 1;               // charges per moment group (k_moments, FP64 path)
   std::vector<int2> itmu;     // FP32 path: moment units (system, tile << 7 | column pair); it12
@@ -58,7 +59,7 @@ struct Layout {
   int max_req = 1, ditem_cap = 1, mitem_cap = 1;
   size_t o_dreq = 0, o_ditems = 0, o_dreqit = 0, o_mitems = 0, o_dpart = 0, o_de = 0;
   size_t o_sb = 0, o_coef2 = 0, o_itsb = 0;
-  size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_sortscr = 0, o_xs = 0, o_boxes = 0, o_itord = 0;
+  size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_sortscr = 0, o_xs = 0, o_boxes = 0, o_itord = 0, o_itsort = 0;
   size_t o_redctr = 0;
   size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0, o_outdesc = 0;
   size_t o_it3m = 0;
@@ -143,11 +144,13 @@ class Engine {
   int2* itsb_d = nullptr;
   int *perm_d = nullptr, *iperm_d = nullptr;  // spatial order (sorted position <-> input index)
   int* key_d = nullptr;            // cell key of every charge
-  int* hist_d = nullptr;           // cell histogram per system (zero between builds)
+  int* hist_d = nullptr;           // cell histogram per system, then a sort counter per system (zero
+                                   // between builds)
   int* sortscr_d = nullptr;        // scratch of the order's sort (2 ints per charge)
   float4* xs_d = nullptr;          // FP32 path: (hi, lo) split of the inputs (k_order_keys)
   float4* boxes_d = nullptr;      // bounding boxes of 32 consecutive sorted records
   int2* itord_d = nullptr;
+  int2* itsort_d = nullptr;
   cudaStream_t side = nullptr;    // second stream of the build (order + records beside the moments)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_img = nullptr;
   int prio_hi = 0, prio_mid = 0;  // greatest stream priority of the device and the next one

@@ -104,7 +104,8 @@ struct SysDev {
   int p, P, M, F1, F2;
   int n;              // charges
   int prec;           // HSMA_FP32 / HSMA_FP64
-  int pad0;
+  int sort_parts;     // blocks of k_order_sort for this system (a power of two; each sorts the
+                      // charges of kOrderCells / sort_parts consecutive cells)
   long long chg;      // offset of this system's charges (xyz at 3*chg, q at chg, phi at chg)
   long long src;      // offset of its 2n real+Kelvin source records (real first)
   long long surf;     // offset of its M surface records
@@ -141,24 +142,30 @@ struct SysDev {
 // over [-a, a]^3 (input index inside a cell).  perm[chg + i] = input index of sorted position
 // i, iperm its inverse.  Pair-sum records, pair partials and move work use sorted positions.
 // launch_order writes the cell keys and the cell histogram (items = (system, block of
-// kOrderBlock charges)), then sorts each system in one block; its first kernel also zeroes the
-// nreset counters at ctr_reset.  hist (kOrderCells ints per system) must be zero on entry and
-// is zero again on exit; scr is scratch of 2 ints per charge (used for systems of more than
-// 4096 charges).
+// kOrderBlock charges)), then sorts each system in sort_parts blocks (sitems = (system, part)),
+// each taking a run of consecutive cells; its first kernel also zeroes the nreset counters at
+// ctr_reset.  hist (kOrderCells ints per system, then one counter per system) must be zero on
+// entry and is zero again on exit; scr is scratch of 2 ints per charge (used by a block whose
+// cells hold more charges than its shared memory).
 constexpr int kOrderGrid = 16;
 constexpr int kOrderCells = kOrderGrid * kOrderGrid * kOrderGrid;
 constexpr int kOrderBlock = 256;  // charges per k_order_keys / k_images work item
 void init_order_kernels();  // one-time function attributes (call outside stream capture)
-// Charges of a system that k_order_sort sorts in shared memory at most (larger ones use the
-// scratch buffer), and the per-launch capacity for an engine whose largest system has max_n.
+// Charges a k_order_sort block sorts in shared memory at most (more use the scratch buffer), and
+// the per-launch capacity for an engine whose largest share of a sort block is max_n charges.
 constexpr int kOrderSmemMaxN = 24576;
 int order_smem_charges(int64_t max_n);
+// Sort blocks for a system of n charges: about one per kSortPartCharges, a power of two up to
+// kSortMaxParts (every block reads all n keys, so a few thousand charges per block).
+constexpr int kSortPartCharges = 2048;
+constexpr int kSortMaxParts = 32;
+int order_sort_parts(int64_t n);
 // xs (FP32 path, else null): 2 float4 per charge in input order, the (hi, lo) split of
 // (x, y, z, q): xs[2 g] = hi parts, xs[2 g + 1] = lo parts.  status: kStOutside for a charge at
 // |x| >= a or with a non-finite coordinate or charge.
-void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, const double* q,
-                  int* key, int* hist, int* scr, int* perm, int* iperm, float4* xs, int* status,
-                  unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st);
+void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const int2* sitems, int nsitems,
+                  const double* xyz, const double* q, int* key, int* hist, int* scr, int* perm, int* iperm,
+                  float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st);
 // Boxes of 32 consecutive sorted records: a warp's targets and a box farther apart than
 // kNearRel a use plain FP32 coordinates in the pair sum, nearer ones the hi/lo-split form.
 constexpr int kBox = 32;

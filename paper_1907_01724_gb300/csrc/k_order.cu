@@ -10,11 +10,13 @@
 //                  path, the (hi, lo) split of its coordinates and charge (64-thread blocks: this
 //                  is the FP64 arithmetic of the build's record chain, which this GPU issues at
 //                  a low rate per SM, so it is spread over many SMs)
-//   k_order_sort   one block per system: exclusive scan of the histogram, scatter to the cells
-//                  (atomic cursor in shared memory: any order inside a cell), then every slot
-//                  finds its place in its cell by counting the cell's smaller input indices (the
-//                  rank; cells hold a few charges), which gives perm and iperm; it leaves the
-//                  histogram zeroed for the next build (zeroed once when the workspace is laid out)
+//   k_order_sort   sort_parts blocks per system, each owning a run of consecutive cells: every
+//                  block scans the whole histogram (the system's last block to have read it
+//                  zeroes it for the next build), reads all the system's keys (many loads in
+//                  flight) and scatters those of its cells (atomic cursor in shared memory: any
+//                  order inside a cell), then every slot finds its place in its cell by counting
+//                  the cell's smaller input indices (the rank; cells hold a few charges), which
+//                  gives perm and iperm
 // Two kernels and no memsets: the order is on the critical path of the overlapped step.
 #include <algorithm>
 
@@ -69,46 +71,41 @@ __global__ __launch_bounds__(kKeyThreads) void k_order_keys(const SysDev* __rest
   }
 }
 
-// One block per system.  s_cell holds the first sorted position of every cell (exclusive scan
-// of the histogram), then (after the scatter) the end of every cell.  The scattered slots
-// (input index and cell) live in shared memory when the system has at most smem_n charges (the
-// launch's dynamic shared memory, sized by the engine for its largest system up to
-// kOrderSmemMaxN), else in the scratch buffer scr (2 ints per charge); the keys of the first
-// kKeyRegs kSortThreads charges are held in registers between the two passes that use them.
+// Blocks of a system: part it.y of S.sort_parts takes cells [k0, k1), k1 - k0 = kOrderCells /
+// sort_parts, i.e. sorted positions [P0, P1).  s_cell holds the first sorted position of every
+// cell (exclusive scan of the histogram), then (after the scatter) the end of each of the
+// block's cells.  The block's scattered slots (input index and cell) live in shared memory when
+// they are at most smem_n (the launch's dynamic shared memory, sized by the engine), else in the
+// scratch buffer scr (2 ints per charge of the system: input indices, then cells).  done[s]
+// counts the system's blocks that have read the histogram; the last one zeroes both.
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kKeyRegs = 4096 / kSortThreads;
+constexpr int kSortBatch = 8;  // keys in flight per thread
 static_assert(kOrderCells % kSortThreads == 0, "cells split evenly over the sort block");
 
 __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __restrict__ sys,
+                                                             const int2* __restrict__ items,
                                                              const int* __restrict__ key, int* __restrict__ hist,
-                                                             int* __restrict__ scr, int* __restrict__ perm,
-                                                             int* __restrict__ iperm, int smem_n)
+                                                             int* __restrict__ done, int* __restrict__ scr,
+                                                             int* __restrict__ perm, int* __restrict__ iperm,
+                                                             int smem_n)
 {
   __shared__ int s_cell[kOrderCells];
   __shared__ int s_wsum[kSortWarps];
+  __shared__ int s_last;
   extern __shared__ int s_slot[];
-  const SysDev& S = sys[blockIdx.x];
-  const int n = S.n;
+  const int2 it = items[blockIdx.x];
+  const SysDev& S = sys[it.x];
+  const int n = S.n, parts = S.sort_parts;
   const long long c0 = S.chg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // k_images, a programmatic dependent of this kernel, is dispatched right away and waits for
   // this grid (a programmatic launch of this kernel after k_order_keys put both blocks on one
   // SM beside a moment block: 3 us slower)
   allow_dependents();
-  int* slot = n <= smem_n ? s_slot : scr + 2 * c0;  // [n] input index, then [n] cell
-  int* skey = slot + (n <= smem_n ? smem_n : n);
-  int* h = hist + (size_t)blockIdx.x * kOrderCells;
+  int* h = hist + (size_t)it.x * kOrderCells;
 
-  // the keys (loads in flight beside the scan)
-  int kr[kKeyRegs];
-#pragma unroll
-  for (int j = 0; j < kKeyRegs; ++j) {
-    const int i = tid + j * kSortThreads;
-    kr[j] = i < n ? key[c0 + i] : 0;
-  }
-
-  // exclusive scan: thread t owns cells [t per, (t + 1) per); the histogram is zeroed behind it
+  // exclusive scan: thread t owns cells [t per, (t + 1) per)
   constexpr int per = kOrderCells / kSortThreads;
   int cnt[per];
   int sum = 0;
@@ -117,8 +114,10 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
     cnt[j] = h[tid * per + j];
     sum += cnt[j];
   }
+  if (parts == 1) {
 #pragma unroll
-  for (int j = 0; j < per; ++j) h[tid * per + j] = 0;
+    for (int j = 0; j < per; ++j) h[tid * per + j] = 0;  // (read by this block alone)
+  }
   int incl = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -136,6 +135,7 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
     }
     if (lane < kSortWarps) s_wsum[lane] = w;
   }
+  if (parts > 1 && tid == 0) s_last = atomicAdd(&done[it.x], 1) == parts - 1;
   __syncthreads();
   int run = incl - sum + (warp > 0 ? s_wsum[warp - 1] : 0);
 #pragma unroll
@@ -143,35 +143,49 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
     s_cell[tid * per + j] = run;
     run += cnt[j];
   }
+  if (parts > 1 && s_last) {
+    // every block of the system has read the histogram (each counted itself after its scan)
+#pragma unroll
+    for (int j = 0; j < per; ++j) h[tid * per + j] = 0;
+    if (tid == 0) done[it.x] = 0;
+  }
   __syncthreads();
 
-  // scatter
+  const int k0 = it.y * (kOrderCells / parts), k1 = k0 + kOrderCells / parts;
+  const int P0 = s_cell[k0], P1 = k1 < kOrderCells ? s_cell[k1] : n;
+  const int m = P1 - P0;
+  int* slot = m <= smem_n ? s_slot : scr + 2 * c0 + P0;
+  int* skey = m <= smem_n ? s_slot + smem_n : scr + 2 * c0 + n + P0;
+  __syncthreads();  // P0 is read before the cursors move
+
+  // scatter the keys of the block's cells
+  for (int i0 = 0; i0 < n; i0 += kSortBatch * kSortThreads) {
+    int kk[kSortBatch];
 #pragma unroll
-  for (int j = 0; j < kKeyRegs; ++j) {
-    const int i = tid + j * kSortThreads;
-    if (i < n) {
-      const int p = atomicAdd(&s_cell[kr[j]], 1);
-      slot[p] = i;
-      skey[p] = kr[j];
+    for (int j = 0; j < kSortBatch; ++j) {
+      const int i = i0 + j * kSortThreads + tid;
+      kk[j] = i < n ? key[c0 + i] : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < kSortBatch; ++j) {
+      if (kk[j] >= k0 && kk[j] < k1) {
+        const int p = atomicAdd(&s_cell[kk[j]], 1) - P0;
+        slot[p] = i0 + j * kSortThreads + tid;
+        skey[p] = kk[j];
+      }
     }
   }
-  for (int i = tid + kKeyRegs * kSortThreads; i < n; i += kSortThreads) {
-    const int k = key[c0 + i];
-    const int p = atomicAdd(&s_cell[k], 1);
-    slot[p] = i;
-    skey[p] = k;
-  }
   __syncthreads();
 
-  // slot a of cell k (which spans [end of cell k - 1, end of cell k)) goes to the cell's start
-  // plus the number of the cell's input indices below its own
-  for (int a = tid; a < n; a += kSortThreads) {
+  // slot a of cell k (which spans [end of cell k - 1, end of cell k), the first from P0) goes to
+  // the cell's start plus the number of the cell's input indices below its own
+  for (int a = tid; a < m; a += kSortThreads) {
     const int v = slot[a], k = skey[a];
-    const int b0 = k ? s_cell[k - 1] : 0, e = s_cell[k];
+    const int b0 = (k > k0 ? s_cell[k - 1] : P0) - P0, e = s_cell[k] - P0;
     int p = b0;
     for (int b = b0; b < e; ++b) p += slot[b] < v;
-    perm[c0 + p] = v;
-    iperm[c0 + v] = p;
+    perm[c0 + P0 + p] = v;
+    iperm[c0 + v] = P0 + p;
   }
 }
 
@@ -180,21 +194,28 @@ void init_order_kernels()
   cudaFuncSetAttribute(k_order_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * sizeof(int) * kOrderSmemMaxN);
 }
 
+int order_sort_parts(int64_t n)
+{
+  int parts = 1;
+  while (parts < kSortMaxParts && (int64_t)parts * kSortPartCharges < n) parts *= 2;
+  return parts;
+}
+
 int order_smem_charges(int64_t max_n)
 {
   int64_t c = std::max<int64_t>(4096, (max_n + 1023) / 1024 * 1024);
   return (int)std::min<int64_t>(c, kOrderSmemMaxN);
 }
 
-void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const double* xyz, const double* q,
-                  int* key, int* hist, int* scr, int* perm, int* iperm, float4* xs, int* status,
-                  unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st)
+void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const int2* sitems, int nsitems,
+                  const double* xyz, const double* q, int* key, int* hist, int* scr, int* perm, int* iperm,
+                  float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st)
 {
-  if (nitems <= 0 || nsys <= 0) return;
+  if (nitems <= 0 || nsys <= 0 || nsitems <= 0) return;
   launch_k(k_order_keys, nitems * kKeySplit, kKeyThreads, 0, st, false, sys, items, xyz, q, key, hist, xs, status,
            ctr_reset, nreset);
-  launch_k(k_order_sort, nsys, kSortThreads, 2 * sizeof(int) * (size_t)smem_n, st, false, sys, (const int*)key, hist,
-           scr, perm, iperm, smem_n);
+  launch_k(k_order_sort, nsitems, kSortThreads, 2 * sizeof(int) * (size_t)smem_n, st, false, sys, sitems,
+           (const int*)key, hist, hist + (size_t)nsys * kOrderCells, scr, perm, iperm, smem_n);
 }
 
 }  // namespace hsma

@@ -72,6 +72,18 @@ def test_primitive_full_size(prec):
 
 
 @pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
+def test_clustered_charges_dense_cells(prec):
+    """6000 charges in a ball of radius 0.06 a off the centre: a handful of the spatial order's
+    16^3 cells hold hundreds of charges each, and the sort block that owns them has more charges
+    than its shared memory (it sorts in the scratch buffer)."""
+    rng = np.random.default_rng(4242)
+    n = 6000
+    xyz = inputs.uniform_ball(rng, n, 0.06) + np.array([0.31, -0.12, 0.2])
+    s = inputs.System(1.0, 2.0, 80.0, 1.0, 12, 200, xyz, rng.choice([-1.0, 1.0], n))
+    check(s, prec)
+
+
+@pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 517, 1029])
 def test_ragged_sizes(prec, n):
     rng = np.random.default_rng(1000 + n)
