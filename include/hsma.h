@@ -113,7 +113,11 @@ HSMA_API int hsma_attach_workspace(hsma_t* h, void* device_ptr, size_t bytes);
  * HSMA_E_OUTSIDE.  Asynchronous with respect to the host once the inputs are copied. */
 HSMA_API int hsma_build_sources(hsma_t* h, int64_t n, const double* xyz, const double* q);
 
-/* Same as hsma_build_sources with inputs already resident on the device. */
+/* Same as hsma_build_sources with inputs already resident on the device, read in place: this
+ * call copies nothing; the next evaluation on the handle (the call that runs the build pass)
+ * reads xyz_dev and q_dev on the handle's stream and keeps its own copy of them.  Until that
+ * evaluation's work has run, the arrays must stay allocated and unchanged (stream-ordered
+ * writes enqueued after that call are fine). */
 HSMA_API int hsma_build_sources_device(hsma_t* h, int64_t n, const double* xyz_dev, const double* q_dev);
 
 /* Potentials at the n charges (Algorithm 1 step 5, by direct tiled summation):
@@ -209,7 +213,8 @@ HSMA_API int hsma_batch_attach_workspace(hsma_batch_t* b, void* device_ptr, size
 HSMA_API int hsma_batch_set_max_requests(hsma_batch_t* b, int max_requests);
 
 /* Build all sources (Sec. 2.4) for n[nsys] charges per system: xyz (sum n, 3) and q (sum n),
- * host or device memory respectively.  A charge outside its cavity or a non-finite value is
+ * host or device memory respectively (device inputs are read in place by the next evaluation,
+ * as for hsma_build_sources_device).  A charge outside its cavity or a non-finite value is
  * reported as HSMA_E_OUTSIDE by the evaluation that runs the pass (see hsma_build_sources). */
 HSMA_API int hsma_batch_build_sources(hsma_batch_t* b, const int64_t* n, const double* xyz, const double* q);
 HSMA_API int hsma_batch_build_sources_device(hsma_batch_t* b, const int64_t* n, const double* xyz_dev,

@@ -39,6 +39,8 @@ int Engine::tune_time_config(int c, int side_mode, int steps, std::vector<float>
   const std::vector<int64_t> ns = cur_ns;
   int rc = set_sizes(ns);
   if (rc) return rc;
+  rc = prepare_inputs();
+  if (rc) return rc;
   rc = run_graph(&g_build, &Engine::issue_build);
   if (rc) return rc;
   sources_ready = true;
@@ -153,6 +155,8 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
   if (!found) tuned.push_back(Tuned{bucket, best, best_side});
   layout_uploaded = false;
   int rc = set_sizes(ns);
+  if (rc) return rc;
+  rc = prepare_inputs();
   if (rc) return rc;
   rc = run_graph(&g_build, &Engine::issue_build);
   if (rc) return rc;

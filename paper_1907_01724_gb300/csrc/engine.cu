@@ -526,6 +526,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   L.o_energy = take(16 * (size_t)nsys);
   L.o_ctr = take(16);
   L.o_outdesc = take(sizeof(OutDesc));
+  L.o_indesc = take(sizeof(InDesc));
   L.o_redctr = take(4 * (size_t)nsys);
   L.o_it12 = take(sizeof(int2) * L.it12.size());
   L.o_it2r = take(sizeof(int2) * L.it2r.size());
@@ -627,6 +628,8 @@ void Engine::carve()
   ctr_red_d = (unsigned int*)(b + L.o_redctr);
   status_d = (int*)(ctr + 2);
   outdesc_d = (OutDesc*)(b + L.o_outdesc);
+  indesc_d = (InDesc*)(b + L.o_indesc);
+  in_loaded = false;
   ctr_delta_d = ctr + 3;
   it12_d = (int2*)(b + L.o_it12);
   it2r_d = (int2*)(b + L.o_it2r);
@@ -760,11 +763,11 @@ Tables Engine::tables() const
 void Engine::issue_moments()
 {
   if (prec == HSMA_FP64) {
-    launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, xyz_d, q_d, Mn_d, tables(), prec, mom_d,
+    launch_moments(sys_d, it12_d, (int)L.it12.size(), L.maxP, L.momG, indesc_d, Mn_d, tables(), prec, mom_d,
                    L.mom_stride, stream);
     return;
   }
-  launch_moment_prep(sys_d, it12_d, (int)L.it12.size(), xyz_d, q_d, Mn_d, mgeo_d, mz_d, mwq_d, mcen_d, stream);
+  launch_moment_prep(sys_d, it12_d, (int)L.it12.size(), indesc_d, Mn_d, mgeo_d, mz_d, mwq_d, mcen_d, stream);
   launch_moment_units(sys_d, itmu_d, (int)L.itmu.size(), mgeo_d, mz_d, mwq_d, mcen_d, tables(), mom_d,
                       L.mom_stride, stream);
 }
@@ -779,8 +782,8 @@ void Engine::issue_build()
     cudaEventRecord(ev_fork, stream);
     cudaStreamWaitEvent(side, ev_fork, 0);
     PriorityScope ps(prio_hi);
-    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), xyz_d, q_d, key_d,
-                 hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, nullptr, 0, L.order_smem_n, side);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), indesc_d, xyz_d, q_d,
+                 key_d, hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, nullptr, 0, L.order_smem_n, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
                   prec, status_d, side);
     cudaEventRecord(ev_join, side);
@@ -880,8 +883,8 @@ void Engine::issue_fused()
   const PairWork srf{it4x_d + L.nRK, nS, ctr_pairs_d, std::min(grid_s * nw, nS)}, none{nullptr, 0, nullptr, 0};
   {
     PriorityScope ps(prio_hi);
-    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), xyz_d, q_d, key_d,
-                 hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), indesc_d, xyz_d, q_d,
+                 key_d, hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
                   prec, status_d, side);
   }
@@ -937,21 +940,42 @@ int Engine::run_graph(cudaGraphExec_t* g, void (Engine::*issue)())
   return HSMA_OK;
 }
 
+// Host inputs are copied to xyz_d, q_d now.  Device inputs are not copied: the build pass (run
+// by the next evaluation) reads them in place through the inputs descriptor, and its first
+// kernel writes the engine's own copy, so a step from device inputs has no copy launches.
 int Engine::build(const double* xyz, const double* q, bool device_inputs)
 {
   CK(cudaSetDevice(device));
   const int64_t n = L.totN;
-  enter();
-  if (n > 0) {
-    const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(xyz_d, xyz, 24 * n, kind, stream));
-    CK(cudaMemcpyAsync(q_d, q, 8 * n, kind, stream));
+  in_pending = false;
+  if (n > 0 && device_inputs) {
+    in_user = InDesc{xyz, q, 1, 0};
+    in_pending = true;
+  } else if (n > 0) {
+    enter();
+    CK(cudaMemcpyAsync(xyz_d, xyz, 24 * n, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(q_d, q, 8 * n, cudaMemcpyHostToDevice, stream));
+    leave();
   }
-  leave();
   sources_ready = true;
   build_pending = true;
   pot_ready = false;
   v_ready = false;
+  return HSMA_OK;
+}
+
+// The inputs descriptor for a build pass about to be launched: the pending device inputs, else
+// the engine's own arrays (a copy of the descriptor only when it changes: none per step when the
+// caller builds from the same device arrays every step, or always from host arrays).
+int Engine::prepare_inputs()
+{
+  const InDesc want = in_pending ? in_user : InDesc{xyz_d, q_d, 0, 0};
+  if (!in_loaded || want.xyz != in_cur.xyz || want.q != in_cur.q || want.copy != in_cur.copy) {
+    in_cur = want;
+    CK(cudaMemcpyAsync(indesc_d, &in_cur, sizeof(InDesc), cudaMemcpyHostToDevice, stream));
+    in_loaded = true;
+  }
+  in_pending = false;
   return HSMA_OK;
 }
 
@@ -960,7 +984,9 @@ int Engine::ensure_built()
   if (!build_pending) return HSMA_OK;
   CK(cudaSetDevice(device));
   enter();
-  int rc = run_graph(&g_build, &Engine::issue_build);
+  int rc = prepare_inputs();
+  if (rc) return rc;
+  rc = run_graph(&g_build, &Engine::issue_build);
   if (rc) return rc;
   leave();
   launches += build_launch_count();
@@ -991,7 +1017,9 @@ int Engine::potentials(const OutDesc& od, bool* wrote)
   }
   if (build_pending && overlap) {
     enter();
-    int rc = run_graph(&g_fused, &Engine::issue_fused);
+    int rc = prepare_inputs();
+    if (rc) return rc;
+    rc = run_graph(&g_fused, &Engine::issue_fused);
     if (rc) return rc;
     leave();
     launches += fused_launch_count();
@@ -1186,8 +1214,8 @@ void Engine::issue_field_fused()
   const PairWork srf{it4fx_d + L.nRKf, nS, ctr_pairs_d, std::min(grid_s, nS)}, none{nullptr, 0, nullptr, 0};
   {
     PriorityScope ps(prio_hi);
-    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), xyz_d, q_d, key_d,
-                 hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
+    launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), indesc_d, xyz_d, q_d,
+                 key_d, hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
     launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
                   prec, status_d, side);
   }
@@ -1218,6 +1246,8 @@ int Engine::field()
   if (rc) return rc;
   if (build_pending && overlap && !L.itord.empty()) {
     enter();
+    rc = prepare_inputs();
+    if (rc) return rc;
     rc = run_graph(&g_field_fused, &Engine::issue_field_fused);
     if (rc) return rc;
     leave();

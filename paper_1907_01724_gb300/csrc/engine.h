@@ -61,7 +61,7 @@ struct Layout {
   size_t o_sb = 0, o_coef2 = 0, o_itsb = 0;
   size_t o_perm = 0, o_iperm = 0, o_key = 0, o_hist = 0, o_sortscr = 0, o_xs = 0, o_boxes = 0, o_itord = 0, o_itsort = 0;
   size_t o_redctr = 0;
-  size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0, o_outdesc = 0;
+  size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0, o_outdesc = 0, o_indesc = 0;
   size_t o_it3m = 0;
   size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0, o_it4x = 0, o_it4f = 0, o_it4fx = 0;
   size_t bytes = 0;
@@ -80,6 +80,14 @@ class Engine {
   int potentials(const OutDesc& od = OutDesc{nullptr, nullptr, nullptr, 0, 0}, bool* wrote = nullptr);
   int set_outputs(const OutDesc& od);
   OutDesc* outdesc_d = nullptr;
+  // Inputs of the next build pass (InDesc in the workspace): the caller's device arrays while a
+  // build from them is pending (the pass reads them in place and copies them to xyz_d, q_d),
+  // else xyz_d, q_d; rewritten only when that changes
+  int prepare_inputs();
+  InDesc* indesc_d = nullptr;
+  InDesc in_user{nullptr, nullptr, 1, 0};  // the caller's device arrays of a pending build
+  InDesc in_cur{nullptr, nullptr, 0, 0};   // what indesc_d holds (when in_loaded)
+  bool in_pending = false, in_loaded = false;
   OutDesc out_cur{nullptr, nullptr, nullptr, 0, 0};  // what outdesc_d holds
   int field();                    // potentials and fields in one pass (lazily allocated buffers)
   int check_status();

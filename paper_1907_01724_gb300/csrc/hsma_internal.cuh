@@ -138,6 +138,17 @@ struct SysDev {
   float2 f_inv_a, f_hdbar, f_Rt_a;
 };
 
+// Inputs of a build pass, in device memory: the charges' coordinates (3 per charge) and values,
+// in input order.  With copy set they are the caller's device arrays, read by the pass itself
+// (no separate copy launch), and k_order_keys also writes them to the engine's own arrays
+// (xyz_own, q_own), which every later kernel reads; otherwise they are the engine's own arrays.
+struct InDesc {
+  const double* xyz;
+  const double* q;
+  int copy;
+  int pad;
+};
+
 // Spatial order (k_order.cu): charges sorted by the Morton index of their cell on a 16^3 grid
 // over [-a, a]^3 (input index inside a cell).  perm[chg + i] = input index of sorted position
 // i, iperm its inverse.  Pair-sum records, pair partials and move work use sorted positions.
@@ -164,8 +175,9 @@ int order_sort_parts(int64_t n);
 // (x, y, z, q): xs[2 g] = hi parts, xs[2 g + 1] = lo parts.  status: kStOutside for a charge at
 // |x| >= a or with a non-finite coordinate or charge.
 void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const int2* sitems, int nsitems,
-                  const double* xyz, const double* q, int* key, int* hist, int* scr, int* perm, int* iperm,
-                  float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st);
+                  const InDesc* in, double* xyz_own, double* q_own, int* key, int* hist, int* scr, int* perm,
+                  int* iperm, float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n,
+                  cudaStream_t st);
 // Boxes of 32 consecutive sorted records: a warp's targets and a box farther apart than
 // kNearRel a use plain FP32 coordinates in the pair sum, nearer ones the hi/lo-split form.
 constexpr int kBox = 32;
@@ -209,9 +221,8 @@ void launch_images(const SysDev* sys, const int2* items, int nitems, const doubl
 // Moment rows: per block, sum_i q_i (M_n - gamma - c_i) T_nm(x_i/a) for the P coefficients
 // (slots 0 .. P-1) and the block's centre constant (slot P).
 // G: charges per moment group (moment_smem_group; the layout's tiles are multiples of it).
-void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const double* xyz,
-                    const double* q, const double* Mn, Tables tab, int prec, double* mom, int mom_stride,
-                    cudaStream_t st);
+void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const InDesc* in,
+                    const double* Mn, Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st);
 // FP32 path, in two kernels.  k_moment_prep (items = (system, block of kMomPrepCharges charges)):
 // per charge its double-float moment inputs -- geo = (2w hi, 2w lo, rho^2 hi, rho^2 lo), the
 // powers (u + i v)^m (mz, (re hi, re lo, im hi, im lo)) and the weights q (M_n - gamma - c)
@@ -231,8 +242,8 @@ __host__ __device__ constexpr int moment_beta_slots(int pmax)
 {
   return (pmax + 1 + kMomUnitSteps) * (pmax + 2 + kMomUnitSteps) / 2;
 }
-void launch_moment_prep(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
-                        const double* Mn, float4* geo, float4* mz, float2* mwq, double* mcen, cudaStream_t st);
+void launch_moment_prep(const SysDev* sys, const int2* items, int nitems, const InDesc* in, const double* Mn,
+                        float4* geo, float4* mz, float2* mwq, double* mcen, cudaStream_t st);
 void launch_moment_units(const SysDev* sys, const int2* units, int nunits, const float4* geo,
                          const float4* mz, const float2* mwq, const double* mcen, Tables tab, double* mom,
                          int mom_stride, cudaStream_t st);

@@ -6,7 +6,8 @@
 // and a 32-source sub-tile each occupy a small box, and the pair kernel evaluates the pairs of
 // well-separated boxes with plain FP32 coordinates, keeping the hi/lo-split form for near ones.
 //   k_order_keys   cell key per charge and the cell histogram of its system (global integer
-//                  atomics), the check that the charge lies inside the cavity and, for the FP32
+//                  atomics), the engine's own copy of device inputs read in place (InDesc),
+//                  the check that the charge lies inside the cavity and, for the FP32
 //                  path, the (hi, lo) split of its coordinates and charge (64-thread blocks: this
 //                  is the FP64 arithmetic of the build's record chain, which this GPU issues at
 //                  a low rate per SM, so it is spread over many SMs)
@@ -47,7 +48,8 @@ __device__ __forceinline__ int cell_key(const SysDev& S, double x, double y, dou
 constexpr int kKeyThreads = 64;
 constexpr int kKeySplit = kOrderBlock / kKeyThreads;
 __global__ __launch_bounds__(kKeyThreads) void k_order_keys(const SysDev* __restrict__ sys, const int2* __restrict__ items,
-                                                            const double* __restrict__ xyz, const double* __restrict__ q,
+                                                            const InDesc* __restrict__ in,
+                                                            double* __restrict__ xyz_own, double* __restrict__ q_own,
                                                             int* __restrict__ key, int* __restrict__ hist,
                                                             float4* __restrict__ xs, int* __restrict__ status,
                                                             unsigned int* __restrict__ ctr_reset, int nreset)
@@ -58,7 +60,15 @@ __global__ __launch_bounds__(kKeyThreads) void k_order_keys(const SysDev* __rest
   const int i = it.y * kOrderBlock + (blockIdx.x % kKeySplit) * kKeyThreads + threadIdx.x;
   if (i >= S.n) return;
   const long long g = S.chg + i;
-  const double x = xyz[3 * g], y = xyz[3 * g + 1], z = xyz[3 * g + 2], qg = q[g];
+  const InDesc d = *in;
+  const double x = d.xyz[3 * g], y = d.xyz[3 * g + 1], z = d.xyz[3 * g + 2], qg = d.q[g];
+  if (d.copy) {
+    // the engine's own copy of the inputs, which the later kernels of the pass read
+    xyz_own[3 * g] = x;
+    xyz_own[3 * g + 1] = y;
+    xyz_own[3 * g + 2] = z;
+    q_own[g] = qg;
+  }
   const int k = cell_key(S, x, y, z);
   key[g] = k;
   atomicAdd(&hist[(size_t)it.x * kOrderCells + k], 1);
@@ -208,12 +218,13 @@ int order_smem_charges(int64_t max_n)
 }
 
 void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const int2* sitems, int nsitems,
-                  const double* xyz, const double* q, int* key, int* hist, int* scr, int* perm, int* iperm,
-                  float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st)
+                  const InDesc* in, double* xyz_own, double* q_own, int* key, int* hist, int* scr, int* perm,
+                  int* iperm, float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n,
+                  cudaStream_t st)
 {
   if (nitems <= 0 || nsys <= 0 || nsitems <= 0) return;
-  launch_k(k_order_keys, nitems * kKeySplit, kKeyThreads, 0, st, false, sys, items, xyz, q, key, hist, xs, status,
-           ctr_reset, nreset);
+  launch_k(k_order_keys, nitems * kKeySplit, kKeyThreads, 0, st, false, sys, items, in, xyz_own, q_own, key, hist,
+           xs, status, ctr_reset, nreset);
   launch_k(k_order_sort, nsitems, kSortThreads, 2 * sizeof(int) * (size_t)smem_n, st, false, sys, sitems,
            (const int*)key, hist, hist + (size_t)nsys * kOrderCells, scr, perm, iperm, smem_n);
 }

@@ -523,11 +523,13 @@ __device__ __forceinline__ MomentInputs moment_inputs_df(const SysDev& S, df x, 
 // are stored as R values in 8-byte slots; slot P holds the block's centre constant.
 template <int MAXJ, class R>
 __global__ __launch_bounds__(kMomThreads) void k_moments(const SysDev* __restrict__ sys, const int2* __restrict__ items,
-                                                         const double* __restrict__ xyz, const double* __restrict__ q,
+                                                         const InDesc* __restrict__ in,
                                                          const double* __restrict__ Mn, Tables tab,
                                                          double* __restrict__ mom, int mom_stride, int G)
 {
   extern __shared__ double sm[];
+  const double* __restrict__ xyz = in->xyz;
+  const double* __restrict__ q = in->q;
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int n = S.n, P = S.P, p = S.p;
@@ -696,34 +698,31 @@ static size_t moment_smem_bytes(int maxP, int G)
 }
 
 template <int MAXJ>
-static void launch_mom(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const double* xyz,
-                       const double* q, const double* Mn, Tables tab, int prec, double* mom, int mom_stride,
-                       cudaStream_t st)
+static void launch_mom(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const InDesc* in,
+                       const double* Mn, Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
 {
   const size_t smem = moment_smem_bytes(maxP, G);
   (void)prec;  // FP64 only (the FP32 path: launch_moment_prep, launch_moment_units)
-  launch_k(k_moments<MAXJ, double>, nitems, kMomThreads, smem, st, false, sys, items, xyz, q, Mn, tab, mom, mom_stride,
-           G);
+  launch_k(k_moments<MAXJ, double>, nitems, kMomThreads, smem, st, false, sys, items, in, Mn, tab, mom, mom_stride, G);
 }
 
-void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const double* xyz,
-                    const double* q,
+void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, int G, const InDesc* in,
                     const double* Mn, Tables tab, int prec, double* mom, int mom_stride, cudaStream_t st)
 {
   if (nitems <= 0) return;
   const int J = (maxP + kMomThreads - 1) / kMomThreads;
   if (J <= 1)
-    launch_mom<1>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<1>(sys, items, nitems, maxP, G, in, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 2)
-    launch_mom<2>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<2>(sys, items, nitems, maxP, G, in, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 4)
-    launch_mom<4>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<4>(sys, items, nitems, maxP, G, in, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 8)
-    launch_mom<8>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<8>(sys, items, nitems, maxP, G, in, Mn, tab, prec, mom, mom_stride, st);
   else if (J <= 16)
-    launch_mom<16>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<16>(sys, items, nitems, maxP, G, in, Mn, tab, prec, mom, mom_stride, st);
   else
-    launch_mom<26>(sys, items, nitems, maxP, G, xyz, q, Mn, tab, prec, mom, mom_stride, st);
+    launch_mom<26>(sys, items, nitems, maxP, G, in, Mn, tab, prec, mom, mom_stride, st);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -738,8 +737,7 @@ void launch_moments(const SysDev* sys, const int2* items, int nitems, int maxP, 
 // m, n = k mod 4 (z^m = z^k (z^4)^s), a quarter of the sequential chain of complex products.
 __global__ __launch_bounds__(kMomPrepThreads) void k_moment_prep(const SysDev* __restrict__ sys,
                                                                  const int2* __restrict__ items,
-                                                                 const double* __restrict__ xyz,
-                                                                 const double* __restrict__ q,
+                                                                 const InDesc* __restrict__ inp,
                                                                  const double* __restrict__ Mn,
                                                                  float4* __restrict__ geo, float4* __restrict__ mz,
                                                                  float2* __restrict__ mwq, double* __restrict__ mcen)
@@ -755,7 +753,7 @@ __global__ __launch_bounds__(kMomPrepThreads) void k_moment_prep(const SysDev* _
   const bool live = i < ns;
   const long long gi = S.chg + (live ? i : 0);
   double xin = 0.0;
-  if (live) xin = sub < 3 ? xyz[3 * gi + sub] : q[gi];
+  if (live) xin = sub < 3 ? inp->xyz[3 * gi + sub] : inp->q[gi];
   if ((int)threadIdx.x <= p) smg[threadIdx.x] = df_from_double(Mn[S.mn + threadIdx.x] - S.gam);
   // every block of the grid is resident once this is reached: the unit kernel's blocks may
   // start (they wait for this grid's writes before reading them)
@@ -988,11 +986,11 @@ __global__ __launch_bounds__(kMomUnitWarps * 32, 24 / kMomUnitWarps) void k_mome
   }
 }
 
-void launch_moment_prep(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
-                        const double* Mn, float4* geo, float4* mz, float2* mwq, double* mcen, cudaStream_t st)
+void launch_moment_prep(const SysDev* sys, const int2* items, int nitems, const InDesc* in, const double* Mn,
+                        float4* geo, float4* mz, float2* mwq, double* mcen, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  launch_k(k_moment_prep, nitems, kMomPrepThreads, 0, st, false, sys, items, xyz, q, Mn, geo, mz, mwq, mcen);
+  launch_k(k_moment_prep, nitems, kMomPrepThreads, 0, st, false, sys, items, in, Mn, geo, mz, mwq, mcen);
 }
 
 void launch_moment_units(const SysDev* sys, const int2* units, int nunits, const float4* geo,

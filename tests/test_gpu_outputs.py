@@ -144,3 +144,45 @@ def test_call_sequences_after_host_outputs(prec):
     for k, (s, r) in enumerate(zip(sy2, r2)):
         scale = max(abs(r["E_total"]), 0.5 * np.sum(np.abs(s.q * r["phi"])))
         assert abs(et[k] - r["E_total"]) <= tol * scale
+
+
+@pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
+def test_device_inputs_read_in_place(prec):
+    """Device inputs are read by the evaluation that runs the build pass, which keeps its own
+    copy: results follow the positions at that evaluation; rewriting the caller's array after it
+    changes nothing the handle returns (another quantity, a field pass) until the next build; the
+    autotuner, run while a build from device arrays is pending, tunes and leaves the handle on
+    those inputs."""
+    tol = 1e-6 if prec == api.HSMA_FP32 else 1e-12
+    sy = systems()
+    n, xyz, q = batch.concat(sy)
+    xyz2 = xyz * 0.97
+    sy2 = [inputs.System(xyz=xyz2[a:a + s.n], q=s.q, a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M,
+                         tau=s.tau) for s, a in zip(sy, np.cumsum([0] + [s.n for s in sy])[:-1])]
+    r1, r2 = refs(sy), refs(sy2)
+    phi1 = np.concatenate([r["phi"] for r in r1])
+    rf1 = np.concatenate([r["phi_rf"] for r in r1])
+    phi2 = np.concatenate([r["phi"] for r in r2])
+    b = batch.from_systems(sy, precision=prec)
+    xyz_d = torch.tensor(xyz, device="cuda")
+    q_d = torch.tensor(q, device="cuda")
+    b.hsma_batch_build_sources(n, xyz_d, q_d)
+    assert rel(b.hsma_batch_potential(), phi1) <= tol
+    xyz_d.mul_(0.97)  # the caller rewrites its array after the evaluation
+    torch.cuda.synchronize()
+    assert rel(b.hsma_batch_potential(api.HSMA_REACTION), rf1) <= tol
+    E = b.hsma_batch_field()
+    off = 0
+    for s in sy:
+        P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau)
+        assert rel(E[off:off + s.n], oracle.field(P, s.xyz, s.q)["E"]) <= tol
+        off += s.n
+    # the next build reads the rewritten array
+    b.hsma_batch_build_sources(n, xyz_d, q_d)
+    assert rel(b.hsma_batch_potential(), phi2) <= tol
+    if prec == api.HSMA_FP32:
+        # a pending build from device arrays, then the autotuner, then an evaluation
+        xyz1_d = torch.tensor(xyz, device="cuda")
+        b.hsma_batch_build_sources(n, xyz1_d, q_d)
+        b.hsma_batch_autotune(1)
+        assert rel(b.hsma_batch_potential(), phi1) <= tol
