@@ -726,9 +726,10 @@ def main():
     ap.add_argument("--pair-config", type=int, default=-1,
                     help="with --only pairs / steps / near_steps: this tile configuration (index of "
                          "batch.pair_configs()) instead of the autotuned one")
-    ap.add_argument("--pair-schedule", type=int, default=-1, choices=[-1, 0, 1],
+    ap.add_argument("--pair-schedule", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="with --only steps / near_steps and --pair-config: the real/Kelvin pair schedule "
-                         "(1 beside the coefficient chain, 0 after it; -1 the library's default)")
+                         "(1 beside the coefficient chain, 2 the same leaving room for a coefficient or "
+                         "surface CTA per SM, 0 after it; -1 the library's default)")
     ap.add_argument("--only", choices=["batched", "serving", "field", "near", "pairs", "steps", "near_steps"],
                     help="run one section alone (profiling); 'pairs': the headline workload's pair kernel "
                          "in separate passes (--steps launches); 'steps' / 'near_steps': --warmup + --steps "

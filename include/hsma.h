@@ -250,12 +250,14 @@ HSMA_API int hsma_batch_set_overlap(hsma_batch_t* b, int on);
 /* Where the graph of a build followed by a potential/energy evaluation (overlap on) runs the
  * pair sum of the real charges and Kelvin images, which needs only the image records:
  * mode = 1 in a launch of its own right after the records, beside the coefficient and surface
- * kernels (a full grid at the lowest launch priority); mode = 0 in one launch with the surface
- * images after those kernels; mode = -1 (the default) the autotuned choice for this size class
- * if there is one (hsma_batch_autotune times both), else 1 for up to 8 cavities and 0 for
- * more.  Results are bitwise the same either way; the choice takes effect at the next build
- * (as hsma_batch_set_pair_config does).  HSMA_E_INVALID_ARG for another mode.
- * hsma_batch_pair_schedule writes the schedule of the current layout (0 or 1) to *mode. */
+ * kernels (at the lowest launch priority, leaving one CTA slot per SM to those kernels);
+ * mode = 2 the same, leaving room for one CTA of the largest of those kernels per SM; mode = 0
+ * in one launch with the surface images after those kernels; mode = -1 (the default) the
+ * autotuned choice for this size class if there is one (hsma_batch_autotune times all three),
+ * else 1 for up to 8 cavities and 0 for more.  Results are bitwise the same either way; the
+ * choice takes effect at the next build (as hsma_batch_set_pair_config does).
+ * HSMA_E_INVALID_ARG for another mode.  hsma_batch_pair_schedule writes the schedule of the
+ * current layout (0, 1 or 2) to *mode. */
 HSMA_API int hsma_batch_set_pair_schedule(hsma_batch_t* b, int mode);
 HSMA_API int hsma_batch_pair_schedule(const hsma_batch_t* b, int* mode);
 
@@ -264,7 +266,7 @@ HSMA_API int hsma_batch_pair_schedule(const hsma_batch_t* b, int* mode);
  * hsma_batch_set_pair_config forces one (-1 = automatic); hsma_batch_autotune times every
  * configuration on the current inputs (reps runs each, CUDA events: the build + potential step
  * in one graph, or with overlap off the potential pass alone; the three fastest again in
- * interleaved rounds; then, with overlap on and no forced schedule, the winner with both pair
+ * interleaved rounds; then, with overlap on and no forced schedule, the winner with the three pair
  * schedules of hsma_batch_set_pair_schedule) and keeps the fastest for this size class;
  * *best and *best_ms (nullable) receive the configuration and its time. */
 HSMA_API int hsma_pair_config_count(void);

@@ -128,15 +128,22 @@ int Engine::autotune(int reps, int* best_out, float* best_ms_out)
   // the schedule of the real/Kelvin items for the winner (only a forced schedule is kept as is)
   int best_side = side0;
   if (overlap && saved_side < 0) {
-    std::vector<float> ts[2];
+    constexpr int kSchedules = 3;
+    std::vector<float> ts[kSchedules];
     for (int round = 0; round < 2 * reps; ++round)
-      for (int sd = 0; sd < 2; ++sd) {
+      for (int sd = 0; sd < kSchedules; ++sd) {
         int rc = tune_time_config(best, sd, 1, ts[sd]);
         if (rc) return rc;
       }
-    const float m0 = median(ts[0]), m1 = median(ts[1]);
-    best_side = m1 <= m0 ? 1 : 0;
-    best_ms = std::min(m0, m1);
+    best_side = 1;
+    best_ms = median(ts[1]);
+    for (int sd : {2, 0}) {
+      const float m = median(ts[sd]);
+      if (m < best_ms) {
+        best_ms = m;
+        best_side = sd;
+      }
+    }
   }
   forced_cfg = saved_forced;
   forced_side = saved_side;
@@ -358,7 +365,7 @@ int hsma_batch_set_overlap(hsma_batch_t* b, int on)
 
 int hsma_batch_set_pair_schedule(hsma_batch_t* b, int mode)
 {
-  if (!b || mode < -1 || mode > 1) return berr(b, HSMA_E_INVALID_ARG, "bad schedule");
+  if (!b || mode < -1 || mode > 2) return berr(b, HSMA_E_INVALID_ARG, "bad schedule");
   if (b->e->forced_side != mode) {
     b->e->forced_side = mode;
     b->e->layout_uploaded = false;  // the next call rebuilds the layout and its graphs

@@ -78,6 +78,10 @@ int Engine::init(int dev, void* user_stream, int precision)
   occ_f32.assign(pair_config_count(), 0);
   for (int c = 0; c < pair_config_count(); ++c) occ_f32[c] = pairs_f32_occupancy(c);
   occ_f64 = pairs_f64_occupancy();
+  regs_f32.assign(pair_config_count(), 0);
+  for (int c = 0; c < pair_config_count(); ++c) regs_f32[c] = pairs_f32_block_regs(c);
+  chain_regs = chain_block_regs(prec);
+  CK(cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, device));
   occ_field.assign(pair_config_count(), 0);
   for (int c = 0; c < pair_config_count(); ++c) occ_field[c] = field_f32_occupancy(c);
   occ_field64 = field_f64_occupancy();
@@ -843,6 +847,7 @@ void Engine::launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t 
 //      main:  k_moment_prep -> k_moment_units -> k_coef_reduce -> k_surface_mat -> k_pairs
 //             (surface items, then the real/Kelvin items the first launch has not taken) -> join
 //             -> k_reduce
+//   2: as 1, with fewer CTAs in the side launch (side_ctas_per_sm)
 //   0: side:  k_order_keys -> k_order_sort -> k_images
 //      main:  the same chain -> [wait records] k_pairs (surface items, then every real/Kelvin
 //             item) -> k_reduce
@@ -867,10 +872,7 @@ void Engine::issue_fused()
   const int slots = num_sms * occ;
   const int nw = L.nw;  // workers per CTA
   const bool side_rk = rk_side != 0 && L.nRK > 0;
-  // the side launch leaves one CTA slot per SM (when there are at least four) to the chain's
-  // kernels, which then run beside it instead of after it: 0.326 against 0.334 ms per headline
-  // step; two slots per SM: 0.342
-  const int grid_rk = std::max(1, std::min((L.nRK + nw - 1) / nw, occ >= 4 ? slots - num_sms : slots));
+  const int grid_rk = std::max(1, std::min((L.nRK + nw - 1) / nw, num_sms * side_ctas_per_sm(occ)));
   const int grid_s = std::max(1, std::min((nS + L.nRK + nw - 1) / nw, slots));
   cudaEventRecord(ev_fork, stream);
   cudaStreamWaitEvent(side, ev_fork, 0);
@@ -907,6 +909,24 @@ void Engine::issue_fused()
   if (side_rk) cudaStreamWaitEvent(stream, ev_join, 0);
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
                 phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, outdesc_d, stream, true);
+}
+
+// CTAs per SM of a real/Kelvin launch beside the coefficient chain.  Its persistent CTAs keep
+// their SM's registers until the real/Kelvin items run out, so the chain's kernels run only in
+// what it leaves free.  Schedule 1 leaves one CTA slot per SM (when there are at least four):
+// 0.326 against 0.334 ms per step at N = 20000 with none left, 0.342 with two.  A slot of a
+// small pair CTA may not hold a coefficient or surface CTA, which then waits for pair CTAs to
+// finish (4 us per step for two cavities of N = 2000 with 64-thread pair CTAs); schedule 2
+// leaves the registers of the largest of those CTAs instead.
+int Engine::side_ctas_per_sm(int occ) const
+{
+  if (rk_side == 2 && prec != HSMA_FP64) {
+    const int cta = std::max(regs_f32[L.cfg], 1);
+    int per = occ;
+    while (per > 1 && (int64_t)per * cta + chain_regs > sm_regs) --per;
+    return per;
+  }
+  return occ >= 4 ? occ - 1 : occ;
 }
 
 int Engine::fused_launch_count() const

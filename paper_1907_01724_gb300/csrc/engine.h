@@ -113,12 +113,16 @@ class Engine {
   // their own beside the moment chain, 0 = with the surface items after it (issue_fused);
   // forced_side >= 0 forces it, otherwise the tuned choice of the size class or a default
   int forced_side = -1;
-  int rk_side = 1;  // the current layout's choice
+  int rk_side = 1;  // the current layout's choice (0, 1 or 2, see issue_fused)
   struct Tuned {
     int bucket, cfg, side;
   };
   std::vector<Tuned> tuned;  // autotuned choices per size class
   std::vector<int> occ_f32, occ_field;
+  std::vector<int> regs_f32;  // registers of a CTA of each FP32 pair configuration
+  int chain_regs = 0;         // registers of the largest coefficient / surface CTA
+  int sm_regs = 65536;        // registers per SM
+  int side_ctas_per_sm(int occ) const;
   int occ_f64 = 1, occ_field64 = 1;
   std::vector<SysSpec> spec;
 

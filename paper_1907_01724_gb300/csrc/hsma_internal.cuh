@@ -281,6 +281,8 @@ PairConfig pair_config(int idx);
 int pair_workers_per_cta(int cfg);  // FP32 pair kernel: warps, each an independent worker
 int pair_kernel_of(int cfg);  // kernel variant (threads, k) of a configuration
 int pairs_f32_occupancy(int cfg);
+int pairs_f32_block_regs(int cfg);  // registers a CTA of the configuration holds
+int chain_block_regs(int prec);     // the same for the largest coefficient / surface CTA
 int pairs_f64_occupancy();
 constexpr int kF64TargetsPerBlock = 128;
 constexpr int kReduceTargetsPerBlock = 32;

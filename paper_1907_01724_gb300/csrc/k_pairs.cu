@@ -104,6 +104,21 @@ int pairs_f32_occupancy(int cfg)
   return b;
 }
 
+// registers a CTA of the configuration holds (the per-thread count in allocation units of 8)
+int pairs_f32_block_regs(int cfg)
+{
+  cudaFuncAttributes a{};
+  int nt = 0;
+  switch (pair_kernel_of(cfg)) {
+#define HSMA_CFG_REGS(i, t, k) \
+  case i: cudaFuncGetAttributes(&a, k_pairs_f32<t, k>); nt = t; break;
+    HSMA_PAIR_CONFIGS(HSMA_CFG_REGS)
+#undef HSMA_CFG_REGS
+    default: break;
+  }
+  return (a.numRegs + 7) / 8 * 8 * nt;
+}
+
 void launch_pairs_f32(int cfg, int grid, const SysDev* sys, PairWork w1, PairWork w2, const float4* src_hi,
                       const float4* src_lo, const float4* surf_a, const float4* surf_b, const float4* boxes,
                       float2* part, cudaStream_t st, bool pdl)

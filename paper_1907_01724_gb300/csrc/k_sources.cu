@@ -34,6 +34,7 @@
 // |m|.
 #include <math.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "df64.cuh"
@@ -1385,6 +1386,32 @@ static void launch_surface_mat(const int2* items, int nitems, size_t smem, const
   else
     launch_pdl(k_surface_mat<PW, df>, nitems, kSurfThreads, smem, st, sys, items, coef, coef2, sb, surf_a, surf_b,
                surf64_a, surf64_b, surfx, surfqd, prec);
+}
+
+// registers of the largest CTA among the coefficient and surface kernels of a precision (the
+// kernels that a real/Kelvin pair launch beside them must leave room for)
+int chain_block_regs(int prec)
+{
+  auto regs = [](const void* f, int threads) {
+    cudaFuncAttributes a{};
+    cudaFuncGetAttributes(&a, f);
+    return (a.numRegs + 7) / 8 * 8 * threads;
+  };
+  int r = 0;
+  if (prec == HSMA_FP64) {
+    r = std::max(r, regs((const void*)k_coef_reduce<double>, kCoefWarps * 32));
+    r = std::max(r, regs((const void*)k_surface_mat<1, double>, kSurfThreads));
+    r = std::max(r, regs((const void*)k_surface_mat<2, double>, kSurfThreads));
+    r = std::max(r, regs((const void*)k_surface_mat<4, double>, kSurfThreads));
+    r = std::max(r, regs((const void*)k_surface<double>, kSurfThreads));
+  } else {
+    r = std::max(r, regs((const void*)k_coef_reduce<df>, kCoefWarps * 32));
+    r = std::max(r, regs((const void*)k_surface_mat<1, df>, kSurfThreads));
+    r = std::max(r, regs((const void*)k_surface_mat<2, df>, kSurfThreads));
+    r = std::max(r, regs((const void*)k_surface_mat<4, df>, kSurfThreads));
+    r = std::max(r, regs((const void*)k_surface<df>, kSurfThreads));
+  }
+  return r;
 }
 
 void launch_surface(const SysDev* sys, const int2* items, int nitems, int maxP, int pw, const double* coef,

@@ -139,12 +139,13 @@ def test_autotune_picks_a_valid_config_and_stays_accurate():
 
 @pytest.mark.parametrize("nsys", [1, 3])
 def test_pair_schedules_agree_bitwise(nsys):
-    """The real/Kelvin pair items beside the coefficient chain (schedule 1) or after it (0): the
-    same items from the same work lists, so potentials, energies and fields are bitwise equal."""
+    """The real/Kelvin pair items beside the coefficient chain (schedules 1 and 2, which differ in
+    the side launch's grid) or after it (0): the same items from the same work lists, so
+    potentials, energies and fields are bitwise equal."""
     systems = mixed_systems(seed=9, sizes=(1500, 700, 2100)[:nsys])
     n, xyz, q = batch.concat(systems)
     out = []
-    for mode in (1, 0):
+    for mode in (1, 2, 0):
         b = batch.from_systems(systems)
         b.hsma_batch_set_pair_schedule(mode)
         b.hsma_batch_build_sources(n, xyz, q)
@@ -154,13 +155,14 @@ def test_pair_schedules_agree_bitwise(nsys):
         b.hsma_batch_build_sources(n, xyz, q)
         E = b.hsma_batch_field()
         out.append((phi, e, E))
-    for a, c in zip(out[0], out[1]):
-        assert np.array_equal(a, c)
+    for other in out[1:]:
+        for a, c in zip(out[0], other):
+            assert np.array_equal(a, c)
 
 
 def test_pair_schedule_rejects_bad_modes():
     b = batch.from_systems(mixed_systems(seed=9, sizes=(100,)))
-    for mode in (-2, 2):
+    for mode in (-2, 3):
         with pytest.raises(api.HsmaError):
             b.hsma_batch_set_pair_schedule(mode)
 
