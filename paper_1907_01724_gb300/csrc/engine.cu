@@ -787,9 +787,9 @@ void Engine::issue_build()
     cudaStreamWaitEvent(side, ev_fork, 0);
     PriorityScope ps(prio_hi);
     launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), indesc_d, xyz_d, q_d,
-                 key_d, hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, nullptr, 0, L.order_smem_n, side);
-    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
-                  prec, status_d, side);
+                 key_d, hist_d, sortscr_d, perm_d, xs_d, status_d, nullptr, 0, L.order_smem_n, side);
+    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, iperm_d, srchi_d, srclo_d, src64_d,
+                  boxes_d, prec, status_d, side);
     cudaEventRecord(ev_join, side);
   }
   issue_moments();
@@ -886,13 +886,15 @@ void Engine::issue_fused()
   {
     PriorityScope ps(prio_hi);
     launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), indesc_d, xyz_d, q_d,
-                 key_d, hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
-    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
-                  prec, status_d, side);
+                 key_d, hist_d, sortscr_d, perm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
+    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, iperm_d, srchi_d, srclo_d, src64_d,
+                  boxes_d, prec, status_d, side);
   }
   cudaEventRecord(ev_img, side);
   if (side_rk) {
-    launch_pair_items(rk, none, grid_rk, side);
+    // a programmatic dependent of k_images (which does not trigger early): its launch is set up
+    // while the records are written, and its CTAs start as soon as they are done
+    launch_pair_items(rk, none, grid_rk, side, true);
     cudaEventRecord(ev_join, side);
   }
   PriorityScope ps(prio_mid);
@@ -1235,9 +1237,9 @@ void Engine::issue_field_fused()
   {
     PriorityScope ps(prio_hi);
     launch_order(sys_d, nsys, itord_d, (int)L.itord.size(), itsort_d, (int)L.itsort.size(), indesc_d, xyz_d, q_d,
-                 key_d, hist_d, sortscr_d, perm_d, iperm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
-    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, srchi_d, srclo_d, src64_d, boxes_d,
-                  prec, status_d, side);
+                 key_d, hist_d, sortscr_d, perm_d, xs_d, status_d, ctr_pairs_d, 2, L.order_smem_n, side);
+    launch_images(sys_d, itord_d, (int)L.itord.size(), xyz_d, q_d, xs_d, perm_d, iperm_d, srchi_d, srclo_d, src64_d,
+                  boxes_d, prec, status_d, side);
   }
   cudaEventRecord(ev_img, side);
   if (side_rk) {

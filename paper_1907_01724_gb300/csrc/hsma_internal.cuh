@@ -151,7 +151,7 @@ struct InDesc {
 
 // Spatial order (k_order.cu): charges sorted by the Morton index of their cell on a 16^3 grid
 // over [-a, a]^3 (input index inside a cell).  perm[chg + i] = input index of sorted position
-// i, iperm its inverse.  Pair-sum records, pair partials and move work use sorted positions.
+// i (its inverse iperm is written by k_images).  Pair-sum records, pair partials and move work use sorted positions.
 // launch_order writes the cell keys and the cell histogram (items = (system, block of
 // kOrderBlock charges)), then sorts each system in sort_parts blocks (sitems = (system, part)),
 // each taking a run of consecutive cells; its first kernel also zeroes the nreset counters at
@@ -176,8 +176,7 @@ int order_sort_parts(int64_t n);
 // |x| >= a or with a non-finite coordinate or charge.
 void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const int2* sitems, int nsitems,
                   const InDesc* in, double* xyz_own, double* q_own, int* key, int* hist, int* scr, int* perm,
-                  int* iperm, float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n,
-                  cudaStream_t st);
+                  float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st);
 // Boxes of 32 consecutive sorted records: a warp's targets and a box farther apart than
 // kNearRel a use plain FP32 coordinates in the pair sum, nearer ones the hi/lo-split form.
 constexpr int kBox = 32;
@@ -213,11 +212,12 @@ void launch_setup(SysDev* sys, int nsys, double* Mn, double* rec_a, double* rec_
                   float2* rec_a2, float2* rec_b2, float2* sect2, float2* mtab, int pmax, dbl4* surfx,
                   cudaStream_t st);
 constexpr int kCoefChunk = 32;  // coefficients per k_coef_reduce block
-// Records at sorted positions (items = (system, block of kOrderBlock sorted positions)); the
-// FP32 path also writes the boxes (2 float4 per box: min and max of the hi coordinates).
+// Records at sorted positions (items = (system, block of kOrderBlock sorted positions)) and the
+// inverse of the order (iperm: input index -> sorted position, for the move kernels); the FP32
+// path also writes the boxes (2 float4 per box: min and max of the hi coordinates).
 void launch_images(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
-                   const float4* xs, const int* perm, float4* src_hi, float4* src_lo, dbl4* src64, float4* boxes,
-                   int prec, int* status, cudaStream_t st);
+                   const float4* xs, const int* perm, int* iperm, float4* src_hi, float4* src_lo, dbl4* src64,
+                   float4* boxes, int prec, int* status, cudaStream_t st);
 // Moment rows: per block, sum_i q_i (M_n - gamma - c_i) T_nm(x_i/a) for the P coefficients
 // (slots 0 .. P-1) and the block's centre constant (slot P).
 // G: charges per moment group (moment_smem_group; the layout's tiles are multiples of it).

@@ -17,7 +17,7 @@
 //                  flight) and scatters those of its cells (atomic cursor in shared memory: any
 //                  order inside a cell), then every slot finds its place in its cell by counting
 //                  the cell's smaller input indices (the rank; cells hold a few charges), which
-//                  gives perm and iperm
+//                  gives perm (k_images, which reads perm on many SMs, writes its inverse)
 // Two kernels and no memsets: the order is on the critical path of the overlapped step.
 #include <algorithm>
 
@@ -97,8 +97,7 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
                                                              const int2* __restrict__ items,
                                                              const int* __restrict__ key, int* __restrict__ hist,
                                                              int* __restrict__ done, int* __restrict__ scr,
-                                                             int* __restrict__ perm, int* __restrict__ iperm,
-                                                             int smem_n)
+                                                             int* __restrict__ perm, int smem_n)
 {
   __shared__ int s_cell[kOrderCells];
   __shared__ int s_wsum[kSortWarps];
@@ -195,7 +194,6 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
     int p = b0;
     for (int b = b0; b < e; ++b) p += slot[b] < v;
     perm[c0 + P0 + p] = v;
-    iperm[c0 + v] = P0 + p;
   }
 }
 
@@ -219,14 +217,13 @@ int order_smem_charges(int64_t max_n)
 
 void launch_order(const SysDev* sys, int nsys, const int2* items, int nitems, const int2* sitems, int nsitems,
                   const InDesc* in, double* xyz_own, double* q_own, int* key, int* hist, int* scr, int* perm,
-                  int* iperm, float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n,
-                  cudaStream_t st)
+                  float4* xs, int* status, unsigned int* ctr_reset, int nreset, int smem_n, cudaStream_t st)
 {
   if (nitems <= 0 || nsys <= 0 || nsitems <= 0) return;
   launch_k(k_order_keys, nitems * kKeySplit, kKeyThreads, 0, st, false, sys, items, in, xyz_own, q_own, key, hist,
            xs, status, ctr_reset, nreset);
   launch_k(k_order_sort, nsitems, kSortThreads, 2 * sizeof(int) * (size_t)smem_n, st, false, sys, sitems,
-           (const int*)key, hist, hist + (size_t)nsys * kOrderCells, scr, perm, iperm, smem_n);
+           (const int*)key, hist, hist + (size_t)nsys * kOrderCells, scr, perm, smem_n);
 }
 
 }  // namespace hsma

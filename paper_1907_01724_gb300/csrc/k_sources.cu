@@ -389,6 +389,7 @@ constexpr int kImgSplit = kOrderBlock / kImgThreads;
 __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict__ sys, const int2* __restrict__ items,
                                                         const double* __restrict__ xyz, const double* __restrict__ q,
                                                         const float4* __restrict__ xs, const int* __restrict__ perm,
+                                                        int* __restrict__ iperm,
                                                         float4* __restrict__ src_hi, float4* __restrict__ src_lo,
                                                         dbl4* __restrict__ src64, float4* __restrict__ boxes, int prec,
                                                         int* __restrict__ status)
@@ -410,6 +411,7 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
   if (prec == HSMA_FP64) {
     if (i < n) {
       const long long gi = S.chg + perm[S.chg + i];
+      iperm[gi] = i;
       const double x = xyz[3 * gi], y = xyz[3 * gi + 1], z = xyz[3 * gi + 2], qi = q[gi];
       const KelvinRec k = kelvin_rec(S, x, y, z, qi);
       if (!(k.r < S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) atomicOr(status, kStOutside);
@@ -430,6 +432,7 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
     const float4 h = xs[2 * gi], l = xs[2 * gi + 1];
     const df X = df_make(h.x, l.x), Y = df_make(h.y, l.y), Z = df_make(h.z, l.z), Q = df_make(h.w, l.w);
     if (on) {
+      iperm[gi] = i;
       src_hi[sr] = make_float4(h.x, h.y, h.z, (df_make(S.f_kc.x, S.f_kc.y) * Q).hi);
       src_lo[sr] = make_float4(l.x, l.y, l.z, 0.f);
       bmin[0] = bmax[0] = h.x;
@@ -486,12 +489,12 @@ __global__ __launch_bounds__(kImgThreads) void k_images(const SysDev* __restrict
 }
 
 void launch_images(const SysDev* sys, const int2* items, int nitems, const double* xyz, const double* q,
-                   const float4* xs, const int* perm, float4* src_hi, float4* src_lo, dbl4* src64, float4* boxes,
-                   int prec, int* status, cudaStream_t st)
+                   const float4* xs, const int* perm, int* iperm, float4* src_hi, float4* src_lo, dbl4* src64,
+                   float4* boxes, int prec, int* status, cudaStream_t st)
 {
   if (nitems <= 0) return;
-  launch_k(k_images, nitems * kImgSplit, kImgThreads, 0, st, true, sys, items, xyz, q, xs, perm, src_hi, src_lo,
-           src64, boxes, prec, status);
+  launch_k(k_images, nitems * kImgSplit, kImgThreads, 0, st, true, sys, items, xyz, q, xs, perm, iperm, src_hi,
+           src_lo, src64, boxes, prec, status);
 }
 
 // Moment inputs of one charge in double-float: u, v, w = x/a, rho^2 = |x|^2/a^2, q and q c with
