@@ -292,17 +292,20 @@ def pair_kernel_alone(b, step, flush, reps):
 
 
 def e2e_run(b, n, xyz, q, units_per_step, world, k):
-    """End to end through the C ABI with pinned host buffers: the H2D copy of the inputs, the
-    step, and the D2H read of the potentials and energies inside the timed region."""
+    """End to end through the C ABI with pinned host buffers: the host-to-device transfer of the
+    inputs (read in place from the page-locked arrays by the pass's first kernels), the step, and
+    the device-to-host transfer of the potentials (written into a page-locked array by the
+    reduction) and of the energies, all inside the timed region."""
     import torch
 
     from paper_1907_01724_gb300 import api
     xyz_h = torch.tensor(xyz).pin_memory().numpy()
     q_h = torch.tensor(q).pin_memory().numpy()
+    phi_h = torch.empty(int(n.sum()), dtype=torch.float64).pin_memory().numpy()
 
     def e2e_step():
         b.hsma_batch_build_sources(n, xyz_h, q_h)
-        b.hsma_batch_potential(api.HSMA_TOTAL)
+        b.hsma_batch_potential(api.HSMA_TOTAL, out=phi_h)
         b.hsma_batch_energy()
 
     for _ in range(3):

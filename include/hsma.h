@@ -110,7 +110,10 @@ HSMA_API int hsma_attach_workspace(hsma_t* h, void* device_ptr, size_t bytes);
  * q: host (n).  n >= 0.  Every |x_i| must be < a with finite coordinates and charges: the
  * first kernel of the pass checks every charge on the device (host and device inputs alike),
  * and the evaluation that runs the pass (hsma_potential, hsma_energy, hsma_field) returns
- * HSMA_E_OUTSIDE.  Asynchronous with respect to the host once the inputs are copied. */
+ * HSMA_E_OUTSIDE.  Pageable host arrays are copied before the call returns (it is then
+ * asynchronous with respect to the host); page-locked host arrays (cudaHostAlloc,
+ * cudaMallocHost, cudaHostRegister) are read in place by the next evaluation, as device arrays
+ * are (see hsma_build_sources_device): keep them unchanged until its work has run. */
 HSMA_API int hsma_build_sources(hsma_t* h, int64_t n, const double* xyz, const double* q);
 
 /* Same as hsma_build_sources with inputs already resident on the device, read in place: this
@@ -121,7 +124,8 @@ HSMA_API int hsma_build_sources(hsma_t* h, int64_t n, const double* xyz, const d
 HSMA_API int hsma_build_sources_device(hsma_t* h, int64_t n, const double* xyz_dev, const double* q_dev);
 
 /* Potentials at the n charges (Algorithm 1 step 5, by direct tiled summation):
- * what = HSMA_TOTAL, HSMA_REACTION or HSMA_COULOMB.  phi: host array of n doubles.
+ * what = HSMA_TOTAL, HSMA_REACTION or HSMA_COULOMB.  phi: host array of n doubles (a
+ * page-locked one is written by the device itself, without a staging copy).
  * Synchronises the handle's stream; returns HSMA_E_NONFINITE for coincident charges. */
 HSMA_API int hsma_potential(hsma_t* h, double* phi, int what);
 
@@ -213,14 +217,15 @@ HSMA_API int hsma_batch_attach_workspace(hsma_batch_t* b, void* device_ptr, size
 HSMA_API int hsma_batch_set_max_requests(hsma_batch_t* b, int max_requests);
 
 /* Build all sources (Sec. 2.4) for n[nsys] charges per system: xyz (sum n, 3) and q (sum n),
- * host or device memory respectively (device inputs are read in place by the next evaluation,
- * as for hsma_build_sources_device).  A charge outside its cavity or a non-finite value is
+ * host or device memory respectively (device and page-locked host inputs are read in place by
+ * the next evaluation, as for hsma_build_sources).  A charge outside its cavity or a non-finite value is
  * reported as HSMA_E_OUTSIDE by the evaluation that runs the pass (see hsma_build_sources). */
 HSMA_API int hsma_batch_build_sources(hsma_batch_t* b, const int64_t* n, const double* xyz, const double* q);
 HSMA_API int hsma_batch_build_sources_device(hsma_batch_t* b, const int64_t* n, const double* xyz_dev,
                                              const double* q_dev);
 
-/* Potentials of all charges (sum n doubles, concatenated), host or device output. */
+/* Potentials of all charges (sum n doubles, concatenated), host or device output (a
+ * page-locked host array is written by the device itself, as for hsma_potential). */
 HSMA_API int hsma_batch_potential(hsma_batch_t* b, double* phi, int what);
 HSMA_API int hsma_batch_potential_device(hsma_batch_t* b, double* phi_dev, int what);
 

@@ -154,16 +154,24 @@ def hsma_build_sources(h: Handle, xyz, q) -> None:
             raise ValueError("xyz and q sizes differ")
         _ensure_workspace(h, n)
         _check(lib.hsma_build_sources(h.ptr, n, _dptr(xyz_a), _dptr(q_a)), h.ptr)
+        h._keep = (xyz_a, q_a)  # page-locked arrays are read by the next evaluation
     h.n = n
 
 
 def hsma_potential(h: Handle, what: int = HSMA_TOTAL, out=None):
-    """Potentials at the charges: numpy array, or into a torch CUDA tensor given as out."""
+    """Potentials at the charges: into out (a torch CUDA tensor, or a float64 numpy array of n
+    entries, written by the device itself when it is page-locked), else a new numpy array."""
     lib = _native.load()
     if out is not None and _is_torch_cuda(out):
         _check(lib.hsma_potential_device(h.ptr, ctypes.c_void_p(out.data_ptr()), int(what)), h.ptr)
         return out
-    phi = np.empty(max(h.n, 0), dtype=np.float64)
+    if out is not None:
+        if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+                and out.flags.writeable and out.size == max(h.n, 0)):
+            raise ValueError(f"out must be a writable C-contiguous float64 array of {max(h.n, 0)} entries")
+        phi = out
+    else:
+        phi = np.empty(max(h.n, 0), dtype=np.float64)
     _check(lib.hsma_potential(h.ptr, _dptr(phi), int(what)), h.ptr)
     return phi
 

@@ -22,6 +22,16 @@ def _arr(x, dtype):
 _p = _native.host_ptr
 
 
+def _host_out(out, count: int) -> np.ndarray:
+    """A writable C-contiguous float64 host array of count entries: out itself, or a new one."""
+    if out is None:
+        return np.empty(count, dtype=np.float64)
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.flags.writeable and out.size == count):
+        raise ValueError(f"out must be a writable C-contiguous float64 array of {count} entries")
+    return out
+
+
 def _is_torch_cuda(x) -> bool:
     return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
 
@@ -107,15 +117,18 @@ class Batch:
         else:
             x = _arr(xyz, np.float64).reshape(-1, 3)
             qq = _arr(q, np.float64)
+            self._keep = (x, qq)  # page-locked arrays are read by the next evaluation
             self._check(self.lib.hsma_batch_build_sources(self.ptr, _p(n), _p(x), _p(qq)))
         self.n = n
         self._ntot = int(n.sum())
 
     def hsma_batch_potential(self, what: int = HSMA_TOTAL, out=None):
+        """Potentials of all charges: into out (a torch CUDA tensor, or a float64 numpy array of
+        sum n entries, written by the device itself when it is page-locked), else a new array."""
         if out is not None and _is_torch_cuda(out):
             self._check(self.lib.hsma_batch_potential_device(self.ptr, ctypes.c_void_p(out.data_ptr()), int(what)))
             return out
-        phi = np.empty(self._ntot, dtype=np.float64)
+        phi = _host_out(out, self._ntot)
         self._check(self.lib.hsma_batch_potential(self.ptr, _p(phi), int(what)))
         return phi
 

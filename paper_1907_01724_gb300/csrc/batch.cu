@@ -316,10 +316,12 @@ static int batch_pot(hsma_batch_t* b, double* phi, int what, bool dev)
   // output) to pinned staging together with the energy terms (hsma_batch_energy then reads them
   // without a second round trip); a pass already run: copies
   hsma::OutDesc od{dev && tot > 0 ? phi : nullptr, nullptr, nullptr, Engine::out_lane(what), 0};
+  double* phi_dev = nullptr;  // a page-locked host output: written by the device itself
   if (!dev) {
     const int rs = b->e->ensure_host_stage(tot);
     if (rs) return bfrom(b, rs);
-    od = b->e->host_outputs(tot, what);
+    phi_dev = static_cast<double*>(const_cast<void*>(hsma::pinned_device_address(phi)));
+    od = b->e->host_outputs(tot, what, phi_dev);
   }
   bool wrote = false;
   int rc = b->e->potentials(od, &wrote);
@@ -331,7 +333,7 @@ static int batch_pot(hsma_batch_t* b, double* phi, int what, bool dev)
     }
     return HSMA_OK;
   }
-  return bfrom(b, b->e->copy_to_host(src, tot, phi, wrote));
+  return bfrom(b, b->e->copy_to_host(src, tot, phi, wrote, phi_dev != nullptr));
 }
 
 static int batch_field(hsma_batch_t* b, double* E, int what, bool dev)

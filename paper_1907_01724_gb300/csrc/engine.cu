@@ -962,16 +962,34 @@ int Engine::run_graph(cudaGraphExec_t* g, void (Engine::*issue)())
   return HSMA_OK;
 }
 
-// Host inputs are copied to xyz_d, q_d now.  Device inputs are not copied: the build pass (run
-// by the next evaluation) reads them in place through the inputs descriptor, and its first
-// kernel writes the engine's own copy, so a step from device inputs has no copy launches.
+// The device address of page-locked host memory (registered or allocated through CUDA), else
+// null (pageable memory, or not host memory).
+const void* pinned_device_address(const void* p)
+{
+  cudaPointerAttributes a{};
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Pageable host inputs are copied to xyz_d, q_d now.  Device inputs and page-locked host inputs
+// are not copied: the build pass (run by the next evaluation) reads them in place through the
+// inputs descriptor, and its first kernel writes the engine's own copy, so such a step has no
+// copy launches.
 int Engine::build(const double* xyz, const double* q, bool device_inputs)
 {
   CK(cudaSetDevice(device));
   const int64_t n = L.totN;
   in_pending = false;
-  if (n > 0 && device_inputs) {
-    in_user = InDesc{xyz, q, 1, 0};
+  const double *xyz_in = device_inputs ? xyz : nullptr, *q_in = device_inputs ? q : nullptr;
+  if (n > 0 && !device_inputs) {
+    xyz_in = static_cast<const double*>(pinned_device_address(xyz));
+    q_in = static_cast<const double*>(pinned_device_address(q));
+  }
+  if (n > 0 && xyz_in && q_in) {
+    in_user = InDesc{xyz_in, q_in, 1, 0};
     in_pending = true;
   } else if (n > 0) {
     enter();
@@ -1311,14 +1329,16 @@ int Engine::out_lane(int what) { return what == HSMA_COULOMB ? 0 : (what == HSMA
 
 // Pinned staging of a host-output pass: values at byte 256, the status bytes at byte 16 (zeroed
 // here: the staging buffer is written only by passes that a host-output call waits for).
-OutDesc Engine::host_outputs(int64_t count, int what)
+// phi_dev: the device address of the caller's page-locked output array (written there directly),
+// else null (written to the staging buffer and copied out by copy_to_host)
+OutDesc Engine::host_outputs(int64_t count, int what, double* phi_dev)
 {
   std::memset(host_stage + 16, 0, kStBits);
-  return OutDesc{count > 0 ? host_stage_dev + 32 : nullptr, energy_h_dev,
+  return OutDesc{count > 0 ? (phi_dev ? phi_dev : host_stage_dev + 32) : nullptr, energy_h_dev,
                  reinterpret_cast<unsigned char*>(host_stage_dev) + 16, out_lane(what), 0};
 }
 
-int Engine::copy_to_host(const double* src_d, int64_t count, double* dst_h, bool written)
+int Engine::copy_to_host(const double* src_d, int64_t count, double* dst_h, bool written, bool direct)
 {
   if (8 * (size_t)std::max<int64_t>(count, 0) + 256 > host_stage_cap)
     return fail(HSMA_E_STATE, "host staging buffer not allocated");
@@ -1333,7 +1353,8 @@ int Engine::copy_to_host(const double* src_d, int64_t count, double* dst_h, bool
     for (int b = 0; b < kStBits; ++b)
       if (sb[b]) st |= 1 << b;
   } else {
-    if (count > 0) CK(cudaMemcpyAsync(vals, src_d, 8 * (size_t)count, cudaMemcpyDeviceToHost, stream));
+    if (count > 0)
+      CK(cudaMemcpyAsync(direct ? dst_h : vals, src_d, 8 * (size_t)count, cudaMemcpyDeviceToHost, stream));
     const int rs = stage_energies();
     if (rs) return rs;
     CK(cudaMemcpyAsync(st_h, status_d, sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -1342,7 +1363,7 @@ int Engine::copy_to_host(const double* src_d, int64_t count, double* dst_h, bool
   }
   const int rc = decode_status(st);
   if (rc) return rc;
-  if (count > 0) std::memcpy(dst_h, vals, 8 * (size_t)count);
+  if (count > 0 && !direct) std::memcpy(dst_h, vals, 8 * (size_t)count);
   energy_h_epoch = pot_epoch;
   return HSMA_OK;
 }
@@ -1607,9 +1628,10 @@ int hsma_potential(hsma_t* h, double* phi, int what)
   int rc = h->e->ensure_host_stage(h->n);
   if (rc) return from_engine(h, rc);
   bool wrote = false;
-  rc = h->e->potentials(h->e->host_outputs(h->n, what), &wrote);
+  double* phi_dev = static_cast<double*>(const_cast<void*>(hsma::pinned_device_address(phi)));
+  rc = h->e->potentials(h->e->host_outputs(h->n, what, phi_dev), &wrote);
   if (rc) return from_engine(h, rc);
-  return from_engine(h, h->e->copy_to_host(src, h->n, phi, wrote));
+  return from_engine(h, h->e->copy_to_host(src, h->n, phi, wrote, phi_dev != nullptr));
 }
 
 int hsma_potential_device(hsma_t* h, double* phi_dev, int what)

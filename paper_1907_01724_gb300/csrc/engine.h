@@ -20,6 +20,7 @@ struct SysSpec {
 int make_spec(double a, double eps1, double eps2, double kappa, const hsma_params* prm, SysSpec* out,
               std::string& why);
 int tune_bucket(int64_t total_n, int nsys);
+const void* pinned_device_address(const void* p);  // page-locked host memory: its device address
 
 // Sizes, offsets into the workspace, and work lists for a set of systems.
 struct Layout {
@@ -228,9 +229,10 @@ class Engine {
   double* host_stage_dev = nullptr;  // device addresses of the pinned buffers (kernel writes)
   double* energy_h_dev = nullptr;
   // the results of a host-output call: written: the pass just run wrote the values and the
-  // energy terms into the pinned buffers itself (OutDesc from host_outputs), else copied here
-  int copy_to_host(const double* src_d, int64_t count, double* dst_h, bool written = false);
-  OutDesc host_outputs(int64_t count, int what);
+  // energy terms into the pinned buffers itself (OutDesc from host_outputs), else copied here;
+  // direct: dst_h is page-locked and was (or is now) written by the device itself
+  int copy_to_host(const double* src_d, int64_t count, double* dst_h, bool written = false, bool direct = false);
+  OutDesc host_outputs(int64_t count, int what, double* phi_dev = nullptr);
   static int out_lane(int what);  // HSMA_TOTAL / HSMA_REACTION / HSMA_COULOMB -> OutDesc::what
   int decode_status(int st);
   bool field_ready = false;       // E is current when pot_ready && field_ready

@@ -63,7 +63,7 @@ __device__ __forceinline__ ChunkInfo decode_chunk(const SysDev& S, int c)
 // ---------------------------------------------------------------------------------------
 #include "k_pairs_f32.cuh"
 
-// Tile configurations: kernel variants (CTA threads, targets per thread), each with 4, 2 or 1
+// Tile configurations: kernel variants (CTA threads, targets per thread), each with 4, 2, 1 or 8
 // pair items per resident CTA slot (fewer, larger items have less per-item overhead, more items
 // balance better); the autotuner picks one per size class.
 #define HSMA_PAIR_CONFIGS(X) \
@@ -76,7 +76,7 @@ static const int kPairKernel[][2] = {
 #undef HSMA_CFG_ENTRY
 };
 constexpr int kPairKernels = (int)(sizeof(kPairKernel) / sizeof(kPairKernel[0]));
-static const int kItemsPerSlot[] = {4, 2, 1};
+static const int kItemsPerSlot[] = {4, 2, 1, 8};
 constexpr int kItemChoices = (int)(sizeof(kItemsPerSlot) / sizeof(kItemsPerSlot[0]));
 
 int pair_config_count() { return kPairKernels * kItemChoices; }

@@ -186,3 +186,48 @@ def test_device_inputs_read_in_place(prec):
         b.hsma_batch_build_sources(n, xyz1_d, q_d)
         b.hsma_batch_autotune(1)
         assert rel(b.hsma_batch_potential(), phi1) <= tol
+
+
+@pytest.mark.parametrize("prec", [api.HSMA_FP32, api.HSMA_FP64])
+def test_page_locked_host_buffers(prec):
+    """Page-locked host inputs are read in place by the evaluation (like device inputs) and a
+    page-locked output array is written by the device itself: the results equal those of the
+    pageable path bitwise; rewriting the page-locked inputs after the evaluation changes nothing
+    the handle returns until the next build, which reads the new values."""
+    tol = 1e-6 if prec == api.HSMA_FP32 else 1e-12
+    sy = systems()
+    n, xyz, q = batch.concat(sy)
+    tot = int(n.sum())
+    r1 = refs(sy)
+    phi1 = np.concatenate([r["phi"] for r in r1])
+    b = batch.from_systems(sy, precision=prec)
+    b.hsma_batch_build_sources(n, xyz, q)
+    ref_pageable = b.hsma_batch_potential()
+    e_pageable, _ = b.hsma_batch_energy()
+    xyz_h = torch.tensor(xyz).pin_memory().numpy()
+    q_h = torch.tensor(q).pin_memory().numpy()
+    out_h = torch.full((tot,), -7.0, dtype=torch.float64).pin_memory().numpy()
+    b.hsma_batch_build_sources(n, xyz_h, q_h)
+    got = b.hsma_batch_potential(out=out_h)
+    assert got is out_h
+    assert np.array_equal(out_h, ref_pageable)
+    e_pinned, _ = b.hsma_batch_energy()
+    assert np.array_equal(e_pinned, e_pageable)
+    assert rel(out_h, phi1) <= tol
+    xyz_h *= 0.97  # the caller rewrites its page-locked inputs after the evaluation
+    out_h[:] = -7.0
+    b.hsma_batch_potential(out=out_h)  # the current pass: copied into the page-locked array
+    assert np.array_equal(out_h, ref_pageable)
+    b.hsma_batch_build_sources(n, xyz_h, q_h)
+    sy2 = [inputs.System(xyz=xyz_h[a:a + s.n].copy(), q=s.q, a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p,
+                         M=s.M, tau=s.tau) for s, a in zip(sy, np.cumsum([0] + [s.n for s in sy])[:-1])]
+    phi2 = np.concatenate([r["phi"] for r in refs(sy2)])
+    assert rel(b.hsma_batch_potential(out=out_h), phi2) <= tol
+    h = api.hsma_create(1.0, 1.0, 78.5, 1.0, api.hsma_default_params(p=12, M=400, precision=prec))
+    try:
+        api.hsma_build_sources(h, xyz_h[:sy[0].n], q_h[:sy[0].n])
+        one = torch.empty(sy[0].n, dtype=torch.float64).pin_memory().numpy()
+        api.hsma_potential(h, out=one)
+        assert rel(one, phi2[:sy[0].n]) <= tol
+    finally:
+        api.hsma_destroy(h)
