@@ -19,8 +19,8 @@ CSRC = os.path.join(_HERE, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_HERE, "_build")
 LIB = os.path.join(BUILD, "libhsma.so")
-SOURCES = ["k_order.cu", "k_sources.cu", "k_pairs.cu", "k_reduce.cu", "k_field.cu", "k_delta.cu", "engine.cu", "batch.cu", "server.cu", "noalloc.cu"]
-HEADERS = ["hsma_internal.cuh", "engine.h", "df64.cuh", "k_pairs_f32.cuh", "pair_work.cuh", "fp32_pair.cuh"]
+SOURCES = ["k_order.cu", "k_sources.cu", "k_pairs.cu", "k_reduce.cu", "k_field.cu", "k_delta.cu", "engine.cu", "batch.cu", "server.cu", "noalloc.cu", "k_tree.cu"]
+HEADERS = ["hsma_internal.cuh", "engine.h", "df64.cuh", "k_pairs_f32.cuh", "pair_work.cuh", "fp32_pair.cuh", "tree.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 LINK_FLAGS = ["-Xlinker", "--exclude-libs,ALL", "-Xcompiler", "-fPIC"]
@@ -135,6 +135,8 @@ def _declare(lib):
         "hsma_kernel_launches": (ctypes.c_int64, [vp]),
         "hsma_set_overlap": (ctypes.c_int, [vp, ctypes.c_int]),
         "hsma_last_pair_time": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
+        "hsma_set_far_field": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
+        "hsma_last_far_time": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "hsma_coefficients": (ctypes.c_int, [vp, vp, i64]),
         "hsma_batch_create": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, vp, pp, ctypes.POINTER(vp)]),
         "hsma_batch_destroy": (None, [vp]),

@@ -227,6 +227,20 @@ def hsma_last_pair_time(h: Handle) -> float:
     return float(ms.value)
 
 
+def hsma_set_far_field(h: Handle, theta: float, order: int = 12) -> None:
+    """Real/Kelvin pair sums by the treecode (opening criterion theta, multipole order 8/12/16);
+    theta = 0 restores the direct sum.  Takes effect at the next hsma_build_sources."""
+    _check(_native.load().hsma_set_far_field(h.ptr, float(theta), int(order)), h.ptr)
+    h._ws_n = None  # the layout (and its workspace size) changes
+
+
+def hsma_last_far_time(h: Handle) -> float:
+    """Milliseconds of the most recent treecode evaluation kernel (CUDA events)."""
+    ms = ctypes.c_float()
+    _check(_native.load().hsma_last_far_time(h.ptr, ctypes.byref(ms)), h.ptr)
+    return float(ms.value)
+
+
 @dataclass
 class Result:
     phi: np.ndarray

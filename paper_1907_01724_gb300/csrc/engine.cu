@@ -86,6 +86,8 @@ int Engine::init(int dev, void* user_stream, int precision)
   for (int c = 0; c < pair_config_count(); ++c) occ_field[c] = field_f32_occupancy(c);
   occ_field64 = field_f64_occupancy();
   CK(cudaEventCreate(&ev_pair0));
+  CK(cudaEventCreate(&ev_tree0));
+  CK(cudaEventCreate(&ev_tree1));
   CK(cudaEventCreate(&ev_pair1));
   CK(cudaEventCreate(&ev_pot1));
   CK(cudaEventCreate(&ev_tune0));
@@ -152,6 +154,8 @@ Engine::~Engine()
   if (fpart_d) cudaFree(fpart_d);
   if (E_d) cudaFree(E_d);
   if (ev_pair0) cudaEventDestroy(ev_pair0);
+  if (ev_tree0) cudaEventDestroy(ev_tree0);
+  if (ev_tree1) cudaEventDestroy(ev_tree1);
   if (ev_pair1) cudaEventDestroy(ev_pair1);
   if (ev_pot1) cudaEventDestroy(ev_pot1);
   if (ev_tune0) cudaEventDestroy(ev_tune0);
@@ -223,6 +227,12 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     for (int s = 0; s < nsys; ++s) U1 += (ns[s] + 31) / 32 * moment_unit_pairs(spec[s].p);
     kg = (int)std::max<int64_t>(1, U1 / (96 * (int64_t)num_sms));
   }
+  // the far-field tree replaces the direct real/Kelvin pair sum of a single FP32 system
+  L.tree = prec != HSMA_FP64 && far_theta > 0.0 && nsys == 1 && ns[0] > 0;
+  if (L.tree) {
+    L.tL = tree_levels(ns[0]);
+    L.tP = far_order;
+  }
   L.sd.resize(nsys);
   int64_t zoff = 0;
   int64_t chg = 0, surf = 0, coef = 0, mn = 0, mom = 0, part = 0, boxes = 0;
@@ -240,6 +250,7 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
     d.n = (int)n;
     d.prec = prec;
     d.sort_parts = order_sort_parts(n);
+    d.key_lv = L.tree ? std::max(kOrderLevels, L.tL) : kOrderLevels;
     d.chg = chg; d.src = 2 * chg; d.surf = surf; d.coef = coef; d.mn = mn;
     d.mom = mom;
     // FP64 path: charges per moment block, enough blocks to cover the SMs twice over the whole
@@ -277,14 +288,20 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
         // real and Kelvin: nb blocks that are also the chunks, nb (nb + 1) items (each unordered
         // pair of blocks once, real and Kelvin); a block is a whole number of the pair kernel's
         // target groups and at most kSymChunkMax charges
-        const double items_rk = items_s * (2.0 * n) / (2.0 * n + 1.3 * sp.M);
-        const int64_t nb = std::max<int64_t>(1, (int64_t)std::floor(std::sqrt(std::max(items_rk, 1.0))));
-        int64_t chunk = (n + nb - 1) / nb;
-        chunk = (chunk + TB - 1) / TB * TB;
-        chunk = std::min<int64_t>(std::max<int64_t>(chunk, TB), kSymChunkMax / TB * TB);
-        d.chunk = (int)chunk;
-        d.ncr = (int)((n + chunk - 1) / chunk);
-        d.nck = d.ncr;
+        const double items_rk = L.tree ? 0.0 : items_s * (2.0 * n) / (2.0 * n + 1.3 * sp.M);
+        if (L.tree) {
+          // one chunk each: the tree's real and Kelvin sums (k_tree_eval), no pair items
+          d.chunk = (int)n;
+          d.ncr = d.nck = 1;
+        } else {
+          const int64_t nb = std::max<int64_t>(1, (int64_t)std::floor(std::sqrt(std::max(items_rk, 1.0))));
+          int64_t chunk = (n + nb - 1) / nb;
+          chunk = (chunk + TB - 1) / TB * TB;
+          chunk = std::min<int64_t>(std::max<int64_t>(chunk, TB), kSymChunkMax / TB * TB);
+          d.chunk = (int)chunk;
+          d.ncr = (int)((n + chunk - 1) / chunk);
+          d.nck = d.ncr;
+        }
         // surface: the rest of the items over the target groups, chunks of whole 32-point boxes
         const double items_sf = std::max(1.0, items_s - items_rk);
         const int64_t ncs_want = std::max<int64_t>(1, std::llround(items_sf / d.n_tb));
@@ -319,16 +336,17 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
       for (int tb = 0; tb < d.n_tb; ++tb)
         for (int c = 0; c < nch; ++c) L.it4.push_back(make_int4(s, tb, c, 0));
     } else if (n > 0) {
-      // the pair kernel: each unordered pair of real/Kelvin blocks once, surface items per group
-      for (int b = 0; b < d.ncr; ++b)
+      // the pair kernel: each unordered pair of real/Kelvin blocks once (none with the tree),
+      // surface items per group
+      for (int b = 0; b < (L.tree ? 0 : d.ncr); ++b)
         for (int c = b; c < d.ncr; ++c) {
           L.it4.push_back(make_int4(s, b, c, 0));
           L.it4.push_back(make_int4(s, b, d.ncr + c, 0));
         }
       for (int tb = 0; tb < d.n_tb; ++tb)
         for (int c = d.ncr + d.nck; c < nch; ++c) L.it4.push_back(make_int4(s, tb, c, 0));
-      // the field kernel: every (target block, chunk) one way
-      const int ntbf = (int)((n + TBf - 1) / TBf);
+      // the field kernel: every (target block, chunk) one way (no field pass with the tree)
+      const int ntbf = L.tree ? 0 : (int)((n + TBf - 1) / TBf);
       for (int tb = 0; tb < ntbf; ++tb)
         for (int c = 0; c < nch; ++c) L.it4f.push_back(make_int4(s, tb, c, 0));
     }
@@ -549,6 +567,16 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
   }
   L.o_sel = take(sizeof(int) * (size_t)nsys);
   L.o_selrng = take(sizeof(int2) * (size_t)nsys);
+  if (L.tree) {
+    const size_t nodes = (size_t)tree_node_count(L.tL), nm = (size_t)tree_nm(L.tP);
+    L.o_tnode = take(sizeof(int2) * nodes);
+    L.o_tgeo = take(sizeof(float4) * 2 * nodes);
+    L.o_tbox = take(sizeof(float4) * 4 * nodes);
+    L.o_tmom = take(sizeof(float2) * 2 * nodes * nm);
+    L.o_tfarp = take(sizeof(float2) * kFarBlocks * (size_t)tree_nm(kFarOrder));
+    L.o_tfarL = take(sizeof(float2) * (size_t)tree_nm(kFarOrder));
+    L.o_tctr = take(16);
+  }
   L.bytes = off;
   return L;
 }
@@ -764,6 +792,54 @@ Tables Engine::tables() const
   return t;
 }
 
+TreeView Engine::tree_view() const
+{
+  TreeView t{};
+  char* b = ws;
+  t.sys = sys_d;
+  t.key = key_d;
+  t.perm = perm_d;
+  t.hi = srchi_d;
+  t.lo = srclo_d;
+  t.node = (int2*)(b + L.o_tnode);
+  t.geo = (float4*)(b + L.o_tgeo);
+  t.box = (float4*)(b + L.o_tbox);
+  t.mom = (float2*)(b + L.o_tmom);
+  t.farp = (float2*)(b + L.o_tfarp);
+  t.farL = (float2*)(b + L.o_tfarL);
+  t.ctr = (unsigned int*)(b + L.o_tctr);
+  t.L = L.tL;
+  t.key_lv = L.sd[0].key_lv;
+  t.P = L.tP;
+  t.cmin = (L.tP + 1) * (L.tP + 1) / 2;
+  t.theta = (float)far_theta;
+  const double a = spec[0].a;
+  t.rfar2 = (float)((kFarImageRel * a) * (kFarImageRel * a));
+  t.inv_a = (float)(1.0 / a);
+  return t;
+}
+
+// The tree's build (after the records) and its evaluation, on stream st; the evaluation's
+// device time is taken with ev_tree0 / ev_tree1.
+void Engine::issue_tree(cudaStream_t st)
+{
+  const TreeView tv = tree_view();
+  const int n = L.sd[0].n;
+  launch_tree_build(tv, n, st);
+  cudaEventRecordWithFlags(ev_tree0, st, cudaEventRecordExternal);
+  launch_tree_eval(tv, n, part_d, st);
+  cudaEventRecordWithFlags(ev_tree1, st, cudaEventRecordExternal);
+  tree_timed = true;
+}
+
+int Engine::last_tree_time(float* ms)
+{
+  if (!tree_timed) return fail(HSMA_E_STATE, "no far-field tree evaluation has run");
+  CK(cudaStreamSynchronize(stream));
+  CK(cudaEventElapsedTime(ms, ev_tree0, ev_tree1));
+  return HSMA_OK;
+}
+
 void Engine::issue_moments()
 {
   if (prec == HSMA_FP64) {
@@ -811,6 +887,7 @@ int Engine::build_launch_count() const
 void Engine::issue_pot()
 {
   const int nsys = (int)L.sd.size();
+  if (L.tree) issue_tree(stream);
   cudaMemsetAsync(ctr_pairs_d, 0, sizeof(unsigned int), stream);
   if (!L.it4.empty()) {
     cudaEventRecordWithFlags(ev_pair0, stream, cudaEventRecordExternal);
@@ -828,7 +905,13 @@ void Engine::issue_pot()
   if (!L.it4.empty()) cudaEventRecordWithFlags(ev_pot1, stream, cudaEventRecordExternal);
 }
 
-int Engine::pot_launch_count() const { return (L.it4.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1); }
+int Engine::pot_launch_count() const
+{
+  return (L.it4.empty() ? 0 : 1) + (L.it5.empty() ? 0 : 1) + (L.tree ? tree_launch_count() : 0);
+}
+
+// k_tree_marks, k_tree_leaf, k_tree_up per level below L, k_tree_far, k_tree_eval
+int Engine::tree_launch_count() const { return 4 + (L.tL - kTreeTop); }
 
 void Engine::launch_pair_items(PairWork w1, PairWork w2, int grid, cudaStream_t st, bool pdl)
 {
@@ -896,6 +979,10 @@ void Engine::issue_fused()
     // while the records are written, and its CTAs start as soon as they are done
     launch_pair_items(rk, none, grid_rk, side, true);
     cudaEventRecord(ev_join, side);
+  } else if (L.tree) {
+    // the far-field tree (build and evaluation) beside the coefficient chain
+    issue_tree(side);
+    cudaEventRecord(ev_join, side);
   }
   PriorityScope ps(prio_mid);
   issue_moments();
@@ -908,7 +995,7 @@ void Engine::issue_fused()
                  L.surf_pw, coef_d, coef2_d, sb_d, tables(), surfa_d, surfb_d, surf64a_d, surf64b_d, surfx_d,
                  surfqd_d, prec, stream);
   launch_pair_items(srf, rk, grid_s, stream, true);
-  if (side_rk) cudaStreamWaitEvent(stream, ev_join, 0);
+  if (side_rk || L.tree) cudaStreamWaitEvent(stream, ev_join, 0);
   launch_reduce(sys_d, sel_d, selrng_d, nsys, it5_d, (int)L.it5.size(), part_d, part64_d, prec, q_d, perm_d, r0_d,
                 phic_d, phir_d, phit_d, epart_d, nullptr, ctr_red_d, status_d, outdesc_d, stream, true);
 }
@@ -935,7 +1022,7 @@ int Engine::fused_launch_count() const
 {
   if (L.itord.empty()) return build_launch_count() + pot_launch_count();
   return build_launch_count() + (rk_side != 0 && L.nRK > 0 ? 1 : 0) + (L.it4x.empty() ? 0 : 1) +
-         (L.it5.empty() ? 0 : 1);
+         (L.it5.empty() ? 0 : 1) + (L.tree ? tree_launch_count() : 0);
 }
 
 int Engine::run_graph(cudaGraphExec_t* g, void (Engine::*issue)())
@@ -1279,6 +1366,7 @@ void Engine::issue_field_fused()
 
 int Engine::field()
 {
+  if (L.tree && have_layout) return fail(HSMA_E_STATE, "fields are not available with the far-field tree");
   if (!sources_ready) return fail(HSMA_E_STATE, "sources have not been built");
   if (pot_ready && field_ready) return HSMA_OK;
   CK(cudaSetDevice(device));
@@ -1736,6 +1824,31 @@ int hsma_last_pair_time(hsma_t* h, float* ms)
   return from_engine(h, h->e->last_pair_time(ms));
 }
 
+int hsma_set_far_field(hsma_t* h, double theta, int order)
+{
+  if (!h) return HSMA_E_INVALID_ARG;
+  if (!(theta == 0.0 || (theta > 0.0 && theta < 1.0)))
+    return set_err(h, HSMA_E_INVALID_ARG, "theta must be 0 (direct sum) or in (0, 1)");
+  if (theta > 0.0 && !hsma::tree_order_supported(order))
+    return set_err(h, HSMA_E_INVALID_ARG, "far-field order must be 8, 12 or 16");
+  if (theta > 0.0 && h->e->prec != HSMA_FP32)
+    return set_err(h, HSMA_E_INVALID_ARG, "the far-field tree needs the FP32 path");
+  h->e->far_theta = theta;
+  if (theta > 0.0) h->e->far_order = order;
+  // a new layout and a new build pass at the next call
+  h->e->layout_uploaded = false;
+  h->e->sources_ready = false;
+  h->e->build_pending = false;
+  h->n = -1;
+  return HSMA_OK;
+}
+
+int hsma_last_far_time(hsma_t* h, float* ms)
+{
+  if (!h || !ms) return HSMA_E_INVALID_ARG;
+  return from_engine(h, h->e->last_tree_time(ms));
+}
+
 }  // extern "C"
 
 namespace hsma {
@@ -1833,6 +1946,7 @@ int Engine::move_batch(const std::vector<DeltaReq>& reqs)
 
 int Engine::delta_energy(int64_t k, const double* x_new, double* de)
 {
+  if (L.tree && have_layout) return fail(HSMA_E_STATE, "single-move energies are not available with the far-field tree");
   if (!x_new || !de) return fail(HSMA_E_INVALID_ARG, "NULL argument");
   if (L.sd.empty()) return fail(HSMA_E_STATE, "sources have not been built");
   DeltaReq r;
@@ -1846,6 +1960,7 @@ int Engine::delta_energy(int64_t k, const double* x_new, double* de)
 
 int Engine::apply_move(int64_t k, const double* x_new)
 {
+  if (L.tree && have_layout) return fail(HSMA_E_STATE, "moves are not available with the far-field tree");
   if (!x_new) return fail(HSMA_E_INVALID_ARG, "NULL argument");
   if (L.sd.empty()) return fail(HSMA_E_STATE, "sources have not been built");
   DeltaReq r;

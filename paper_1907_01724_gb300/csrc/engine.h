@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "hsma_internal.cuh"
+#include "tree.h"
 
 namespace hsma {
 
@@ -65,6 +66,11 @@ struct Layout {
   size_t o_mom = 0, o_coef = 0, o_r0 = 0, o_phic = 0, o_phir = 0, o_phit = 0, o_epart = 0, o_energy = 0, o_ctr = 0, o_outdesc = 0, o_indesc = 0;
   size_t o_it3m = 0;
   size_t o_it12 = 0, o_it2r = 0, o_it3 = 0, o_it5 = 0, o_it4 = 0, o_it4x = 0, o_it4f = 0, o_it4fx = 0;
+  // far-field tree (one FP32 system, Engine::far_theta > 0): node levels, order, and its arrays;
+  // the pair kernel then takes only the surface items and chunks 0 / 1 are the tree's sums
+  bool tree = false;
+  int tL = 0, tP = 0;
+  size_t o_tnode = 0, o_tgeo = 0, o_tbox = 0, o_tmom = 0, o_tfarp = 0, o_tfarL = 0, o_tctr = 0;
   size_t bytes = 0;
 };
 
@@ -114,6 +120,14 @@ class Engine {
   // their own beside the moment chain, 0 = with the surface items after it (issue_fused);
   // forced_side >= 0 forces it, otherwise the tuned choice of the size class or a default
   int forced_side = -1;
+  // far field of the real/Kelvin pair sums by the treecode of k_tree.cu (single FP32 system):
+  // far_theta = 0 keeps the direct sum; takes effect at the next layout
+  double far_theta = 0.0;
+  int far_order = 12;
+  TreeView tree_view() const;
+  cudaEvent_t ev_tree0 = nullptr, ev_tree1 = nullptr;  // around the tree evaluation
+  bool tree_timed = false;
+  int last_tree_time(float* ms);
   int rk_side = 1;  // the current layout's choice (0, 1 or 2, see issue_fused)
   struct Tuned {
     int bucket, cfg, side;
@@ -262,6 +276,8 @@ class Engine {
   void launch_field_reduce(cudaStream_t st);
   void issue_field_fused();
   int fused_launch_count() const;
+  void issue_tree(cudaStream_t st);
+  int tree_launch_count() const;
   int build_launch_count() const;
   int pot_launch_count() const;
   int run_graph(cudaGraphExec_t* g, void (Engine::*issue)());

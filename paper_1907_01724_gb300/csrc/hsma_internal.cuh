@@ -106,6 +106,8 @@ struct SysDev {
   int prec;           // HSMA_FP32 / HSMA_FP64
   int sort_parts;     // blocks of k_order_sort for this system (a power of two; each sorts the
                       // charges of kOrderCells / sort_parts consecutive cells)
+  int key_lv;         // levels of the order key: Morton index on a 2^key_lv grid (>= kOrderLevels;
+                      // finer than the 16^3 cells only for the far-field tree)
   long long chg;      // offset of this system's charges (xyz at 3*chg, q at chg, phi at chg)
   long long src;      // offset of its 2n real+Kelvin source records (real first)
   long long surf;     // offset of its M surface records
@@ -150,7 +152,8 @@ struct InDesc {
 };
 
 // Spatial order (k_order.cu): charges sorted by the Morton index of their cell on a 16^3 grid
-// over [-a, a]^3 (input index inside a cell).  perm[chg + i] = input index of sorted position
+// over [-a, a]^3 and, inside a cell, by their key (the Morton index on the finer 2^key_lv grid, the
+// same as the cell's when key_lv = kOrderLevels) and their input index.  perm[chg + i] = input index of sorted position
 // i (its inverse iperm is written by k_images).  Pair-sum records, pair partials and move work use sorted positions.
 // launch_order writes the cell keys and the cell histogram (items = (system, block of
 // kOrderBlock charges)), then sorts each system in sort_parts blocks (sitems = (system, part)),
@@ -158,7 +161,8 @@ struct InDesc {
 // ctr_reset.  hist (kOrderCells ints per system, then one counter per system) must be zero on
 // entry and is zero again on exit; scr is scratch of 2 ints per charge (used by a block whose
 // cells hold more charges than its shared memory).
-constexpr int kOrderGrid = 16;
+constexpr int kOrderLevels = 4;
+constexpr int kOrderGrid = 1 << kOrderLevels;
 constexpr int kOrderCells = kOrderGrid * kOrderGrid * kOrderGrid;
 constexpr int kOrderBlock = 256;  // charges per k_order_keys / k_images work item
 void init_order_kernels();  // one-time function attributes (call outside stream capture)

@@ -1,8 +1,9 @@
 // Spatial order of the charges of every system, for the near/far split of the pair sum.
 //
 // Charges are sorted by the Morton index of their cell on a 16^3 grid over [-a, a]^3, and
-// inside a cell by their input index, so the order (hence every summation order downstream)
-// is deterministic.  Consecutive charges in this order are close in space: a warp's targets
+// inside a cell by their key (the Morton index on a 2^key_lv grid: the cell's own index unless
+// the far-field tree asks for a finer order) and then their input index, so the order (hence
+// every summation order downstream) is deterministic.  Consecutive charges in this order are close in space: a warp's targets
 // and a 32-source sub-tile each occupy a small box, and the pair kernel evaluates the pairs of
 // well-separated boxes with plain FP32 coordinates, keeping the hi/lo-split form for near ones.
 //   k_order_keys   cell key per charge and the cell histogram of its system (global integer
@@ -28,20 +29,24 @@ namespace hsma {
 
 __device__ __forceinline__ unsigned int spread3(unsigned int v)
 {
-  // interleave the 4 low bits of v with two zero bits each
-  v &= 0xFu;
-  v = (v | (v << 4)) & 0x0C3u;
-  v = (v | (v << 2)) & 0x249u;
+  // interleave the 10 low bits of v with two zero bits each
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
   return v;
 }
 
+// Morton index of the charge's cell on the 2^key_lv grid over [-a, a]^3
 __device__ __forceinline__ int cell_key(const SysDev& S, double x, double y, double z)
 {
-  const double s = 0.5 * kOrderGrid * S.inv_a;
+  const int G = 1 << S.key_lv;
+  const double s = 0.5 * G * S.inv_a;
   int ix = (int)floor((x + S.a) * s), iy = (int)floor((y + S.a) * s), iz = (int)floor((z + S.a) * s);
-  ix = min(max(ix, 0), kOrderGrid - 1);
-  iy = min(max(iy, 0), kOrderGrid - 1);
-  iz = min(max(iz, 0), kOrderGrid - 1);
+  ix = min(max(ix, 0), G - 1);
+  iy = min(max(iy, 0), G - 1);
+  iz = min(max(iz, 0), G - 1);
   return (int)(spread3((unsigned)ix) | (spread3((unsigned)iy) << 1) | (spread3((unsigned)iz) << 2));
 }
 
@@ -71,7 +76,7 @@ __global__ __launch_bounds__(kKeyThreads) void k_order_keys(const SysDev* __rest
   }
   const int k = cell_key(S, x, y, z);
   key[g] = k;
-  atomicAdd(&hist[(size_t)it.x * kOrderCells + k], 1);
+  atomicAdd(&hist[(size_t)it.x * kOrderCells + (k >> (3 * (S.key_lv - kOrderLevels)))], 1);
   const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
   if (!(r2 < S.a * S.a) || !isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qg)) atomicOr(status, kStOutside);
   if (xs) {
@@ -106,6 +111,7 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
   const int2 it = items[blockIdx.x];
   const SysDev& S = sys[it.x];
   const int n = S.n, parts = S.sort_parts;
+  const int ksh = 3 * (S.key_lv - kOrderLevels);  // key -> cell
   const long long c0 = S.chg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // k_images, a programmatic dependent of this kernel, is dispatched right away and waits for
@@ -177,8 +183,9 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
     }
 #pragma unroll
     for (int j = 0; j < kSortBatch; ++j) {
-      if (kk[j] >= k0 && kk[j] < k1) {
-        const int p = atomicAdd(&s_cell[kk[j]], 1) - P0;
+      const int cell = kk[j] >> ksh;  // (-1 stays -1)
+      if (cell >= k0 && cell < k1) {
+        const int p = atomicAdd(&s_cell[cell], 1) - P0;
         slot[p] = i0 + j * kSortThreads + tid;
         skey[p] = kk[j];
       }
@@ -187,12 +194,20 @@ __global__ __launch_bounds__(kSortThreads) void k_order_sort(const SysDev* __res
   __syncthreads();
 
   // slot a of cell k (which spans [end of cell k - 1, end of cell k), the first from P0) goes to
-  // the cell's start plus the number of the cell's input indices below its own
+  // the cell's start plus the number of the cell's charges before it: the input indices below
+  // its own or, with a finer key, the (key, input index) pairs below its own
   for (int a = tid; a < m; a += kSortThreads) {
-    const int v = slot[a], k = skey[a];
+    const int v = slot[a], kf = skey[a], k = kf >> ksh;
     const int b0 = (k > k0 ? s_cell[k - 1] : P0) - P0, e = s_cell[k] - P0;
     int p = b0;
-    for (int b = b0; b < e; ++b) p += slot[b] < v;
+    if (ksh == 0) {
+      for (int b = b0; b < e; ++b) p += slot[b] < v;
+    } else {
+      for (int b = b0; b < e; ++b) {
+        const int kb = skey[b];
+        p += kb < kf || (kb == kf && slot[b] < v);
+      }
+    }
     perm[c0 + P0 + p] = v;
   }
 }
