@@ -191,7 +191,7 @@ HSMA_API int hsma_last_pair_time(hsma_t* h, float* ms);
  * treecode over the spatial order of the charges: an octree of the charges (and, node by node,
  * of their Kelvin images), multipole moments of the given order (8, 12 or 16) per node, and per
  * group of 32 charges a traversal that takes a node through its moments when
- * (node radius + group radius) <= theta * (centre distance) and it holds at least
+ * node radius <= theta * (centre distance - group radius) and it holds at least
  * (order + 1)^2 / 2 charges, else opens it or sums it directly; Kelvin images farther than 3a
  * from the centre enter through one expansion of order 20 about the centre.  The surface images
  * keep their direct sum.  theta = 0 (the default) restores the direct sum.  Takes effect at the

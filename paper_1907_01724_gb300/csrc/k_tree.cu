@@ -17,8 +17,10 @@
 //                 the children's moments to the parent's centre (a warp per node)
 //   k_tree_far    the far images' expansion about the centre (fixed-order block sums, the last
 //                 block adds the blocks in order)
-//   k_tree_eval   a warp per 32 consecutive targets: depth-first traversal of both trees from the
-//                 level-kTreeTop cells; a node far from the group (opening criterion theta) with at
+//   k_tree_eval   persistent warps over items (32 consecutive targets, one tree): depth-first
+//                 traversal of the item's tree from the
+//                 level-kTreeTop cells; a node far from the group (radius <= theta (distance from
+//                 the group's centre - the group's radius)) with at
 //                 least cmin records is evaluated from its moments at each target, a near leaf (or a
 //                 far node too small for its moments to pay) by the direct pair sum with hi/lo
 //                 coordinate differences; then the far-image expansion at each target.  Writes the
@@ -518,7 +520,8 @@ __device__ __forceinline__ float l2p_far(const float2* __restrict__ L, float4 th
   const float r2 = ux * ux + uy * uy + uz * uz;
   float dr = 1.f, di = 0.f;  // R_0^0
   float acc = 0.f;
-#pragma unroll
+  // (once per Kelvin item: rolled loops keep the registers for the traversal)
+#pragma unroll 1
   for (int m = 0; m <= kFarOrder; ++m) {
     if (m > 0) {
       const float f = 0.5f / (float)m;
@@ -530,7 +533,7 @@ __device__ __forceinline__ float l2p_far(const float2* __restrict__ L, float4 th
     float2 ll = __ldg(Lc);
     float col = ll.x * dr - ll.y * di;
     float p0r = 0.f, p0i = 0.f, p1r = dr, p1i = di;
-#pragma unroll
+#pragma unroll 1
     for (int nn = m + 1; nn <= kFarOrder; ++nn) {
       const float A = (float)(2 * nn - 1) * uz;
       const float inv = 1.f / (float)(nn * nn - m * m);
@@ -549,10 +552,13 @@ __device__ __forceinline__ float l2p_far(const float2* __restrict__ L, float4 th
 }
 
 // Direct sum of the records [be.x, be.y) at the lane's target, staged 32 at a time through the
-// warp's shared buffers; the source at sorted position `self` is skipped, and (Kelvin tree)
-// records beyond rfar2 count as zero.
+// warp's shared buffers, with the exact (hi, lo) coordinate difference of inv_hilo (accurate to
+// FP32 rounding at any distance, e.g. a charge next to its own Kelvin image).  checked: the node
+// holds some of the group's own targets, and the source at sorted position `self` is skipped;
+// kelvin: records beyond rfar2 count as zero.
 __device__ __forceinline__ float p2p(const float4* __restrict__ H, const float4* __restrict__ Lo, int2 be, float4 th,
-                                     float4 tl, int self, bool kelvin, float rfar2, float4* sh, float4* sl)
+                                     float4 tl, int self, bool checked, bool kelvin, float rfar2, float4* sh,
+                                     float4* sl)
 {
   const int lane = threadIdx.x & 31;
   float acc = 0.f;
@@ -567,27 +573,34 @@ __device__ __forceinline__ float p2p(const float4* __restrict__ H, const float4*
     }
     __syncwarp();
     const int m = min(32, be.y - j0);
-    for (int k = 0; k < m; ++k) {
-      const float4 s = sh[k], u = sl[k];
-      const float inv = inv_hilo(th.x, th.y, th.z, tl.x, tl.y, tl.z, s.x, s.y, s.z, u.x, u.y, u.z);
-      const float v = s.w * inv;
-      acc += (j0 + k == self) ? 0.f : v;
+    if (!checked) {
+#pragma unroll 4
+      for (int k = 0; k < m; ++k) {
+        const float4 s = sh[k], u = sl[k];
+        acc = fmaf(s.w, inv_hilo(th.x, th.y, th.z, tl.x, tl.y, tl.z, s.x, s.y, s.z, u.x, u.y, u.z), acc);
+      }
+    } else {
+      for (int k = 0; k < m; ++k) {
+        const float4 s = sh[k], u = sl[k];
+        const float v = s.w * inv_hilo(th.x, th.y, th.z, tl.x, tl.y, tl.z, s.x, s.y, s.z, u.x, u.y, u.z);
+        acc += (j0 + k == self) ? 0.f : v;
+      }
     }
   }
   return acc;
 }
 
+// One work item: a group of 32 consecutive targets (sorted positions 32 grp ..) against one tree
+// (tr = 0: real charges, 1: Kelvin images and the far-image expansion); traversal and evaluation,
+// written to the item's own partial row (chunk tr).
 template <int P>
-__global__ __launch_bounds__(32 * kTreeEvalWarps) void k_tree_eval(TreeView t, float2* __restrict__ part)
+__device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict__ part, int grp, int tr, int* stk,
+                                           float4* sh, float4* sl)
 {
   constexpr int NM = tree_nm(P);
-  __shared__ int s_stack[kTreeEvalWarps][kTreeStack];
-  __shared__ float4 s_h[kTreeEvalWarps][32], s_l[kTreeEvalWarps][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const SysDev& S = t.sys[0];
   const int n = S.n;
-  const int grp = blockIdx.x * kTreeEvalWarps + w;
-  if (grp * 32 >= n) return;  // whole warps
   const int i = grp * 32 + lane;
   const bool on = i < n;
   const int ic = on ? i : n - 1;
@@ -602,10 +615,9 @@ __global__ __launch_bounds__(32 * kTreeEvalWarps) void k_tree_eval(TreeView t, f
     rg = sqrtf(warp_max(dx * dx + dy * dy + dz * dz)) * 1.000001f + 2e-7f * a;
   }
   const long long nodes = tree_node_count(t.L);
-  df acc[2] = {df_make(0.f, 0.f), df_make(0.f, 0.f)};
-  int* stk = s_stack[w];
+  df acc = df_make(0.f, 0.f);
   constexpr int R = 1 << (3 * kTreeTop);
-  for (int tr = 0; tr < 2; ++tr) {
+  {
     const float4* __restrict__ H = t.hi + S.src + (long long)tr * n;
     const float4* __restrict__ Lo = t.lo + S.src + (long long)tr * n;
     const float4* __restrict__ G = t.geo + (long long)tr * nodes;
@@ -625,12 +637,15 @@ __global__ __launch_bounds__(32 * kTreeEvalWarps) void k_tree_eval(TreeView t, f
       const float4 gc = G[g];
       if (gc.w < 0.f) continue;
       const float dx = gc.x - ox, dy = gc.y - oy, dz = gc.z - oz;
-      const bool far = gc.w + rg <= t.theta * sqrtf(dx * dx + dy * dy + dz * dz);
+      // every target of the group is at least d - rg from the centre: the series of the node's
+      // moments converges there with ratio at most theta
+      const bool far = gc.w <= t.theta * (sqrtf(dx * dx + dy * dy + dz * dz) - rg);
       float v;
       if (far && be.y - be.x >= t.cmin) {
         v = m2p<P>(MM + g * NM, gc, th, tl);
       } else if (far || l == t.L) {
-        v = p2p(H, Lo, be, th, tl, self, tr == 1, t.rfar2, s_h[w], s_l[w]);
+        const bool checked = tr == 0 && be.x < grp * 32 + 32 && be.y > grp * 32;
+        v = p2p(H, Lo, be, th, tl, self, checked, tr == 1, t.rfar2, sh, sl);
       } else {
         // open: the non-empty children, the lowest cell on top
         const long long gch = tree_node_index(l + 1, 8LL * c);
@@ -642,13 +657,31 @@ __global__ __launch_bounds__(32 * kTreeEvalWarps) void k_tree_eval(TreeView t, f
         __syncwarp();
         continue;
       }
-      acc[tr] = acc[tr] + two_sum(v, 0.f);
+      acc = acc + two_sum(v, 0.f);
     }
   }
-  acc[1] = acc[1] + two_sum(l2p_far(t.farL, th, tl, t.inv_a), 0.f);
-  if (on) {
-    part[S.part + i] = make_float2(acc[0].hi, acc[0].lo);
-    part[S.part + n + i] = make_float2(acc[1].hi, acc[1].lo);
+  if (tr == 1) acc = acc + two_sum(l2p_far(t.farL, th, tl, t.inv_a), 0.f);
+  if (on) part[S.part + (long long)tr * n + i] = make_float2(acc.hi, acc.lo);
+}
+
+template <int P>
+__global__ __launch_bounds__(32 * kTreeEvalWarps, kTreeEvalMinBlocks) void k_tree_eval(TreeView t,
+                                                                                       float2* __restrict__ part)
+{
+  constexpr int NM = tree_nm(P);
+  __shared__ int s_stack[kTreeEvalWarps][kTreeStack];
+  __shared__ float4 s_h[kTreeEvalWarps][32], s_l[kTreeEvalWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const SysDev& S = t.sys[0];
+  const int n = S.n;
+  const int items = 2 * ((n + 31) / 32), workers = gridDim.x * kTreeEvalWarps;
+  // persistent warps: the first item by the warp's index, then items from the work counter (the
+  // cost of an item varies with its distance from the interface and from the centre)
+  for (int it = blockIdx.x * kTreeEvalWarps + w; it < items;) {
+    eval_group<P>(t, part, it >> 1, it & 1, s_stack[w], s_h[w], s_l[w]);
+    int nx = 0;
+    if (lane == 0) nx = workers + (int)atomicAdd(t.ctr + 1, 1u);
+    it = __shfl_sync(0xffffffffu, nx, 0);
   }
 }
 
@@ -676,7 +709,7 @@ static void build_p(const TreeView& t, int n, cudaStream_t st)
 void launch_tree_build(const TreeView& t, int n, cudaStream_t st)
 {
   cudaMemsetAsync(t.node, 0, sizeof(int2) * (size_t)tree_node_count(t.L), st);
-  cudaMemsetAsync(t.ctr, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(t.ctr, 0, 2 * sizeof(unsigned int), st);  // k_tree_far's and k_tree_eval's counters
   if (n <= 0) return;
   k_tree_marks<<<(n + 255) / 256, 256, 0, st>>>(t);
   if (t.P == 8) build_p<8>(t, n, st);
@@ -688,8 +721,16 @@ void launch_tree_build(const TreeView& t, int n, cudaStream_t st)
 void launch_tree_eval(const TreeView& t, int n, float2* part, cudaStream_t st)
 {
   if (n <= 0) return;
-  const int groups = (n + 31) / 32;
-  const unsigned blocks = (unsigned)((groups + kTreeEvalWarps - 1) / kTreeEvalWarps);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int items = 2 * ((n + 31) / 32);
+  const unsigned blocks = (unsigned)std::min<long long>((items + kTreeEvalWarps - 1) / kTreeEvalWarps,
+                                                        (long long)sms * kTreeEvalMinBlocks);
   if (t.P == 8) k_tree_eval<8><<<blocks, 32 * kTreeEvalWarps, 0, st>>>(t, part);
   else if (t.P == 12) k_tree_eval<12><<<blocks, 32 * kTreeEvalWarps, 0, st>>>(t, part);
   else k_tree_eval<16><<<blocks, 32 * kTreeEvalWarps, 0, st>>>(t, part);

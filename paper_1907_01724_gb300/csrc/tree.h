@@ -16,9 +16,10 @@ namespace hsma {
 // 2^key_lv per axis).  Dense per-level arrays: node (l, c) sits at tree_node_index(l, c).
 constexpr int kTreeTop = 2;       // traversal roots: the 64 cells of level 2
 constexpr int kTreeMaxLevel = 7;  // finest node level supported
-constexpr int kFarOrder = 20;     // order of the origin-centred expansion of the far images
-constexpr float kFarImageRel = 3.0f;  // Kelvin images beyond this multiple of a: far images
-constexpr int kTreeEvalWarps = 4;     // warps (target groups) per k_tree_eval block
+constexpr int kFarOrder = 24;     // order of the origin-centred expansion of the far images
+constexpr float kFarImageRel = 2.0f;  // Kelvin images beyond this multiple of a: far images
+constexpr int kTreeEvalWarps = 4;     // warps (persistent target-group workers) per k_tree_eval block
+constexpr int kTreeEvalMinBlocks = 8; // resident k_tree_eval blocks per SM the kernel is built for
 constexpr int kTreeStack = 128;       // traversal stack entries per warp
 constexpr int kFarBlocks = 64;        // blocks of k_tree_far
 
@@ -40,13 +41,13 @@ struct TreeView {
   float2* mom;               // [2][nodes][nm]: multipole moments about the centre, in units of the radius
   float2* farp;              // [kFarBlocks][tree_nm(kFarOrder)]: block partials of the far-image expansion
   float2* farL;              // [tree_nm(kFarOrder)]: the far-image expansion
-  unsigned int* ctr;         // completion counter of k_tree_far
+  unsigned int* ctr;         // [0]: completion counter of k_tree_far, [1]: k_tree_eval's work counter
   int L;                     // finest node level
   int key_lv;                // levels of the record order's key (>= L)
   int P;                     // multipole order
   int cmin;                  // smallest node that is evaluated through its moments
   float theta;               // opening criterion: a node is far from a target group when
-                             // (radius of node + radius of group) <= theta * (centre distance)
+                             // radius of node <= theta * (centre distance - radius of group)
   float rfar2;               // (kFarImageRel a)^2
   float inv_a;
 };
