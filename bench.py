@@ -366,6 +366,57 @@ def run_near_interface(local, stream, gpu_name, steps):
             "l2": "flushed before every timed step (256 MB write)"}
 
 
+def run_far_field(local, stream, steps: int = 5, theta: float = 0.5, order: int = 12):
+    """The paper's N = 1e6 timing workload (Sec. 4.2: p = 20, F1/F2 = 987/1597) with the
+    treecode far field (hsma_set_far_field) against the direct pair sum on the same GPU: whole
+    build + potential steps from device inputs (L2 flushed before each, CUDA events), the tree's
+    evaluation kernel alone, and the norm-wise difference of the two FP32 results."""
+    import torch
+
+    from paper_1907_01724_gb300 import api, inputs
+    s = inputs.far_field_system()
+    dev = torch.device(f"cuda:{local}")
+    xyz_d = torch.tensor(s.xyz, device=dev)
+    q_d = torch.tensor(s.q, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    units = pairs(s)
+    res = {"workload": f"1 cavity N={s.n} uniform in a=1, eps1=2, eps2=80, kappa*a=5, p=20, F1/F2=987/1597 "
+                       f"(M={s.M}), tau=0.1 (the paper's N = 1e6 timing workload, Sec. 4.2)",
+           "pairs_per_step": units}
+    phis = {}
+    for label, th in (("tree", theta), ("direct", 0.0)):
+        prm = api.hsma_default_params(p=s.p, M=s.M, tau=s.tau, precision=api.HSMA_FP32, device=local,
+                                      stream=stream.cuda_stream)
+        h = api.hsma_create(s.a, s.eps1, s.eps2, s.kappa, prm)
+        if th > 0:
+            api.hsma_set_far_field(h, th, order)
+        phi_d = torch.empty(s.n, dtype=torch.float64, device=dev)
+
+        def step():
+            api.hsma_build_sources(h, xyz_d, q_d)
+            api.hsma_potential(h, api.HSMA_TOTAL, out=phi_d)
+
+        k = steps if th > 0 else max(2, steps // 2)
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        t = timed_steps(step, stream, flush, k)
+        entry = {"ms_per_step": t / k * 1e3, "steps": k, "pair_evals_per_s": units * k / t}
+        if th > 0:
+            entry.update({"theta": th, "order": order, "eval_kernel_ms": api.hsma_last_far_time(h),
+                          "kernel": "k_tree_eval"})
+        phis[label] = phi_d.cpu().numpy()
+        res[label] = entry
+        api.hsma_destroy(h)
+        del phi_d
+        torch.cuda.empty_cache()
+    d = phis["tree"] - phis["direct"]
+    res["speedup_vs_direct"] = res["direct"]["ms_per_step"] / res["tree"]["ms_per_step"]
+    res["tree_vs_direct_rel_l2"] = float((d @ d) ** 0.5 / (phis["direct"] @ phis["direct"]) ** 0.5)
+    res["paper_context"] = "HSMA + FMM, N = 1e6: 24 s on 32 cores of 4x Opteron 6272 (Sec. 4.2); not the target"
+    return res
+
+
 def run_batched(local, stream, gpu_name):
     """512 independent cavities (N log-uniform in [100, 1e4]) in one batch: build + potentials +
     energies per launch pair; requests = systems evaluated.  Compared with the plain FP64
@@ -657,12 +708,13 @@ def run_ours(args):
 
     e2e = e2e_run(b, n, xyz, q, units, world, max(10, args.steps))
 
-    near = batched = serving = fieldres = None
+    near = batched = serving = fieldres = far = None
     if rank == 0 and world == 1 and not args.no_extras:
         near = run_near_interface(local, stream, gpu_name, args.steps)
         fieldres = run_field(local, stream, near_interface_workload(0), gpu_name)
         batched = run_batched(local, stream, gpu_name)
         serving = run_serving(local)
+        far = run_far_field(local, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
@@ -672,6 +724,7 @@ def run_ours(args):
                 "config": config_dict(systems, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches), "accuracy_vs_oracle": acc, "fp64_path": fp64,
                 "near_interface": near, "field": fieldres, "batched": batched, "serving": serving,
+                "far_field": far,
                 "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -733,7 +786,8 @@ def main():
                     help="with --only steps / near_steps and --pair-config: the real/Kelvin pair schedule "
                          "(1 beside the coefficient chain, 2 the same leaving room for a coefficient or "
                          "surface CTA per SM, 0 after it; -1 the library's default)")
-    ap.add_argument("--only", choices=["batched", "serving", "field", "near", "pairs", "steps", "near_steps"],
+    ap.add_argument("--only", choices=["batched", "serving", "field", "near", "pairs", "steps", "near_steps",
+                                       "far"],
                     help="run one section alone (profiling); 'pairs': the headline workload's pair kernel "
                          "in separate passes (--steps launches); 'steps' / 'near_steps': --warmup + --steps "
                          "whole-path steps of the headline / near-interface workload and nothing else")
@@ -751,6 +805,8 @@ def main():
             out = run_field(0, st, near_interface_workload(0), name)
         elif args.only == "near":
             out = run_near_interface(0, st, name, args.steps)
+        elif args.only == "far":
+            out = run_far_field(0, st, steps=args.steps)
         elif args.only == "pairs":
             out = run_pairs_only(0, st, name, args.steps, args.warmup, args.pair_config)
         elif args.only in ("steps", "near_steps"):

@@ -473,8 +473,9 @@ __global__ __launch_bounds__(32 * kFarWarps) void k_tree_far(TreeView t)
 
 // ---------------------------------------------------------------------------------------
 // Evaluation.
-// phi at target (th, tl) of a node's moments M (centre and radius gc).
-template <int P>
+// phi at target (th, tl) of a node's moments M (stored to order P; centre and radius gc), the
+// series truncated at order Q <= P.
+template <int P, int Q>
 __device__ __forceinline__ float m2p(const float2* __restrict__ M, float4 gc, float4 th, float4 tl)
 {
   const float ir = 1.f / gc.w;
@@ -485,7 +486,7 @@ __device__ __forceinline__ float m2p(const float2* __restrict__ M, float4 gc, fl
   float dr = rsqrt_mufu(r2), di = 0.f;  // I_0^0
   float acc = 0.f;
 #pragma unroll
-  for (int m = 0; m <= P; ++m) {
+  for (int m = 0; m <= Q; ++m) {
     if (m > 0) {
       const float f = (float)(2 * m - 1);
       const float nr = f * (dr * px - di * py);
@@ -497,7 +498,7 @@ __device__ __forceinline__ float m2p(const float2* __restrict__ M, float4 gc, fl
     float col = mm.x * dr - mm.y * di;
     float p0r = 0.f, p0i = 0.f, p1r = dr, p1i = di;
 #pragma unroll
-    for (int nn = m + 1; nn <= P; ++nn) {
+    for (int nn = m + 1; nn <= Q; ++nn) {
       const float A = (float)(2 * nn - 1) * wz, B = (float)((nn - 1) * (nn - 1) - m * m) * i2;
       const float qr = A * p1r - B * p0r, qi = A * p1i - B * p0i;
       mm = __ldg(Mc + (nn - m));
@@ -638,11 +639,11 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
       if (gc.w < 0.f) continue;
       const float dx = gc.x - ox, dy = gc.y - oy, dz = gc.z - oz;
       // every target of the group is at least d - rg from the centre: the series of the node's
-      // moments converges there with ratio at most theta
+      // moments converges there with ratio rho/(d - rg), at most theta
       const bool far = gc.w <= t.theta * (sqrtf(dx * dx + dy * dy + dz * dz) - rg);
       float v;
       if (far && be.y - be.x >= t.cmin) {
-        v = m2p<P>(MM + g * NM, gc, th, tl);
+        v = m2p<P, P>(MM + g * NM, gc, th, tl);
       } else if (far || l == t.L) {
         const bool checked = tr == 0 && be.x < grp * 32 + 32 && be.y > grp * 32;
         v = p2p(H, Lo, be, th, tl, self, checked, tr == 1, t.rfar2, sh, sl);

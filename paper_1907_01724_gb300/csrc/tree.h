@@ -21,7 +21,7 @@ constexpr float kFarImageRel = 2.0f;  // Kelvin images beyond this multiple of a
 constexpr int kTreeEvalWarps = 4;     // warps (persistent target-group workers) per k_tree_eval block
 constexpr int kTreeEvalMinBlocks = 8; // resident k_tree_eval blocks per SM the kernel is built for
 constexpr int kTreeStack = 128;       // traversal stack entries per warp
-constexpr int kFarBlocks = 64;        // blocks of k_tree_far
+constexpr int kFarBlocks = 512;       // blocks of k_tree_far
 
 __host__ __device__ constexpr long long tree_node_index(int l, long long c) { return ((1LL << (3 * l)) - 1) / 7 + c; }
 __host__ __device__ constexpr long long tree_node_count(int L) { return ((1LL << (3 * (L + 1))) - 1) / 7; }

@@ -101,6 +101,16 @@ def primitive_system(n: int = 20000, seed_offset: int = 0) -> System:
                   name=f"N{n}_uniform_eps78.5_78.5_ka3_M2000_p30")
 
 
+def far_field_system(n: int = 1_000_000, seed_offset: int = 0) -> System:
+    """The paper's CPU-time workload (Sec. 4.2): N random charges in the unit sphere, p = 20,
+    tau = 0.1, F1/F2 = 987/1597 (M = 3196 points per shell), with the accuracy study's dielectric
+    data eps1 = 2, eps2 = 80, kappa a = 5 (Sec. 4)."""
+    rng = np.random.default_rng(SEED_BASE + 5 + seed_offset)
+    n = even(n)
+    return System(1.0, 2.0, 80.0, 5.0, 20, 3196, uniform_ball(rng, n, 1.0), neutral_charges(rng, n),
+                  name=f"N{n}_uniform_eps2_80_ka5_M3196_p20")
+
+
 def _loguniform_int(rng, lo: int, hi: int, size: int) -> np.ndarray:
     return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size))).astype(np.int64)
 
