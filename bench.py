@@ -417,6 +417,28 @@ def run_far_field(local, stream, steps: int = 5, theta: float = 0.5, order: int 
     return res
 
 
+def run_tree_only(local, stream, n: int, steps: int, theta: float = 0.5, order: int = 12):
+    """The far-field workload's charges at N = n with the treecode, the build and the potential
+    pass in separate graphs, `steps` passes (for profiling the tree's kernels)."""
+    import torch
+
+    from paper_1907_01724_gb300 import api, inputs
+    s = inputs.far_field_system(n)
+    prm = api.hsma_default_params(p=s.p, M=s.M, tau=s.tau, precision=api.HSMA_FP32, device=local,
+                                  stream=stream.cuda_stream)
+    h = api.hsma_create(s.a, s.eps1, s.eps2, s.kappa, prm)
+    api.hsma_set_far_field(h, theta, order)
+    api.hsma_set_overlap(h, False)
+    ms = []
+    for _ in range(steps):
+        api.hsma_build_sources(h, s.xyz, s.q)
+        api.hsma_potential(h, api.HSMA_TOTAL)
+        ms.append(api.hsma_last_far_time(h))
+    api.hsma_destroy(h)
+    torch.cuda.synchronize()
+    return {"workload": s.name, "theta": theta, "order": order, "passes": steps, "eval_kernel_ms": ms}
+
+
 def run_batched(local, stream, gpu_name):
     """512 independent cavities (N log-uniform in [100, 1e4]) in one batch: build + potentials +
     energies per launch pair; requests = systems evaluated.  Compared with the plain FP64
@@ -787,10 +809,12 @@ def main():
                          "(1 beside the coefficient chain, 2 the same leaving room for a coefficient or "
                          "surface CTA per SM, 0 after it; -1 the library's default)")
     ap.add_argument("--only", choices=["batched", "serving", "field", "near", "pairs", "steps", "near_steps",
-                                       "far"],
+                                       "far", "tree"],
                     help="run one section alone (profiling); 'pairs': the headline workload's pair kernel "
                          "in separate passes (--steps launches); 'steps' / 'near_steps': --warmup + --steps "
                          "whole-path steps of the headline / near-interface workload and nothing else")
+    ap.add_argument("--far-n", type=int, default=1_000_000,
+                    help="with --only tree: charges of the far-field workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.only:
@@ -807,6 +831,8 @@ def main():
             out = run_near_interface(0, st, name, args.steps)
         elif args.only == "far":
             out = run_far_field(0, st, steps=args.steps)
+        elif args.only == "tree":
+            out = run_tree_only(0, st, args.far_n, args.steps)
         elif args.only == "pairs":
             out = run_pairs_only(0, st, name, args.steps, args.warmup, args.pair_config)
         elif args.only in ("steps", "near_steps"):
