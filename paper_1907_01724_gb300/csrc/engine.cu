@@ -290,9 +290,9 @@ Layout Engine::make_layout(const std::vector<int64_t>& ns, int cfg) const
         // target groups and at most kSymChunkMax charges
         const double items_rk = L.tree ? 0.0 : items_s * (2.0 * n) / (2.0 * n + 1.3 * sp.M);
         if (L.tree) {
-          // one chunk each: the tree's real and Kelvin sums (k_tree_eval), no pair items
+          // kTreeRootSplit chunks each: the tree's real and Kelvin sums (k_tree_eval), no pair items
           d.chunk = (int)n;
-          d.ncr = d.nck = 1;
+          d.ncr = d.nck = kTreeRootSplit;
         } else {
           const int64_t nb = std::max<int64_t>(1, (int64_t)std::floor(std::sqrt(std::max(items_rk, 1.0))));
           int64_t chunk = (n + nb - 1) / nb;

@@ -17,15 +17,16 @@
 //                 the children's moments to the parent's centre (a warp per node)
 //   k_tree_far    the far images' expansion about the centre (fixed-order block sums, the last
 //                 block adds the blocks in order)
-//   k_tree_eval   persistent warps over items (32 consecutive targets, one tree): depth-first
-//                 traversal of the item's tree from the
+//   k_tree_eval   persistent warps over items (32 consecutive targets, one tree, a quarter of
+//                 its root cells): depth-first traversal of the item's subtrees from the
 //                 level-kTreeTop cells; a node far from the group (radius <= theta (distance from
 //                 the group's centre - the group's radius)) with at
 //                 least cmin records is evaluated from its moments at each target, a near leaf (or a
 //                 far node too small for its moments to pay) by the direct pair sum with hi/lo
 //                 coordinate differences; then the far-image expansion at each target.  Writes the
-//                 real and the Kelvin sums as the (hi, lo) partials of chunks 0 and 1, which the
-//                 reduction adds as it adds every chunk.
+//                 real and the Kelvin sums as the (hi, lo) partials of chunks 0..kTreeRootSplit-1
+//                 and kTreeRootSplit..2 kTreeRootSplit-1, which the reduction adds as it adds every
+//                 chunk.
 // Every sum runs in a fixed order (no atomics on values), so results do not depend on scheduling.
 //
 // Solid harmonics (unnormalised associated Legendre functions P_n^m without the Condon-Shortley
@@ -591,12 +592,13 @@ __device__ __forceinline__ float p2p(const float4* __restrict__ H, const float4*
   return acc;
 }
 
-// One work item: a group of 32 consecutive targets (sorted positions 32 grp ..) against one tree
-// (tr = 0: real charges, 1: Kelvin images and the far-image expansion); traversal and evaluation,
-// written to the item's own partial row (chunk tr).
+// One work item: a group of 32 consecutive targets (sorted positions 32 grp ..) against the
+// subtrees of one tree below root cells [rs R/kTreeRootSplit, (rs + 1) R/kTreeRootSplit) (tr = 0:
+// real charges, 1: Kelvin images, the far-image expansion with rs = 0); traversal and evaluation,
+// written to the item's own partial row (chunk tr kTreeRootSplit + rs).
 template <int P>
-__device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict__ part, int grp, int tr, int* stk,
-                                           float4* sh, float4* sl)
+__device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict__ part, int grp, int tr, int rs,
+                                           int* stk, float4* sh, float4* sl)
 {
   constexpr int NM = tree_nm(P);
   const int lane = threadIdx.x & 31;
@@ -625,8 +627,9 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
     const float2* __restrict__ MM = t.mom + (long long)tr * nodes * NM;
     const int self = tr == 0 ? i : -1;
     __syncwarp();
-    for (int k = lane; k < R; k += 32) stk[R - 1 - k] = (kTreeTop << 26) | k;  // cell 0 on top
-    int sp = R;
+    constexpr int RS = R / kTreeRootSplit;
+    for (int k = lane; k < RS; k += 32) stk[RS - 1 - k] = (kTreeTop << 26) | (rs * RS + k);  // lowest on top
+    int sp = RS;
     __syncwarp();
     while (sp > 0) {
       const int e = stk[--sp];
@@ -661,8 +664,8 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
       acc = acc + two_sum(v, 0.f);
     }
   }
-  if (tr == 1) acc = acc + two_sum(l2p_far(t.farL, th, tl, t.inv_a), 0.f);
-  if (on) part[S.part + (long long)tr * n + i] = make_float2(acc.hi, acc.lo);
+  if (tr == 1 && rs == 0) acc = acc + two_sum(l2p_far(t.farL, th, tl, t.inv_a), 0.f);
+  if (on) part[S.part + (long long)(tr * kTreeRootSplit + rs) * n + i] = make_float2(acc.hi, acc.lo);
 }
 
 template <int P>
@@ -675,11 +678,13 @@ __global__ __launch_bounds__(32 * kTreeEvalWarps, kTreeEvalMinBlocks) void k_tre
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const SysDev& S = t.sys[0];
   const int n = S.n;
-  const int items = 2 * ((n + 31) / 32), workers = gridDim.x * kTreeEvalWarps;
+  constexpr int IPG = 2 * kTreeRootSplit;  // items per group
+  const int items = IPG * ((n + 31) / 32), workers = gridDim.x * kTreeEvalWarps;
   // persistent warps: the first item by the warp's index, then items from the work counter (the
   // cost of an item varies with its distance from the interface and from the centre)
   for (int it = blockIdx.x * kTreeEvalWarps + w; it < items;) {
-    eval_group<P>(t, part, it >> 1, it & 1, s_stack[w], s_h[w], s_l[w]);
+    const int r = it % IPG;
+    eval_group<P>(t, part, it / IPG, r & 1, r >> 1, s_stack[w], s_h[w], s_l[w]);
     int nx = 0;
     if (lane == 0) nx = workers + (int)atomicAdd(t.ctr + 1, 1u);
     it = __shfl_sync(0xffffffffu, nx, 0);
@@ -729,7 +734,7 @@ void launch_tree_eval(const TreeView& t, int n, float2* part, cudaStream_t st)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  const int items = 2 * ((n + 31) / 32);
+  const int items = 2 * kTreeRootSplit * ((n + 31) / 32);
   const unsigned blocks = (unsigned)std::min<long long>((items + kTreeEvalWarps - 1) / kTreeEvalWarps,
                                                         (long long)sms * kTreeEvalMinBlocks);
   if (t.P == 8) k_tree_eval<8><<<blocks, 32 * kTreeEvalWarps, 0, st>>>(t, part);

@@ -110,7 +110,7 @@ def test_batched_moves_match_single_handles(prec):
         xyz2[ks[r]] = xs[r]
         ref = oracle_of(inputs.System(s.a, s.eps1, s.eps2, s.kappa, s.p, s.M, xyz2, s.q))
         scale = max(abs(ref["E_total"]), 0.5 * np.sum(np.abs(s.q * ref["phi"])))
-        assert abs(et[sys_idx[r]] - ref["E_total"]) <= 4 * TOL[prec] * scale
+        assert abs(et[sys_idx[r]] - ref["E_total"]) <= TOL[prec] * scale
 
 
 def test_two_moves_of_one_system_rejected():
