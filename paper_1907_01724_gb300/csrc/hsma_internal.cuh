@@ -173,7 +173,7 @@ int order_smem_charges(int64_t max_n);
 // Sort blocks for a system of n charges: about one per kSortPartCharges, a power of two up to
 // kSortMaxParts (every block reads all n keys, so a few thousand charges per block).
 constexpr int kSortPartCharges = 2048;
-constexpr int kSortMaxParts = 32;
+constexpr int kSortMaxParts = 128;
 int order_sort_parts(int64_t n);
 // xs (FP32 path, else null): 2 float4 per charge in input order, the (hi, lo) split of
 // (x, y, z, q): xs[2 g] = hi parts, xs[2 g + 1] = lo parts.  status: kStOutside for a charge at

@@ -15,7 +15,7 @@ namespace hsma {
 // prefix c (a contiguous range, because records are in Morton order of a grid at least as fine,
 // 2^key_lv per axis).  Dense per-level arrays: node (l, c) sits at tree_node_index(l, c).
 constexpr int kTreeTop = 2;       // traversal roots: the 64 cells of level 2
-constexpr int kTreeRootSplit = 4; // work items per (group, tree): the roots in this many runs
+constexpr int kTreeRootSplit = 8; // work items per (group, tree): the roots in this many runs
 constexpr int kTreeMaxLevel = 7;  // finest node level supported
 constexpr int kFarOrder = 24;     // order of the origin-centred expansion of the far images
 constexpr float kFarImageRel = 2.0f;  // Kelvin images beyond this multiple of a: far images
