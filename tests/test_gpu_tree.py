@@ -87,6 +87,20 @@ def test_tree_edge_charges():
     check_full(s)
 
 
+def test_tree_clustered_60000():
+    """Three dense clusters (radius 0.04a, 15000 charges each: leaf cells of hundreds of charges,
+    sorted in the scratch buffer) among 15000 uniform charges: every potential and both energies."""
+    rng = np.random.default_rng(inputs.SEED_BASE + 78)
+    parts = [inputs.uniform_ball(rng, 15000, 1.0)]
+    for c in ([0.5, 0.1, -0.2], [-0.3, -0.6, 0.2], [0.0, 0.2, 0.9]):
+        parts.append(np.array(c) + 0.04 * inputs.uniform_ball(rng, 15000, 1.0))
+    xyz = np.concatenate(parts)
+    xyz = xyz[rng.permutation(len(xyz))]
+    s = inputs.System(1.0, 1.0, 80.0, 2.0, 20, 1000, xyz, inputs.neutral_charges(rng, len(xyz)),
+                      name="N60000_clusters")
+    check_full(s)
+
+
 def test_tree_sampled_200000():
     """N = 200000 uniform (four node levels, far images): potentials at 2000 sampled charges
     against the oracle's direct sums at those charges."""
