@@ -243,7 +243,46 @@ def cpu_baselines(systems, quick: bool):
         _, rate1, el1, rounds1, _ = oracle_run(systems, budget_s=0.0, max_rounds=1, nthreads=1)
         cpu["single_thread"] = {"value": rate1, "unit": "pair-evals/s", "cores": 1,
                                 "sample": f"whole workload x{rounds1}, {el1:.1f} s"}
+        cpu["batched_extrapolated"], cpu["serving_extrapolated"] = oracle_extrapolated(th)
     return refs, cpu
+
+
+def oracle_extrapolated(th: int):
+    """The oracle on seeded random subsets of the batched and serving workloads, scaled to the
+    whole workload by pair count (labelled extrapolated): 8 of the 512 cavities; 4 of the 64
+    chains with N <= 8000, with the request mix's mean pairs per request (a full energy is one
+    whole-method evaluation; a move's energy change is two, as the oracle defines it)."""
+    import oracle
+
+    from paper_1907_01724_gb300 import inputs
+    rng = np.random.default_rng(11)
+    bs = inputs.batched_systems()
+    idx = sorted(rng.choice(len(bs), 8, replace=False).tolist())
+    t0 = time.perf_counter()
+    for i in idx:
+        s = bs[i]
+        oracle.hsma(oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau,
+                                       nthreads=th), s.xyz, s.q)
+    tb = time.perf_counter() - t0
+    ps, pa = sum(pairs(bs[i]) for i in idx), sum(pairs(s) for s in bs)
+    batched = {"kind": "oracle, extrapolated by pair count", "cores": th,
+               "sample": f"cavities {idx} of {len(bs)} ({ps:.3g} of {pa:.3g} pairs), {tb:.2f} s",
+               "pair_evals_per_s": ps / tb, "systems_per_s": len(bs) / (tb * pa / ps)}
+    wl = inputs.serving_workload()
+    small = [c for c in range(len(wl.chains)) if wl.chains[c].n <= 8000]
+    cs = sorted(rng.choice(small, 4, replace=False).tolist())
+    t0 = time.perf_counter()
+    for c in cs:
+        s = wl.chains[c]
+        oracle.hsma(oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau,
+                                       nthreads=th), s.xyz, s.q)
+    tsv = time.perf_counter() - t0
+    rate = sum(pairs(wl.chains[c]) for c in cs) / tsv
+    per_req = sum(pairs(s) for s in wl.chains) / len(wl.chains) * (wl.frac_delta * 2 + (1 - wl.frac_delta))
+    serving = {"kind": "oracle, extrapolated by pair count", "cores": th,
+               "sample": f"chains {cs} (N <= 8000) of {len(wl.chains)}, one evaluation each, {tsv:.2f} s",
+               "pair_evals_per_s": rate, "mean_pairs_per_request": per_req, "req_per_s": rate / per_req}
+    return batched, serving
 
 
 def accuracy(systems, refs, phi, et):
@@ -737,6 +776,9 @@ def run_ours(args):
         batched = run_batched(local, stream, gpu_name)
         serving = run_serving(local)
         far = run_far_field(local, stream)
+        if cpu is not None:
+            batched["oracle_extrapolated"] = cpu.get("batched_extrapolated")
+            serving["oracle_extrapolated"] = cpu.get("serving_extrapolated")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
