@@ -486,9 +486,24 @@ __device__ __forceinline__ float m2p(const float2* __restrict__ M, float4 gc, fl
   const float px = ux * i2, py = uy * i2, wz = uz * i2;
   float dr = rsqrt_mufu(r2), di = 0.f;  // I_0^0
   float acc = 0.f;
+  {
+    // m = 0: the column is real (written out: IEEE arithmetic does not let the compiler drop
+    // the zero imaginary parts)
+    float p0 = 0.f, p1 = dr;
+    float col = __ldg(M).x * dr;
 #pragma unroll
-  for (int m = 0; m <= Q; ++m) {
-    if (m > 0) {
+    for (int nn = 1; nn <= Q; ++nn) {
+      const float A = (float)(2 * nn - 1) * wz, B = (float)((nn - 1) * (nn - 1)) * i2;
+      const float q = A * p1 - B * p0;
+      col = fmaf(__ldg(M + nn).x, q, col);
+      p0 = p1;
+      p1 = q;
+    }
+    acc = col;
+  }
+#pragma unroll
+  for (int m = 1; m <= Q; ++m) {
+    {
       const float f = (float)(2 * m - 1);
       const float nr = f * (dr * px - di * py);
       di = f * (dr * py + di * px);
@@ -510,7 +525,7 @@ __device__ __forceinline__ float m2p(const float2* __restrict__ M, float4 gc, fl
       p1r = qr;
       p1i = qi;
     }
-    acc += m == 0 ? col : 2.f * col;
+    acc = fmaf(2.f, col, acc);
   }
   return acc * ir;
 }
@@ -557,14 +572,15 @@ __device__ __forceinline__ float l2p_far(const float2* __restrict__ L, float4 th
 // warp's shared buffers, with the exact (hi, lo) coordinate difference of inv_hilo (accurate to
 // FP32 rounding at any distance, e.g. a charge next to its own Kelvin image).  checked: the node
 // holds some of the group's own targets, and the source at sorted position `self` is skipped;
-// kelvin: records beyond rfar2 count as zero.
-__device__ __forceinline__ float p2p(const float4* __restrict__ H, const float4* __restrict__ Lo, int2 be, float4 th,
-                                     float4 tl, int self, bool checked, bool kelvin, float rfar2, float4* sh,
-                                     float4* sl)
+// kelvin: records beyond rfar2 count as zero.  Each batch's FP32 sum is added to the compensated
+// total (a leaf of a dense cluster holds thousands of sources of similar size and mixed sign).
+__device__ __forceinline__ void p2p(const float4* __restrict__ H, const float4* __restrict__ Lo, int2 be, float4 th,
+                                    float4 tl, int self, bool checked, bool kelvin, float rfar2, float4* sh, float4* sl,
+                                    df& total)
 {
   const int lane = threadIdx.x & 31;
-  float acc = 0.f;
   for (int j0 = be.x; j0 < be.y; j0 += 32) {
+    float acc = 0.f;  // one batch of 32 sources, folded into the compensated total below
     const int j = j0 + lane;
     __syncwarp();  // the previous batch has been read
     if (j < be.y) {
@@ -588,8 +604,8 @@ __device__ __forceinline__ float p2p(const float4* __restrict__ H, const float4*
         acc += (j0 + k == self) ? 0.f : v;
       }
     }
+    total = total + two_sum(acc, 0.f);
   }
-  return acc;
 }
 
 // One work item: a group of 32 consecutive targets (sorted positions 32 grp ..) against the
@@ -644,12 +660,11 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
       // every target of the group is at least d - rg from the centre: the series of the node's
       // moments converges there with ratio rho/(d - rg), at most theta
       const bool far = gc.w <= t.theta * (sqrtf(dx * dx + dy * dy + dz * dz) - rg);
-      float v;
       if (far && be.y - be.x >= t.cmin) {
-        v = m2p<P, P>(MM + g * NM, gc, th, tl);
+        acc = acc + two_sum(m2p<P, P>(MM + g * NM, gc, th, tl), 0.f);
       } else if (far || l == t.L) {
         const bool checked = tr == 0 && be.x < grp * 32 + 32 && be.y > grp * 32;
-        v = p2p(H, Lo, be, th, tl, self, checked, tr == 1, t.rfar2, sh, sl);
+        p2p(H, Lo, be, th, tl, self, checked, tr == 1, t.rfar2, sh, sl, acc);
       } else {
         // open: the non-empty children, the lowest cell on top
         const long long gch = tree_node_index(l + 1, 8LL * c);
@@ -659,9 +674,7 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
         if (lane < 8 && ((ne >> lane) & 1u)) stk[sp + __popc(ne >> (lane + 1))] = ((l + 1) << 26) | (8 * c + lane);
         sp += __popc(ne);
         __syncwarp();
-        continue;
       }
-      acc = acc + two_sum(v, 0.f);
     }
   }
   if (tr == 1 && rs == 0) acc = acc + two_sum(l2p_far(t.farL, th, tl, t.inv_a), 0.f);
