@@ -17,10 +17,10 @@
 //                 the children's moments to the parent's centre (a warp per node)
 //   k_tree_far    the far images' expansion about the centre (fixed-order block sums, the last
 //                 block adds the blocks in order)
-//   k_tree_eval   persistent warps over items (32 consecutive targets, one tree, a quarter of
+//   k_tree_eval   persistent warps over items (32 consecutive targets, one tree, an eighth of
 //                 its root cells): depth-first traversal of the item's subtrees from the
-//                 level-kTreeTop cells; a node far from the group (radius <= theta (distance from
-//                 the group's centre - the group's radius)) with at
+//                 level-kTreeTop cells; a node far from every target of the group (radius <=
+//                 theta (distance of the target from the centre)) with at
 //                 least cmin records is evaluated from its moments at each target, a near leaf (or a
 //                 far node too small for its moments to pay) by the direct pair sum with hi/lo
 //                 coordinate differences; then the far-image expansion at each target.  Writes the
@@ -624,15 +624,7 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
   const bool on = i < n;
   const int ic = on ? i : n - 1;
   const float4 th = t.hi[S.src + ic], tl = t.lo[S.src + ic];
-  // the group's bounding sphere (centre of its box)
-  const float ox = 0.5f * (warp_min(th.x) + warp_max(th.x)), oy = 0.5f * (warp_min(th.y) + warp_max(th.y));
-  const float oz = 0.5f * (warp_min(th.z) + warp_max(th.z));
-  const float a = 1.f / t.inv_a;
-  float rg;
-  {
-    const float dx = th.x - ox, dy = th.y - oy, dz = th.z - oz;
-    rg = sqrtf(warp_max(dx * dx + dy * dy + dz * dz)) * 1.000001f + 2e-7f * a;
-  }
+  const float theta2 = t.theta * t.theta, margin = 4e-7f / t.inv_a;
   const long long nodes = tree_node_count(t.L);
   df acc = df_make(0.f, 0.f);
   constexpr int R = 1 << (3 * kTreeTop);
@@ -656,10 +648,11 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
       if (be.y <= be.x) continue;
       const float4 gc = G[g];
       if (gc.w < 0.f) continue;
-      const float dx = gc.x - ox, dy = gc.y - oy, dz = gc.z - oz;
-      // every target of the group is at least d - rg from the centre: the series of the node's
-      // moments converges there with ratio rho/(d - rg), at most theta
-      const bool far = gc.w <= t.theta * (sqrtf(dx * dx + dy * dy + dz * dz) - rg);
+      // the node is far when its series converges with ratio rho / |t - c| <= theta at every
+      // target of the group (each lane tests its own target; a margin covers the lo parts)
+      const float dx = th.x - gc.x, dy = th.y - gc.y, dz = th.z - gc.z;
+      const float rm = gc.w + margin;
+      const bool far = __all_sync(0xffffffffu, rm * rm <= theta2 * fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
       if (far && be.y - be.x >= t.cmin) {
         acc = acc + two_sum(m2p<P, P>(MM + g * NM, gc, th, tl), 0.f);
       } else if (far || l == t.L) {

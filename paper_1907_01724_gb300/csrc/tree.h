@@ -48,7 +48,7 @@ struct TreeView {
   int P;                     // multipole order
   int cmin;                  // smallest node that is evaluated through its moments
   float theta;               // opening criterion: a node is far from a target group when
-                             // radius of node <= theta * (centre distance - radius of group)
+                             // radius of node <= theta * (distance of each target from its centre)
   float rfar2;               // (kFarImageRel a)^2
   float inv_a;
 };
