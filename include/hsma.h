@@ -191,15 +191,15 @@ HSMA_API int hsma_last_pair_time(hsma_t* h, float* ms);
  * treecode over the spatial order of the charges: an octree of the charges (and, node by node,
  * of their Kelvin images), multipole moments of the given order (8, 12 or 16) per node, and per
  * group of 32 charges a traversal that takes a node through its moments when
- * node radius <= theta * (centre distance - group radius) and it holds at least
+ * node radius <= theta * (its distance from each charge of the group) and it holds at least
  * (order + 1)^2 / 2 charges, else opens it or sums it directly; Kelvin images farther than 3a
  * from the centre enter through one expansion of order 20 about the centre.  The surface images
  * keep their direct sum.  theta = 0 (the default) restores the direct sum.  Takes effect at the
  * next hsma_build_sources (call this first; it discards the current sources).  With the tree on,
  * hsma_field, hsma_delta_energy and hsma_apply_move return HSMA_E_STATE.  HSMA_E_INVALID_ARG for
  * theta outside [0, 1), another order, or an FP64 handle.  Its error against the direct sum
- * falls with theta and rises with the order; theta = 0.5 with order 12 stays near 1e-7 relative
- * (norm-wise) for charges spread through the cavity. */
+ * falls with theta and rises with the order; theta = 0.5 with order 12 stays below 5e-7 relative
+ * (norm-wise) against the exact sums, uniform or clustered charges. */
 HSMA_API int hsma_set_far_field(hsma_t* h, double theta, int order);
 
 /* Device time in milliseconds of the most recent treecode evaluation (the traversal kernel,
