@@ -118,6 +118,15 @@ def test_tree_sampled_200000():
     assert e_rf <= TOL, ("phi_rf", e_rf)
 
 
+@pytest.mark.parametrize("n", [1, 3, 33, 1001])
+def test_tree_tiny_and_ragged(n):
+    """A handful of charges (one partial group of 32, empty cells everywhere) and ragged tails."""
+    rng = np.random.default_rng(inputs.SEED_BASE + 79 + n)
+    q = inputs.neutral_charges(rng, n) if n > 1 else np.array([1.0])
+    s = inputs.System(1.0, 1.0, 80.0, 1.0, 20, 400, inputs.uniform_ball(rng, n, 1.0), q, name=f"N{n}_tiny")
+    check_full(s)
+
+
 def test_tree_deterministic_and_switch_back():
     """Two tree builds give bitwise equal results; theta = 0 restores the direct path bitwise."""
     s = uniform(20000, 2)
