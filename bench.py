@@ -405,22 +405,24 @@ def run_near_interface(local, stream, gpu_name, steps):
             "l2": "flushed before every timed step (256 MB write)"}
 
 
-def run_far_field(local, stream, steps: int = 5, theta: float = 0.5, order: int = 12):
+def run_far_field(local, stream, steps: int = 5, theta: float = 0.5, order: int = 12, n: int = 1_000_000,
+                  smaller: int | None = 200_000):
     """The paper's N = 1e6 timing workload (Sec. 4.2: p = 20, F1/F2 = 987/1597) with the
     treecode far field (hsma_set_far_field) against the direct pair sum on the same GPU: whole
     build + potential steps from device inputs (L2 flushed before each, CUDA events), the tree's
-    evaluation kernel alone, and the norm-wise difference of the two FP32 results."""
+    evaluation kernel alone, and the norm-wise difference of the two FP32 results; the same at
+    N = `smaller` (its `smaller` entry) for the trend with N."""
     import torch
 
     from paper_1907_01724_gb300 import api, inputs
-    s = inputs.far_field_system()
+    s = inputs.far_field_system(n)
     dev = torch.device(f"cuda:{local}")
     xyz_d = torch.tensor(s.xyz, device=dev)
     q_d = torch.tensor(s.q, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     units = pairs(s)
     res = {"workload": f"1 cavity N={s.n} uniform in a=1, eps1=2, eps2=80, kappa*a=5, p=20, F1/F2=987/1597 "
-                       f"(M={s.M}), tau=0.1 (the paper's N = 1e6 timing workload, Sec. 4.2)",
+                       f"(M={s.M}), tau=0.1 (the paper's timing workload, Sec. 4.2)",
            "pairs_per_step": units}
     phis = {}
     for label, th in (("tree", theta), ("direct", 0.0)):
@@ -453,6 +455,10 @@ def run_far_field(local, stream, steps: int = 5, theta: float = 0.5, order: int 
     res["speedup_vs_direct"] = res["direct"]["ms_per_step"] / res["tree"]["ms_per_step"]
     res["tree_vs_direct_rel_l2"] = float((d @ d) ** 0.5 / (phis["direct"] @ phis["direct"]) ** 0.5)
     res["paper_context"] = "HSMA + FMM, N = 1e6: 24 s on 32 cores of 4x Opteron 6272 (Sec. 4.2); not the target"
+    if smaller:
+        sm = run_far_field(local, stream, steps, theta, order, n=smaller, smaller=None)
+        res["smaller"] = {k: sm[k] for k in ("workload", "tree", "direct", "speedup_vs_direct",
+                                             "tree_vs_direct_rel_l2")}
     return res
 
 

@@ -231,7 +231,10 @@ __global__ __launch_bounds__(32 * kUpWarps) void k_tree_up(TreeView t, int l)
 {
   constexpr int NM = tree_nm(P);
   constexpr int OUT = (NM + 31) / 32;
-  __shared__ float2 sA[kUpWarps][NM], sB[kUpWarps][NM];
+  constexpr int KW = 2 * P + 1;  // k = -P..P
+  // per warp, for the child being shifted: A[j][k] = s^j A_j^k and B[l][t] = conj(B_l^t), dense
+  // over -P <= k, t <= P (entries with |k| > j or |t| > l are never read)
+  __shared__ float2 sAd[kUpWarps][(P + 1) * KW], sBd[kUpWarps][(P + 1) * KW];
   __shared__ float sPow[kUpWarps][P + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long c = (long long)blockIdx.x * kUpWarps + w;
@@ -300,9 +303,8 @@ __global__ __launch_bounds__(32 * kUpWarps) void k_tree_up(TreeView t, int l)
       const float s = kr * irp;
       const float bxv = (kx - cx) * irp, byv = (ky - cy) * irp, bzv = (kz - cz) * irp;
       const float2* Mc = t.mom + (base + g0 + k) * NM;
-      for (int i = lane; i < NM; i += 32) sA[w][i] = Mc[i];
       if (lane <= P) {
-        // column m = lane of R(b), and s^lane
+        // column m = lane of R(b) into B (both signs of t), and s^lane
         const int m = lane;
         const float r2 = bxv * bxv + byv * byv + bzv * bzv;
         float dr = 1.f, di = 0.f;
@@ -312,22 +314,39 @@ __global__ __launch_bounds__(32 * kUpWarps) void k_tree_up(TreeView t, int l)
           di = (dr * byv + di * bxv) * f;
           dr = nr;
         }
-        const int col = tree_col(P, m);
-        sB[w][col] = make_float2(dr, di);
+        const float sgn = (m & 1) ? -1.f : 1.f;
         float p0r = 0.f, p0i = 0.f, p1r = dr, p1i = di;
-        for (int nn = m + 1; nn <= P; ++nn) {
-          const float A = (float)(2 * nn - 1) * bzv;
-          const float inv = 1.f / (float)(nn * nn - m * m);
-          const float qr = (A * p1r - r2 * p0r) * inv, qi = (A * p1i - r2 * p0i) * inv;
-          sB[w][col + nn - m] = make_float2(qr, qi);
-          p0r = p1r;
-          p0i = p1i;
-          p1r = qr;
-          p1i = qi;
+        for (int nn = m; nn <= P; ++nn) {
+          if (nn > m) {
+            const float A = (float)(2 * nn - 1) * bzv;
+            const float inv = 1.f / (float)(nn * nn - m * m);
+            const float qr = (A * p1r - r2 * p0r) * inv, qi = (A * p1i - r2 * p0i) * inv;
+            p0r = p1r;
+            p0i = p1i;
+            p1r = qr;
+            p1i = qi;
+          }
+          // conj(B_nn^m) = (-1)^m conj(R_nn^m); conj(B_nn^-m) = R_nn^m
+          sBd[w][nn * KW + P + m] = make_float2(sgn * p1r, -sgn * p1i);
+          if (m > 0) sBd[w][nn * KW + P - m] = make_float2(p1r, p1i);
         }
         float sp = 1.f;
         for (int j = 0; j < m; ++j) sp *= s;
         sPow[w][m] = sp;
+      }
+      __syncwarp();
+      for (int e = lane; e < (P + 1) * KW; e += 32) {
+        const int j = e / KW, kk = e - j * KW - P;
+        if (kk > j || -kk > j) continue;
+        const int ka = kk >= 0 ? kk : -kk;
+        float2 A = Mc[tree_col(P, ka) + j - ka];
+        if (kk >= 0) {
+          if (kk & 1) A = make_float2(-A.x, -A.y);
+        } else {
+          A.y = -A.y;
+        }
+        const float sj = sPow[w][j];
+        sAd[w][e] = make_float2(sj * A.x, sj * A.y);
       }
       __syncwarp();
 #pragma unroll
@@ -338,31 +357,15 @@ __global__ __launch_bounds__(32 * kUpWarps) void k_tree_up(TreeView t, int l)
         for (int j = 0; j <= n; ++j) {
           const int l2 = n - j;
           const int k0 = max(-j, m - l2), k1 = min(j, m + l2);
-          float tr_ = 0.f, ti_ = 0.f;
+          const float2* Aj = &sAd[w][j * KW + P];
+          const float2* Bl = &sBd[w][l2 * KW + P + m];  // Bl[-kk] = conj(B_{l2}^{m-kk})
           for (int kk = k0; kk <= k1; ++kk) {
-            float2 A;
-            if (kk >= 0) {
-              A = sA[w][tree_col(P, kk) + j - kk];
-              if (kk & 1) A = make_float2(-A.x, -A.y);
-            } else {
-              A = sA[w][tree_col(P, -kk) + j + kk];
-              A.y = -A.y;
-            }
-            const int tt = m - kk;
-            float2 B;  // conj(B_{l2}^{tt})
-            if (tt >= 0) {
-              B = sB[w][tree_col(P, tt) + l2 - tt];
-              B.y = -B.y;
-              if (tt & 1) B = make_float2(-B.x, -B.y);
-            } else {
-              B = sB[w][tree_col(P, -tt) + l2 + tt];
-            }
-            tr_ += A.x * B.x - A.y * B.y;
-            ti_ += A.x * B.y + A.y * B.x;
+            const float2 A = Aj[kk], B = Bl[-kk];
+            ar = fmaf(A.x, B.x, ar);
+            ar = fmaf(-A.y, B.y, ar);
+            ai = fmaf(A.x, B.y, ai);
+            ai = fmaf(A.y, B.x, ai);
           }
-          const float sj = sPow[w][j];
-          ar += sj * tr_;
-          ai += sj * ti_;
         }
         accr[q] += ar;
         acci[q] += ai;
