@@ -192,8 +192,8 @@ HSMA_API int hsma_last_pair_time(hsma_t* h, float* ms);
  * of their Kelvin images), multipole moments of the given order (8, 12 or 16) per node, and per
  * group of 32 charges a traversal that takes a node through its moments when
  * node radius <= theta * (its distance from each charge of the group) and it holds at least
- * (order + 1)^2 / 2 charges, else opens it or sums it directly; Kelvin images farther than 3a
- * from the centre enter through one expansion of order 20 about the centre.  The surface images
+ * (order + 1)^2 / 3 charges, else opens it or sums it directly; Kelvin images farther than 2a
+ * from the centre enter through one expansion of order 24 about the centre.  The surface images
  * keep their direct sum.  theta = 0 (the default) restores the direct sum.  Takes effect at the
  * next hsma_build_sources (call this first; it discards the current sources).  With the tree on,
  * hsma_field, hsma_delta_energy and hsma_apply_move return HSMA_E_STATE.  HSMA_E_INVALID_ARG for
