@@ -244,7 +244,35 @@ def cpu_baselines(systems, quick: bool):
         cpu["single_thread"] = {"value": rate1, "unit": "pair-evals/s", "cores": 1,
                                 "sample": f"whole workload x{rounds1}, {el1:.1f} s"}
         cpu["batched_extrapolated"], cpu["serving_extrapolated"] = oracle_extrapolated(th)
+        cpu["far_field_sampled"] = oracle_far_field_sample(th)
     return refs, cpu
+
+
+_FAR_REF = {}  # sampled oracle potentials of the far-field workload (filled by the CPU leg)
+
+
+def oracle_far_field_sample(th: int, n: int = 1_000_000, samples: int = 500):
+    """The oracle on the far-field workload: its whole source build (Kelvin images, the
+    correction series at the 3M surface points, O(N M p)) and the potentials at `samples` seeded
+    charges (2N + 3M sources each); the far-field section compares the tree with them."""
+    import oracle
+
+    from paper_1907_01724_gb300 import inputs
+    s = inputs.far_field_system(n)
+    P = oracle.make_params(a=s.a, eps1=s.eps1, eps2=s.eps2, kappa=s.kappa, p=s.p, M=s.M, tau=s.tau, nthreads=th)
+    t0 = time.perf_counter()
+    src = oracle.build_sources(P, s.xyz, s.q)
+    tb = time.perf_counter() - t0
+    idx = np.sort(np.random.default_rng(13).choice(s.n, samples, replace=False))
+    t0 = time.perf_counter()
+    pc, pr = oracle.evaluate(P, s.xyz, s.q, src, s.xyz[idx], self_index=idx)
+    te = time.perf_counter() - t0
+    _FAR_REF[n] = (idx, pc + pr)
+    return {"kind": "oracle", "cores": th,
+            "sample": f"N={s.n}: whole source build {tb:.1f} s, then {samples} seeded charges' potentials "
+                      f"against the {2 * s.n + 3 * s.M} sources {te:.2f} s",
+            "value": samples * (2 * s.n - 1 + 3 * s.M) / te, "unit": "pair-evals/s (the sampled potentials)",
+            "build_s": tb}
 
 
 def oracle_extrapolated(th: int):
@@ -454,6 +482,12 @@ def run_far_field(local, stream, steps: int = 5, theta: float = 0.5, order: int 
     d = phis["tree"] - phis["direct"]
     res["speedup_vs_direct"] = res["direct"]["ms_per_step"] / res["tree"]["ms_per_step"]
     res["tree_vs_direct_rel_l2"] = float((d @ d) ** 0.5 / (phis["direct"] @ phis["direct"]) ** 0.5)
+    if n in _FAR_REF:
+        idx, ref = _FAR_REF[n]
+        for label in ("tree", "direct"):
+            e = phis[label][idx] - ref
+            res[label]["rel_l2_vs_oracle_sampled"] = float((e @ e) ** 0.5 / (ref @ ref) ** 0.5)
+        res["oracle_sample"] = f"{len(idx)} seeded charges (the CPU leg's far_field_sampled)"
     res["paper_context"] = "HSMA + FMM, N = 1e6: 24 s on 32 cores of 4x Opteron 6272 (Sec. 4.2); not the target"
     if smaller:
         sm = run_far_field(local, stream, steps, theta, order, n=smaller, smaller=None)
