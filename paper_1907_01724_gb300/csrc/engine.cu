@@ -813,6 +813,7 @@ TreeView Engine::tree_view() const
   t.P = L.tP;
   t.cmin = (L.tP + 1) * (L.tP + 1) / 3;  // ~850 instructions per evaluation against ~16 per pair
   t.theta = (float)far_theta;
+  t.log_eps = (float)(std::log(0.1) + (L.tP + 1) * std::log(far_theta > 0.0 ? far_theta : 0.5));
   const double a = spec[0].a;
   t.rfar2 = (float)((kFarImageRel * a) * (kFarImageRel * a));
   t.inv_a = (float)(1.0 / a);

@@ -533,6 +533,56 @@ __device__ __forceinline__ float m2p(const float2* __restrict__ M, float4 gc, fl
   return acc * ir;
 }
 
+// The same sum row by row (n outer), truncated at a runtime order q <= P: rows n and n - 1 of
+// I_n^m stay in registers, so one code path serves every order (the nodes far beyond the opening
+// criterion need far fewer terms for the same truncation bound).
+template <int P>
+__device__ __forceinline__ float m2p_rows(const float2* __restrict__ M, float4 gc, float4 th, float4 tl, int q)
+{
+  const float ir = 1.f / gc.w;
+  const float ux = ((th.x - gc.x) + tl.x) * ir, uy = ((th.y - gc.y) + tl.y) * ir, uz = ((th.z - gc.z) + tl.z) * ir;
+  const float r2 = ux * ux + uy * uy + uz * uz;
+  const float i2 = __frcp_rn(r2);
+  const float px = ux * i2, py = uy * i2, wz = uz * i2;
+  float ar[P + 1], ai[P + 1], br[P + 1], bi[P + 1];  // rows n - 1 (a) and n - 2 (b)
+#pragma unroll
+  for (int m = 0; m <= P; ++m) ar[m] = ai[m] = br[m] = bi[m] = 0.f;
+  ar[0] = rsqrt_mufu(r2);  // I_0^0
+  float acc0 = __ldg(M).x * ar[0], acc1 = 0.f;  // m = 0 terms, m > 0 terms (weight 2)
+#pragma unroll
+  for (int n = 1; n <= P; ++n) {
+    if (n > q) break;
+    const float A = (float)(2 * n - 1) * wz;
+    // the new diagonal I_n^n from I_{n-1}^{n-1}
+    const float f = (float)(2 * n - 1);
+    const float dr = f * (ar[n - 1] * px - ai[n - 1] * py), di = f * (ar[n - 1] * py + ai[n - 1] * px);
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      const float B = (float)((n - 1) * (n - 1) - m * m) * i2;  // (zero for m = n - 1)
+      const float nr = A * ar[m] - B * br[m], ni = A * ai[m] - B * bi[m];
+      br[m] = ar[m];
+      bi[m] = ai[m];
+      ar[m] = nr;
+      ai[m] = ni;
+      const float2 mm = __ldg(M + tree_col(P, m) + (n - m));
+      if (m == 0) {
+        acc0 = fmaf(mm.x, nr, acc0);
+      } else {
+        acc1 = fmaf(mm.x, nr, acc1);
+        acc1 = fmaf(-mm.y, ni, acc1);
+      }
+    }
+    br[n] = 0.f;
+    bi[n] = 0.f;
+    ar[n] = dr;
+    ai[n] = di;
+    const float2 mm = __ldg(M + tree_col(P, n));
+    acc1 = fmaf(mm.x, dr, acc1);
+    acc1 = fmaf(-mm.y, di, acc1);
+  }
+  return fmaf(2.f, acc1, acc0) * ir;
+}
+
 // phi at the target of the far images' expansion (|x| < a)
 __device__ __forceinline__ float l2p_far(const float2* __restrict__ L, float4 th, float4 tl, float inv_a)
 {
@@ -655,9 +705,19 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
       // target of the group (each lane tests its own target; a margin covers the lo parts)
       const float dx = th.x - gc.x, dy = th.y - gc.y, dz = th.z - gc.z;
       const float rm = gc.w + margin;
-      const bool far = __all_sync(0xffffffffu, rm * rm <= theta2 * fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+      const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      const bool far = __all_sync(0xffffffffu, rm * rm <= theta2 * d2);
       if (far && be.y - be.x >= t.cmin) {
-        acc = acc + two_sum(m2p<P, P>(MM + g * NM, gc, th, tl), 0.f);
+        // the order whose truncation at the group's largest ratio rho/|t - c| stays within a tenth
+        // of the order-P bound at theta: (q + 1) log(ratio) <= log(0.1 theta^(P+1))
+        if constexpr (P <= 12) {
+          const float r2max = warp_max(rm * rm / d2);
+          const int q = min(P, max(2, (int)ceilf(t.log_eps / (0.5f * __logf(r2max))) - 1));
+          acc = acc + two_sum(m2p_rows<P>(MM + g * NM, gc, th, tl, q), 0.f);
+        } else {
+          // (two rows of order 16 do not fit the registers: every node at order P, by columns)
+          acc = acc + two_sum(m2p<P, P>(MM + g * NM, gc, th, tl), 0.f);
+        }
       } else if (far || l == t.L) {
         const bool checked = tr == 0 && be.x < grp * 32 + 32 && be.y > grp * 32;
         p2p(H, Lo, be, th, tl, self, checked, tr == 1, t.rfar2, sh, sl, acc);

@@ -20,7 +20,7 @@ constexpr int kTreeMaxLevel = 7;  // finest node level supported
 constexpr int kFarOrder = 24;     // order of the origin-centred expansion of the far images
 constexpr float kFarImageRel = 2.0f;  // Kelvin images beyond this multiple of a: far images
 constexpr int kTreeEvalWarps = 4;     // warps (persistent target-group workers) per k_tree_eval block
-constexpr int kTreeEvalMinBlocks = 8; // resident k_tree_eval blocks per SM the kernel is built for
+constexpr int kTreeEvalMinBlocks = 6; // resident k_tree_eval blocks per SM the kernel is built for
 constexpr int kTreeStack = 128;       // traversal stack entries per warp
 constexpr int kFarBlocks = 512;       // blocks of k_tree_far
 
@@ -49,6 +49,7 @@ struct TreeView {
   int cmin;                  // smallest node that is evaluated through its moments
   float theta;               // opening criterion: a node is far from a target group when
                              // radius of node <= theta * (distance of each target from its centre)
+  float log_eps;             // log(0.1 theta^(P+1)): the truncation bound of a node's series
   float rfar2;               // (kFarImageRel a)^2
   float inv_a;
 };
