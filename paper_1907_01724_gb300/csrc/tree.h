@@ -20,7 +20,7 @@ constexpr int kTreeMaxLevel = 7;  // finest node level supported
 constexpr int kFarOrder = 24;     // order of the origin-centred expansion of the far images
 constexpr float kFarImageRel = 2.0f;  // Kelvin images beyond this multiple of a: far images
 constexpr int kTreeEvalWarps = 4;     // warps (persistent target-group workers) per k_tree_eval block
-constexpr int kTreeEvalMinBlocks = 6; // resident k_tree_eval blocks per SM the kernel is built for
+constexpr int kTreeEvalMinBlocks = 7; // resident k_tree_eval blocks per SM the kernel is built for
 constexpr int kTreeStack = 128;       // traversal stack entries per warp
 constexpr int kFarBlocks = 512;       // blocks of k_tree_far
 
