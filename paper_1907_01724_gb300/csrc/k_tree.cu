@@ -667,7 +667,7 @@ __device__ __forceinline__ void p2p(const float4* __restrict__ H, const float4* 
 // written to the item's own partial row (chunk tr kTreeRootSplit + rs).
 template <int P>
 __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict__ part, int grp, int tr, int rs,
-                                           int* stk, float4* sh, float4* sl)
+                                           int* stk, int2* sbe, float4* sgc, float4* sh, float4* sl)
 {
   constexpr int NM = tree_nm(P);
   const int lane = threadIdx.x & 31;
@@ -689,18 +689,36 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
     const int self = tr == 0 ? i : -1;
     __syncwarp();
     constexpr int RS = R / kTreeRootSplit;
-    for (int k = lane; k < RS; k += 32) stk[RS - 1 - k] = (kTreeTop << 26) | (rs * RS + k);  // lowest on top
-    int sp = RS;
-    __syncwarp();
+    static_assert(RS <= 32, "a lane per root of an item");
+    int sp = 0;
+    {
+      // the item's roots with sources, the lowest cell on top; a stack entry carries the node's
+      // record range and geometry, read when it is pushed (eight or fewer loads side by side)
+      const long long gr = tree_node_index(kTreeTop, rs * RS + lane);
+      int2 rb = make_int2(0, 0);
+      float4 rgc = make_float4(0.f, 0.f, 0.f, -1.f);
+      if (lane < RS) {
+        rb = t.node[gr];
+        if (rb.y > rb.x) rgc = G[gr];
+      }
+      const unsigned ok = __ballot_sync(0xffffffffu, lane < RS && rb.y > rb.x && rgc.w >= 0.f);
+      if (lane < RS && ((ok >> lane) & 1u)) {
+        const int at = __popc(ok >> (lane + 1));
+        stk[at] = (kTreeTop << 26) | (rs * RS + lane);
+        sbe[at] = rb;
+        sgc[at] = rgc;
+      }
+      sp = __popc(ok);
+      __syncwarp();
+    }
     while (sp > 0) {
-      const int e = stk[--sp];
+      --sp;
+      const int e = stk[sp];
+      const int2 be = sbe[sp];
+      const float4 gc = sgc[sp];
       __syncwarp();  // every lane has read the entry before a push overwrites it
       const int l = e >> 26, c = e & ((1 << 26) - 1);
       const long long g = tree_node_index(l, c);
-      const int2 be = t.node[g];
-      if (be.y <= be.x) continue;
-      const float4 gc = G[g];
-      if (gc.w < 0.f) continue;
       // the node is far when its series converges with ratio rho / |t - c| <= theta at every
       // target of the group (each lane tests its own target; a margin covers the lo parts)
       const float dx = th.x - gc.x, dy = th.y - gc.y, dz = th.z - gc.z;
@@ -722,12 +740,21 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
         const bool checked = tr == 0 && be.x < grp * 32 + 32 && be.y > grp * 32;
         p2p(H, Lo, be, th, tl, self, checked, tr == 1, t.rfar2, sh, sl, acc);
       } else {
-        // open: the non-empty children, the lowest cell on top
+        // open: the children with sources, the lowest cell on top
         const long long gch = tree_node_index(l + 1, 8LL * c);
         int2 cb = make_int2(0, 0);
-        if (lane < 8) cb = t.node[gch + lane];
-        const unsigned ne = __ballot_sync(0xffffffffu, lane < 8 && cb.y > cb.x);
-        if (lane < 8 && ((ne >> lane) & 1u)) stk[sp + __popc(ne >> (lane + 1))] = ((l + 1) << 26) | (8 * c + lane);
+        float4 cg = make_float4(0.f, 0.f, 0.f, -1.f);
+        if (lane < 8) {
+          cb = t.node[gch + lane];
+          if (cb.y > cb.x) cg = G[gch + lane];
+        }
+        const unsigned ne = __ballot_sync(0xffffffffu, lane < 8 && cb.y > cb.x && cg.w >= 0.f);
+        if (lane < 8 && ((ne >> lane) & 1u)) {
+          const int at = sp + __popc(ne >> (lane + 1));
+          stk[at] = ((l + 1) << 26) | (8 * c + lane);
+          sbe[at] = cb;
+          sgc[at] = cg;
+        }
         sp += __popc(ne);
         __syncwarp();
       }
@@ -743,6 +770,8 @@ __global__ __launch_bounds__(32 * kTreeEvalWarps, kTreeEvalMinBlocks) void k_tre
 {
   constexpr int NM = tree_nm(P);
   __shared__ int s_stack[kTreeEvalWarps][kTreeStack];
+  __shared__ int2 s_sbe[kTreeEvalWarps][kTreeStack];
+  __shared__ float4 s_sgc[kTreeEvalWarps][kTreeStack];
   __shared__ float4 s_h[kTreeEvalWarps][32], s_l[kTreeEvalWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const SysDev& S = t.sys[0];
@@ -753,7 +782,7 @@ __global__ __launch_bounds__(32 * kTreeEvalWarps, kTreeEvalMinBlocks) void k_tre
   // cost of an item varies with its distance from the interface and from the centre)
   for (int it = blockIdx.x * kTreeEvalWarps + w; it < items;) {
     const int r = it % IPG;
-    eval_group<P>(t, part, it / IPG, r & 1, r >> 1, s_stack[w], s_h[w], s_l[w]);
+    eval_group<P>(t, part, it / IPG, r & 1, r >> 1, s_stack[w], s_sbe[w], s_sgc[w], s_h[w], s_l[w]);
     int nx = 0;
     if (lane == 0) nx = workers + (int)atomicAdd(t.ctr + 1, 1u);
     it = __shfl_sync(0xffffffffu, nx, 0);
