@@ -537,7 +537,7 @@ __device__ __forceinline__ float m2p(const float2* __restrict__ M, float4 gc, fl
 // I_n^m stay in registers, so one code path serves every order (the nodes far beyond the opening
 // criterion need far fewer terms for the same truncation bound).
 template <int P>
-__device__ __forceinline__ float m2p_rows(const float2* __restrict__ M, float4 gc, float4 th, float4 tl, int q)
+__device__ __forceinline__ float m2p_rows(const float2* M, float4 gc, float4 th, float4 tl, int q)
 {
   const float ir = 1.f / gc.w;
   const float ux = ((th.x - gc.x) + tl.x) * ir, uy = ((th.y - gc.y) + tl.y) * ir, uz = ((th.z - gc.z) + tl.z) * ir;
@@ -548,7 +548,7 @@ __device__ __forceinline__ float m2p_rows(const float2* __restrict__ M, float4 g
 #pragma unroll
   for (int m = 0; m <= P; ++m) ar[m] = ai[m] = br[m] = bi[m] = 0.f;
   ar[0] = rsqrt_mufu(r2);  // I_0^0
-  float acc0 = __ldg(M).x * ar[0], acc1 = 0.f;  // m = 0 terms, m > 0 terms (weight 2)
+  float acc0 = M[0].x * ar[0], acc1 = 0.f;  // m = 0 terms, m > 0 terms (weight 2)
 #pragma unroll
   for (int n = 1; n <= P; ++n) {
     if (n > q) break;
@@ -564,7 +564,7 @@ __device__ __forceinline__ float m2p_rows(const float2* __restrict__ M, float4 g
       bi[m] = ai[m];
       ar[m] = nr;
       ai[m] = ni;
-      const float2 mm = __ldg(M + tree_col(P, m) + (n - m));
+      const float2 mm = M[tree_col(P, m) + (n - m)];
       if (m == 0) {
         acc0 = fmaf(mm.x, nr, acc0);
       } else {
@@ -576,7 +576,7 @@ __device__ __forceinline__ float m2p_rows(const float2* __restrict__ M, float4 g
     bi[n] = 0.f;
     ar[n] = dr;
     ai[n] = di;
-    const float2 mm = __ldg(M + tree_col(P, n));
+    const float2 mm = M[tree_col(P, n)];
     acc1 = fmaf(mm.x, dr, acc1);
     acc1 = fmaf(-mm.y, di, acc1);
   }
@@ -667,7 +667,7 @@ __device__ __forceinline__ void p2p(const float4* __restrict__ H, const float4* 
 // written to the item's own partial row (chunk tr kTreeRootSplit + rs).
 template <int P>
 __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict__ part, int grp, int tr, int rs,
-                                           int* stk, int2* sbe, float4* sgc, float4* sh, float4* sl)
+                                           int* stk, int2* sbe, float4* sgc, float4* sh, float4* sl, float2* smom)
 {
   constexpr int NM = tree_nm(P);
   const int lane = threadIdx.x & 31;
@@ -731,7 +731,12 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
         if constexpr (P <= 12) {
           const float r2max = warp_max(rm * rm / d2);
           const int q = min(P, max(2, (int)ceilf(t.log_eps / (0.5f * __logf(r2max))) - 1));
-          acc = acc + two_sum(m2p_rows<P>(MM + g * NM, gc, th, tl, q), 0.f);
+          // the node's moments staged in shared memory by one coalesced warp load
+          const float2* src = MM + g * NM;
+          for (int i = lane; i < NM; i += 32) smom[i] = __ldg(src + i);
+          __syncwarp();
+          acc = acc + two_sum(m2p_rows<P>(smom, gc, th, tl, q), 0.f);
+          __syncwarp();
         } else {
           // (two rows of order 16 do not fit the registers: every node at order P, by columns)
           acc = acc + two_sum(m2p<P, P>(MM + g * NM, gc, th, tl), 0.f);
@@ -772,6 +777,7 @@ __global__ __launch_bounds__(32 * kTreeEvalWarps, kTreeEvalMinBlocks) void k_tre
   __shared__ int s_stack[kTreeEvalWarps][kTreeStack];
   __shared__ int2 s_sbe[kTreeEvalWarps][kTreeStack];
   __shared__ float4 s_sgc[kTreeEvalWarps][kTreeStack];
+  __shared__ float2 s_mom[kTreeEvalWarps][NM];
   __shared__ float4 s_h[kTreeEvalWarps][32], s_l[kTreeEvalWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const SysDev& S = t.sys[0];
@@ -782,7 +788,7 @@ __global__ __launch_bounds__(32 * kTreeEvalWarps, kTreeEvalMinBlocks) void k_tre
   // cost of an item varies with its distance from the interface and from the centre)
   for (int it = blockIdx.x * kTreeEvalWarps + w; it < items;) {
     const int r = it % IPG;
-    eval_group<P>(t, part, it / IPG, r & 1, r >> 1, s_stack[w], s_sbe[w], s_sgc[w], s_h[w], s_l[w]);
+    eval_group<P>(t, part, it / IPG, r & 1, r >> 1, s_stack[w], s_sbe[w], s_sgc[w], s_h[w], s_l[w], s_mom[w]);
     int nx = 0;
     if (lane == 0) nx = workers + (int)atomicAdd(t.ctr + 1, 1u);
     it = __shfl_sync(0xffffffffu, nx, 0);
