@@ -39,6 +39,18 @@ def host_ptr(a) -> ctypes.c_void_p:
     except (TypeError, ValueError, BufferError):
         return ctypes.c_void_p(a.ctypes.data)
 
+def cached_ptr(cache: dict, slot: str, a) -> ctypes.c_void_p:
+    """host_ptr(a), remembered per call slot while the caller passes the same array object again
+    (a per-step loop's inputs and outputs): the cache keeps a reference to the array, which also
+    keeps numpy from resizing it in place under the remembered address."""
+    ent = cache.get(slot)
+    if ent is not None and ent[0] is a:
+        return ent[1]
+    ptr = host_ptr(a)
+    cache[slot] = (a, ptr)
+    return ptr
+
+
 def _nvcc() -> str:
     for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
         if c and os.path.exists(c):

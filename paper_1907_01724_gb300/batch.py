@@ -104,6 +104,10 @@ class Batch:
             self._check(self.lib.hsma_batch_attach_workspace(self.ptr, ctypes.c_void_p(self.workspace.data_ptr()),
                                                              ctypes.c_size_t(self.workspace.numel())))
 
+    def _ptr(self, slot, a):
+        cache = self.__dict__.setdefault("_ptrs", {})
+        return _native.cached_ptr(cache, slot, a)
+
     def hsma_batch_build_sources(self, n, xyz, q):
         n = _arr(n, np.int64)
         self._ensure_workspace(n)
@@ -115,10 +119,13 @@ class Batch:
             self._check(self.lib.hsma_batch_build_sources_device(self.ptr, _p(n), ctypes.c_void_p(x.data_ptr()),
                                                                  ctypes.c_void_p(qq.data_ptr())))
         else:
-            x = _arr(xyz, np.float64).reshape(-1, 3)
+            x = _arr(xyz, np.float64)
+            if x.ndim != 2:
+                x = x.reshape(-1, 3)
             qq = _arr(q, np.float64)
             self._keep = (x, qq)  # page-locked arrays are read by the next evaluation
-            self._check(self.lib.hsma_batch_build_sources(self.ptr, _p(n), _p(x), _p(qq)))
+            self._check(self.lib.hsma_batch_build_sources(self.ptr, self._ptr("n", n), self._ptr("xyz", x),
+                                                          self._ptr("q", qq)))
         self.n = n
         self._ntot = int(n.sum())
 
@@ -129,7 +136,7 @@ class Batch:
             self._check(self.lib.hsma_batch_potential_device(self.ptr, ctypes.c_void_p(out.data_ptr()), int(what)))
             return out
         phi = _host_out(out, self._ntot)
-        self._check(self.lib.hsma_batch_potential(self.ptr, _p(phi), int(what)))
+        self._check(self.lib.hsma_batch_potential(self.ptr, self._ptr("phi", phi), int(what)))
         return phi
 
     def hsma_batch_set_overlap(self, on: bool):
@@ -144,10 +151,17 @@ class Batch:
         return E
 
     def hsma_batch_energy(self):
-        e = np.empty((2, self.nsys))  # (E_total, E_rf) rows: one buffer, one address lookup
-        p = _p(e).value
-        self._check(self.lib.hsma_batch_energy(self.ptr, ctypes.c_void_p(p), ctypes.c_void_p(p + 8 * self.nsys)))
-        return e[0], e[1]
+        # (E_total, E_rf) rows of one reused buffer (its two addresses computed once); the caller
+        # gets copies
+        buf = self.__dict__.get("_ebuf")
+        if buf is None or buf[0].shape[1] != self.nsys:
+            e = np.empty((2, self.nsys))
+            p = _p(e).value
+            buf = (e, ctypes.c_void_p(p), ctypes.c_void_p(p + 8 * self.nsys))
+            self._ebuf = buf
+        e, p0, p1 = buf
+        self._check(self.lib.hsma_batch_energy(self.ptr, p0, p1))
+        return e[0].copy(), e[1].copy()
 
     def hsma_batch_delta_energy(self, sys, k, x_new):
         sys = _arr(sys, np.int32)
