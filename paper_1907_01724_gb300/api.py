@@ -76,6 +76,7 @@ class Handle:
         self.use_torch_workspace = use_torch_workspace
         self.workspace = None
         self.n = -1
+        self.ptrs = {}  # host addresses per call slot (_native.cached_ptr)
 
     def __del__(self):
         try:
@@ -153,7 +154,8 @@ def hsma_build_sources(h: Handle, xyz, q) -> None:
         if xyz_a.shape[0] != n:
             raise ValueError("xyz and q sizes differ")
         _ensure_workspace(h, n)
-        _check(lib.hsma_build_sources(h.ptr, n, _dptr(xyz_a), _dptr(q_a)), h.ptr)
+        _check(lib.hsma_build_sources(h.ptr, n, _native.cached_ptr(h.ptrs, "xyz", xyz_a),
+                                      _native.cached_ptr(h.ptrs, "q", q_a)), h.ptr)
         h._keep = (xyz_a, q_a)  # page-locked arrays are read by the next evaluation
     h.n = n
 
@@ -172,7 +174,7 @@ def hsma_potential(h: Handle, what: int = HSMA_TOTAL, out=None):
         phi = out
     else:
         phi = np.empty(max(h.n, 0), dtype=np.float64)
-    _check(lib.hsma_potential(h.ptr, _dptr(phi), int(what)), h.ptr)
+    _check(lib.hsma_potential(h.ptr, _native.cached_ptr(h.ptrs, "phi", phi), int(what)), h.ptr)
     return phi
 
 
