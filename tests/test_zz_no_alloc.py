@@ -5,7 +5,8 @@ host application owns all device memory, fixed-budget real-time loops) use
 hsma_coulomb_potential_noalloc, whose scratch memory is a static device array.  This file is
 collected last on purpose.  It checks, through the C ABI, that two calls in a row reproduce
 hsma_potential(..., HSMA_COULOMB) within the FP32 tolerance of the tests (1e-6 norm-wise), up
-to the largest accepted size, and that sizes beyond the maximum are rejected.
+to the largest accepted size, that sizes beyond the maximum are rejected, and that the call
+captures in a CUDA graph and runs without moving the device's free memory.
 """
 import ctypes
 
@@ -69,3 +70,37 @@ def test_noalloc_rejects_sizes_beyond_maximum():
     rc = lib.hsma_coulomb_potential_noalloc(n, ctypes.c_void_p(xyz_d.data_ptr()), ctypes.c_void_p(q_d.data_ptr()),
                                             1.0, ctypes.c_void_p(out.data_ptr()), None)
     assert rc == -1
+
+
+def test_noalloc_captures_in_a_graph_without_allocating():
+    """A call captured in a CUDA graph (global capture mode: no synchronising call may run while
+    the capture is open) replays to the same values, and a call after the first one leaves the
+    device's free memory where it was, at the largest accepted size."""
+    import torch
+    lib = _native.load()
+    s = inputs.near_interface_system(kappa_a=2.0, n=MAX_N)
+    kfac = (1.0 / (4.0 * np.pi)) / s.eps1
+    xyz_d = torch.tensor(s.xyz, device="cuda")
+    q_d = torch.tensor(s.q, device="cuda")
+    eager = torch.full((s.n,), float("nan"), dtype=torch.float64, device="cuda")
+    graphed = torch.full((s.n,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    assert _noalloc(lib, xyz_d, q_d, kfac, eager, stream) == 0  # the warm-up call
+    stream.synchronize()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert _noalloc(lib, xyz_d, q_d, kfac, eager, stream) == 0
+    stream.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+    g = torch.cuda.CUDAGraph()
+    rcs = []
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="global"):
+        rcs.append(_noalloc(lib, xyz_d, q_d, kfac, graphed, stream))
+    assert rcs == [0]
+    expected = eager.cpu()
+    for _ in range(2):
+        graphed.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(graphed.cpu(), expected)
