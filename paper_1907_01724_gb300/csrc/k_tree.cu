@@ -690,6 +690,8 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
     __syncwarp();
     constexpr int RS = R / kTreeRootSplit;
     static_assert(RS <= 32, "a lane per root of an item");
+    // depth first: an opened node leaves at most 8 - 1 more entries, once per level below the roots
+    static_assert(RS + 7 * (kTreeMaxLevel - kTreeTop) <= kTreeStack, "traversal stack depth");
     int sp = 0;
     {
       // the item's roots with sources, the lowest cell on top; a stack entry carries the node's
