@@ -128,12 +128,77 @@ __device__ __forceinline__ float pair_r2(const float4 a, float tx, float ty, flo
   return fmaf(dz, dz, r2);
 }
 
+// Packed FP32 over the target slots 2h and 2h + 1 of a lane (K even): one FFMA2 / FADD2 / FMUL2
+// instruction (sm_100 and later) does an operation for both slots, rounded per component
+// exactly as the scalar operation, so every sum is bitwise that of the scalar form.  The pair
+// sums are issue-bound (the rsqrt, one MUFU operation per pair, stays scalar): packing halves
+// the issue slots of their FP32 part.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+template <int FORM>
+__device__ __forceinline__ float2 pair_r2_x2(const float4 a, float2 tx, float2 ty, float2 tz, float2 c)
+{
+  if (FORM == kFormExp)
+    return __ffma2_rn(tx, bc2(a.x), __ffma2_rn(ty, bc2(a.y), __ffma2_rn(tz, bc2(a.z), __fadd2_rn(bc2(a.w), c))));
+  const float2 h = bc2(0.5f);
+  const float2 dx = __ffma2_rn(h, bc2(a.x), tx), dy = __ffma2_rn(h, bc2(a.y), ty), dz = __ffma2_rn(h, bc2(a.z), tz);
+  float2 r2 = __fmul2_rn(dx, dx);
+  r2 = __ffma2_rn(dy, dy, r2);
+  return __ffma2_rn(dz, dz, r2);
+}
+
+template <int K>
+__device__ __forceinline__ void pack2(const float (&v)[K], float2 (&p)[K / 2])
+{
+#pragma unroll
+  for (int h = 0; h < K / 2; ++h) p[h] = make_float2(v[2 * h], v[2 * h + 1]);
+}
+template <int K>
+__device__ __forceinline__ void unpack2(const float2 (&p)[K / 2], float (&v)[K])
+{
+#pragma unroll
+  for (int h = 0; h < K / 2; ++h) {
+    v[2 * h] = p[h].x;
+    v[2 * h + 1] = p[h].y;
+  }
+}
+
+// One source of a box against the lane's K targets, packed (K even).
+template <int K, int FORM>
+__device__ __forceinline__ void pair_oneway_x2(const float4 a, float q, const float2 (&X)[K / 2],
+                                               const float2 (&Y)[K / 2], const float2 (&Z)[K / 2],
+                                               const float2 (&C)[K / 2], float2 (&A)[K / 2])
+{
+#pragma unroll
+  for (int h = 0; h < K / 2; ++h) {
+    const float2 r2 = pair_r2_x2<FORM>(a, X[h], Y[h], Z[h], C[h]);
+    A[h] = __ffma2_rn(bc2(q), make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y)), A[h]);
+  }
+}
+
 // One-way sums of a box (cnt sources of the warp's buffer) into the lane's K targets.
 template <int K, int FORM>
 __device__ __forceinline__ void box_oneway(const float4* __restrict__ bA, const float* __restrict__ bQ, int cnt,
                                            const float (&tx)[K], const float (&ty)[K], const float (&tz)[K],
                                            const float (&c)[K], float (&acc)[K])
 {
+  if constexpr (K % 2 == 0) {
+    float2 X[K / 2], Y[K / 2], Z[K / 2], C[K / 2], A[K / 2];
+    pack2<K>(tx, X);
+    pack2<K>(ty, Y);
+    pack2<K>(tz, Z);
+    pack2<K>(c, C);
+    pack2<K>(acc, A);
+    if (cnt == kBox) {
+#pragma unroll 4
+      for (int s = 0; s < kBox; ++s) pair_oneway_x2<K, FORM>(bA[s], bQ[s], X, Y, Z, C, A);
+    } else {
+#pragma unroll 2
+      for (int s = 0; s < cnt; ++s) pair_oneway_x2<K, FORM>(bA[s], bQ[s], X, Y, Z, C, A);
+    }
+    unpack2<K>(A, acc);
+    return;
+  }
   if (cnt == kBox) {
 #pragma unroll 4
     for (int s = 0; s < kBox; ++s) {
@@ -160,6 +225,29 @@ __device__ __forceinline__ void box_oneway_checked(const float4* __restrict__ bA
                                                    int cnt, float thr2, const float (&tx)[K], const float (&ty)[K],
                                                    const float (&tz)[K], float (&acc)[K], unsigned (&mk)[K])
 {
+  if constexpr (K % 2 == 0) {
+    float2 X[K / 2], Y[K / 2], Z[K / 2], A[K / 2];
+    pack2<K>(tx, X);
+    pack2<K>(ty, Y);
+    pack2<K>(tz, Z);
+    pack2<K>(acc, A);
+#pragma unroll 4
+    for (int s = 0; s < cnt; ++s) {
+      const float4 a = bA[s];
+      const float q = bQ[s];
+#pragma unroll
+      for (int h = 0; h < K / 2; ++h) {
+        const float2 r2 = pair_r2_x2<kFormMid>(a, X[h], Y[h], Z[h], bc2(0.f));
+        const bool c0 = r2.x < thr2, c1 = r2.y < thr2;
+        if (c0) mk[2 * h] |= 1u << s;
+        if (c1) mk[2 * h + 1] |= 1u << s;
+        const float i0 = rsqrt_mufu(r2.x), i1 = rsqrt_mufu(r2.y);
+        A[h] = __ffma2_rn(bc2(q), make_float2(c0 ? 0.f : i0, c1 ? 0.f : i1), A[h]);
+      }
+    }
+    unpack2<K>(A, acc);
+    return;
+  }
 #pragma unroll 4
   for (int s = 0; s < cnt; ++s) {
     const float4 a = bA[s];
@@ -197,6 +285,39 @@ __device__ __forceinline__ float box_ring(const float4* __restrict__ bA, const f
   float sacc[kRing];
 #pragma unroll
   for (int r = 0; r < kRing; ++r) sacc[r] = 0.f;
+  if constexpr (K % 2 == 0 && kRing == 1) {
+    // packed: the targets' terms two slots per instruction; the transposed sum in slot order
+    float2 X[K / 2], Y[K / 2], Z[K / 2], C[K / 2], AC[K / 2];
+    pack2<K>(tx, X);
+    pack2<K>(ty, Y);
+    pack2<K>(tz, Z);
+    pack2<K>(c, C);
+    pack2<K>(acc, AC);
+    float sa = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < kBox; ++j) {
+      const float4 a = A[j];
+      const float q = Q[j];
+#pragma unroll
+      for (int h = 0; h < K / 2; ++h) {
+        const float2 r2 = pair_r2_x2<FORM>(a, X[h], Y[h], Z[h], C[h]);
+        float i0 = rsqrt_mufu(r2.x), i1 = rsqrt_mufu(r2.y);
+        if (CHECKED) {
+          const bool c0 = r2.x < thr2, c1 = r2.y < thr2;
+          if (c0) mk[2 * h] |= 1u << j;
+          if (c1) mk[2 * h + 1] |= 1u << j;
+          i0 = c0 ? 0.f : i0;
+          i1 = c1 ? 0.f : i1;
+        }
+        AC[h] = __ffma2_rn(bc2(q), make_float2(i0, i1), AC[h]);
+        sa = fmaf(wt[2 * h], i0, sa);
+        sa = fmaf(wt[2 * h + 1], i1, sa);
+      }
+      sa = __shfl_sync(0xffffffffu, sa, (lane + 1) & 31);
+    }
+    unpack2<K>(AC, acc);
+    return sa;
+  }
 #pragma unroll 8
   for (int j0 = 0; j0 < kBox; j0 += kRing) {
 #pragma unroll
@@ -324,23 +445,54 @@ __global__ __launch_bounds__(NT, pair_min_blocks<NT, K>()) void k_pairs_f32(cons
           bQ[lane] = rd;
         }
         __syncwarp();
+        if constexpr (K % 2 == 0) {
+          // packed (slots 2h, 2h + 1); t - y as t + (-y), the same rounding
+          float2 X[K / 2], Y[K / 2], Z[K / 2], A[K / 2];
+          pack2<K>(tx, X);
+          pack2<K>(ty, Y);
+          pack2<K>(tz, Z);
+          pack2<K>(acc, A);
 #pragma unroll 2
-        for (int s = 0; s < cnt; ++s) {
-          const float4 y = bA[s];
-          const float Dp = bQ[s];
+          for (int s = 0; s < cnt; ++s) {
+            const float4 y = bA[s];
+            const float Dp = bQ[s];
+            const float2 yx = bc2(y.x), yy = bc2(y.y), yz = bc2(y.z);
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const float dx = tx[k] - y.x, dy = ty[k] - y.y, dz = tz[k] - y.z;
-            float r2 = dx * dx;
-            r2 = fmaf(dy, dy, r2);
-            r2 = fmaf(dz, dz, r2);
-            const float inv = rsqrt_mufu(r2);
-            float dot = dx * y.x;
-            dot = fmaf(dy, y.y, dot);
-            dot = fmaf(dz, y.z, dot);
-            const float u = dot * (inv * inv);
-            const float v = fmaf(Dp, u, y.w);
-            acc[k] = fmaf(v, inv, acc[k]);
+            for (int h = 0; h < K / 2; ++h) {
+              const float2 dx = __fadd2_rn(X[h], bc2(-y.x)), dy = __fadd2_rn(Y[h], bc2(-y.y)),
+                           dz = __fadd2_rn(Z[h], bc2(-y.z));
+              float2 r2 = __fmul2_rn(dx, dx);
+              r2 = __ffma2_rn(dy, dy, r2);
+              r2 = __ffma2_rn(dz, dz, r2);
+              const float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+              float2 dot = __fmul2_rn(dx, yx);
+              dot = __ffma2_rn(dy, yy, dot);
+              dot = __ffma2_rn(dz, yz, dot);
+              const float2 u = __fmul2_rn(dot, __fmul2_rn(inv, inv));
+              const float2 v = __ffma2_rn(bc2(Dp), u, bc2(y.w));
+              A[h] = __ffma2_rn(v, inv, A[h]);
+            }
+          }
+          unpack2<K>(A, acc);
+        } else {
+#pragma unroll 2
+          for (int s = 0; s < cnt; ++s) {
+            const float4 y = bA[s];
+            const float Dp = bQ[s];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const float dx = tx[k] - y.x, dy = ty[k] - y.y, dz = tz[k] - y.z;
+              float r2 = dx * dx;
+              r2 = fmaf(dy, dy, r2);
+              r2 = fmaf(dz, dz, r2);
+              const float inv = rsqrt_mufu(r2);
+              float dot = dx * y.x;
+              dot = fmaf(dy, y.y, dot);
+              dot = fmaf(dz, y.z, dot);
+              const float u = dot * (inv * inv);
+              const float v = fmaf(Dp, u, y.w);
+              acc[k] = fmaf(v, inv, acc[k]);
+            }
           }
         }
         if ((b + 1) % kFoldBoxes == 0 || b + 1 == nb) {
