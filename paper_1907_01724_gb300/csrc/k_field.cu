@@ -155,7 +155,56 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
       float ap[K], ax[K], ay[K], az[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) ap[k] = ax[k] = ay[k] = az[k] = 0.f;
-      if (ch.type == 2) {
+      if (ch.type == 2 && K % 2 == 0) {
+        // packed FP32 over target slots 2h, 2h + 1 (FFMA2 / FADD2 / FMUL2, each component
+        // rounded as the scalar form below: the same sums, half the FP32 issue slots)
+        constexpr int H = K / 2 > 0 ? K / 2 : 1;
+        float2 X[H], Y[H], Z[H], AP[H], AX[H], AY[H], AZ[H];
+#pragma unroll
+        for (int h = 0; h < K / 2; ++h) {
+          X[h] = make_float2(txh[2 * h], txh[2 * h + 1]);
+          Y[h] = make_float2(tyh[2 * h], tyh[2 * h + 1]);
+          Z[h] = make_float2(tzh[2 * h], tzh[2 * h + 1]);
+          AP[h] = AX[h] = AY[h] = AZ[h] = make_float2(0.f, 0.f);
+        }
+        for (int s = 0; s < cnt; ++s) {
+          const float4 y = A[s];
+          const float Dp = B[s].x;
+          const float Dp3 = 3.f * Dp;
+          const float2 yx = make_float2(y.x, y.x), yy = make_float2(y.y, y.y), yz = make_float2(y.z, y.z);
+          const float2 yw = make_float2(y.w, y.w), dp = make_float2(Dp, Dp), dp3 = make_float2(Dp3, Dp3);
+          const float2 ndp = make_float2(-Dp, -Dp);
+#pragma unroll
+          for (int h = 0; h < K / 2; ++h) {
+            const float2 dx = __fadd2_rn(X[h], make_float2(-y.x, -y.x));
+            const float2 dy = __fadd2_rn(Y[h], make_float2(-y.y, -y.y));
+            const float2 dz = __fadd2_rn(Z[h], make_float2(-y.z, -y.z));
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+            const float2 inv2 = __fmul2_rn(inv, inv);
+            float2 dot = __fmul2_rn(dx, yx);
+            dot = __ffma2_rn(dy, yy, dot);
+            dot = __ffma2_rn(dz, yz, dot);
+            const float2 u = __fmul2_rn(dot, inv2);
+            AP[h] = __ffma2_rn(__ffma2_rn(dp, u, yw), inv, AP[h]);
+            const float2 inv3 = __fmul2_rn(inv, inv2);
+            const float2 c0 = __fmul2_rn(__ffma2_rn(dp3, u, yw), inv3);
+            const float2 c1 = __fmul2_rn(ndp, inv3);
+            AX[h] = __ffma2_rn(c1, yx, __ffma2_rn(c0, dx, AX[h]));
+            AY[h] = __ffma2_rn(c1, yy, __ffma2_rn(c0, dy, AY[h]));
+            AZ[h] = __ffma2_rn(c1, yz, __ffma2_rn(c0, dz, AZ[h]));
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < K / 2; ++h) {
+          ap[2 * h] = AP[h].x; ap[2 * h + 1] = AP[h].y;
+          ax[2 * h] = AX[h].x; ax[2 * h + 1] = AX[h].y;
+          ay[2 * h] = AY[h].x; ay[2 * h + 1] = AY[h].y;
+          az[2 * h] = AZ[h].x; az[2 * h + 1] = AZ[h].y;
+        }
+      } else if (ch.type == 2) {
         for (int s = 0; s < cnt; ++s) {
           const float4 y = A[s];
           const float Dp = B[s].x;
@@ -190,7 +239,49 @@ __global__ __launch_bounds__(NT) void k_field_f32(const SysDev* __restrict__ sys
           const float gx = fmaxf(0.f, fmaxf(wmnx - bmx.x, bmn.x - wmxx));
           const float gy = fmaxf(0.f, fmaxf(wmny - bmx.y, bmn.y - wmxy));
           const float gz = fmaxf(0.f, fmaxf(wmnz - bmx.z, bmn.z - wmxz));
-          if (gx * gx + gy * gy + gz * gz > S.dc2) {
+          if (gx * gx + gy * gy + gz * gz > S.dc2 && K % 2 == 0) {
+            // packed, as the surface sums above
+            constexpr int H = K / 2 > 0 ? K / 2 : 1;
+            float2 X[H], Y[H], Z[H], AP[H], AX[H], AY[H], AZ[H];
+#pragma unroll
+            for (int h = 0; h < K / 2; ++h) {
+              X[h] = make_float2(txh[2 * h], txh[2 * h + 1]);
+              Y[h] = make_float2(tyh[2 * h], tyh[2 * h + 1]);
+              Z[h] = make_float2(tzh[2 * h], tzh[2 * h + 1]);
+              AP[h] = make_float2(ap[2 * h], ap[2 * h + 1]);
+              AX[h] = make_float2(ax[2 * h], ax[2 * h + 1]);
+              AY[h] = make_float2(ay[2 * h], ay[2 * h + 1]);
+              AZ[h] = make_float2(az[2 * h], az[2 * h + 1]);
+            }
+#pragma unroll 2
+            for (int s = u; s < ue; ++s) {
+              const float4 hs = A[s];
+              const float2 hw = make_float2(hs.w, hs.w);
+#pragma unroll
+              for (int h = 0; h < K / 2; ++h) {
+                const float2 dx = __fadd2_rn(X[h], make_float2(-hs.x, -hs.x));
+                const float2 dy = __fadd2_rn(Y[h], make_float2(-hs.y, -hs.y));
+                const float2 dz = __fadd2_rn(Z[h], make_float2(-hs.z, -hs.z));
+                float2 r2 = __fmul2_rn(dx, dx);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                const float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+                const float2 qi = __fmul2_rn(hw, inv);
+                AP[h] = __fadd2_rn(AP[h], qi);
+                const float2 c = __fmul2_rn(qi, __fmul2_rn(inv, inv));
+                AX[h] = __ffma2_rn(c, dx, AX[h]);
+                AY[h] = __ffma2_rn(c, dy, AY[h]);
+                AZ[h] = __ffma2_rn(c, dz, AZ[h]);
+              }
+            }
+#pragma unroll
+            for (int h = 0; h < K / 2; ++h) {
+              ap[2 * h] = AP[h].x; ap[2 * h + 1] = AP[h].y;
+              ax[2 * h] = AX[h].x; ax[2 * h + 1] = AX[h].y;
+              ay[2 * h] = AY[h].x; ay[2 * h + 1] = AY[h].y;
+              az[2 * h] = AZ[h].x; az[2 * h + 1] = AZ[h].y;
+            }
+          } else if (gx * gx + gy * gy + gz * gz > S.dc2) {
 #pragma unroll 2
             for (int s = u; s < ue; ++s) {
               const float4 h = A[s];
