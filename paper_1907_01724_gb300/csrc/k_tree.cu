@@ -544,43 +544,39 @@ __device__ __forceinline__ float m2p_rows(const float2* M, float4 gc, float4 th,
   const float r2 = ux * ux + uy * uy + uz * uz;
   const float i2 = __frcp_rn(r2);
   const float px = ux * i2, py = uy * i2, wz = uz * i2;
-  float ar[P + 1], ai[P + 1], br[P + 1], bi[P + 1];  // rows n - 1 (a) and n - 2 (b)
+  // rows n - 1 (a) and n - 2 (b) as (re, im) pairs: the recurrence's complex-by-real products
+  // and the dot product with the (re, -im) moments as packed FP32 (FFMA2 / FMUL2)
+  float2 a[P + 1], b[P + 1];
 #pragma unroll
-  for (int m = 0; m <= P; ++m) ar[m] = ai[m] = br[m] = bi[m] = 0.f;
-  ar[0] = rsqrt_mufu(r2);  // I_0^0
-  float acc0 = M[0].x * ar[0], acc1 = 0.f;  // m = 0 terms, m > 0 terms (weight 2)
+  for (int m = 0; m <= P; ++m) a[m] = b[m] = make_float2(0.f, 0.f);
+  a[0].x = rsqrt_mufu(r2);  // I_0^0
+  float acc0 = M[0].x * a[0].x;       // m = 0 terms
+  float2 acc1 = make_float2(0.f, 0.f);  // m > 0 terms (weight 2): the re re and -im im parts
 #pragma unroll
   for (int n = 1; n <= P; ++n) {
     if (n > q) break;
     const float A = (float)(2 * n - 1) * wz;
+    const float2 A2 = make_float2(A, A);
     // the new diagonal I_n^n from I_{n-1}^{n-1}
     const float f = (float)(2 * n - 1);
-    const float dr = f * (ar[n - 1] * px - ai[n - 1] * py), di = f * (ar[n - 1] * py + ai[n - 1] * px);
+    const float dr = f * (a[n - 1].x * px - a[n - 1].y * py), di = f * (a[n - 1].x * py + a[n - 1].y * px);
 #pragma unroll
     for (int m = 0; m < n; ++m) {
-      const float B = (float)((n - 1) * (n - 1) - m * m) * i2;  // (zero for m = n - 1)
-      const float nr = A * ar[m] - B * br[m], ni = A * ai[m] - B * bi[m];
-      br[m] = ar[m];
-      bi[m] = ai[m];
-      ar[m] = nr;
-      ai[m] = ni;
+      const float nB = (float)(m * m - (n - 1) * (n - 1)) * i2;  // -B (zero for m = n - 1)
+      const float2 nv = __ffma2_rn(make_float2(nB, nB), b[m], __fmul2_rn(A2, a[m]));
+      b[m] = a[m];
+      a[m] = nv;
       const float2 mm = M[tree_col(P, m) + (n - m)];
-      if (m == 0) {
-        acc0 = fmaf(mm.x, nr, acc0);
-      } else {
-        acc1 = fmaf(mm.x, nr, acc1);
-        acc1 = fmaf(-mm.y, ni, acc1);
-      }
+      if (m == 0)
+        acc0 = fmaf(mm.x, nv.x, acc0);
+      else
+        acc1 = __ffma2_rn(mm, nv, acc1);
     }
-    br[n] = 0.f;
-    bi[n] = 0.f;
-    ar[n] = dr;
-    ai[n] = di;
-    const float2 mm = M[tree_col(P, n)];
-    acc1 = fmaf(mm.x, dr, acc1);
-    acc1 = fmaf(-mm.y, di, acc1);
+    b[n] = make_float2(0.f, 0.f);
+    a[n] = make_float2(dr, di);
+    acc1 = __ffma2_rn(M[tree_col(P, n)], a[n], acc1);
   }
-  return fmaf(2.f, acc1, acc0) * ir;
+  return fmaf(2.f, acc1.x + acc1.y, acc0) * ir;
 }
 
 // phi at the target of the far images' expansion (|x| < a)
@@ -735,7 +731,10 @@ __device__ __forceinline__ void eval_group(const TreeView& t, float2* __restrict
           const int q = min(P, max(2, (int)ceilf(t.log_eps / (0.5f * __logf(r2max))) - 1));
           // the node's moments staged in shared memory by one coalesced warp load
           const float2* src = MM + g * NM;
-          for (int i = lane; i < NM; i += 32) smom[i] = __ldg(src + i);
+          for (int i = lane; i < NM; i += 32) {
+            const float2 v = __ldg(src + i);
+            smom[i] = make_float2(v.x, -v.y);  // (re, -im): the series' dot product as FFMA2
+          }
           __syncwarp();
           acc = acc + two_sum(m2p_rows<P>(smom, gc, th, tl, q), 0.f);
           __syncwarp();
